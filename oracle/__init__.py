@@ -1,0 +1,39 @@
+"""FP64 CPU oracle of the wavefront-sensor forward model.
+
+TEST INFRASTRUCTURE ONLY.  Nothing in the product path imports this package:
+it may be used by ``tests/``, by ``__graft_entry__.smoke()`` (to check one
+small GPU invocation) and by ``bench.py``'s CPU-baseline / reference legs.  It
+shares no code, table or constant generator with the CUDA library; the only
+code both sides use is the seeded input generator package ``synth``.
+
+The paper (a framework paper) names the processing objects of the hot path
+(App. A, Tab. 4: AtmoEvolution, AtmoPropagation, ModulatedPyramid, SH, CCD,
+PyrSlopec, ShSlopec, Modalrec, ImCalibrator, RecCalibrator) and their
+parameters (App. B, Listing 2) but prints no equation for them.  This oracle
+writes the textbook physics of those objects out in plain NumPy, in float64,
+with ``numpy.fft`` (pocketfft) as the only library primitive for the
+transforms.  Every reading of a point the paper leaves open is stated in the
+docstring of the function that makes it.
+
+Modules and their pins (tests/test_oracle_*.py):
+
+* ``dft``       centred DFT; pinned to a brute-force O(n^4) sum.
+* ``geometry``  pupil stop, valid subapertures, quadrant index maps,
+                modulation angles; pinned to hand-counted tiny cases and to
+                symmetry counts.
+* ``screens``   von Karman FFT screens with subharmonics; pinned to the exact
+                ensemble structure function, the Kolmogorov 5/3 law and the
+                phase variance.
+* ``atmo``      frozen-flow layer extraction; pinned to exact rolls, linear
+                ramps (bilinear reproduces them) and the zero-height on-axis
+                identity.
+* ``pyramid``   modulated pyramid intensity and binning; pinned to Parseval
+                flux, mirror/transpose symmetries, equal quadrant flux, tilt
+                antisymmetry, and the unit-mask identity.
+* ``sh``        Shack-Hartmann spots; pinned to zero centroid for a flat
+                wavefront, exact circular roll under an integer tilt, and
+                per-subaperture Parseval flux.
+* ``slopes``    pyramid and centre-of-gravity slopes; pinned through the
+                pyramid / SH invariants above and hand-computed detectors.
+* ``recon``     modal reconstructor MVM; pinned to a direct sum.
+"""

@@ -1,0 +1,82 @@
+"""Integer geometry of the sensors: pupil stop, valid subapertures, index maps,
+and the modulation-point angle table.
+
+Follows the data objects PupilStop, PupData and SubapData (App. A, Tab. 3) and
+the calibrators PyrPupdataCalibrator / ShSubapCalibrator (App. A, Tab. 4).  The
+paper selects valid pupil pixels with a flux threshold on a calibration image
+(App. B, Listing 2, the ``th0.30`` tag of ``pupdata_object``); the calibration
+data are not public, so this oracle uses the geometric reading below, which is
+exact in integers.
+"""
+import math
+
+import numpy as np
+
+
+def pupil_mask(n_pix: int, obsc_frac: float) -> np.ndarray:
+    """Circular pupil stop with a central obscuration, (n_pix, n_pix) uint8.
+
+    Pixel (j, i) (row j, column i) has doubled centred coordinates
+    (2i - n + 1, 2j - n + 1); it is inside iff
+        r4 = (2i - n + 1)^2 + (2j - n + 1)^2 <= n^2   and   r4 > (obsc * n)^2.
+    r4 and n^2 are integers; the obscuration bound is the float64 product
+    e * e with e = obsc * n.
+    """
+    n = int(n_pix)
+    idx = 2 * np.arange(n, dtype=np.int64) - n + 1
+    r4 = idx[None, :] ** 2 + idx[:, None] ** 2
+    e = float(obsc_frac) * n
+    thr = e * e
+    inside = (r4 <= n * n) & (r4.astype(np.float64) > thr)
+    return inside.astype(np.uint8)
+
+
+def valid_subaps(mask: np.ndarray, n_sub: int) -> np.ndarray:
+    """Valid subapertures of an n_sub x n_sub grid over the pupil stop.
+
+    A subaperture of b x b pupil pixels (b = n_pix / n_sub) is valid iff at
+    least half of its pixels are inside the stop: 2 * count >= b^2.  Returns
+    int32 linear indices a * n_sub + b_col in row-major (row a first) order.
+    """
+    n = mask.shape[0]
+    assert n % n_sub == 0
+    b = n // n_sub
+    counts = mask.reshape(n_sub, b, n_sub, b).sum(axis=(1, 3)).astype(np.int64)
+    ok = 2 * counts >= b * b
+    return np.flatnonzero(ok.ravel()).astype(np.int32)
+
+
+def pyr_quadrant_index(valid: np.ndarray, n_sub: int) -> np.ndarray:
+    """Detector linear indices of the four pupil images of each subaperture.
+
+    The detector is 2 n_sub x 2 n_sub (row = y).  The pyramid face (+x, +y)
+    images the pupil into the quadrant of larger row and column indices, and
+    so on; subaperture (a, b) lands at the same (a, b) inside each quadrant:
+        Q1 (+x,+y): (n_sub + a, n_sub + b)    Q2 (-x,+y): (n_sub + a, b)
+        Q3 (-x,-y): (a, b)                     Q4 (+x,-y): (a, n_sub + b)
+    Returns int32 (4, n_valid): rows Q1..Q4.
+    """
+    a = valid // n_sub
+    bb = valid % n_sub
+    w = 2 * n_sub
+    q1 = (n_sub + a) * w + (n_sub + bb)
+    q2 = (n_sub + a) * w + bb
+    q3 = a * w + bb
+    q4 = a * w + (n_sub + bb)
+    return np.stack([q1, q2, q3, q4]).astype(np.int32)
+
+
+def mod_angles(n_mod: int):
+    """Modulation points: theta_m = (2 pi m) / n_mod, m = 0..n_mod-1, counter-
+    clockwise from +x (ModulatedPyramid ``mod_amp``, App. B, Listing 2).
+
+    Returns float64 arrays (cos theta_m, sin theta_m), each from the C
+    library's cos/sin on the same float64 argument ((2 * pi) * m) / n_mod.
+    """
+    c = np.empty(n_mod)
+    s = np.empty(n_mod)
+    for m in range(n_mod):
+        th = 2.0 * math.pi * m / n_mod
+        c[m] = math.cos(th)
+        s[m] = math.sin(th)
+    return c, s

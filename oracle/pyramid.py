@@ -1,0 +1,73 @@
+"""Modulated four-face pyramid wavefront sensor (FP64).
+
+Follows ModulatedPyramid (App. A, Tab. 4) with the parameters of App. B,
+Listing 2 (``pup_diam``, ``pup_dist``, ``mod_amp`` in lambda/D,
+``output_resolution``) and the CCD integration with noise off (Listing 2:
+``photon_noise``/``readout_noise`` False).  Step order per frame, for each
+modulation point m = 0..n_mod-1:
+
+  1. tilt:  E_m(x, y) = A exp(i phi) exp(2 pi i r (x cos t_m + y sin t_m) / Np)
+     with x, y the centred pupil coordinates in pixels and r = ``mod_amp``
+     (a tilt of r cycles across the pupil moves the focal spot by r lambda/D);
+  2. pad:   place E_m centred in an N x N zero grid, N = pad * Np;
+  3. FFT:   F = centred forward DFT (unnormalised);
+  4. mask:  F(u, v) *= exp(-2 pi i c (|u| + |v|) / N), c = pup_dist / 2, so each
+            face adds the tilt that moves its pupil image by (+-c, +-c) pixels;
+            the (+, +) face images into the (+x, +y) quadrant;
+  5. IFFT:  O = centred inverse DFT (1/N^2);
+  6. accumulate I += |O|^2 / n_mod.
+Then the N x N intensity is binned in b x b blocks, b = Np / n_sub, to the
+2 n_sub x 2 n_sub detector.
+
+Readings (the paper prints no formula): centred grids (see ``dft``); amplitude
+1 per in-pupil pixel, so the detector sums to the number of pupil pixels;
+pup_dist = Np so the four images tile the padded grid exactly.
+"""
+import numpy as np
+
+from .dft import centred_coords, centred_dft2, centred_idft2
+from .geometry import mod_angles
+
+
+def pyramid_mask(N: int, pup_dist: float) -> np.ndarray:
+    """exp(-2 pi i c (|u| + |v|) / N) on the centred N x N frequency grid."""
+    c = pup_dist / 2.0
+    u = np.abs(centred_coords(N))
+    m1 = np.exp(-2j * np.pi * c * u / N)
+    return m1[:, None] * m1[None, :]
+
+
+def pwfs_intensity(amp: np.ndarray, phase: np.ndarray, pad: int, n_mod: int,
+                   mod_amp: float, pup_dist: float, mask=None) -> np.ndarray:
+    """Modulation-averaged N x N intensity (steps 1-6)."""
+    Np = amp.shape[0]
+    N = pad * Np
+    off = (N - Np) // 2
+    x = centred_coords(Np)
+    E = amp * np.exp(1j * phase)
+    M = pyramid_mask(N, pup_dist) if mask is None else mask
+    cs, sn = mod_angles(n_mod)
+    I = np.zeros((N, N))
+    for m in range(n_mod):
+        tilt = np.exp(2j * np.pi * mod_amp
+                      * (x[None, :] * cs[m] + x[:, None] * sn[m]) / Np)
+        P = np.zeros((N, N), dtype=np.complex128)
+        P[off:off + Np, off:off + Np] = E * tilt
+        O = centred_idft2(centred_dft2(P) * M)
+        I += np.abs(O) ** 2
+    return I / n_mod
+
+
+def bin_image(I: np.ndarray, b: int) -> np.ndarray:
+    """Sum of b x b blocks (CCD binning, noise off)."""
+    n = I.shape[0]
+    assert n % b == 0
+    k = n // b
+    return I.reshape(k, b, k, b).sum(axis=(1, 3))
+
+
+def pwfs_image(amp, phase, pad, n_mod, mod_amp, n_sub, pup_dist):
+    """Detector image 2 n_sub x 2 n_sub (with pad = 2 and pup_dist = Np)."""
+    Np = amp.shape[0]
+    I = pwfs_intensity(amp, phase, pad, n_mod, mod_amp, pup_dist)
+    return bin_image(I, Np // n_sub)
