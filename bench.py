@@ -1,0 +1,405 @@
+"""Pyramid-WFS frames/s at ELT scale on GB300, with the roofline of the
+dominant kernel and the FP64 oracle timed on the host cores as a baseline.
+
+One step = one frame of the 39 m single-pyramid system (480 px pupil, 960^2
+FFT, 48 modulation points, 96 x 96 subapertures, 35 layers, 4000-mode MVM):
+layer extraction -> modulated pyramid image -> slopes -> reconstructor,
+through the C ABI of libspecula_gb300.  Inputs are resident in HBM before
+the timed region; L2 is flushed (a 256 MB write) between timed frames, outside
+the frame's CUDA events.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl specula|reference]
+
+Under torchrun each rank runs an independent replica (its own seeded
+atmosphere); value = frames of all ranks / max over ranks of the timed span.
+"""
+import argparse
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "pwfs39m"
+METRIC = "pyramid-WFS frames/s (ELT scale) + roofline %, mixed vs plain FP32 at stated err"
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def fp32_peak_tflops(sm_mhz):
+    # 152 SMs x 128 FP32 lanes x 2 flops per FMA x clock
+    return SM_COUNT * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+
+
+def fft_flops(n):
+    return 5.0 * n * math.log2(n)
+
+
+def kernel_flops(wl):
+    """Algorithmic FLOPs per (batch, modulation point) item of each pyramid
+    pass (benchFFT convention 5 N log2 N per N-point transform, pruned inputs
+    counted as full transforms; element-wise work not counted)."""
+    s = wl.sensors[0]
+    n = s.pupil.n_pix
+    N = s.pwfs.pad * n
+    return {"pwfs_rows_fwd": n * fft_flops(N),
+            "pwfs_cols": 2 * N * fft_flops(N),
+            "pwfs_rows_inv": N * fft_flops(N)}
+
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is None:
+            return
+        time.sleep(0.3)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                smax.append(float(f[1]))
+            except ValueError:
+                continue
+            for k, name in enumerate(names):
+                if f[3 + k].lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def read_traffic():
+    """dram bytes per launch of the dominant kernel from the committed ncu
+    summary (a line 'traffic_bytes_per_launch <kernel> <workload> <bytes>')."""
+    out = {}
+    d = os.path.join(ROOT, "profiles")
+    if not os.path.isdir(d):
+        return out
+    for f in os.listdir(d):
+        if not f.endswith((".txt", ".md")):
+            continue
+        for line in open(os.path.join(d, f)):
+            m = re.match(r"\s*traffic_bytes_per_launch\s+(\S+)\s+(\S+)\s+([0-9.eE+]+)", line)
+            if m:
+                out[(m.group(1), m.group(2))] = float(m.group(3))
+    return out
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ------------------------------------------------------------------ CPU oracle
+
+class OracleSample:
+    """The FP64 oracle on one frame of the ELT workload: all 35 layers
+    extracted, n_mod_timed of the 48 modulation points imaged (time scaled to
+    48), slopes and the 4000-mode MVM.  Two oracle screens are cycled over the
+    35 layers (the timing does not depend on screen values)."""
+
+    def __init__(self, n_mod_timed=4):
+        import synth
+        from oracle import geometry, pyramid, screens
+        wl = synth.workload(WORKLOAD)
+        s = wl.sensors[0]
+        self.wl, self.s, self.n = wl, s, s.pupil.n_pix
+        base = [screens.fft_screen(l.side, l.pitch_m, l.r0_m, l.L0_m,
+                                   synth.screen_noise(l.seed, l.side),
+                                   synth.subharmonic_noise(l.seed)).astype(np.float32)
+                for l in wl.layers[:2]]
+        self.scr = [base[k % 2].astype(np.float64) for k in range(len(wl.layers))]
+        self.amp = geometry.pupil_mask(self.n, s.pupil.obsc_frac).astype(np.float64)
+        self.valid = geometry.valid_subaps(self.amp.astype(np.uint8), s.pwfs.n_sub)
+        ns = 2 * len(self.valid)
+        self.R = synth.normal_draws(7, (wl.n_modes, ns)) / np.sqrt(ns)
+        self.mask = pyramid.pyramid_mask(2 * self.n, self.n)
+        self.n_mod_timed = n_mod_timed
+        self.desc = (f"one {WORKLOAD} frame: 35-layer extraction + {n_mod_timed} of "
+                     f"{s.pwfs.n_mod} modulation points (time scaled x"
+                     f"{s.pwfs.n_mod // n_mod_timed}) + slopes + {wl.n_modes}x{ns} MVM; "
+                     f"FP64 NumPy oracle, single process")
+
+    def step(self, t=0.001):
+        """Seconds of oracle work for one full frame (scaled as described)."""
+        from oracle import atmo, geometry, pyramid, recon, slopes
+        from oracle.dft import centred_coords, centred_dft2, centred_idft2
+        s, n = self.s, self.n
+        t0 = time.perf_counter()
+        phi = atmo.atmo_extract(self.scr, self.wl.layers, s.source, n, s.pupil.pitch_m, t)
+        t1 = time.perf_counter()
+        cs, sn = geometry.mod_angles(s.pwfs.n_mod)
+        stride = s.pwfs.n_mod // self.n_mod_timed
+        N = 2 * n
+        off = (N - n) // 2
+        x = centred_coords(n)
+        E = self.amp * np.exp(1j * phi)
+        I = np.zeros((N, N))
+        for m in range(0, s.pwfs.n_mod, stride):
+            tilt = np.exp(2j * np.pi * s.pwfs.mod_amp
+                          * (x[None, :] * cs[m] + x[:, None] * sn[m]) / n)
+            P = np.zeros((N, N), dtype=np.complex128)
+            P[off:off + n, off:off + n] = E * tilt
+            I += np.abs(centred_idft2(centred_dft2(P) * self.mask)) ** 2
+        t2 = time.perf_counter()
+        det = pyramid.bin_image(I / self.n_mod_timed, n // s.pwfs.n_sub)
+        sl = slopes.pyr_slopes(det, s.pwfs.n_sub, self.valid)
+        recon.mvm(self.R, sl)
+        t3 = time.perf_counter()
+        return (t1 - t0) + (t2 - t1) * (s.pwfs.n_mod / self.n_mod_timed) + (t3 - t2)
+
+
+def cpu_cores_used():
+    # NumPy's pocketfft and the oracle loops run on one thread
+    return 1
+
+
+def reference_leg(args, ws, rank):
+    if rank != 0:
+        return
+    sample = OracleSample()
+    desc = sample.desc
+    times = []
+    for k in range(args.warmup + args.steps):
+        t = sample.step(0.001 * (k + 1))
+        if k >= args.warmup:
+            times.append(t)
+    per = sum(times) / len(times)
+    value = 1.0 / per
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "frames/s",
+            "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": per * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": desc},
+            "cpu_baseline": {"value": value, "unit": "frames/s", "cores": cpu_cores_used(),
+                             "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": "frames/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU leg
+
+def gpu_leg(args, ws, rank, local):
+    import torch
+    from paper_2602_06688_gb300 import build
+    build.build()
+    import paper_2602_06688_gb300 as sp
+    from paper_2602_06688_gb300.frame import PwfsFrame
+    import synth
+
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    wl = synth.workload(WORKLOAD)
+    ctx = sp.Context(local)
+    fr = PwfsFrame(ctx, wl, seed_offset=1000 * rank)
+    dt = wl.dt_s
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
+    K, W = args.steps, args.warmup
+
+    def timed(nsteps, t0_step, with_flush=True):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(nsteps)]
+        for k in range(nsteps):
+            if with_flush:
+                flush.zero_()
+            ev[k][0].record()
+            fr.frame((t0_step + k) * dt)
+            ev[k][1].record()
+        torch.cuda.synchronize()
+        return [a.elapsed_time(b) for a, b in ev]
+
+    for k in range(W):
+        fr.frame(k * dt)
+    torch.cuda.synchronize()
+
+    # ---- headline: plain FP32 path
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    n0 = sp.specula_launch_count(ctx)
+    with ClockSampler(local) as clk:
+        wall0 = time.perf_counter()
+        ms = timed(K, W)
+        wall1 = time.perf_counter()
+    launches = sp.specula_launch_count(ctx) - n0
+    total_ms = sum(ms)
+    if dist:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / K
+    value = ws * K / (total_ms / 1e3)
+    fp32_modes = fr.modes.clone()
+    fp32_slopes = fr.slopes.clone()
+
+    # ---- precision variants of the reconstructor (same frame otherwise)
+    variants = {}
+    R64 = fr.R.double()
+    ref_modes = (R64 @ fp32_slopes.double())
+    for name, prec in (("fp32", sp.PREC_FP32), ("bf16x2", sp.PREC_BF16X2), ("bf16", sp.PREC_BF16)):
+        fr.set_precision(prec)
+        for k in range(3):
+            fr.frame((W + K + k) * dt)
+        msv = timed(K, W)
+        # modal error of this reconstructor on the FP32 slopes, vs FP64 R s
+        out = torch.empty_like(fr.modes)
+        sp.specula_recon(ctx, fr.rec, fp32_slopes, out)
+        torch.cuda.synchronize()
+        err = float(torch.linalg.vector_norm(out.double() - ref_modes) /
+                    torch.linalg.vector_norm(ref_modes))
+        variants[name] = {"frames_per_s": K / (sum(msv) / 1e3), "ms_per_step": sum(msv) / K,
+                          "modal_rel_rms_err_vs_fp64": err}
+    fr.set_precision(sp.PREC_FP32)
+
+    # ---- live per-kernel roofline (library event tracing on the launch stream)
+    sp.specula_prof_enable(ctx, 64 * (K + 4))
+    timed(K, W)
+    prof = sp.specula_prof_read(ctx)
+    sp.specula_prof_enable(ctx, 0)
+    pk, how = peaks()
+    flops = kernel_flops(wl)
+    n_items = wl.sensors[0].pwfs.n_mod * K
+    kern = {}
+    for name, (tms, n) in prof.items():
+        kern[name] = {"total_ms": tms, "launches": n, "share": 0.0}
+    tot = sum(v["total_ms"] for v in kern.values())
+    for v in kern.values():
+        v["share"] = v["total_ms"] / tot if tot else 0.0
+    dom = max(kern, key=lambda k: kern[k]["total_ms"])
+    clocks = clk.summary()
+    sm_max = (clocks or {}).get("sm_max_mhz") or pk.get("sm_max_mhz", 2070.0)
+    peak_alu = fp32_peak_tflops(sm_max)
+    roof = None
+    traffic = read_traffic()
+    if dom in flops:
+        achieved = flops[dom] * n_items / (kern[dom]["total_ms"] / 1e3) / 1e12
+        tr = traffic.get((dom, WORKLOAD))
+        roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak_alu,
+                "unit": "TFLOP/s", "frac": achieved / peak_alu,
+                "traffic": tr * 1.0 if tr is not None else None,
+                "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz (derived)",
+                "flops_per_launch": flops[dom] * n_items / kern[dom]["launches"]}
+    for name in flops:
+        if name in kern:
+            kern[name]["achieved_tflops"] = flops[name] * n_items / (kern[name]["total_ms"] / 1e3) / 1e12
+    if "recon" in kern:
+        rb = fr.n_modes * fr.n_slopes * 4.0
+        gbs = rb * kern["recon"]["launches"] / (kern["recon"]["total_ms"] / 1e3) / 1e9
+        kern["recon"]["achieved_gbs"] = gbs
+        kern["recon"]["hbm_frac"] = gbs / pk["hbm_gbs"]
+
+    # ---- end to end through the public API with host buffers
+    t_host = torch.empty(1, dtype=torch.float64).pin_memory()
+    t_dev = torch.empty(1, dtype=torch.float64, device="cuda")
+    modes_host = torch.empty(fr.n_modes, dtype=torch.float32).pin_memory()
+    torch.cuda.synchronize()
+    e0 = time.perf_counter()
+    for k in range(K):
+        t_host[0] = (W + k) * dt
+        t_dev.copy_(t_host, non_blocking=True)
+        fr.frame(0.0, t_dev=t_dev)
+        modes_host.copy_(fr.modes, non_blocking=True)
+        torch.cuda.synchronize()
+    e1 = time.perf_counter()
+    e2e = ws * K / (e1 - e0)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": ws,
+                "steps": K, "warmup": W, "ms_per_step": ms_per_step,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32", "data": "synthetic (seeded von Karman screens, seeded stand-in R)",
+                "config": {"workload": WORKLOAD, "pupil_px": 480, "fft": 960, "n_mod": 48,
+                           "n_sub": 96, "layers": 35, "n_modes": fr.n_modes,
+                           "n_slopes": fr.n_slopes, "l2": "flushed between timed frames",
+                           "wall_ms_per_step_incl_flush": (wall1 - wall0) * 1e3 / K},
+                "roofline": roof, "kernels": kern, "variants": variants,
+                "e2e": {"value": e2e, "unit": "frames/s", "h2d_bytes_per_step": 8,
+                        "d2h_bytes_per_step": 4 * fr.n_modes,
+                        "note": "per step: pinned host time -> device, frame, modes -> pinned host, sync"},
+                "gpu_launches": launches, "clocks": clocks,
+                "peaks": {"source": how, "hbm_gbs": pk.get("hbm_gbs")}}
+        if not args.no_cpu_baseline:
+            sample = OracleSample()
+            per = min(sample.step(0.001 * (k + 1)) for k in range(3))
+            desc = sample.desc + ", best of 3"
+            line["cpu_baseline"] = {"value": 1.0 / per, "unit": "frames/s",
+                                    "cores": cpu_cores_used(), "kind": "oracle", "sample": desc}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="specula", choices=["specula", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    ws, rank, local = dist_setup()
+    if args.impl == "reference":
+        reference_leg(args, ws, rank)
+        return
+    gpu_leg(args, ws, rank, local)
+
+
+if __name__ == "__main__":
+    main()

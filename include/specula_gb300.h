@@ -1,0 +1,312 @@
+/*
+ * specula_gb300 — C ABI of the GB300-native wavefront-sensor hot path.
+ *
+ * One frame of an adaptive-optics simulation's sensing chain, as the paper's
+ * processing objects compute it (App. A, Tab. 4): AtmoEvolution +
+ * AtmoPropagation (layer extraction), ModulatedPyramid / SH (sensor image),
+ * CCD (binning, noise off), PyrSlopec / ShSlopec (slopes) and Modalrec
+ * (reconstructor matrix-vector product), with the parameters of App. B,
+ * Listing 2.  The paper prints no equation for these objects; the formulas
+ * each call implements are stated beside it.
+ *
+ * Conventions shared by every call
+ *  - Arrays are row-major [y][x].  Grids are centred: sample i of a side-n grid
+ *    sits at i - (n-1)/2.
+ *  - "*_dev" pointers are device memory owned by the caller; "*_host" pointers
+ *    are host memory owned by the caller.  The library keeps no pointer
+ *    beyond the call unless a plan call says so.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Per-frame
+ *    calls (atmo_extract, pwfs_image, sh_image, slopes, recon) only enqueue
+ *    kernels: they allocate nothing and never synchronise the host, so they
+ *    can be captured into a CUDA graph (the rule of Sect. 2.3 for a
+ *    processing object's trigger phase).  Plan calls may allocate.
+ *  - Every call validates its arguments on the host and returns a negative
+ *    status before launching anything.  Device-side conditions (non-finite
+ *    guard, bounded waits) are recorded in a per-context status word read by
+ *    specula_ctx_status.
+ *  - One context per device per host thread; calls on one context are not
+ *    thread-safe.
+ */
+#ifndef SPECULA_GB300_H
+#define SPECULA_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes --------------------------------------------------------- */
+#define SPECULA_OK            0
+#define SPECULA_EINVAL       -1  /* bad argument (null pointer, size, range)   */
+#define SPECULA_ENOMEM       -2  /* device or host allocation failed           */
+#define SPECULA_ECUDA        -3  /* a CUDA runtime call failed                 */
+#define SPECULA_ETIMEOUT     -4  /* a bounded device wait expired              */
+#define SPECULA_EUNSUPPORTED -5  /* valid request outside the built sizes      */
+#define SPECULA_ENONFINITE   -6  /* non-finite value seen by a guarded kernel  */
+#define SPECULA_ENOPLAN      -7  /* per-frame call without a matching plan     */
+
+/* Human-readable text of a status code (static storage; never NULL). */
+const char *specula_strerror(int status);
+
+/* Library ABI version (major * 10000 + minor * 100 + patch). */
+int specula_version(void);
+
+/* ---- descriptors -------------------------------------------------------- */
+
+/* Telescope pupil sampled on n_pix x n_pix pixels of pitch_m metres with a
+ * central obscuration obsc_frac of the diameter (PupilStop, App. A, Tab. 3;
+ * Listing 2 `pixel_pupil`, `pixel_pitch`). */
+typedef struct {
+  int32_t n_pix;
+  double pitch_m;
+  double obsc_frac;
+} specula_pupil_desc;
+
+/* Guide star: direction (radians on sky), height (INFINITY for a natural
+ * star; finite for a laser star, which compresses each layer's footprint by
+ * 1 - h/height) and wavelength (Source, App. A, Tab. 3; Listing 2
+ * `polar_coordinates`, `wavelengthInNm`). */
+typedef struct {
+  double theta_x_rad, theta_y_rad, height_m, wavelength_nm;
+} specula_source_desc;
+
+/* One frozen-flow turbulence layer: side x side screen of pitch_m metres at
+ * height_m, translated by the wind (vx, vy) m/s (Layer, App. A, Tab. 3;
+ * AtmoEvolution in Listing 2). */
+typedef struct {
+  int32_t side;
+  double pitch_m, height_m, vx_mps, vy_mps;
+} specula_layer_desc;
+
+/* Modulated pyramid (ModulatedPyramid, Listing 2): FFT side N = pad * n_pix;
+ * n_mod modulation points on a circle of mod_amp lambda/D; images binned to
+ * n_sub x n_sub per pupil image; pup_dist_px = separation of the pupil images
+ * (this build supports pad = 2 and pup_dist_px = n_pix, where the four
+ * images tile the padded grid). */
+typedef struct {
+  int32_t pad, n_mod, n_sub, pup_dist_px;
+  double mod_amp;
+} specula_pwfs_desc;
+
+/* Shack-Hartmann (SH / Lenslet, App. A, Tabs. 3-4): n_sub x n_sub lenslets of
+ * sub_pix pupil pixels, each imaged with an fft_n x fft_n DFT. */
+typedef struct {
+  int32_t n_sub, sub_pix, fft_n;
+} specula_sh_desc;
+
+#define SPECULA_SLOPES_PYR 0
+#define SPECULA_SLOPES_SH  1
+
+/* Slope computer (PyrSlopec / ShSlopec, App. A, Tab. 4).  subap_idx_dev lists
+ * the valid subapertures as a * n_sub + b (row a, column b), ascending; for
+ * SH, the image holds one fft_n^2 spot per listed subaperture. */
+typedef struct {
+  int32_t kind;            /* SPECULA_SLOPES_PYR or SPECULA_SLOPES_SH  */
+  int32_t n_sub;           /* subapertures across one pupil image       */
+  int32_t n_valid;         /* entries of subap_idx_dev                  */
+  int32_t fft_n;           /* SH spot side (ignored for PYR)            */
+  const int32_t *subap_idx_dev;
+} specula_slopec_desc;
+
+#define SPECULA_PREC_FP32   0   /* R in float32                                   */
+#define SPECULA_PREC_BF16   1   /* R rounded to bfloat16                          */
+#define SPECULA_PREC_BF16X2 2   /* R = hi + lo, both bfloat16 (split precision)   */
+
+/* Linear modal reconstructor (Modalrec / Recmat, Listing 2 `recmat_object`):
+ * R is n_modes x n_slopes, row-major.  FP32: R_dev is float*.  BF16: R_dev is
+ * the bfloat16 copy.  BF16X2: R_dev = hi, R_lo_dev = lo (see
+ * specula_recon_convert). */
+typedef struct {
+  int32_t n_modes, n_slopes, precision;
+  const void *R_dev;
+  const void *R_lo_dev;
+} specula_recon_desc;
+
+/* ---- context -------------------------------------------------------------- */
+typedef struct specula_ctx specula_ctx;
+
+/* Create a context on CUDA device `device`: selects the device, uploads the
+ * FFT codelet twiddle tables and allocates the device status word.
+ * May allocate.  *out is set on success. */
+int specula_ctx_create(specula_ctx **out, int device);
+
+/* Destroy a context and every plan it owns.  Synchronises the device. */
+int specula_ctx_destroy(specula_ctx *ctx);
+
+/* Wait for the device, return the device status word (SPECULA_OK if no
+ * device-side condition was recorded) in *device_status and clear it. */
+int specula_ctx_status(specula_ctx *ctx, int32_t *device_status);
+
+/* ---- tracing -----------------------------------------------------------------
+ * LoopControl reports the simulation speed (Sect. 2.4); these calls give the
+ * per-kernel view behind it.  Kernel ids: */
+#define SPECULA_K_PWFS_ROWS_FWD 0   /* pyramid pass A: field, tilt, row FFT       */
+#define SPECULA_K_PWFS_COLS     1   /* pyramid pass B: column FFT, mask, IFFT     */
+#define SPECULA_K_PWFS_ROWS_INV 2   /* pyramid pass C: row IFFT, |E|^2, binning   */
+#define SPECULA_K_ATMO          3   /* layer extraction                           */
+#define SPECULA_K_SLOPES        4   /* slope computers                            */
+#define SPECULA_K_RECON         5   /* reconstructor MVM                          */
+#define SPECULA_K_SH            6   /* Shack-Hartmann spots                       */
+#define SPECULA_K_COUNT         8
+
+/* Enable (capacity > 0: room for that many kernel records; allocates CUDA
+ * events; set-up call) or disable (capacity = 0) per-kernel event timing.
+ * While enabled, each kernel a per-frame call launches is bracketed by a pair
+ * of events recorded on its own stream (eager launches only; do not enable
+ * while capturing a graph).  Records beyond capacity are dropped. */
+int specula_prof_enable(specula_ctx *ctx, int32_t capacity);
+
+/* Synchronise, then return for each kernel id k < SPECULA_K_COUNT the summed
+ * elapsed milliseconds ms_host[k] and the number of records n_host[k] since
+ * the last read (arrays of SPECULA_K_COUNT entries), and clear the records. */
+int specula_prof_read(specula_ctx *ctx, double *ms_host, int64_t *n_host);
+
+/* Number of kernels this context has launched since it was created. */
+int specula_launch_count(specula_ctx *ctx, int64_t *count);
+
+/* ---- integer geometry (host; bit-exact; no GPU needed) ---------------------
+ * Pupil stop (PupilStop): pixel (j, i) is inside iff
+ *   r4 = (2i - n + 1)^2 + (2j - n + 1)^2 <= n^2  and  r4 > (obsc * n)^2,
+ * the last bound as the float64 product e * e, e = obsc_frac * n_pix.
+ * Writes n_pix^2 bytes (1 inside, 0 outside) to mask_host. */
+int specula_pupil_mask_host(const specula_pupil_desc *pupil, uint8_t *mask_host);
+
+/* Valid subapertures (PupData / SubapData; PyrPupdataCalibrator /
+ * ShSubapCalibrator, App. A, Tab. 4; geometric reading of the flux threshold):
+ * a b x b block (b = n_pix / n_sub) is valid iff 2 * (pixels inside) >= b^2.
+ * Writes the ascending linear indices a * n_sub + b to idx_host (capacity
+ * n_sub^2) and their count to *n_valid. */
+int specula_valid_subaps_host(const specula_pupil_desc *pupil, int32_t n_sub,
+                              int32_t *idx_host, int32_t *n_valid);
+
+/* Modulation points (ModulatedPyramid `mod_amp`): theta_m = (2 pi m) / n_mod,
+ * m = 0..n_mod-1, counter-clockwise from +x; writes cos/sin in float64. */
+int specula_mod_table_host(int32_t n_mod, double *cos_host, double *sin_host);
+
+/* ---- integer geometry on the device ----------------------------------------
+ * Same rules as the host versions, computed by kernels (bit-exact). */
+int specula_pupil_mask(specula_ctx *ctx, const specula_pupil_desc *pupil,
+                       float *amp_dev, void *stream);
+/* idx_dev: capacity n_sub^2 int32; n_valid_dev: one int32. */
+int specula_valid_subaps(specula_ctx *ctx, const specula_pupil_desc *pupil,
+                         int32_t n_sub, int32_t *idx_dev, int32_t *n_valid_dev,
+                         void *stream);
+
+/* ---- phase screens (set-up; may allocate) -----------------------------------
+ * Von Karman screen by the FFT method (AtmoEvolution, App. A, Tab. 4; Listing
+ * 2 `L0`, `Cn2`, `seed`), radians at 500 nm:
+ *   Phi(f) = 0.023 r0^(-5/3) (|f|^2 + L0^-2)^(-11/6), Phi(0) = 0;
+ *   screen[y][x] = Re sum_k c_k sqrt(Phi(f_k)) df exp(2 pi i f_k.(x,y) pitch),
+ * f_k = signed FFT index / (side pitch), df = 1 / (side pitch); plus three
+ * levels of subharmonics (spacing df/3^p, the eight non-zero offsets of a
+ * 3 x 3 grid, same amplitude rule) whose sum has its mean removed.
+ * noise_dev: side*side complex float64 (interleaved re, im), element
+ * [ky][kx] for FFT indices (ky, kx).  noise_sub_host: 3*3*3 complex float64
+ * [p][b][a] for level p+1, offset (a-1, b-1).  L0_m = INFINITY: Kolmogorov.
+ * Computed in float64 on the device and rounded to float32 once.  side must
+ * be a power of two in [32, 4096]. */
+int specula_screen_generate(specula_ctx *ctx, int32_t side, double pitch_m,
+                            double r0_m, double L0_m, const double *noise_dev,
+                            const double *noise_sub_host, float *screen_dev,
+                            void *stream);
+
+/* ---- per-frame calls ------------------------------------------------------- */
+
+/* Layer extraction (AtmoEvolution + AtmoPropagation, geometric propagation):
+ *   phase[j][i] = (500 / lambda) sum_l bilinear_periodic(S_l, u_l(i), v_l(j))
+ *   u = ((x_i * s) + ((h * theta_x) - (vx * t))) / pitch_l + side_l / 2,
+ *   x_i = (i - (n_pix - 1) / 2) * pupil pitch, s = 1 - h / H,
+ * with floor(u) and the fraction decided in float64 exactly in this
+ * operation order, the interpolation in float32.  t = *t_dev if t_dev is not
+ * NULL (device double, for graph replay), else t_s.  screens_dev is a host
+ * array of n_layers device pointers (side_l^2 floats each).  n_layers <= 64.
+ * phase_dev: n_pix^2 floats, radians at the source wavelength. */
+int specula_atmo_extract(specula_ctx *ctx, int32_t n_layers,
+                         const specula_layer_desc *layers,
+                         const float *const *screens_dev,
+                         const specula_source_desc *source,
+                         const specula_pupil_desc *pupil, double t_s,
+                         const double *t_dev, float *phase_dev, void *stream);
+
+/* Build (or reuse) the tables and workspace of a pyramid geometry: modulation
+ * tilt tables, pyramid-mask tables and FFT twiddles, computed in float64 on
+ * the host and rounded once to float32.  May allocate.  Supported FFT sides
+ * N = pad * n_pix: 64, 128, 240, 320, 960. */
+int specula_pwfs_plan(specula_ctx *ctx, const specula_pupil_desc *pupil,
+                      const specula_pwfs_desc *pwfs);
+
+/* Tile choice of a pyramid plan (the autotuner's knobs): `chunk` = number of
+ * (batch element, modulation point) items whose intermediates are kept in
+ * the workspace at once (the pipeline runs chunk by chunk, so a chunk that
+ * fits L2 keeps the intermediates on chip); `ka` = modulation items handled
+ * per warp in the row-transform pass (amortises the field's sincos).
+ * set: may reallocate the workspace (set-up call); chunk in [1, 4096], ka in
+ * [1, 64].  get: reads the current values. */
+int specula_pwfs_set_tiles(specula_ctx *ctx, const specula_pupil_desc *pupil,
+                           const specula_pwfs_desc *pwfs, int32_t chunk, int32_t ka);
+int specula_pwfs_get_tiles(specula_ctx *ctx, const specula_pupil_desc *pupil,
+                           const specula_pwfs_desc *pwfs, int32_t *chunk, int32_t *ka);
+
+/* Modulated pyramid image (ModulatedPyramid + CCD, noise off).  For each of
+ * n_batch phase maps and each modulation point m:
+ *   E_m = amp exp(i phase) exp(2 pi i r (x cos t_m + y sin t_m) / n_pix),
+ * centred in an N x N zero grid; F = centred DFT; F *= exp(-2 pi i c (|u| +
+ * |v|) / N), c = pup_dist / 2; O = inverse centred DFT (1/N^2);
+ * I = (1/n_mod) sum_m |O|^2; det = b x b block sums of I, b = n_pix / n_sub.
+ * amp_dev: n_pix^2 floats (shared by the batch); phase_dev: n_batch *
+ * n_pix^2 floats; det_dev: n_batch * (N/b)^2 floats.  n_sub = n_pix gives
+ * the unbinned N x N intensity.  Requires a plan (else SPECULA_ENOPLAN). */
+int specula_pwfs_image(specula_ctx *ctx, const specula_pupil_desc *pupil,
+                       const specula_pwfs_desc *pwfs, const float *amp_dev,
+                       const float *phase_dev, int32_t n_batch, float *det_dev,
+                       void *stream);
+
+/* Build (or reuse) the tables of a Shack-Hartmann geometry and its valid
+ * subaperture list (host rule above).  May allocate.  Supported fft_n: 24
+ * with sub_pix 12, and 16 with sub_pix 8.  *n_valid receives the count. */
+int specula_sh_plan(specula_ctx *ctx, const specula_pupil_desc *pupil,
+                    const specula_sh_desc *sh, int32_t *n_valid);
+
+/* Shack-Hartmann spots (SH): for each valid subaperture (ascending index), its
+ * sub_pix^2 block of E = amp exp(i phase) is centred in an fft_n^2 zero grid;
+ * spot = |centred DFT|^2 / fft_n^2.  spots_dev: n_batch * n_valid * fft_n^2
+ * floats.  Requires a plan. */
+int specula_sh_image(specula_ctx *ctx, const specula_pupil_desc *pupil,
+                     const specula_sh_desc *sh, const float *amp_dev,
+                     const float *phase_dev, int32_t n_batch, float *spots_dev,
+                     void *stream);
+
+/* Slopes (PyrSlopec / ShSlopec).  Output per batch element: all x slopes of
+ * the listed subapertures, then all y slopes (2 * n_valid floats).
+ *  PYR: img is the 2 n_sub x 2 n_sub detector; with Q1 (+x,+y) at
+ *   (n_sub + a, n_sub + b), Q2 (-x,+y) at (n_sub + a, b), Q3 (-x,-y) at
+ *   (a, b), Q4 (+x,-y) at (a, n_sub + b):
+ *   Sx = ((Q1 + Q4) - (Q2 + Q3)) / T, Sy = ((Q1 + Q2) - (Q3 + Q4)) / T,
+ *   T = mean over the listed subapertures of Q1 + Q2 + Q3 + Q4.
+ *  SH: img holds n_valid spots of fft_n^2; centre of gravity over the whole
+ *   window, x = j - (fft_n - 1)/2 pixels.
+ * ref_dev (nullable): 2 * n_valid reference slopes subtracted from each
+ * batch element.  Reductions run in a fixed order (bit-reproducible). */
+int specula_slopes(specula_ctx *ctx, const specula_slopec_desc *slopec,
+                   const float *img_dev, const float *ref_dev, int32_t n_batch,
+                   float *slopes_dev, void *stream);
+
+/* Modal reconstruction (Modalrec): modes[b] = R slopes[b] for n_batch slope
+ * vectors of n_slopes floats; modes_dev: n_batch * n_modes floats.
+ * Accumulation in float32 for every precision. */
+int specula_recon(specula_ctx *ctx, const specula_recon_desc *rec,
+                  const float *slopes_dev, int32_t n_batch, float *modes_dev,
+                  void *stream);
+
+/* Reduced-precision copies of a float32 R: BF16 writes hi = bf16(R) (round to
+ * nearest even); BF16X2 also writes lo = bf16(R - float(hi)).  hi_dev / lo_dev
+ * hold n_modes * n_slopes uint16 each (lo_dev unused for BF16). */
+int specula_recon_convert(specula_ctx *ctx, int32_t n_modes, int32_t n_slopes,
+                          const float *R_dev, int32_t precision, void *hi_dev,
+                          void *lo_dev, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SPECULA_GB300_H */

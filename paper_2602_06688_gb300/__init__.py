@@ -1,0 +1,316 @@
+"""Python binding of libspecula_gb300 (GB300-native wavefront-sensor hot path).
+
+Each function has the name of the C entry point it wraps
+(include/specula_gb300.h) and only marshals arguments: torch tensors supply
+device memory (``data_ptr``) and the current CUDA stream; every computation
+runs in the library's CUDA kernels.  A missing library raises ImportError at
+first use — there is no fallback path.
+"""
+import ctypes as C
+
+import numpy as np
+
+from . import _abi
+from ._abi import (  # noqa: F401
+    PupilDesc, SourceDesc, LayerDesc, PwfsDesc, ShDesc, SlopecDesc, ReconDesc,
+    SpeculaError, SLOPES_PYR, SLOPES_SH, PREC_FP32, PREC_BF16, PREC_BF16X2,
+    OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED, ENONFINITE, ENOPLAN,
+)
+
+
+def lib():
+    return _abi.load()
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _dev(t, dtype=None, numel=None, name="tensor"):
+    """Device pointer of a contiguous CUDA tensor, after shape/dtype checks."""
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{name} must have dtype {dtype}, got {t.dtype}")
+    if numel is not None and t.numel() < numel:
+        raise ValueError(f"{name} holds {t.numel()} elements, needs {numel}")
+    return C.c_void_p(t.data_ptr())
+
+
+# ---- descriptor helpers (from the synth workload records) --------------------
+
+def pupil_desc(p):
+    return PupilDesc(int(p.n_pix), float(p.pitch_m), float(p.obsc_frac))
+
+
+def source_desc(s):
+    return SourceDesc(float(s.theta_x_rad), float(s.theta_y_rad), float(s.height_m),
+                      float(s.wavelength_nm))
+
+
+def layer_desc(l):
+    return LayerDesc(int(l.side), float(l.pitch_m), float(l.height_m), float(l.vx_mps),
+                     float(l.vy_mps))
+
+
+def pwfs_desc(g):
+    return PwfsDesc(int(g.pad), int(g.n_mod), int(g.n_sub), int(g.pup_dist_px),
+                    float(g.mod_amp))
+
+
+def sh_desc(g):
+    return ShDesc(int(g.n_sub), int(g.sub_pix), int(g.fft_n))
+
+
+# ---- context ------------------------------------------------------------------
+
+class Context:
+    """Owns a specula_ctx handle (plans, tables, device status word)."""
+
+    def __init__(self, device=0):
+        h = C.c_void_p()
+        _abi.check(lib().specula_ctx_create(C.byref(h), int(device)), "specula_ctx_create")
+        self.handle = h
+        self.device = device
+
+    def close(self):
+        if self.handle:
+            lib().specula_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @property
+    def _as_parameter_(self):
+        return self.handle
+
+
+def specula_ctx_create(device=0):
+    return Context(device)
+
+
+def specula_ctx_destroy(ctx):
+    ctx.close()
+
+
+def specula_ctx_status(ctx):
+    v = C.c_int32()
+    _abi.check(lib().specula_ctx_status(ctx.handle, C.byref(v)), "specula_ctx_status")
+    return v.value
+
+
+K_PWFS_ROWS_FWD, K_PWFS_COLS, K_PWFS_ROWS_INV, K_ATMO, K_SLOPES, K_RECON, K_SH = range(7)
+K_COUNT = 8
+KERNEL_NAMES = ["pwfs_rows_fwd", "pwfs_cols", "pwfs_rows_inv", "atmo_extract", "slopes",
+                "recon", "sh_spots", "unused"]
+
+
+def specula_prof_enable(ctx, capacity):
+    _abi.check(lib().specula_prof_enable(ctx.handle, int(capacity)), "specula_prof_enable")
+
+
+def specula_prof_read(ctx):
+    """Returns {kernel name: (total ms, records)} since the last read."""
+    ms = np.zeros(K_COUNT, dtype=np.float64)
+    n = np.zeros(K_COUNT, dtype=np.int64)
+    _abi.check(lib().specula_prof_read(ctx.handle, ms.ctypes.data_as(C.c_void_p),
+                                       n.ctypes.data_as(C.c_void_p)), "specula_prof_read")
+    return {KERNEL_NAMES[k]: (float(ms[k]), int(n[k])) for k in range(K_COUNT) if n[k]}
+
+
+def specula_launch_count(ctx):
+    v = C.c_int64()
+    _abi.check(lib().specula_launch_count(ctx.handle, C.byref(v)), "specula_launch_count")
+    return v.value
+
+
+def specula_strerror(status):
+    return lib().specula_strerror(int(status)).decode()
+
+
+def specula_version():
+    return lib().specula_version()
+
+
+# ---- integer geometry ------------------------------------------------------------
+
+def specula_pupil_mask_host(pupil):
+    n = pupil.n_pix
+    out = np.zeros((n, n), dtype=np.uint8)
+    _abi.check(lib().specula_pupil_mask_host(C.byref(pupil), out.ctypes.data_as(C.c_void_p)),
+               "specula_pupil_mask_host")
+    return out
+
+
+def specula_valid_subaps_host(pupil, n_sub):
+    idx = np.zeros(n_sub * n_sub, dtype=np.int32)
+    nv = C.c_int32()
+    _abi.check(lib().specula_valid_subaps_host(C.byref(pupil), int(n_sub),
+                                               idx.ctypes.data_as(C.c_void_p), C.byref(nv)),
+               "specula_valid_subaps_host")
+    return idx[:nv.value].copy()
+
+
+def specula_mod_table_host(n_mod):
+    c = np.zeros(n_mod)
+    s = np.zeros(n_mod)
+    _abi.check(lib().specula_mod_table_host(int(n_mod), c.ctypes.data_as(C.c_void_p),
+                                            s.ctypes.data_as(C.c_void_p)),
+               "specula_mod_table_host")
+    return c, s
+
+
+def specula_pupil_mask(ctx, pupil, amp, stream=None):
+    import torch
+    _abi.check(lib().specula_pupil_mask(
+        ctx.handle, C.byref(pupil), _dev(amp, torch.float32, pupil.n_pix ** 2, "amp"),
+        _stream(stream)), "specula_pupil_mask")
+
+
+def specula_valid_subaps(ctx, pupil, n_sub, idx, n_valid, stream=None):
+    import torch
+    _abi.check(lib().specula_valid_subaps(
+        ctx.handle, C.byref(pupil), int(n_sub), _dev(idx, torch.int32, n_sub * n_sub, "idx"),
+        _dev(n_valid, torch.int32, 1, "n_valid"), _stream(stream)), "specula_valid_subaps")
+
+
+# ---- screens ------------------------------------------------------------------------
+
+def specula_screen_generate(ctx, side, pitch_m, r0_m, L0_m, noise, noise_sub, screen,
+                            stream=None):
+    """noise: CUDA complex128 (side, side) tensor; noise_sub: (3, 3, 3) complex
+    array (host); screen: CUDA float32 (side, side) output."""
+    import torch
+    sub = np.ascontiguousarray(np.asarray(noise_sub, dtype=np.complex128))
+    if sub.size != 27:
+        raise ValueError("noise_sub must hold 3*3*3 complex values")
+    _abi.check(lib().specula_screen_generate(
+        ctx.handle, int(side), float(pitch_m), float(r0_m), float(L0_m),
+        _dev(noise, torch.complex128, side * side, "noise"), sub.ctypes.data_as(C.c_void_p),
+        _dev(screen, torch.float32, side * side, "screen"), _stream(stream)),
+        "specula_screen_generate")
+
+
+# ---- per-frame calls -----------------------------------------------------------------
+
+def specula_atmo_extract(ctx, layers, screens, source, pupil, t, phase, t_dev=None,
+                         stream=None):
+    import torch
+    n = len(layers)
+    if len(screens) != n:
+        raise ValueError("one screen per layer")
+    L = (LayerDesc * n)(*layers)
+    ptrs = (C.c_void_p * n)(*[C.c_void_p(s.data_ptr()) for s in screens])
+    for s, l in zip(screens, layers):
+        _dev(s, torch.float32, l.side * l.side, "screen")
+    _abi.check(lib().specula_atmo_extract(
+        ctx.handle, n, L, ptrs, C.byref(source), C.byref(pupil), float(t),
+        _dev(t_dev, torch.float64, 1, "t_dev"),
+        _dev(phase, torch.float32, pupil.n_pix ** 2, "phase"), _stream(stream)),
+        "specula_atmo_extract")
+
+
+def specula_pwfs_plan(ctx, pupil, pwfs):
+    _abi.check(lib().specula_pwfs_plan(ctx.handle, C.byref(pupil), C.byref(pwfs)),
+               "specula_pwfs_plan")
+
+
+def specula_pwfs_set_tiles(ctx, pupil, pwfs, chunk, ka):
+    _abi.check(lib().specula_pwfs_set_tiles(ctx.handle, C.byref(pupil), C.byref(pwfs),
+                                            int(chunk), int(ka)), "specula_pwfs_set_tiles")
+
+
+def specula_pwfs_get_tiles(ctx, pupil, pwfs):
+    ch, ka = C.c_int32(), C.c_int32()
+    _abi.check(lib().specula_pwfs_get_tiles(ctx.handle, C.byref(pupil), C.byref(pwfs),
+                                            C.byref(ch), C.byref(ka)), "specula_pwfs_get_tiles")
+    return ch.value, ka.value
+
+
+def specula_pwfs_image(ctx, pupil, pwfs, amp, phase, det, stream=None):
+    """phase: (n_batch, n, n) or (n, n); det: (n_batch, 2 n_sub, 2 n_sub)."""
+    import torch
+    n = pupil.n_pix
+    nb = phase.numel() // (n * n)
+    side = 2 * pwfs.n_sub
+    _abi.check(lib().specula_pwfs_image(
+        ctx.handle, C.byref(pupil), C.byref(pwfs), _dev(amp, torch.float32, n * n, "amp"),
+        _dev(phase, torch.float32, nb * n * n, "phase"), nb,
+        _dev(det, torch.float32, nb * side * side, "det"), _stream(stream)),
+        "specula_pwfs_image")
+
+
+def specula_sh_plan(ctx, pupil, sh):
+    nv = C.c_int32()
+    _abi.check(lib().specula_sh_plan(ctx.handle, C.byref(pupil), C.byref(sh), C.byref(nv)),
+               "specula_sh_plan")
+    return nv.value
+
+
+def specula_sh_image(ctx, pupil, sh, amp, phase, spots, n_valid, stream=None):
+    import torch
+    n = pupil.n_pix
+    nb = phase.numel() // (n * n)
+    _abi.check(lib().specula_sh_image(
+        ctx.handle, C.byref(pupil), C.byref(sh), _dev(amp, torch.float32, n * n, "amp"),
+        _dev(phase, torch.float32, nb * n * n, "phase"), nb,
+        _dev(spots, torch.float32, nb * n_valid * sh.fft_n ** 2, "spots"), _stream(stream)),
+        "specula_sh_image")
+
+
+def specula_slopes(ctx, slopec, img, ref, slopes, stream=None):
+    import torch
+    nb = slopes.numel() // (2 * slopec.n_valid)
+    _abi.check(lib().specula_slopes(
+        ctx.handle, C.byref(slopec), _dev(img, torch.float32, None, "img"),
+        _dev(ref, torch.float32, 2 * slopec.n_valid, "ref"), nb,
+        _dev(slopes, torch.float32, nb * 2 * slopec.n_valid, "slopes"), _stream(stream)),
+        "specula_slopes")
+
+
+def specula_recon(ctx, rec, slopes, modes, stream=None):
+    import torch
+    nb = slopes.numel() // rec.n_slopes
+    _abi.check(lib().specula_recon(
+        ctx.handle, C.byref(rec), _dev(slopes, torch.float32, nb * rec.n_slopes, "slopes"), nb,
+        _dev(modes, torch.float32, nb * rec.n_modes, "modes"), _stream(stream)),
+        "specula_recon")
+
+
+def specula_recon_convert(ctx, R, precision, hi, lo=None, stream=None):
+    import torch
+    nm, ns = R.shape
+    _abi.check(lib().specula_recon_convert(
+        ctx.handle, int(nm), int(ns), _dev(R, torch.float32, nm * ns, "R"), int(precision),
+        _dev(hi, None, nm * ns, "hi"), _dev(lo, None, nm * ns, "lo"), _stream(stream)),
+        "specula_recon_convert")
+
+
+def slopec_desc(kind, n_sub, idx_dev, fft_n=0):
+    return SlopecDesc(int(kind), int(n_sub), int(idx_dev.numel()), int(fft_n),
+                      C.c_void_p(idx_dev.data_ptr()))
+
+
+def recon_desc(n_modes, n_slopes, precision, R_dev, R_lo_dev=None):
+    return ReconDesc(int(n_modes), int(n_slopes), int(precision), C.c_void_p(R_dev.data_ptr()),
+                     C.c_void_p(R_lo_dev.data_ptr()) if R_lo_dev is not None else None)
+

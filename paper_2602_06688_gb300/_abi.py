@@ -1,0 +1,121 @@
+"""ctypes declarations of the C ABI in include/specula_gb300.h.
+
+Loading fails loudly when the compiled library is missing: there is no
+fallback implementation.
+"""
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libspecula_gb300.so")
+
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED, ENONFINITE, ENOPLAN = \
+    0, -1, -2, -3, -4, -5, -6, -7
+SLOPES_PYR, SLOPES_SH = 0, 1
+PREC_FP32, PREC_BF16, PREC_BF16X2 = 0, 1, 2
+
+
+class PupilDesc(C.Structure):
+    _fields_ = [("n_pix", C.c_int32), ("pitch_m", C.c_double),
+                ("obsc_frac", C.c_double)]
+
+
+class SourceDesc(C.Structure):
+    _fields_ = [("theta_x_rad", C.c_double), ("theta_y_rad", C.c_double),
+                ("height_m", C.c_double), ("wavelength_nm", C.c_double)]
+
+
+class LayerDesc(C.Structure):
+    _fields_ = [("side", C.c_int32), ("pitch_m", C.c_double),
+                ("height_m", C.c_double), ("vx_mps", C.c_double),
+                ("vy_mps", C.c_double)]
+
+
+class PwfsDesc(C.Structure):
+    _fields_ = [("pad", C.c_int32), ("n_mod", C.c_int32), ("n_sub", C.c_int32),
+                ("pup_dist_px", C.c_int32), ("mod_amp", C.c_double)]
+
+
+class ShDesc(C.Structure):
+    _fields_ = [("n_sub", C.c_int32), ("sub_pix", C.c_int32),
+                ("fft_n", C.c_int32)]
+
+
+class SlopecDesc(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("n_sub", C.c_int32),
+                ("n_valid", C.c_int32), ("fft_n", C.c_int32),
+                ("subap_idx_dev", C.c_void_p)]
+
+
+class ReconDesc(C.Structure):
+    _fields_ = [("n_modes", C.c_int32), ("n_slopes", C.c_int32),
+                ("precision", C.c_int32), ("R_dev", C.c_void_p),
+                ("R_lo_dev", C.c_void_p)]
+
+
+P = C.POINTER
+vp = C.c_void_p
+i32 = C.c_int32
+dbl = C.c_double
+
+# name -> (restype, argtypes)
+SIGNATURES = {
+    "specula_strerror": (C.c_char_p, [C.c_int]),
+    "specula_version": (C.c_int, []),
+    "specula_ctx_create": (C.c_int, [P(vp), C.c_int]),
+    "specula_ctx_destroy": (C.c_int, [vp]),
+    "specula_ctx_status": (C.c_int, [vp, P(i32)]),
+    "specula_prof_enable": (C.c_int, [vp, i32]),
+    "specula_prof_read": (C.c_int, [vp, vp, vp]),
+    "specula_launch_count": (C.c_int, [vp, P(C.c_int64)]),
+    "specula_pupil_mask_host": (C.c_int, [P(PupilDesc), vp]),
+    "specula_valid_subaps_host": (C.c_int, [P(PupilDesc), i32, vp, P(i32)]),
+    "specula_mod_table_host": (C.c_int, [i32, vp, vp]),
+    "specula_pupil_mask": (C.c_int, [vp, P(PupilDesc), vp, vp]),
+    "specula_valid_subaps": (C.c_int, [vp, P(PupilDesc), i32, vp, vp, vp]),
+    "specula_screen_generate": (C.c_int, [vp, i32, dbl, dbl, dbl, vp, vp, vp, vp]),
+    "specula_atmo_extract": (C.c_int, [vp, i32, P(LayerDesc), P(vp), P(SourceDesc),
+                                       P(PupilDesc), dbl, vp, vp, vp]),
+    "specula_pwfs_plan": (C.c_int, [vp, P(PupilDesc), P(PwfsDesc)]),
+    "specula_pwfs_set_tiles": (C.c_int, [vp, P(PupilDesc), P(PwfsDesc), i32, i32]),
+    "specula_pwfs_get_tiles": (C.c_int, [vp, P(PupilDesc), P(PwfsDesc), P(i32), P(i32)]),
+    "specula_pwfs_image": (C.c_int, [vp, P(PupilDesc), P(PwfsDesc), vp, vp, i32, vp, vp]),
+    "specula_sh_plan": (C.c_int, [vp, P(PupilDesc), P(ShDesc), P(i32)]),
+    "specula_sh_image": (C.c_int, [vp, P(PupilDesc), P(ShDesc), vp, vp, i32, vp, vp]),
+    "specula_slopes": (C.c_int, [vp, P(SlopecDesc), vp, vp, i32, vp, vp]),
+    "specula_recon": (C.c_int, [vp, P(ReconDesc), vp, i32, vp, vp]),
+    "specula_recon_convert": (C.c_int, [vp, i32, i32, vp, i32, vp, vp, vp]),
+}
+
+_lib = None
+
+
+def load():
+    """Load libspecula_gb300.so (built by ``build.build()``); raise if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(
+            f"{LIB_PATH} is missing: build it with "
+            "paper_2602_06688_gb300.build.build() (nvcc, sm_103a)")
+    lib = C.CDLL(LIB_PATH)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class SpeculaError(RuntimeError):
+    def __init__(self, status, where):
+        text = load().specula_strerror(status).decode()
+        super().__init__(f"{where}: {text} ({status})")
+        self.status = status
+
+
+def check(status, where):
+    if status != OK:
+        raise SpeculaError(status, where)
+    return status

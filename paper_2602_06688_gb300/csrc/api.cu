@@ -1,0 +1,381 @@
+// Context, status codes, integer geometry and argument validation of the
+// C ABI (include/specula_gb300.h).
+#include <math.h>
+#include <string.h>
+
+#include <new>
+
+#include "internal.h"
+
+using namespace specula;
+
+extern "C" const char *specula_strerror(int s) {
+  switch (s) {
+    case SPECULA_OK: return "ok";
+    case SPECULA_EINVAL: return "invalid argument";
+    case SPECULA_ENOMEM: return "out of memory";
+    case SPECULA_ECUDA: return "CUDA runtime error";
+    case SPECULA_ETIMEOUT: return "bounded device wait expired";
+    case SPECULA_EUNSUPPORTED: return "size or option not supported by this build";
+    case SPECULA_ENONFINITE: return "non-finite value detected";
+    case SPECULA_ENOPLAN: return "no plan for this geometry (call the plan function first)";
+    default: return "unknown status";
+  }
+}
+
+extern "C" int specula_version(void) { return 100; }
+
+extern "C" int specula_ctx_create(specula_ctx **out, int device) {
+  if (!out) return SPECULA_EINVAL;
+  *out = nullptr;
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess) return SPECULA_ECUDA;
+  if (device < 0 || device >= n) return SPECULA_EINVAL;
+  SPECULA_CK(cudaSetDevice(device));
+  specula_ctx *c = new (std::nothrow) specula_ctx();
+  if (!c) return SPECULA_ENOMEM;
+  c->device = device;
+  if (cudaMalloc(&c->status_dev, sizeof(int32_t)) != cudaSuccess) {
+    delete c;
+    return SPECULA_ENOMEM;
+  }
+  if (cudaMemset(c->status_dev, 0, sizeof(int32_t)) != cudaSuccess) {
+    cudaFree(c->status_dev);
+    delete c;
+    return SPECULA_ECUDA;
+  }
+  int s = pwfs_init_device();
+  if (!s) s = sh_init_device();
+  if (s) {
+    cudaFree(c->status_dev);
+    delete c;
+    return s;
+  }
+  *out = c;
+  return SPECULA_OK;
+}
+
+static void prof_free(specula_ctx *ctx) {
+  for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
+  ctx->ev.clear();
+  ctx->ev_next = 0;
+  ctx->rec_kid.clear();
+  ctx->prof = false;
+}
+
+extern "C" int specula_ctx_destroy(specula_ctx *ctx) {
+  if (!ctx) return SPECULA_EINVAL;
+  cudaSetDevice(ctx->device);
+  cudaDeviceSynchronize();
+  prof_free(ctx);
+  ctx->pwfs.clear();
+  ctx->sh.clear();
+  if (ctx->status_dev) cudaFree(ctx->status_dev);
+  delete ctx;
+  return SPECULA_OK;
+}
+
+extern "C" int specula_prof_enable(specula_ctx *ctx, int32_t capacity) {
+  if (!ctx || capacity < 0 || capacity > (1 << 20)) return SPECULA_EINVAL;
+  SPECULA_CK(cudaSetDevice(ctx->device));
+  SPECULA_CK(cudaDeviceSynchronize());
+  prof_free(ctx);
+  if (capacity == 0) return SPECULA_OK;
+  ctx->ev.resize(2 * (size_t)capacity);
+  for (auto &e : ctx->ev)
+    if (cudaEventCreate(&e) != cudaSuccess) {
+      e = nullptr;
+      prof_free(ctx);
+      return SPECULA_ECUDA;
+    }
+  ctx->rec_kid.reserve(capacity);
+  ctx->prof = true;
+  return SPECULA_OK;
+}
+
+extern "C" int specula_prof_read(specula_ctx *ctx, double *ms_host, int64_t *n_host) {
+  if (!ctx || !ms_host || !n_host) return SPECULA_EINVAL;
+  SPECULA_CK(cudaSetDevice(ctx->device));
+  SPECULA_CK(cudaDeviceSynchronize());
+  for (int k = 0; k < SPECULA_K_COUNT; ++k) {
+    ms_host[k] = 0.0;
+    n_host[k] = 0;
+  }
+  for (size_t i = 0; i < ctx->rec_kid.size(); ++i) {
+    float ms = 0.f;
+    SPECULA_CK(cudaEventElapsedTime(&ms, ctx->ev[2 * i], ctx->ev[2 * i + 1]));
+    const int k = ctx->rec_kid[i];
+    if (k >= 0 && k < SPECULA_K_COUNT) {
+      ms_host[k] += ms;
+      n_host[k] += 1;
+    }
+  }
+  ctx->rec_kid.clear();
+  ctx->ev_next = 0;
+  return SPECULA_OK;
+}
+
+extern "C" int specula_launch_count(specula_ctx *ctx, int64_t *count) {
+  if (!ctx || !count) return SPECULA_EINVAL;
+  *count = ctx->launches;
+  return SPECULA_OK;
+}
+
+extern "C" int specula_ctx_status(specula_ctx *ctx, int32_t *device_status) {
+  if (!ctx || !device_status) return SPECULA_EINVAL;
+  SPECULA_CK(cudaSetDevice(ctx->device));
+  SPECULA_CK(cudaDeviceSynchronize());
+  int32_t v = 0;
+  SPECULA_CK(cudaMemcpy(&v, ctx->status_dev, sizeof(v), cudaMemcpyDeviceToHost));
+  SPECULA_CK(cudaMemset(ctx->status_dev, 0, sizeof(int32_t)));
+  *device_status = v;
+  return SPECULA_OK;
+}
+
+// ---- integer geometry --------------------------------------------------------
+
+namespace specula {
+
+int host_pupil_mask(int n, double obsc, uint8_t *mask) {
+  const double e = obsc * (double)n;
+  const double thr = e * e;
+  const int64_t nn = (int64_t)n * n;
+  for (int j = 0; j < n; ++j) {
+    const int64_t dy = 2 * (int64_t)j - n + 1;
+    for (int i = 0; i < n; ++i) {
+      const int64_t dx = 2 * (int64_t)i - n + 1;
+      const int64_t r4 = dx * dx + dy * dy;
+      mask[(size_t)j * n + i] = (r4 <= nn && (double)r4 > thr) ? 1 : 0;
+    }
+  }
+  return SPECULA_OK;
+}
+
+int host_valid_subaps(int n, double obsc, int n_sub, int32_t *idx, int32_t *n_valid) {
+  const int b = n / n_sub;
+  std::vector<uint8_t> m((size_t)n * n);
+  host_pupil_mask(n, obsc, m.data());
+  int cnt = 0;
+  for (int a = 0; a < n_sub; ++a)
+    for (int c = 0; c < n_sub; ++c) {
+      int in = 0;
+      for (int y = 0; y < b; ++y)
+        for (int x = 0; x < b; ++x) in += m[(size_t)(a * b + y) * n + (c * b + x)];
+      if (2 * in >= b * b) idx[cnt++] = a * n_sub + c;
+    }
+  *n_valid = cnt;
+  return SPECULA_OK;
+}
+
+}  // namespace specula
+
+static int check_pupil(const specula_pupil_desc *p) {
+  if (!p) return SPECULA_EINVAL;
+  if (p->n_pix < 2 || p->n_pix > 8192) return SPECULA_EINVAL;
+  if (!(p->obsc_frac >= 0.0 && p->obsc_frac < 1.0)) return SPECULA_EINVAL;
+  if (!(p->pitch_m > 0.0) || !isfinite(p->pitch_m)) return SPECULA_EINVAL;
+  return SPECULA_OK;
+}
+
+extern "C" int specula_pupil_mask_host(const specula_pupil_desc *pupil, uint8_t *mask_host) {
+  int s = check_pupil(pupil);
+  if (s) return s;
+  if (!mask_host) return SPECULA_EINVAL;
+  return host_pupil_mask(pupil->n_pix, pupil->obsc_frac, mask_host);
+}
+
+extern "C" int specula_valid_subaps_host(const specula_pupil_desc *pupil, int32_t n_sub,
+                                         int32_t *idx_host, int32_t *n_valid) {
+  int s = check_pupil(pupil);
+  if (s) return s;
+  if (!idx_host || !n_valid || n_sub < 1 || pupil->n_pix % n_sub) return SPECULA_EINVAL;
+  return host_valid_subaps(pupil->n_pix, pupil->obsc_frac, n_sub, idx_host, n_valid);
+}
+
+extern "C" int specula_mod_table_host(int32_t n_mod, double *cos_host, double *sin_host) {
+  if (n_mod < 1 || !cos_host || !sin_host) return SPECULA_EINVAL;
+  for (int m = 0; m < n_mod; ++m) {
+    const double th = 2.0 * M_PI * m / n_mod;
+    cos_host[m] = cos(th);
+    sin_host[m] = sin(th);
+  }
+  return SPECULA_OK;
+}
+
+// Device versions of the integer rules.
+__global__ void k_pupil_mask(int n, double thr, float *amp) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y;
+  if (i >= n || j >= n) return;
+  const long long dx = 2LL * i - n + 1, dy = 2LL * j - n + 1;
+  const long long r4 = dx * dx + dy * dy;
+  amp[(size_t)j * n + i] = (r4 <= (long long)n * n && (double)r4 > thr) ? 1.0f : 0.0f;
+}
+
+// One CTA: count pupil pixels per subaperture, flag, ordered compaction.
+__global__ void k_valid_subaps(int n, double thr, int n_sub, int32_t *idx, int32_t *n_valid) {
+  __shared__ int32_t s_scan[1024];
+  const int b = n / n_sub;
+  const int total = n_sub * n_sub;
+  const int per = (total + blockDim.x - 1) / blockDim.x;   // <= 16 (n_sub <= 128)
+  const int t = threadIdx.x;
+  uint32_t flags = 0;
+  int mine = 0;
+  for (int q = 0; q < per; ++q) {
+    const int s = t * per + q;
+    if (s >= total) break;
+    const int a = s / n_sub, c = s % n_sub;
+    int in = 0;
+    for (int y = 0; y < b; ++y) {
+      const long long dy = 2LL * (a * b + y) - n + 1;
+      for (int x = 0; x < b; ++x) {
+        const long long dx = 2LL * (c * b + x) - n + 1;
+        const long long r4 = dx * dx + dy * dy;
+        in += (r4 <= (long long)n * n && (double)r4 > thr) ? 1 : 0;
+      }
+    }
+    if (2 * in >= b * b) { flags |= 1u << q; ++mine; }
+  }
+  s_scan[t] = mine;
+  __syncthreads();
+  // inclusive Hillis-Steele scan
+  for (int off = 1; off < (int)blockDim.x; off <<= 1) {
+    int v = (t >= off) ? s_scan[t - off] : 0;
+    __syncthreads();
+    s_scan[t] += v;
+    __syncthreads();
+  }
+  int pos = s_scan[t] - mine;
+  for (int q = 0; q < per; ++q) {
+    const int s = t * per + q;
+    if (s >= total) break;
+    if (flags & (1u << q)) idx[pos++] = s;
+  }
+  if (t == blockDim.x - 1) *n_valid = s_scan[t];
+}
+
+extern "C" int specula_pupil_mask(specula_ctx *ctx, const specula_pupil_desc *pupil,
+                                  float *amp_dev, void *stream) {
+  if (!ctx || !amp_dev) return SPECULA_EINVAL;
+  int s = check_pupil(pupil);
+  if (s) return s;
+  const int n = pupil->n_pix;
+  const double e = pupil->obsc_frac * (double)n;
+  dim3 grid((n + 127) / 128, n);
+  k_pupil_mask<<<grid, 128, 0, (cudaStream_t)stream>>>(n, e * e, amp_dev);
+  SPECULA_CK_LAUNCH();
+  return SPECULA_OK;
+}
+
+extern "C" int specula_valid_subaps(specula_ctx *ctx, const specula_pupil_desc *pupil,
+                                    int32_t n_sub, int32_t *idx_dev, int32_t *n_valid_dev,
+                                    void *stream) {
+  if (!ctx || !idx_dev || !n_valid_dev) return SPECULA_EINVAL;
+  int s = check_pupil(pupil);
+  if (s) return s;
+  if (n_sub < 1 || n_sub > 128 || pupil->n_pix % n_sub) return SPECULA_EINVAL;
+  const int n = pupil->n_pix;
+  const double e = pupil->obsc_frac * (double)n;
+  k_valid_subaps<<<1, 1024, 0, (cudaStream_t)stream>>>(n, e * e, n_sub, idx_dev, n_valid_dev);
+  SPECULA_CK_LAUNCH();
+  return SPECULA_OK;
+}
+
+// ---- pyramid / SH dispatch -----------------------------------------------------
+
+static int check_pwfs(const specula_pupil_desc *pupil, const specula_pwfs_desc *p) {
+  int s = check_pupil(pupil);
+  if (s) return s;
+  if (!p) return SPECULA_EINVAL;
+  if (p->pad < 1 || p->n_mod < 1 || p->n_mod > 4096 || p->n_sub < 1) return SPECULA_EINVAL;
+  if (pupil->n_pix % p->n_sub) return SPECULA_EINVAL;
+  if (!(p->mod_amp >= 0.0) || !isfinite(p->mod_amp)) return SPECULA_EINVAL;
+  if (p->pad != 2 || p->pup_dist_px != pupil->n_pix) return SPECULA_EUNSUPPORTED;
+  return SPECULA_OK;
+}
+
+extern "C" int specula_pwfs_plan(specula_ctx *ctx, const specula_pupil_desc *pupil,
+                                 const specula_pwfs_desc *pwfs) {
+  if (!ctx) return SPECULA_EINVAL;
+  int s = check_pwfs(pupil, pwfs);
+  if (s) return s;
+  if (pwfs_plan_find(ctx, pupil, pwfs)) return SPECULA_OK;
+  SPECULA_CK(cudaSetDevice(ctx->device));
+  PwfsPlan *p = nullptr;
+  return pwfs_plan_build(ctx, pupil, pwfs, &p);
+}
+
+extern "C" int specula_pwfs_set_tiles(specula_ctx *ctx, const specula_pupil_desc *pupil,
+                                      const specula_pwfs_desc *pwfs, int32_t chunk, int32_t ka) {
+  if (!ctx) return SPECULA_EINVAL;
+  int s = check_pwfs(pupil, pwfs);
+  if (s) return s;
+  if (chunk < 1 || chunk > 4096 || ka < 1 || ka > 64) return SPECULA_EINVAL;
+  PwfsPlan *p = pwfs_plan_find(ctx, pupil, pwfs);
+  if (!p) return SPECULA_ENOPLAN;
+  SPECULA_CK(cudaSetDevice(ctx->device));
+  return pwfs_set_tiles(p, chunk, ka);
+}
+
+extern "C" int specula_pwfs_get_tiles(specula_ctx *ctx, const specula_pupil_desc *pupil,
+                                      const specula_pwfs_desc *pwfs, int32_t *chunk, int32_t *ka) {
+  if (!ctx || !chunk || !ka) return SPECULA_EINVAL;
+  int s = check_pwfs(pupil, pwfs);
+  if (s) return s;
+  PwfsPlan *p = pwfs_plan_find(ctx, pupil, pwfs);
+  if (!p) return SPECULA_ENOPLAN;
+  *chunk = p->chunk;
+  *ka = p->ka;
+  return SPECULA_OK;
+}
+
+extern "C" int specula_pwfs_image(specula_ctx *ctx, const specula_pupil_desc *pupil,
+                                  const specula_pwfs_desc *pwfs, const float *amp_dev,
+                                  const float *phase_dev, int32_t n_batch, float *det_dev,
+                                  void *stream) {
+  if (!ctx || !amp_dev || !phase_dev || !det_dev || n_batch < 0) return SPECULA_EINVAL;
+  int s = check_pwfs(pupil, pwfs);
+  if (s) return s;
+  PwfsPlan *p = pwfs_plan_find(ctx, pupil, pwfs);
+  if (!p) return SPECULA_ENOPLAN;
+  if (n_batch == 0) return SPECULA_OK;
+  return pwfs_run(ctx, p, amp_dev, phase_dev, n_batch, det_dev, (cudaStream_t)stream);
+}
+
+static int check_sh(const specula_pupil_desc *pupil, const specula_sh_desc *sh) {
+  int s = check_pupil(pupil);
+  if (s) return s;
+  if (!sh || sh->n_sub < 1 || sh->sub_pix < 1 || sh->fft_n < sh->sub_pix) return SPECULA_EINVAL;
+  if (sh->n_sub * sh->sub_pix != pupil->n_pix) return SPECULA_EINVAL;
+  if (!((sh->fft_n == 24 && sh->sub_pix == 12) || (sh->fft_n == 16 && sh->sub_pix == 8)))
+    return SPECULA_EUNSUPPORTED;
+  return SPECULA_OK;
+}
+
+extern "C" int specula_sh_plan(specula_ctx *ctx, const specula_pupil_desc *pupil,
+                               const specula_sh_desc *sh, int32_t *n_valid) {
+  if (!ctx) return SPECULA_EINVAL;
+  int s = check_sh(pupil, sh);
+  if (s) return s;
+  ShPlan *p = sh_plan_find(ctx, pupil, sh);
+  if (!p) {
+    SPECULA_CK(cudaSetDevice(ctx->device));
+    s = sh_plan_build(ctx, pupil, sh, &p);
+    if (s) return s;
+  }
+  if (n_valid) *n_valid = p->n_valid;
+  return SPECULA_OK;
+}
+
+extern "C" int specula_sh_image(specula_ctx *ctx, const specula_pupil_desc *pupil,
+                                const specula_sh_desc *sh, const float *amp_dev,
+                                const float *phase_dev, int32_t n_batch, float *spots_dev,
+                                void *stream) {
+  if (!ctx || !amp_dev || !phase_dev || !spots_dev || n_batch < 0) return SPECULA_EINVAL;
+  int s = check_sh(pupil, sh);
+  if (s) return s;
+  ShPlan *p = sh_plan_find(ctx, pupil, sh);
+  if (!p) return SPECULA_ENOPLAN;
+  if (n_batch == 0) return SPECULA_OK;
+  return sh_run(ctx, p, amp_dev, phase_dev, n_batch, spots_dev, (cudaStream_t)stream);
+}

@@ -1,0 +1,174 @@
+// In-register mixed-radix DFT codelets (FP32 complex) for sm_103a.
+//
+// The pyramid and Shack-Hartmann sensors are FFT pipelines (App. A, Tab. 4:
+// ModulatedPyramid, SH; workload sizes in Sect. 6, Tab. 2).  Every transform
+// here is composed of small DFTs that one thread evaluates on values held in
+// its registers; all indices are compile-time constants after unrolling, so
+// permutations are free register renames and twiddles are constant-bank
+// operands.
+//
+// Twiddle values W_n^j = exp(-2 pi i j / n) come from a table computed on the
+// host in float64 from cos/sin and rounded once to float32 (see
+// upload_codelet_twiddles).  Multiples of a quarter turn are applied exactly.
+//
+// Each translation unit that includes this header gets its own constant
+// table and must call upload_codelet_twiddles() once per device.
+#pragma once
+#include <cuda_runtime.h>
+#include <math.h>
+
+namespace specula {
+
+// ---- small complex helpers ------------------------------------------------
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 cmulc(float2 a, float2 b) {  // a * conj(b)
+  return make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+// multiply by -i (forward) or +i (inverse)
+template <bool INV> __device__ __forceinline__ float2 mul_mi(float2 a) {
+  return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+}
+
+// ---- codelet twiddle table -------------------------------------------------
+// Sizes for which W_n^j is tabulated; offsets are compile-time.
+constexpr int kCodeletSizes[] = {3, 5, 6, 8, 10, 12, 15, 16, 20, 24, 30, 32, 40, 48, 60, 64};
+constexpr int kNumCodeletSizes = sizeof(kCodeletSizes) / sizeof(int);
+constexpr int codelet_offset(int n, int i = 0, int acc = 0) {
+  return i >= kNumCodeletSizes ? -1
+         : (kCodeletSizes[i] == n ? acc : codelet_offset(n, i + 1, acc + kCodeletSizes[i]));
+}
+constexpr int codelet_total(int i = 0) {
+  return i >= kNumCodeletSizes ? 0 : kCodeletSizes[i] + codelet_total(i + 1);
+}
+constexpr int kCodeletTotal = codelet_total();
+
+// (cos, sin) of 2 pi j / n, per TU
+static __constant__ float2 c_codelet_tw[kCodeletTotal];
+
+static inline cudaError_t upload_codelet_twiddles() {
+  float2 h[kCodeletTotal];
+  for (int s = 0; s < kNumCodeletSizes; ++s) {
+    int n = kCodeletSizes[s];
+    int off = codelet_offset(n);
+    for (int j = 0; j < n; ++j) {
+      double a = 2.0 * M_PI * (double)j / (double)n;
+      h[off + j] = make_float2((float)cos(a), (float)sin(a));
+    }
+  }
+  return cudaMemcpyToSymbol(c_codelet_tw, h, sizeof(h));
+}
+
+// W_N^J for the forward (exp(-2 pi i J/N)) or inverse (exp(+...)) sign.
+template <int N, bool INV>
+__device__ __forceinline__ float2 apply_tw(float2 a, int j) {
+  j = j % N;
+  if (j == 0) return a;
+  if (4 * j == N) return mul_mi<INV>(a);
+  if (2 * j == N) return make_float2(-a.x, -a.y);
+  if (4 * j == 3 * N) return mul_mi<!INV>(a);
+  static_assert(codelet_offset(N) >= 0, "codelet size not tabulated");
+  float2 w = c_codelet_tw[codelet_offset(N) + j];
+  return INV ? cmul(a, w) : cmulc(a, w);
+}
+
+// ---- base butterflies --------------------------------------------------------
+template <bool INV> __device__ __forceinline__ void bfly2(float2 &a, float2 &b) {
+  float2 t = a;
+  a = cadd(t, b);
+  b = csub(t, b);
+}
+
+template <bool INV> __device__ __forceinline__ void bfly3(float2 &x0, float2 &x1, float2 &x2) {
+  // c = cos(2pi/3) = -1/2, s = sin(2pi/3) from the table
+  const float2 w = c_codelet_tw[codelet_offset(3) + 1];
+  float2 t1 = cadd(x1, x2);
+  float2 t2 = make_float2(x0.x + w.x * t1.x, x0.y + w.x * t1.y);
+  float2 d = csub(x1, x2);
+  float2 t3 = mul_mi<INV>(make_float2(w.y * d.x, w.y * d.y));
+  x0 = cadd(x0, t1);
+  x1 = cadd(t2, t3);
+  x2 = csub(t2, t3);
+}
+
+template <bool INV> __device__ __forceinline__ void bfly4(float2 &x0, float2 &x1, float2 &x2, float2 &x3) {
+  float2 a = cadd(x0, x2), b = csub(x0, x2);
+  float2 c = cadd(x1, x3), d = mul_mi<INV>(csub(x1, x3));
+  x0 = cadd(a, c);
+  x2 = csub(a, c);
+  x1 = cadd(b, d);
+  x3 = csub(b, d);
+}
+
+template <bool INV>
+__device__ __forceinline__ void bfly5(float2 &x0, float2 &x1, float2 &x2, float2 &x3, float2 &x4) {
+  const float2 w1 = c_codelet_tw[codelet_offset(5) + 1];  // (cos 2pi/5, sin 2pi/5)
+  const float2 w2 = c_codelet_tw[codelet_offset(5) + 2];  // (cos 4pi/5, sin 4pi/5)
+  float2 a1 = cadd(x1, x4), b1 = csub(x1, x4);
+  float2 a2 = cadd(x2, x3), b2 = csub(x2, x3);
+  float2 p1 = make_float2(x0.x + w1.x * a1.x + w2.x * a2.x, x0.y + w1.x * a1.y + w2.x * a2.y);
+  float2 p2 = make_float2(x0.x + w2.x * a1.x + w1.x * a2.x, x0.y + w2.x * a1.y + w1.x * a2.y);
+  float2 q1 = mul_mi<INV>(make_float2(w1.y * b1.x + w2.y * b2.x, w1.y * b1.y + w2.y * b2.y));
+  float2 q2 = mul_mi<INV>(make_float2(w2.y * b1.x - w1.y * b2.x, w2.y * b1.y - w1.y * b2.y));
+  x0 = make_float2(x0.x + a1.x + a2.x, x0.y + a1.y + a2.y);
+  x1 = cadd(p1, q1);
+  x4 = csub(p1, q1);
+  x2 = cadd(p2, q2);
+  x3 = csub(p2, q2);
+}
+
+// ---- generic in-register DFT: X[k] = sum_n x[n] W_N^{nk}, natural order ----
+template <int N> struct first_factor {
+  static constexpr int value = (N % 4 == 0 && N != 8) ? 4 : (N % 2 == 0 ? 2 : (N % 3 == 0 ? 3 : (N % 5 == 0 ? 5 : N)));
+};
+
+template <int N, bool INV> struct RegDFT {
+  static __device__ __forceinline__ void run(float2 (&x)[N]) {
+    constexpr int P = first_factor<N>::value;
+    constexpr int Q = N / P;
+    static_assert(P * Q == N && P > 1, "unsupported codelet size");
+    // n = n1 + P n2, k = Q k1 + k2:
+    //   Y[n1][k2] = W_N^{n1 k2} sum_{n2} x[n1 + P n2] W_Q^{n2 k2}
+    //   X[Q k1 + k2] = sum_{n1} Y[n1][k2] W_P^{n1 k1}
+    float2 y[P][Q];
+#pragma unroll
+    for (int n1 = 0; n1 < P; ++n1) {
+#pragma unroll
+      for (int n2 = 0; n2 < Q; ++n2) y[n1][n2] = x[n1 + P * n2];
+      RegDFT<Q, INV>::run(y[n1]);
+#pragma unroll
+      for (int k2 = 0; k2 < Q; ++k2) y[n1][k2] = apply_tw<N, INV>(y[n1][k2], n1 * k2);
+    }
+#pragma unroll
+    for (int k2 = 0; k2 < Q; ++k2) {
+      float2 z[P];
+#pragma unroll
+      for (int n1 = 0; n1 < P; ++n1) z[n1] = y[n1][k2];
+      RegDFT<P, INV>::run(z);
+#pragma unroll
+      for (int k1 = 0; k1 < P; ++k1) x[Q * k1 + k2] = z[k1];
+    }
+  }
+};
+
+template <bool INV> struct RegDFT<1, INV> {
+  static __device__ __forceinline__ void run(float2 (&)[1]) {}
+};
+template <bool INV> struct RegDFT<2, INV> {
+  static __device__ __forceinline__ void run(float2 (&x)[2]) { bfly2<INV>(x[0], x[1]); }
+};
+template <bool INV> struct RegDFT<3, INV> {
+  static __device__ __forceinline__ void run(float2 (&x)[3]) { bfly3<INV>(x[0], x[1], x[2]); }
+};
+template <bool INV> struct RegDFT<4, INV> {
+  static __device__ __forceinline__ void run(float2 (&x)[4]) { bfly4<INV>(x[0], x[1], x[2], x[3]); }
+};
+template <bool INV> struct RegDFT<5, INV> {
+  static __device__ __forceinline__ void run(float2 (&x)[5]) { bfly5<INV>(x[0], x[1], x[2], x[3], x[4]); }
+};
+
+}  // namespace specula

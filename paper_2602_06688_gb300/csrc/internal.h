@@ -1,0 +1,130 @@
+// Internal declarations shared by the translation units of libspecula_gb300.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <memory>
+#include <vector>
+
+#include "../../include/specula_gb300.h"
+
+#define SPECULA_CK(call)                                   \
+  do {                                                     \
+    cudaError_t e_ = (call);                               \
+    if (e_ != cudaSuccess) return SPECULA_ECUDA;           \
+  } while (0)
+
+#define SPECULA_CK_LAUNCH()                                \
+  do {                                                     \
+    cudaError_t e_ = cudaGetLastError();                   \
+    if (e_ != cudaSuccess) return SPECULA_ECUDA;           \
+  } while (0)
+
+namespace specula {
+
+// A device buffer owned by a plan.
+struct DevBuf {
+  void *p = nullptr;
+  size_t bytes = 0;
+  DevBuf() = default;
+  DevBuf(const DevBuf &) = delete;
+  DevBuf &operator=(const DevBuf &) = delete;
+  ~DevBuf() { if (p) cudaFree(p); }
+  int alloc(size_t n) {
+    if (p) { cudaFree(p); p = nullptr; }
+    bytes = n;
+    if (n == 0) return SPECULA_OK;
+    return cudaMalloc(&p, n) == cudaSuccess ? SPECULA_OK : SPECULA_ENOMEM;
+  }
+  int upload(const void *h, size_t n) {
+    int s = alloc(n);
+    if (s) return s;
+    return cudaMemcpy(p, h, n, cudaMemcpyHostToDevice) == cudaSuccess ? SPECULA_OK : SPECULA_ECUDA;
+  }
+  template <class T> T *as() const { return static_cast<T *>(p); }
+};
+
+// Pyramid plan: tables and the per-chunk intermediate workspace.
+struct PwfsPlan {
+  int n_pix, pad, n_mod, n_sub, pup_dist;
+  double mod_amp;
+  int N, N1, N2;
+  int chunk;            // modulation items per pipeline chunk
+  int ka;               // items per warp in the row-forward pass
+  DevBuf gx, gy;        // [n_mod][n_pix] float2: tilt x pre-phase (x and y parts)
+  DevBuf mask;          // [N] float2: pyramid mask factor per axis, x (1/N)
+  DevBuf twA, twB;      // [N] float2: inter-step twiddles (cos, sin)
+  DevBuf rows;          // [chunk][n_pix][N] float2: after the row transform
+  DevBuf cols;          // [chunk][N][N] float2: after the column pass
+};
+
+struct ShPlan {
+  int n_pix, n_sub, sub_pix, fft_n;
+  int n_valid;
+  DevBuf valid;         // [n_valid] int32
+  DevBuf pre;           // [fft_n] float2: centred-DFT input phase
+  DevBuf tw;            // [fft_n] float2 twiddles
+};
+
+}  // namespace specula
+
+struct specula_ctx {
+  int device = 0;
+  int32_t *status_dev = nullptr;
+  std::vector<std::unique_ptr<specula::PwfsPlan>> pwfs;
+  std::vector<std::unique_ptr<specula::ShPlan>> sh;
+  // tracing: kernels launched, and optional per-kernel CUDA-event pairs
+  int64_t launches = 0;
+  bool prof = false;
+  std::vector<cudaEvent_t> ev;      // 2 per record
+  size_t ev_next = 0;
+  std::vector<int> rec_kid;         // kernel id of record i (events 2i, 2i+1)
+};
+
+namespace specula {
+
+// Bracket one kernel launch with events on its stream when tracing is on.
+inline int prof_begin(specula_ctx *c, cudaStream_t st) {
+  c->launches++;
+  if (!c->prof || c->ev_next + 2 > c->ev.size()) return -1;
+  const int slot = (int)c->ev_next;
+  c->ev_next += 2;
+  cudaEventRecord(c->ev[slot], st);
+  return slot;
+}
+inline void prof_end(specula_ctx *c, int slot, int kid, cudaStream_t st) {
+  if (slot < 0) return;
+  cudaEventRecord(c->ev[slot + 1], st);
+  c->rec_kid.push_back(kid);   // capacity reserved when tracing is enabled
+}
+
+#define SPECULA_LAUNCH(ctx, kid, st, ...)            \
+  do {                                               \
+    const int slot_ = prof_begin((ctx), (st));       \
+    __VA_ARGS__;                                     \
+    SPECULA_CK_LAUNCH();                             \
+    prof_end((ctx), slot_, (kid), (st));             \
+  } while (0)
+// per-translation-unit device initialisation (constant tables)
+int pwfs_init_device();
+int sh_init_device();
+
+// launchers implemented in the kernel translation units
+int pwfs_plan_build(specula_ctx *ctx, const specula_pupil_desc *pupil,
+                    const specula_pwfs_desc *pwfs, PwfsPlan **out);
+PwfsPlan *pwfs_plan_find(specula_ctx *ctx, const specula_pupil_desc *pupil,
+                         const specula_pwfs_desc *pwfs);
+int pwfs_set_tiles(PwfsPlan *p, int chunk, int ka);
+int pwfs_run(specula_ctx *ctx, PwfsPlan *plan, const float *amp, const float *phase,
+             int n_batch, float *det, cudaStream_t st);
+int sh_plan_build(specula_ctx *ctx, const specula_pupil_desc *pupil,
+                  const specula_sh_desc *sh, ShPlan **out);
+ShPlan *sh_plan_find(specula_ctx *ctx, const specula_pupil_desc *pupil,
+                     const specula_sh_desc *sh);
+int sh_run(specula_ctx *ctx, ShPlan *plan, const float *amp, const float *phase,
+           int n_batch, float *spots, cudaStream_t st);
+
+// host geometry (api.cu)
+int host_pupil_mask(int n, double obsc, uint8_t *mask);
+int host_valid_subaps(int n, double obsc, int n_sub, int32_t *idx, int32_t *n_valid);
+}  // namespace specula

@@ -1,0 +1,510 @@
+// Modulated pyramid wavefront sensor image (ModulatedPyramid + CCD binning,
+// App. A, Tab. 4; parameters of App. B, Listing 2).
+//
+// Per modulation point m the sensor computes, on the N x N padded grid
+// (N = 2 n_pix), I_m = |IDFT2( M . DFT2( pad(E . tilt_m) ) )|^2 with centred
+// transforms.  The centred forward transform is an unshifted FFT between an
+// input phase p(n) = exp(i pi (N-1) n / N) and an output phase; the output
+// phase cancels against the input phase of the centred inverse, whose own
+// output phase disappears in |.|^2.  So the GPU evaluates
+//     I_m = |IFFT2( M . FFT2( pad(E . tilt_m . p_x p_y) ) )|^2 / N^4,
+// with tilt_m . p folded into per-axis tables gx[m][i], gy[m][j] and the
+// 1/N^2 folded into the per-axis mask tables.
+//
+// Pipeline, one chunk of K (batch, modulation-point) items at a time so that
+// the intermediates stay L2-resident:
+//   A  k_rows_fwd     field E = amp exp(i phase) (sincos once per row and
+//                     batch element), times gx gy, row FFT of the n_pix
+//                     non-zero rows (input half zero: pruned)   -> rows ws
+//   B  k_cols         per column tile: column FFT (pruned) -> mask ->
+//                     inverse column FFT, all in shared memory -> cols ws
+//   C  k_rows_inv_bin row inverse FFT -> |.|^2 -> sum over the chunk's
+//                     modulation points in registers -> b x b binning ->
+//                     detector (written by the chunk holding m = 0, then
+//                     accumulated in chunk order: deterministic, no atomics)
+//
+// Each N-point transform is a two-level split N = N1 x N2 evaluated by one
+// group of G lanes: step 1, lane n1 < N1 holds x[n1 + N1 n2] (n2 < N2) and
+// does an N2-point register DFT, multiplies by W_N^{n1 k2}; the values are
+// exchanged through shared memory; step 2, lane k2 < N2 does an N1-point
+// register DFT and holds X[N2 k1 + k2].  With N2 % 4 == 0 the non-zero half
+// of a zero-padded input (indices N/4 .. 3N/4) is exactly registers
+// N2/4 .. 3N2/4 of every lane, so zero inputs are never loaded.
+#include <math.h>
+
+#include <algorithm>
+
+#include "fft_regs.cuh"
+#include "internal.h"
+
+namespace specula {
+
+int pwfs_init_device() {
+  return upload_codelet_twiddles() == cudaSuccess ? SPECULA_OK : SPECULA_ECUDA;
+}
+
+template <int N1_, int N2_> struct Split {
+  static constexpr int N1 = N1_, N2 = N2_, N = N1_ * N2_;
+  static constexpr int MX = N1_ > N2_ ? N1_ : N2_;
+  static constexpr int G = MX <= 8 ? 8 : (MX <= 16 ? 16 : 32);  // lanes per vector
+  static constexpr int S1 = N1_ | 1;   // exchange stride, standard split (odd: no conflicts)
+  static constexpr int S2 = N2_ | 1;   // exchange stride, swapped split
+  static constexpr int XB = N2_ * S1;  // exchange buffer per vector (complex)
+  static_assert(N2_ % 4 == 0, "pruned zero-padded input needs N2 % 4 == 0");
+  static_assert(MX <= 32, "one vector per warp at most");
+};
+
+constexpr int round_cs(int base) { return base + ((2 - base % 16) + 16) % 16; }
+constexpr int imax3(int a, int b, int c) { return a > b ? (a > c ? a : c) : (b > c ? b : c); }
+
+// --------------------------------------------------------------------------
+// Pass A: field formation + modulation tilt + row FFT of the non-zero rows.
+// grid (ceil(n_pix / VPC), ceil(n_items / ka)); block VPC * G threads.
+template <int N1, int N2>
+__global__ void __launch_bounds__(256) k_rows_fwd(
+    const float *__restrict__ amp, const float *__restrict__ phase,
+    const float2 *__restrict__ gx, const float2 *__restrict__ gy,
+    const float2 *__restrict__ twA, float2 *__restrict__ rows_out, int n_pix, int n_mod,
+    int item0, int n_items, int ka) {
+  using S = Split<N1, N2>;
+  constexpr int N = S::N, G = S::G, S1 = S::S1;
+  constexpr int Q0 = N2 / 4, QH = N2 / 2;
+  extern __shared__ float2 smem[];
+  float2 *s_tw = smem;
+  const int vpc = blockDim.x / G;
+  for (int t = threadIdx.x; t < N; t += blockDim.x) s_tw[t] = twA[t];
+  const int vec = threadIdx.x / G, lane = threadIdx.x % G;
+  float2 *xb = smem + N + vec * S::XB;
+  const int j = blockIdx.x * vpc + vec;
+  const bool row_ok = j < n_pix;
+  const bool in_lane = row_ok && lane < N1;
+  __syncthreads();
+
+  float2 e[QH];
+  int cur_b = -1;
+  const int it_begin = blockIdx.y * ka;
+  for (int q = 0; q < ka; ++q) {
+    const int it = it_begin + q;
+    if (it >= n_items) break;
+    const int gi = item0 + it;
+    const int b = gi / n_mod, m = gi - b * n_mod;
+    if (b != cur_b) {
+      cur_b = b;
+#pragma unroll
+      for (int h = 0; h < QH; ++h) {
+        e[h] = make_float2(0.f, 0.f);
+        if (in_lane) {
+          const int i = lane + N1 * h;   // = lane + N1 (n2 - N2/4)
+          const size_t p = (size_t)j * n_pix + i;
+          float sv, cv;
+          sincosf(phase[(size_t)b * n_pix * n_pix + p], &sv, &cv);
+          const float a = amp[p];
+          e[h] = make_float2(a * cv, a * sv);
+        }
+      }
+    }
+    float2 r[N2];
+    const float2 gyv = row_ok ? gy[(size_t)m * n_pix + j] : make_float2(0.f, 0.f);
+#pragma unroll
+    for (int n2 = 0; n2 < N2; ++n2) r[n2] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int h = 0; h < QH; ++h) {
+      if (in_lane) {
+        const int i = lane + N1 * h;
+        r[Q0 + h] = cmul(cmul(e[h], gx[(size_t)m * n_pix + i]), gyv);
+      }
+    }
+    RegDFT<N2, false>::run(r);
+    __syncwarp();
+    if (lane < N1) {
+#pragma unroll
+      for (int k2 = 0; k2 < N2; ++k2) xb[k2 * S1 + lane] = cmulc(r[k2], s_tw[k2 * N1 + lane]);
+    }
+    __syncwarp();
+    if (lane < N2) {
+      float2 r2[N1];
+#pragma unroll
+      for (int n1 = 0; n1 < N1; ++n1) r2[n1] = xb[lane * S1 + n1];
+      RegDFT<N1, false>::run(r2);
+      if (row_ok) {
+        float2 *dst = rows_out + ((size_t)it * n_pix + j) * N + lane;
+#pragma unroll
+        for (int k1 = 0; k1 < N1; ++k1) dst[N2 * k1] = r2[k1];
+      }
+    }
+  }
+}
+
+// --------------------------------------------------------------------------
+// Pass B: per tile of TC columns: column FFT (rows n_pix non-zero) -> pyramid
+// mask -> inverse column FFT, all in shared memory.
+// grid (N / TC, n_items); block TC * G threads.
+template <int N1, int N2, int TC>
+struct ColsCfg {
+  using S = Split<N1, N2>;
+  static constexpr int CS = round_cs(imax3(S::N, N2 * S::S1, N1 * S::S2));
+  static constexpr size_t smem = (size_t)(2 * S::N + TC * CS) * sizeof(float2);
+};
+
+template <int N1, int N2, int TC>
+__global__ void __launch_bounds__(256) k_cols(
+    const float2 *__restrict__ rows_in, float2 *__restrict__ cols_out,
+    const float2 *__restrict__ twA, const float2 *__restrict__ twB,
+    const float2 *__restrict__ mask, int n_pix) {
+  using S = Split<N1, N2>;
+  constexpr int N = S::N, G = S::G, S1 = S::S1, S2 = S::S2;
+  constexpr int CS = ColsCfg<N1, N2, TC>::CS;
+  constexpr int Q0 = N2 / 4, QH = N2 / 2;
+  extern __shared__ float2 smem[];
+  float2 *s_twA = smem, *s_twB = smem + N, *s_tile = smem + 2 * N;
+  const int it = blockIdx.y;
+  const int col0 = blockIdx.x * TC;
+  constexpr int off = N / 4;
+  for (int t = threadIdx.x; t < N; t += blockDim.x) {
+    s_twA[t] = twA[t];
+    s_twB[t] = twB[t];
+  }
+  const float2 *src = rows_in + (size_t)it * n_pix * N + col0;
+  for (int e = threadIdx.x; e < n_pix * TC; e += blockDim.x) {
+    const int c = e % TC, jj = e / TC;
+    s_tile[c * CS + off + jj] = src[(size_t)jj * N + c];
+  }
+  __syncthreads();
+
+  const int vec = threadIdx.x / G, lane = threadIdx.x % G;
+  float2 *col = s_tile + vec * CS;
+
+  // forward, standard split; non-zero input rows are registers Q0..Q0+QH-1
+  float2 r[N2];
+#pragma unroll
+  for (int n2 = 0; n2 < N2; ++n2) r[n2] = make_float2(0.f, 0.f);
+  if (lane < N1) {
+#pragma unroll
+    for (int h = 0; h < QH; ++h) r[Q0 + h] = col[lane + N1 * (Q0 + h)];
+  }
+  RegDFT<N2, false>::run(r);
+  __syncwarp();
+  if (lane < N1) {
+#pragma unroll
+    for (int k2 = 0; k2 < N2; ++k2) col[k2 * S1 + lane] = cmulc(r[k2], s_twA[k2 * N1 + lane]);
+  }
+  __syncwarp();
+  float2 r2[N1];
+  if (lane < N2) {
+#pragma unroll
+    for (int n1 = 0; n1 < N1; ++n1) r2[n1] = col[lane * S1 + n1];
+  } else {
+#pragma unroll
+    for (int n1 = 0; n1 < N1; ++n1) r2[n1] = make_float2(0.f, 0.f);
+  }
+  RegDFT<N1, false>::run(r2);
+  // lane k2 holds F[v = N2 k1 + k2] of column k = col0 + vec
+  const float2 mk = mask[col0 + vec];
+  if (lane < N2) {
+#pragma unroll
+    for (int k1 = 0; k1 < N1; ++k1) r2[k1] = cmul(r2[k1], cmul(mask[N2 * k1 + lane], mk));
+  }
+  // inverse, swapped split: lane n1' = k2 (< N2), registers n2' = k1 (< N1)
+  RegDFT<N1, true>::run(r2);
+  __syncwarp();
+  if (lane < N2) {
+#pragma unroll
+    for (int k2 = 0; k2 < N1; ++k2) col[k2 * S2 + lane] = cmul(r2[k2], s_twB[k2 * N2 + lane]);
+  }
+  __syncwarp();
+  float2 r3[N2];
+  if (lane < N1) {
+#pragma unroll
+    for (int n1 = 0; n1 < N2; ++n1) r3[n1] = col[lane * S2 + n1];
+  } else {
+#pragma unroll
+    for (int n1 = 0; n1 < N2; ++n1) r3[n1] = make_float2(0.f, 0.f);
+  }
+  RegDFT<N2, true>::run(r3);
+  __syncwarp();
+  if (lane < N1) {
+#pragma unroll
+    for (int k1 = 0; k1 < N2; ++k1) col[N1 * k1 + lane] = r3[k1];   // y = N1 k1' + k2'
+  }
+  __syncthreads();
+  float2 *dst = cols_out + (size_t)it * N * N + col0;
+  for (int e = threadIdx.x; e < N * TC; e += blockDim.x) {
+    const int c = e % TC, y = e / TC;
+    dst[(size_t)y * N + c] = s_tile[c * CS + y];
+  }
+}
+
+// --------------------------------------------------------------------------
+// Pass C: row inverse FFT, |.|^2, sum over the chunk's modulation points,
+// b x b binning into the detector.  grid (N / bsz); block round32(bsz * G).
+template <int N1, int N2>
+__device__ __forceinline__ void flush_bins(const float *s_I, float *det, int N, int bsz,
+                                           int strip, bool first) {
+  const int nd = N / bsz;
+  for (int q = threadIdx.x; q < nd; q += blockDim.x) {
+    float v = 0.f;
+    for (int rr = 0; rr < bsz; ++rr)
+      for (int xx = 0; xx < bsz; ++xx) v += s_I[rr * N + q * bsz + xx];
+    float *d = det + (size_t)strip * nd + q;
+    if (first) *d = v;
+    else *d += v;
+  }
+}
+
+template <int N1, int N2>
+__global__ void __launch_bounds__(256) k_rows_inv_bin(
+    const float2 *__restrict__ cols_in, const float2 *__restrict__ twA, float *__restrict__ det,
+    int n_mod, int item0, int n_items, int bsz, float scale) {
+  using S = Split<N1, N2>;
+  constexpr int N = S::N, G = S::G, S1 = S::S1;
+  extern __shared__ float2 smem[];
+  float2 *s_tw = smem;
+  const int nvec = blockDim.x / G;
+  float *s_I = reinterpret_cast<float *>(smem + N + nvec * S::XB);   // [bsz][N]
+  for (int t = threadIdx.x; t < N; t += blockDim.x) s_tw[t] = twA[t];
+  const int vec = threadIdx.x / G, lane = threadIdx.x % G;
+  float2 *xb = smem + N + vec * S::XB;
+  const bool act = vec < bsz;
+  const int y = blockIdx.x * bsz + vec;
+  const int nd = N / bsz;
+  __syncthreads();
+
+  float acc[N1];
+#pragma unroll
+  for (int k1 = 0; k1 < N1; ++k1) acc[k1] = 0.f;
+  int cur_b = item0 / n_mod;
+  bool first = (item0 - cur_b * n_mod) == 0;
+  for (int it = 0; it < n_items; ++it) {
+    const int gi = item0 + it;
+    const int b = gi / n_mod, m = gi - b * n_mod;
+    if (b != cur_b) {
+      if (act && lane < N2) {
+#pragma unroll
+        for (int k1 = 0; k1 < N1; ++k1) s_I[vec * N + N2 * k1 + lane] = acc[k1] * scale;
+      }
+      __syncthreads();
+      flush_bins<N1, N2>(s_I, det + (size_t)cur_b * nd * nd, N, bsz, blockIdx.x, first);
+      __syncthreads();
+#pragma unroll
+      for (int k1 = 0; k1 < N1; ++k1) acc[k1] = 0.f;
+      cur_b = b;
+      first = (m == 0);
+    }
+    float2 r[N2];
+    if (act && lane < N1) {
+      const float2 *src = cols_in + ((size_t)it * N + y) * N + lane;
+#pragma unroll
+      for (int n2 = 0; n2 < N2; ++n2) r[n2] = src[N1 * n2];
+    } else {
+#pragma unroll
+      for (int n2 = 0; n2 < N2; ++n2) r[n2] = make_float2(0.f, 0.f);
+    }
+    RegDFT<N2, true>::run(r);
+    __syncwarp();
+    if (lane < N1) {
+#pragma unroll
+      for (int k2 = 0; k2 < N2; ++k2) xb[k2 * S1 + lane] = cmul(r[k2], s_tw[k2 * N1 + lane]);
+    }
+    __syncwarp();
+    if (lane < N2) {
+      float2 r2[N1];
+#pragma unroll
+      for (int n1 = 0; n1 < N1; ++n1) r2[n1] = xb[lane * S1 + n1];
+      RegDFT<N1, true>::run(r2);
+#pragma unroll
+      for (int k1 = 0; k1 < N1; ++k1) acc[k1] += r2[k1].x * r2[k1].x + r2[k1].y * r2[k1].y;
+    }
+  }
+  if (act && lane < N2) {
+#pragma unroll
+    for (int k1 = 0; k1 < N1; ++k1) s_I[vec * N + N2 * k1 + lane] = acc[k1] * scale;
+  }
+  __syncthreads();
+  flush_bins<N1, N2>(s_I, det + (size_t)cur_b * nd * nd, N, bsz, blockIdx.x, first);
+}
+
+// --------------------------------------------------------------------------
+// host side
+
+constexpr int kColsTile = 8;
+
+struct Launch {
+  size_t smemA, smemB, smemC;
+  int blockA, blockB, blockC;
+};
+
+template <int N1, int N2>
+static int configure(int bsz, Launch *L) {
+  using S = Split<N1, N2>;
+  L->blockA = 256;
+  const int vpcA = 256 / S::G;
+  L->smemA = (size_t)(S::N + vpcA * S::XB) * sizeof(float2);
+  L->blockB = kColsTile * S::G;
+  L->smemB = ColsCfg<N1, N2, kColsTile>::smem;
+  const int thrC = ((bsz * S::G + 31) / 32) * 32;
+  if (thrC > 256) return SPECULA_EUNSUPPORTED;   // bin side too large for one CTA strip
+  L->blockC = thrC;
+  const int nvecC = thrC / S::G;
+  L->smemC = (size_t)(S::N + nvecC * S::XB) * sizeof(float2) + (size_t)bsz * S::N * sizeof(float);
+  if (L->smemA > 227 * 1024 || L->smemB > 227 * 1024 || L->smemC > 227 * 1024) return SPECULA_EUNSUPPORTED;
+  if (cudaFuncSetAttribute(k_rows_fwd<N1, N2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L->smemA) != cudaSuccess) return SPECULA_ECUDA;
+  if (cudaFuncSetAttribute(k_cols<N1, N2, kColsTile>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L->smemB) != cudaSuccess) return SPECULA_ECUDA;
+  if (cudaFuncSetAttribute(k_rows_inv_bin<N1, N2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L->smemC) != cudaSuccess) return SPECULA_ECUDA;
+  return SPECULA_OK;
+}
+
+template <int N1, int N2>
+static int run_split(specula_ctx *ctx, PwfsPlan *p, const float *amp, const float *phase, int n_batch, float *det,
+                     cudaStream_t st) {
+  using S = Split<N1, N2>;
+  const int bsz = p->n_pix / p->n_sub;
+  Launch L;
+  int s = configure<N1, N2>(bsz, &L);
+  if (s) return s;
+  const int total = n_batch * p->n_mod;
+  const int vpcA = L.blockA / S::G;
+  const float scale = 1.0f / (float)p->n_mod;
+  for (int i0 = 0; i0 < total; i0 += p->chunk) {
+    const int ni = std::min(p->chunk, total - i0);
+    dim3 gA((p->n_pix + vpcA - 1) / vpcA, (ni + p->ka - 1) / p->ka);
+    SPECULA_LAUNCH(ctx, SPECULA_K_PWFS_ROWS_FWD, st,
+                   k_rows_fwd<N1, N2><<<gA, L.blockA, L.smemA, st>>>(
+                       amp, phase, p->gx.as<float2>(), p->gy.as<float2>(), p->twA.as<float2>(),
+                       p->rows.as<float2>(), p->n_pix, p->n_mod, i0, ni, p->ka));
+    dim3 gB(S::N / kColsTile, ni);
+    SPECULA_LAUNCH(ctx, SPECULA_K_PWFS_COLS, st,
+                   k_cols<N1, N2, kColsTile><<<gB, L.blockB, L.smemB, st>>>(
+                       p->rows.as<float2>(), p->cols.as<float2>(), p->twA.as<float2>(),
+                       p->twB.as<float2>(), p->mask.as<float2>(), p->n_pix));
+    SPECULA_LAUNCH(ctx, SPECULA_K_PWFS_ROWS_INV, st,
+                   k_rows_inv_bin<N1, N2><<<S::N / bsz, L.blockC, L.smemC, st>>>(
+                       p->cols.as<float2>(), p->twA.as<float2>(), det, p->n_mod, i0, ni, bsz,
+                       scale));
+  }
+  return SPECULA_OK;
+}
+
+static bool split_for(int N, int *N1, int *N2) {
+  switch (N) {
+    case 64: *N1 = 8; *N2 = 8; return true;
+    case 128: *N1 = 8; *N2 = 16; return true;
+    case 240: *N1 = 15; *N2 = 16; return true;
+    case 320: *N1 = 20; *N2 = 16; return true;
+    case 960: *N1 = 30; *N2 = 32; return true;
+    default: return false;
+  }
+}
+
+int pwfs_set_tiles(PwfsPlan *p, int chunk, int ka) {
+  const size_t need_rows = (size_t)chunk * p->n_pix * p->N * sizeof(float2);
+  const size_t need_cols = (size_t)chunk * p->N * p->N * sizeof(float2);
+  int s;
+  if (need_rows > p->rows.bytes || need_cols > p->cols.bytes) {
+    cudaDeviceSynchronize();   // the old workspace may still be in use
+    if ((s = p->rows.alloc(need_rows))) return s;
+    if ((s = p->cols.alloc(need_cols))) return s;
+  }
+  p->chunk = chunk;
+  p->ka = ka;
+  return SPECULA_OK;
+}
+
+int pwfs_run(specula_ctx *ctx, PwfsPlan *p, const float *amp, const float *phase, int n_batch,
+             float *det, cudaStream_t st) {
+  switch (p->N) {
+    case 64: return run_split<8, 8>(ctx, p, amp, phase, n_batch, det, st);
+    case 128: return run_split<8, 16>(ctx, p, amp, phase, n_batch, det, st);
+    case 240: return run_split<15, 16>(ctx, p, amp, phase, n_batch, det, st);
+    case 320: return run_split<20, 16>(ctx, p, amp, phase, n_batch, det, st);
+    case 960: return run_split<30, 32>(ctx, p, amp, phase, n_batch, det, st);
+    default: return SPECULA_EUNSUPPORTED;
+  }
+}
+
+PwfsPlan *pwfs_plan_find(specula_ctx *ctx, const specula_pupil_desc *pupil,
+                         const specula_pwfs_desc *d) {
+  for (auto &p : ctx->pwfs)
+    if (p->n_pix == pupil->n_pix && p->pad == d->pad && p->n_mod == d->n_mod &&
+        p->n_sub == d->n_sub && p->pup_dist == d->pup_dist_px && p->mod_amp == d->mod_amp)
+      return p.get();
+  return nullptr;
+}
+
+// exp(i * pi * num / den) with num reduced exactly modulo 2 den
+static inline void exp_ipi(long long num, long long den, double *c, double *s) {
+  long long r = num % (2 * den);
+  if (r < 0) r += 2 * den;
+  const double a = M_PI * (double)r / (double)den;
+  *c = cos(a);
+  *s = sin(a);
+}
+
+int pwfs_plan_build(specula_ctx *ctx, const specula_pupil_desc *pupil,
+                    const specula_pwfs_desc *d, PwfsPlan **out) {
+  const int Np = pupil->n_pix, N = d->pad * Np;
+  int N1, N2;
+  if (!split_for(N, &N1, &N2)) return SPECULA_EUNSUPPORTED;
+  std::unique_ptr<PwfsPlan> p(new PwfsPlan());
+  p->n_pix = Np; p->pad = d->pad; p->n_mod = d->n_mod; p->n_sub = d->n_sub;
+  p->pup_dist = d->pup_dist_px; p->mod_amp = d->mod_amp;
+  p->N = N; p->N1 = N1; p->N2 = N2;
+  const int off = (N - Np) / 2;
+
+  // modulation tilt x centred-DFT input phase, per axis, float64 -> float32
+  std::vector<float2> gx((size_t)d->n_mod * Np), gy((size_t)d->n_mod * Np);
+  for (int m = 0; m < d->n_mod; ++m) {
+    const double th = 2.0 * M_PI * m / d->n_mod;
+    const double ct = cos(th), sn = sin(th);
+    for (int i = 0; i < Np; ++i) {
+      const double x = (double)i - (Np - 1) / 2.0;
+      double pc, ps;
+      exp_ipi((long long)(N - 1) * (off + i), N, &pc, &ps);
+      const double ax = 2.0 * M_PI * d->mod_amp * x * ct / Np;
+      const double ay = 2.0 * M_PI * d->mod_amp * x * sn / Np;
+      const double cx = cos(ax), sx = sin(ax), cy = cos(ay), sy = sin(ay);
+      gx[(size_t)m * Np + i] = make_float2((float)(cx * pc - sx * ps), (float)(cx * ps + sx * pc));
+      gy[(size_t)m * Np + i] = make_float2((float)(cy * pc - sy * ps), (float)(cy * ps + sy * pc));
+    }
+  }
+  // pyramid mask per axis: exp(-2 pi i c |u| / N) / N, c = pup_dist / 2,
+  // u = k - (N-1)/2: angle = -pi pup_dist |2k - N + 1| / (2N)
+  std::vector<float2> mk(N);
+  for (int k = 0; k < N; ++k) {
+    long long a = 2LL * k - N + 1;
+    if (a < 0) a = -a;
+    double c, s;
+    exp_ipi(-(long long)d->pup_dist_px * a, 2LL * N, &c, &s);
+    mk[k] = make_float2((float)(c / N), (float)(s / N));
+  }
+  // inter-step twiddles (cos, sin)(2 pi (a b mod N) / N)
+  std::vector<float2> ta(N), tb(N);
+  for (int a = 0; a < N2; ++a)
+    for (int b = 0; b < N1; ++b) {
+      double c, s;
+      exp_ipi(2LL * ((long long)a * b % N), N, &c, &s);
+      ta[a * N1 + b] = make_float2((float)c, (float)s);
+    }
+  for (int a = 0; a < N1; ++a)
+    for (int b = 0; b < N2; ++b) {
+      double c, s;
+      exp_ipi(2LL * ((long long)a * b % N), N, &c, &s);
+      tb[a * N2 + b] = make_float2((float)c, (float)s);
+    }
+  int s;
+  if ((s = p->gx.upload(gx.data(), gx.size() * sizeof(float2)))) return s;
+  if ((s = p->gy.upload(gy.data(), gy.size() * sizeof(float2)))) return s;
+  if ((s = p->mask.upload(mk.data(), mk.size() * sizeof(float2)))) return s;
+  if ((s = p->twA.upload(ta.data(), ta.size() * sizeof(float2)))) return s;
+  if ((s = p->twB.upload(tb.data(), tb.size() * sizeof(float2)))) return s;
+
+  // chunk: keep the two intermediates of a chunk near 48 MB (L2-resident)
+  const size_t per_item = ((size_t)Np * N + (size_t)N * N) * sizeof(float2);
+  int chunk = (int)std::max<size_t>(1, (48u << 20) / per_item);
+  chunk = std::min(chunk, 64);
+  if ((s = pwfs_set_tiles(p.get(), chunk, 2))) return s;
+  *out = p.get();
+  ctx->pwfs.push_back(std::move(p));
+  return SPECULA_OK;
+}
+
+}  // namespace specula

@@ -1,0 +1,204 @@
+// Modal reconstructor: modes[b] = R slopes[b] (Modalrec / Recmat, App. A,
+// Tabs. 3-4; Listing 2 `recmat_object`).
+//
+// At batch 1 the product is bound by reading R once from HBM (4 bytes per
+// element in float32, 2 in bfloat16).  One warp owns one row of R and streams
+// it with 16-byte loads that bypass L1 allocation; the slope vectors stay in
+// L1 through read-only loads.  NB slope vectors share each row load.  The
+// per-lane partial sums run in a fixed order and are combined by a fixed
+// shuffle tree: bit-reproducible.
+#include <cuda_bf16.h>
+
+#include "internal.h"
+
+namespace specula {
+
+constexpr int kReconWarps = 8;
+
+__device__ __forceinline__ float4 ld_stream(const float4 *p) {
+  float4 v;
+  asm volatile("ld.global.nc.L1::no_allocate.v4.f32 {%0,%1,%2,%3}, [%4];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "l"(p));
+  return v;
+}
+__device__ __forceinline__ uint4 ld_stream_u4(const uint4 *p) {
+  uint4 v;
+  asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "l"(p));
+  return v;
+}
+__device__ __forceinline__ float bf_lo(uint32_t u) { return __uint_as_float(u << 16); }
+__device__ __forceinline__ float bf_hi(uint32_t u) { return __uint_as_float(u & 0xffff0000u); }
+
+__device__ __forceinline__ float warp_sum_r(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// FP32, vectorised (n_slopes % 4 == 0, 16-byte aligned rows).
+template <int NB>
+__global__ void __launch_bounds__(kReconWarps * 32) k_mvm_f32(
+    const float *__restrict__ R, const float *__restrict__ s, float *__restrict__ m, int n_modes,
+    int n_slopes, int n_batch, int b0) {
+  const int row = blockIdx.x * kReconWarps + threadIdx.x / 32;
+  const int lane = threadIdx.x & 31;
+  if (row >= n_modes) return;
+  const float4 *r4 = reinterpret_cast<const float4 *>(R + (size_t)row * n_slopes);
+  const int n4 = n_slopes / 4;
+  float acc[NB];
+#pragma unroll
+  for (int q = 0; q < NB; ++q) acc[q] = 0.f;
+  for (int j = lane; j < n4; j += 32) {
+    const float4 a = ld_stream(r4 + j);
+#pragma unroll
+    for (int q = 0; q < NB; ++q) {
+      if (b0 + q < n_batch) {
+        const float4 x = __ldg(reinterpret_cast<const float4 *>(s + (size_t)(b0 + q) * n_slopes) + j);
+        acc[q] += a.x * x.x + a.y * x.y + a.z * x.z + a.w * x.w;
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < NB; ++q) {
+    const float v = warp_sum_r(acc[q]);
+    if (lane == 0 && b0 + q < n_batch) m[(size_t)(b0 + q) * n_modes + row] = v;
+  }
+}
+
+// FP32, scalar fallback for unaligned sizes.
+__global__ void __launch_bounds__(kReconWarps * 32) k_mvm_f32_scalar(
+    const float *__restrict__ R, const float *__restrict__ s, float *__restrict__ m, int n_modes,
+    int n_slopes, int n_batch) {
+  const int row = blockIdx.x * kReconWarps + threadIdx.x / 32;
+  const int lane = threadIdx.x & 31;
+  if (row >= n_modes) return;
+  for (int b = 0; b < n_batch; ++b) {
+    float acc = 0.f;
+    for (int j = lane; j < n_slopes; j += 32)
+      acc += R[(size_t)row * n_slopes + j] * s[(size_t)b * n_slopes + j];
+    acc = warp_sum_r(acc);
+    if (lane == 0) m[(size_t)b * n_modes + row] = acc;
+  }
+}
+
+// BF16 (SPLIT = false) or BF16 hi + lo (SPLIT = true); n_slopes % 8 == 0.
+template <int NB, bool SPLIT>
+__global__ void __launch_bounds__(kReconWarps * 32) k_mvm_bf16(
+    const uint16_t *__restrict__ Rh, const uint16_t *__restrict__ Rl, const float *__restrict__ s,
+    float *__restrict__ m, int n_modes, int n_slopes, int n_batch, int b0) {
+  const int row = blockIdx.x * kReconWarps + threadIdx.x / 32;
+  const int lane = threadIdx.x & 31;
+  if (row >= n_modes) return;
+  const uint4 *h8 = reinterpret_cast<const uint4 *>(Rh + (size_t)row * n_slopes);
+  const uint4 *l8 = SPLIT ? reinterpret_cast<const uint4 *>(Rl + (size_t)row * n_slopes) : nullptr;
+  const int n8 = n_slopes / 8;
+  float acc[NB];
+#pragma unroll
+  for (int q = 0; q < NB; ++q) acc[q] = 0.f;
+  for (int j = lane; j < n8; j += 32) {
+    const uint4 hv = ld_stream_u4(h8 + j);
+    float r[8] = {bf_lo(hv.x), bf_hi(hv.x), bf_lo(hv.y), bf_hi(hv.y),
+                  bf_lo(hv.z), bf_hi(hv.z), bf_lo(hv.w), bf_hi(hv.w)};
+    if (SPLIT) {
+      const uint4 lv = ld_stream_u4(l8 + j);
+      r[0] += bf_lo(lv.x); r[1] += bf_hi(lv.x); r[2] += bf_lo(lv.y); r[3] += bf_hi(lv.y);
+      r[4] += bf_lo(lv.z); r[5] += bf_hi(lv.z); r[6] += bf_lo(lv.w); r[7] += bf_hi(lv.w);
+    }
+#pragma unroll
+    for (int q = 0; q < NB; ++q) {
+      if (b0 + q < n_batch) {
+        const float4 *sv = reinterpret_cast<const float4 *>(s + (size_t)(b0 + q) * n_slopes) + 2 * j;
+        const float4 x0 = __ldg(sv), x1 = __ldg(sv + 1);
+        acc[q] += r[0] * x0.x + r[1] * x0.y + r[2] * x0.z + r[3] * x0.w +
+                  r[4] * x1.x + r[5] * x1.y + r[6] * x1.z + r[7] * x1.w;
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < NB; ++q) {
+    const float v = warp_sum_r(acc[q]);
+    if (lane == 0 && b0 + q < n_batch) m[(size_t)(b0 + q) * n_modes + row] = v;
+  }
+}
+
+__global__ void k_convert_bf16(const float *__restrict__ R, uint16_t *__restrict__ hi,
+                               uint16_t *__restrict__ lo, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const float v = R[i];
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    hi[i] = __bfloat16_as_ushort(h);
+    if (lo) lo[i] = __bfloat16_as_ushort(__float2bfloat16_rn(v - __bfloat162float(h)));
+  }
+}
+
+}  // namespace specula
+
+using namespace specula;
+
+extern "C" int specula_recon(specula_ctx *ctx, const specula_recon_desc *rec,
+                             const float *slopes_dev, int32_t n_batch, float *modes_dev,
+                             void *stream) {
+  if (!ctx || !rec || !slopes_dev || !modes_dev || n_batch < 0) return SPECULA_EINVAL;
+  if (rec->n_modes < 1 || rec->n_slopes < 1 || !rec->R_dev) return SPECULA_EINVAL;
+  if (n_batch == 0) return SPECULA_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  const unsigned grid = (rec->n_modes + kReconWarps - 1) / kReconWarps;
+  const int blk = kReconWarps * 32;
+  const bool al16 = ((uintptr_t)rec->R_dev % 16 == 0) && ((uintptr_t)slopes_dev % 16 == 0);
+  constexpr int NB = 4;
+  switch (rec->precision) {
+    case SPECULA_PREC_FP32:
+      if (rec->n_slopes % 4 == 0 && al16) {
+        for (int b0 = 0; b0 < n_batch; b0 += NB) {
+          if (n_batch - b0 == 1)
+            SPECULA_LAUNCH(ctx, SPECULA_K_RECON, st, k_mvm_f32<1><<<grid, blk, 0, st>>>((const float *)rec->R_dev, slopes_dev, modes_dev,
+                                               rec->n_modes, rec->n_slopes, n_batch, b0));
+          else
+            SPECULA_LAUNCH(ctx, SPECULA_K_RECON, st, k_mvm_f32<NB><<<grid, blk, 0, st>>>((const float *)rec->R_dev, slopes_dev, modes_dev,
+                                                rec->n_modes, rec->n_slopes, n_batch, b0));
+        }
+      } else {
+        SPECULA_LAUNCH(ctx, SPECULA_K_RECON, st, k_mvm_f32_scalar<<<grid, blk, 0, st>>>((const float *)rec->R_dev, slopes_dev, modes_dev,
+                                               rec->n_modes, rec->n_slopes, n_batch));
+      }
+      return SPECULA_OK;
+    case SPECULA_PREC_BF16:
+    case SPECULA_PREC_BF16X2: {
+      const bool split = rec->precision == SPECULA_PREC_BF16X2;
+      if (split && !rec->R_lo_dev) return SPECULA_EINVAL;
+      if (rec->n_slopes % 8 != 0 || !al16 || (split && (uintptr_t)rec->R_lo_dev % 16))
+        return SPECULA_EUNSUPPORTED;
+      for (int b0 = 0; b0 < n_batch; b0 += NB) {
+        const bool one = n_batch - b0 == 1;
+        const uint16_t *h = (const uint16_t *)rec->R_dev, *l = (const uint16_t *)rec->R_lo_dev;
+        if (split) {
+          if (one) SPECULA_LAUNCH(ctx, SPECULA_K_RECON, st, k_mvm_bf16<1, true><<<grid, blk, 0, st>>>(h, l, slopes_dev, modes_dev, rec->n_modes, rec->n_slopes, n_batch, b0));
+          else SPECULA_LAUNCH(ctx, SPECULA_K_RECON, st, k_mvm_bf16<NB, true><<<grid, blk, 0, st>>>(h, l, slopes_dev, modes_dev, rec->n_modes, rec->n_slopes, n_batch, b0));
+        } else {
+          if (one) SPECULA_LAUNCH(ctx, SPECULA_K_RECON, st, k_mvm_bf16<1, false><<<grid, blk, 0, st>>>(h, l, slopes_dev, modes_dev, rec->n_modes, rec->n_slopes, n_batch, b0));
+          else SPECULA_LAUNCH(ctx, SPECULA_K_RECON, st, k_mvm_bf16<NB, false><<<grid, blk, 0, st>>>(h, l, slopes_dev, modes_dev, rec->n_modes, rec->n_slopes, n_batch, b0));
+        }
+      }
+      return SPECULA_OK;
+    }
+    default:
+      return SPECULA_EINVAL;
+  }
+}
+
+extern "C" int specula_recon_convert(specula_ctx *ctx, int32_t n_modes, int32_t n_slopes,
+                                     const float *R_dev, int32_t precision, void *hi_dev,
+                                     void *lo_dev, void *stream) {
+  if (!ctx || !R_dev || !hi_dev || n_modes < 1 || n_slopes < 1) return SPECULA_EINVAL;
+  if (precision != SPECULA_PREC_BF16 && precision != SPECULA_PREC_BF16X2) return SPECULA_EINVAL;
+  if (precision == SPECULA_PREC_BF16X2 && !lo_dev) return SPECULA_EINVAL;
+  const size_t n = (size_t)n_modes * n_slopes;
+  k_convert_bf16<<<1216, 256, 0, (cudaStream_t)stream>>>(
+      R_dev, (uint16_t *)hi_dev, precision == SPECULA_PREC_BF16X2 ? (uint16_t *)lo_dev : nullptr, n);
+  SPECULA_CK_LAUNCH();
+  return SPECULA_OK;
+}

@@ -1,0 +1,198 @@
+// Von Karman phase screens by the FFT method with subharmonics (set-up call;
+// AtmoEvolution, App. A, Tab. 4; Listing 2 `L0`, `Cn2`, `seed`).
+//
+//   Phi(f) = 0.023 r0^(-5/3) (|f|^2 + L0^-2)^(-11/6), Phi(0) = 0  [rad^2 m^2]
+//   screen[y][x] = Re sum_k c_k sqrt(Phi(f_k)) df exp(2 pi i f_k . (x, y) pitch)
+//                + subharmonics - their spatial mean
+//
+// Everything runs in float64 on the device (a set-up cost, not per frame):
+// spectral weighting, a radix-2 Stockham FFT along rows in shared memory, a
+// tiled transpose, the second row pass, and a final kernel that adds the
+// separable subharmonic sum and rounds to float32 once.
+#include <math.h>
+
+#include <vector>
+
+#include "internal.h"
+
+namespace specula {
+
+// A[ky][kx] = noise[ky][kx] * sqrt(Phi(f)) * df
+__global__ void k_psd_weight(const double2 *__restrict__ noise, double2 *__restrict__ A, int M,
+                             double Md, double coef, double k0) {
+  const int kx = blockIdx.x * blockDim.x + threadIdx.x, ky = blockIdx.y;
+  if (kx >= M) return;
+  const int sx = kx >= M / 2 ? kx - M : kx, sy = ky >= M / 2 ? ky - M : ky;
+  const double fx = (double)sx / Md, fy = (double)sy / Md;
+  const double f2 = fx * fx + fy * fy;
+  double a = 0.0;
+  if (f2 > 0.0) a = sqrt(coef * pow(f2 + k0, -11.0 / 6.0)) / Md;
+  const double2 c = noise[(size_t)ky * M + kx];
+  A[(size_t)ky * M + kx] = make_double2(c.x * a, c.y * a);
+}
+
+// In-place unnormalised inverse DFT of each row (exp(+2 pi i k n / M)),
+// radix-2 Stockham in shared memory.  One CTA per row.
+__global__ void k_fft_rows_f64(double2 *__restrict__ data, const double2 *__restrict__ tw, int M,
+                               int logM) {
+  extern __shared__ double2 sm[];
+  double2 *a = sm, *b = sm + M;
+  double2 *row = data + (size_t)blockIdx.x * M;
+  for (int i = threadIdx.x; i < M; i += blockDim.x) a[i] = row[i];
+  __syncthreads();
+  // Stockham: stage with half-size Ls, stride; out[j*2Ls + k] etc.
+  int L = 1;
+  for (int s = 0; s < logM; ++s) {
+    const int Ls = L;  // current sub-transform length
+    L <<= 1;
+    const int half = M / 2;
+    for (int q = threadIdx.x; q < half; q += blockDim.x) {
+      const int k = q % Ls;        // index within sub-transform
+      const int j = q / Ls;        // which sub-transform pair
+      const double2 u = a[j * Ls + k];
+      const double2 v0 = a[j * Ls + k + half];
+      // twiddle exp(+2 pi i k / L) = tw[k * (M / L)]
+      const double2 w = tw[k * (M / L)];
+      const double2 v = make_double2(v0.x * w.x - v0.y * w.y, v0.x * w.y + v0.y * w.x);
+      b[j * L + k] = make_double2(u.x + v.x, u.y + v.y);
+      b[j * L + k + Ls] = make_double2(u.x - v.x, u.y - v.y);
+    }
+    __syncthreads();
+    double2 *t = a; a = b; b = t;
+  }
+  for (int i = threadIdx.x; i < M; i += blockDim.x) row[i] = a[i];
+}
+
+__global__ void k_transpose_f64(const double2 *__restrict__ in, double2 *__restrict__ out, int M) {
+  __shared__ double2 tile[32][33];
+  const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y)
+    tile[r][threadIdx.x] = in[(size_t)(by + r) * M + bx + threadIdx.x];
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += blockDim.y)
+    out[(size_t)(bx + r) * M + by + threadIdx.x] = tile[threadIdx.x][r];
+}
+
+// screen[y][x] = Re(T[x][y]) + sum_{p,a,b} Re(C[p][b][a] tx[p][a][x] tx[p][b][y]) - mean
+__global__ void k_screen_final(const double2 *__restrict__ T, const double2 *__restrict__ tab,
+                               const double2 *__restrict__ coef, double sub_mean, int M,
+                               int levels, float *__restrict__ out) {
+  __shared__ double2 tile[32][33];
+  const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
+  // T is stored transposed: T[x][y]
+  for (int r = threadIdx.y; r < 32; r += blockDim.y)
+    tile[r][threadIdx.x] = T[(size_t)(bx + r) * M + by + threadIdx.x];
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int y = by + r, x = bx + threadIdx.x;
+    double v = tile[threadIdx.x][r].x;
+    double sub = 0.0;
+    for (int p = 0; p < levels; ++p)
+      for (int bb = 0; bb < 3; ++bb)
+        for (int aa = 0; aa < 3; ++aa) {
+          if (aa == 1 && bb == 1) continue;
+          const double2 ex = tab[((size_t)p * 3 + aa) * M + x];
+          const double2 ey = tab[((size_t)p * 3 + bb) * M + y];
+          const double2 e = make_double2(ex.x * ey.x - ex.y * ey.y, ex.x * ey.y + ex.y * ey.x);
+          const double2 c = coef[(p * 3 + bb) * 3 + aa];
+          sub += c.x * e.x - c.y * e.y;
+        }
+    out[(size_t)y * M + x] = (float)(v + (sub - sub_mean));
+  }
+}
+
+}  // namespace specula
+
+using namespace specula;
+
+static double psd_host(double fx, double fy, double r0, double L0) {
+  const double f2 = fx * fx + fy * fy;
+  if (!(f2 > 0)) return 0.0;
+  const double k0 = isinf(L0) ? 0.0 : 1.0 / (L0 * L0);
+  return 0.023 * pow(r0, -5.0 / 3.0) * pow(f2 + k0, -11.0 / 6.0);
+}
+
+extern "C" int specula_screen_generate(specula_ctx *ctx, int32_t side, double pitch_m,
+                                       double r0_m, double L0_m, const double *noise_dev,
+                                       const double *noise_sub_host, float *screen_dev,
+                                       void *stream) {
+  if (!ctx || !noise_dev || !noise_sub_host || !screen_dev) return SPECULA_EINVAL;
+  if (side < 32 || side > 4096 || (side & (side - 1))) return SPECULA_EINVAL;
+  if (!(pitch_m > 0) || !(r0_m > 0) || !(L0_m > 0)) return SPECULA_EINVAL;
+  SPECULA_CK(cudaSetDevice(ctx->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  const int M = side;
+  int logM = 0;
+  while ((1 << logM) < M) ++logM;
+  const double Md = (double)M * pitch_m;
+  const double df = 1.0 / Md;
+  const double coef = 0.023 * pow(r0_m, -5.0 / 3.0);
+  const double k0 = isinf(L0_m) ? 0.0 : 1.0 / (L0_m * L0_m);
+  const int levels = 3;
+
+  // host tables: FFT twiddles exp(+2 pi i k / M); subharmonic exponentials and
+  // coefficients; the spatial mean of the subharmonic sum
+  std::vector<double2> tw(M / 2);
+  for (int k = 0; k < M / 2; ++k) {
+    const double a = 2.0 * M_PI * (double)k / (double)M;
+    tw[k] = make_double2(cos(a), sin(a));
+  }
+  std::vector<double2> tab((size_t)levels * 3 * M), coefs(levels * 9);
+  std::vector<double2> tmean(levels * 3);
+  double sub_mean = 0.0;
+  for (int p = 0; p < levels; ++p) {
+    const double dfp = df / pow(3.0, p + 1);
+    for (int a = 0; a < 3; ++a) {
+      const double f = (a - 1) * dfp;
+      double sr = 0, si = 0;
+      for (int x = 0; x < M; ++x) {
+        const double ang = 2.0 * M_PI * f * ((double)x * pitch_m);
+        const double2 e = make_double2(cos(ang), sin(ang));
+        tab[((size_t)p * 3 + a) * M + x] = e;
+        sr += e.x;
+        si += e.y;
+      }
+      tmean[p * 3 + a] = make_double2(sr / M, si / M);
+    }
+    for (int b = 0; b < 3; ++b)
+      for (int a = 0; a < 3; ++a) {
+        double2 c = make_double2(0, 0);
+        if (!(a == 1 && b == 1)) {
+          const double amp = sqrt(psd_host((a - 1) * dfp, (b - 1) * dfp, r0_m, L0_m)) * dfp;
+          const double *n = noise_sub_host + 2 * ((p * 3 + b) * 3 + a);
+          c = make_double2(n[0] * amp, n[1] * amp);
+          const double2 mx = tmean[p * 3 + a], my = tmean[p * 3 + b];
+          const double2 e = make_double2(mx.x * my.x - mx.y * my.y, mx.x * my.y + mx.y * my.x);
+          sub_mean += c.x * e.x - c.y * e.y;
+        }
+        coefs[(p * 3 + b) * 3 + a] = c;
+      }
+  }
+
+  DevBuf A, B, dtw, dtab, dcoef;
+  int s;
+  if ((s = A.alloc((size_t)M * M * sizeof(double2)))) return s;
+  if ((s = B.alloc((size_t)M * M * sizeof(double2)))) return s;
+  if ((s = dtw.upload(tw.data(), tw.size() * sizeof(double2)))) return s;
+  if ((s = dtab.upload(tab.data(), tab.size() * sizeof(double2)))) return s;
+  if ((s = dcoef.upload(coefs.data(), coefs.size() * sizeof(double2)))) return s;
+
+  k_psd_weight<<<dim3((M + 255) / 256, M), 256, 0, st>>>((const double2 *)noise_dev,
+                                                          A.as<double2>(), M, Md, coef, k0);
+  SPECULA_CK_LAUNCH();
+  const size_t sm = 2 * (size_t)M * sizeof(double2);
+  if (sm > 48 * 1024)
+    SPECULA_CK(cudaFuncSetAttribute(k_fft_rows_f64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  k_fft_rows_f64<<<M, 256, sm, st>>>(A.as<double2>(), dtw.as<double2>(), M, logM);
+  SPECULA_CK_LAUNCH();
+  k_transpose_f64<<<dim3(M / 32, M / 32), dim3(32, 8), 0, st>>>(A.as<double2>(), B.as<double2>(), M);
+  SPECULA_CK_LAUNCH();
+  k_fft_rows_f64<<<M, 256, sm, st>>>(B.as<double2>(), dtw.as<double2>(), M, logM);
+  SPECULA_CK_LAUNCH();
+  k_screen_final<<<dim3(M / 32, M / 32), dim3(32, 8), 0, st>>>(
+      B.as<double2>(), dtab.as<double2>(), dcoef.as<double2>(), sub_mean, M, levels, screen_dev);
+  SPECULA_CK_LAUNCH();
+  // the temporaries are freed on return; wait for the kernels that use them
+  SPECULA_CK(cudaStreamSynchronize(st));
+  return SPECULA_OK;
+}

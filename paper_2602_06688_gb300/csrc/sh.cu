@@ -1,0 +1,137 @@
+// Shack-Hartmann spots (SH / Lenslet / SubapData, App. A, Tabs. 3-4; the
+// per-subaperture FFT workload of Sect. 6, Tab. 2).
+//
+// For each valid subaperture, its SP x SP block of E = amp exp(i phase) is
+// centred in an NF x NF zero grid and imaged with the centred DFT:
+//   spot = |DFT2(pad(E) . p_x p_y)|^2 / NF^2,  p(n) = exp(i pi (NF-1) n / NF)
+// (the centred transform's output phase disappears in |.|^2).
+//
+// One warp per (batch element, subaperture): lanes r < SP transform the SP
+// non-zero rows in registers (NF-point DFT, half the inputs zero), the row
+// spectra are transposed through shared memory, lanes k < NF transform the
+// columns and write the spot column-interleaved (coalesced across lanes).
+#include <math.h>
+
+#include "fft_regs.cuh"
+#include "internal.h"
+
+namespace specula {
+
+int sh_init_device() {
+  return upload_codelet_twiddles() == cudaSuccess ? SPECULA_OK : SPECULA_ECUDA;
+}
+
+constexpr int kShWarps = 8;
+
+template <int NF, int SP>
+__global__ void __launch_bounds__(kShWarps * 32) k_sh_spots(
+    const float *__restrict__ amp, const float *__restrict__ phase,
+    const int32_t *__restrict__ valid, const float2 *__restrict__ pre, int n_pix, int n_sub,
+    int n_valid, int n_batch, float *__restrict__ spots) {
+  constexpr int OFF = (NF - SP) / 2;
+  constexpr int XS = SP | 1;
+  __shared__ float2 s_x[kShWarps][NF * XS];
+  const int w = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const long long task = (long long)blockIdx.x * kShWarps + w;
+  const bool ok = task < (long long)n_valid * n_batch;
+  const int bidx = ok ? (int)(task / n_valid) : 0;
+  const int sidx = ok ? (int)(task % n_valid) : 0;
+  const int idx = ok ? valid[sidx] : 0;
+  const int a = idx / n_sub, bcol = idx % n_sub;
+  float2 *xs = s_x[w];
+
+  // rows: lane r < SP holds padded row OFF + r
+  float2 v[NF];
+#pragma unroll
+  for (int n = 0; n < NF; ++n) v[n] = make_float2(0.f, 0.f);
+  if (ok && lane < SP) {
+    const size_t rowbase = (size_t)(a * SP + lane) * n_pix + (size_t)bcol * SP;
+    const float *ph = phase + (size_t)bidx * n_pix * n_pix + rowbase;
+    const float *am = amp + rowbase;
+    const float2 py = pre[OFF + lane];
+#pragma unroll
+    for (int c = 0; c < SP; ++c) {
+      float sv, cv;
+      sincosf(ph[c], &sv, &cv);
+      const float A = am[c];
+      v[OFF + c] = cmul(cmul(make_float2(A * cv, A * sv), pre[OFF + c]), py);
+    }
+  }
+  RegDFT<NF, false>::run(v);
+  __syncwarp();
+  if (lane < SP) {
+#pragma unroll
+    for (int k = 0; k < NF; ++k) xs[k * XS + lane] = v[k];
+  }
+  __syncwarp();
+  // columns: lane k < NF
+#pragma unroll
+  for (int n = 0; n < NF; ++n) v[n] = make_float2(0.f, 0.f);
+  if (lane < NF) {
+#pragma unroll
+    for (int r = 0; r < SP; ++r) v[OFF + r] = xs[lane * XS + r];
+  }
+  RegDFT<NF, false>::run(v);
+  if (ok && lane < NF) {
+    constexpr float inv = 1.0f / (float)(NF * NF);
+    float *dst = spots + (size_t)task * NF * NF + lane;
+#pragma unroll
+    for (int q = 0; q < NF; ++q) dst[q * NF] = (v[q].x * v[q].x + v[q].y * v[q].y) * inv;
+  }
+}
+
+ShPlan *sh_plan_find(specula_ctx *ctx, const specula_pupil_desc *pupil, const specula_sh_desc *sh) {
+  for (auto &p : ctx->sh)
+    if (p->n_pix == pupil->n_pix && p->n_sub == sh->n_sub && p->sub_pix == sh->sub_pix &&
+        p->fft_n == sh->fft_n)
+      return p.get();
+  return nullptr;
+}
+
+int sh_plan_build(specula_ctx *ctx, const specula_pupil_desc *pupil, const specula_sh_desc *sh,
+                  ShPlan **out) {
+  std::unique_ptr<ShPlan> p(new ShPlan());
+  p->n_pix = pupil->n_pix;
+  p->n_sub = sh->n_sub;
+  p->sub_pix = sh->sub_pix;
+  p->fft_n = sh->fft_n;
+  std::vector<int32_t> idx((size_t)sh->n_sub * sh->n_sub);
+  int32_t nv = 0;
+  host_valid_subaps(pupil->n_pix, pupil->obsc_frac, sh->n_sub, idx.data(), &nv);
+  p->n_valid = nv;
+  const int NF = sh->fft_n;
+  std::vector<float2> pre(NF);
+  for (int n = 0; n < NF; ++n) {
+    long long r = ((long long)(NF - 1) * n) % (2 * NF);
+    const double ang = M_PI * (double)r / (double)NF;
+    pre[n] = make_float2((float)cos(ang), (float)sin(ang));
+  }
+  int s;
+  if ((s = p->valid.upload(idx.data(), (size_t)(nv > 0 ? nv : 1) * sizeof(int32_t)))) return s;
+  if ((s = p->pre.upload(pre.data(), pre.size() * sizeof(float2)))) return s;
+  *out = p.get();
+  ctx->sh.push_back(std::move(p));
+  return SPECULA_OK;
+}
+
+int sh_run(specula_ctx *ctx, ShPlan *p, const float *amp, const float *phase, int n_batch,
+           float *spots, cudaStream_t st) {
+  const long long tasks = (long long)p->n_valid * n_batch;
+  if (tasks == 0) return SPECULA_OK;
+  const unsigned grid = (unsigned)((tasks + kShWarps - 1) / kShWarps);
+  if (p->fft_n == 24 && p->sub_pix == 12)
+    SPECULA_LAUNCH(ctx, SPECULA_K_SH, st,
+                   k_sh_spots<24, 12><<<grid, kShWarps * 32, 0, st>>>(
+                       amp, phase, p->valid.as<int32_t>(), p->pre.as<float2>(), p->n_pix,
+                       p->n_sub, p->n_valid, n_batch, spots));
+  else if (p->fft_n == 16 && p->sub_pix == 8)
+    SPECULA_LAUNCH(ctx, SPECULA_K_SH, st,
+                   k_sh_spots<16, 8><<<grid, kShWarps * 32, 0, st>>>(
+                       amp, phase, p->valid.as<int32_t>(), p->pre.as<float2>(), p->n_pix,
+                       p->n_sub, p->n_valid, n_batch, spots));
+  else
+    return SPECULA_EUNSUPPORTED;
+  return SPECULA_OK;
+}
+
+}  // namespace specula

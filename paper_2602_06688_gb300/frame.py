@@ -1,0 +1,97 @@
+"""A pyramid-WFS frame through the C ABI: extraction -> image -> slopes -> MVM.
+
+This is the per-time-step chain of the paper's SOUL example (App. B, Listing
+2: atmo -> prop -> pyramid -> detector -> slopec -> rec), with the phase
+screens generated on the device from seeded noise.  All arithmetic runs in
+libspecula_gb300; this class only owns buffers and issues the calls.
+"""
+import numpy as np
+
+import synth
+from . import (PREC_BF16, PREC_BF16X2, PREC_FP32, SLOPES_PYR, layer_desc, pupil_desc,
+               pwfs_desc, recon_desc, slopec_desc, source_desc, specula_atmo_extract,
+               specula_pupil_mask, specula_pwfs_image, specula_pwfs_plan, specula_recon,
+               specula_recon_convert, specula_screen_generate, specula_slopes,
+               specula_valid_subaps_host)
+
+
+def seeded_reconstructor(n_modes, n_slopes, seed):
+    """A seeded stand-in reconstructor (float32, N(0, 1/n_slopes)) for timing
+    workloads whose calibration is not part of the measured frame."""
+    return (synth.normal_draws(seed, (n_modes, n_slopes)) / np.sqrt(n_slopes)).astype(np.float32)
+
+
+class PwfsFrame:
+    def __init__(self, ctx, wl, sensor=0, precision=PREC_FP32, R=None, n_modes=None,
+                 seed_offset=0, device="cuda"):
+        import torch
+        self.torch = torch
+        self.ctx = ctx
+        s = wl.sensors[sensor]
+        if s.kind != "pwfs":
+            raise ValueError("sensor is not a pyramid")
+        self.wl = wl
+        self.pupil = pupil_desc(s.pupil)
+        self.pwfs = pwfs_desc(s.pwfs)
+        self.src = source_desc(s.source)
+        self.layers = [layer_desc(l) for l in wl.layers]
+        n = s.pupil.n_pix
+        self.n_pix = n
+        self.screens = []
+        for l in wl.layers:
+            noise = torch.tensor(synth.screen_noise(l.seed + seed_offset, l.side), device=device)
+            scr = torch.empty(l.side, l.side, device=device, dtype=torch.float32)
+            specula_screen_generate(ctx, l.side, l.pitch_m, l.r0_m, l.L0_m, noise,
+                                    synth.subharmonic_noise(l.seed + seed_offset), scr)
+            del noise
+            self.screens.append(scr)
+        self.amp = torch.empty(n, n, device=device)
+        specula_pupil_mask(ctx, self.pupil, self.amp)
+        valid = specula_valid_subaps_host(self.pupil, s.pwfs.n_sub)
+        self.valid = torch.tensor(valid, device=device)
+        self.n_valid = len(valid)
+        self.n_slopes = 2 * self.n_valid
+        self.n_modes = n_modes or wl.n_modes
+        specula_pwfs_plan(ctx, self.pupil, self.pwfs)
+        d = 2 * s.pwfs.n_sub
+        self.phase = torch.zeros(n, n, device=device)
+        self.det = torch.empty(d, d, device=device)
+        self.slopes = torch.empty(self.n_slopes, device=device)
+        self.ref = torch.empty(self.n_slopes, device=device)
+        self.modes = torch.empty(self.n_modes, device=device)
+        self.slopec = slopec_desc(SLOPES_PYR, s.pwfs.n_sub, self.valid)
+        if R is None:
+            R = seeded_reconstructor(self.n_modes, self.n_slopes, seed=7 + seed_offset)
+        self.R = torch.tensor(np.asarray(R, dtype=np.float32), device=device)
+        self.set_precision(precision)
+        # reference slopes: a flat wavefront in the same geometry
+        specula_pwfs_image(ctx, self.pupil, self.pwfs, self.amp, self.phase, self.det)
+        specula_slopes(ctx, self.slopec, self.det, None, self.ref)
+        torch.cuda.synchronize()
+
+    def set_precision(self, precision):
+        torch = self.torch
+        self.precision = precision
+        if precision == PREC_FP32:
+            self.rec = recon_desc(self.n_modes, self.n_slopes, PREC_FP32, self.R)
+            return
+        self.R_hi = torch.empty(self.R.shape, dtype=torch.int16, device=self.R.device)
+        self.R_lo = torch.empty(self.R.shape, dtype=torch.int16, device=self.R.device)
+        specula_recon_convert(self.ctx, self.R, PREC_BF16X2, self.R_hi, self.R_lo)
+        if precision == PREC_BF16:
+            self.rec = recon_desc(self.n_modes, self.n_slopes, PREC_BF16, self.R_hi)
+        elif precision == PREC_BF16X2:
+            self.rec = recon_desc(self.n_modes, self.n_slopes, PREC_BF16X2, self.R_hi, self.R_lo)
+        else:
+            raise ValueError(precision)
+
+    def frame(self, t, t_dev=None, stream=None):
+        """Enqueue one frame at time t (or *t_dev) on the current stream."""
+        ctx = self.ctx
+        specula_atmo_extract(ctx, self.layers, self.screens, self.src, self.pupil, t,
+                             self.phase, t_dev=t_dev, stream=stream)
+        specula_pwfs_image(ctx, self.pupil, self.pwfs, self.amp, self.phase, self.det,
+                           stream=stream)
+        specula_slopes(ctx, self.slopec, self.det, self.ref, self.slopes, stream=stream)
+        specula_recon(ctx, self.rec, self.slopes, self.modes, stream=stream)
+        return self.modes
