@@ -283,7 +283,16 @@ def gpu_leg(args, ws, rank, local):
         total_ms = float(t.item())
     ms_per_step = total_ms / K
     value = ws * K / (total_ms / 1e3)
-    fp32_modes = fr.modes.clone()
+    if args.quick:
+        # headline frames only (used for profiler launch lists)
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": value, "unit": "frames/s",
+                              "ms_per_step": ms_per_step, "quick": True,
+                              "gpu_launches": launches}), flush=True)
+        ctx.close()
+        if dist:
+            dist.destroy_process_group()
+        return
     fp32_slopes = fr.slopes.clone()
 
     # ---- precision variants of the reconstructor (same frame otherwise)
@@ -391,6 +400,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="specula", choices=["specula", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--quick", action="store_true",
+                    help="headline frames only (no variants, tracing pass, e2e or baseline)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

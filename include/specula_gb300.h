@@ -148,7 +148,9 @@ int specula_ctx_status(specula_ctx *ctx, int32_t *device_status);
 #define SPECULA_K_SLOPES        4   /* slope computers                            */
 #define SPECULA_K_RECON         5   /* reconstructor MVM                          */
 #define SPECULA_K_SH            6   /* Shack-Hartmann spots                       */
-#define SPECULA_K_COUNT         8
+#define SPECULA_K_PWFS_FIELD    7   /* pyramid: field E = amp exp(i phase)        */
+#define SPECULA_K_PWFS_BIN      8   /* pyramid: per-item bins -> detector         */
+#define SPECULA_K_COUNT         10
 
 /* Enable (capacity > 0: room for that many kernel records; allocates CUDA
  * events; set-up call) or disable (capacity = 0) per-kernel event timing.

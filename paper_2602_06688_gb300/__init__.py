@@ -118,10 +118,11 @@ def specula_ctx_status(ctx):
     return v.value
 
 
-K_PWFS_ROWS_FWD, K_PWFS_COLS, K_PWFS_ROWS_INV, K_ATMO, K_SLOPES, K_RECON, K_SH = range(7)
-K_COUNT = 8
+(K_PWFS_ROWS_FWD, K_PWFS_COLS, K_PWFS_ROWS_INV, K_ATMO, K_SLOPES, K_RECON, K_SH,
+ K_PWFS_FIELD, K_PWFS_BIN) = range(9)
+K_COUNT = 10
 KERNEL_NAMES = ["pwfs_rows_fwd", "pwfs_cols", "pwfs_rows_inv", "atmo_extract", "slopes",
-                "recon", "sh_spots", "unused"]
+                "recon", "sh_spots", "pwfs_field", "pwfs_bin", "unused"]
 
 
 def specula_prof_enable(ctx, capacity):
@@ -306,11 +307,23 @@ def specula_recon_convert(ctx, R, precision, hi, lo=None, stream=None):
 
 
 def slopec_desc(kind, n_sub, idx_dev, fft_n=0):
+    import torch
+    _dev(idx_dev, torch.int32, None, "subap_idx")
     return SlopecDesc(int(kind), int(n_sub), int(idx_dev.numel()), int(fft_n),
                       C.c_void_p(idx_dev.data_ptr()))
 
 
 def recon_desc(n_modes, n_slopes, precision, R_dev, R_lo_dev=None):
+    import torch
+    want = torch.float32 if precision == PREC_FP32 else (torch.int16, torch.bfloat16,
+                                                          torch.uint16)
+    for t in (R_dev, R_lo_dev):
+        if t is None:
+            continue
+        ok = t.dtype == want if precision == PREC_FP32 else t.dtype in want
+        if not ok or not t.is_cuda or not t.is_contiguous() or t.numel() < n_modes * n_slopes:
+            raise ValueError(f"reconstructor tensor must be a contiguous CUDA tensor of "
+                             f"{n_modes}x{n_slopes} {want}, got {t.dtype} {tuple(t.shape)}")
     return ReconDesc(int(n_modes), int(n_slopes), int(precision), C.c_void_p(R_dev.data_ptr()),
                      C.c_void_p(R_lo_dev.data_ptr()) if R_lo_dev is not None else None)
 

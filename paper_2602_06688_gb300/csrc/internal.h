@@ -50,12 +50,17 @@ struct PwfsPlan {
   double mod_amp;
   int N, N1, N2;
   int chunk;            // modulation items per pipeline chunk
-  int ka;               // items per warp in the row-forward pass
+  int ka;               // items per row group in the row-forward pass
+  int nbw;              // field slots: batch elements one chunk can touch
+  int blockA, blockB, blockC;
+  size_t smemA, smemB, smemC;
   DevBuf gx, gy;        // [n_mod][n_pix] float2: tilt x pre-phase (x and y parts)
   DevBuf mask;          // [N] float2: pyramid mask factor per axis, x (1/N)
   DevBuf twA, twB;      // [N] float2: inter-step twiddles (cos, sin)
+  DevBuf field;         // [nbw][n_pix][n_pix] float2: E = amp exp(i phase)
   DevBuf rows;          // [chunk][n_pix][N] float2: after the row transform
   DevBuf cols;          // [chunk][N][N] float2: after the column pass
+  DevBuf part;          // [chunk][nd][nd] float: binned intensity per item
 };
 
 struct ShPlan {

@@ -11,17 +11,18 @@
 // with tilt_m . p folded into per-axis tables gx[m][i], gy[m][j] and the
 // 1/N^2 folded into the per-axis mask tables.
 //
-// Pipeline, one chunk of K (batch, modulation-point) items at a time so that
-// the intermediates stay L2-resident:
-//   A  k_rows_fwd     field E = amp exp(i phase) (sincos once per row and
-//                     batch element), times gx gy, row FFT of the n_pix
-//                     non-zero rows (input half zero: pruned)   -> rows ws
-//   B  k_cols         per column tile: column FFT (pruned) -> mask ->
-//                     inverse column FFT, all in shared memory -> cols ws
-//   C  k_rows_inv_bin row inverse FFT -> |.|^2 -> sum over the chunk's
-//                     modulation points in registers -> b x b binning ->
-//                     detector (written by the chunk holding m = 0, then
-//                     accumulated in chunk order: deterministic, no atomics)
+// Pipeline, one chunk of K (batch element, modulation point) items at a time
+// so that the intermediates stay L2-resident:
+//   F  k_field          E = amp exp(i phase) once per batch element
+//   A  k_rows_fwd       E . gx . gy, row FFT of the n_pix non-zero rows
+//                       (input half zero: pruned)              -> rows ws
+//   B  k_cols           per column tile (staged with cp.async): column FFT
+//                       (pruned) -> mask -> inverse column FFT  -> cols ws
+//   C  k_rows_inv_part  per (bin strip, item): row inverse FFT -> |.|^2 /
+//                       n_mod -> b x b bins                     -> part ws
+//   D  k_bin_reduce     detector += sum of the chunk's items' bins, items in
+//                       order; the chunk holding m = 0 writes (no atomics:
+//                       bit-reproducible)
 //
 // Each N-point transform is a two-level split N = N1 x N2 evaluated by one
 // group of G lanes: step 1, lane n1 < N1 holds x[n1 + N1 n2] (n2 < N2) and
@@ -57,15 +58,37 @@ template <int N1_, int N2_> struct Split {
 constexpr int round_cs(int base) { return base + ((2 - base % 16) + 16) % 16; }
 constexpr int imax3(int a, int b, int c) { return a > b ? (a > c ? a : c) : (b > c ? b : c); }
 
+__device__ __forceinline__ void cp_async8(void *smem_dst, const void *gsrc) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
 // --------------------------------------------------------------------------
-// Pass A: field formation + modulation tilt + row FFT of the non-zero rows.
+// F: field of the batch elements b0 .. b0 + gridDim.y - 1 into slots b % nbw.
+__global__ void __launch_bounds__(256) k_field(const float *__restrict__ amp,
+                                               const float *__restrict__ phase,
+                                               float2 *__restrict__ field, int npix2, int b0,
+                                               int nbw) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= npix2) return;
+  const int b = b0 + blockIdx.y;
+  float sv, cv;
+  sincosf(phase[(size_t)b * npix2 + e], &sv, &cv);
+  const float a = amp[e];
+  field[(size_t)(b % nbw) * npix2 + e] = make_float2(a * cv, a * sv);
+}
+
+// --------------------------------------------------------------------------
+// A: E . gx . gy and the row FFT of the non-zero rows.
 // grid (ceil(n_pix / VPC), ceil(n_items / ka)); block VPC * G threads.
 template <int N1, int N2>
 __global__ void __launch_bounds__(256) k_rows_fwd(
-    const float *__restrict__ amp, const float *__restrict__ phase,
-    const float2 *__restrict__ gx, const float2 *__restrict__ gy,
-    const float2 *__restrict__ twA, float2 *__restrict__ rows_out, int n_pix, int n_mod,
-    int item0, int n_items, int ka) {
+    const float2 *__restrict__ field, const float2 *__restrict__ gx,
+    const float2 *__restrict__ gy, const float2 *__restrict__ twA, float2 *__restrict__ rows_out,
+    int n_pix, int n_mod, int nbw, int item0, int n_items, int ka) {
   using S = Split<N1, N2>;
   constexpr int N = S::N, G = S::G, S1 = S::S1;
   constexpr int Q0 = N2 / 4, QH = N2 / 2;
@@ -90,29 +113,18 @@ __global__ void __launch_bounds__(256) k_rows_fwd(
     const int b = gi / n_mod, m = gi - b * n_mod;
     if (b != cur_b) {
       cur_b = b;
+      const float2 *src = field + ((size_t)(b % nbw) * n_pix + (row_ok ? j : 0)) * n_pix + lane;
 #pragma unroll
-      for (int h = 0; h < QH; ++h) {
-        e[h] = make_float2(0.f, 0.f);
-        if (in_lane) {
-          const int i = lane + N1 * h;   // = lane + N1 (n2 - N2/4)
-          const size_t p = (size_t)j * n_pix + i;
-          float sv, cv;
-          sincosf(phase[(size_t)b * n_pix * n_pix + p], &sv, &cv);
-          const float a = amp[p];
-          e[h] = make_float2(a * cv, a * sv);
-        }
-      }
+      for (int h = 0; h < QH; ++h) e[h] = in_lane ? src[N1 * h] : make_float2(0.f, 0.f);
     }
     float2 r[N2];
     const float2 gyv = row_ok ? gy[(size_t)m * n_pix + j] : make_float2(0.f, 0.f);
 #pragma unroll
     for (int n2 = 0; n2 < N2; ++n2) r[n2] = make_float2(0.f, 0.f);
+    if (in_lane) {
+      const float2 *g = gx + (size_t)m * n_pix + lane;
 #pragma unroll
-    for (int h = 0; h < QH; ++h) {
-      if (in_lane) {
-        const int i = lane + N1 * h;
-        r[Q0 + h] = cmul(cmul(e[h], gx[(size_t)m * n_pix + i]), gyv);
-      }
+      for (int h = 0; h < QH; ++h) r[Q0 + h] = cmul(cmul(e[h], g[N1 * h]), gyv);
     }
     RegDFT<N2, false>::run(r);
     __syncwarp();
@@ -136,8 +148,9 @@ __global__ void __launch_bounds__(256) k_rows_fwd(
 }
 
 // --------------------------------------------------------------------------
-// Pass B: per tile of TC columns: column FFT (rows n_pix non-zero) -> pyramid
-// mask -> inverse column FFT, all in shared memory.
+// B: per tile of TC columns: column FFT (rows n_pix non-zero) -> pyramid
+// mask -> inverse column FFT, in a column-major shared tile whose column
+// stride CS = 2 (mod 16) complex keeps the row-wise staging conflict-free.
 // grid (N / TC, n_items); block TC * G threads.
 template <int N1, int N2, int TC>
 struct ColsCfg {
@@ -160,18 +173,21 @@ __global__ void __launch_bounds__(256) k_cols(
   const int it = blockIdx.y;
   const int col0 = blockIdx.x * TC;
   constexpr int off = N / 4;
+  // all staging loads in flight at once (asynchronous copies into the tile)
+  const float2 *src = rows_in + (size_t)it * n_pix * N + col0;
+  for (int e = threadIdx.x; e < n_pix * TC; e += blockDim.x) {
+    const int c = e % TC, jj = e / TC;
+    cp_async8(s_tile + c * CS + off + jj, src + (size_t)jj * N + c);
+  }
   for (int t = threadIdx.x; t < N; t += blockDim.x) {
     s_twA[t] = twA[t];
     s_twB[t] = twB[t];
   }
-  const float2 *src = rows_in + (size_t)it * n_pix * N + col0;
-  for (int e = threadIdx.x; e < n_pix * TC; e += blockDim.x) {
-    const int c = e % TC, jj = e / TC;
-    s_tile[c * CS + off + jj] = src[(size_t)jj * N + c];
-  }
+  const int vec = threadIdx.x / G, lane = threadIdx.x % G;
+  const float2 mk = mask[col0 + vec];
+  cp_async_wait_all();
   __syncthreads();
 
-  const int vec = threadIdx.x / G, lane = threadIdx.x % G;
   float2 *col = s_tile + vec * CS;
 
   // forward, standard split; non-zero input rows are registers Q0..Q0+QH-1
@@ -199,7 +215,6 @@ __global__ void __launch_bounds__(256) k_cols(
   }
   RegDFT<N1, false>::run(r2);
   // lane k2 holds F[v = N2 k1 + k2] of column k = col0 + vec
-  const float2 mk = mask[col0 + vec];
   if (lane < N2) {
 #pragma unroll
     for (int k1 = 0; k1 < N1; ++k1) r2[k1] = cmul(r2[k1], cmul(mask[N2 * k1 + lane], mk));
@@ -235,92 +250,75 @@ __global__ void __launch_bounds__(256) k_cols(
 }
 
 // --------------------------------------------------------------------------
-// Pass C: row inverse FFT, |.|^2, sum over the chunk's modulation points,
-// b x b binning into the detector.  grid (N / bsz); block round32(bsz * G).
+// C: per (bin strip, item): row inverse FFTs, |.|^2 scaled by 1/n_mod, and
+// the b x b bins of the strip.  grid (N / bsz, n_items); block round32(bsz G).
 template <int N1, int N2>
-__device__ __forceinline__ void flush_bins(const float *s_I, float *det, int N, int bsz,
-                                           int strip, bool first) {
-  const int nd = N / bsz;
-  for (int q = threadIdx.x; q < nd; q += blockDim.x) {
-    float v = 0.f;
-    for (int rr = 0; rr < bsz; ++rr)
-      for (int xx = 0; xx < bsz; ++xx) v += s_I[rr * N + q * bsz + xx];
-    float *d = det + (size_t)strip * nd + q;
-    if (first) *d = v;
-    else *d += v;
-  }
-}
-
-template <int N1, int N2>
-__global__ void __launch_bounds__(256) k_rows_inv_bin(
-    const float2 *__restrict__ cols_in, const float2 *__restrict__ twA, float *__restrict__ det,
-    int n_mod, int item0, int n_items, int bsz, float scale) {
+__global__ void __launch_bounds__(256) k_rows_inv_part(
+    const float2 *__restrict__ cols_in, const float2 *__restrict__ twA, float *__restrict__ part,
+    int bsz, float scale) {
   using S = Split<N1, N2>;
   constexpr int N = S::N, G = S::G, S1 = S::S1;
   extern __shared__ float2 smem[];
   float2 *s_tw = smem;
   const int nvec = blockDim.x / G;
   float *s_I = reinterpret_cast<float *>(smem + N + nvec * S::XB);   // [bsz][N]
-  for (int t = threadIdx.x; t < N; t += blockDim.x) s_tw[t] = twA[t];
   const int vec = threadIdx.x / G, lane = threadIdx.x % G;
-  float2 *xb = smem + N + vec * S::XB;
   const bool act = vec < bsz;
-  const int y = blockIdx.x * bsz + vec;
-  const int nd = N / bsz;
-  __syncthreads();
-
-  float acc[N1];
+  const int it = blockIdx.y;
+  const int y = blockIdx.x * bsz + (act ? vec : 0);
+  float2 r[N2];
+  if (act && lane < N1) {
+    const float2 *src = cols_in + ((size_t)it * N + y) * N + lane;
 #pragma unroll
-  for (int k1 = 0; k1 < N1; ++k1) acc[k1] = 0.f;
-  int cur_b = item0 / n_mod;
-  bool first = (item0 - cur_b * n_mod) == 0;
-  for (int it = 0; it < n_items; ++it) {
-    const int gi = item0 + it;
-    const int b = gi / n_mod, m = gi - b * n_mod;
-    if (b != cur_b) {
-      if (act && lane < N2) {
+    for (int n2 = 0; n2 < N2; ++n2) r[n2] = src[N1 * n2];
+  } else {
 #pragma unroll
-        for (int k1 = 0; k1 < N1; ++k1) s_I[vec * N + N2 * k1 + lane] = acc[k1] * scale;
-      }
-      __syncthreads();
-      flush_bins<N1, N2>(s_I, det + (size_t)cur_b * nd * nd, N, bsz, blockIdx.x, first);
-      __syncthreads();
-#pragma unroll
-      for (int k1 = 0; k1 < N1; ++k1) acc[k1] = 0.f;
-      cur_b = b;
-      first = (m == 0);
-    }
-    float2 r[N2];
-    if (act && lane < N1) {
-      const float2 *src = cols_in + ((size_t)it * N + y) * N + lane;
-#pragma unroll
-      for (int n2 = 0; n2 < N2; ++n2) r[n2] = src[N1 * n2];
-    } else {
-#pragma unroll
-      for (int n2 = 0; n2 < N2; ++n2) r[n2] = make_float2(0.f, 0.f);
-    }
-    RegDFT<N2, true>::run(r);
-    __syncwarp();
-    if (lane < N1) {
-#pragma unroll
-      for (int k2 = 0; k2 < N2; ++k2) xb[k2 * S1 + lane] = cmul(r[k2], s_tw[k2 * N1 + lane]);
-    }
-    __syncwarp();
-    if (lane < N2) {
-      float2 r2[N1];
-#pragma unroll
-      for (int n1 = 0; n1 < N1; ++n1) r2[n1] = xb[lane * S1 + n1];
-      RegDFT<N1, true>::run(r2);
-#pragma unroll
-      for (int k1 = 0; k1 < N1; ++k1) acc[k1] += r2[k1].x * r2[k1].x + r2[k1].y * r2[k1].y;
-    }
+    for (int n2 = 0; n2 < N2; ++n2) r[n2] = make_float2(0.f, 0.f);
   }
+  for (int t = threadIdx.x; t < N; t += blockDim.x) s_tw[t] = twA[t];
+  float2 *xb = smem + N + vec * S::XB;
+  __syncthreads();
+  RegDFT<N2, true>::run(r);
+  if (lane < N1) {
+#pragma unroll
+    for (int k2 = 0; k2 < N2; ++k2) xb[k2 * S1 + lane] = cmul(r[k2], s_tw[k2 * N1 + lane]);
+  }
+  __syncwarp();
   if (act && lane < N2) {
+    float2 r2[N1];
 #pragma unroll
-    for (int k1 = 0; k1 < N1; ++k1) s_I[vec * N + N2 * k1 + lane] = acc[k1] * scale;
+    for (int n1 = 0; n1 < N1; ++n1) r2[n1] = xb[lane * S1 + n1];
+    RegDFT<N1, true>::run(r2);
+#pragma unroll
+    for (int k1 = 0; k1 < N1; ++k1)
+      s_I[vec * N + N2 * k1 + lane] = (r2[k1].x * r2[k1].x + r2[k1].y * r2[k1].y) * scale;
   }
   __syncthreads();
-  flush_bins<N1, N2>(s_I, det + (size_t)cur_b * nd * nd, N, bsz, blockIdx.x, first);
+  const int nd = N / bsz;
+  float *dst = part + ((size_t)it * nd + blockIdx.x) * nd;
+  for (int q = threadIdx.x; q < nd; q += blockDim.x) {
+    float v = 0.f;
+    for (int rr = 0; rr < bsz; ++rr)
+      for (int xx = 0; xx < bsz; ++xx) v += s_I[rr * N + q * bsz + xx];
+    dst[q] = v;
+  }
+}
+
+// --------------------------------------------------------------------------
+// D: det[b] (+)= sum over the chunk's items of b, in item order.
+// grid (ceil(nd^2 / 256), batch elements in the chunk).
+__global__ void __launch_bounds__(256) k_bin_reduce(const float *__restrict__ part,
+                                                    float *__restrict__ det, int nd2, int n_mod,
+                                                    int item0, int n_items) {
+  const int pix = blockIdx.x * blockDim.x + threadIdx.x;
+  if (pix >= nd2) return;
+  const int b = item0 / n_mod + blockIdx.y;
+  const int lo = max(item0, b * n_mod), hi = min(item0 + n_items, (b + 1) * n_mod);
+  float v = 0.f;
+  for (int gi = lo; gi < hi; ++gi) v += part[(size_t)(gi - item0) * nd2 + pix];
+  float *d = det + (size_t)b * nd2 + pix;
+  if (lo == b * n_mod) *d = v;
+  else *d += v;
 }
 
 // --------------------------------------------------------------------------
@@ -328,58 +326,73 @@ __global__ void __launch_bounds__(256) k_rows_inv_bin(
 
 constexpr int kColsTile = 8;
 
-struct Launch {
-  size_t smemA, smemB, smemC;
-  int blockA, blockB, blockC;
-};
-
 template <int N1, int N2>
-static int configure(int bsz, Launch *L) {
+static int configure(PwfsPlan *p) {
   using S = Split<N1, N2>;
-  L->blockA = 256;
+  const int bsz = p->n_pix / p->n_sub;
+  p->blockA = 256;
   const int vpcA = 256 / S::G;
-  L->smemA = (size_t)(S::N + vpcA * S::XB) * sizeof(float2);
-  L->blockB = kColsTile * S::G;
-  L->smemB = ColsCfg<N1, N2, kColsTile>::smem;
+  p->smemA = (size_t)(S::N + vpcA * S::XB) * sizeof(float2);
+  p->blockB = kColsTile * S::G;
+  p->smemB = ColsCfg<N1, N2, kColsTile>::smem;
   const int thrC = ((bsz * S::G + 31) / 32) * 32;
   if (thrC > 256) return SPECULA_EUNSUPPORTED;   // bin side too large for one CTA strip
-  L->blockC = thrC;
+  p->blockC = thrC;
   const int nvecC = thrC / S::G;
-  L->smemC = (size_t)(S::N + nvecC * S::XB) * sizeof(float2) + (size_t)bsz * S::N * sizeof(float);
-  if (L->smemA > 227 * 1024 || L->smemB > 227 * 1024 || L->smemC > 227 * 1024) return SPECULA_EUNSUPPORTED;
-  if (cudaFuncSetAttribute(k_rows_fwd<N1, N2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L->smemA) != cudaSuccess) return SPECULA_ECUDA;
-  if (cudaFuncSetAttribute(k_cols<N1, N2, kColsTile>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L->smemB) != cudaSuccess) return SPECULA_ECUDA;
-  if (cudaFuncSetAttribute(k_rows_inv_bin<N1, N2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L->smemC) != cudaSuccess) return SPECULA_ECUDA;
+  p->smemC = (size_t)(S::N + nvecC * S::XB) * sizeof(float2) + (size_t)bsz * S::N * sizeof(float);
+  if (p->smemA > 227 * 1024 || p->smemB > 227 * 1024 || p->smemC > 227 * 1024)
+    return SPECULA_EUNSUPPORTED;
+  SPECULA_CK(cudaFuncSetAttribute(k_rows_fwd<N1, N2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)p->smemA));
+  SPECULA_CK(cudaFuncSetAttribute(k_cols<N1, N2, kColsTile>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smemB));
+  SPECULA_CK(cudaFuncSetAttribute(k_rows_inv_part<N1, N2>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smemC));
   return SPECULA_OK;
 }
 
 template <int N1, int N2>
-static int run_split(specula_ctx *ctx, PwfsPlan *p, const float *amp, const float *phase, int n_batch, float *det,
-                     cudaStream_t st) {
+static int run_split(specula_ctx *ctx, PwfsPlan *p, const float *amp, const float *phase,
+                     int n_batch, float *det, cudaStream_t st) {
   using S = Split<N1, N2>;
-  const int bsz = p->n_pix / p->n_sub;
-  Launch L;
-  int s = configure<N1, N2>(bsz, &L);
-  if (s) return s;
+  const int Np = p->n_pix;
+  const int bsz = Np / p->n_sub;
+  const int nd = S::N / bsz;
   const int total = n_batch * p->n_mod;
-  const int vpcA = L.blockA / S::G;
+  const int vpcA = p->blockA / S::G;
   const float scale = 1.0f / (float)p->n_mod;
+  int field_done = -1;   // highest batch element whose field is in its slot
   for (int i0 = 0; i0 < total; i0 += p->chunk) {
     const int ni = std::min(p->chunk, total - i0);
-    dim3 gA((p->n_pix + vpcA - 1) / vpcA, (ni + p->ka - 1) / p->ka);
+    const int b0 = i0 / p->n_mod, b1 = (i0 + ni - 1) / p->n_mod;
+    const int fb = std::max(b0, field_done + 1);
+    if (fb <= b1) {
+      dim3 gF((Np * Np + 255) / 256, b1 - fb + 1);
+      SPECULA_LAUNCH(ctx, SPECULA_K_PWFS_FIELD, st,
+                     k_field<<<gF, 256, 0, st>>>(amp, phase, p->field.as<float2>(), Np * Np, fb,
+                                                 p->nbw));
+      field_done = b1;
+    }
+    dim3 gA((Np + vpcA - 1) / vpcA, (ni + p->ka - 1) / p->ka);
     SPECULA_LAUNCH(ctx, SPECULA_K_PWFS_ROWS_FWD, st,
-                   k_rows_fwd<N1, N2><<<gA, L.blockA, L.smemA, st>>>(
-                       amp, phase, p->gx.as<float2>(), p->gy.as<float2>(), p->twA.as<float2>(),
-                       p->rows.as<float2>(), p->n_pix, p->n_mod, i0, ni, p->ka));
+                   k_rows_fwd<N1, N2><<<gA, p->blockA, p->smemA, st>>>(
+                       p->field.as<float2>(), p->gx.as<float2>(), p->gy.as<float2>(),
+                       p->twA.as<float2>(), p->rows.as<float2>(), Np, p->n_mod, p->nbw, i0, ni,
+                       p->ka));
     dim3 gB(S::N / kColsTile, ni);
     SPECULA_LAUNCH(ctx, SPECULA_K_PWFS_COLS, st,
-                   k_cols<N1, N2, kColsTile><<<gB, L.blockB, L.smemB, st>>>(
+                   k_cols<N1, N2, kColsTile><<<gB, p->blockB, p->smemB, st>>>(
                        p->rows.as<float2>(), p->cols.as<float2>(), p->twA.as<float2>(),
-                       p->twB.as<float2>(), p->mask.as<float2>(), p->n_pix));
+                       p->twB.as<float2>(), p->mask.as<float2>(), Np));
+    dim3 gC(S::N / bsz, ni);
     SPECULA_LAUNCH(ctx, SPECULA_K_PWFS_ROWS_INV, st,
-                   k_rows_inv_bin<N1, N2><<<S::N / bsz, L.blockC, L.smemC, st>>>(
-                       p->cols.as<float2>(), p->twA.as<float2>(), det, p->n_mod, i0, ni, bsz,
+                   k_rows_inv_part<N1, N2><<<gC, p->blockC, p->smemC, st>>>(
+                       p->cols.as<float2>(), p->twA.as<float2>(), p->part.as<float>(), bsz,
                        scale));
+    dim3 gD((nd * nd + 255) / 256, b1 - b0 + 1);
+    SPECULA_LAUNCH(ctx, SPECULA_K_PWFS_BIN, st,
+                   k_bin_reduce<<<gD, 256, 0, st>>>(p->part.as<float>(), det, nd * nd, p->n_mod,
+                                                    i0, ni));
   }
   return SPECULA_OK;
 }
@@ -396,16 +409,24 @@ static bool split_for(int N, int *N1, int *N2) {
 }
 
 int pwfs_set_tiles(PwfsPlan *p, int chunk, int ka) {
+  const int nd = 2 * p->n_sub;
+  const int nbw = (chunk + p->n_mod - 1) / p->n_mod + 1;
+  const size_t need_field = (size_t)nbw * p->n_pix * p->n_pix * sizeof(float2);
   const size_t need_rows = (size_t)chunk * p->n_pix * p->N * sizeof(float2);
   const size_t need_cols = (size_t)chunk * p->N * p->N * sizeof(float2);
+  const size_t need_part = (size_t)chunk * nd * nd * sizeof(float);
   int s;
-  if (need_rows > p->rows.bytes || need_cols > p->cols.bytes) {
+  if (need_rows > p->rows.bytes || need_cols > p->cols.bytes || need_field > p->field.bytes ||
+      need_part > p->part.bytes) {
     cudaDeviceSynchronize();   // the old workspace may still be in use
+    if ((s = p->field.alloc(need_field))) return s;
     if ((s = p->rows.alloc(need_rows))) return s;
     if ((s = p->cols.alloc(need_cols))) return s;
+    if ((s = p->part.alloc(need_part))) return s;
   }
   p->chunk = chunk;
   p->ka = ka;
+  p->nbw = nbw;
   return SPECULA_OK;
 }
 
@@ -417,6 +438,17 @@ int pwfs_run(specula_ctx *ctx, PwfsPlan *p, const float *amp, const float *phase
     case 240: return run_split<15, 16>(ctx, p, amp, phase, n_batch, det, st);
     case 320: return run_split<20, 16>(ctx, p, amp, phase, n_batch, det, st);
     case 960: return run_split<30, 32>(ctx, p, amp, phase, n_batch, det, st);
+    default: return SPECULA_EUNSUPPORTED;
+  }
+}
+
+static int configure_for(PwfsPlan *p) {
+  switch (p->N) {
+    case 64: return configure<8, 8>(p);
+    case 128: return configure<8, 16>(p);
+    case 240: return configure<15, 16>(p);
+    case 320: return configure<20, 16>(p);
+    case 960: return configure<30, 32>(p);
     default: return SPECULA_EUNSUPPORTED;
   }
 }
@@ -448,6 +480,8 @@ int pwfs_plan_build(specula_ctx *ctx, const specula_pupil_desc *pupil,
   p->n_pix = Np; p->pad = d->pad; p->n_mod = d->n_mod; p->n_sub = d->n_sub;
   p->pup_dist = d->pup_dist_px; p->mod_amp = d->mod_amp;
   p->N = N; p->N1 = N1; p->N2 = N2;
+  int s = configure_for(p.get());
+  if (s) return s;
   const int off = (N - Np) / 2;
 
   // modulation tilt x centred-DFT input phase, per axis, float64 -> float32
@@ -472,25 +506,24 @@ int pwfs_plan_build(specula_ctx *ctx, const specula_pupil_desc *pupil,
   for (int k = 0; k < N; ++k) {
     long long a = 2LL * k - N + 1;
     if (a < 0) a = -a;
-    double c, s;
-    exp_ipi(-(long long)d->pup_dist_px * a, 2LL * N, &c, &s);
-    mk[k] = make_float2((float)(c / N), (float)(s / N));
+    double c, sn;
+    exp_ipi(-(long long)d->pup_dist_px * a, 2LL * N, &c, &sn);
+    mk[k] = make_float2((float)(c / N), (float)(sn / N));
   }
   // inter-step twiddles (cos, sin)(2 pi (a b mod N) / N)
   std::vector<float2> ta(N), tb(N);
   for (int a = 0; a < N2; ++a)
     for (int b = 0; b < N1; ++b) {
-      double c, s;
-      exp_ipi(2LL * ((long long)a * b % N), N, &c, &s);
-      ta[a * N1 + b] = make_float2((float)c, (float)s);
+      double c, sn;
+      exp_ipi(2LL * ((long long)a * b % N), N, &c, &sn);
+      ta[a * N1 + b] = make_float2((float)c, (float)sn);
     }
   for (int a = 0; a < N1; ++a)
     for (int b = 0; b < N2; ++b) {
-      double c, s;
-      exp_ipi(2LL * ((long long)a * b % N), N, &c, &s);
-      tb[a * N2 + b] = make_float2((float)c, (float)s);
+      double c, sn;
+      exp_ipi(2LL * ((long long)a * b % N), N, &c, &sn);
+      tb[a * N2 + b] = make_float2((float)c, (float)sn);
     }
-  int s;
   if ((s = p->gx.upload(gx.data(), gx.size() * sizeof(float2)))) return s;
   if ((s = p->gy.upload(gy.data(), gy.size() * sizeof(float2)))) return s;
   if ((s = p->mask.upload(mk.data(), mk.size() * sizeof(float2)))) return s;
@@ -501,7 +534,7 @@ int pwfs_plan_build(specula_ctx *ctx, const specula_pupil_desc *pupil,
   const size_t per_item = ((size_t)Np * N + (size_t)N * N) * sizeof(float2);
   int chunk = (int)std::max<size_t>(1, (48u << 20) / per_item);
   chunk = std::min(chunk, 64);
-  if ((s = pwfs_set_tiles(p.get(), chunk, 2))) return s;
+  if ((s = pwfs_set_tiles(p.get(), chunk, 1))) return s;
   *out = p.get();
   ctx->pwfs.push_back(std::move(p));
   return SPECULA_OK;

@@ -58,7 +58,7 @@ def test_sh_spots_and_slopes(env, n_sub, sub_pix, fft_n, obsc, nb):
 def test_recon_precisions(env, nm, ns, nb):
     torch, sp, ctx = env
     rng = np.random.default_rng(nm)
-    R = rng.standard_normal((nm, ns)).astype(np.float32) / np.sqrt(ns)
+    R = (rng.standard_normal((nm, ns)) / np.sqrt(ns)).astype(np.float32)
     s = rng.standard_normal((nb, ns)).astype(np.float32)
     ref = recon.mvm(R.astype(np.float64), s.astype(np.float64))
     mag = np.abs(s.astype(np.float64)) @ np.abs(R.astype(np.float64)).T   # sum_j |R_ij s_j|
