@@ -9,10 +9,11 @@
 // indices agree exactly with any IEEE float64 evaluation of the same formula.
 // The interpolation and the layer sum run in float32.
 //
-// A CTA covers a 32 x 32 pixel tile: it first evaluates the tile's 32 column
-// and 32 row coordinates of every layer in float64 into shared memory (64
-// evaluations per layer instead of 1024), then each thread gathers four
-// pixels.  A warp reads 32 consecutive columns of one screen row: coalesced.
+// A CTA covers a 32 x 8 pixel tile: it first evaluates the tile's 32 column
+// and 8 row coordinates of every layer in float64 into shared memory (40
+// evaluations per layer instead of 256), then each thread sums its pixel over
+// the layers, four layers' gathers in flight at a time.  A warp reads 32
+// consecutive columns of one screen row: coalesced.
 #include <math.h>
 
 #include "internal.h"
@@ -20,7 +21,7 @@
 namespace specula {
 
 constexpr int kMaxLayers = 64;
-constexpr int kTile = 32;
+constexpr int kTileX = 32, kTileY = 8;
 
 struct AtmoParams {
   const float *scr[kMaxLayers];
@@ -50,56 +51,46 @@ __device__ __forceinline__ void coord(double idx, int n, double pupil_pitch, dou
 __global__ void __launch_bounds__(256) k_atmo_extract(const AtmoParams P, double t_host,
                                                       const double *__restrict__ t_dev,
                                                       float *__restrict__ phase) {
-  __shared__ int s_ix[kMaxLayers][kTile], s_iy[kMaxLayers][kTile];
-  __shared__ float s_fx[kMaxLayers][kTile], s_fy[kMaxLayers][kTile];
+  __shared__ int s_ix[kMaxLayers][kTileX], s_iy[kMaxLayers][kTileY];
+  __shared__ float s_fx[kMaxLayers][kTileX], s_fy[kMaxLayers][kTileY];
   const double t = t_dev ? *t_dev : t_host;
-  const int x0 = blockIdx.x * kTile, y0 = blockIdx.y * kTile;
+  const int x0 = blockIdx.x * kTileX, y0 = blockIdx.y * kTileY;
   const int nthr = blockDim.x * blockDim.y;
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-  for (int e = tid; e < P.n_layers * 2 * kTile; e += nthr) {
-    const int l = e / (2 * kTile), r = e % (2 * kTile);
+  constexpr int PER = kTileX + kTileY;
+  for (int e = tid; e < P.n_layers * PER; e += nthr) {
+    const int l = e / PER, r = e % PER;
     const double s = __dsub_rn(1.0, __ddiv_rn(P.h[l], P.H));
-    if (r < kTile) {
+    if (r < kTileX) {
       coord((double)(x0 + r), P.n_pix, P.pupil_pitch, s, P.h[l], P.theta_x, P.vx[l], t,
             P.pitch[l], P.side[l], &s_ix[l][r], &s_fx[l][r]);
     } else {
-      const int q = r - kTile;
+      const int q = r - kTileX;
       coord((double)(y0 + q), P.n_pix, P.pupil_pitch, s, P.h[l], P.theta_y, P.vy[l], t,
             P.pitch[l], P.side[l], &s_iy[l][q], &s_fy[l][q]);
     }
   }
   __syncthreads();
-  const int tx = threadIdx.x;
-  const int i = x0 + tx;
-  float acc[kTile / 8];
-#pragma unroll
-  for (int q = 0; q < kTile / 8; ++q) acc[q] = 0.f;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int i = x0 + tx, j = y0 + ty;
+  float acc = 0.f;
+#pragma unroll 4
   for (int l = 0; l < P.n_layers; ++l) {
     const float *S = P.scr[l];
     const int M = P.side[l];
     const int ix0 = s_ix[l][tx];
     const int ix1 = ix0 + 1 == M ? 0 : ix0 + 1;
     const float fx = s_fx[l][tx];
-#pragma unroll
-    for (int q = 0; q < kTile / 8; ++q) {
-      const int ty = threadIdx.y + 8 * q;
-      const int iy0 = s_iy[l][ty];
-      const int iy1 = iy0 + 1 == M ? 0 : iy0 + 1;
-      const float fy = s_fy[l][ty];
-      const float s00 = __ldg(S + (size_t)iy0 * M + ix0), s01 = __ldg(S + (size_t)iy0 * M + ix1);
-      const float s10 = __ldg(S + (size_t)iy1 * M + ix0), s11 = __ldg(S + (size_t)iy1 * M + ix1);
-      const float a = s00 + fx * (s01 - s00);
-      const float b = s10 + fx * (s11 - s10);
-      acc[q] += a + fy * (b - a);
-    }
+    const int iy0 = s_iy[l][ty];
+    const int iy1 = iy0 + 1 == M ? 0 : iy0 + 1;
+    const float fy = s_fy[l][ty];
+    const float s00 = __ldg(S + (size_t)iy0 * M + ix0), s01 = __ldg(S + (size_t)iy0 * M + ix1);
+    const float s10 = __ldg(S + (size_t)iy1 * M + ix0), s11 = __ldg(S + (size_t)iy1 * M + ix1);
+    const float a = s00 + fx * (s01 - s00);
+    const float b = s10 + fx * (s11 - s10);
+    acc += a + fy * (b - a);
   }
-  if (i < P.n_pix) {
-#pragma unroll
-    for (int q = 0; q < kTile / 8; ++q) {
-      const int j = y0 + threadIdx.y + 8 * q;
-      if (j < P.n_pix) phase[(size_t)j * P.n_pix + i] = acc[q] * P.scale;
-    }
-  }
+  if (i < P.n_pix && j < P.n_pix) phase[(size_t)j * P.n_pix + i] = acc * P.scale;
 }
 
 }  // namespace specula
@@ -139,7 +130,7 @@ extern "C" int specula_atmo_extract(specula_ctx *ctx, int32_t n_layers,
     P.vx[l] = L.vx_mps;
     P.vy[l] = L.vy_mps;
   }
-  dim3 grid((pupil->n_pix + kTile - 1) / kTile, (pupil->n_pix + kTile - 1) / kTile);
+  dim3 grid((pupil->n_pix + kTileX - 1) / kTileX, (pupil->n_pix + kTileY - 1) / kTileY);
   dim3 block(32, 8);
   SPECULA_LAUNCH(ctx, SPECULA_K_ATMO, (cudaStream_t)stream,
                  k_atmo_extract<<<grid, block, 0, (cudaStream_t)stream>>>(P, t_s, t_dev, phase_dev));

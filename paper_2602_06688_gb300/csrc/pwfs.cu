@@ -19,9 +19,9 @@
 //   B  k_cols           per column tile (staged with cp.async): column FFT
 //                       (pruned) -> mask -> inverse column FFT  -> cols ws
 //   C  k_rows_inv_part  per (bin strip, item): row inverse FFT -> |.|^2 /
-//                       n_mod -> b x b bins                     -> part ws
-//   D  k_bin_reduce     detector += sum of the chunk's items' bins, items in
-//                       order; the chunk holding m = 0 writes (no atomics:
+//                       n_mod -> b x b bins              -> part[b][m] ws
+//   D  k_bin_reduce     once a batch element's n_mod items are done: the
+//                       detector = sum over m in order (no atomics:
 //                       bit-reproducible)
 //
 // Each N-point transform is a two-level split N = N1 x N2 evaluated by one
@@ -30,7 +30,9 @@
 // exchanged through shared memory; step 2, lane k2 < N2 does an N1-point
 // register DFT and holds X[N2 k1 + k2].  With N2 % 4 == 0 the non-zero half
 // of a zero-padded input (indices N/4 .. 3N/4) is exactly registers
-// N2/4 .. 3N2/4 of every lane, so zero inputs are never loaded.
+// N2/4 .. 3N2/4 of every lane, so zero inputs are never loaded.  The
+// inter-step twiddles are read through the read-only cache: lane n1 reads
+// table[k2][n1], so a warp's reads are consecutive for each k2.
 #include <math.h>
 
 #include <algorithm>
@@ -53,6 +55,7 @@ template <int N1_, int N2_> struct Split {
   static constexpr int XB = N2_ * S1;  // exchange buffer per vector (complex)
   static_assert(N2_ % 4 == 0, "pruned zero-padded input needs N2 % 4 == 0");
   static_assert(MX <= 32, "one vector per warp at most");
+  static_assert(2 * XB >= N, "a vector's exchange buffer must hold N floats");
 };
 
 constexpr int round_cs(int base) { return base + ((2 - base % 16) + 16) % 16; }
@@ -85,7 +88,7 @@ __global__ void __launch_bounds__(256) k_field(const float *__restrict__ amp,
 // A: E . gx . gy and the row FFT of the non-zero rows.
 // grid (ceil(n_pix / VPC), ceil(n_items / ka)); block VPC * G threads.
 template <int N1, int N2>
-__global__ void __launch_bounds__(256) k_rows_fwd(
+__global__ void __launch_bounds__(256, 2) k_rows_fwd(
     const float2 *__restrict__ field, const float2 *__restrict__ gx,
     const float2 *__restrict__ gy, const float2 *__restrict__ twA, float2 *__restrict__ rows_out,
     int n_pix, int n_mod, int nbw, int item0, int n_items, int ka) {
@@ -93,15 +96,12 @@ __global__ void __launch_bounds__(256) k_rows_fwd(
   constexpr int N = S::N, G = S::G, S1 = S::S1;
   constexpr int Q0 = N2 / 4, QH = N2 / 2;
   extern __shared__ float2 smem[];
-  float2 *s_tw = smem;
   const int vpc = blockDim.x / G;
-  for (int t = threadIdx.x; t < N; t += blockDim.x) s_tw[t] = twA[t];
   const int vec = threadIdx.x / G, lane = threadIdx.x % G;
-  float2 *xb = smem + N + vec * S::XB;
+  float2 *xb = smem + vec * S::XB;
   const int j = blockIdx.x * vpc + vec;
   const bool row_ok = j < n_pix;
   const bool in_lane = row_ok && lane < N1;
-  __syncthreads();
 
   float2 e[QH];
   int cur_b = -1;
@@ -124,13 +124,14 @@ __global__ void __launch_bounds__(256) k_rows_fwd(
     if (in_lane) {
       const float2 *g = gx + (size_t)m * n_pix + lane;
 #pragma unroll
-      for (int h = 0; h < QH; ++h) r[Q0 + h] = cmul(cmul(e[h], g[N1 * h]), gyv);
+      for (int h = 0; h < QH; ++h) r[Q0 + h] = cmul(cmul(e[h], __ldg(g + N1 * h)), gyv);
     }
     RegDFT<N2, false>::run(r);
     __syncwarp();
     if (lane < N1) {
 #pragma unroll
-      for (int k2 = 0; k2 < N2; ++k2) xb[k2 * S1 + lane] = cmulc(r[k2], s_tw[k2 * N1 + lane]);
+      for (int k2 = 0; k2 < N2; ++k2)
+        xb[k2 * S1 + lane] = cmulc(r[k2], __ldg(twA + k2 * N1 + lane));
     }
     __syncwarp();
     if (lane < N2) {
@@ -156,11 +157,11 @@ template <int N1, int N2, int TC>
 struct ColsCfg {
   using S = Split<N1, N2>;
   static constexpr int CS = round_cs(imax3(S::N, N2 * S::S1, N1 * S::S2));
-  static constexpr size_t smem = (size_t)(2 * S::N + TC * CS) * sizeof(float2);
+  static constexpr size_t smem = (size_t)(TC * CS) * sizeof(float2);
 };
 
 template <int N1, int N2, int TC>
-__global__ void __launch_bounds__(256) k_cols(
+__global__ void __launch_bounds__(256, 3) k_cols(
     const float2 *__restrict__ rows_in, float2 *__restrict__ cols_out,
     const float2 *__restrict__ twA, const float2 *__restrict__ twB,
     const float2 *__restrict__ mask, int n_pix) {
@@ -169,7 +170,7 @@ __global__ void __launch_bounds__(256) k_cols(
   constexpr int CS = ColsCfg<N1, N2, TC>::CS;
   constexpr int Q0 = N2 / 4, QH = N2 / 2;
   extern __shared__ float2 smem[];
-  float2 *s_twA = smem, *s_twB = smem + N, *s_tile = smem + 2 * N;
+  float2 *s_tile = smem;
   const int it = blockIdx.y;
   const int col0 = blockIdx.x * TC;
   constexpr int off = N / 4;
@@ -179,12 +180,8 @@ __global__ void __launch_bounds__(256) k_cols(
     const int c = e % TC, jj = e / TC;
     cp_async8(s_tile + c * CS + off + jj, src + (size_t)jj * N + c);
   }
-  for (int t = threadIdx.x; t < N; t += blockDim.x) {
-    s_twA[t] = twA[t];
-    s_twB[t] = twB[t];
-  }
   const int vec = threadIdx.x / G, lane = threadIdx.x % G;
-  const float2 mk = mask[col0 + vec];
+  const float2 mk = __ldg(mask + col0 + vec);
   cp_async_wait_all();
   __syncthreads();
 
@@ -202,7 +199,8 @@ __global__ void __launch_bounds__(256) k_cols(
   __syncwarp();
   if (lane < N1) {
 #pragma unroll
-    for (int k2 = 0; k2 < N2; ++k2) col[k2 * S1 + lane] = cmulc(r[k2], s_twA[k2 * N1 + lane]);
+    for (int k2 = 0; k2 < N2; ++k2)
+      col[k2 * S1 + lane] = cmulc(r[k2], __ldg(twA + k2 * N1 + lane));
   }
   __syncwarp();
   float2 r2[N1];
@@ -217,14 +215,16 @@ __global__ void __launch_bounds__(256) k_cols(
   // lane k2 holds F[v = N2 k1 + k2] of column k = col0 + vec
   if (lane < N2) {
 #pragma unroll
-    for (int k1 = 0; k1 < N1; ++k1) r2[k1] = cmul(r2[k1], cmul(mask[N2 * k1 + lane], mk));
+    for (int k1 = 0; k1 < N1; ++k1)
+      r2[k1] = cmul(r2[k1], cmul(__ldg(mask + N2 * k1 + lane), mk));
   }
   // inverse, swapped split: lane n1' = k2 (< N2), registers n2' = k1 (< N1)
   RegDFT<N1, true>::run(r2);
   __syncwarp();
   if (lane < N2) {
 #pragma unroll
-    for (int k2 = 0; k2 < N1; ++k2) col[k2 * S2 + lane] = cmul(r2[k2], s_twB[k2 * N2 + lane]);
+    for (int k2 = 0; k2 < N1; ++k2)
+      col[k2 * S2 + lane] = cmul(r2[k2], __ldg(twB + k2 * N2 + lane));
   }
   __syncwarp();
   float2 r3[N2];
@@ -251,21 +251,21 @@ __global__ void __launch_bounds__(256) k_cols(
 
 // --------------------------------------------------------------------------
 // C: per (bin strip, item): row inverse FFTs, |.|^2 scaled by 1/n_mod, and
-// the b x b bins of the strip.  grid (N / bsz, n_items); block round32(bsz G).
+// the b x b bins of the strip into part[b % nbw][m].  Each warp's intensity
+// row reuses its own exchange buffer.  grid (N / bsz, n_items);
+// block round32(bsz G).
 template <int N1, int N2>
-__global__ void __launch_bounds__(256) k_rows_inv_part(
+__global__ void __launch_bounds__(256, 2) k_rows_inv_part(
     const float2 *__restrict__ cols_in, const float2 *__restrict__ twA, float *__restrict__ part,
-    int bsz, float scale) {
+    int bsz, float scale, int n_mod, int nbw, int item0) {
   using S = Split<N1, N2>;
   constexpr int N = S::N, G = S::G, S1 = S::S1;
   extern __shared__ float2 smem[];
-  float2 *s_tw = smem;
-  const int nvec = blockDim.x / G;
-  float *s_I = reinterpret_cast<float *>(smem + N + nvec * S::XB);   // [bsz][N]
   const int vec = threadIdx.x / G, lane = threadIdx.x % G;
   const bool act = vec < bsz;
   const int it = blockIdx.y;
   const int y = blockIdx.x * bsz + (act ? vec : 0);
+  float2 *xb = smem + vec * S::XB;
   float2 r[N2];
   if (act && lane < N1) {
     const float2 *src = cols_in + ((size_t)it * N + y) * N + lane;
@@ -275,50 +275,53 @@ __global__ void __launch_bounds__(256) k_rows_inv_part(
 #pragma unroll
     for (int n2 = 0; n2 < N2; ++n2) r[n2] = make_float2(0.f, 0.f);
   }
-  for (int t = threadIdx.x; t < N; t += blockDim.x) s_tw[t] = twA[t];
-  float2 *xb = smem + N + vec * S::XB;
-  __syncthreads();
   RegDFT<N2, true>::run(r);
   if (lane < N1) {
 #pragma unroll
-    for (int k2 = 0; k2 < N2; ++k2) xb[k2 * S1 + lane] = cmul(r[k2], s_tw[k2 * N1 + lane]);
+    for (int k2 = 0; k2 < N2; ++k2) xb[k2 * S1 + lane] = cmul(r[k2], __ldg(twA + k2 * N1 + lane));
   }
   __syncwarp();
-  if (act && lane < N2) {
-    float2 r2[N1];
+  float2 r2[N1];
+  if (lane < N2) {
 #pragma unroll
     for (int n1 = 0; n1 < N1; ++n1) r2[n1] = xb[lane * S1 + n1];
+  }
+  __syncwarp();
+  float *s_row = reinterpret_cast<float *>(xb);   // this warp's intensity row
+  if (act && lane < N2) {
     RegDFT<N1, true>::run(r2);
 #pragma unroll
     for (int k1 = 0; k1 < N1; ++k1)
-      s_I[vec * N + N2 * k1 + lane] = (r2[k1].x * r2[k1].x + r2[k1].y * r2[k1].y) * scale;
+      s_row[N2 * k1 + lane] = (r2[k1].x * r2[k1].x + r2[k1].y * r2[k1].y) * scale;
   }
   __syncthreads();
   const int nd = N / bsz;
-  float *dst = part + ((size_t)it * nd + blockIdx.x) * nd;
+  const int gi = item0 + it;
+  const int b = gi / n_mod, m = gi - b * n_mod;
+  float *dst = part + (((size_t)(b % nbw) * n_mod + m) * nd + blockIdx.x) * nd;
+  const float *s_I = reinterpret_cast<const float *>(smem);
+  constexpr int RS = 2 * S::XB;   // row stride of the intensity rows (floats)
   for (int q = threadIdx.x; q < nd; q += blockDim.x) {
     float v = 0.f;
     for (int rr = 0; rr < bsz; ++rr)
-      for (int xx = 0; xx < bsz; ++xx) v += s_I[rr * N + q * bsz + xx];
+      for (int xx = 0; xx < bsz; ++xx) v += s_I[rr * RS + q * bsz + xx];
     dst[q] = v;
   }
 }
 
 // --------------------------------------------------------------------------
-// D: det[b] (+)= sum over the chunk's items of b, in item order.
-// grid (ceil(nd^2 / 256), batch elements in the chunk).
+// D: det[b] = sum over m = 0 .. n_mod-1 of part[b % nbw][m], in order.
+// grid (ceil(nd^2 / 256), number of batch elements from b0).
 __global__ void __launch_bounds__(256) k_bin_reduce(const float *__restrict__ part,
                                                     float *__restrict__ det, int nd2, int n_mod,
-                                                    int item0, int n_items) {
+                                                    int nbw, int b0) {
   const int pix = blockIdx.x * blockDim.x + threadIdx.x;
   if (pix >= nd2) return;
-  const int b = item0 / n_mod + blockIdx.y;
-  const int lo = max(item0, b * n_mod), hi = min(item0 + n_items, (b + 1) * n_mod);
+  const int b = b0 + blockIdx.y;
+  const float *src = part + (size_t)(b % nbw) * n_mod * nd2 + pix;
   float v = 0.f;
-  for (int gi = lo; gi < hi; ++gi) v += part[(size_t)(gi - item0) * nd2 + pix];
-  float *d = det + (size_t)b * nd2 + pix;
-  if (lo == b * n_mod) *d = v;
-  else *d += v;
+  for (int m = 0; m < n_mod; ++m) v += src[(size_t)m * nd2];
+  det[(size_t)b * nd2 + pix] = v;
 }
 
 // --------------------------------------------------------------------------
@@ -332,14 +335,14 @@ static int configure(PwfsPlan *p) {
   const int bsz = p->n_pix / p->n_sub;
   p->blockA = 256;
   const int vpcA = 256 / S::G;
-  p->smemA = (size_t)(S::N + vpcA * S::XB) * sizeof(float2);
+  p->smemA = (size_t)(vpcA * S::XB) * sizeof(float2);
   p->blockB = kColsTile * S::G;
   p->smemB = ColsCfg<N1, N2, kColsTile>::smem;
   const int thrC = ((bsz * S::G + 31) / 32) * 32;
   if (thrC > 256) return SPECULA_EUNSUPPORTED;   // bin side too large for one CTA strip
   p->blockC = thrC;
   const int nvecC = thrC / S::G;
-  p->smemC = (size_t)(S::N + nvecC * S::XB) * sizeof(float2) + (size_t)bsz * S::N * sizeof(float);
+  p->smemC = (size_t)(nvecC * S::XB) * sizeof(float2);
   if (p->smemA > 227 * 1024 || p->smemB > 227 * 1024 || p->smemC > 227 * 1024)
     return SPECULA_EUNSUPPORTED;
   SPECULA_CK(cudaFuncSetAttribute(k_rows_fwd<N1, N2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -362,6 +365,7 @@ static int run_split(specula_ctx *ctx, PwfsPlan *p, const float *amp, const floa
   const int vpcA = p->blockA / S::G;
   const float scale = 1.0f / (float)p->n_mod;
   int field_done = -1;   // highest batch element whose field is in its slot
+  int det_done = -1;     // highest batch element whose detector is written
   for (int i0 = 0; i0 < total; i0 += p->chunk) {
     const int ni = std::min(p->chunk, total - i0);
     const int b0 = i0 / p->n_mod, b1 = (i0 + ni - 1) / p->n_mod;
@@ -388,11 +392,16 @@ static int run_split(specula_ctx *ctx, PwfsPlan *p, const float *amp, const floa
     SPECULA_LAUNCH(ctx, SPECULA_K_PWFS_ROWS_INV, st,
                    k_rows_inv_part<N1, N2><<<gC, p->blockC, p->smemC, st>>>(
                        p->cols.as<float2>(), p->twA.as<float2>(), p->part.as<float>(), bsz,
-                       scale));
-    dim3 gD((nd * nd + 255) / 256, b1 - b0 + 1);
-    SPECULA_LAUNCH(ctx, SPECULA_K_PWFS_BIN, st,
-                   k_bin_reduce<<<gD, 256, 0, st>>>(p->part.as<float>(), det, nd * nd, p->n_mod,
-                                                    i0, ni));
+                       scale, p->n_mod, p->nbw, i0));
+    // batch elements whose last modulation point is in this chunk
+    const int complete = (i0 + ni) / p->n_mod - 1;
+    if (complete > det_done) {
+      dim3 gD((nd * nd + 255) / 256, complete - det_done);
+      SPECULA_LAUNCH(ctx, SPECULA_K_PWFS_BIN, st,
+                     k_bin_reduce<<<gD, 256, 0, st>>>(p->part.as<float>(), det, nd * nd,
+                                                      p->n_mod, p->nbw, det_done + 1));
+      det_done = complete;
+    }
   }
   return SPECULA_OK;
 }
@@ -414,15 +423,15 @@ int pwfs_set_tiles(PwfsPlan *p, int chunk, int ka) {
   const size_t need_field = (size_t)nbw * p->n_pix * p->n_pix * sizeof(float2);
   const size_t need_rows = (size_t)chunk * p->n_pix * p->N * sizeof(float2);
   const size_t need_cols = (size_t)chunk * p->N * p->N * sizeof(float2);
-  const size_t need_part = (size_t)chunk * nd * nd * sizeof(float);
+  const size_t need_part = (size_t)nbw * p->n_mod * nd * nd * sizeof(float);
   int s;
   if (need_rows > p->rows.bytes || need_cols > p->cols.bytes || need_field > p->field.bytes ||
       need_part > p->part.bytes) {
     cudaDeviceSynchronize();   // the old workspace may still be in use
-    if ((s = p->field.alloc(need_field))) return s;
-    if ((s = p->rows.alloc(need_rows))) return s;
-    if ((s = p->cols.alloc(need_cols))) return s;
-    if ((s = p->part.alloc(need_part))) return s;
+    if ((s = p->field.alloc(std::max(need_field, p->field.bytes)))) return s;
+    if ((s = p->rows.alloc(std::max(need_rows, p->rows.bytes)))) return s;
+    if ((s = p->cols.alloc(std::max(need_cols, p->cols.bytes)))) return s;
+    if ((s = p->part.alloc(std::max(need_part, p->part.bytes)))) return s;
   }
   p->chunk = chunk;
   p->ka = ka;

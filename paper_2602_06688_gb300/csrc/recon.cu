@@ -51,13 +51,23 @@ __global__ void __launch_bounds__(kReconWarps * 32) k_mvm_f32(
   float acc[NB];
 #pragma unroll
   for (int q = 0; q < NB; ++q) acc[q] = 0.f;
-  for (int j = lane; j < n4; j += 32) {
-    const float4 a = ld_stream(r4 + j);
+  // four independent 16-byte row loads in flight per lane
+  for (int j0 = lane; j0 < n4; j0 += 4 * 32) {
+    float4 a[4];
 #pragma unroll
-    for (int q = 0; q < NB; ++q) {
-      if (b0 + q < n_batch) {
-        const float4 x = __ldg(reinterpret_cast<const float4 *>(s + (size_t)(b0 + q) * n_slopes) + j);
-        acc[q] += a.x * x.x + a.y * x.y + a.z * x.z + a.w * x.w;
+    for (int u = 0; u < 4; ++u)
+      a[u] = (j0 + 32 * u < n4) ? ld_stream(r4 + j0 + 32 * u) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int j = j0 + 32 * u;
+      if (j < n4) {
+#pragma unroll
+        for (int q = 0; q < NB; ++q) {
+          if (b0 + q < n_batch) {
+            const float4 x = __ldg(reinterpret_cast<const float4 *>(s + (size_t)(b0 + q) * n_slopes) + j);
+            acc[q] += a[u].x * x.x + a[u].y * x.y + a[u].z * x.z + a[u].w * x.w;
+          }
+        }
       }
     }
   }
@@ -98,6 +108,7 @@ __global__ void __launch_bounds__(kReconWarps * 32) k_mvm_bf16(
   float acc[NB];
 #pragma unroll
   for (int q = 0; q < NB; ++q) acc[q] = 0.f;
+#pragma unroll 4
   for (int j = lane; j < n8; j += 32) {
     const uint4 hv = ld_stream_u4(h8 + j);
     float r[8] = {bf_lo(hv.x), bf_hi(hv.x), bf_lo(hv.y), bf_hi(hv.y),

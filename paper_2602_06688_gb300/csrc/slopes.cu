@@ -6,7 +6,7 @@
 
 namespace specula {
 
-constexpr int kPyrThreads = 512;
+constexpr int kPyrThreads = 1024;
 
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
@@ -35,6 +35,7 @@ __global__ void __launch_bounds__(kPyrThreads) k_pyr_slopes(
   const int w2 = 2 * n_sub;
   const float *d = det + (size_t)b * w2 * w2;
   float part = 0.f;
+#pragma unroll 4
   for (int k = threadIdx.x; k < n_valid; k += blockDim.x) {
     const int s = checked_idx(idx, k, n_sub, status);
     const int a = s / n_sub, c = s % n_sub;
@@ -53,6 +54,7 @@ __global__ void __launch_bounds__(kPyrThreads) k_pyr_slopes(
   __syncthreads();
   const float T = s_T;
   float *o = out + (size_t)b * 2 * n_valid;
+#pragma unroll 4
   for (int k = threadIdx.x; k < n_valid; k += blockDim.x) {
     const int s = checked_idx(idx, k, n_sub, status);
     const int a = s / n_sub, c = s % n_sub;
