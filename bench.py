@@ -245,7 +245,7 @@ def gpu_leg(args, ws, rank, local):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     wl = synth.workload(WORKLOAD)
     ctx = sp.Context(local)
-    fr = PwfsFrame(ctx, wl, seed_offset=1000 * rank)
+    fr = PwfsFrame(ctx, wl, seed_offset=1000 * rank, autotune=True)
     dt = wl.dt_s
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
     K, W = args.steps, args.warmup
@@ -374,6 +374,7 @@ def gpu_leg(args, ws, rank, local):
                 "config": {"workload": WORKLOAD, "pupil_px": 480, "fft": 960, "n_mod": 48,
                            "n_sub": 96, "layers": 35, "n_modes": fr.n_modes,
                            "n_slopes": fr.n_slopes, "l2": "flushed between timed frames",
+                           "pwfs_tiles": {"chunk": fr.tiles[0], "ka": fr.tiles[1]} if fr.tiles else None,
                            "wall_ms_per_step_incl_flush": (wall1 - wall0) * 1e3 / K},
                 "roofline": roof, "kernels": kern, "variants": variants,
                 "e2e": {"value": e2e, "unit": "frames/s", "h2d_bytes_per_step": 8,

@@ -250,6 +250,18 @@ int specula_pwfs_set_tiles(specula_ctx *ctx, const specula_pupil_desc *pupil,
 int specula_pwfs_get_tiles(specula_ctx *ctx, const specula_pupil_desc *pupil,
                            const specula_pwfs_desc *pwfs, int32_t *chunk, int32_t *ka);
 
+/* Autotuner: time every candidate (chunk in {1,2,3,4,6,8,12,16,24,32,48,64}
+ * up to the batch's item count and with workspace <= max_workspace_bytes;
+ * ka in {1, 2}) with CUDA events over `reps` images of the caller's inputs on
+ * `stream`, keep the fastest in the plan and return it.  Set-up call: may
+ * reallocate the workspace and synchronises the stream.  det_dev is
+ * overwritten. */
+int specula_pwfs_autotune(specula_ctx *ctx, const specula_pupil_desc *pupil,
+                          const specula_pwfs_desc *pwfs, const float *amp_dev,
+                          const float *phase_dev, int32_t n_batch, float *det_dev,
+                          int32_t reps, int64_t max_workspace_bytes, int32_t *chunk,
+                          int32_t *ka, void *stream);
+
 /* Modulated pyramid image (ModulatedPyramid + CCD, noise off).  For each of
  * n_batch phase maps and each modulation point m:
  *   E_m = amp exp(i phase) exp(2 pi i r (x cos t_m + y sin t_m) / n_pix),

@@ -247,6 +247,23 @@ def specula_pwfs_get_tiles(ctx, pupil, pwfs):
     return ch.value, ka.value
 
 
+def specula_pwfs_autotune(ctx, pupil, pwfs, amp, phase, det, reps=3,
+                          max_workspace_bytes=512 << 20, stream=None):
+    """Time the candidate tilings on these buffers, keep and return the best
+    (chunk, ka)."""
+    import torch
+    n = pupil.n_pix
+    nb = phase.numel() // (n * n)
+    side = 2 * pwfs.n_sub
+    ch, ka = C.c_int32(), C.c_int32()
+    _abi.check(lib().specula_pwfs_autotune(
+        ctx.handle, C.byref(pupil), C.byref(pwfs), _dev(amp, torch.float32, n * n, "amp"),
+        _dev(phase, torch.float32, nb * n * n, "phase"), nb,
+        _dev(det, torch.float32, nb * side * side, "det"), int(reps), int(max_workspace_bytes),
+        C.byref(ch), C.byref(ka), _stream(stream)), "specula_pwfs_autotune")
+    return ch.value, ka.value
+
+
 def specula_pwfs_image(ctx, pupil, pwfs, amp, phase, det, stream=None):
     """phase: (n_batch, n, n) or (n, n); det: (n_batch, 2 n_sub, 2 n_sub)."""
     import torch

@@ -79,6 +79,8 @@ SIGNATURES = {
     "specula_pwfs_plan": (C.c_int, [vp, P(PupilDesc), P(PwfsDesc)]),
     "specula_pwfs_set_tiles": (C.c_int, [vp, P(PupilDesc), P(PwfsDesc), i32, i32]),
     "specula_pwfs_get_tiles": (C.c_int, [vp, P(PupilDesc), P(PwfsDesc), P(i32), P(i32)]),
+    "specula_pwfs_autotune": (C.c_int, [vp, P(PupilDesc), P(PwfsDesc), vp, vp, i32, vp, i32,
+                                        C.c_int64, P(i32), P(i32), vp]),
     "specula_pwfs_image": (C.c_int, [vp, P(PupilDesc), P(PwfsDesc), vp, vp, i32, vp, vp]),
     "specula_sh_plan": (C.c_int, [vp, P(PupilDesc), P(ShDesc), P(i32)]),
     "specula_sh_image": (C.c_int, [vp, P(PupilDesc), P(ShDesc), vp, vp, i32, vp, vp]),

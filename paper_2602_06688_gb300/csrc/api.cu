@@ -317,6 +317,27 @@ extern "C" int specula_pwfs_set_tiles(specula_ctx *ctx, const specula_pupil_desc
   return pwfs_set_tiles(p, chunk, ka);
 }
 
+extern "C" int specula_pwfs_autotune(specula_ctx *ctx, const specula_pupil_desc *pupil,
+                                     const specula_pwfs_desc *pwfs, const float *amp_dev,
+                                     const float *phase_dev, int32_t n_batch, float *det_dev,
+                                     int32_t reps, int64_t max_workspace_bytes, int32_t *chunk,
+                                     int32_t *ka, void *stream) {
+  if (!ctx || !amp_dev || !phase_dev || !det_dev || !chunk || !ka) return SPECULA_EINVAL;
+  if (n_batch < 1 || reps < 1 || reps > 1000 || max_workspace_bytes < 1) return SPECULA_EINVAL;
+  int s = check_pwfs(pupil, pwfs);
+  if (s) return s;
+  PwfsPlan *p = pwfs_plan_find(ctx, pupil, pwfs);
+  if (!p) return SPECULA_ENOPLAN;
+  SPECULA_CK(cudaSetDevice(ctx->device));
+  int bc = 0, bk = 0;
+  s = pwfs_autotune(ctx, p, amp_dev, phase_dev, n_batch, det_dev, (cudaStream_t)stream, reps,
+                    (size_t)max_workspace_bytes, &bc, &bk);
+  if (s) return s;
+  *chunk = bc;
+  *ka = bk;
+  return SPECULA_OK;
+}
+
 extern "C" int specula_pwfs_get_tiles(specula_ctx *ctx, const specula_pupil_desc *pupil,
                                       const specula_pwfs_desc *pwfs, int32_t *chunk, int32_t *ka) {
   if (!ctx || !chunk || !ka) return SPECULA_EINVAL;

@@ -120,6 +120,9 @@ int pwfs_plan_build(specula_ctx *ctx, const specula_pupil_desc *pupil,
 PwfsPlan *pwfs_plan_find(specula_ctx *ctx, const specula_pupil_desc *pupil,
                          const specula_pwfs_desc *pwfs);
 int pwfs_set_tiles(PwfsPlan *p, int chunk, int ka);
+int pwfs_autotune(specula_ctx *ctx, PwfsPlan *p, const float *amp, const float *phase,
+                  int n_batch, float *det, cudaStream_t st, int reps, size_t max_ws_bytes,
+                  int *best_chunk, int *best_ka);
 int pwfs_run(specula_ctx *ctx, PwfsPlan *plan, const float *amp, const float *phase,
              int n_batch, float *det, cudaStream_t st);
 int sh_plan_build(specula_ctx *ctx, const specula_pupil_desc *pupil,

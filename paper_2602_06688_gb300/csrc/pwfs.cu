@@ -451,6 +451,46 @@ int pwfs_run(specula_ctx *ctx, PwfsPlan *p, const float *amp, const float *phase
   }
 }
 
+// Time each candidate tiling on the caller's buffers (set-up call: may
+// reallocate the workspace and synchronises) and keep the fastest.
+int pwfs_autotune(specula_ctx *ctx, PwfsPlan *p, const float *amp, const float *phase,
+                  int n_batch, float *det, cudaStream_t st, int reps, size_t max_ws_bytes,
+                  int *best_chunk, int *best_ka) {
+  static const int kChunks[] = {1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64};
+  const size_t per_item = ((size_t)p->n_pix * p->N + (size_t)p->N * p->N) * sizeof(float2);
+  const int total = n_batch * p->n_mod;
+  float best = 1e30f;
+  int bc = p->chunk, bk = p->ka;
+  cudaEvent_t e0, e1;
+  SPECULA_CK(cudaEventCreate(&e0));
+  SPECULA_CK(cudaEventCreate(&e1));
+  int status = SPECULA_OK;
+  for (int c : kChunks) {
+    if (c > std::max(total, 1) && c != 1) break;
+    if ((size_t)c * per_item > max_ws_bytes && c != 1) break;
+    for (int ka = 1; ka <= 2; ++ka) {
+      if (ka > c) break;
+      if ((status = pwfs_set_tiles(p, c, ka))) goto done;
+      if ((status = pwfs_run(ctx, p, amp, phase, n_batch, det, st))) goto done;   // warm-up
+      cudaEventRecord(e0, st);
+      for (int r = 0; r < reps; ++r)
+        if ((status = pwfs_run(ctx, p, amp, phase, n_batch, det, st))) goto done;
+      cudaEventRecord(e1, st);
+      if (cudaEventSynchronize(e1) != cudaSuccess) { status = SPECULA_ECUDA; goto done; }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) { best = ms; bc = c; bk = ka; }
+    }
+  }
+  status = pwfs_set_tiles(p, bc, bk);
+  *best_chunk = bc;
+  *best_ka = bk;
+done:
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return status;
+}
+
 static int configure_for(PwfsPlan *p) {
   switch (p->N) {
     case 64: return configure<8, 8>(p);

@@ -23,7 +23,7 @@ def seeded_reconstructor(n_modes, n_slopes, seed):
 
 class PwfsFrame:
     def __init__(self, ctx, wl, sensor=0, precision=PREC_FP32, R=None, n_modes=None,
-                 seed_offset=0, device="cuda"):
+                 seed_offset=0, device="cuda", autotune=False):
         import torch
         self.torch = torch
         self.ctx = ctx
@@ -68,6 +68,14 @@ class PwfsFrame:
         specula_pwfs_image(ctx, self.pupil, self.pwfs, self.amp, self.phase, self.det)
         specula_slopes(ctx, self.slopec, self.det, None, self.ref)
         torch.cuda.synchronize()
+        self.tiles = None
+        if autotune:
+            from .autotune import tune_pwfs
+            specula_atmo_extract(ctx, self.layers, self.screens, self.src, self.pupil, 0.0,
+                                 self.phase)
+            self.tiles = tune_pwfs(ctx, self.pupil, self.pwfs, self.amp, self.phase, self.det,
+                                   force=autotune == "force")
+            torch.cuda.synchronize()
 
     def set_precision(self, precision):
         torch = self.torch

@@ -152,3 +152,34 @@ def test_plan_required_and_bad_args(env):
     with pytest.raises(sp.SpeculaError) as e:
         sp.specula_pwfs_plan(ctx, pu, sp.PwfsDesc(2, 4, 16, 60, 3.0))
     assert e.value.status == sp.EUNSUPPORTED
+
+
+def test_tiling_invariance_and_autotune(env):
+    """Every (chunk, ka) tiling gives a bit-identical detector (item bins are
+    reduced in modulation order whatever the chunking), and the autotuner
+    returns one of the candidates."""
+    torch, sp, ctx = env
+    n_pix, n_mod, n_sub = 32, 8, 8
+    pu = sp.PupilDesc(n_pix, 0.25, 0.2)
+    pw = sp.PwfsDesc(2, n_mod, n_sub, n_pix, 3.0)
+    sp.specula_pwfs_plan(ctx, pu, pw)
+    amp = torch.empty(n_pix, n_pix, device="cuda")
+    sp.specula_pupil_mask(ctx, pu, amp)
+    ph = torch.tensor(np.stack([kolmogorov_phase(n_pix, 0.25, 0.15, seed=s) for s in (1, 2, 3)])
+                      .astype(np.float32), device="cuda")
+    outs = []
+    for chunk, ka in [(1, 1), (3, 2), (5, 1), (8, 2), (24, 1)]:
+        sp.specula_pwfs_set_tiles(ctx, pu, pw, chunk, ka)
+        det = torch.empty(3, 2 * n_sub, 2 * n_sub, device="cuda")
+        sp.specula_pwfs_image(ctx, pu, pw, amp, ph, det)
+        torch.cuda.synchronize()
+        outs.append(det.cpu())
+    for o in outs[1:]:
+        assert torch.equal(o, outs[0])
+    det = torch.empty(3, 2 * n_sub, 2 * n_sub, device="cuda")
+    ch, ka = sp.specula_pwfs_autotune(ctx, pu, pw, amp, ph, det, reps=2)
+    assert ch in (1, 2, 3, 4, 6, 8, 12, 16, 24) and ka in (1, 2)
+    assert sp.specula_pwfs_get_tiles(ctx, pu, pw) == (ch, ka)
+    sp.specula_pwfs_image(ctx, pu, pw, amp, ph, det)
+    torch.cuda.synchronize()
+    assert torch.equal(det.cpu(), outs[0])
