@@ -250,33 +250,44 @@ def gpu_leg(args, ws, rank, local):
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
     K, W = args.steps, args.warmup
 
-    def timed(nsteps, t0_step, with_flush=True):
+    st = torch.cuda.Stream()
+
+    def timed(nsteps, t0_step, graph=True, with_flush=True):
+        """Per-frame CUDA events on the launch stream; the L2 flush runs
+        between frames, outside the events."""
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
               for _ in range(nsteps)]
-        for k in range(nsteps):
-            if with_flush:
-                flush.zero_()
-            ev[k][0].record()
-            fr.frame((t0_step + k) * dt)
-            ev[k][1].record()
+        with torch.cuda.stream(st):
+            for k in range(nsteps):
+                if with_flush:
+                    flush.zero_()
+                ev[k][0].record(st)
+                if graph:
+                    fr.replay((t0_step + k) * dt, st)
+                else:
+                    fr.frame((t0_step + k) * dt, stream=st)
+                ev[k][1].record(st)
         torch.cuda.synchronize()
         return [a.elapsed_time(b) for a, b in ev]
 
     for k in range(W):
         fr.frame(k * dt)
     torch.cuda.synchronize()
+    fr.capture(st)
+    graph_kernels = fr.graph.kernel_count()
+    timed(W, 0)
 
-    # ---- headline: plain FP32 path
+    # ---- headline: plain FP32 path, whole frame replayed as one CUDA graph
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    n0 = sp.specula_launch_count(ctx)
     with ClockSampler(local) as clk:
         wall0 = time.perf_counter()
         ms = timed(K, W)
         wall1 = time.perf_counter()
-    launches = sp.specula_launch_count(ctx) - n0
+    launches = graph_kernels * K
     total_ms = sum(ms)
+    ms_eager = timed(K, W, graph=False)
     if dist:
         t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -301,8 +312,9 @@ def gpu_leg(args, ws, rank, local):
     ref_modes = (R64 @ fp32_slopes.double())
     for name, prec in (("fp32", sp.PREC_FP32), ("bf16x2", sp.PREC_BF16X2), ("bf16", sp.PREC_BF16)):
         fr.set_precision(prec)
-        for k in range(3):
-            fr.frame((W + K + k) * dt)
+        fr.graph.close()
+        fr.capture(st)
+        timed(3, W)
         msv = timed(K, W)
         # modal error of this reconstructor on the FP32 slopes, vs FP64 R s
         out = torch.empty_like(fr.modes)
@@ -313,10 +325,13 @@ def gpu_leg(args, ws, rank, local):
         variants[name] = {"frames_per_s": K / (sum(msv) / 1e3), "ms_per_step": sum(msv) / K,
                           "modal_rel_rms_err_vs_fp64": err}
     fr.set_precision(sp.PREC_FP32)
+    fr.graph.close()
+    fr.capture(st)
 
-    # ---- live per-kernel roofline (library event tracing on the launch stream)
+    # ---- live per-kernel roofline (library event tracing on the launch
+    # stream; tracing brackets eager launches, so this pass runs eagerly)
     sp.specula_prof_enable(ctx, 64 * (K + 4))
-    timed(K, W)
+    timed(K, W, graph=False)
     prof = sp.specula_prof_read(ctx)
     sp.specula_prof_enable(ctx, 0)
     pk, how = peaks()
@@ -351,18 +366,19 @@ def gpu_leg(args, ws, rank, local):
         kern["recon"]["achieved_gbs"] = gbs
         kern["recon"]["hbm_frac"] = gbs / pk["hbm_gbs"]
 
-    # ---- end to end through the public API with host buffers
+    # ---- end to end through the public API with host buffers: per frame the
+    # time goes host -> device, the captured frame runs, the modes come back
     t_host = torch.empty(1, dtype=torch.float64).pin_memory()
-    t_dev = torch.empty(1, dtype=torch.float64, device="cuda")
     modes_host = torch.empty(fr.n_modes, dtype=torch.float32).pin_memory()
     torch.cuda.synchronize()
     e0 = time.perf_counter()
-    for k in range(K):
-        t_host[0] = (W + k) * dt
-        t_dev.copy_(t_host, non_blocking=True)
-        fr.frame(0.0, t_dev=t_dev)
-        modes_host.copy_(fr.modes, non_blocking=True)
-        torch.cuda.synchronize()
+    with torch.cuda.stream(st):
+        for k in range(K):
+            t_host[0] = (W + k) * dt
+            fr.t_dev.copy_(t_host, non_blocking=True)
+            fr.graph.launch(st)
+            modes_host.copy_(fr.modes, non_blocking=True)
+            st.synchronize()
     e1 = time.perf_counter()
     e2e = ws * K / (e1 - e0)
 
@@ -375,6 +391,8 @@ def gpu_leg(args, ws, rank, local):
                            "n_sub": 96, "layers": 35, "n_modes": fr.n_modes,
                            "n_slopes": fr.n_slopes, "l2": "flushed between timed frames",
                            "pwfs_tiles": {"chunk": fr.tiles[0], "ka": fr.tiles[1]} if fr.tiles else None,
+                           "frame": "one CUDA graph per frame (%d kernels)" % graph_kernels,
+                           "eager_frames_per_s": K / (sum(ms_eager) / 1e3),
                            "wall_ms_per_step_incl_flush": (wall1 - wall0) * 1e3 / K},
                 "roofline": roof, "kernels": kern, "variants": variants,
                 "e2e": {"value": e2e, "unit": "frames/s", "h2d_bytes_per_step": 8,

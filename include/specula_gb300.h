@@ -167,6 +167,23 @@ int specula_prof_read(specula_ctx *ctx, double *ms_host, int64_t *n_host);
 /* Number of kernels this context has launched since it was created. */
 int specula_launch_count(specula_ctx *ctx, int64_t *count);
 
+/* ---- frame graphs ---------------------------------------------------------------
+ * The processing objects' trigger phase is captured once into a CUDA graph
+ * and replayed every time step (Sect. 2.3, `build_stream`).  begin starts a
+ * thread-local capture on `stream` (a created stream, not the legacy NULL
+ * stream); every per-frame call issued on that stream until end is
+ * recorded, not run; end instantiates the graph.  A frame that must advance
+ * in time reads t from device memory (specula_atmo_extract t_dev), which the
+ * caller updates before each launch.  Tracing must be disabled while
+ * capturing.  begin/end may allocate; launch only enqueues. */
+typedef struct specula_graph specula_graph;
+int specula_graph_begin(specula_ctx *ctx, void *stream);
+int specula_graph_end(specula_ctx *ctx, void *stream, specula_graph **out);
+int specula_graph_launch(specula_graph *graph, void *stream);
+/* Number of kernel nodes in the graph. */
+int specula_graph_kernel_count(specula_graph *graph, int64_t *count);
+int specula_graph_destroy(specula_graph *graph);
+
 /* ---- integer geometry (host; bit-exact; no GPU needed) ---------------------
  * Pupil stop (PupilStop): pixel (j, i) is inside iff
  *   r4 = (2i - n + 1)^2 + (2j - n + 1)^2 <= n^2  and  r4 > (obsc * n)^2,

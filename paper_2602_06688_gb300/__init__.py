@@ -144,6 +144,57 @@ def specula_launch_count(ctx):
     return v.value
 
 
+class Graph:
+    """An instantiated CUDA graph of per-frame calls (specula_graph_*)."""
+
+    def __init__(self, handle):
+        self.handle = handle
+
+    def launch(self, stream=None):
+        _abi.check(lib().specula_graph_launch(self.handle, _stream(stream)),
+                   "specula_graph_launch")
+
+    def kernel_count(self):
+        v = C.c_int64()
+        _abi.check(lib().specula_graph_kernel_count(self.handle, C.byref(v)),
+                   "specula_graph_kernel_count")
+        return v.value
+
+    def close(self):
+        if self.handle:
+            lib().specula_graph_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def specula_graph_begin(ctx, stream):
+    _abi.check(lib().specula_graph_begin(ctx.handle, _stream(stream)), "specula_graph_begin")
+
+
+def specula_graph_end(ctx, stream):
+    h = C.c_void_p()
+    _abi.check(lib().specula_graph_end(ctx.handle, _stream(stream), C.byref(h)),
+               "specula_graph_end")
+    return Graph(h)
+
+
+def specula_graph_launch(graph, stream=None):
+    graph.launch(stream)
+
+
+def specula_graph_kernel_count(graph):
+    return graph.kernel_count()
+
+
+def specula_graph_destroy(graph):
+    graph.close()
+
+
 def specula_strerror(status):
     return lib().specula_strerror(int(status)).decode()
 

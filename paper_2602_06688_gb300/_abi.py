@@ -68,6 +68,11 @@ SIGNATURES = {
     "specula_prof_enable": (C.c_int, [vp, i32]),
     "specula_prof_read": (C.c_int, [vp, vp, vp]),
     "specula_launch_count": (C.c_int, [vp, P(C.c_int64)]),
+    "specula_graph_begin": (C.c_int, [vp, vp]),
+    "specula_graph_end": (C.c_int, [vp, vp, P(vp)]),
+    "specula_graph_launch": (C.c_int, [vp, vp]),
+    "specula_graph_kernel_count": (C.c_int, [vp, P(C.c_int64)]),
+    "specula_graph_destroy": (C.c_int, [vp]),
     "specula_pupil_mask_host": (C.c_int, [P(PupilDesc), vp]),
     "specula_valid_subaps_host": (C.c_int, [P(PupilDesc), i32, vp, P(i32)]),
     "specula_mod_table_host": (C.c_int, [i32, vp, vp]),

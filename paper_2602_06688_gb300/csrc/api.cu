@@ -46,8 +46,11 @@ extern "C" int specula_ctx_create(specula_ctx **out, int device) {
   }
   int s = pwfs_init_device();
   if (!s) s = sh_init_device();
+  if (!s) s = atmo_alloc_tables(c);
   if (s) {
     cudaFree(c->status_dev);
+    if (c->atmo_tab_i) cudaFree(c->atmo_tab_i);
+    if (c->atmo_tab_f) cudaFree(c->atmo_tab_f);
     delete c;
     return s;
   }
@@ -71,6 +74,8 @@ extern "C" int specula_ctx_destroy(specula_ctx *ctx) {
   ctx->pwfs.clear();
   ctx->sh.clear();
   if (ctx->status_dev) cudaFree(ctx->status_dev);
+  if (ctx->atmo_tab_i) cudaFree(ctx->atmo_tab_i);
+  if (ctx->atmo_tab_f) cudaFree(ctx->atmo_tab_f);
   delete ctx;
   return SPECULA_OK;
 }
@@ -112,6 +117,72 @@ extern "C" int specula_prof_read(specula_ctx *ctx, double *ms_host, int64_t *n_h
   }
   ctx->rec_kid.clear();
   ctx->ev_next = 0;
+  return SPECULA_OK;
+}
+
+struct specula_graph {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int device = 0;
+};
+
+extern "C" int specula_graph_begin(specula_ctx *ctx, void *stream) {
+  if (!ctx || !stream) return SPECULA_EINVAL;
+  if (ctx->prof) return SPECULA_EINVAL;
+  SPECULA_CK(cudaSetDevice(ctx->device));
+  SPECULA_CK(cudaStreamBeginCapture((cudaStream_t)stream, cudaStreamCaptureModeThreadLocal));
+  return SPECULA_OK;
+}
+
+extern "C" int specula_graph_end(specula_ctx *ctx, void *stream, specula_graph **out) {
+  if (!ctx || !stream || !out) return SPECULA_EINVAL;
+  *out = nullptr;
+  cudaGraph_t g = nullptr;
+  SPECULA_CK(cudaStreamEndCapture((cudaStream_t)stream, &g));
+  specula_graph *sg = new (std::nothrow) specula_graph();
+  if (!sg) {
+    cudaGraphDestroy(g);
+    return SPECULA_ENOMEM;
+  }
+  sg->graph = g;
+  sg->device = ctx->device;
+  if (cudaGraphInstantiate(&sg->exec, g, 0) != cudaSuccess) {
+    cudaGraphDestroy(g);
+    delete sg;
+    return SPECULA_ECUDA;
+  }
+  *out = sg;
+  return SPECULA_OK;
+}
+
+extern "C" int specula_graph_launch(specula_graph *graph, void *stream) {
+  if (!graph || !graph->exec) return SPECULA_EINVAL;
+  SPECULA_CK(cudaGraphLaunch(graph->exec, (cudaStream_t)stream));
+  return SPECULA_OK;
+}
+
+extern "C" int specula_graph_kernel_count(specula_graph *graph, int64_t *count) {
+  if (!graph || !count) return SPECULA_EINVAL;
+  size_t n = 0;
+  SPECULA_CK(cudaGraphGetNodes(graph->graph, nullptr, &n));
+  std::vector<cudaGraphNode_t> nodes(n);
+  if (n) SPECULA_CK(cudaGraphGetNodes(graph->graph, nodes.data(), &n));
+  int64_t k = 0;
+  for (size_t i = 0; i < n; ++i) {
+    cudaGraphNodeType t;
+    SPECULA_CK(cudaGraphNodeGetType(nodes[i], &t));
+    if (t == cudaGraphNodeTypeKernel) ++k;
+  }
+  *count = k;
+  return SPECULA_OK;
+}
+
+extern "C" int specula_graph_destroy(specula_graph *graph) {
+  if (!graph) return SPECULA_EINVAL;
+  cudaSetDevice(graph->device);
+  if (graph->exec) cudaGraphExecDestroy(graph->exec);
+  if (graph->graph) cudaGraphDestroy(graph->graph);
+  delete graph;
   return SPECULA_OK;
 }
 

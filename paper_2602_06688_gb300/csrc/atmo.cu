@@ -9,18 +9,21 @@
 // indices agree exactly with any IEEE float64 evaluation of the same formula.
 // The interpolation and the layer sum run in float32.
 //
-// A CTA covers a 32 x 8 pixel tile: it first evaluates the tile's 32 column
-// and 8 row coordinates of every layer in float64 into shared memory (40
-// evaluations per layer instead of 256), then each thread sums its pixel over
-// the layers, four layers' gathers in flight at a time.  A warp reads 32
-// consecutive columns of one screen row: coalesced.
+// The coordinates are separable (u depends on the column only, v on the row
+// only), so k_atmo_coords evaluates them once per frame, 2 n_pix per layer,
+// into a context-owned table (float64 is slow on this part: evaluating them
+// per tile would cost more than the gathers).  k_atmo_extract covers 32 x 8
+// pixel tiles: it stages its tile's table entries in shared memory, then each
+// thread sums its pixel over the layers, four layers' gathers in flight at a
+// time.  A warp reads 32 consecutive columns of one screen row: coalesced.
 #include <math.h>
 
 #include "internal.h"
 
 namespace specula {
 
-constexpr int kMaxLayers = 64;
+constexpr int kMaxLayers = SPECULA_ATMO_MAX_LAYERS;
+constexpr int kMaxPix = SPECULA_ATMO_MAX_PIX;
 constexpr int kTileX = 32, kTileY = 8;
 
 struct AtmoParams {
@@ -34,40 +37,55 @@ struct AtmoParams {
   float scale;   // 500 / lambda
 };
 
-__device__ __forceinline__ void coord(double idx, int n, double pupil_pitch, double s, double h,
-                                      double theta, double v, double t, double pitch, int side,
-                                      int *i0, float *fr) {
-  const double x = __dmul_rn(__dsub_rn(idx, (double)(n - 1) / 2.0), pupil_pitch);
-  const double off = __dsub_rn(__dmul_rn(h, theta), __dmul_rn(v, t));
-  const double u = __dadd_rn(__ddiv_rn(__dadd_rn(__dmul_rn(x, s), off), pitch), (double)side / 2.0);
+// table layout: [layer][axis (0 = x, 1 = y)][pixel]
+__global__ void __launch_bounds__(256) k_atmo_coords(const AtmoParams P, double t_host,
+                                                     const double *__restrict__ t_dev,
+                                                     int *__restrict__ tab_i,
+                                                     float *__restrict__ tab_f) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = P.n_pix;
+  if (e >= P.n_layers * 2 * n) return;
+  const int l = e / (2 * n), r = e % (2 * n);
+  const int axis = r / n, idx = r % n;
+  const double t = t_dev ? *t_dev : t_host;
+  const double s = __dsub_rn(1.0, __ddiv_rn(P.h[l], P.H));
+  const double theta = axis ? P.theta_y : P.theta_x;
+  const double v = axis ? P.vy[l] : P.vx[l];
+  const int side = P.side[l];
+  const double x = __dmul_rn(__dsub_rn((double)idx, (double)(n - 1) / 2.0), P.pupil_pitch);
+  const double off = __dsub_rn(__dmul_rn(P.h[l], theta), __dmul_rn(v, t));
+  const double u =
+      __dadd_rn(__ddiv_rn(__dadd_rn(__dmul_rn(x, s), off), P.pitch[l]), (double)side / 2.0);
   const double u0 = floor(u);
   const double f = __dsub_rn(u, u0);
   long long k = (long long)u0 % side;
   if (k < 0) k += side;
-  *i0 = (int)k;
-  *fr = (float)f;
+  const size_t o = ((size_t)l * 2 + axis) * kMaxPix + idx;
+  tab_i[o] = (int)k;
+  tab_f[o] = (float)f;
 }
 
-__global__ void __launch_bounds__(256) k_atmo_extract(const AtmoParams P, double t_host,
-                                                      const double *__restrict__ t_dev,
+__global__ void __launch_bounds__(256) k_atmo_extract(const AtmoParams P,
+                                                      const int *__restrict__ tab_i,
+                                                      const float *__restrict__ tab_f,
                                                       float *__restrict__ phase) {
   __shared__ int s_ix[kMaxLayers][kTileX], s_iy[kMaxLayers][kTileY];
   __shared__ float s_fx[kMaxLayers][kTileX], s_fy[kMaxLayers][kTileY];
-  const double t = t_dev ? *t_dev : t_host;
   const int x0 = blockIdx.x * kTileX, y0 = blockIdx.y * kTileY;
   const int nthr = blockDim.x * blockDim.y;
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
   constexpr int PER = kTileX + kTileY;
   for (int e = tid; e < P.n_layers * PER; e += nthr) {
     const int l = e / PER, r = e % PER;
-    const double s = __dsub_rn(1.0, __ddiv_rn(P.h[l], P.H));
     if (r < kTileX) {
-      coord((double)(x0 + r), P.n_pix, P.pupil_pitch, s, P.h[l], P.theta_x, P.vx[l], t,
-            P.pitch[l], P.side[l], &s_ix[l][r], &s_fx[l][r]);
+      const int i = min(x0 + r, P.n_pix - 1);
+      s_ix[l][r] = tab_i[(size_t)(2 * l) * kMaxPix + i];
+      s_fx[l][r] = tab_f[(size_t)(2 * l) * kMaxPix + i];
     } else {
       const int q = r - kTileX;
-      coord((double)(y0 + q), P.n_pix, P.pupil_pitch, s, P.h[l], P.theta_y, P.vy[l], t,
-            P.pitch[l], P.side[l], &s_iy[l][q], &s_fy[l][q]);
+      const int j = min(y0 + q, P.n_pix - 1);
+      s_iy[l][q] = tab_i[(size_t)(2 * l + 1) * kMaxPix + j];
+      s_fy[l][q] = tab_f[(size_t)(2 * l + 1) * kMaxPix + j];
     }
   }
   __syncthreads();
@@ -93,6 +111,13 @@ __global__ void __launch_bounds__(256) k_atmo_extract(const AtmoParams P, double
   if (i < P.n_pix && j < P.n_pix) phase[(size_t)j * P.n_pix + i] = acc * P.scale;
 }
 
+int atmo_alloc_tables(specula_ctx *ctx) {
+  const size_t n = (size_t)kMaxLayers * 2 * kMaxPix;
+  if (cudaMalloc(&ctx->atmo_tab_i, n * sizeof(int)) != cudaSuccess) return SPECULA_ENOMEM;
+  if (cudaMalloc(&ctx->atmo_tab_f, n * sizeof(float)) != cudaSuccess) return SPECULA_ENOMEM;
+  return SPECULA_OK;
+}
+
 }  // namespace specula
 
 using namespace specula;
@@ -106,7 +131,8 @@ extern "C" int specula_atmo_extract(specula_ctx *ctx, int32_t n_layers,
   if (!ctx || !layers || !screens_dev || !src || !pupil || !phase_dev) return SPECULA_EINVAL;
   if (n_layers < 1) return SPECULA_EINVAL;
   if (n_layers > kMaxLayers) return SPECULA_EUNSUPPORTED;
-  if (pupil->n_pix < 1 || pupil->n_pix > 16384 || !(pupil->pitch_m > 0)) return SPECULA_EINVAL;
+  if (pupil->n_pix < 1 || !(pupil->pitch_m > 0)) return SPECULA_EINVAL;
+  if (pupil->n_pix > kMaxPix) return SPECULA_EUNSUPPORTED;
   if (!(src->wavelength_nm > 0) || !(src->height_m > 0)) return SPECULA_EINVAL;
   if (!t_dev && !isfinite(t_s)) return SPECULA_EINVAL;
   AtmoParams P;
@@ -130,9 +156,15 @@ extern "C" int specula_atmo_extract(specula_ctx *ctx, int32_t n_layers,
     P.vx[l] = L.vx_mps;
     P.vy[l] = L.vy_mps;
   }
+  cudaStream_t st = (cudaStream_t)stream;
+  const int nc = n_layers * 2 * pupil->n_pix;
+  SPECULA_LAUNCH(ctx, SPECULA_K_ATMO, st,
+                 k_atmo_coords<<<(nc + 255) / 256, 256, 0, st>>>(P, t_s, t_dev, ctx->atmo_tab_i,
+                                                                 ctx->atmo_tab_f));
   dim3 grid((pupil->n_pix + kTileX - 1) / kTileX, (pupil->n_pix + kTileY - 1) / kTileY);
   dim3 block(32, 8);
-  SPECULA_LAUNCH(ctx, SPECULA_K_ATMO, (cudaStream_t)stream,
-                 k_atmo_extract<<<grid, block, 0, (cudaStream_t)stream>>>(P, t_s, t_dev, phase_dev));
+  SPECULA_LAUNCH(ctx, SPECULA_K_ATMO, st,
+                 k_atmo_extract<<<grid, block, 0, st>>>(P, ctx->atmo_tab_i, ctx->atmo_tab_f,
+                                                        phase_dev));
   return SPECULA_OK;
 }

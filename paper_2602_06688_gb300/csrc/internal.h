@@ -73,9 +73,15 @@ struct ShPlan {
 
 }  // namespace specula
 
+// capacity of the per-context extraction coordinate table
+#define SPECULA_ATMO_MAX_LAYERS 64
+#define SPECULA_ATMO_MAX_PIX 8192
+
 struct specula_ctx {
   int device = 0;
   int32_t *status_dev = nullptr;
+  int *atmo_tab_i = nullptr;        // [64][2][8192] screen sample index
+  float *atmo_tab_f = nullptr;      // [64][2][8192] interpolation fraction
   std::vector<std::unique_ptr<specula::PwfsPlan>> pwfs;
   std::vector<std::unique_ptr<specula::ShPlan>> sh;
   // tracing: kernels launched, and optional per-kernel CUDA-event pairs
@@ -113,6 +119,7 @@ inline void prof_end(specula_ctx *c, int slot, int kid, cudaStream_t st) {
 // per-translation-unit device initialisation (constant tables)
 int pwfs_init_device();
 int sh_init_device();
+int atmo_alloc_tables(specula_ctx *ctx);
 
 // launchers implemented in the kernel translation units
 int pwfs_plan_build(specula_ctx *ctx, const specula_pupil_desc *pupil,

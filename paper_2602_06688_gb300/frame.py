@@ -93,6 +93,28 @@ class PwfsFrame:
         else:
             raise ValueError(precision)
 
+    def capture(self, stream):
+        """Record one frame into a CUDA graph on `stream` (a torch.cuda.Stream);
+        the graph reads the frame time from self.t_dev."""
+        from . import specula_graph_begin, specula_graph_end
+        torch = self.torch
+        self.t_dev = torch.zeros(1, dtype=torch.float64, device=self.R.device)
+        torch.cuda.synchronize()
+        specula_graph_begin(self.ctx, stream)
+        try:
+            self.frame(0.0, t_dev=self.t_dev, stream=stream)
+        finally:
+            self.graph = specula_graph_end(self.ctx, stream)
+        return self.graph
+
+    def replay(self, t, stream):
+        """Set the frame time and launch the captured frame on `stream`."""
+        torch = self.torch
+        with torch.cuda.stream(stream):
+            self.t_dev.fill_(t)
+        self.graph.launch(stream)
+        return self.modes
+
     def frame(self, t, t_dev=None, stream=None):
         """Enqueue one frame at time t (or *t_dev) on the current stream."""
         ctx = self.ctx

@@ -1,0 +1,73 @@
+"""GPU parity of a whole frame (extraction -> pyramid -> slopes -> MVM) against
+the oracle chain, and graph replay against eager launches."""
+import numpy as np
+import pytest
+
+import synth
+from gpu_common import load_pkg, need_gpu, norm_intensity_error
+from oracle import atmo, geometry, pyramid, recon, slopes
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = need_gpu()
+    sp = load_pkg()
+    ctx = sp.Context(0)
+    yield torch, sp, ctx
+    ctx.close()
+
+
+@pytest.mark.parametrize("name", ["pwfs8m_tiny", "pwfs8m"])
+def test_frame_vs_oracle_chain(env, name):
+    torch, sp, ctx = env
+    from paper_2602_06688_gb300.frame import PwfsFrame
+    wl = synth.workload(name)
+    fr = PwfsFrame(ctx, wl)
+    s = wl.sensors[0]
+    n, nsub = s.pupil.n_pix, s.pwfs.n_sub
+    t = 0.123
+    fr.frame(t)
+    torch.cuda.synchronize()
+    # oracle on the GPU's screens (float32 values; generator parity is tested
+    # separately) and the same stand-in reconstructor
+    scr = [x.cpu().numpy().astype(np.float64) for x in fr.screens]
+    phi = atmo.atmo_extract(scr, wl.layers, s.source, n, s.pupil.pitch_m, t)
+    ph_gpu = fr.phase.cpu().numpy().astype(np.float64)
+    assert np.max(np.abs(ph_gpu - phi)) <= 1e-5 * (1 + np.abs(phi).max())
+    amp = geometry.pupil_mask(n, s.pupil.obsc_frac).astype(np.float64)
+    valid = geometry.valid_subaps(amp.astype(np.uint8), nsub)
+    g = s.pwfs
+    det_ref = pyramid.pwfs_image(amp, phi, g.pad, g.n_mod, g.mod_amp, nsub, n)
+    flat = pyramid.pwfs_image(amp, np.zeros_like(phi), g.pad, g.n_mod, g.mod_amp, nsub, n)
+    det = fr.det.cpu().numpy().astype(np.float64)
+    assert norm_intensity_error(det, det_ref) <= 1e-5
+    s_ref = slopes.pyr_slopes(det_ref, nsub, valid, ref=slopes.pyr_slopes(flat, nsub, valid))
+    T = det_ref.sum() / len(valid)
+    tol = 2 * (5e-5 * det_ref.max() / T + 1e-5 * np.abs(s_ref).max())
+    sl = fr.slopes.cpu().numpy().astype(np.float64)
+    assert np.max(np.abs(sl - s_ref)) <= tol
+    R = fr.R.cpu().numpy().astype(np.float64)
+    m_ref = recon.mvm(R, sl)
+    mag = np.abs(R) @ np.abs(sl)
+    assert np.all(np.abs(fr.modes.cpu().numpy() - m_ref) <= 1e-5 * mag)
+
+
+def test_graph_replay_matches_eager(env):
+    torch, sp, ctx = env
+    from paper_2602_06688_gb300.frame import PwfsFrame
+    fr = PwfsFrame(ctx, synth.workload("pwfs8m_tiny"))
+    st = torch.cuda.Stream()
+    g = fr.capture(st)
+    assert g.kernel_count() >= 6
+    for t in (0.0, 0.017, 0.5):
+        fr.frame(t)
+        torch.cuda.synchronize()
+        eager = fr.modes.clone()
+        fr.modes.zero_()
+        torch.cuda.synchronize()
+        fr.replay(t, st)
+        torch.cuda.synchronize()
+        assert torch.equal(fr.modes, eager)
+    g.close()
