@@ -150,6 +150,7 @@ int specula_ctx_status(specula_ctx *ctx, int32_t *device_status);
 #define SPECULA_K_SH            6   /* Shack-Hartmann spots                       */
 #define SPECULA_K_PWFS_FIELD    7   /* pyramid: field E = amp exp(i phase)        */
 #define SPECULA_K_PWFS_BIN      8   /* pyramid: per-item bins -> detector         */
+#define SPECULA_K_CALIB         9   /* calibration kernels (IM, float64 algebra)  */
 #define SPECULA_K_COUNT         10
 
 /* Enable (capacity > 0: room for that many kernel records; allocates CUDA
@@ -336,6 +337,40 @@ int specula_recon(specula_ctx *ctx, const specula_recon_desc *rec,
 int specula_recon_convert(specula_ctx *ctx, int32_t n_modes, int32_t n_slopes,
                           const float *R_dev, int32_t precision, void *hi_dev,
                           void *lo_dev, void *stream);
+
+/* ---- calibration (set-up calls: may allocate, synchronise the stream) ------
+ * Modal basis (stands in for the non-public KL files of Listing 2,
+ * `ifunc_object`): Zernike modes in Noll order without piston, j = 2 ..
+ * n_modes + 1, sqrt(n+1) R_n^|m|(rho) (x sqrt 2 cos/sin |m| theta for m != 0,
+ * cos for even j), rho = |(x, y)| / (n_pix / 2) at centred pixel coordinates,
+ * theta = atan2(y, x), zero outside the pupil stop.  Evaluated in float64.
+ * basis_host: n_modes * n_pix^2 doubles; basis_dev: the same as float32. */
+int specula_modal_basis_host(const specula_pupil_desc *pupil, int32_t n_modes,
+                             double *basis_host);
+int specula_modal_basis(specula_ctx *ctx, const specula_pupil_desc *pupil, int32_t n_modes,
+                        float *basis_dev, void *stream);
+
+/* Push-pull interaction matrix (ImCalibrator + PushPullGenerator, App. A,
+ * Tab. 4): IM[s][j] = (S_s(+a Z_j) - S_s(-a Z_j)) / (2a), S the pyramid slopes
+ * (kind PYR, no reference) of the phase +-a Z_j, a = push_amp radians at the
+ * WFS wavelength.  basis_dev: n_modes * n_pix^2 floats; im_dev: n_slopes *
+ * n_modes doubles, row-major (n_slopes = 2 n_valid).  Requires a pyramid
+ * plan.  Allocates a 16-mode workspace for the call. */
+int specula_calib_intmat(specula_ctx *ctx, const specula_pupil_desc *pupil,
+                         const specula_pwfs_desc *pwfs, const float *amp_dev,
+                         const float *basis_dev, int32_t n_modes, double push_amp,
+                         const specula_slopec_desc *slopec, double *im_dev, void *stream);
+
+/* Truncated pseudo-inverse in float64 on the GPU (RecCalibrator, App. A,
+ * Tab. 4): A is m x n row-major (device doubles); R = V diag(1/lambda) V^T
+ * A^T with (lambda, V) the eigen-pairs of A^T A (parallel cyclic Jacobi) and
+ * eigenvalues <= rcond^2 lambda_max discarded — the Moore-Penrose inverse with
+ * singular values below rcond sigma_max dropped.  R_dev: n x m doubles;
+ * R32_dev (nullable): the same rounded to float32; *rank: kept count.
+ * n <= 8192, 0 < rcond < 1. */
+int specula_pinv_fp64(specula_ctx *ctx, const double *A_dev, int32_t m, int32_t n,
+                      double rcond, double *R_dev, float *R32_dev, int32_t *rank,
+                      void *stream);
 
 #ifdef __cplusplus
 }

@@ -119,10 +119,10 @@ def specula_ctx_status(ctx):
 
 
 (K_PWFS_ROWS_FWD, K_PWFS_COLS, K_PWFS_ROWS_INV, K_ATMO, K_SLOPES, K_RECON, K_SH,
- K_PWFS_FIELD, K_PWFS_BIN) = range(9)
+ K_PWFS_FIELD, K_PWFS_BIN, K_CALIB) = range(10)
 K_COUNT = 10
 KERNEL_NAMES = ["pwfs_rows_fwd", "pwfs_cols", "pwfs_rows_inv", "atmo_extract", "slopes",
-                "recon", "sh_spots", "pwfs_field", "pwfs_bin", "unused"]
+                "recon", "sh_spots", "pwfs_field", "pwfs_bin", "calib"]
 
 
 def specula_prof_enable(ctx, capacity):
@@ -372,6 +372,45 @@ def specula_recon_convert(ctx, R, precision, hi, lo=None, stream=None):
         ctx.handle, int(nm), int(ns), _dev(R, torch.float32, nm * ns, "R"), int(precision),
         _dev(hi, None, nm * ns, "hi"), _dev(lo, None, nm * ns, "lo"), _stream(stream)),
         "specula_recon_convert")
+
+
+def specula_modal_basis_host(pupil, n_modes):
+    out = np.zeros((n_modes, pupil.n_pix, pupil.n_pix))
+    _abi.check(lib().specula_modal_basis_host(C.byref(pupil), int(n_modes),
+                                              out.ctypes.data_as(C.c_void_p)),
+               "specula_modal_basis_host")
+    return out
+
+
+def specula_modal_basis(ctx, pupil, n_modes, basis, stream=None):
+    import torch
+    _abi.check(lib().specula_modal_basis(
+        ctx.handle, C.byref(pupil), int(n_modes),
+        _dev(basis, torch.float32, n_modes * pupil.n_pix ** 2, "basis"), _stream(stream)),
+        "specula_modal_basis")
+
+
+def specula_calib_intmat(ctx, pupil, pwfs, amp, basis, n_modes, push_amp, slopec, im,
+                         stream=None):
+    import torch
+    _abi.check(lib().specula_calib_intmat(
+        ctx.handle, C.byref(pupil), C.byref(pwfs), _dev(amp, torch.float32, pupil.n_pix ** 2, "amp"),
+        _dev(basis, torch.float32, n_modes * pupil.n_pix ** 2, "basis"), int(n_modes),
+        float(push_amp), C.byref(slopec),
+        _dev(im, torch.float64, 2 * slopec.n_valid * n_modes, "im"), _stream(stream)),
+        "specula_calib_intmat")
+
+
+def specula_pinv_fp64(ctx, A, rcond, R, R32=None, stream=None):
+    """A: (m, n) float64 CUDA tensor; R: (n, m) float64 output.  Returns rank."""
+    import torch
+    m, n = A.shape
+    rk = C.c_int32()
+    _abi.check(lib().specula_pinv_fp64(
+        ctx.handle, _dev(A, torch.float64, m * n, "A"), int(m), int(n), float(rcond),
+        _dev(R, torch.float64, m * n, "R"), _dev(R32, torch.float32, m * n, "R32"),
+        C.byref(rk), _stream(stream)), "specula_pinv_fp64")
+    return rk.value
 
 
 def slopec_desc(kind, n_sub, idx_dev, fft_n=0):

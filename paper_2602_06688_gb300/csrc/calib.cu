@@ -1,0 +1,408 @@
+// Calibration: modal basis, push-pull interaction matrix, FP64 pseudo-inverse.
+//
+// ImCalibrator / RecCalibrator / PushPullGenerator (App. A, Tab. 4) and the
+// Intmat / Recmat data objects (Tab. 3); the modal basis stands in for the KL
+// files of App. B, Listing 2, which are not public.
+//
+//  * basis: Zernike modes in Noll order without piston (j = 2 .. n_modes+1),
+//    unit RMS on the unit disk, sampled at pupil pixel centres, zero outside
+//    the stop; evaluated on the host in float64, stored as float32.
+//  * IM[:, j] = (s(+a Z_j) - s(-a Z_j)) / (2 a): batches of 16 modes, 32 phase
+//    maps, run through the pyramid and slope kernels; columns formed in
+//    float64 from the float32 slopes.
+//  * R = pinv(A) with eigenvalues of A^T A below rcond^2 lambda_max discarded
+//    (singular values below rcond sigma_max): Gram matrix by a float64 GEMM,
+//    eigen-decomposition by parallel cyclic Jacobi (round-robin pairs, one
+//    rotation per disjoint pair per round), R = V diag(1/lambda) V^T A^T.
+//    Float64 throughout, on the GPU (a set-up cost).
+#include <math.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "internal.h"
+
+namespace specula {
+
+// ---------------------------------------------------------------- basis (host)
+
+static void noll_nm(int j, int *n_out, int *m_out) {
+  int n = 0;
+  while ((n + 1) * (n + 2) / 2 < j) ++n;
+  const int k = j - n * (n + 1) / 2 - 1;
+  const int mabs = (n % 2 == 0) ? 2 * ((k + 1) / 2) : 2 * (k / 2) + 1;
+  *n_out = n;
+  *m_out = (mabs == 0 || j % 2 == 0) ? mabs : -mabs;
+}
+
+static double factorial(int k) {
+  double f = 1.0;
+  for (int i = 2; i <= k; ++i) f *= (double)i;
+  return f;
+}
+
+static double zernike_value(int j, double rho, double theta) {
+  int n, m;
+  noll_nm(j, &n, &m);
+  const int ma = m < 0 ? -m : m;
+  double r = 0.0;
+  for (int s = 0; s <= (n - ma) / 2; ++s) {
+    const double c = ((s % 2) ? -1.0 : 1.0) * factorial(n - s) /
+                     (factorial(s) * factorial((n + ma) / 2 - s) * factorial((n - ma) / 2 - s));
+    r += c * pow(rho, n - 2 * s);
+  }
+  if (m == 0) return sqrt((double)(n + 1)) * r;
+  const double ang = m > 0 ? cos(ma * theta) : sin(ma * theta);
+  return sqrt(2.0 * (n + 1)) * r * ang;
+}
+
+int modal_basis_host(int n_pix, double obsc, int n_modes, double *out) {
+  std::vector<uint8_t> mask((size_t)n_pix * n_pix);
+  host_pupil_mask(n_pix, obsc, mask.data());
+  const double half = n_pix / 2.0, c0 = (n_pix - 1) / 2.0;
+  for (int q = 0; q < n_modes; ++q) {
+    const int j = q + 2;
+    for (int y = 0; y < n_pix; ++y)
+      for (int x = 0; x < n_pix; ++x) {
+        const size_t p = (size_t)y * n_pix + x;
+        double v = 0.0;
+        if (mask[p]) {
+          const double dx = x - c0, dy = y - c0;
+          v = zernike_value(j, sqrt(dx * dx + dy * dy) / half, atan2(dy, dx));
+        }
+        out[(size_t)q * n_pix * n_pix + p] = v;
+      }
+  }
+  return SPECULA_OK;
+}
+
+// ---------------------------------------------------------------- push-pull IM
+
+__global__ void k_pushpull(const float *__restrict__ basis, int npix2, int j0, int nq, float a,
+                           float *__restrict__ phase) {
+  const size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (e >= (size_t)npix2 * nq) return;
+  const int q = (int)(e / npix2);
+  const size_t p = e % npix2;
+  const float z = basis[(size_t)(j0 + q) * npix2 + p];
+  phase[(size_t)(2 * q) * npix2 + p] = a * z;
+  phase[(size_t)(2 * q + 1) * npix2 + p] = -a * z;
+}
+
+__global__ void k_im_cols(const float *__restrict__ sl, int n_slopes, int n_modes, int j0, int nq,
+                          double a, double *__restrict__ im) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n_slopes * nq) return;
+  const int q = e / n_slopes, s = e % n_slopes;
+  const double d = (double)sl[(size_t)(2 * q) * n_slopes + s] -
+                   (double)sl[(size_t)(2 * q + 1) * n_slopes + s];
+  im[(size_t)s * n_modes + j0 + q] = d / (2.0 * a);
+}
+
+// ---------------------------------------------------------------- float64 GEMM
+// C[i][j] = sum_k X(i,k) d(k) Y(k,j), X(i,k) = X[i xi + k xk], Y(k,j) = Y[k yk + j yj]
+constexpr int GT = 64, GK = 16;
+
+__global__ void __launch_bounds__(256) k_gemm_f64(const double *__restrict__ X, long xi, long xk,
+                                                  const double *__restrict__ Y, long yk, long yj,
+                                                  const double *__restrict__ d, double *__restrict__ C,
+                                                  int M, int N, int K) {
+  __shared__ double Xs[GK][GT + 1], Ys[GK][GT + 1];
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  const int i0 = blockIdx.y * GT, j0 = blockIdx.x * GT;
+  double acc[4][4] = {};
+  for (int k0 = 0; k0 < K; k0 += GK) {
+    for (int e = threadIdx.x; e < GK * GT; e += 256) {
+      const int kk = e / GT, ii = e % GT;
+      const int k = k0 + kk;
+      const int i = i0 + ii, j = j0 + ii;
+      double xv = 0.0, yv = 0.0;
+      if (k < K && i < M) xv = X[i * xi + k * xk] * (d ? d[k] : 1.0);
+      if (k < K && j < N) yv = Y[k * yk + j * yj];
+      Xs[kk][ii] = xv;
+      Ys[kk][ii] = yv;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < GK; ++kk) {
+      double xr[4], yr[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        xr[u] = Xs[kk][ty + 16 * u];
+        yr[u] = Ys[kk][tx + 16 * u];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = fma(xr[u], yr[v], acc[u][v]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int i = i0 + ty + 16 * u, j = j0 + tx + 16 * v;
+      if (i < M && j < N) C[(size_t)i * N + j] = acc[u][v];
+    }
+}
+
+static int gemm_f64(specula_ctx *ctx, cudaStream_t st, const double *X, long xi, long xk,
+                    const double *Y, long yk, long yj, const double *d, double *C, int M, int N,
+                    int K) {
+  dim3 grid((N + GT - 1) / GT, (M + GT - 1) / GT);
+  SPECULA_LAUNCH(ctx, SPECULA_K_CALIB, st,
+                 k_gemm_f64<<<grid, 256, 0, st>>>(X, xi, xk, Y, yk, yj, d, C, M, N, K));
+  return SPECULA_OK;
+}
+
+// ---------------------------------------------------------------- Jacobi
+// Round r of the circle method on np (even) slots: slot 0 holds index 0, slot
+// k >= 1 holds ((k - 1 + r) mod (np - 1)) + 1; pair i = (slot i, slot np-1-i).
+__device__ __forceinline__ int rr_index(int slot, int r, int np) {
+  return slot == 0 ? 0 : ((slot - 1 + r) % (np - 1)) + 1;
+}
+
+__global__ void k_jacobi_params(const double *__restrict__ G, int n, int np, int r,
+                                int2 *__restrict__ pq, double2 *__restrict__ cs) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= np / 2) return;
+  int p = rr_index(i, r, np), q = rr_index(np - 1 - i, r, np);
+  if (p > q) { const int t = p; p = q; q = t; }
+  double c = 1.0, s = 0.0;
+  if (q < n) {
+    const double apq = G[(size_t)p * n + q];
+    if (apq != 0.0) {
+      const double app = G[(size_t)p * n + p], aqq = G[(size_t)q * n + q];
+      const double th = (aqq - app) / (2.0 * apq);
+      const double t = (th >= 0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+      c = 1.0 / sqrt(t * t + 1.0);
+      s = t * c;
+    }
+  } else {
+    q = p;   // dummy partner (odd n): identity
+  }
+  pq[i] = make_int2(p, q);
+  cs[i] = make_double2(c, s);
+}
+
+// G <- J^T G: rows p, q of each pair
+__global__ void k_jacobi_rows(double *__restrict__ G, int n, const int2 *__restrict__ pq,
+                              const double2 *__restrict__ cs) {
+  const int i = blockIdx.y;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int2 e = pq[i];
+  if (j >= n || e.x == e.y) return;
+  const double2 r = cs[i];
+  const double gp = G[(size_t)e.x * n + j], gq = G[(size_t)e.y * n + j];
+  G[(size_t)e.x * n + j] = r.x * gp - r.y * gq;
+  G[(size_t)e.y * n + j] = r.y * gp + r.x * gq;
+}
+
+// G <- G J and V <- V J: columns p, q of each pair
+__global__ void k_jacobi_cols(double *__restrict__ G, double *__restrict__ V, int n,
+                              const int2 *__restrict__ pq, const double2 *__restrict__ cs) {
+  const int i = blockIdx.y;
+  const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  const int2 e = pq[i];
+  if (row >= n || e.x == e.y) return;
+  const double2 r = cs[i];
+  double *g = G + (size_t)row * n;
+  double gp = g[e.x], gq = g[e.y];
+  g[e.x] = r.x * gp - r.y * gq;
+  g[e.y] = r.y * gp + r.x * gq;
+  double *v = V + (size_t)row * n;
+  gp = v[e.x];
+  gq = v[e.y];
+  v[e.x] = r.x * gp - r.y * gq;
+  v[e.y] = r.y * gp + r.x * gq;
+}
+
+// off-diagonal and total squared norms (one CTA, fixed order)
+__global__ void k_offnorm(const double *__restrict__ G, int n, double *__restrict__ out) {
+  __shared__ double so[256], st[256];
+  double o = 0.0, t = 0.0;
+  for (size_t e = threadIdx.x; e < (size_t)n * n; e += blockDim.x) {
+    const double v = G[e];
+    const size_t r = e / n, c = e % n;
+    t += v * v;
+    if (r != c) o += v * v;
+  }
+  so[threadIdx.x] = o;
+  st[threadIdx.x] = t;
+  __syncthreads();
+  for (int h = 128; h > 0; h >>= 1) {
+    if ((int)threadIdx.x < h) {
+      so[threadIdx.x] += so[threadIdx.x + h];
+      st[threadIdx.x] += st[threadIdx.x + h];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    out[0] = so[0];
+    out[1] = st[0];
+  }
+}
+
+__global__ void k_identity(double *__restrict__ V, int n) {
+  const size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (e < (size_t)n * n) V[e] = (e / n == e % n) ? 1.0 : 0.0;
+}
+
+// d[k] = 1/lambda_k for kept eigenvalues, else 0; count in rank
+__global__ void k_inv_eigs(const double *__restrict__ G, int n, double rcond,
+                           double *__restrict__ d, int *__restrict__ rank) {
+  __shared__ double s_max;
+  if (threadIdx.x == 0) {
+    double mx = 0.0;
+    for (int k = 0; k < n; ++k) mx = fmax(mx, G[(size_t)k * n + k]);
+    s_max = mx;
+    *rank = 0;
+  }
+  __syncthreads();
+  const double thr = rcond * rcond * s_max;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    const double l = G[(size_t)k * n + k];
+    const bool keep = l > thr && l > 0.0;
+    d[k] = keep ? 1.0 / l : 0.0;
+    if (keep) atomicAdd(rank, 1);
+  }
+}
+
+__global__ void k_f64_to_f32(const double *__restrict__ a, float *__restrict__ b, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x)
+    b[i] = (float)a[i];
+}
+
+}  // namespace specula
+
+using namespace specula;
+
+extern "C" int specula_modal_basis_host(const specula_pupil_desc *pupil, int32_t n_modes,
+                                        double *basis_host) {
+  if (!pupil || !basis_host || n_modes < 1 || n_modes > 20000) return SPECULA_EINVAL;
+  if (pupil->n_pix < 2 || pupil->n_pix > 8192 || !(pupil->obsc_frac >= 0 && pupil->obsc_frac < 1))
+    return SPECULA_EINVAL;
+  return modal_basis_host(pupil->n_pix, pupil->obsc_frac, n_modes, basis_host);
+}
+
+extern "C" int specula_modal_basis(specula_ctx *ctx, const specula_pupil_desc *pupil,
+                                   int32_t n_modes, float *basis_dev, void *stream) {
+  if (!ctx || !basis_dev) return SPECULA_EINVAL;
+  if (!pupil || n_modes < 1 || n_modes > 20000 || pupil->n_pix < 2 || pupil->n_pix > 8192)
+    return SPECULA_EINVAL;
+  const size_t np2 = (size_t)pupil->n_pix * pupil->n_pix;
+  std::vector<double> h(np2 * n_modes);
+  int s = modal_basis_host(pupil->n_pix, pupil->obsc_frac, n_modes, h.data());
+  if (s) return s;
+  std::vector<float> f(h.size());
+  for (size_t i = 0; i < h.size(); ++i) f[i] = (float)h[i];
+  SPECULA_CK(cudaSetDevice(ctx->device));
+  SPECULA_CK(cudaMemcpyAsync(basis_dev, f.data(), f.size() * sizeof(float),
+                             cudaMemcpyHostToDevice, (cudaStream_t)stream));
+  SPECULA_CK(cudaStreamSynchronize((cudaStream_t)stream));
+  return SPECULA_OK;
+}
+
+extern "C" int specula_calib_intmat(specula_ctx *ctx, const specula_pupil_desc *pupil,
+                                    const specula_pwfs_desc *pwfs, const float *amp_dev,
+                                    const float *basis_dev, int32_t n_modes, double push_amp,
+                                    const specula_slopec_desc *slopec, double *im_dev,
+                                    void *stream) {
+  if (!ctx || !pupil || !pwfs || !amp_dev || !basis_dev || !slopec || !im_dev) return SPECULA_EINVAL;
+  if (n_modes < 1 || !(push_amp > 0) || !isfinite(push_amp)) return SPECULA_EINVAL;
+  if (slopec->kind != SPECULA_SLOPES_PYR || !slopec->subap_idx_dev || slopec->n_valid < 1)
+    return SPECULA_EINVAL;
+  PwfsPlan *p = pwfs_plan_find(ctx, pupil, pwfs);
+  if (!p) return SPECULA_ENOPLAN;
+  if (slopec->n_sub != pwfs->n_sub) return SPECULA_EINVAL;
+  SPECULA_CK(cudaSetDevice(ctx->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  const int MB = 16;
+  const int npix2 = pupil->n_pix * pupil->n_pix;
+  const int nd = 2 * pwfs->n_sub;
+  const int ns = 2 * slopec->n_valid;
+  DevBuf ph, det, sl;
+  int s;
+  if ((s = ph.alloc((size_t)2 * MB * npix2 * sizeof(float)))) return s;
+  if ((s = det.alloc((size_t)2 * MB * nd * nd * sizeof(float)))) return s;
+  if ((s = sl.alloc((size_t)2 * MB * ns * sizeof(float)))) return s;
+  for (int j0 = 0; j0 < n_modes; j0 += MB) {
+    const int nq = std::min(MB, n_modes - j0);
+    const size_t tot = (size_t)npix2 * nq;
+    SPECULA_LAUNCH(ctx, SPECULA_K_CALIB, st,
+                   k_pushpull<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(
+                       basis_dev, npix2, j0, nq, (float)push_amp, ph.as<float>()));
+    if ((s = pwfs_run(ctx, p, amp_dev, ph.as<float>(), 2 * nq, det.as<float>(), st))) return s;
+    if ((s = slopes_pyr_run(ctx, slopec->subap_idx_dev, slopec->n_sub, slopec->n_valid,
+                            det.as<float>(), nullptr, 2 * nq, sl.as<float>(), st)))
+      return s;
+    SPECULA_LAUNCH(ctx, SPECULA_K_CALIB, st,
+                   k_im_cols<<<(ns * nq + 255) / 256, 256, 0, st>>>(sl.as<float>(), ns, n_modes,
+                                                                      j0, nq, push_amp, im_dev));
+  }
+  SPECULA_CK(cudaStreamSynchronize(st));   // the workspace is freed on return
+  return SPECULA_OK;
+}
+
+extern "C" int specula_pinv_fp64(specula_ctx *ctx, const double *A_dev, int32_t m, int32_t n,
+                                 double rcond, double *R_dev, float *R32_dev, int32_t *rank,
+                                 void *stream) {
+  if (!ctx || !A_dev || !R_dev || !rank) return SPECULA_EINVAL;
+  if (m < 1 || n < 1 || n > 8192 || !(rcond > 0) || !(rcond < 1)) return SPECULA_EINVAL;
+  SPECULA_CK(cudaSetDevice(ctx->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  DevBuf G, V, D, PQ, CS, NRM, RK;
+  const int np = n + (n & 1);
+  int s;
+  if ((s = G.alloc((size_t)n * n * sizeof(double)))) return s;
+  if ((s = V.alloc((size_t)n * n * sizeof(double)))) return s;
+  if ((s = D.alloc((size_t)n * sizeof(double)))) return s;
+  if ((s = PQ.alloc((size_t)np / 2 * sizeof(int2)))) return s;
+  if ((s = CS.alloc((size_t)np / 2 * sizeof(double2)))) return s;
+  if ((s = NRM.alloc(2 * sizeof(double)))) return s;
+  if ((s = RK.alloc(sizeof(int)))) return s;
+  // G = A^T A
+  if ((s = gemm_f64(ctx, st, A_dev, 1, n, A_dev, n, 1, nullptr, G.as<double>(), n, n, m))) return s;
+  SPECULA_LAUNCH(ctx, SPECULA_K_CALIB, st,
+                 k_identity<<<(unsigned)(((size_t)n * n + 255) / 256), 256, 0, st>>>(V.as<double>(), n));
+  const int npairs = np / 2;
+  const dim3 gr((n + 255) / 256, npairs);
+  for (int sweep = 0; sweep < 40; ++sweep) {
+    for (int r = 0; r < np - 1; ++r) {
+      SPECULA_LAUNCH(ctx, SPECULA_K_CALIB, st,
+                     k_jacobi_params<<<(npairs + 127) / 128, 128, 0, st>>>(
+                         G.as<double>(), n, np, r, PQ.as<int2>(), CS.as<double2>()));
+      SPECULA_LAUNCH(ctx, SPECULA_K_CALIB, st,
+                     k_jacobi_rows<<<gr, 256, 0, st>>>(G.as<double>(), n, PQ.as<int2>(),
+                                                       CS.as<double2>()));
+      SPECULA_LAUNCH(ctx, SPECULA_K_CALIB, st,
+                     k_jacobi_cols<<<gr, 256, 0, st>>>(G.as<double>(), V.as<double>(), n,
+                                                       PQ.as<int2>(), CS.as<double2>()));
+    }
+    SPECULA_LAUNCH(ctx, SPECULA_K_CALIB, st,
+                   k_offnorm<<<1, 256, 0, st>>>(G.as<double>(), n, NRM.as<double>()));
+    double h[2];
+    SPECULA_CK(cudaMemcpyAsync(h, NRM.p, sizeof(h), cudaMemcpyDeviceToHost, st));
+    SPECULA_CK(cudaStreamSynchronize(st));
+    if (!(h[0] > 1e-30 * h[1])) break;
+  }
+  SPECULA_LAUNCH(ctx, SPECULA_K_CALIB, st,
+                 k_inv_eigs<<<1, 256, 0, st>>>(G.as<double>(), n, rcond, D.as<double>(),
+                                               RK.as<int>()));
+  // W = V diag(d) V^T into G's storage, then R = W A^T
+  if ((s = gemm_f64(ctx, st, V.as<double>(), n, 1, V.as<double>(), 1, n, D.as<double>(),
+                    G.as<double>(), n, n, n)))
+    return s;
+  if ((s = gemm_f64(ctx, st, G.as<double>(), n, 1, A_dev, 1, n, nullptr, R_dev, n, m, n))) return s;
+  if (R32_dev) {
+    SPECULA_LAUNCH(ctx, SPECULA_K_CALIB, st,
+                   k_f64_to_f32<<<1216, 256, 0, st>>>(R_dev, R32_dev, (size_t)n * m));
+  }
+  int hr = 0;
+  SPECULA_CK(cudaMemcpyAsync(&hr, RK.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+  SPECULA_CK(cudaStreamSynchronize(st));
+  *rank = hr;
+  return SPECULA_OK;
+}

@@ -139,6 +139,9 @@ ShPlan *sh_plan_find(specula_ctx *ctx, const specula_pupil_desc *pupil,
 int sh_run(specula_ctx *ctx, ShPlan *plan, const float *amp, const float *phase,
            int n_batch, float *spots, cudaStream_t st);
 
+int slopes_pyr_run(specula_ctx *ctx, const int32_t *idx, int n_sub, int n_valid,
+                   const float *det, const float *ref, int n_batch, float *out, cudaStream_t st);
+
 // host geometry (api.cu)
 int host_pupil_mask(int n, double obsc, uint8_t *mask);
 int host_valid_subaps(int n, double obsc, int n_sub, int32_t *idx, int32_t *n_valid);

@@ -104,6 +104,14 @@ __global__ void __launch_bounds__(256) k_sh_cog(const float *__restrict__ spots,
   }
 }
 
+int slopes_pyr_run(specula_ctx *ctx, const int32_t *idx, int n_sub, int n_valid,
+                   const float *det, const float *ref, int n_batch, float *out, cudaStream_t st) {
+  SPECULA_LAUNCH(ctx, SPECULA_K_SLOPES, st,
+                 k_pyr_slopes<<<n_batch, kPyrThreads, 0, st>>>(det, idx, ref, n_sub, n_valid, out,
+                                                               ctx->status_dev));
+  return SPECULA_OK;
+}
+
 }  // namespace specula
 
 using namespace specula;
@@ -117,10 +125,8 @@ extern "C" int specula_slopes(specula_ctx *ctx, const specula_slopec_desc *d, co
   cudaStream_t st = (cudaStream_t)stream;
   if (d->kind == SPECULA_SLOPES_PYR) {
     if (!d->subap_idx_dev || d->n_valid > d->n_sub * d->n_sub) return SPECULA_EINVAL;
-    SPECULA_LAUNCH(ctx, SPECULA_K_SLOPES, st,
-                   k_pyr_slopes<<<n_batch, kPyrThreads, 0, st>>>(img_dev, d->subap_idx_dev, ref_dev,
-                                                                 d->n_sub, d->n_valid, slopes_dev,
-                                                                 ctx->status_dev));
+    return slopes_pyr_run(ctx, d->subap_idx_dev, d->n_sub, d->n_valid, img_dev, ref_dev, n_batch,
+                          slopes_dev, st);
   } else if (d->kind == SPECULA_SLOPES_SH) {
     if (d->fft_n < 2) return SPECULA_EINVAL;
     const long long tasks = (long long)d->n_valid * n_batch;

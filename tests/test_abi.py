@@ -72,6 +72,16 @@ def test_mod_table_bit_exact(sp, n_mod):
     assert np.array_equal(c.astype(np.float32), rc.astype(np.float32))
 
 
+@pytest.mark.parametrize("n,obsc,nm", [(32, 0.0, 20), (64, 0.11, 200)])
+def test_host_modal_basis_matches_oracle(sp, n, obsc, nm):
+    from oracle import modal
+    got = sp.specula_modal_basis_host(sp.PupilDesc(n, 0.1, obsc), nm)
+    ref = modal.modal_basis(n, obsc, nm)
+    # float64 on both sides; high radial orders lose a few digits to the
+    # alternating factorial sums
+    assert np.max(np.abs(got - ref)) <= 1e-8 * np.abs(ref).max()
+
+
 def test_host_validation_returns_codes(sp):
     lib = sp.lib()
     bad = sp.PupilDesc(0, 0.1, 0.0)
