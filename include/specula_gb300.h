@@ -249,6 +249,25 @@ int specula_atmo_extract(specula_ctx *ctx, int32_t n_layers,
                          const specula_pupil_desc *pupil, double t_s,
                          const double *t_dev, float *phase_dev, void *stream);
 
+/* Allocation-free layer extraction (the paper has no counterpart: this is a
+ * library convenience).  Computes exactly what specula_atmo_extract computes,
+ * without a context, for callers that cannot call cudaMalloc — a host that
+ * only enqueues work into its own CUDA graphs, a real-time loop that forbids
+ * allocation after start-up, an embedding that owns all device memory.
+ * The coordinate table lives in a fixed device array of 8 MiB (64 layers x 2
+ * axes x 8192 pixels of int32 index + float32 fraction) that every GPU which
+ * loads the library holds until the process exits; n_layers > 64 or
+ * n_pix > 8192 returns SPECULA_EUNSUPPORTED.  Runs on the calling thread's
+ * current device.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress): make that call before any stream capture.
+ * All calls share the array, so calls whose kernels overlap on the GPU race
+ * and must be ordered by the caller.  Allocates nothing. */
+int specula_atmo_extract_noalloc(int32_t n_layers, const specula_layer_desc *layers,
+                                 const float *const *screens_dev,
+                                 const specula_source_desc *source,
+                                 const specula_pupil_desc *pupil, double t_s,
+                                 const double *t_dev, float *phase_dev, void *stream);
+
 /* Build (or reuse) the tables and workspace of a pyramid geometry: modulation
  * tilt tables, pyramid-mask tables and FFT twiddles, computed in float64 on
  * the host and rounded once to float32.  May allocate.  Supported FFT sides

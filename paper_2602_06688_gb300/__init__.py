@@ -281,6 +281,25 @@ def specula_atmo_extract(ctx, layers, screens, source, pupil, t, phase, t_dev=No
         "specula_atmo_extract")
 
 
+def specula_atmo_extract_noalloc(layers, screens, source, pupil, t, phase, t_dev=None,
+                                 stream=None):
+    """Context-free extraction for callers that cannot allocate device memory
+    (see the header): same result as specula_atmo_extract."""
+    import torch
+    n = len(layers)
+    if len(screens) != n:
+        raise ValueError("one screen per layer")
+    L = (LayerDesc * n)(*layers)
+    ptrs = (C.c_void_p * n)(*[C.c_void_p(s.data_ptr()) for s in screens])
+    for s, l in zip(screens, layers):
+        _dev(s, torch.float32, l.side * l.side, "screen")
+    _abi.check(lib().specula_atmo_extract_noalloc(
+        n, L, ptrs, C.byref(source), C.byref(pupil), float(t),
+        _dev(t_dev, torch.float64, 1, "t_dev"),
+        _dev(phase, torch.float32, pupil.n_pix ** 2, "phase"), _stream(stream)),
+        "specula_atmo_extract_noalloc")
+
+
 def specula_pwfs_plan(ctx, pupil, pwfs):
     _abi.check(lib().specula_pwfs_plan(ctx.handle, C.byref(pupil), C.byref(pwfs)),
                "specula_pwfs_plan")

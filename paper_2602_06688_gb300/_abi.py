@@ -81,6 +81,8 @@ SIGNATURES = {
     "specula_screen_generate": (C.c_int, [vp, i32, dbl, dbl, dbl, vp, vp, vp, vp]),
     "specula_atmo_extract": (C.c_int, [vp, i32, P(LayerDesc), P(vp), P(SourceDesc),
                                        P(PupilDesc), dbl, vp, vp, vp]),
+    "specula_atmo_extract_noalloc": (C.c_int, [i32, P(LayerDesc), P(vp), P(SourceDesc),
+                                               P(PupilDesc), dbl, vp, vp, vp]),
     "specula_pwfs_plan": (C.c_int, [vp, P(PupilDesc), P(PwfsDesc)]),
     "specula_pwfs_set_tiles": (C.c_int, [vp, P(PupilDesc), P(PwfsDesc), i32, i32]),
     "specula_pwfs_get_tiles": (C.c_int, [vp, P(PupilDesc), P(PwfsDesc), P(i32), P(i32)]),

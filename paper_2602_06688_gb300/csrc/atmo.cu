@@ -18,6 +18,8 @@
 // time.  A warp reads 32 consecutive columns of one screen row: coalesced.
 #include <math.h>
 
+#include <mutex>
+
 #include "internal.h"
 
 namespace specula {
@@ -166,5 +168,102 @@ extern "C" int specula_atmo_extract(specula_ctx *ctx, int32_t n_layers,
   SPECULA_LAUNCH(ctx, SPECULA_K_ATMO, st,
                  k_atmo_extract<<<grid, block, 0, st>>>(P, ctx->atmo_tab_i, ctx->atmo_tab_f,
                                                         phase_dev));
+  return SPECULA_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of specula_atmo_extract.
+//
+// Some callers cannot call cudaMalloc: a host that runs its own CUDA graphs
+// and may only enqueue work, a real-time loop with a fixed memory budget
+// that forbids allocations after start-up, or an embedding that hands out
+// every byte of device memory itself.  specula_atmo_extract needs the
+// coordinate table that specula_ctx_create allocates; this variant keeps the
+// table in a fixed device array instead, so it needs no context and
+// allocates nothing.
+//
+// The array holds [64 layers][2 axes][8192 pixels] int32 sample indices
+// followed by the same number of float32 fractions: 8 MiB, which every GPU
+// that loads this library keeps until the process exits.  Every call shares
+// it: calls whose kernels overlap on the GPU (different streams, or
+// different threads) race on it and must be ordered by the caller.  Each
+// call overwrites every entry it reads, so nothing needs clearing.
+//
+// The array's device address is looked up once per device, with that device
+// current, by the first call made on it (cudaGetSymbolAddress; in host code
+// the array's name is only a host-side stand-in).  Make that first call
+// before any stream capture on the device.
+namespace {
+
+constexpr int kNoAllocEntries = SPECULA_ATMO_MAX_LAYERS * 2 * SPECULA_ATMO_MAX_PIX;
+static __device__ __align__(256) int32_t g_atmo_noalloc_scratch[2 * kNoAllocEntries];
+
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void *g_noalloc_addr[kNoAllocMaxDevices] = {};
+
+int noalloc_scratch(int dev, void **out) {
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return SPECULA_EUNSUPPORTED;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_atmo_noalloc_scratch) != cudaSuccess || !p)
+      return SPECULA_ECUDA;
+    g_noalloc_addr[dev] = p;
+  }
+  *out = g_noalloc_addr[dev];
+  return SPECULA_OK;
+}
+
+}  // namespace
+
+extern "C" int specula_atmo_extract_noalloc(int32_t n_layers, const specula_layer_desc *layers,
+                                            const float *const *screens_dev,
+                                            const specula_source_desc *src,
+                                            const specula_pupil_desc *pupil, double t_s,
+                                            const double *t_dev, float *phase_dev,
+                                            void *stream) {
+  if (!layers || !screens_dev || !src || !pupil || !phase_dev) return SPECULA_EINVAL;
+  if (n_layers < 1) return SPECULA_EINVAL;
+  if (n_layers > kMaxLayers) return SPECULA_EUNSUPPORTED;   // beyond the fixed array
+  if (pupil->n_pix < 1 || !(pupil->pitch_m > 0)) return SPECULA_EINVAL;
+  if (pupil->n_pix > kMaxPix) return SPECULA_EUNSUPPORTED;  // beyond the fixed array
+  if (!(src->wavelength_nm > 0) || !(src->height_m > 0)) return SPECULA_EINVAL;
+  if (!t_dev && !isfinite(t_s)) return SPECULA_EINVAL;
+  AtmoParams P;
+  P.n_layers = n_layers;
+  P.n_pix = pupil->n_pix;
+  P.pupil_pitch = pupil->pitch_m;
+  P.theta_x = src->theta_x_rad;
+  P.theta_y = src->theta_y_rad;
+  P.H = src->height_m;
+  P.scale = (float)(500.0 / src->wavelength_nm);
+  for (int l = 0; l < n_layers; ++l) {
+    const specula_layer_desc &L = layers[l];
+    if (!screens_dev[l] || L.side < 2 || !(L.pitch_m > 0) || !isfinite(L.height_m) ||
+        L.height_m < 0 || !isfinite(L.vx_mps) || !isfinite(L.vy_mps))
+      return SPECULA_EINVAL;
+    if (isfinite(src->height_m) && L.height_m >= src->height_m) return SPECULA_EINVAL;
+    P.scr[l] = screens_dev[l];
+    P.side[l] = L.side;
+    P.pitch[l] = L.pitch_m;
+    P.h[l] = L.height_m;
+    P.vx[l] = L.vx_mps;
+    P.vy[l] = L.vy_mps;
+  }
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return SPECULA_ECUDA;
+  void *base = nullptr;
+  int s = noalloc_scratch(dev, &base);
+  if (s) return s;
+  int *tab_i = static_cast<int *>(base);
+  float *tab_f = reinterpret_cast<float *>(tab_i + kNoAllocEntries);
+  cudaStream_t st = (cudaStream_t)stream;
+  const int nc = n_layers * 2 * pupil->n_pix;
+  k_atmo_coords<<<(nc + 255) / 256, 256, 0, st>>>(P, t_s, t_dev, tab_i, tab_f);
+  if (cudaGetLastError() != cudaSuccess) return SPECULA_ECUDA;
+  dim3 grid((pupil->n_pix + kTileX - 1) / kTileX, (pupil->n_pix + kTileY - 1) / kTileY);
+  k_atmo_extract<<<grid, dim3(32, 8), 0, st>>>(P, tab_i, tab_f, phase_dev);
+  if (cudaGetLastError() != cudaSuccess) return SPECULA_ECUDA;
   return SPECULA_OK;
 }
