@@ -151,7 +151,9 @@ int specula_ctx_status(specula_ctx *ctx, int32_t *device_status);
 #define SPECULA_K_PWFS_FIELD    7   /* pyramid: field E = amp exp(i phase)        */
 #define SPECULA_K_PWFS_BIN      8   /* pyramid: per-item bins -> detector         */
 #define SPECULA_K_CALIB         9   /* calibration kernels (IM, float64 algebra)  */
-#define SPECULA_K_COUNT         10
+#define SPECULA_K_GEMM          10  /* tcgen05 BF16 GEMM and split-K reduction    */
+#define SPECULA_K_MLP           11  /* learned-reconstructor element-wise kernels */
+#define SPECULA_K_COUNT         12
 
 /* Enable (capacity > 0: room for that many kernel records; allocates CUDA
  * events; set-up call) or disable (capacity = 0) per-kernel event timing.
@@ -356,6 +358,19 @@ int specula_recon(specula_ctx *ctx, const specula_recon_desc *rec,
 int specula_recon_convert(specula_ctx *ctx, int32_t n_modes, int32_t n_slopes,
                           const float *R_dev, int32_t precision, void *hi_dev,
                           void *lo_dev, void *stream);
+
+/* ---- tensor-core GEMM ---------------------------------------------------------
+ * C[M][N] = A[M][K] . B[N][K]^T with A, B bfloat16 row-major (both K-major),
+ * accumulated in float32 on the tcgen05 tensor cores; C float32 row-major.
+ * The dense contractions of the learned reconstructor use it (BASELINE's
+ * learned part; the paper's Modalrec is the MVM above).  M and N multiples
+ * of 128, K a multiple of 64, A and B 16-byte aligned.  splits > 1 divides K
+ * into slices computed by separate CTAs whose float32 partials go to work_dev
+ * (splits * M * N floats, caller-owned) and are summed in slice order.
+ * Per-frame call: enqueues only. */
+int specula_gemm_bf16(specula_ctx *ctx, const void *A_dev, const void *B_dev, int32_t M,
+                      int32_t N, int32_t K, float *C_dev, int32_t splits, float *work_dev,
+                      void *stream);
 
 /* ---- calibration (set-up calls: may allocate, synchronise the stream) ------
  * Modal basis (stands in for the non-public KL files of Listing 2,

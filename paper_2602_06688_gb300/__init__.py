@@ -119,10 +119,10 @@ def specula_ctx_status(ctx):
 
 
 (K_PWFS_ROWS_FWD, K_PWFS_COLS, K_PWFS_ROWS_INV, K_ATMO, K_SLOPES, K_RECON, K_SH,
- K_PWFS_FIELD, K_PWFS_BIN, K_CALIB) = range(10)
-K_COUNT = 10
+ K_PWFS_FIELD, K_PWFS_BIN, K_CALIB, K_GEMM, K_MLP) = range(12)
+K_COUNT = 12
 KERNEL_NAMES = ["pwfs_rows_fwd", "pwfs_cols", "pwfs_rows_inv", "atmo_extract", "slopes",
-                "recon", "sh_spots", "pwfs_field", "pwfs_bin", "calib"]
+                "recon", "sh_spots", "pwfs_field", "pwfs_bin", "calib", "gemm", "mlp"]
 
 
 def specula_prof_enable(ctx, capacity):
@@ -391,6 +391,19 @@ def specula_recon_convert(ctx, R, precision, hi, lo=None, stream=None):
         ctx.handle, int(nm), int(ns), _dev(R, torch.float32, nm * ns, "R"), int(precision),
         _dev(hi, None, nm * ns, "hi"), _dev(lo, None, nm * ns, "lo"), _stream(stream)),
         "specula_recon_convert")
+
+
+def specula_gemm_bf16(ctx, A, B, C, splits=1, work=None, stream=None):
+    """C (M, N) float32 = A (M, K) bf16 @ B (N, K)^T bf16 on the tensor cores."""
+    import torch
+    M, K = A.shape
+    N = B.shape[0]
+    if B.shape[1] != K:
+        raise ValueError("A and B must share K")
+    _abi.check(lib().specula_gemm_bf16(
+        ctx.handle, _dev(A, torch.bfloat16, M * K, "A"), _dev(B, torch.bfloat16, N * K, "B"),
+        int(M), int(N), int(K), _dev(C, torch.float32, M * N, "C"), int(splits),
+        _dev(work, torch.float32, None, "work"), _stream(stream)), "specula_gemm_bf16")
 
 
 def specula_modal_basis_host(pupil, n_modes):

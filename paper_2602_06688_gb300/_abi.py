@@ -94,6 +94,7 @@ SIGNATURES = {
     "specula_slopes": (C.c_int, [vp, P(SlopecDesc), vp, vp, i32, vp, vp]),
     "specula_recon": (C.c_int, [vp, P(ReconDesc), vp, i32, vp, vp]),
     "specula_recon_convert": (C.c_int, [vp, i32, i32, vp, i32, vp, vp, vp]),
+    "specula_gemm_bf16": (C.c_int, [vp, vp, vp, i32, i32, i32, vp, i32, vp, vp]),
     "specula_modal_basis_host": (C.c_int, [P(PupilDesc), i32, vp]),
     "specula_modal_basis": (C.c_int, [vp, P(PupilDesc), i32, vp, vp]),
     "specula_calib_intmat": (C.c_int, [vp, P(PupilDesc), P(PwfsDesc), vp, vp, i32, dbl,

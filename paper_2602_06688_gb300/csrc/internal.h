@@ -139,6 +139,11 @@ ShPlan *sh_plan_find(specula_ctx *ctx, const specula_pupil_desc *pupil,
 int sh_run(specula_ctx *ctx, ShPlan *plan, const float *amp, const float *phase,
            int n_batch, float *spots, cudaStream_t st);
 
+int gemm_check(const void *A, const void *B, int M, int N, int K);
+int gemm_splits(int K, int want);
+int gemm_bf16_tn(specula_ctx *ctx, const void *A, const void *B, int M, int N, int K, float *C,
+                 int splits, float *work, cudaStream_t st);
+
 int slopes_pyr_run(specula_ctx *ctx, const int32_t *idx, int n_sub, int n_valid,
                    const float *det, const float *ref, int n_batch, float *out, cudaStream_t st);
 

@@ -1,0 +1,57 @@
+"""GPU parity: the tcgen05 BF16 GEMM against a float64 product of the same
+bf16-rounded operands.  FP32 accumulation: |C - ref| <= 2e-5 sum_k |a_ik b_jk|."""
+import numpy as np
+import pytest
+
+from gpu_common import load_pkg, need_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = need_gpu()
+    sp = load_pkg()
+    ctx = sp.Context(0)
+    yield torch, sp, ctx
+    ctx.close()
+
+
+@pytest.mark.parametrize("M,N,K,splits", [(128, 128, 64, 1), (128, 128, 256, 1),
+                                          (256, 384, 640, 1), (256, 384, 640, 3),
+                                          (128, 256, 2560, 8), (384, 128, 1024, 5)])
+def test_gemm_bf16_parity(env, M, N, K, splits):
+    torch, sp, ctx = env
+    g = torch.Generator(device="cpu").manual_seed(M * 7 + N * 3 + K)
+    A = torch.randn(M, K, generator=g).bfloat16()
+    B = torch.randn(N, K, generator=g).bfloat16()
+    Ad, Bd = A.cuda(), B.cuda()
+    C = torch.full((M, N), float("nan"), device="cuda")
+    work = torch.empty(splits * M * N, device="cuda") if splits > 1 else None
+    sp.specula_gemm_bf16(ctx, Ad, Bd, C, splits=splits, work=work)
+    torch.cuda.synchronize()
+    assert sp.specula_ctx_status(ctx) == 0
+    a = A.float().numpy().astype(np.float64)
+    b = B.float().numpy().astype(np.float64)
+    ref = a @ b.T
+    mag = np.abs(a) @ np.abs(b).T
+    got = C.cpu().numpy().astype(np.float64)
+    assert np.all(np.isfinite(got))
+    assert np.all(np.abs(got - ref) <= 2e-5 * mag + 1e-30), np.max(np.abs(got - ref) / mag)
+
+
+def test_gemm_deterministic_and_rejects_shapes(env):
+    torch, sp, ctx = env
+    A = torch.randn(256, 512, device="cuda").bfloat16()
+    B = torch.randn(256, 512, device="cuda").bfloat16()
+    C1 = torch.empty(256, 256, device="cuda")
+    C2 = torch.empty(256, 256, device="cuda")
+    w = torch.empty(4 * 256 * 256, device="cuda")
+    sp.specula_gemm_bf16(ctx, A, B, C1, splits=4, work=w)
+    sp.specula_gemm_bf16(ctx, A, B, C2, splits=4, work=w)
+    torch.cuda.synchronize()
+    assert torch.equal(C1, C2)
+    with pytest.raises(sp.SpeculaError) as e:
+        sp.specula_gemm_bf16(ctx, A[:, :100].contiguous(), B[:, :100].contiguous(),
+                             torch.empty(256, 256, device="cuda"))
+    assert e.value.status == sp.EUNSUPPORTED
