@@ -372,6 +372,38 @@ int specula_gemm_bf16(specula_ctx *ctx, const void *A_dev, const void *B_dev, in
                       int32_t N, int32_t K, float *C_dev, int32_t splits, float *work_dev,
                       void *stream);
 
+/* ---- learned reconstructor ----------------------------------------------------
+ * A perceptron slopes -> modal coefficients, n_in -> n_h1 -> n_h2 -> n_out with
+ * exact-erf GELU between layers (not in the paper, whose reconstructor is
+ * the linear Modalrec; the learned part follows the configuration this
+ * library targets).  FP32 master weights and Adam moments, bf16 copies for
+ * the tcgen05 GEMMs, FP32 accumulation.  Hidden widths must be multiples of
+ * 128; the input/output widths and the batch are padded internally.
+ * create/destroy/set/get may allocate and synchronise; forward, backward and
+ * adam only enqueue.  One model per stream at a time. */
+typedef struct specula_mlp specula_mlp;
+int specula_mlp_create(specula_ctx *ctx, int32_t n_in, int32_t n_h1, int32_t n_h2,
+                       int32_t n_out, int32_t batch_max, specula_mlp **out);
+int specula_mlp_destroy(specula_mlp *mlp);
+/* layer l in {0,1,2}: W_host (out x in, row-major) and b_host (out) floats;
+ * set resets that layer's Adam moments and the step count. */
+int specula_mlp_set_layer(specula_mlp *mlp, int32_t layer, const float *W_host,
+                          const float *b_host);
+int specula_mlp_get_layer(specula_mlp *mlp, int32_t layer, float *W_host, float *b_host);
+/* gradient of the last backward for layer l (same layouts as get_layer) */
+int specula_mlp_get_grad(specula_mlp *mlp, int32_t layer, float *dW_host, float *db_host);
+/* Y_dev (nullable): batch x n_out floats; X_dev: batch x n_in floats. */
+int specula_mlp_forward(specula_mlp *mlp, const float *X_dev, int32_t batch, float *Y_dev,
+                        void *stream);
+/* Gradients of loss = mean over batch and outputs of (Y - T)^2 for the last
+ * forward (same batch); T_dev: batch x n_out floats; loss_dev (nullable): one
+ * float. */
+int specula_mlp_backward(specula_mlp *mlp, const float *T_dev, int32_t batch, float *loss_dev,
+                         void *stream);
+/* Adam on every parameter with the last gradients: m = b1 m + (1-b1) g,
+ * v = b2 v + (1-b2) g^2, w -= lr sqrt(1-b2^t)/(1-b1^t) m / (sqrt(v) + eps). */
+int specula_mlp_adam(specula_mlp *mlp, float lr, float b1, float b2, float eps, void *stream);
+
 /* ---- calibration (set-up calls: may allocate, synchronise the stream) ------
  * Modal basis (stands in for the non-public KL files of Listing 2,
  * `ifunc_object`): Zernike modes in Noll order without piston, j = 2 ..

@@ -406,6 +406,100 @@ def specula_gemm_bf16(ctx, A, B, C, splits=1, work=None, stream=None):
         _dev(work, torch.float32, None, "work"), _stream(stream)), "specula_gemm_bf16")
 
 
+class MLP:
+    """Learned reconstructor handle (specula_mlp_*)."""
+
+    def __init__(self, ctx, sizes, batch_max):
+        n_in, h1, h2, n_out = sizes
+        h = C.c_void_p()
+        _abi.check(lib().specula_mlp_create(ctx.handle, int(n_in), int(h1), int(h2), int(n_out),
+                                            int(batch_max), C.byref(h)), "specula_mlp_create")
+        self.handle, self.sizes = h, tuple(sizes)
+
+    def close(self):
+        if self.handle:
+            lib().specula_mlp_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_layer(self, l, W, b):
+        W = np.ascontiguousarray(W, dtype=np.float32)
+        b = np.ascontiguousarray(b, dtype=np.float32)
+        assert W.shape == (self.sizes[l + 1], self.sizes[l]) and b.shape == (self.sizes[l + 1],)
+        _abi.check(lib().specula_mlp_set_layer(self.handle, int(l), W.ctypes.data_as(C.c_void_p),
+                                               b.ctypes.data_as(C.c_void_p)),
+                   "specula_mlp_set_layer")
+
+    def _get(self, fn, l, name):
+        W = np.zeros((self.sizes[l + 1], self.sizes[l]), dtype=np.float32)
+        b = np.zeros(self.sizes[l + 1], dtype=np.float32)
+        _abi.check(fn(self.handle, int(l), W.ctypes.data_as(C.c_void_p),
+                      b.ctypes.data_as(C.c_void_p)), name)
+        return W, b
+
+    def get_layer(self, l):
+        return self._get(lib().specula_mlp_get_layer, l, "specula_mlp_get_layer")
+
+    def get_grad(self, l):
+        return self._get(lib().specula_mlp_get_grad, l, "specula_mlp_get_grad")
+
+    def forward(self, X, Y=None, stream=None):
+        import torch
+        B = X.shape[0]
+        _abi.check(lib().specula_mlp_forward(
+            self.handle, _dev(X, torch.float32, B * self.sizes[0], "X"), int(B),
+            _dev(Y, torch.float32, B * self.sizes[3], "Y"), _stream(stream)),
+            "specula_mlp_forward")
+
+    def backward(self, T, loss=None, stream=None):
+        import torch
+        B = T.shape[0]
+        _abi.check(lib().specula_mlp_backward(
+            self.handle, _dev(T, torch.float32, B * self.sizes[3], "T"), int(B),
+            _dev(loss, torch.float32, 1, "loss"), _stream(stream)), "specula_mlp_backward")
+
+    def adam(self, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8, stream=None):
+        _abi.check(lib().specula_mlp_adam(self.handle, float(lr), float(b1), float(b2),
+                                          float(eps), _stream(stream)), "specula_mlp_adam")
+
+
+def specula_mlp_create(ctx, n_in, n_h1, n_h2, n_out, batch_max):
+    return MLP(ctx, (n_in, n_h1, n_h2, n_out), batch_max)
+
+
+def specula_mlp_destroy(mlp):
+    mlp.close()
+
+
+def specula_mlp_set_layer(mlp, layer, W, b):
+    mlp.set_layer(layer, W, b)
+
+
+def specula_mlp_get_layer(mlp, layer):
+    return mlp.get_layer(layer)
+
+
+def specula_mlp_get_grad(mlp, layer):
+    return mlp.get_grad(layer)
+
+
+def specula_mlp_forward(mlp, X, Y=None, stream=None):
+    mlp.forward(X, Y, stream)
+
+
+def specula_mlp_backward(mlp, T, loss=None, stream=None):
+    mlp.backward(T, loss, stream)
+
+
+def specula_mlp_adam(mlp, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8, stream=None):
+    mlp.adam(lr, b1, b2, eps, stream)
+
+
 def specula_modal_basis_host(pupil, n_modes):
     out = np.zeros((n_modes, pupil.n_pix, pupil.n_pix))
     _abi.check(lib().specula_modal_basis_host(C.byref(pupil), int(n_modes),

@@ -95,6 +95,14 @@ SIGNATURES = {
     "specula_recon": (C.c_int, [vp, P(ReconDesc), vp, i32, vp, vp]),
     "specula_recon_convert": (C.c_int, [vp, i32, i32, vp, i32, vp, vp, vp]),
     "specula_gemm_bf16": (C.c_int, [vp, vp, vp, i32, i32, i32, vp, i32, vp, vp]),
+    "specula_mlp_create": (C.c_int, [vp, i32, i32, i32, i32, i32, P(vp)]),
+    "specula_mlp_destroy": (C.c_int, [vp]),
+    "specula_mlp_set_layer": (C.c_int, [vp, i32, vp, vp]),
+    "specula_mlp_get_layer": (C.c_int, [vp, i32, vp, vp]),
+    "specula_mlp_get_grad": (C.c_int, [vp, i32, vp, vp]),
+    "specula_mlp_forward": (C.c_int, [vp, vp, i32, vp, vp]),
+    "specula_mlp_backward": (C.c_int, [vp, vp, i32, vp, vp]),
+    "specula_mlp_adam": (C.c_int, [vp, C.c_float, C.c_float, C.c_float, C.c_float, vp]),
     "specula_modal_basis_host": (C.c_int, [P(PupilDesc), i32, vp]),
     "specula_modal_basis": (C.c_int, [vp, P(PupilDesc), i32, vp, vp]),
     "specula_calib_intmat": (C.c_int, [vp, P(PupilDesc), P(PwfsDesc), vp, vp, i32, dbl,
