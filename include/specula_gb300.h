@@ -233,6 +233,31 @@ int specula_screen_generate(specula_ctx *ctx, int32_t side, double pitch_m,
                             const double *noise_sub_host, float *screen_dev,
                             void *stream);
 
+/* Counter-based normals (Philox4x32-10, Salmon et al., SC 2011; uniforms
+ * (x + 0.5) 2^-32, Box-Muller): for sample b in [sample0, sample0 +
+ * n_samples), n_per_sample complex values, element 2i and 2i+1 from counter
+ * (i low, i high, b, stream_id) with key (seed low, seed high).  out_dev:
+ * n_samples * n_per_sample complex float64, interleaved. */
+int specula_rng_complex(specula_ctx *ctx, uint64_t seed, int32_t sample0, int32_t n_samples,
+                        int32_t stream_id, int64_t n_per_sample, double *out_dev, void *stream);
+
+/* Batch of independent von Karman screens (same construction as
+ * specula_screen_generate) whose noise is drawn on the device: screen b uses
+ * the Philox complex normals of sample sample0 + b, stream 0 for the FFT
+ * grid (element ky * side + kx) and stream 1 for the 27 subharmonic values
+ * (element (p * 3 + b) * 3 + a).  screens_dev: n_screens * side^2 floats.
+ * Set-up call: allocates at most 1 GiB of float64 work arrays. */
+int specula_screen_generate_batch(specula_ctx *ctx, int32_t n_screens, int32_t side,
+                                  double pitch_m, double r0_m, double L0_m, uint64_t seed,
+                                  int32_t sample0, float *screens_dev, void *stream);
+
+/* Random pupil phases from screens (AtmoRandomPhase, App. A, Tab. 4):
+ * phase[b][j][i] = scale[b] * screen[b][j + o][i + o], o = (side - n_pix)/2,
+ * for n screens; scale_dev: n floats (e.g. (r0_ref / r0_b)^(5/6) 500 /
+ * lambda). */
+int specula_random_phase(specula_ctx *ctx, const float *screens_dev, int32_t n, int32_t side,
+                         int32_t n_pix, const float *scale_dev, float *phase_dev, void *stream);
+
 /* ---- per-frame calls ------------------------------------------------------- */
 
 /* Layer extraction (AtmoEvolution + AtmoPropagation, geometric propagation):

@@ -281,6 +281,33 @@ def specula_atmo_extract(ctx, layers, screens, source, pupil, t, phase, t_dev=No
         "specula_atmo_extract")
 
 
+def specula_rng_complex(ctx, seed, sample0, n_samples, stream_id, n_per_sample, out,
+                        stream=None):
+    import torch
+    _abi.check(lib().specula_rng_complex(
+        ctx.handle, int(seed), int(sample0), int(n_samples), int(stream_id), int(n_per_sample),
+        _dev(out, torch.complex128, n_samples * n_per_sample, "out"), _stream(stream)),
+        "specula_rng_complex")
+
+
+def specula_screen_generate_batch(ctx, n_screens, side, pitch_m, r0_m, L0_m, seed, sample0,
+                                  screens, stream=None):
+    import torch
+    _abi.check(lib().specula_screen_generate_batch(
+        ctx.handle, int(n_screens), int(side), float(pitch_m), float(r0_m), float(L0_m),
+        int(seed), int(sample0), _dev(screens, torch.float32, n_screens * side * side, "screens"),
+        _stream(stream)), "specula_screen_generate_batch")
+
+
+def specula_random_phase(ctx, screens, n, side, n_pix, scale, phase, stream=None):
+    import torch
+    _abi.check(lib().specula_random_phase(
+        ctx.handle, _dev(screens, torch.float32, n * side * side, "screens"), int(n), int(side),
+        int(n_pix), _dev(scale, torch.float32, n, "scale"),
+        _dev(phase, torch.float32, n * n_pix * n_pix, "phase"), _stream(stream)),
+        "specula_random_phase")
+
+
 def specula_atmo_extract_noalloc(layers, screens, source, pupil, t, phase, t_dev=None,
                                  stream=None):
     """Context-free extraction for callers that cannot allocate device memory

@@ -81,6 +81,10 @@ SIGNATURES = {
     "specula_screen_generate": (C.c_int, [vp, i32, dbl, dbl, dbl, vp, vp, vp, vp]),
     "specula_atmo_extract": (C.c_int, [vp, i32, P(LayerDesc), P(vp), P(SourceDesc),
                                        P(PupilDesc), dbl, vp, vp, vp]),
+    "specula_rng_complex": (C.c_int, [vp, C.c_uint64, i32, i32, i32, C.c_int64, vp, vp]),
+    "specula_screen_generate_batch": (C.c_int, [vp, i32, i32, dbl, dbl, dbl, C.c_uint64, i32,
+                                                vp, vp]),
+    "specula_random_phase": (C.c_int, [vp, vp, i32, i32, i32, vp, vp, vp]),
     "specula_atmo_extract_noalloc": (C.c_int, [i32, P(LayerDesc), P(vp), P(SourceDesc),
                                                P(PupilDesc), dbl, vp, vp, vp]),
     "specula_pwfs_plan": (C.c_int, [vp, P(PupilDesc), P(PwfsDesc)]),

@@ -101,6 +101,156 @@ __global__ void k_screen_final(const double2 *__restrict__ T, const double2 *__r
   }
 }
 
+// ---- counter-based noise: Philox4x32-10 (Salmon et al., SC 2011) ------------
+// Ten rounds of (hi0, lo0) = M0 c0, (hi1, lo1) = M1 c2,
+// c <- (hi1 ^ c1 ^ k0, lo1, hi0 ^ c3 ^ k1, lo0), key bumped by the Weyl
+// constants between rounds; uniforms (x + 0.5) 2^-32; Box-Muller normals.
+__device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint64_t p0 = (uint64_t)0xD2511F53u * c[0];
+    const uint64_t p1 = (uint64_t)0xCD9E8D57u * c[2];
+    const uint32_t n0 = (uint32_t)(p1 >> 32) ^ c[1] ^ k0;
+    const uint32_t n2 = (uint32_t)(p0 >> 32) ^ c[3] ^ k1;
+    c[1] = (uint32_t)p1;
+    c[3] = (uint32_t)p0;
+    c[0] = n0;
+    c[2] = n2;
+    if (r < 9) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+  }
+}
+
+// four standard normals for counter (pair index, sample, stream)
+__device__ __forceinline__ void normals4(uint64_t pair, uint32_t sample, uint32_t stream,
+                                         uint64_t seed, double g[4]) {
+  uint32_t c[4] = {(uint32_t)pair, (uint32_t)(pair >> 32), sample, stream};
+  philox4x32_10(c, (uint32_t)seed, (uint32_t)(seed >> 32));
+  double u[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) u[i] = ((double)c[i] + 0.5) * (1.0 / 4294967296.0);
+  const double r0 = sqrt(-2.0 * log(u[0])), r1 = sqrt(-2.0 * log(u[2]));
+  const double t0 = 2.0 * M_PI * u[1], t1 = 2.0 * M_PI * u[3];
+  g[0] = r0 * cos(t0);
+  g[1] = r0 * sin(t0);
+  g[2] = r1 * cos(t1);
+  g[3] = r1 * sin(t1);
+}
+
+// n complex normals per sample: element 2i, 2i+1 from counter i
+__global__ void k_rng_complex(uint64_t seed, int sample0, int stream_id, long long n,
+                              double2 *__restrict__ out) {
+  const long long pair = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const int b = blockIdx.y;
+  if (2 * pair >= n) return;
+  double g[4];
+  normals4((uint64_t)pair, (uint32_t)(sample0 + b), (uint32_t)stream_id, seed, g);
+  out[(size_t)b * n + 2 * pair] = make_double2(g[0], g[1]);
+  if (2 * pair + 1 < n) out[(size_t)b * n + 2 * pair + 1] = make_double2(g[2], g[3]);
+}
+
+// Philox screen noise (stream 0) times the spectral amplitude, per screen b
+__global__ void k_noise_psd_batch(double2 *__restrict__ A, int M, double Md, double coef,
+                                  double k0, uint64_t seed, int sample0) {
+  const long long pair = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const int b = blockIdx.y;
+  const long long n = (long long)M * M;
+  if (2 * pair >= n) return;
+  double g[4];
+  normals4((uint64_t)pair, (uint32_t)(sample0 + b), 0u, seed, g);
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const long long e = 2 * pair + q;
+    const int ky = (int)(e / M), kx = (int)(e % M);
+    const int sx = kx >= M / 2 ? kx - M : kx, sy = ky >= M / 2 ? ky - M : ky;
+    const double fx = (double)sx / Md, fy = (double)sy / Md;
+    const double f2 = fx * fx + fy * fy;
+    double a = 0.0;
+    if (f2 > 0.0) a = sqrt(coef * pow(f2 + k0, -11.0 / 6.0)) / Md;
+    A[(size_t)b * n + e] = make_double2(g[2 * q] * a, g[2 * q + 1] * a);
+  }
+}
+
+__global__ void k_transpose_f64_batch(const double2 *__restrict__ in, double2 *__restrict__ out,
+                                      int M) {
+  __shared__ double2 tile[32][33];
+  const size_t off = (size_t)blockIdx.z * M * M;
+  const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y)
+    tile[r][threadIdx.x] = in[off + (size_t)(by + r) * M + bx + threadIdx.x];
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += blockDim.y)
+    out[off + (size_t)(bx + r) * M + by + threadIdx.x] = tile[threadIdx.x][r];
+}
+
+// per screen: subharmonic coefficients (Philox stream 1: 27 complex values,
+// element (p * 3 + b) * 3 + a) times the amplitudes, and the spatial mean of
+// the subharmonic sum (separable: sum Re(c mean(ex_a) mean(ey_b)))
+__global__ void k_sub_coef_batch(const double *__restrict__ amp27, const double2 *__restrict__ tmean,
+                                 uint64_t seed, int sample0, int n_screens,
+                                 double2 *__restrict__ coef, double *__restrict__ sub_mean) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= n_screens) return;
+  double2 c[28];
+  for (int pr = 0; pr < 14; ++pr) {
+    double g[4];
+    normals4((uint64_t)pr, (uint32_t)(sample0 + b), 1u, seed, g);
+    c[2 * pr] = make_double2(g[0], g[1]);
+    c[2 * pr + 1] = make_double2(g[2], g[3]);
+  }
+  double mean = 0.0;
+  for (int e = 0; e < 27; ++e) {
+    const int p = e / 9, bb = (e / 3) % 3, a = e % 3;
+    const double2 v = make_double2(c[e].x * amp27[e], c[e].y * amp27[e]);
+    coef[(size_t)b * 27 + e] = v;
+    const double2 mx = tmean[p * 3 + a], my = tmean[p * 3 + bb];
+    const double2 m = make_double2(mx.x * my.x - mx.y * my.y, mx.x * my.y + mx.y * my.x);
+    mean += v.x * m.x - v.y * m.y;
+  }
+  sub_mean[b] = mean;
+}
+
+__global__ void k_screen_final_batch(const double2 *__restrict__ T, const double2 *__restrict__ tab,
+                                     const double2 *__restrict__ coef,
+                                     const double *__restrict__ sub_mean, int M, int levels,
+                                     float *__restrict__ out) {
+  __shared__ double2 tile[32][33];
+  const int b = blockIdx.z;
+  const size_t off = (size_t)b * M * M;
+  const double2 *cf = coef + (size_t)b * 27;
+  const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
+  for (int r = threadIdx.y; r < 32; r += blockDim.y)
+    tile[r][threadIdx.x] = T[off + (size_t)(bx + r) * M + by + threadIdx.x];
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int y = by + r, x = bx + threadIdx.x;
+    double sub = 0.0;
+    for (int p = 0; p < levels; ++p)
+      for (int bb = 0; bb < 3; ++bb)
+        for (int aa = 0; aa < 3; ++aa) {
+          if (aa == 1 && bb == 1) continue;
+          const double2 ex = tab[((size_t)p * 3 + aa) * M + x];
+          const double2 ey = tab[((size_t)p * 3 + bb) * M + y];
+          const double2 e = make_double2(ex.x * ey.x - ex.y * ey.y, ex.x * ey.y + ex.y * ey.x);
+          const double2 c = cf[(p * 3 + bb) * 3 + aa];
+          sub += c.x * e.x - c.y * e.y;
+        }
+    out[off + (size_t)y * M + x] = (float)(tile[threadIdx.x][r].x + (sub - sub_mean[b]));
+  }
+}
+
+// phase[b][j][i] = scale[b] * screen[b][j + o][i + o], o = (side - n) / 2
+__global__ void k_random_phase(const float *__restrict__ scr, int side, int n,
+                               const float *__restrict__ scale, float *__restrict__ phase) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y, b = blockIdx.z;
+  if (i >= n) return;
+  const int o = (side - n) / 2;
+  phase[((size_t)b * n + j) * n + i] =
+      scale[b] * scr[((size_t)b * side + j + o) * side + i + o];
+}
+
 }  // namespace specula
 
 using namespace specula;
@@ -194,5 +344,122 @@ extern "C" int specula_screen_generate(specula_ctx *ctx, int32_t side, double pi
   SPECULA_CK_LAUNCH();
   // the temporaries are freed on return; wait for the kernels that use them
   SPECULA_CK(cudaStreamSynchronize(st));
+  return SPECULA_OK;
+}
+
+extern "C" int specula_rng_complex(specula_ctx *ctx, uint64_t seed, int32_t sample0,
+                                   int32_t n_samples, int32_t stream_id, int64_t n_per_sample,
+                                   double *out_dev, void *stream) {
+  if (!ctx || !out_dev || n_samples < 1 || n_per_sample < 1 || sample0 < 0 || stream_id < 0)
+    return SPECULA_EINVAL;
+  if (n_samples > 65535) return SPECULA_EUNSUPPORTED;
+  const long long pairs = (n_per_sample + 1) / 2;
+  dim3 grid((unsigned)((pairs + 255) / 256), n_samples);
+  cudaStream_t st = (cudaStream_t)stream;
+  SPECULA_LAUNCH(ctx, SPECULA_K_CALIB, st,
+                 k_rng_complex<<<grid, 256, 0, st>>>(seed, sample0, stream_id, n_per_sample,
+                                                     (double2 *)out_dev));
+  return SPECULA_OK;
+}
+
+extern "C" int specula_screen_generate_batch(specula_ctx *ctx, int32_t n_screens, int32_t side,
+                                             double pitch_m, double r0_m, double L0_m,
+                                             uint64_t seed, int32_t sample0, float *screens_dev,
+                                             void *stream) {
+  if (!ctx || !screens_dev || n_screens < 1 || sample0 < 0) return SPECULA_EINVAL;
+  if (side < 32 || side > 4096 || (side & (side - 1))) return SPECULA_EINVAL;
+  if (!(pitch_m > 0) || !(r0_m > 0) || !(L0_m > 0)) return SPECULA_EINVAL;
+  SPECULA_CK(cudaSetDevice(ctx->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  const int M = side;
+  int logM = 0;
+  while ((1 << logM) < M) ++logM;
+  const double Md = (double)M * pitch_m;
+  const double df = 1.0 / Md;
+  const double coef = 0.023 * pow(r0_m, -5.0 / 3.0);
+  const double k0 = isinf(L0_m) ? 0.0 : 1.0 / (L0_m * L0_m);
+  const int levels = 3;
+  std::vector<double2> tw(M / 2);
+  for (int k = 0; k < M / 2; ++k) {
+    const double a = 2.0 * M_PI * (double)k / (double)M;
+    tw[k] = make_double2(cos(a), sin(a));
+  }
+  std::vector<double2> tab((size_t)levels * 3 * M), tmean(levels * 3);
+  std::vector<double> amp27(27, 0.0);
+  for (int p = 0; p < levels; ++p) {
+    const double dfp = df / pow(3.0, p + 1);
+    for (int a = 0; a < 3; ++a) {
+      const double f = (a - 1) * dfp;
+      double sr = 0, si = 0;
+      for (int x = 0; x < M; ++x) {
+        const double ang = 2.0 * M_PI * f * ((double)x * pitch_m);
+        const double2 e = make_double2(cos(ang), sin(ang));
+        tab[((size_t)p * 3 + a) * M + x] = e;
+        sr += e.x;
+        si += e.y;
+      }
+      tmean[p * 3 + a] = make_double2(sr / M, si / M);
+    }
+    for (int b = 0; b < 3; ++b)
+      for (int a = 0; a < 3; ++a)
+        if (!(a == 1 && b == 1))
+          amp27[(p * 3 + b) * 3 + a] = sqrt(psd_host((a - 1) * dfp, (b - 1) * dfp, r0_m, L0_m)) * dfp;
+  }
+  DevBuf dtw, dtab, dtmean, damp;
+  int s;
+  if ((s = dtw.upload(tw.data(), tw.size() * sizeof(double2)))) return s;
+  if ((s = dtab.upload(tab.data(), tab.size() * sizeof(double2)))) return s;
+  if ((s = dtmean.upload(tmean.data(), tmean.size() * sizeof(double2)))) return s;
+  if ((s = damp.upload(amp27.data(), amp27.size() * sizeof(double)))) return s;
+  // screens per group: two complex float64 work arrays of at most 1 GiB in all
+  const size_t per = (size_t)M * M * sizeof(double2);
+  const int G = (int)std::max<size_t>(1, std::min<size_t>(n_screens, (1ull << 30) / (2 * per)));
+  DevBuf A, B, cf, sm;
+  if ((s = A.alloc(G * per)) || (s = B.alloc(G * per)) ||
+      (s = cf.alloc((size_t)G * 27 * sizeof(double2))) || (s = sm.alloc((size_t)G * sizeof(double))))
+    return s;
+  const size_t smem = 2 * (size_t)M * sizeof(double2);
+  if (smem > 48 * 1024)
+    SPECULA_CK(cudaFuncSetAttribute(k_fft_rows_f64, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem));
+  for (int g0 = 0; g0 < n_screens; g0 += G) {
+    const int ng = std::min(G, n_screens - g0);
+    const long long pairs = (long long)M * M / 2;
+    SPECULA_LAUNCH(ctx, SPECULA_K_CALIB, st,
+                   k_noise_psd_batch<<<dim3((unsigned)((pairs + 255) / 256), ng), 256, 0, st>>>(
+                       A.as<double2>(), M, Md, coef, k0, seed, sample0 + g0));
+    SPECULA_LAUNCH(ctx, SPECULA_K_CALIB, st,
+                   k_fft_rows_f64<<<ng * M, 256, smem, st>>>(A.as<double2>(), dtw.as<double2>(), M,
+                                                             logM));
+    SPECULA_LAUNCH(ctx, SPECULA_K_CALIB, st,
+                   k_transpose_f64_batch<<<dim3(M / 32, M / 32, ng), dim3(32, 8), 0, st>>>(
+                       A.as<double2>(), B.as<double2>(), M));
+    SPECULA_LAUNCH(ctx, SPECULA_K_CALIB, st,
+                   k_fft_rows_f64<<<ng * M, 256, smem, st>>>(B.as<double2>(), dtw.as<double2>(), M,
+                                                             logM));
+    SPECULA_LAUNCH(ctx, SPECULA_K_CALIB, st,
+                   k_sub_coef_batch<<<(ng + 63) / 64, 64, 0, st>>>(
+                       damp.as<double>(), dtmean.as<double2>(), seed, sample0 + g0, ng,
+                       cf.as<double2>(), sm.as<double>()));
+    SPECULA_LAUNCH(ctx, SPECULA_K_CALIB, st,
+                   k_screen_final_batch<<<dim3(M / 32, M / 32, ng), dim3(32, 8), 0, st>>>(
+                       B.as<double2>(), dtab.as<double2>(), cf.as<double2>(), sm.as<double>(), M,
+                       levels, screens_dev + (size_t)g0 * M * M));
+  }
+  SPECULA_CK(cudaStreamSynchronize(st));   // the work arrays are freed on return
+  return SPECULA_OK;
+}
+
+extern "C" int specula_random_phase(specula_ctx *ctx, const float *screens_dev, int32_t n,
+                                    int32_t side, int32_t n_pix, const float *scale_dev,
+                                    float *phase_dev, void *stream) {
+  if (!ctx || !screens_dev || !scale_dev || !phase_dev || n < 1 || n_pix < 1 || side < n_pix)
+    return SPECULA_EINVAL;
+  if (n > 65535) return SPECULA_EUNSUPPORTED;
+  cudaStream_t st = (cudaStream_t)stream;
+  dim3 grid((n_pix + 127) / 128, n_pix, n);
+  SPECULA_LAUNCH(ctx, SPECULA_K_ATMO, st,
+                 k_random_phase<<<grid, 128, 0, st>>>(screens_dev, side, n_pix, scale_dev,
+                                                      phase_dev));
   return SPECULA_OK;
 }
