@@ -429,6 +429,17 @@ int specula_mlp_backward(specula_mlp *mlp, const float *T_dev, int32_t batch, fl
  * v = b2 v + (1-b2) g^2, w -= lr sqrt(1-b2^t)/(1-b1^t) m / (sqrt(v) + eps). */
 int specula_mlp_adam(specula_mlp *mlp, float lr, float b1, float b2, float eps, void *stream);
 
+/* Per-column statistics and affine maps for standardising the learned
+ * reconstructor's inputs and outputs.  col_stats: mean and (population)
+ * standard deviation of each column of X (rows x cols floats), summed in
+ * float64 in row order.  affine_cols: out[r][c] = (X[r][c] - shift[c]) *
+ * mul[c] (out may equal X). */
+int specula_col_stats(specula_ctx *ctx, const float *X_dev, int32_t rows, int32_t cols,
+                      float *mean_dev, float *std_dev, void *stream);
+int specula_affine_cols(specula_ctx *ctx, const float *X_dev, int64_t rows, int32_t cols,
+                        const float *shift_dev, const float *mul_dev, float *out_dev,
+                        void *stream);
+
 /* ---- calibration (set-up calls: may allocate, synchronise the stream) ------
  * Modal basis (stands in for the non-public KL files of Listing 2,
  * `ifunc_object`): Zernike modes in Noll order without piston, j = 2 ..

@@ -433,6 +433,24 @@ def specula_gemm_bf16(ctx, A, B, C, splits=1, work=None, stream=None):
         _dev(work, torch.float32, None, "work"), _stream(stream)), "specula_gemm_bf16")
 
 
+def specula_col_stats(ctx, X, mean, std, stream=None):
+    import torch
+    R, Cc = X.shape
+    _abi.check(lib().specula_col_stats(
+        ctx.handle, _dev(X, torch.float32, R * Cc, "X"), int(R), int(Cc),
+        _dev(mean, torch.float32, Cc, "mean"), _dev(std, torch.float32, Cc, "std"),
+        _stream(stream)), "specula_col_stats")
+
+
+def specula_affine_cols(ctx, X, shift, mul, out, stream=None):
+    import torch
+    R, Cc = X.shape
+    _abi.check(lib().specula_affine_cols(
+        ctx.handle, _dev(X, torch.float32, R * Cc, "X"), int(R), int(Cc),
+        _dev(shift, torch.float32, Cc, "shift"), _dev(mul, torch.float32, Cc, "mul"),
+        _dev(out, torch.float32, R * Cc, "out"), _stream(stream)), "specula_affine_cols")
+
+
 class MLP:
     """Learned reconstructor handle (specula_mlp_*)."""
 

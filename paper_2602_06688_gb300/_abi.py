@@ -99,6 +99,8 @@ SIGNATURES = {
     "specula_recon": (C.c_int, [vp, P(ReconDesc), vp, i32, vp, vp]),
     "specula_recon_convert": (C.c_int, [vp, i32, i32, vp, i32, vp, vp, vp]),
     "specula_gemm_bf16": (C.c_int, [vp, vp, vp, i32, i32, i32, vp, i32, vp, vp]),
+    "specula_col_stats": (C.c_int, [vp, vp, i32, i32, vp, vp, vp]),
+    "specula_affine_cols": (C.c_int, [vp, vp, C.c_int64, i32, vp, vp, vp, vp]),
     "specula_mlp_create": (C.c_int, [vp, i32, i32, i32, i32, i32, P(vp)]),
     "specula_mlp_destroy": (C.c_int, [vp]),
     "specula_mlp_set_layer": (C.c_int, [vp, i32, vp, vp]),

@@ -161,9 +161,60 @@ __global__ void k_cast_w(const float *__restrict__ W, int R, int C, __nv_bfloat1
   tile_bf16_pair(R, C, Wb, WbT, [&](int r, int c) { return W[(size_t)r * C + c]; });
 }
 
+// column mean and standard deviation of X [R][C] (float64 sums, rows in order)
+__global__ void k_col_stats(const float *__restrict__ X, int R, int C, float *__restrict__ mean,
+                            float *__restrict__ stdv) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= C) return;
+  double s = 0.0, s2 = 0.0;
+  for (int r = 0; r < R; ++r) {
+    const double v = X[(size_t)r * C + c];
+    s += v;
+    s2 += v * v;
+  }
+  const double m = s / R;
+  const double var = s2 / R - m * m;
+  mean[c] = (float)m;
+  stdv[c] = (float)sqrt(var > 0.0 ? var : 0.0);
+}
+
+// out[r][c] = (X[r][c] - shift[c]) * mul[c]
+__global__ void k_affine_cols(const float *__restrict__ X, size_t n, int C,
+                              const float *__restrict__ shift, const float *__restrict__ mul,
+                              float *__restrict__ out) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const int c = (int)(e % C);
+    out[e] = (X[e] - shift[c]) * mul[c];
+  }
+}
+
 }  // namespace specula
 
 using namespace specula;
+
+extern "C" int specula_col_stats(specula_ctx *ctx, const float *X_dev, int32_t rows,
+                                 int32_t cols, float *mean_dev, float *std_dev, void *stream) {
+  if (!ctx || !X_dev || !mean_dev || !std_dev || rows < 1 || cols < 1) return SPECULA_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  SPECULA_LAUNCH(ctx, SPECULA_K_MLP, st,
+                 k_col_stats<<<(cols + 127) / 128, 128, 0, st>>>(X_dev, rows, cols, mean_dev,
+                                                                 std_dev));
+  return SPECULA_OK;
+}
+
+extern "C" int specula_affine_cols(specula_ctx *ctx, const float *X_dev, int64_t rows,
+                                   int32_t cols, const float *shift_dev, const float *mul_dev,
+                                   float *out_dev, void *stream) {
+  if (!ctx || !X_dev || !shift_dev || !mul_dev || !out_dev || rows < 1 || cols < 1)
+    return SPECULA_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t n = (size_t)rows * cols;
+  SPECULA_LAUNCH(ctx, SPECULA_K_MLP, st,
+                 k_affine_cols<<<(unsigned)std::min<size_t>((n + 255) / 256, 8192), 256, 0, st>>>(
+                     X_dev, n, cols, shift_dev, mul_dev, out_dev));
+  return SPECULA_OK;
+}
 
 struct specula_mlp {
   specula_ctx *ctx = nullptr;
