@@ -228,6 +228,53 @@ def reference_leg(args, ws, rank):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ learned
+
+def learned_leg(ctx, n_train=200000, n_test=5000, epochs=12):
+    """The learned-reconstructor configuration (8 m pyramid geometry, 2512 ->
+    1024 -> 1024 -> 500): pairs generated by the GPU simulator, network
+    trained by the library's kernels, residual compared with the calibrated
+    linear MVM on held-out frames (disjoint sample indices)."""
+    import torch
+    import synth
+    from paper_2602_06688_gb300.learned import LearnedPipeline
+    wl = synth.workload("learned8m")
+    t0 = time.perf_counter()
+    p = LearnedPipeline(ctx, wl)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    Xtr, Ttr = p.make_pairs(n_train, 0)
+    Xte, Tte = p.make_pairs(n_test, 10 ** 6)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    hist = p.fit(Xtr, Ttr, epochs=epochs)
+    torch.cuda.synchronize()
+    t3 = time.perf_counter()
+    res = p.evaluate(Xte, Tte)
+    # batched inference throughput of both reconstructors on the test set
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    p.predict(Xte)
+    e1.record()
+    torch.cuda.synchronize()
+    mlp_ms = e0.elapsed_time(e1)
+    e0.record()
+    p.linear(Xte)
+    e1.record()
+    torch.cuda.synchronize()
+    lin_ms = e0.elapsed_time(e1)
+    return {"workload": "learned8m", "net": "2512-1024-1024-500 GELU (bf16 tcgen05, FP32 acc)",
+            "train_pairs": n_train, "test_pairs": n_test, "epochs": epochs, "batch": 256,
+            "r0_range_m": [0.06, 0.20],
+            "residual_rms_rad": {"linear_mvm": res["linear"], "learned": res["learned"],
+                                 "true_modes_rms": res["labels"]},
+            "learned_gain": res["linear"] / res["learned"],
+            "calibration_s": t1 - t0, "pair_generation_s": t2 - t1, "training_s": t3 - t2,
+            "final_train_loss": hist[-1],
+            "inference_frames_per_s": {"learned_batched": n_test / (mlp_ms / 1e3),
+                                       "linear_batched": n_test / (lin_ms / 1e3)}}
+
+
 # ------------------------------------------------------------------ GPU leg
 
 def gpu_leg(args, ws, rank, local):
@@ -308,8 +355,8 @@ def gpu_leg(args, ws, rank, local):
 
     # ---- precision variants of the reconstructor (same frame otherwise)
     variants = {}
-    R64 = fr.R.double()
-    ref_modes = (R64 @ fp32_slopes.double())
+    # FP64 reference product on the host for the error report
+    ref_modes = fr.R.cpu().numpy().astype(np.float64) @ fp32_slopes.cpu().numpy().astype(np.float64)
     for name, prec in (("fp32", sp.PREC_FP32), ("bf16x2", sp.PREC_BF16X2), ("bf16", sp.PREC_BF16)):
         fr.set_precision(prec)
         fr.graph.close()
@@ -320,11 +367,30 @@ def gpu_leg(args, ws, rank, local):
         out = torch.empty_like(fr.modes)
         sp.specula_recon(ctx, fr.rec, fp32_slopes, out)
         torch.cuda.synchronize()
-        err = float(torch.linalg.vector_norm(out.double() - ref_modes) /
-                    torch.linalg.vector_norm(ref_modes))
+        err = float(np.linalg.norm(out.cpu().numpy().astype(np.float64) - ref_modes) /
+                    np.linalg.norm(ref_modes))
         variants[name] = {"frames_per_s": K / (sum(msv) / 1e3), "ms_per_step": sum(msv) / K,
                           "modal_rel_rms_err_vs_fp64": err}
     fr.set_precision(sp.PREC_FP32)
+    # learned reconstructor at ELT scale in place of the MVM (frame timing;
+    # its accuracy is measured on the 8 m configuration below)
+    import synth as _synth
+    sizes = (fr.n_slopes, 2048, 2048, fr.n_modes)
+    mlp = sp.MLP(ctx, sizes, 128)
+    for l in range(3):
+        bnd = 1.0 / math.sqrt(sizes[l])
+        mlp.set_layer(l, _synth.uniform_draws(300 + 2 * l, (sizes[l + 1], sizes[l]), -bnd, bnd),
+                      _synth.uniform_draws(301 + 2 * l, (sizes[l + 1],), -bnd, bnd))
+    fr.use_learned(mlp)
+    fr.graph.close()
+    fr.capture(st)
+    timed(3, W)
+    msl = timed(K, W)
+    variants["learned_mlp"] = {"frames_per_s": K / (sum(msl) / 1e3), "ms_per_step": sum(msl) / K,
+                               "net": "%d-2048-2048-%d GELU, bf16 tcgen05 GEMMs, batch 1"
+                                      % (fr.n_slopes, fr.n_modes)}
+    fr.use_learned(None)
+    mlp.close()
     fr.graph.close()
     fr.capture(st)
 
@@ -400,6 +466,8 @@ def gpu_leg(args, ws, rank, local):
                         "note": "per step: pinned host time -> device, frame, modes -> pinned host, sync"},
                 "gpu_launches": launches, "clocks": clocks,
                 "peaks": {"source": how, "hbm_gbs": pk.get("hbm_gbs")}}
+        if not args.no_learned:
+            line["learned"] = learned_leg(ctx)
         if not args.no_cpu_baseline:
             sample = OracleSample()
             per = min(sample.step(0.001 * (k + 1)) for k in range(3))
@@ -419,6 +487,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="specula", choices=["specula", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-learned", action="store_true",
+                    help="skip the learned-reconstructor training run on the 8 m system")
     ap.add_argument("--quick", action="store_true",
                     help="headline frames only (no variants, tracing pass, e2e or baseline)")
     args = ap.parse_args()

@@ -63,6 +63,7 @@ class PwfsFrame:
         if R is None:
             R = seeded_reconstructor(self.n_modes, self.n_slopes, seed=7 + seed_offset)
         self.R = torch.tensor(np.asarray(R, dtype=np.float32), device=device)
+        self.learned = None
         self.set_precision(precision)
         # reference slopes: a flat wavefront in the same geometry
         specula_pwfs_image(ctx, self.pupil, self.pwfs, self.amp, self.phase, self.det)
@@ -123,5 +124,13 @@ class PwfsFrame:
         specula_pwfs_image(ctx, self.pupil, self.pwfs, self.amp, self.phase, self.det,
                            stream=stream)
         specula_slopes(ctx, self.slopec, self.det, self.ref, self.slopes, stream=stream)
-        specula_recon(ctx, self.rec, self.slopes, self.modes, stream=stream)
+        if self.learned is not None:
+            self.learned.forward(self.slopes.view(1, -1), self.modes.view(1, -1), stream=stream)
+        else:
+            specula_recon(ctx, self.rec, self.slopes, self.modes, stream=stream)
         return self.modes
+
+    def use_learned(self, mlp):
+        """Reconstruct with a learned network (an MLP handle sized n_slopes ->
+        ... -> n_modes) instead of the linear MVM; None restores the MVM."""
+        self.learned = mlp
