@@ -405,7 +405,10 @@ int specula_gemm_bf16(specula_ctx *ctx, const void *A_dev, const void *B_dev, in
  * the tcgen05 GEMMs, FP32 accumulation.  Hidden widths must be multiples of
  * 128; the input/output widths and the batch are padded internally.
  * create/destroy/set/get may allocate and synchronise; forward, backward and
- * adam only enqueue.  One model per stream at a time. */
+ * adam only enqueue.  One model per stream at a time.  The model keeps a
+ * pointer to its context: destroy it before the context (destroy itself
+ * does not touch the context, so a late destroy is harmless, but any other
+ * call on a model whose context is gone is undefined). */
 typedef struct specula_mlp specula_mlp;
 int specula_mlp_create(specula_ctx *ctx, int32_t n_in, int32_t n_h1, int32_t n_h2,
                        int32_t n_out, int32_t batch_max, specula_mlp **out);

@@ -7,6 +7,7 @@ runs in the library's CUDA kernels.  A missing library raises ImportError at
 first use — there is no fallback path.
 """
 import ctypes as C
+import weakref
 
 import numpy as np
 
@@ -81,9 +82,13 @@ class Context:
         _abi.check(lib().specula_ctx_create(C.byref(h), int(device)), "specula_ctx_create")
         self.handle = h
         self.device = device
+        # models created on this context; closed first so none outlives it
+        self._children = weakref.WeakSet()
 
     def close(self):
         if self.handle:
+            for ch in list(self._children):
+                ch.close()
             lib().specula_ctx_destroy(self.handle)
             self.handle = None
 
@@ -460,6 +465,7 @@ class MLP:
         _abi.check(lib().specula_mlp_create(ctx.handle, int(n_in), int(h1), int(h2), int(n_out),
                                             int(batch_max), C.byref(h)), "specula_mlp_create")
         self.handle, self.sizes = h, tuple(sizes)
+        ctx._children.add(self)
 
     def close(self):
         if self.handle:

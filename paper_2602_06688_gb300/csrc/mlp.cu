@@ -218,6 +218,7 @@ extern "C" int specula_affine_cols(specula_ctx *ctx, const float *X_dev, int64_t
 
 struct specula_mlp {
   specula_ctx *ctx = nullptr;
+  int device = 0;  // copied from ctx so destroy never dereferences it
   int n[4];        // true widths: n_in, h1, h2, n_out
   int np[4];       // padded widths
   int bmax;        // padded batch capacity
@@ -263,6 +264,7 @@ extern "C" int specula_mlp_create(specula_ctx *ctx, int32_t n_in, int32_t n_h1, 
   SPECULA_CK(cudaSetDevice(ctx->device));
   std::unique_ptr<specula_mlp> p(new specula_mlp());
   p->ctx = ctx;
+  p->device = ctx->device;
   p->n[0] = n_in; p->n[1] = n_h1; p->n[2] = n_h2; p->n[3] = n_out;
   p->np[0] = round_up(n_in, 128); p->np[1] = n_h1; p->np[2] = n_h2; p->np[3] = round_up(n_out, 128);
   p->bmax = round_up(batch_max, 128);
@@ -317,7 +319,7 @@ extern "C" int specula_mlp_create(specula_ctx *ctx, int32_t n_in, int32_t n_h1, 
 
 extern "C" int specula_mlp_destroy(specula_mlp *mlp) {
   if (!mlp) return SPECULA_EINVAL;
-  cudaSetDevice(mlp->ctx->device);
+  cudaSetDevice(mlp->device);
   cudaDeviceSynchronize();
   delete mlp;
   return SPECULA_OK;

@@ -129,3 +129,22 @@ def test_training_reduces_loss_and_is_deterministic(env):
     assert l1 == l2
     for l in range(3):
         assert np.array_equal(m1.get_layer(l)[0], m2.get_layer(l)[0])
+
+
+def test_model_outliving_its_context_leaves_no_error(env):
+    """Closing a context closes the models made on it; a model used after
+    that raises, and later contexts and models work normally."""
+    torch, sp, _ = env
+    c2 = sp.Context(0)
+    m = sp.MLP(c2, SIZES, 128)
+    c2.close()
+    assert m.handle is None
+    with pytest.raises(sp.SpeculaError):
+        m.forward(torch.zeros(4, SIZES[0], device="cuda"))
+    c3 = sp.Context(0)
+    m3 = _model(sp, c3, _params32(SIZES, seed=3), SIZES, 128)
+    Y = torch.empty(4, SIZES[3], device="cuda")
+    m3.forward(torch.zeros(4, SIZES[0], device="cuda"), Y)
+    torch.cuda.synchronize()
+    assert torch.isfinite(Y).all()
+    c3.close()
