@@ -275,6 +275,35 @@ def learned_leg(ctx, n_train=200000, n_test=5000, epochs=12):
                                        "linear_batched": n_test / (lin_ms / 1e3)}}
 
 
+def gemm_leg(ctx, pk, n=8192, reps=10):
+    """The tcgen05 BF16 GEMM (C = A B^T, FP32 accumulate) on an n^3 problem,
+    against the measured cuBLAS BF16 burst peak."""
+    import torch
+    import paper_2602_06688_gb300 as sp
+    g = torch.Generator(device="cuda").manual_seed(11)
+    A = torch.randn(n, n, device="cuda", generator=g).to(torch.bfloat16)
+    B = torch.randn(n, n, device="cuda", generator=g).to(torch.bfloat16)
+    Cm = torch.empty(n, n, device="cuda")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    best = float("inf")
+    for _ in range(3):
+        sp.specula_gemm_bf16(ctx, A, B, Cm)
+    for _ in range(reps):
+        e0.record()
+        sp.specula_gemm_bf16(ctx, A, B, Cm)
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    tf = 2.0 * n ** 3 / (best / 1e3) / 1e12
+    peak = pk.get("bf16_tflops")
+    out = {"kernel": "k_gemm_bf16_tn (TMA + tcgen05, 128x128 tiles, TMEM accumulator)",
+           "shape": [n, n, n], "best_ms": best, "achieved_tflops": tf,
+           "peak_tflops": peak, "frac": (tf / peak) if peak else None,
+           "peak_source": "measured cuBLAS bf16 burst" if peak else None}
+    del A, B, Cm
+    return out
+
+
 # ------------------------------------------------------------------ GPU leg
 
 def gpu_leg(args, ws, rank, local):
@@ -468,6 +497,7 @@ def gpu_leg(args, ws, rank, local):
                 "peaks": {"source": how, "hbm_gbs": pk.get("hbm_gbs")}}
         if not args.no_learned:
             line["learned"] = learned_leg(ctx)
+            line["gemm_bf16"] = gemm_leg(ctx, pk)
         if not args.no_cpu_baseline:
             sample = OracleSample()
             per = min(sample.step(0.001 * (k + 1)) for k in range(3))

@@ -82,7 +82,7 @@ typedef struct {
 /* Modulated pyramid (ModulatedPyramid, Listing 2): FFT side N = pad * n_pix;
  * n_mod modulation points on a circle of mod_amp lambda/D; images binned to
  * n_sub x n_sub per pupil image; pup_dist_px = separation of the pupil images
- * (this build supports pad = 2 and pup_dist_px = n_pix, where the four
+ * (this library supports pad = 2 and pup_dist_px = n_pix, where the four
  * images tile the padded grid). */
 typedef struct {
   int32_t pad, n_mod, n_sub, pup_dist_px;
@@ -153,7 +153,8 @@ int specula_ctx_status(specula_ctx *ctx, int32_t *device_status);
 #define SPECULA_K_CALIB         9   /* calibration kernels (IM, float64 algebra)  */
 #define SPECULA_K_GEMM          10  /* tcgen05 BF16 GEMM and split-K reduction    */
 #define SPECULA_K_MLP           11  /* learned-reconstructor element-wise kernels */
-#define SPECULA_K_COUNT         12
+#define SPECULA_K_MWFS          12  /* multi-sensor frame, one persistent launch  */
+#define SPECULA_K_COUNT         13
 
 /* Enable (capacity > 0: room for that many kernel records; allocates CUDA
  * events; set-up call) or disable (capacity = 0) per-kernel event timing.
@@ -384,11 +385,80 @@ int specula_recon_convert(specula_ctx *ctx, int32_t n_modes, int32_t n_slopes,
                           const float *R_dev, int32_t precision, void *hi_dev,
                           void *lo_dev, void *stream);
 
+/* ---- multi-sensor system in one persistent launch ---------------------------
+ * All wavefront sensors of a system (Shack-Hartmann and pyramids of different
+ * sizes, each with its own guide star), their slopes and the reconstructor
+ * product on the concatenated slopes, computed by one kernel launch per
+ * frame (the multi-sensor systems of Sect. 6, Tab. 2; App. A, Tab. 4:
+ * AtmoPropagation per source, SH / ModulatedPyramid, ShSlopec / PyrSlopec,
+ * Modalrec).  Each sensor computes what the single-sensor calls compute:
+ * specula_atmo_extract for its source, then specula_sh_image +
+ * SPECULA_SLOPES_SH (centre of gravity taken directly from the spot, which is
+ * not stored) or specula_pwfs_image + SPECULA_SLOPES_PYR; the reconstructor
+ * is modes = R slopes with R n_modes x n_slopes float32, summed per sensor
+ * then over sensors in sensor order.  Every sensor's valid subapertures come
+ * from the geometric rule of specula_valid_subaps_host.  Built kernel
+ * variants: pyramids with FFT side 128 or 240 (one side per system, pad 2,
+ * pup_dist_px = n_pix, b = n_pix / n_sub <= 16); SH with sub_pix 12 and
+ * fft_n 24.  Up to 16 sensors and 64 layers. */
+#define SPECULA_WFS_PYR 0
+#define SPECULA_WFS_SH  1
+typedef struct {
+  int32_t kind;                 /* SPECULA_WFS_PYR or SPECULA_WFS_SH   */
+  specula_pupil_desc pupil;
+  specula_source_desc source;
+  specula_pwfs_desc pwfs;       /* kind PYR                            */
+  specula_sh_desc sh;           /* kind SH                             */
+} specula_wfs_desc;
+typedef struct specula_mwfs specula_mwfs;
+
+/* Plan the system (set-up call: allocates, synchronises).  screens_dev is a
+ * host array of n_layers device pointers and R_dev (n_modes x n_slopes
+ * float32, NULL when n_modes = 0) is device memory; the library keeps these
+ * pointers, so they must stay valid until specula_mwfs_destroy.  Slopes are
+ * concatenated in sensor order, each sensor's block all x then all y
+ * (specula_mwfs_info gives the offsets). */
+int specula_mwfs_create(specula_ctx *ctx, int32_t n_sensors, const specula_wfs_desc *sensors,
+                        int32_t n_layers, const specula_layer_desc *layers,
+                        const float *const *screens_dev, int32_t n_modes, const float *R_dev,
+                        specula_mwfs **out);
+int specula_mwfs_destroy(specula_mwfs *mwfs);
+/* Per-sensor valid-subaperture count and slope offset (sensor >= 0), and
+ * the total slope count (any sensor; pass -1 for the total only). */
+int specula_mwfs_info(const specula_mwfs *mwfs, int32_t sensor, int32_t *n_valid,
+                      int32_t *slope_offset, int32_t *n_slopes_total);
+/* Number of tasks of one frame, CTAs launched, and the most CTAs that fit
+ * on the device at once. */
+int specula_mwfs_schedule(const specula_mwfs *mwfs, int32_t *n_tasks, int32_t *grid,
+                          int32_t *max_grid);
+/* CTAs per launch (0: as many as fit); the frame's result does not depend on
+ * it except for float rounding order, which it does not change either
+ * (every reduction has a fixed order). */
+int specula_mwfs_set_grid(specula_mwfs *mwfs, int32_t ctas);
+/* One frame at time t (t = *t_dev if t_dev is not NULL): slopes_dev
+ * (n_slopes floats) minus ref_dev (nullable, same layout), and modes_dev
+ * (n_modes floats; must be NULL exactly when n_modes = 0).  Per-frame call:
+ * enqueues one kernel, allocates nothing.  A dependency wait longer than 2 s
+ * ends the launch early with SPECULA_ETIMEOUT in the context status word. */
+int specula_mwfs_frame(specula_mwfs *mwfs, double t_s, const double *t_dev,
+                       const float *ref_dev, float *slopes_dev, float *modes_dev, void *stream);
+/* Slopes of a flat wavefront (no layers), no reference subtracted: the
+ * reference slopes of every sensor in one launch. */
+int specula_mwfs_reference(specula_mwfs *mwfs, float *ref_dev, float *modes_dev, void *stream);
+/* Copy sensor `sensor`'s last phase (n_pix^2 floats, radians at its
+ * wavelength; a Shack-Hartmann sensor's phase is computed on the pixels of
+ * its valid subapertures only and is 0 elsewhere) or pyramid detector
+ * ((2 n_sub)^2 floats) into dst_dev. */
+#define SPECULA_MWFS_PHASE    0
+#define SPECULA_MWFS_DETECTOR 1
+int specula_mwfs_read(const specula_mwfs *mwfs, int32_t sensor, int32_t what, float *dst_dev,
+                      void *stream);
+
 /* ---- tensor-core GEMM ---------------------------------------------------------
  * C[M][N] = A[M][K] . B[N][K]^T with A, B bfloat16 row-major (both K-major),
  * accumulated in float32 on the tcgen05 tensor cores; C float32 row-major.
- * The dense contractions of the learned reconstructor use it (BASELINE's
- * learned part; the paper's Modalrec is the MVM above).  M and N multiples
+ * The dense contractions of the learned reconstructor use it (the paper's
+ * own reconstructor, Modalrec, is the MVM above).  M and N multiples
  * of 128, K a multiple of 64, A and B 16-byte aligned.  splits > 1 divides K
  * into slices computed by separate CTAs whose float32 partials go to work_dev
  * (splits * M * N floats, caller-owned) and are summed in slice order.
@@ -400,8 +470,8 @@ int specula_gemm_bf16(specula_ctx *ctx, const void *A_dev, const void *B_dev, in
 /* ---- learned reconstructor ----------------------------------------------------
  * A perceptron slopes -> modal coefficients, n_in -> n_h1 -> n_h2 -> n_out with
  * exact-erf GELU between layers (not in the paper, whose reconstructor is
- * the linear Modalrec; the learned part follows the configuration this
- * library targets).  FP32 master weights and Adam moments, bf16 copies for
+ * the linear Modalrec; a nonlinear alternative to it, trained on pairs the
+ * simulator generates).  FP32 master weights and Adam moments, bf16 copies for
  * the tcgen05 GEMMs, FP32 accumulation.  Hidden widths must be multiples of
  * 128; the input/output widths and the batch are padded internally.
  * create/destroy/set/get may allocate and synchronise; forward, backward and

@@ -36,4 +36,19 @@ Modules and their pins (tests/test_oracle_*.py):
 * ``slopes``    pyramid and centre-of-gravity slopes; pinned through the
                 pyramid / SH invariants above and hand-computed detectors.
 * ``recon``     modal reconstructor MVM; pinned to a direct sum.
+* ``modal``     Zernike modal basis (Noll order) and least-squares projection;
+                pinned to the Noll table, closed forms of low orders,
+                continuous orthonormality and exact coefficient recovery.
+* ``calib``     push-pull interaction matrix and truncated pseudo-inverse;
+                pinned to the Penrose conditions, tip/tilt transpose symmetry
+                and sign, and reconstructor closure R IM = I on kept modes.
+* ``mlp``       learned reconstructor (GELU perceptron, MSE, Adam); pinned to
+                erf values of GELU, central finite differences of the
+                backward pass, the first Adam step and a training decrease.
+* ``philox``    Philox4x32-10 counter-based generator and Box-Muller normals;
+                pinned to the published known-answer vectors.
+* ``system``    a multi-sensor system: the chains above per sensor, slopes
+                concatenated; pinned to zero slopes for flat screens, equal
+                SH slopes in every subaperture for a linear phase ramp, and
+                block-wise agreement with the single-sensor chains.
 """

@@ -13,7 +13,7 @@ import numpy as np
 
 from . import _abi
 from ._abi import (  # noqa: F401
-    PupilDesc, SourceDesc, LayerDesc, PwfsDesc, ShDesc, SlopecDesc, ReconDesc,
+    PupilDesc, SourceDesc, LayerDesc, PwfsDesc, ShDesc, SlopecDesc, ReconDesc, WfsDesc,
     SpeculaError, SLOPES_PYR, SLOPES_SH, PREC_FP32, PREC_BF16, PREC_BF16X2,
     OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED, ENONFINITE, ENOPLAN,
 )
@@ -124,10 +124,10 @@ def specula_ctx_status(ctx):
 
 
 (K_PWFS_ROWS_FWD, K_PWFS_COLS, K_PWFS_ROWS_INV, K_ATMO, K_SLOPES, K_RECON, K_SH,
- K_PWFS_FIELD, K_PWFS_BIN, K_CALIB, K_GEMM, K_MLP) = range(12)
-K_COUNT = 12
+ K_PWFS_FIELD, K_PWFS_BIN, K_CALIB, K_GEMM, K_MLP, K_MWFS) = range(13)
+K_COUNT = 13
 KERNEL_NAMES = ["pwfs_rows_fwd", "pwfs_cols", "pwfs_rows_inv", "atmo_extract", "slopes",
-                "recon", "sh_spots", "pwfs_field", "pwfs_bin", "calib", "gemm", "mlp"]
+                "recon", "sh_spots", "pwfs_field", "pwfs_bin", "calib", "gemm", "mlp", "mwfs"]
 
 
 def specula_prof_enable(ctx, capacity):
@@ -611,3 +611,135 @@ def recon_desc(n_modes, n_slopes, precision, R_dev, R_lo_dev=None):
     return ReconDesc(int(n_modes), int(n_slopes), int(precision), C.c_void_p(R_dev.data_ptr()),
                      C.c_void_p(R_lo_dev.data_ptr()) if R_lo_dev is not None else None)
 
+
+# ---- multi-sensor system in one persistent launch -----------------------------------
+WFS_PYR, WFS_SH = 0, 1
+MWFS_PHASE, MWFS_DETECTOR = 0, 1
+
+
+def wfs_desc(sensor):
+    """WfsDesc from a workload sensor (kind 'pwfs' or 'sh')."""
+    d = WfsDesc()
+    d.pupil = pupil_desc(sensor.pupil)
+    d.source = source_desc(sensor.source)
+    if sensor.kind == "pwfs":
+        d.kind = WFS_PYR
+        d.pwfs = pwfs_desc(sensor.pwfs)
+    elif sensor.kind == "sh":
+        d.kind = WFS_SH
+        g = sensor.sh
+        d.sh = ShDesc(g.n_sub, g.sub_pix, g.fft_n)
+    else:
+        raise ValueError(sensor.kind)
+    return d
+
+
+class Mwfs:
+    """Multi-sensor system (specula_mwfs_*): every sensor, the slopes and the
+    reconstructor product in one persistent launch per frame.  Keeps
+    references to the screens and R, whose device memory the library uses."""
+
+    def __init__(self, ctx, sensors, layers, screens, R=None):
+        import torch
+        descs = (WfsDesc * len(sensors))(*sensors)
+        lds = (LayerDesc * len(layers))(*layers)
+        for t in screens:
+            _dev(t, torch.float32, None, "screen")
+        ptrs = (C.c_void_p * len(screens))(*[t.data_ptr() for t in screens])
+        n_modes = 0 if R is None else int(R.shape[0])
+        h = C.c_void_p()
+        _abi.check(lib().specula_mwfs_create(
+            ctx.handle, len(sensors), descs, len(layers), lds, ptrs, n_modes,
+            _dev(R, torch.float32, None, "R"), C.byref(h)), "specula_mwfs_create")
+        self.handle = h
+        self._keep = (list(screens), R)
+        self.n_sensors, self.n_modes = len(sensors), n_modes
+        tot = C.c_int32()
+        _abi.check(lib().specula_mwfs_info(h, -1, None, None, C.byref(tot)), "specula_mwfs_info")
+        self.n_slopes = tot.value
+        if R is not None and R.shape[1] != self.n_slopes:
+            self.close()
+            raise ValueError(f"R must have {self.n_slopes} columns")
+        self.n_valid, self.slope_offset = [], []
+        for k in range(len(sensors)):
+            nv, off = C.c_int32(), C.c_int32()
+            _abi.check(lib().specula_mwfs_info(h, k, C.byref(nv), C.byref(off), None),
+                       "specula_mwfs_info")
+            self.n_valid.append(nv.value)
+            self.slope_offset.append(off.value)
+        ctx._children.add(self)
+
+    def close(self):
+        if self.handle:
+            lib().specula_mwfs_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def schedule(self):
+        nt, g, mg = C.c_int32(), C.c_int32(), C.c_int32()
+        _abi.check(lib().specula_mwfs_schedule(self.handle, C.byref(nt), C.byref(g), C.byref(mg)),
+                   "specula_mwfs_schedule")
+        return {"n_tasks": nt.value, "grid": g.value, "max_grid": mg.value}
+
+    def set_grid(self, ctas):
+        _abi.check(lib().specula_mwfs_set_grid(self.handle, int(ctas)), "specula_mwfs_set_grid")
+
+    def frame(self, t, slopes, modes=None, ref=None, t_dev=None, stream=None):
+        import torch
+        _abi.check(lib().specula_mwfs_frame(
+            self.handle, float(t), _dev(t_dev, torch.float64, 1, "t_dev"),
+            _dev(ref, torch.float32, self.n_slopes, "ref"),
+            _dev(slopes, torch.float32, self.n_slopes, "slopes"),
+            _dev(modes, torch.float32, self.n_modes, "modes"), _stream(stream)),
+            "specula_mwfs_frame")
+
+    def reference(self, ref, modes=None, stream=None):
+        import torch
+        _abi.check(lib().specula_mwfs_reference(
+            self.handle, _dev(ref, torch.float32, self.n_slopes, "ref"),
+            _dev(modes, torch.float32, self.n_modes, "modes"), _stream(stream)),
+            "specula_mwfs_reference")
+
+    def read(self, sensor, what, dst, stream=None):
+        import torch
+        _abi.check(lib().specula_mwfs_read(self.handle, int(sensor), int(what),
+                                           _dev(dst, torch.float32, None, "dst"), _stream(stream)),
+                   "specula_mwfs_read")
+
+
+def specula_mwfs_create(ctx, sensors, layers, screens, R=None):
+    return Mwfs(ctx, sensors, layers, screens, R)
+
+
+def specula_mwfs_destroy(m):
+    m.close()
+
+
+def specula_mwfs_frame(m, t, slopes, modes=None, ref=None, t_dev=None, stream=None):
+    m.frame(t, slopes, modes, ref, t_dev, stream)
+
+
+def specula_mwfs_reference(m, ref, modes=None, stream=None):
+    m.reference(ref, modes, stream)
+
+
+def specula_mwfs_read(m, sensor, what, dst, stream=None):
+    m.read(sensor, what, dst, stream)
+
+
+def specula_mwfs_info(m):
+    return {"n_valid": list(m.n_valid), "slope_offset": list(m.slope_offset),
+            "n_slopes": m.n_slopes}
+
+
+def specula_mwfs_schedule(m):
+    return m.schedule()
+
+
+def specula_mwfs_set_grid(m, ctas):
+    m.set_grid(ctas)

@@ -47,6 +47,11 @@ class SlopecDesc(C.Structure):
                 ("subap_idx_dev", C.c_void_p)]
 
 
+class WfsDesc(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("pupil", PupilDesc), ("source", SourceDesc),
+                ("pwfs", PwfsDesc), ("sh", ShDesc)]
+
+
 class ReconDesc(C.Structure):
     _fields_ = [("n_modes", C.c_int32), ("n_slopes", C.c_int32),
                 ("precision", C.c_int32), ("R_dev", C.c_void_p),
@@ -114,6 +119,15 @@ SIGNATURES = {
     "specula_calib_intmat": (C.c_int, [vp, P(PupilDesc), P(PwfsDesc), vp, vp, i32, dbl,
                                        P(SlopecDesc), vp, vp]),
     "specula_pinv_fp64": (C.c_int, [vp, vp, i32, i32, dbl, vp, vp, P(i32), vp]),
+    "specula_mwfs_create": (C.c_int, [vp, i32, P(WfsDesc), i32, P(LayerDesc), P(vp), i32, vp,
+                                      P(vp)]),
+    "specula_mwfs_destroy": (C.c_int, [vp]),
+    "specula_mwfs_info": (C.c_int, [vp, i32, P(i32), P(i32), P(i32)]),
+    "specula_mwfs_schedule": (C.c_int, [vp, P(i32), P(i32), P(i32)]),
+    "specula_mwfs_set_grid": (C.c_int, [vp, i32]),
+    "specula_mwfs_frame": (C.c_int, [vp, dbl, vp, vp, vp, vp, vp]),
+    "specula_mwfs_reference": (C.c_int, [vp, vp, vp, vp]),
+    "specula_mwfs_read": (C.c_int, [vp, i32, i32, vp, vp]),
 }
 
 _lib = None

@@ -16,7 +16,7 @@ extern "C" const char *specula_strerror(int s) {
     case SPECULA_ENOMEM: return "out of memory";
     case SPECULA_ECUDA: return "CUDA runtime error";
     case SPECULA_ETIMEOUT: return "bounded device wait expired";
-    case SPECULA_EUNSUPPORTED: return "size or option not supported by this build";
+    case SPECULA_EUNSUPPORTED: return "size or option not supported by this library";
     case SPECULA_ENONFINITE: return "non-finite value detected";
     case SPECULA_ENOPLAN: return "no plan for this geometry (call the plan function first)";
     default: return "unknown status";
@@ -46,6 +46,7 @@ extern "C" int specula_ctx_create(specula_ctx **out, int device) {
   }
   int s = pwfs_init_device();
   if (!s) s = sh_init_device();
+  if (!s) s = mwfs_init_device();
   if (!s) s = atmo_alloc_tables(c);
   if (s) {
     cudaFree(c->status_dev);

@@ -119,6 +119,7 @@ inline void prof_end(specula_ctx *c, int slot, int kid, cudaStream_t st) {
 // per-translation-unit device initialisation (constant tables)
 int pwfs_init_device();
 int sh_init_device();
+int mwfs_init_device();
 int atmo_alloc_tables(specula_ctx *ctx);
 
 // launchers implemented in the kernel translation units
@@ -146,6 +147,8 @@ int gemm_bf16_tn(specula_ctx *ctx, const void *A, const void *B, int M, int N, i
 
 int slopes_pyr_run(specula_ctx *ctx, const int32_t *idx, int n_sub, int n_valid,
                    const float *det, const float *ref, int n_batch, float *out, cudaStream_t st);
+
+bool pwfs_split_for(int N, int *N1, int *N2);
 
 // host geometry (api.cu)
 int host_pupil_mask(int n, double obsc, uint8_t *mask);

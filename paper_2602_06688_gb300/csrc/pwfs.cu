@@ -39,27 +39,13 @@
 
 #include "fft_regs.cuh"
 #include "internal.h"
+#include "pwfs_common.cuh"
 
 namespace specula {
 
 int pwfs_init_device() {
   return upload_codelet_twiddles() == cudaSuccess ? SPECULA_OK : SPECULA_ECUDA;
 }
-
-template <int N1_, int N2_> struct Split {
-  static constexpr int N1 = N1_, N2 = N2_, N = N1_ * N2_;
-  static constexpr int MX = N1_ > N2_ ? N1_ : N2_;
-  static constexpr int G = MX <= 8 ? 8 : (MX <= 16 ? 16 : 32);  // lanes per vector
-  static constexpr int S1 = N1_ | 1;   // exchange stride, standard split (odd: no conflicts)
-  static constexpr int S2 = N2_ | 1;   // exchange stride, swapped split
-  static constexpr int XB = N2_ * S1;  // exchange buffer per vector (complex)
-  static_assert(N2_ % 4 == 0, "pruned zero-padded input needs N2 % 4 == 0");
-  static_assert(MX <= 32, "one vector per warp at most");
-  static_assert(2 * XB >= N, "a vector's exchange buffer must hold N floats");
-};
-
-constexpr int round_cs(int base) { return base + ((2 - base % 16) + 16) % 16; }
-constexpr int imax3(int a, int b, int c) { return a > b ? (a > c ? a : c) : (b > c ? b : c); }
 
 __device__ __forceinline__ void cp_async8(void *smem_dst, const void *gsrc) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
@@ -406,7 +392,7 @@ static int run_split(specula_ctx *ctx, PwfsPlan *p, const float *amp, const floa
   return SPECULA_OK;
 }
 
-static bool split_for(int N, int *N1, int *N2) {
+bool pwfs_split_for(int N, int *N1, int *N2) {
   switch (N) {
     case 64: *N1 = 8; *N2 = 8; return true;
     case 128: *N1 = 8; *N2 = 16; return true;
@@ -520,30 +506,20 @@ static inline void exp_ipi(long long num, long long den, double *c, double *s) {
   *s = sin(a);
 }
 
-int pwfs_plan_build(specula_ctx *ctx, const specula_pupil_desc *pupil,
-                    const specula_pwfs_desc *d, PwfsPlan **out) {
-  const int Np = pupil->n_pix, N = d->pad * Np;
-  int N1, N2;
-  if (!split_for(N, &N1, &N2)) return SPECULA_EUNSUPPORTED;
-  std::unique_ptr<PwfsPlan> p(new PwfsPlan());
-  p->n_pix = Np; p->pad = d->pad; p->n_mod = d->n_mod; p->n_sub = d->n_sub;
-  p->pup_dist = d->pup_dist_px; p->mod_amp = d->mod_amp;
-  p->N = N; p->N1 = N1; p->N2 = N2;
-  int s = configure_for(p.get());
-  if (s) return s;
+void pwfs_host_tables(int Np, int N, int N1, int N2, int n_mod, double mod_amp, int pup_dist,
+                      PwfsTablesHost *t) {
   const int off = (N - Np) / 2;
-
   // modulation tilt x centred-DFT input phase, per axis, float64 -> float32
-  std::vector<float2> gx((size_t)d->n_mod * Np), gy((size_t)d->n_mod * Np);
-  for (int m = 0; m < d->n_mod; ++m) {
-    const double th = 2.0 * M_PI * m / d->n_mod;
+  std::vector<float2> gx((size_t)n_mod * Np), gy((size_t)n_mod * Np);
+  for (int m = 0; m < n_mod; ++m) {
+    const double th = 2.0 * M_PI * m / n_mod;
     const double ct = cos(th), sn = sin(th);
     for (int i = 0; i < Np; ++i) {
       const double x = (double)i - (Np - 1) / 2.0;
       double pc, ps;
       exp_ipi((long long)(N - 1) * (off + i), N, &pc, &ps);
-      const double ax = 2.0 * M_PI * d->mod_amp * x * ct / Np;
-      const double ay = 2.0 * M_PI * d->mod_amp * x * sn / Np;
+      const double ax = 2.0 * M_PI * mod_amp * x * ct / Np;
+      const double ay = 2.0 * M_PI * mod_amp * x * sn / Np;
       const double cx = cos(ax), sx = sin(ax), cy = cos(ay), sy = sin(ay);
       gx[(size_t)m * Np + i] = make_float2((float)(cx * pc - sx * ps), (float)(cx * ps + sx * pc));
       gy[(size_t)m * Np + i] = make_float2((float)(cy * pc - sy * ps), (float)(cy * ps + sy * pc));
@@ -556,7 +532,7 @@ int pwfs_plan_build(specula_ctx *ctx, const specula_pupil_desc *pupil,
     long long a = 2LL * k - N + 1;
     if (a < 0) a = -a;
     double c, sn;
-    exp_ipi(-(long long)d->pup_dist_px * a, 2LL * N, &c, &sn);
+    exp_ipi(-(long long)pup_dist * a, 2LL * N, &c, &sn);
     mk[k] = make_float2((float)(c / N), (float)(sn / N));
   }
   // inter-step twiddles (cos, sin)(2 pi (a b mod N) / N)
@@ -573,6 +549,27 @@ int pwfs_plan_build(specula_ctx *ctx, const specula_pupil_desc *pupil,
       exp_ipi(2LL * ((long long)a * b % N), N, &c, &sn);
       tb[a * N2 + b] = make_float2((float)c, (float)sn);
     }
+  t->gx = std::move(gx);
+  t->gy = std::move(gy);
+  t->mask = std::move(mk);
+  t->twA = std::move(ta);
+  t->twB = std::move(tb);
+}
+
+int pwfs_plan_build(specula_ctx *ctx, const specula_pupil_desc *pupil,
+                    const specula_pwfs_desc *d, PwfsPlan **out) {
+  const int Np = pupil->n_pix, N = d->pad * Np;
+  int N1, N2;
+  if (!pwfs_split_for(N, &N1, &N2)) return SPECULA_EUNSUPPORTED;
+  std::unique_ptr<PwfsPlan> p(new PwfsPlan());
+  p->n_pix = Np; p->pad = d->pad; p->n_mod = d->n_mod; p->n_sub = d->n_sub;
+  p->pup_dist = d->pup_dist_px; p->mod_amp = d->mod_amp;
+  p->N = N; p->N1 = N1; p->N2 = N2;
+  int s = configure_for(p.get());
+  if (s) return s;
+  PwfsTablesHost T;
+  pwfs_host_tables(Np, N, N1, N2, d->n_mod, d->mod_amp, d->pup_dist_px, &T);
+  const std::vector<float2> &gx = T.gx, &gy = T.gy, &mk = T.mask, &ta = T.twA, &tb = T.twB;
   if ((s = p->gx.upload(gx.data(), gx.size() * sizeof(float2)))) return s;
   if ((s = p->gy.upload(gy.data(), gy.size() * sizeof(float2)))) return s;
   if ((s = p->mask.upload(mk.data(), mk.size() * sizeof(float2)))) return s;

@@ -8,6 +8,7 @@ Five systems, shaped like the paper's (Sect. 6, Tab. 2; App. B, Listing 2):
 * ``mwfs39m``       6 LGS Shack-Hartmann (68x68 subaps of 12 px, 24^2 FFT) and
                     3 NGS pyramids (120 px, 240^2 FFT, 16 mod points), D = 39 m
 * ``pwfs39m``       one ELT-scale pyramid WFS, 480 px, 960^2 FFT, 48 mod points
+* ``mwfs8m_small``  a small multi-sensor system (2 SH + 2 pyramids) for tests
 
 Values the paper does not state are readings chosen here (obscuration of the
 39 m pupil, WFS wavelength 750 nm as in Listing 2, outer scale 40 m as in
@@ -163,6 +164,33 @@ def _mwfs39m():
                     n_frames=1000, dt_s=1e-3, r0_m=0.157)
 
 
+def _mwfs8m_small():
+    """A small multi-sensor system for parity tests: two laser-star SH (96 px,
+    8 x 8 subapertures of 12 px, 24^2 FFT) and two natural-star pyramids
+    (64 px, 128^2 FFT, 8 modulation points), three layers."""
+    D = 8.0
+    sh_pup = Pupil(96, D / 96, 0.2)
+    py_pup = Pupil(64, D / 64, 0.2)
+    sensors = []
+    for k in range(2):
+        a = math.radians(90.0 * k + 20.0)
+        sensors.append(Sensor('sh', sh_pup,
+                              Source(20 * ARCSEC * math.cos(a), 20 * ARCSEC * math.sin(a),
+                                     90e3, 589.0),
+                              sh=ShGeom(n_sub=8, sub_pix=12, fft_n=24)))
+    for k in range(2):
+        a = math.radians(180.0 * k + 45.0)
+        sensors.append(Sensor('pwfs', py_pup,
+                              Source(30 * ARCSEC * math.cos(a), 30 * ARCSEC * math.sin(a),
+                                     math.inf, 750.0),
+                              pwfs=PwfsGeom(pad=2, n_mod=8, mod_amp=3.0, n_sub=16,
+                                            pup_dist_px=64)))
+    h = np.array([0.0, 4e3, 10e3])
+    layers = _profile(6, 3, 0.15, h, [0.6, 0.3, 0.1], [5.0, 10.0, 20.0], 256, D / 96, 40.0, 6)
+    return Workload('mwfs8m_small', D, tuple(sensors), layers, n_modes=64,
+                    n_frames=100, dt_s=1e-3, r0_m=0.15)
+
+
 def _pwfs39m():
     D, n = 39.0, 480
     pup = Pupil(n, D / n, 0.28)
@@ -181,6 +209,7 @@ WORKLOADS = {
     'pwfs8m': _pwfs8m,
     'learned8m': _learned8m,
     'mwfs39m': _mwfs39m,
+    'mwfs8m_small': _mwfs8m_small,
     'pwfs39m': _pwfs39m,
 }
 
