@@ -58,7 +58,6 @@ constexpr int kMwMaxSensors = 16;
 constexpr int kMwMaxLayers = 64;
 constexpr int kMwShSubPerTask = 16;
 constexpr int kMwCoordsPerTask = kMwThreads;
-constexpr int kMwFieldPxPerTask = 2048;
 constexpr int kMwBinPerTask = 1024;
 constexpr int kMwMvmRows = 32;
 constexpr int kMwFinalRows = 1024;
@@ -90,6 +89,7 @@ struct MwSensor {
   int n_sub, n_valid, slope_off;
   const int32_t *valid;
   const float2 *pre;           // SH: [NF] centred-DFT input phase
+  unsigned long long win_ok;   // SH: bit l set if a task's span on layer l < side - 2
   int n_mod, nd, bsz, spt;     // pyramid
   const float2 *gx, *gy, *mask, *twA, *twB;
   float2 *field, *rows, *cols;
@@ -162,6 +162,13 @@ __device__ __forceinline__ float4 mw_ld_stream(const float4 *p) {
   return v;
 }
 
+__device__ __forceinline__ void cp_async4(void *smem_dst, const void *gsrc) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
 // ---- extraction ------------------------------------------------------------------
 // Table entries [e0, e1) of [layer][axis][pixel] (same arithmetic as
 // k_atmo_coords).  float64 throughput is low on this part, so the tasks are
@@ -192,68 +199,338 @@ __device__ void mw_coords(const MwParams &P, const MwSensor &S, int e0, int e1) 
   }
 }
 
-// Phase at pupil pixel (X, Y): bilinear periodic samples summed over the
+// Phase of a block of pupil pixels: bilinear periodic samples summed over the
 // layers in order, times 500 / lambda (the arithmetic of k_atmo_extract).
-__device__ __forceinline__ float mw_phase(const MwParams &P, const MwSensor &S, int X, int Y) {
-  float acc = 0.f;
-  if (!P.flat) {
-    const int n = S.n_pix;
-#pragma unroll 2
-    for (int l = 0; l < P.n_layers; ++l) {
-      const float *Sc = P.L[l].scr;
-      const int M = P.L[l].side;
-      const int ix0 = __ldcg(S.tab_i + (size_t)(2 * l) * n + X);
-      const float fx = __ldcg(S.tab_f + (size_t)(2 * l) * n + X);
-      const int iy0 = __ldcg(S.tab_i + (size_t)(2 * l + 1) * n + Y);
-      const float fy = __ldcg(S.tab_f + (size_t)(2 * l + 1) * n + Y);
-      const int ix1 = ix0 + 1 == M ? 0 : ix0 + 1;
-      const int iy1 = iy0 + 1 == M ? 0 : iy0 + 1;
-      const float s00 = __ldg(Sc + (size_t)iy0 * M + ix0), s01 = __ldg(Sc + (size_t)iy0 * M + ix1);
-      const float s10 = __ldg(Sc + (size_t)iy1 * M + ix0), s11 = __ldg(Sc + (size_t)iy1 * M + ix1);
-      const float a = s00 + fx * (s01 - s00);
-      const float b = s10 + fx * (s11 - s10);
-      acc += a + fy * (b - a);
+// The block's pixels use ncs distinct columns and nrs distinct rows (their
+// "slots"); pixel q < npx (thread q % 256, register q / 256) reads column
+// slot cs and row slot rs given by pix(q).  For each chunk of kMwLayerChunk
+// layers the CTA first stages the table entries of its slots in shared
+// memory (one round of independent L2 loads), then every thread issues the
+// screen gathers of all its pixels together.
+constexpr int kMwLayerChunk = 8;
+
+//
+// With WIN > 0 the caller guarantees that its column slots xf..xl and row
+// slots yf..yl are the extreme ones (the sampling coordinate grows with the
+// pupil coordinate when the layer is below the guide star): the screen
+// window they span, if it holds at most WIN samples, is staged in shared
+// memory with coalesced loads and the interpolation reads it there — the
+// same samples, so the same result as the direct gathers.
+template <int PPT, int WIN, class ColF, class RowF, class PixF>
+__device__ __forceinline__ void mw_extract_block(const MwParams &P, const MwSensor &S, int ncs,
+                                                 int nrs, ColF colX, RowF rowY, PixF pix, int npx,
+                                                 float (&acc)[PPT], int *s_i, float *s_f,
+                                                 float *s_win = nullptr, int xf = 0, int xl = 0,
+                                                 int yf = 0, int yl = 0) {
+#pragma unroll
+  for (int i = 0; i < PPT; ++i) acc[i] = 0.f;
+  if (P.flat) return;
+  const int n = S.n_pix;
+  const int per = ncs + nrs;
+  for (int l0 = 0; l0 < P.n_layers; l0 += kMwLayerChunk) {
+    const int lc = min(kMwLayerChunk, P.n_layers - l0);
+    __syncthreads();   // the previous chunk's readers are done
+    for (int e = threadIdx.x; e < lc * per; e += kMwThreads) {
+      const int l = e / per, r = e - l * per;
+      const size_t o = r < ncs ? (size_t)(2 * (l0 + l)) * n + colX(r)
+                               : (size_t)(2 * (l0 + l) + 1) * n + rowY(r - ncs);
+      s_i[e] = __ldcg(S.tab_i + o);
+      s_f[e] = __ldcg(S.tab_f + o);
+    }
+    __syncthreads();
+    for (int l = 0; l < lc; ++l) {
+      const float *Sc = P.L[l0 + l].scr;
+      const int M = P.L[l0 + l].side;
+      const int *ti = s_i + l * per;
+      const float *tf = s_f + l * per;
+      if (WIN > 0 && ((S.win_ok >> (l0 + l)) & 1ull)) {
+        const int x0 = ti[xf], y0 = ti[ncs + yf];
+        const int wx = (ti[xl] - x0 + M) % M + 2, wy = (ti[ncs + yl] - y0 + M) % M + 2;
+        if (wx * wy <= WIN && wx <= M && wy <= M) {   // uniform over the CTA
+          __syncthreads();   // the previous layer's window readers are done
+          for (int e = threadIdx.x; e < wx * wy; e += kMwThreads) {
+            const int r = e / wx, c = e - r * wx;
+            int yy = y0 + r, xx = x0 + c;
+            if (yy >= M) yy -= M;
+            if (xx >= M) xx -= M;
+            s_win[e] = __ldg(Sc + (size_t)yy * M + xx);
+          }
+          __syncthreads();
+#pragma unroll
+          for (int i = 0; i < PPT; ++i) {
+            const int q = threadIdx.x + i * kMwThreads;
+            if (q < npx) {
+              int cs, rs;
+              pix(q, cs, rs);
+              int cx = ti[cs] - x0, cy = ti[ncs + rs] - y0;
+              if (cx < 0) cx += M;
+              if (cy < 0) cy += M;
+              if (cx > wx - 2 || cy > wy - 2) {   // never with a valid task split
+                atomicExch(P.status, SPECULA_EINVAL);
+                cx = min(cx, wx - 2);
+                cy = min(cy, wy - 2);
+              }
+              const float fx = tf[cs], fy = tf[ncs + rs];
+              const float *w0 = s_win + cy * wx + cx;
+              const float s00 = w0[0], s01 = w0[1], s10 = w0[wx], s11 = w0[wx + 1];
+              const float a = s00 + fx * (s01 - s00);
+              const float b = s10 + fx * (s11 - s10);
+              acc[i] += a + fy * (b - a);
+            }
+          }
+          continue;
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < PPT; ++i) {
+        const int q = threadIdx.x + i * kMwThreads;
+        if (q < npx) {
+          int cs, rs;
+          pix(q, cs, rs);
+          const int ix0 = ti[cs], iy0 = ti[ncs + rs];
+          const float fx = tf[cs], fy = tf[ncs + rs];
+          const int ix1 = ix0 + 1 == M ? 0 : ix0 + 1;
+          const int iy1 = iy0 + 1 == M ? 0 : iy0 + 1;
+          const float s00 = __ldg(Sc + (size_t)iy0 * M + ix0);
+          const float s01 = __ldg(Sc + (size_t)iy0 * M + ix1);
+          const float s10 = __ldg(Sc + (size_t)iy1 * M + ix0);
+          const float s11 = __ldg(Sc + (size_t)iy1 * M + ix1);
+          const float a = s00 + fx * (s01 - s00);
+          const float b = s10 + fx * (s11 - s10);
+          acc[i] += a + fy * (b - a);
+        }
+      }
     }
   }
-  return acc * S.scale;
 }
 
-// Pyramid field of pixels [p0, p1) (row-major).
-__device__ void mw_field(const MwParams &P, const MwSensor &S, int p0, int p1) {
-  const int n = S.n_pix;
-  for (int e = p0 + threadIdx.x; e < p1; e += kMwThreads) {
-    const int Y = e / n, X = e - Y * n;
-    const float ph = mw_phase(P, S, X, Y);
-    S.phase[e] = ph;
-    float sv, cv;
-    sincosf(ph, &sv, &cv);
-    const float a = __ldg(S.amp + e);
-    S.field[e] = make_float2(a * cv, a * sv);
+constexpr int kMwFieldPx = 4 * kMwThreads;   // pixels per FIELD task (whole rows)
+
+// Pyramid field of rows [y0, y1) (at most kMwFieldPx pixels).
+__device__ void mw_field(const MwParams &P, const MwSensor &S, int y0, int y1, float2 *smem) {
+  const int n = S.n_pix, nr = y1 - y0;
+  int *s_i = reinterpret_cast<int *>(smem);
+  float *s_f = reinterpret_cast<float *>(s_i + kMwLayerChunk * (n + nr));
+  float acc[4];
+  mw_extract_block<4, 0>(
+      P, S, n, nr, [](int c) { return c; }, [y0](int r) { return y0 + r; },
+      [n](int q, int &cs, int &rs) {
+        rs = q / n;
+        cs = q - rs * n;
+      },
+      nr * n, acc, s_i, s_f);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int q = threadIdx.x + i * kMwThreads;
+    if (q < nr * n) {
+      const size_t e = (size_t)y0 * n + q;
+      const float ph = acc[i] * S.scale;
+      S.phase[e] = ph;
+      float sv, cv;
+      sincosf(ph, &sv, &cv);
+      const float a = __ldg(S.amp + e);
+      S.field[e] = make_float2(a * cv, a * sv);
+    }
   }
 }
 
 // ---- Shack-Hartmann ----------------------------------------------------------------
-// Subapertures [v0, v1): one warp per subaperture.  The spot arithmetic is
-// that of k_sh_spots; the centre of gravity is taken in registers.
+// Subapertures [v0, v1) (at most kMwShSubPerTask, one subaperture row,
+// ascending columns spanning fewer than kMwShSubPerTask: the host split).
+// The CTA extracts the phase of their pixels as one strip of SP rows x
+// W = kMwShSubPerTask SP column slots (slot c: subaperture c / SP, column
+// c % SP), then one warp per subaperture images it: the spot arithmetic of
+// k_sh_spots, with the centre of gravity taken in registers.
+template <int NF, int SP>
+struct MwShSmem {
+  static constexpr int W = kMwShSubPerTask * SP;                        // column slots
+  static constexpr int kPh = kMwShSubPerTask * SP * SP;                 // floats
+  static constexpr int kTab = 2 * kMwLayerChunk * (W + SP);             // int + float
+  static constexpr int kWin = 4096;                                     // one screen window
+  static constexpr int kFft = kMwWarps * NF * (SP | 1) * 2;            // floats
+  static_assert(kFft <= kTab + 2 * kWin, "the FFT exchange reuses the extraction space");
+  static_assert((W * SP) % kMwThreads == 0, "whole pixels per thread");
+  static constexpr size_t bytes = (size_t)(kPh + kTab + 2 * kWin + 2 * kMwShSubPerTask) * 4;
+};
+
+// Strip extraction: per chunk of layers the table entries of the W column
+// slots and SP rows go to shared memory; per layer, when the host marked
+// the layer's span as shorter than the screen (S.win_ok), the screen window
+// the strip samples is staged in shared memory with coalesced row loads
+// (the sampling coordinate grows with the pupil coordinate below the guide
+// star, so slots 0 and ns SP - 1, rows 0 and SP - 1 bound it) and the
+// interpolation reads it there; otherwise it gathers from the screen.  Both
+// read the same samples: the result is that of k_atmo_extract.
+template <int SP, int PPT>
+__device__ __forceinline__ void mw_sh_extract(const MwParams &P, const MwSensor &S, int ns,
+                                              const int *s_ab, int *s_i, float *s_f,
+                                              float *s_win, int win_cap, float (&acc)[PPT]) {
+  constexpr int W = kMwShSubPerTask * SP, PER = W + SP;
+#pragma unroll
+  for (int i = 0; i < PPT; ++i) acc[i] = 0.f;
+  if (P.flat) return;
+  const int n = S.n_pix, wc = ns * SP, arow = s_ab[0];
+  for (int l0 = 0; l0 < P.n_layers; l0 += kMwLayerChunk) {
+    const int lc = min(kMwLayerChunk, P.n_layers - l0);
+    __syncthreads();
+    // all of this thread's table loads in flight before any store
+    constexpr int TPT = (kMwLayerChunk * PER + kMwThreads - 1) / kMwThreads;
+    int vi[TPT];
+    float vf[TPT];
+#pragma unroll
+    for (int k = 0; k < TPT; ++k) {
+      const int e = threadIdx.x + k * kMwThreads;
+      if (e < lc * PER) {
+        const int l = e / PER, r = e - l * PER;
+        int pix, axis = 0;
+        if (r < W) {
+          const int c = r < wc ? r : wc - 1;   // unused slots repeat the last column
+          pix = s_ab[kMwShSubPerTask + c / SP] * SP + c % SP;
+        } else {
+          pix = arow * SP + (r - W);
+          axis = 1;
+        }
+        const size_t o = (size_t)(2 * (l0 + l) + axis) * n + pix;
+        vi[k] = __ldcg(S.tab_i + o);
+        vf[k] = __ldcg(S.tab_f + o);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < TPT; ++k) {
+      const int e = threadIdx.x + k * kMwThreads;
+      if (e < lc * PER) {
+        s_i[e] = vi[k];
+        s_f[e] = vf[k];
+      }
+    }
+    __syncthreads();
+    // windows double-buffered: layer l + 1's window is copied (cp.async)
+    // while layer l interpolates from the other buffer
+    auto win_geom = [&](int l, int &x0, int &y0, int &wx, int &wy) {
+      const int *ti = s_i + l * PER;
+      const int M = P.L[l0 + l].side;
+      x0 = ti[0];
+      y0 = ti[W];
+      wx = (ti[wc - 1] - x0 + M) % M + 2;
+      wy = (ti[W + SP - 1] - y0 + M) % M + 2;
+      return ((S.win_ok >> (l0 + l)) & 1ull) && wx * wy <= win_cap;
+    };
+    auto issue = [&](int l, float *buf) {
+      int x0, y0, wx, wy;
+      if (!win_geom(l, x0, y0, wx, wy)) return;
+      const float *Sc = P.L[l0 + l].scr;
+      const int M = P.L[l0 + l].side;
+      for (int c = threadIdx.x; c < wx; c += kMwThreads) {
+        int xx = x0 + c;
+        if (xx >= M) xx -= M;
+        for (int r = 0; r < wy; ++r) {
+          int yy = y0 + r;
+          if (yy >= M) yy -= M;
+          cp_async4(buf + r * wx + c, Sc + (size_t)yy * M + xx);
+        }
+      }
+    };
+    issue(0, s_win);
+    cp_async_commit();
+    for (int l = 0; l < lc; ++l) {
+      float *cur = s_win + (l & 1) * win_cap;
+      if (l + 1 < lc) issue(l + 1, s_win + ((l + 1) & 1) * win_cap);
+      cp_async_commit();
+      cp_async_wait_1();     // all but the newest group: layer l's window is in
+      __syncthreads();
+      const float *Sc = P.L[l0 + l].scr;
+      const int M = P.L[l0 + l].side;
+      const int *ti = s_i + l * PER;
+      const float *tf = s_f + l * PER;
+      int x0, y0, wx, wy;
+      if (win_geom(l, x0, y0, wx, wy)) {   // uniform over the CTA
+#pragma unroll
+        for (int i = 0; i < PPT; ++i) {
+          const int q = threadIdx.x + i * kMwThreads;
+          const int r = q / W, c = q - r * W;
+          if (c < wc) {
+            int cx = ti[c] - x0, cy = ti[W + r] - y0;
+            if (cx < 0) cx += M;
+            if (cy < 0) cy += M;
+            if (cx > wx - 2 || cy > wy - 2) {   // never with the host's task split
+              atomicExch(P.status, SPECULA_EINVAL);
+              cx = min(cx, wx - 2);
+              cy = min(cy, wy - 2);
+            }
+            const float fx = tf[c], fy = tf[W + r];
+            const float *w0 = cur + cy * wx + cx;
+            const float s00 = w0[0], s01 = w0[1], s10 = w0[wx], s11 = w0[wx + 1];
+            const float a = s00 + fx * (s01 - s00);
+            const float b = s10 + fx * (s11 - s10);
+            acc[i] += a + fy * (b - a);
+          }
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < PPT; ++i) {
+          const int q = threadIdx.x + i * kMwThreads;
+          const int r = q / W, c = q - r * W;
+          if (c < wc) {
+            const int ix0 = ti[c], iy0 = ti[W + r];
+            const float fx = tf[c], fy = tf[W + r];
+            const int ix1 = ix0 + 1 == M ? 0 : ix0 + 1;
+            const int iy1 = iy0 + 1 == M ? 0 : iy0 + 1;
+            const float s00 = __ldg(Sc + (size_t)iy0 * M + ix0);
+            const float s01 = __ldg(Sc + (size_t)iy0 * M + ix1);
+            const float s10 = __ldg(Sc + (size_t)iy1 * M + ix0);
+            const float s11 = __ldg(Sc + (size_t)iy1 * M + ix1);
+            const float a = s00 + fx * (s01 - s00);
+            const float b = s10 + fx * (s11 - s10);
+            acc[i] += a + fy * (b - a);
+          }
+        }
+      }
+      __syncthreads();   // readers of `cur` are done before it is refilled
+    }
+  }
+}
+
 template <int NF, int SP>
 __device__ void mw_sh(const MwParams &P, const MwSensor &S, int v0, int v1, float2 *smem) {
   constexpr int OFF = (NF - SP) / 2;
   constexpr int XS = SP | 1;
-  const int w = threadIdx.x / 32, lane = threadIdx.x % 32;
-  float2 *xs = smem + w * (NF * XS);
-  float *ph = reinterpret_cast<float *>(smem + kMwWarps * NF * XS) + w * SP * SP;
+  using L = MwShSmem<NF, SP>;
+  constexpr int W = L::W;
+  constexpr int PPT = W * SP / kMwThreads;
+  float *ph = reinterpret_cast<float *>(smem);
+  float *region = ph + L::kPh;                     // tables + window, then FFT exchange
+  float *s_win = region + L::kTab;                 // two windows
+  int *s_ab = reinterpret_cast<int *>(s_win + 2 * L::kWin);
+  const int ns = v1 - v0;
+  for (int k = threadIdx.x; k < ns; k += kMwThreads) {
+    const int idx = __ldg(S.valid + v0 + k);
+    s_ab[k] = idx / S.n_sub;
+    s_ab[kMwShSubPerTask + k] = idx % S.n_sub;
+  }
+  __syncthreads();
+  int *s_i = reinterpret_cast<int *>(region);
+  float *s_f = region + kMwLayerChunk * (W + SP);
+  float acc[PPT];
+  mw_sh_extract<SP, PPT>(P, S, ns, s_ab, s_i, s_f, s_win, L::kWin, acc);
   const int n = S.n_pix;
-  for (int v = v0 + w; v < v1; v += kMwWarps) {
-    const int idx = __ldg(S.valid + v);
-    const int a = idx / S.n_sub, bc = idx % S.n_sub;
-    for (int p = lane; p < SP * SP; p += 32) {
-      const int r = p / SP, c = p - r * SP;
-      const int X = bc * SP + c, Y = a * SP + r;
-      const float f = mw_phase(P, S, X, Y);
-      ph[p] = f;
-      S.phase[(size_t)Y * n + X] = f;
+#pragma unroll
+  for (int i = 0; i < PPT; ++i) {
+    const int q = threadIdx.x + i * kMwThreads;
+    const int r = q / W, cs = q - r * W;
+    if (cs < ns * SP) {
+      const int sub = cs / SP, c = cs % SP;
+      const float f = acc[i] * S.scale;
+      ph[sub * SP * SP + r * SP + c] = f;
+      S.phase[(size_t)(s_ab[sub] * SP + r) * n + (size_t)s_ab[kMwShSubPerTask + sub] * SP + c] = f;
     }
-    __syncwarp();
+  }
+  __syncthreads();
+  const int w = threadIdx.x / 32, lane = threadIdx.x % 32;
+  float2 *xs = reinterpret_cast<float2 *>(region) + w * (NF * XS);
+  for (int sub = w; sub < ns; sub += kMwWarps) {
+    const int v = v0 + sub;
+    const int a = s_ab[sub], bc = s_ab[kMwShSubPerTask + sub];
+    const float *phs = ph + sub * SP * SP;
     float2 vv[NF];
 #pragma unroll
     for (int q = 0; q < NF; ++q) vv[q] = make_float2(0.f, 0.f);
@@ -263,7 +540,7 @@ __device__ void mw_sh(const MwParams &P, const MwSensor &S, int v0, int v1, floa
 #pragma unroll
       for (int c = 0; c < SP; ++c) {
         float sv, cv;
-        sincosf(ph[lane * SP + c], &sv, &cv);
+        sincosf(phs[lane * SP + c], &sv, &cv);
         const float A = __ldg(am + c);
         vv[OFF + c] = cmul(cmul(make_float2(A * cv, A * sv), __ldg(S.pre + OFF + c)), py);
       }
@@ -588,7 +865,7 @@ __device__ void mw_final(const MwParams &P, int r0, int r1) {
 
 // ---- the persistent kernel ---------------------------------------------------------
 template <int PN1, int PN2, int NF, int SP>
-__global__ void __launch_bounds__(kMwThreads, 2) k_mwfs(const __grid_constant__ MwParams P) {
+__global__ void __launch_bounds__(kMwThreads, 3) k_mwfs(const __grid_constant__ MwParams P) {
   extern __shared__ __align__(16) float2 mw_smem[];
   __shared__ int s_t, s_ok;
   __shared__ float s_w[kMwWarps];
@@ -612,7 +889,7 @@ __global__ void __launch_bounds__(kMwThreads, 2) k_mwfs(const __grid_constant__ 
     const MwSensor &S = P.S[tk.sensor];
     switch (tk.type) {
       case MT_COORDS: mw_coords(P, S, tk.a, tk.b); break;
-      case MT_FIELD: mw_field(P, S, tk.a, tk.b); break;
+      case MT_FIELD: mw_field(P, S, tk.a, tk.b, mw_smem); break;
       case MT_SH:
         if constexpr (NF > 0) mw_sh<NF, SP>(P, S, tk.a, tk.b, mw_smem);
         break;
@@ -645,12 +922,13 @@ __global__ void __launch_bounds__(kMwThreads, 2) k_mwfs(const __grid_constant__ 
 }
 
 template <int PN1, int PN2, int NF, int SP>
-static size_t mw_smem_bytes(int max_slopes) {
+static size_t mw_smem_bytes(int max_slopes, int max_field_slots) {
   using Sp = Split<PN1, PN2>;
-  size_t b = (size_t)kMwWarps * NF * (SP | 1) * sizeof(float2) + (size_t)kMwWarps * SP * SP * 4;
+  size_t b = MwShSmem<NF, SP>::bytes;
   b = std::max(b, (size_t)(kMwThreads / Sp::G) * Sp::XB * sizeof(float2));   // rows, rinv
   b = std::max(b, MwCols<PN1, PN2>::smem);
   b = std::max(b, (size_t)max_slopes * sizeof(float));
+  b = std::max(b, (size_t)2 * kMwLayerChunk * max_field_slots * 4);            // field tables
   return (b + 15) / 16 * 16;
 }
 
@@ -659,7 +937,7 @@ typedef void (*MwKernel)(MwParams);
 struct MwVariant {
   int pn1, pn2, nf, sp;
   MwKernel fn;
-  size_t (*smem)(int);
+  size_t (*smem)(int, int);
 };
 
 static const MwVariant kMwVariants[] = {
@@ -680,6 +958,7 @@ struct specula_mwfs {
   DevBuf tasks, ctr, mpart;
   std::vector<MwTask> host_tasks;
   std::vector<int> n_valid, slope_off, kind, det_n;
+  std::vector<std::vector<int32_t>> valid_host;
   int n_slopes = 0;
   int grid = 0, max_grid = 0;
   size_t smem = 0;
@@ -693,26 +972,50 @@ struct specula_mwfs {
 
 namespace {
 
-// Dependency-aware proportional merge: emit A in order; after each A task
-// emit B tasks while B lags A proportionally and the next B task's
-// dependency counter has all its producers already emitted.
-void merge_lists(const std::vector<MwTask> &A, const std::vector<MwTask> &B,
-                 const std::vector<int> &produced_total, std::vector<int> &emitted,
-                 std::vector<MwTask> &out) {
-  size_t ib = 0;
-  auto ready = [&](const MwTask &t) {
-    return t.wait_ctr < 0 || emitted[t.wait_ctr] >= produced_total[t.wait_ctr];
+// Emit A in order and release the (independent of each other) tasks of B
+// once the last producer of their dependency went out at least `lag`
+// positions earlier (about two waves of CTAs: by the time a CTA takes such
+// a task, its dependency has most likely completed, so it does not idle).
+// From the first position where some B task is eligible, B tasks leave at a
+// steady rate over the rest of A, in the order they became eligible; what is
+// left follows A.
+void release_when_ready(const std::vector<MwTask> &A, const std::vector<MwTask> &B,
+                        const std::vector<int> &produced_total, std::vector<int> &emitted,
+                        std::vector<MwTask> &out, int lag) {
+  std::vector<long> last_pos(produced_total.size(), -1);
+  std::vector<char> pooled(B.size(), 0);
+  std::vector<size_t> pool;
+  size_t head = 0, n_out = 0;
+  long first = -1;
+  auto eligible = [&](const MwTask &t, long pos) {
+    if (t.wait_ctr < 0) return true;
+    return emitted[t.wait_ctr] >= produced_total[t.wait_ctr] && pos - last_pos[t.wait_ctr] >= lag;
+  };
+  auto refill = [&](long pos) {
+    for (size_t i = 0; i < B.size(); ++i)
+      if (!pooled[i] && eligible(B[i], pos)) {
+        pooled[i] = 1;
+        pool.push_back(i);
+      }
   };
   auto emit = [&](const MwTask &t) {
+    last_pos[t.done_ctr] = (long)out.size();
     out.push_back(t);
     emitted[t.done_ctr]++;
   };
   for (size_t ia = 0; ia < A.size(); ++ia) {
     emit(A[ia]);
-    while (ib < B.size() && (double)ib / B.size() <= (double)(ia + 1) / A.size() && ready(B[ib]))
-      emit(B[ib++]);
+    refill((long)out.size());
+    if (first < 0 && head < pool.size()) first = (long)ia;
+    if (first < 0) continue;
+    const double frac = (double)(ia + 1 - first) / (double)(A.size() - first);
+    while (head < pool.size() && (double)n_out < frac * B.size()) {
+      emit(B[pool[head++]]);
+      n_out++;
+    }
   }
-  while (ib < B.size()) emit(B[ib++]);
+  refill(1L << 40);
+  while (head < pool.size()) emit(B[pool[head++]]);
 }
 
 MwTask mk(int type, int sensor, int a, int b, int wait_ctr, int wait_val, int done_ctr) {
@@ -748,6 +1051,8 @@ extern "C" int specula_mwfs_create(specula_ctx *ctx, int32_t n_sensors,
     if (pu.n_pix < 2 || !(pu.pitch_m > 0) || !(pu.obsc_frac >= 0 && pu.obsc_frac < 1))
       return SPECULA_EINVAL;
     if (!(d.source.wavelength_nm > 0) || !(d.source.height_m > 0)) return SPECULA_EINVAL;
+    for (int l = 0; l < n_layers; ++l)   // the cone factor 1 - h/H must stay positive
+      if (!(layers[l].height_m < d.source.height_m)) return SPECULA_EUNSUPPORTED;
     if (d.kind == SPECULA_WFS_PYR) {
       const specula_pwfs_desc &g = d.pwfs;
       if (g.n_mod < 1 || g.n_sub < 1 || g.pad != 2 || g.pup_dist_px != pu.n_pix ||
@@ -755,6 +1060,7 @@ extern "C" int specula_mwfs_create(specula_ctx *ctx, int32_t n_sensors,
         return g.n_mod < 1 || g.n_sub < 1 ? SPECULA_EINVAL : SPECULA_EUNSUPPORTED;
       const int N = 2 * pu.n_pix;
       if (pN && pN != N) return SPECULA_EUNSUPPORTED;
+      if (pu.n_pix > kMwFieldPx) return SPECULA_EUNSUPPORTED;
       pN = N;
     } else if (d.kind == SPECULA_WFS_SH) {
       const specula_sh_desc &h = d.sh;
@@ -793,7 +1099,7 @@ extern "C" int specula_mwfs_create(specula_ctx *ctx, int32_t n_sensors,
   static_assert(Split<8, 16>::G == 16 && Split<15, 16>::G == 16, "one vector width");
   const int G = 16;   // lanes per vector of both supported pyramid splits
   int st = SPECULA_OK;
-  int off = 0, max_slopes = 0;
+  int off = 0, max_slopes = 0, max_field_slots = 0;
   for (int k = 0; k < n_sensors; ++k) {
     const specula_wfs_desc &d = sensors[k];
     MwSensor &S = P.S[k];
@@ -833,6 +1139,7 @@ extern "C" int specula_mwfs_create(specula_ctx *ctx, int32_t n_sensors,
     off += 2 * nv;
     max_slopes = std::max(max_slopes, 2 * nv);
     m->n_valid.push_back(nv);
+    m->valid_host.emplace_back(idx.begin(), idx.begin() + nv);
     m->slope_off.push_back(S.slope_off);
     m->kind.push_back(d.kind);
     if (d.kind == SPECULA_WFS_SH) {
@@ -847,6 +1154,17 @@ extern "C" int specula_mwfs_create(specula_ctx *ctx, int32_t n_sensors,
       SPECULA_CK(cudaMemcpy(b->p, pre.data(), NF * sizeof(float2), cudaMemcpyHostToDevice));
       S.pre = b->as<float2>();
       m->det_n.push_back(0);
+      // a task spans < kMwShSubPerTask subapertures of one row: its sampling
+      // span on layer l is at most (16 sub_pix - 1) r + 2 screen samples,
+      // r = pupil pitch (1 - h/H) / layer pitch; the window path needs it
+      // below the side, where the wrapped width equals the true width
+      S.win_ok = 0;
+      for (int l = 0; l < n_layers; ++l) {
+        const double cone = 1.0 - layers[l].height_m / d.source.height_m;
+        const double r = d.pupil.pitch_m * cone / layers[l].pitch_m;
+        const double span = (kMwShSubPerTask * d.sh.sub_pix - 1) * r + 3.0;
+        if (span < (double)layers[l].side - 2.0) S.win_ok |= 1ull << l;
+      }
     } else {
       const specula_pwfs_desc &g = d.pwfs;
       const int N = 2 * n;
@@ -916,18 +1234,29 @@ extern "C" int specula_mwfs_create(specula_ctx *ctx, int32_t n_sensors,
     const int n = S.n_pix;
     if (m->kind[k] == SPECULA_WFS_SH) {
       c_sh[k] = new_ctr();
-      for (int v0 = 0; v0 < S.n_valid; v0 += kMwShSubPerTask) {
-        L_sh_by[k].push_back(mk(MT_SH, k, v0, std::min(S.n_valid, v0 + kMwShSubPerTask),
-                                c_coords[k], n_coords[k], c_sh[k]));
+      // runs of valid subapertures in one row spanning < 16 columns, so a
+      // task's screen window stays small
+      const std::vector<int32_t> &vl = m->valid_host[k];
+      int v0 = 0;
+      while (v0 < S.n_valid) {
+        const int a0 = vl[v0] / S.n_sub, b0 = vl[v0] % S.n_sub;
+        int v1 = v0 + 1;
+        while (v1 < S.n_valid && v1 - v0 < kMwShSubPerTask && vl[v1] / S.n_sub == a0 &&
+               vl[v1] % S.n_sub - b0 < kMwShSubPerTask)
+          ++v1;
+        L_sh_by[k].push_back(mk(MT_SH, k, v0, v1, c_coords[k], n_coords[k], c_sh[k]));
         n_sh[k]++;
+        v0 = v1;
       }
       continue;
     }
     const int N = 2 * n;
     c_field[k] = new_ctr();
-    for (int p0 = 0; p0 < n * n; p0 += kMwFieldPxPerTask) {
-      L_field.push_back(mk(MT_FIELD, k, p0, std::min(n * n, p0 + kMwFieldPxPerTask), c_coords[k],
-                           n_coords[k], c_field[k]));
+    const int rpt = std::max(1, kMwFieldPx / n);
+    max_field_slots = std::max(max_field_slots, n + rpt);
+    for (int y0 = 0; y0 < n; y0 += rpt) {
+      L_field.push_back(mk(MT_FIELD, k, y0, std::min(n, y0 + rpt), c_coords[k], n_coords[k],
+                           c_field[k]));
       n_field[k]++;
     }
     const int nrg = (n + VPC - 1) / VPC, nct = N / TC, nsg = (S.nd + S.spt - 1) / S.spt;
@@ -978,18 +1307,18 @@ extern "C" int specula_mwfs_create(specula_ctx *ctx, int32_t n_sensors,
   auto count = [&](const std::vector<MwTask> &v) { for (auto &t : v) produced[t.done_ctr]++; };
   count(L_coords); count(L_field); count(L_pyr); count(L_mvm); count(L_final);
   for (auto &v : L_sh_by) count(v);
-  std::vector<MwTask> A, order, SH;
+  std::vector<MwTask> A, order;
   for (auto &t : L_coords) { order.push_back(t); emitted[t.done_ctr]++; }
   for (auto &t : L_field) { order.push_back(t); emitted[t.done_ctr]++; }
-  // SH subaperture tasks (ready once their coordinates are) fill the gaps
-  // between the dependent pyramid passes; the MVM tasks of each finished
-  // sensor are spread over what follows
-  for (auto &v : L_sh_by) SH.insert(SH.end(), v.begin(), v.end());
-  {
-    std::vector<int> em = emitted;
-    merge_lists(L_pyr, SH, produced, em, A);
-  }
-  merge_lists(A, L_mvm, produced, emitted, order);
+  // SH sensors one after another (each finishes early and its MVM tasks can
+  // stream R from HBM while the rest compute), then the pyramid passes, whose
+  // dependency chains the MVM tasks fill; the pyramids' own MVM tasks end
+  // the frame.
+  for (int k = 0; k < n_sensors; ++k) A.insert(A.end(), L_sh_by[k].begin(), L_sh_by[k].end());
+  A.insert(A.end(), L_pyr.begin(), L_pyr.end());
+  int sms = 0;
+  SPECULA_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
+  release_when_ready(A, L_mvm, produced, emitted, order, 4 * sms);
   for (auto &t : L_final) { order.push_back(t); emitted[t.done_ctr]++; }
   // every dependency precedes its consumer
   {
@@ -1009,14 +1338,12 @@ extern "C" int specula_mwfs_create(specula_ctx *ctx, int32_t n_sensors,
   P.n_ctr = nctr;
   P.status = ctx->status_dev;
 
-  m->smem = var->smem(max_slopes);
+  m->smem = var->smem(max_slopes, max_field_slots);
   if (m->smem > 227 * 1024) return SPECULA_EUNSUPPORTED;
   SPECULA_CK(cudaFuncSetAttribute(var->fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)m->smem));
   int occ = 0;
   SPECULA_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, var->fn, kMwThreads, m->smem));
-  int sms = 0;
-  SPECULA_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
   if (occ < 1) return SPECULA_EUNSUPPORTED;
   m->sm_count = sms;
   m->occupancy = occ;
