@@ -304,33 +304,89 @@ __device__ __forceinline__ void mw_extract_block(const MwParams &P, const MwSens
   }
 }
 
-constexpr int kMwFieldPx = 4 * kMwThreads;   // pixels per FIELD task (whole rows)
+constexpr int kMwFieldPx = kMwThreads;   // pixels per FIELD task (whole rows)
 
-// Pyramid field of rows [y0, y1) (at most kMwFieldPx pixels).
+// Pyramid field of rows [y0, y1) (at most kMwFieldPx pixels, one per
+// thread).  A pyramid's pupil samples the screens sparsely (several screen
+// samples apart), so there is no window to stage: per chunk of layers the
+// table entries go to shared memory, then each thread issues the gathers of
+// four layers at once before interpolating them in layer order.
 __device__ void mw_field(const MwParams &P, const MwSensor &S, int y0, int y1, float2 *smem) {
-  const int n = S.n_pix, nr = y1 - y0;
+  const int n = S.n_pix, nr = y1 - y0, per = n + nr;
   int *s_i = reinterpret_cast<int *>(smem);
-  float *s_f = reinterpret_cast<float *>(s_i + kMwLayerChunk * (n + nr));
-  float acc[4];
-  mw_extract_block<4, 0>(
-      P, S, n, nr, [](int c) { return c; }, [y0](int r) { return y0 + r; },
-      [n](int q, int &cs, int &rs) {
-        rs = q / n;
-        cs = q - rs * n;
-      },
-      nr * n, acc, s_i, s_f);
+  float *s_f = reinterpret_cast<float *>(s_i + kMwLayerChunk * per);
+  const int q = threadIdx.x;
+  const bool act = q < nr * n;
+  const int r = act ? q / n : 0, c = act ? q - r * n : 0;
+  float acc = 0.f;
+  if (!P.flat) {
+    for (int l0 = 0; l0 < P.n_layers; l0 += kMwLayerChunk) {
+      const int lc = min(kMwLayerChunk, P.n_layers - l0);
+      __syncthreads();
+      constexpr int TPT = 4;   // table entries per thread: chunk (n + rows) <= 4 x 256 (host check)
+      int vi[TPT];
+      float vf[TPT];
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int q = threadIdx.x + i * kMwThreads;
-    if (q < nr * n) {
-      const size_t e = (size_t)y0 * n + q;
-      const float ph = acc[i] * S.scale;
-      S.phase[e] = ph;
-      float sv, cv;
-      sincosf(ph, &sv, &cv);
-      const float a = __ldg(S.amp + e);
-      S.field[e] = make_float2(a * cv, a * sv);
+      for (int k = 0; k < TPT; ++k) {
+        const int e = threadIdx.x + k * kMwThreads;
+        if (e < lc * per) {
+          const int l = e / per, rr = e - l * per;
+          const size_t o = rr < n ? (size_t)(2 * (l0 + l)) * n + rr
+                                  : (size_t)(2 * (l0 + l) + 1) * n + y0 + (rr - n);
+          vi[k] = __ldcg(S.tab_i + o);
+          vf[k] = __ldcg(S.tab_f + o);
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < TPT; ++k) {
+        const int e = threadIdx.x + k * kMwThreads;
+        if (e < lc * per) {
+          s_i[e] = vi[k];
+          s_f[e] = vf[k];
+        }
+      }
+      __syncthreads();
+      if (act) {
+        // two layers' gathers in flight, interpolated in layer order
+        for (int l = 0; l < lc; l += 2) {
+          const bool two = l + 1 < lc;
+          const float *Sa = P.L[l0 + l].scr;
+          const int Ma = P.L[l0 + l].side;
+          const int ia = s_i[l * per + c], ja = s_i[l * per + n + r];
+          const float *Sb = two ? P.L[l0 + l + 1].scr : Sa;
+          const int Mb = two ? P.L[l0 + l + 1].side : Ma;
+          const int lb = two ? l + 1 : l;
+          const int ib = s_i[lb * per + c], jb = s_i[lb * per + n + r];
+          const int ia1 = ia + 1 == Ma ? 0 : ia + 1, ja1 = ja + 1 == Ma ? 0 : ja + 1;
+          const int ib1 = ib + 1 == Mb ? 0 : ib + 1, jb1 = jb + 1 == Mb ? 0 : jb + 1;
+          const float a00 = __ldg(Sa + (size_t)ja * Ma + ia), a01 = __ldg(Sa + (size_t)ja * Ma + ia1);
+          const float a10 = __ldg(Sa + (size_t)ja1 * Ma + ia), a11 = __ldg(Sa + (size_t)ja1 * Ma + ia1);
+          const float b00 = __ldg(Sb + (size_t)jb * Mb + ib), b01 = __ldg(Sb + (size_t)jb * Mb + ib1);
+          const float b10 = __ldg(Sb + (size_t)jb1 * Mb + ib), b11 = __ldg(Sb + (size_t)jb1 * Mb + ib1);
+          {
+            const float fx = s_f[l * per + c], fy = s_f[l * per + n + r];
+            const float a = a00 + fx * (a01 - a00);
+            const float b = a10 + fx * (a11 - a10);
+            acc += a + fy * (b - a);
+          }
+          if (two) {
+            const float fx = s_f[lb * per + c], fy = s_f[lb * per + n + r];
+            const float a = b00 + fx * (b01 - b00);
+            const float b = b10 + fx * (b11 - b10);
+            acc += a + fy * (b - a);
+          }
+        }
+      }
     }
+  }
+  if (act) {
+    const size_t e = (size_t)(y0 + r) * n + c;
+    const float ph = acc * S.scale;
+    S.phase[e] = ph;
+    float sv, cv;
+    sincosf(ph, &sv, &cv);
+    const float a = __ldg(S.amp + e);
+    S.field[e] = make_float2(a * cv, a * sv);
   }
 }
 
@@ -775,8 +831,17 @@ __device__ void mw_rinv(const MwSensor &S, int m, int sg, float2 *smem) {
 __device__ void mw_bin(const MwSensor &S, int p0, int p1) {
   const int nd2 = S.nd * S.nd;
   for (int p = p0 + threadIdx.x; p < p1; p += kMwThreads) {
+    // eight loads in flight, summed in modulation order
     float v = 0.f;
-    for (int m = 0; m < S.n_mod; ++m) v += __ldcg(S.part + (size_t)m * nd2 + p);
+    int m = 0;
+    for (; m + 8 <= S.n_mod; m += 8) {
+      float t[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) t[k] = __ldcg(S.part + (size_t)(m + k) * nd2 + p);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) v += t[k];
+    }
+    for (; m < S.n_mod; ++m) v += __ldcg(S.part + (size_t)m * nd2 + p);
     S.det[p] = v;
   }
 }
@@ -785,6 +850,7 @@ __device__ void mw_pyr_slopes(const MwParams &P, const MwSensor &S, float *s_w) 
   const int ns = S.n_sub, w2 = 2 * ns;
   const float *d = S.det;
   float part = 0.f;
+#pragma unroll 4
   for (int k = threadIdx.x; k < S.n_valid; k += kMwThreads) {
     const int s = __ldg(S.valid + k);
     const int a = s / ns, c = s % ns;
@@ -800,6 +866,7 @@ __device__ void mw_pyr_slopes(const MwParams &P, const MwSensor &S, float *s_w) 
   const float T = t / (float)S.n_valid;
   float *o = P.slopes + S.slope_off;
   const float *ref = P.ref ? P.ref + S.slope_off : nullptr;
+#pragma unroll 4
   for (int k = threadIdx.x; k < S.n_valid; k += kMwThreads) {
     const int s = __ldg(S.valid + k);
     const int a = s / ns, c = s % ns;
@@ -1060,7 +1127,7 @@ extern "C" int specula_mwfs_create(specula_ctx *ctx, int32_t n_sensors,
         return g.n_mod < 1 || g.n_sub < 1 ? SPECULA_EINVAL : SPECULA_EUNSUPPORTED;
       const int N = 2 * pu.n_pix;
       if (pN && pN != N) return SPECULA_EUNSUPPORTED;
-      if (pu.n_pix > kMwFieldPx) return SPECULA_EUNSUPPORTED;
+      if (pu.n_pix > kMwFieldPx) return SPECULA_EUNSUPPORTED;   // whole rows per FIELD task
       pN = N;
     } else if (d.kind == SPECULA_WFS_SH) {
       const specula_sh_desc &h = d.sh;
@@ -1254,6 +1321,7 @@ extern "C" int specula_mwfs_create(specula_ctx *ctx, int32_t n_sensors,
     c_field[k] = new_ctr();
     const int rpt = std::max(1, kMwFieldPx / n);
     max_field_slots = std::max(max_field_slots, n + rpt);
+    if (kMwLayerChunk * (n + rpt) > 4 * kMwThreads) return SPECULA_EUNSUPPORTED;
     for (int y0 = 0; y0 < n; y0 += rpt) {
       L_field.push_back(mk(MT_FIELD, k, y0, std::min(n, y0 + rpt), c_coords[k], n_coords[k],
                            c_field[k]));
