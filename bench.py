@@ -23,6 +23,10 @@ import subprocess
 import sys
 import time
 
+# the oracle baselines are timed single-threaded per process (BLAS included)
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
 import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -133,6 +137,17 @@ def read_traffic():
     return out
 
 
+def aggregate_ranks(total_ms, steps, ws, dist=None, device="cpu"):
+    """(ms per step, whole-job frames/s): the slowest rank's timed span over
+    the frames all ranks processed (each rank runs its own replica)."""
+    if dist is not None and ws > 1:
+        import torch
+        t = torch.tensor([float(total_ms)], device=device, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    return total_ms / steps, ws * steps / (total_ms / 1e3)
+
+
 def dist_setup():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -200,8 +215,71 @@ class OracleSample:
 
 
 def cpu_cores_used():
-    # NumPy's pocketfft and the oracle loops run on one thread
+    # NumPy's pocketfft and the oracle loops run on one thread; BLAS is
+    # limited to one thread at start-up
     return 1
+
+
+# ---- the oracle on all host cores: modulation points split over processes
+_POOL = {}
+
+
+def _pool_init(mask, n, mod_amp, n_mod):
+    _POOL.update(mask=mask, n=n, mod_amp=mod_amp, n_mod=n_mod)
+
+
+def _pool_mod_points(args):
+    """Summed |IDFT(mask DFT(pad(E tilt_m)))|^2 over the given points."""
+    E, ms = args
+    from oracle import geometry
+    from oracle.dft import centred_coords, centred_dft2, centred_idft2
+    n, N = _POOL["n"], 2 * _POOL["n"]
+    off = (N - n) // 2
+    x = centred_coords(n)
+    cs, sn = geometry.mod_angles(_POOL["n_mod"])
+    I = np.zeros((N, N))
+    for m in ms:
+        tilt = np.exp(2j * np.pi * _POOL["mod_amp"] * (x[None, :] * cs[m] + x[:, None] * sn[m]) / n)
+        P = np.zeros((N, N), dtype=np.complex128)
+        P[off:off + n, off:off + n] = E * tilt
+        I += np.abs(centred_idft2(centred_dft2(P) * _POOL["mask"])) ** 2
+    return I
+
+
+def all_cores_baseline(sample, n_frames=2):
+    """One full frame (all 48 modulation points) of the oracle with the
+    modulation points spread over one spawned process per host core."""
+    import multiprocessing as mp
+    from oracle import atmo, pyramid, recon, slopes
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    s = sample.s
+    pool = mp.get_context("spawn").Pool(cores, initializer=_pool_init,
+                                         initargs=(sample.mask, sample.n, s.pwfs.mod_amp,
+                                                   s.pwfs.n_mod))
+    try:
+        chunks = [list(range(k, s.pwfs.n_mod, cores)) for k in range(min(cores, s.pwfs.n_mod))]
+        times = []
+        for f in range(n_frames + 1):
+            t0 = time.perf_counter()
+            phi = atmo.atmo_extract(sample.scr, sample.wl.layers, s.source, sample.n,
+                                    s.pupil.pitch_m, 0.001 * (f + 1))
+            E = sample.amp * np.exp(1j * phi)
+            parts = pool.map_async(_pool_mod_points, [(E, c) for c in chunks]).get(timeout=600)
+            I = parts[0]
+            for q in parts[1:]:
+                I = I + q
+            det = pyramid.bin_image(I / s.pwfs.n_mod, sample.n // s.pwfs.n_sub)
+            sl = slopes.pyr_slopes(det, s.pwfs.n_sub, sample.valid)
+            recon.mvm(sample.R, sl)
+            if f > 0:
+                times.append(time.perf_counter() - t0)
+    finally:
+        pool.close()
+        pool.join()
+    return {"value": 1.0 / min(times), "unit": "frames/s", "cores": cores, "kind": "oracle",
+            "sample": "one full %s frame (all %d modulation points spread over %d spawned "
+                      "processes, extraction / slopes / MVM in the parent), best of %d"
+                      % (WORKLOAD, s.pwfs.n_mod, cores, n_frames)}
 
 
 def reference_leg(args, ws, rank):
@@ -273,6 +351,70 @@ def learned_leg(ctx, n_train=200000, n_test=5000, epochs=12):
             "final_train_loss": hist[-1],
             "inference_frames_per_s": {"learned_batched": n_test / (mlp_ms / 1e3),
                                        "linear_batched": n_test / (lin_ms / 1e3)}}
+
+
+def systems_leg(ctx, steps=50):
+    """The other systems of the paper's scale list, one frame per step from a
+    CUDA graph, L2 flushed between frames outside the events: the 8 m single
+    pyramid (FP32 / split-BF16 / BF16 reconstructor) and the 39 m
+    multi-sensor system (6 laser-star SH + 3 pyramids + MVM) in one
+    persistent launch against the same frame as per-sensor launches."""
+    import torch
+    import synth
+    import paper_2602_06688_gb300 as sp
+    from paper_2602_06688_gb300.frame import PwfsFrame
+    from paper_2602_06688_gb300.system import System
+    st = torch.cuda.Stream()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+
+    def time_graph(g, set_t, n):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(n)]
+        with torch.cuda.stream(st):
+            for k in range(n):
+                flush.zero_()
+                set_t(k)
+                ev[k][0].record(st)
+                g.launch(st)
+                ev[k][1].record(st)
+        torch.cuda.synchronize()
+        return [a.elapsed_time(b) for a, b in ev]
+
+    out = {}
+    wl = synth.workload("pwfs8m")
+    fr = PwfsFrame(ctx, wl, autotune=True)
+    res = {}
+    for name, prec in (("fp32", sp.PREC_FP32), ("bf16x2", sp.PREC_BF16X2), ("bf16", sp.PREC_BF16)):
+        fr.set_precision(prec)
+        g = fr.capture(st)
+        time_graph(g, lambda k: fr.t_dev.fill_(wl.dt_s * k), 5)
+        ms = time_graph(g, lambda k: fr.t_dev.fill_(wl.dt_s * k), steps)
+        res[name] = {"frames_per_s": steps / (sum(ms) / 1e3), "ms_per_step": sum(ms) / steps}
+        g.close()
+    out["pwfs8m"] = {"config": "8.4 m, 160 px pupil, 320^2 FFT, 24 mod points, 40x40 subaps, "
+                               "3 layers, 500 modes", "tiles": fr.tiles, "recon_variants": res}
+    del fr
+    wl = synth.workload("mwfs39m")
+    S = System(ctx, wl)
+    res = {}
+    for name, sep in (("one_persistent_launch", False), ("per_sensor_launches", True)):
+        g = S.capture(st, separate=sep)
+        time_graph(g, lambda k: S.t_dev.fill_(wl.dt_s * k), 5)
+        ms = time_graph(g, lambda k: S.t_dev.fill_(wl.dt_s * k), steps)
+        res[name] = {"frames_per_s": steps / (sum(ms) / 1e3), "ms_per_step": sum(ms) / steps,
+                     "kernels_per_frame": g.kernel_count()}
+        g.close()
+    sched = S.m.schedule()
+    out["mwfs39m"] = {"config": "39 m: 6 laser-star SH (68x68 x 12 px, 24^2 FFT) + 3 pyramids "
+                                "(120 px, 240^2 FFT, 16 mod), 10 layers, 4000 x %d MVM, FP32"
+                                % S.n_slopes,
+                      "tasks_per_frame": sched["n_tasks"], "ctas": sched["grid"], **res,
+                      "speedup_persistent": res["per_sensor_launches"]["ms_per_step"]
+                      / res["one_persistent_launch"]["ms_per_step"]}
+    S.m.close()
+    del S
+    torch.cuda.empty_cache()
+    return out
 
 
 def gemm_leg(ctx, pk, n=8192, reps=10):
@@ -361,15 +503,12 @@ def gpu_leg(args, ws, rank, local):
         wall0 = time.perf_counter()
         ms = timed(K, W)
         wall1 = time.perf_counter()
-    launches = graph_kernels * K
-    total_ms = sum(ms)
-    ms_eager = timed(K, W, graph=False)
+    torch.cuda.synchronize()
     if dist:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    ms_per_step = total_ms / K
-    value = ws * K / (total_ms / 1e3)
+        dist.barrier()
+    launches = graph_kernels * K
+    ms_per_step, value = aggregate_ranks(sum(ms), K, ws, dist, "cuda")
+    ms_eager = timed(K, W, graph=False)
     if args.quick:
         # headline frames only (used for profiler launch lists)
         if rank == 0:
@@ -495,6 +634,8 @@ def gpu_leg(args, ws, rank, local):
                         "note": "per step: pinned host time -> device, frame, modes -> pinned host, sync"},
                 "gpu_launches": launches, "clocks": clocks,
                 "peaks": {"source": how, "hbm_gbs": pk.get("hbm_gbs")}}
+        if not args.no_systems:
+            line["systems"] = systems_leg(ctx)
         if not args.no_learned:
             line["learned"] = learned_leg(ctx)
             line["gemm_bf16"] = gemm_leg(ctx, pk)
@@ -504,6 +645,7 @@ def gpu_leg(args, ws, rank, local):
             desc = sample.desc + ", best of 3"
             line["cpu_baseline"] = {"value": 1.0 / per, "unit": "frames/s",
                                     "cores": cpu_cores_used(), "kind": "oracle", "sample": desc}
+            line["cpu_baseline_all_cores"] = all_cores_baseline(sample)
         print(json.dumps(line), flush=True)
     ctx.close()
     if dist:
@@ -517,6 +659,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="specula", choices=["specula", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-systems", action="store_true",
+                    help="skip the 8 m and 39 m multi-sensor system timings")
     ap.add_argument("--no-learned", action="store_true",
                     help="skip the learned-reconstructor training run on the 8 m system")
     ap.add_argument("--quick", action="store_true",

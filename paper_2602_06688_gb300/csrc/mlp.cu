@@ -1,8 +1,8 @@
 // Learned nonlinear reconstructor: a 3-layer perceptron (slopes -> modes)
 // with GELU, trained by the project's own forward/backward kernels and Adam.
-// Not in the paper (its reconstructor is the linear Modalrec); the learned
-// part, its sizes, BF16 weights with FP32 accumulation and batch 256 come
-// from the learned-reconstructor configuration this library targets.
+// Not in the paper (its reconstructor is the linear Modalrec): a nonlinear
+// alternative trained on simulated pairs, with BF16 weights, FP32
+// accumulation and batch 256 (the 8 m and 39 m learned workloads).
 //
 // Layout.  Widths are padded to multiples of 128 (zero pads stay zero: their
 // inputs and output gradients are zero) and the batch to a multiple of 128,
