@@ -58,11 +58,16 @@ def fft_flops(n):
 def kernel_flops(wl):
     """Algorithmic FLOPs per (batch, modulation point) item of each pyramid
     pass (benchFFT convention 5 N log2 N per N-point transform, pruned inputs
-    counted as full transforms; element-wise work not counted)."""
+    counted as full transforms; element-wise work not counted).  Two-pass
+    form: the row filter transforms the n_pix pupil rows forward and back,
+    the column filter all N columns forward and back; three-pass form: n_pix
+    forward rows, N columns forward and back, N inverse rows."""
     s = wl.sensors[0]
     n = s.pupil.n_pix
     N = s.pwfs.pad * n
-    return {"pwfs_rows_fwd": n * fft_flops(N),
+    return {"pwfs_rowfilt": 2 * n * fft_flops(N),
+            "pwfs_colfilt_bin": 2 * N * fft_flops(N),
+            "pwfs_rows_fwd": n * fft_flops(N),
             "pwfs_cols": 2 * N * fft_flops(N),
             "pwfs_rows_inv": N * fft_flops(N)}
 
@@ -392,7 +397,9 @@ def systems_leg(ctx, steps=50):
         res[name] = {"frames_per_s": steps / (sum(ms) / 1e3), "ms_per_step": sum(ms) / steps}
         g.close()
     out["pwfs8m"] = {"config": "8.4 m, 160 px pupil, 320^2 FFT, 24 mod points, 40x40 subaps, "
-                               "3 layers, 500 modes", "tiles": fr.tiles, "recon_variants": res}
+                               "3 layers, 500 modes",
+                      "tiles": {"chunk": fr.tiles[0], "ka": fr.tiles[1], "passes": fr.tiles[2]},
+                      "recon_variants": res}
     del fr
     wl = synth.workload("mwfs39m")
     S = System(ctx, wl)
@@ -624,7 +631,8 @@ def gpu_leg(args, ws, rank, local):
                 "config": {"workload": WORKLOAD, "pupil_px": 480, "fft": 960, "n_mod": 48,
                            "n_sub": 96, "layers": 35, "n_modes": fr.n_modes,
                            "n_slopes": fr.n_slopes, "l2": "flushed between timed frames",
-                           "pwfs_tiles": {"chunk": fr.tiles[0], "ka": fr.tiles[1]} if fr.tiles else None,
+                           "pwfs_tiles": {"chunk": fr.tiles[0], "ka": fr.tiles[1],
+                                          "passes": fr.tiles[2]} if fr.tiles else None,
                            "frame": "one CUDA graph per frame (%d kernels)" % graph_kernels,
                            "eager_frames_per_s": K / (sum(ms_eager) / 1e3),
                            "wall_ms_per_step_incl_flush": (wall1 - wall0) * 1e3 / K},

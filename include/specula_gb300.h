@@ -49,6 +49,11 @@ extern "C" {
 /* Human-readable text of a status code (static storage; never NULL). */
 const char *specula_strerror(int status);
 
+/* Text of the CUDA error behind the calling thread's last SPECULA_ECUDA
+ * (error name, description, source location); "" if none yet.  Static
+ * thread-local storage, valid until the thread's next failing call. */
+const char *specula_last_cuda_error(void);
+
 /* Library ABI version (major * 10000 + minor * 100 + patch). */
 int specula_version(void);
 
@@ -154,7 +159,9 @@ int specula_ctx_status(specula_ctx *ctx, int32_t *device_status);
 #define SPECULA_K_GEMM          10  /* tcgen05 BF16 GEMM and split-K reduction    */
 #define SPECULA_K_MLP           11  /* learned-reconstructor element-wise kernels */
 #define SPECULA_K_MWFS          12  /* multi-sensor frame, one persistent launch  */
-#define SPECULA_K_COUNT         13
+#define SPECULA_K_PWFS_ROWFILT  13  /* pyramid two-pass form: row filter          */
+#define SPECULA_K_PWFS_COLFILT  14  /* pyramid two-pass form: column filter, bins */
+#define SPECULA_K_COUNT         15
 
 /* Enable (capacity > 0: room for that many kernel records; allocates CUDA
  * events; set-up call) or disable (capacity = 0) per-kernel event timing.
@@ -307,17 +314,26 @@ int specula_pwfs_plan(specula_ctx *ctx, const specula_pupil_desc *pupil,
  * (batch element, modulation point) items whose intermediates are kept in
  * the workspace at once (the pipeline runs chunk by chunk, so a chunk that
  * fits L2 keeps the intermediates on chip); `ka` = modulation items handled
- * per warp in the row-transform pass (amortises the field's sincos).
+ * per warp in the row-transform pass (amortises the field's sincos);
+ * `passes` = the form of the 2D filter IDFT2(M . DFT2(P)): 3 = row FFTs,
+ * column FFT + mask + inverse, row inverse FFTs + |.|^2 + bins; 2 = the
+ * separable form (the mask is Mx(u) My(v)): row FFT + x mask + row inverse,
+ * then column FFT + y mask + column inverse + |.|^2 + bins, without the
+ * N x N intermediate.  Both compute the same image (float rounding aside).
  * set: may reallocate the workspace (set-up call); chunk in [1, 4096], ka in
- * [1, 64].  get: reads the current values. */
+ * [1, 64], passes 2 or 3 (2 returns SPECULA_EUNSUPPORTED where its column
+ * tile does not fit).  get: reads the current values. */
 int specula_pwfs_set_tiles(specula_ctx *ctx, const specula_pupil_desc *pupil,
-                           const specula_pwfs_desc *pwfs, int32_t chunk, int32_t ka);
+                           const specula_pwfs_desc *pwfs, int32_t chunk, int32_t ka,
+                           int32_t passes);
 int specula_pwfs_get_tiles(specula_ctx *ctx, const specula_pupil_desc *pupil,
-                           const specula_pwfs_desc *pwfs, int32_t *chunk, int32_t *ka);
+                           const specula_pwfs_desc *pwfs, int32_t *chunk, int32_t *ka,
+                           int32_t *passes);
 
-/* Autotuner: time every candidate (chunk in {1,2,3,4,6,8,12,16,24,32,48,64}
- * up to the batch's item count and with workspace <= max_workspace_bytes;
- * ka in {1, 2}) with CUDA events over `reps` images of the caller's inputs on
+/* Autotuner: time every candidate (passes in {2, 3}; chunk in
+ * {1,2,3,4,6,8,12,16,24,32,48,64} up to the batch's item count and with
+ * workspace <= max_workspace_bytes; ka in {1, 2}) with CUDA events over
+ * `reps` images of the caller's inputs on
  * `stream`, keep the fastest in the plan and return it.  Set-up call: may
  * reallocate the workspace and synchronises the stream.  det_dev is
  * overwritten. */
@@ -325,7 +341,7 @@ int specula_pwfs_autotune(specula_ctx *ctx, const specula_pupil_desc *pupil,
                           const specula_pwfs_desc *pwfs, const float *amp_dev,
                           const float *phase_dev, int32_t n_batch, float *det_dev,
                           int32_t reps, int64_t max_workspace_bytes, int32_t *chunk,
-                          int32_t *ka, void *stream);
+                          int32_t *ka, int32_t *passes, void *stream);
 
 /* Modulated pyramid image (ModulatedPyramid + CCD, noise off).  For each of
  * n_batch phase maps and each modulation point m:

@@ -109,6 +109,11 @@ class Context:
         return self.handle
 
 
+def specula_last_cuda_error():
+    """Text of the CUDA error behind this thread's last SPECULA_ECUDA."""
+    return lib().specula_last_cuda_error().decode()
+
+
 def specula_ctx_create(device=0):
     return Context(device)
 
@@ -124,10 +129,12 @@ def specula_ctx_status(ctx):
 
 
 (K_PWFS_ROWS_FWD, K_PWFS_COLS, K_PWFS_ROWS_INV, K_ATMO, K_SLOPES, K_RECON, K_SH,
- K_PWFS_FIELD, K_PWFS_BIN, K_CALIB, K_GEMM, K_MLP, K_MWFS) = range(13)
-K_COUNT = 13
+ K_PWFS_FIELD, K_PWFS_BIN, K_CALIB, K_GEMM, K_MLP, K_MWFS, K_PWFS_ROWFILT,
+ K_PWFS_COLFILT) = range(15)
+K_COUNT = 15
 KERNEL_NAMES = ["pwfs_rows_fwd", "pwfs_cols", "pwfs_rows_inv", "atmo_extract", "slopes",
-                "recon", "sh_spots", "pwfs_field", "pwfs_bin", "calib", "gemm", "mlp", "mwfs"]
+                "recon", "sh_spots", "pwfs_field", "pwfs_bin", "calib", "gemm", "mlp", "mwfs",
+                "pwfs_rowfilt", "pwfs_colfilt_bin"]
 
 
 def specula_prof_enable(ctx, capacity):
@@ -337,33 +344,36 @@ def specula_pwfs_plan(ctx, pupil, pwfs):
                "specula_pwfs_plan")
 
 
-def specula_pwfs_set_tiles(ctx, pupil, pwfs, chunk, ka):
+def specula_pwfs_set_tiles(ctx, pupil, pwfs, chunk, ka, passes=2):
     _abi.check(lib().specula_pwfs_set_tiles(ctx.handle, C.byref(pupil), C.byref(pwfs),
-                                            int(chunk), int(ka)), "specula_pwfs_set_tiles")
+                                            int(chunk), int(ka), int(passes)),
+               "specula_pwfs_set_tiles")
 
 
 def specula_pwfs_get_tiles(ctx, pupil, pwfs):
-    ch, ka = C.c_int32(), C.c_int32()
+    """(chunk, ka, passes) of the plan."""
+    ch, ka, ps = C.c_int32(), C.c_int32(), C.c_int32()
     _abi.check(lib().specula_pwfs_get_tiles(ctx.handle, C.byref(pupil), C.byref(pwfs),
-                                            C.byref(ch), C.byref(ka)), "specula_pwfs_get_tiles")
-    return ch.value, ka.value
+                                            C.byref(ch), C.byref(ka), C.byref(ps)),
+               "specula_pwfs_get_tiles")
+    return ch.value, ka.value, ps.value
 
 
 def specula_pwfs_autotune(ctx, pupil, pwfs, amp, phase, det, reps=3,
                           max_workspace_bytes=512 << 20, stream=None):
     """Time the candidate tilings on these buffers, keep and return the best
-    (chunk, ka)."""
+    (chunk, ka, passes)."""
     import torch
     n = pupil.n_pix
     nb = phase.numel() // (n * n)
     side = 2 * pwfs.n_sub
-    ch, ka = C.c_int32(), C.c_int32()
+    ch, ka, ps = C.c_int32(), C.c_int32(), C.c_int32()
     _abi.check(lib().specula_pwfs_autotune(
         ctx.handle, C.byref(pupil), C.byref(pwfs), _dev(amp, torch.float32, n * n, "amp"),
         _dev(phase, torch.float32, nb * n * n, "phase"), nb,
         _dev(det, torch.float32, nb * side * side, "det"), int(reps), int(max_workspace_bytes),
-        C.byref(ch), C.byref(ka), _stream(stream)), "specula_pwfs_autotune")
-    return ch.value, ka.value
+        C.byref(ch), C.byref(ka), C.byref(ps), _stream(stream)), "specula_pwfs_autotune")
+    return ch.value, ka.value, ps.value
 
 
 def specula_pwfs_image(ctx, pupil, pwfs, amp, phase, det, stream=None):

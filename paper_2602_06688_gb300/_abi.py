@@ -66,6 +66,7 @@ dbl = C.c_double
 # name -> (restype, argtypes)
 SIGNATURES = {
     "specula_strerror": (C.c_char_p, [C.c_int]),
+    "specula_last_cuda_error": (C.c_char_p, []),
     "specula_version": (C.c_int, []),
     "specula_ctx_create": (C.c_int, [P(vp), C.c_int]),
     "specula_ctx_destroy": (C.c_int, [vp]),
@@ -93,10 +94,11 @@ SIGNATURES = {
     "specula_atmo_extract_noalloc": (C.c_int, [i32, P(LayerDesc), P(vp), P(SourceDesc),
                                                P(PupilDesc), dbl, vp, vp, vp]),
     "specula_pwfs_plan": (C.c_int, [vp, P(PupilDesc), P(PwfsDesc)]),
-    "specula_pwfs_set_tiles": (C.c_int, [vp, P(PupilDesc), P(PwfsDesc), i32, i32]),
-    "specula_pwfs_get_tiles": (C.c_int, [vp, P(PupilDesc), P(PwfsDesc), P(i32), P(i32)]),
+    "specula_pwfs_set_tiles": (C.c_int, [vp, P(PupilDesc), P(PwfsDesc), i32, i32, i32]),
+    "specula_pwfs_get_tiles": (C.c_int, [vp, P(PupilDesc), P(PwfsDesc), P(i32), P(i32),
+                                         P(i32)]),
     "specula_pwfs_autotune": (C.c_int, [vp, P(PupilDesc), P(PwfsDesc), vp, vp, i32, vp, i32,
-                                        C.c_int64, P(i32), P(i32), vp]),
+                                        C.c_int64, P(i32), P(i32), P(i32), vp]),
     "specula_pwfs_image": (C.c_int, [vp, P(PupilDesc), P(PwfsDesc), vp, vp, i32, vp, vp]),
     "specula_sh_plan": (C.c_int, [vp, P(PupilDesc), P(ShDesc), P(i32)]),
     "specula_sh_image": (C.c_int, [vp, P(PupilDesc), P(ShDesc), vp, vp, i32, vp, vp]),
@@ -153,7 +155,12 @@ def load():
 
 class SpeculaError(RuntimeError):
     def __init__(self, status, where):
-        text = load().specula_strerror(status).decode()
+        lib = load()
+        text = lib.specula_strerror(status).decode()
+        if status == ECUDA:
+            detail = lib.specula_last_cuda_error().decode()
+            if detail:
+                text += f": {detail}"
         super().__init__(f"{where}: {text} ({status})")
         self.status = status
 

@@ -17,7 +17,7 @@ def cache_path():
 
 
 def _key(device_name, pupil, pwfs, n_batch):
-    return (f"{device_name}|np{pupil.n_pix}|pad{pwfs.pad}|mod{pwfs.n_mod}|sub{pwfs.n_sub}"
+    return (f"v2|{device_name}|np{pupil.n_pix}|pad{pwfs.pad}|mod{pwfs.n_mod}|sub{pwfs.n_sub}"
             f"|b{n_batch}")
 
 
@@ -44,18 +44,18 @@ def _store(d):
 def tune_pwfs(ctx, pupil, pwfs, amp, phase, det, force=False, reps=3,
               max_workspace_bytes=512 << 20):
     """Apply the cached tiling for this geometry, or run the autotuner and
-    cache its choice.  Returns (chunk, ka, from_cache)."""
+    cache its choice.  Returns (chunk, ka, passes, from_cache)."""
     import torch
     n = pupil.n_pix
     n_batch = phase.numel() // (n * n)
     key = _key(torch.cuda.get_device_name(ctx.device), pupil, pwfs, n_batch)
     d = _load()
     if not force and key in d:
-        ch, ka = d[key]
-        specula_pwfs_set_tiles(ctx, pupil, pwfs, ch, ka)
-        return ch, ka, True
-    ch, ka = specula_pwfs_autotune(ctx, pupil, pwfs, amp, phase, det, reps=reps,
-                                   max_workspace_bytes=max_workspace_bytes)
-    d[key] = [ch, ka]
+        ch, ka, ps = d[key]
+        specula_pwfs_set_tiles(ctx, pupil, pwfs, ch, ka, ps)
+        return ch, ka, ps, True
+    ch, ka, ps = specula_pwfs_autotune(ctx, pupil, pwfs, amp, phase, det, reps=reps,
+                                       max_workspace_bytes=max_workspace_bytes)
+    d[key] = [ch, ka, ps]
     _store(d)
-    return ch, ka, False
+    return ch, ka, ps, False

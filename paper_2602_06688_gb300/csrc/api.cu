@@ -1,9 +1,13 @@
 // Context, status codes, integer geometry and argument validation of the
 // C ABI (include/specula_gb300.h).
 #include <math.h>
+#include <stdio.h>
 #include <string.h>
 
+#include <map>
+#include <mutex>
 #include <new>
+#include <utility>
 
 #include "internal.h"
 
@@ -207,6 +211,34 @@ extern "C" int specula_ctx_status(specula_ctx *ctx, int32_t *device_status) {
 // ---- integer geometry --------------------------------------------------------
 
 namespace specula {
+static thread_local char t_last_error[256] = "";
+void note_cuda_error(cudaError_t e, const char *file, int line) {
+  const char *f = strrchr(file, '/');
+  snprintf(t_last_error, sizeof(t_last_error), "%s (%s) at %s:%d", cudaGetErrorName(e),
+           cudaGetErrorString(e), f ? f + 1 : file, line);
+}
+}  // namespace specula
+
+extern "C" const char *specula_last_cuda_error(void) { return specula::t_last_error; }
+
+namespace specula {
+int ensure_dynamic_smem(const void *fn, size_t bytes) {
+  if (bytes <= 48 * 1024) return SPECULA_OK;
+  static std::mutex mu;
+  static std::map<std::pair<int, const void *>, size_t> cur;
+  int dev = 0;
+  SPECULA_CK(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(mu);
+  size_t &c = cur[std::make_pair(dev, fn)];
+  if (bytes > c) {
+    SPECULA_CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    c = bytes;
+  }
+  return SPECULA_OK;
+}
+}  // namespace specula
+
+namespace specula {
 
 int host_pupil_mask(int n, double obsc, uint8_t *mask) {
   const double e = obsc * (double)n;
@@ -378,47 +410,53 @@ extern "C" int specula_pwfs_plan(specula_ctx *ctx, const specula_pupil_desc *pup
 }
 
 extern "C" int specula_pwfs_set_tiles(specula_ctx *ctx, const specula_pupil_desc *pupil,
-                                      const specula_pwfs_desc *pwfs, int32_t chunk, int32_t ka) {
+                                      const specula_pwfs_desc *pwfs, int32_t chunk, int32_t ka,
+                                      int32_t passes) {
   if (!ctx) return SPECULA_EINVAL;
   int s = check_pwfs(pupil, pwfs);
   if (s) return s;
   if (chunk < 1 || chunk > 4096 || ka < 1 || ka > 64) return SPECULA_EINVAL;
+  if (passes != 2 && passes != 3) return SPECULA_EINVAL;
   PwfsPlan *p = pwfs_plan_find(ctx, pupil, pwfs);
   if (!p) return SPECULA_ENOPLAN;
   SPECULA_CK(cudaSetDevice(ctx->device));
-  return pwfs_set_tiles(p, chunk, ka);
+  return pwfs_set_tiles(p, chunk, ka, passes);
 }
 
 extern "C" int specula_pwfs_autotune(specula_ctx *ctx, const specula_pupil_desc *pupil,
                                      const specula_pwfs_desc *pwfs, const float *amp_dev,
                                      const float *phase_dev, int32_t n_batch, float *det_dev,
                                      int32_t reps, int64_t max_workspace_bytes, int32_t *chunk,
-                                     int32_t *ka, void *stream) {
-  if (!ctx || !amp_dev || !phase_dev || !det_dev || !chunk || !ka) return SPECULA_EINVAL;
+                                     int32_t *ka, int32_t *passes, void *stream) {
+  if (!ctx || !amp_dev || !phase_dev || !det_dev || !chunk || !ka || !passes)
+    return SPECULA_EINVAL;
   if (n_batch < 1 || reps < 1 || reps > 1000 || max_workspace_bytes < 1) return SPECULA_EINVAL;
   int s = check_pwfs(pupil, pwfs);
   if (s) return s;
   PwfsPlan *p = pwfs_plan_find(ctx, pupil, pwfs);
   if (!p) return SPECULA_ENOPLAN;
   SPECULA_CK(cudaSetDevice(ctx->device));
-  int bc = 0, bk = 0;
+  int bc = 0, bk = 0, bp = 0;
   s = pwfs_autotune(ctx, p, amp_dev, phase_dev, n_batch, det_dev, (cudaStream_t)stream, reps,
-                    (size_t)max_workspace_bytes, &bc, &bk);
+                    (size_t)max_workspace_bytes, &bc, &bk, &bp);
   if (s) return s;
   *chunk = bc;
   *ka = bk;
+  *passes = bp;
   return SPECULA_OK;
 }
 
 extern "C" int specula_pwfs_get_tiles(specula_ctx *ctx, const specula_pupil_desc *pupil,
-                                      const specula_pwfs_desc *pwfs, int32_t *chunk, int32_t *ka) {
-  if (!ctx || !chunk || !ka) return SPECULA_EINVAL;
+                                      const specula_pwfs_desc *pwfs, int32_t *chunk, int32_t *ka,
+                                      int32_t *passes) {
+  if (!ctx || !chunk || !ka || !passes) return SPECULA_EINVAL;
   int s = check_pwfs(pupil, pwfs);
   if (s) return s;
   PwfsPlan *p = pwfs_plan_find(ctx, pupil, pwfs);
   if (!p) return SPECULA_ENOPLAN;
   *chunk = p->chunk;
   *ka = p->ka;
+  *passes = p->passes;
   return SPECULA_OK;
 }
 

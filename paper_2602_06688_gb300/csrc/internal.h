@@ -8,16 +8,27 @@
 
 #include "../../include/specula_gb300.h"
 
+namespace specula {
+// the CUDA error behind the calling thread's last SPECULA_ECUDA (api.cu)
+void note_cuda_error(cudaError_t e, const char *file, int line);
+}
+
 #define SPECULA_CK(call)                                   \
   do {                                                     \
     cudaError_t e_ = (call);                               \
-    if (e_ != cudaSuccess) return SPECULA_ECUDA;           \
+    if (e_ != cudaSuccess) {                               \
+      specula::note_cuda_error(e_, __FILE__, __LINE__);    \
+      return SPECULA_ECUDA;                                \
+    }                                                      \
   } while (0)
 
 #define SPECULA_CK_LAUNCH()                                \
   do {                                                     \
     cudaError_t e_ = cudaGetLastError();                   \
-    if (e_ != cudaSuccess) return SPECULA_ECUDA;           \
+    if (e_ != cudaSuccess) {                               \
+      specula::note_cuda_error(e_, __FILE__, __LINE__);    \
+      return SPECULA_ECUDA;                                \
+    }                                                      \
   } while (0)
 
 namespace specula {
@@ -54,12 +65,16 @@ struct PwfsPlan {
   int nbw;              // field slots: batch elements one chunk can touch
   int blockA, blockB, blockC;
   size_t smemA, smemB, smemC;
+  int passes;           // 2: row filter + column filter/bins; 3: rows, cols, rows
+  bool two_ok;          // the two-pass form fits this geometry
+  int blockR, blockK;   // two-pass blocks (K: TC columns x G lanes)
+  size_t smemR, smemK;
   DevBuf gx, gy;        // [n_mod][n_pix] float2: tilt x pre-phase (x and y parts)
   DevBuf mask;          // [N] float2: pyramid mask factor per axis, x (1/N)
   DevBuf twA, twB;      // [N] float2: inter-step twiddles (cos, sin)
   DevBuf field;         // [nbw][n_pix][n_pix] float2: E = amp exp(i phase)
   DevBuf rows;          // [chunk][n_pix][N] float2: after the row transform
-  DevBuf cols;          // [chunk][N][N] float2: after the column pass
+  DevBuf cols;          // [chunk][N][N] float2: after the column pass (three-pass form)
   DevBuf part;          // [chunk][nd][nd] float: binned intensity per item
 };
 
@@ -127,10 +142,10 @@ int pwfs_plan_build(specula_ctx *ctx, const specula_pupil_desc *pupil,
                     const specula_pwfs_desc *pwfs, PwfsPlan **out);
 PwfsPlan *pwfs_plan_find(specula_ctx *ctx, const specula_pupil_desc *pupil,
                          const specula_pwfs_desc *pwfs);
-int pwfs_set_tiles(PwfsPlan *p, int chunk, int ka);
+int pwfs_set_tiles(PwfsPlan *p, int chunk, int ka, int passes);
 int pwfs_autotune(specula_ctx *ctx, PwfsPlan *p, const float *amp, const float *phase,
                   int n_batch, float *det, cudaStream_t st, int reps, size_t max_ws_bytes,
-                  int *best_chunk, int *best_ka);
+                  int *best_chunk, int *best_ka, int *best_passes);
 int pwfs_run(specula_ctx *ctx, PwfsPlan *plan, const float *amp, const float *phase,
              int n_batch, float *det, cudaStream_t st);
 int sh_plan_build(specula_ctx *ctx, const specula_pupil_desc *pupil,
@@ -139,6 +154,12 @@ ShPlan *sh_plan_find(specula_ctx *ctx, const specula_pupil_desc *pupil,
                      const specula_sh_desc *sh);
 int sh_run(specula_ctx *ctx, ShPlan *plan, const float *amp, const float *phase,
            int n_batch, float *spots, cudaStream_t st);
+
+// Raise (never lower) a kernel's dynamic shared-memory limit to `bytes` on
+// the current device.  The limit belongs to the function, shared by every
+// plan that launches it, so a later plan with a smaller need must not shrink
+// what an earlier one relies on.  Needs up to 48 KB need no call.
+int ensure_dynamic_smem(const void *fn, size_t bytes);
 
 int gemm_check(const void *A, const void *B, int M, int N, int K);
 int gemm_splits(int K, int want);

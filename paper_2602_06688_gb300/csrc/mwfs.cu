@@ -1408,8 +1408,7 @@ extern "C" int specula_mwfs_create(specula_ctx *ctx, int32_t n_sensors,
 
   m->smem = var->smem(max_slopes, max_field_slots);
   if (m->smem > 227 * 1024) return SPECULA_EUNSUPPORTED;
-  SPECULA_CK(cudaFuncSetAttribute(var->fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)m->smem));
+  if ((st = ensure_dynamic_smem((const void *)var->fn, m->smem))) return st;
   int occ = 0;
   SPECULA_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, var->fn, kMwThreads, m->smem));
   if (occ < 1) return SPECULA_EUNSUPPORTED;

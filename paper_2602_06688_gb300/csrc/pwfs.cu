@@ -296,6 +296,210 @@ __global__ void __launch_bounds__(256, 2) k_rows_inv_part(
 }
 
 // --------------------------------------------------------------------------
+// Two-pass form.  The pyramid mask is separable, M(u, v) = Mx(u) My(v), and
+// so is the centred 2D transform, hence
+//     IDFT2(M . DFT2(P)) = (IDFT_y My DFT_y) (IDFT_x Mx DFT_x) P :
+// the x filter acts on each row alone and the y filter on each column alone.
+// Pass R filters the n_pix non-zero rows of every item (forward row FFT of
+// the pruned input, x mask, inverse row FFT); pass K filters every column
+// (forward FFT of its n_pix non-zero entries, y mask, inverse FFT), squares,
+// scales by 1/n_mod and bins, so the N x N intermediate of the three-pass
+// form is never written.  The inverse row transform's output phase depends
+// on x only and vanishes in |.|^2.
+
+template <int N1, int N2> struct RowFiltCfg {
+  using S = Split<N1, N2>;
+  static constexpr int XBF = N2 * S::S1 > N1 * S::S2 ? N2 * S::S1 : N1 * S::S2;
+};
+
+// R: grid (ceil(n_pix / VPC), ceil(n_items / ka)); block VPC * G threads.
+template <int N1, int N2>
+__global__ void __launch_bounds__(256, 2) k_rowfilt(
+    const float2 *__restrict__ field, const float2 *__restrict__ gx,
+    const float2 *__restrict__ gy, const float2 *__restrict__ twA, const float2 *__restrict__ twB,
+    const float2 *__restrict__ mask, float2 *__restrict__ rows_out, int n_pix, int n_mod, int nbw,
+    int item0, int n_items, int ka) {
+  using S = Split<N1, N2>;
+  constexpr int N = S::N, G = S::G, S1 = S::S1, S2 = S::S2;
+  constexpr int Q0 = N2 / 4, QH = N2 / 2;
+  extern __shared__ float2 smem[];
+  const int vpc = blockDim.x / G;
+  const int vec = threadIdx.x / G, lane = threadIdx.x % G;
+  float2 *xb = smem + vec * RowFiltCfg<N1, N2>::XBF;
+  const int j = blockIdx.x * vpc + vec;
+  const bool row_ok = j < n_pix;
+  const bool in_lane = row_ok && lane < N1;
+  float2 e[QH];
+  int cur_b = -1;
+  const int it_begin = blockIdx.y * ka;
+  for (int q = 0; q < ka; ++q) {
+    const int it = it_begin + q;
+    if (it >= n_items) break;
+    const int gi = item0 + it;
+    const int b = gi / n_mod, m = gi - b * n_mod;
+    if (b != cur_b) {
+      cur_b = b;
+      const float2 *src = field + ((size_t)(b % nbw) * n_pix + (row_ok ? j : 0)) * n_pix + lane;
+#pragma unroll
+      for (int h = 0; h < QH; ++h) e[h] = in_lane ? src[N1 * h] : make_float2(0.f, 0.f);
+    }
+    // forward row transform, pruned input (standard split)
+    float2 r[N2];
+    const float2 gyv = row_ok ? gy[(size_t)m * n_pix + j] : make_float2(0.f, 0.f);
+#pragma unroll
+    for (int n2 = 0; n2 < N2; ++n2) r[n2] = make_float2(0.f, 0.f);
+    if (in_lane) {
+      const float2 *g = gx + (size_t)m * n_pix + lane;
+#pragma unroll
+      for (int h = 0; h < QH; ++h) r[Q0 + h] = cmul(cmul(e[h], __ldg(g + N1 * h)), gyv);
+    }
+    RegDFT<N2, false>::run(r);
+    __syncwarp();
+    if (lane < N1) {
+#pragma unroll
+      for (int k2 = 0; k2 < N2; ++k2) xb[k2 * S1 + lane] = cmulc(r[k2], __ldg(twA + k2 * N1 + lane));
+    }
+    __syncwarp();
+    float2 r2[N1];
+    if (lane < N2) {
+#pragma unroll
+      for (int n1 = 0; n1 < N1; ++n1) r2[n1] = xb[lane * S1 + n1];
+    } else {
+#pragma unroll
+      for (int n1 = 0; n1 < N1; ++n1) r2[n1] = make_float2(0.f, 0.f);
+    }
+    RegDFT<N1, false>::run(r2);
+    // x mask, then the inverse row transform (swapped split)
+    if (lane < N2) {
+#pragma unroll
+      for (int k1 = 0; k1 < N1; ++k1) r2[k1] = cmul(r2[k1], __ldg(mask + N2 * k1 + lane));
+    }
+    RegDFT<N1, true>::run(r2);
+    __syncwarp();
+    if (lane < N2) {
+#pragma unroll
+      for (int k2 = 0; k2 < N1; ++k2) xb[k2 * S2 + lane] = cmul(r2[k2], __ldg(twB + k2 * N2 + lane));
+    }
+    __syncwarp();
+    float2 r3[N2];
+    if (lane < N1) {
+#pragma unroll
+      for (int n1 = 0; n1 < N2; ++n1) r3[n1] = xb[lane * S2 + n1];
+    } else {
+#pragma unroll
+      for (int n1 = 0; n1 < N2; ++n1) r3[n1] = make_float2(0.f, 0.f);
+    }
+    RegDFT<N2, true>::run(r3);
+    __syncwarp();
+    if (row_ok && lane < N1) {
+      float2 *dst = rows_out + ((size_t)it * n_pix + j) * N + lane;
+#pragma unroll
+      for (int k1 = 0; k1 < N2; ++k1) dst[N1 * k1] = r3[k1];   // x = N1 k1 + lane
+    }
+  }
+}
+
+// K: per tile of TC = blockDim.x / G columns (a multiple of the bin side):
+// column filter, |.|^2 / n_mod, b x b bins -> part[b % nbw][m][ybin][xbin].
+// grid (N / TC, n_items).
+template <int N1, int N2> struct ColFiltCfg {
+  using S = Split<N1, N2>;
+  static constexpr int CS = imax3(S::N, N2 * S::S1, N1 * S::S2) | 1;   // odd column stride
+};
+
+template <int N1, int N2>
+__global__ void __launch_bounds__(256, 3) k_colfilt_bin(
+    const float2 *__restrict__ rows_in, const float2 *__restrict__ twA,
+    const float2 *__restrict__ twB, const float2 *__restrict__ mask, float *__restrict__ part,
+    int n_pix, int bsz, float scale, int n_mod, int nbw, int item0) {
+  using S = Split<N1, N2>;
+  constexpr int N = S::N, G = S::G, S1 = S::S1, S2 = S::S2;
+  constexpr int CS = ColFiltCfg<N1, N2>::CS;
+  constexpr int Q0 = N2 / 4, QH = N2 / 2;
+  constexpr int off = N / 4;
+  extern __shared__ float2 smem[];
+  float2 *s_tile = smem;
+  const int TC = blockDim.x / G;
+  const int it = blockIdx.y;
+  const int col0 = blockIdx.x * TC;
+  {
+    // each thread stages one column of the tile, every G-th row, all
+    // copies in flight at once
+    const int c = threadIdx.x % TC;
+    const float2 *src = rows_in + (size_t)it * n_pix * N + col0 + c;
+    for (int jj = threadIdx.x / TC; jj < n_pix; jj += G)
+      cp_async8(s_tile + c * CS + off + jj, src + (size_t)jj * N);
+  }
+  const int vec = threadIdx.x / G, lane = threadIdx.x % G;
+  cp_async_wait_all();
+  __syncthreads();
+  float2 *col = s_tile + vec * CS;
+  float2 r[N2];
+#pragma unroll
+  for (int n2 = 0; n2 < N2; ++n2) r[n2] = make_float2(0.f, 0.f);
+  if (lane < N1) {
+#pragma unroll
+    for (int h = 0; h < QH; ++h) r[Q0 + h] = col[lane + N1 * (Q0 + h)];
+  }
+  RegDFT<N2, false>::run(r);
+  __syncwarp();
+  if (lane < N1) {
+#pragma unroll
+    for (int k2 = 0; k2 < N2; ++k2) col[k2 * S1 + lane] = cmulc(r[k2], __ldg(twA + k2 * N1 + lane));
+  }
+  __syncwarp();
+  float2 r2[N1];
+  if (lane < N2) {
+#pragma unroll
+    for (int n1 = 0; n1 < N1; ++n1) r2[n1] = col[lane * S1 + n1];
+  } else {
+#pragma unroll
+    for (int n1 = 0; n1 < N1; ++n1) r2[n1] = make_float2(0.f, 0.f);
+  }
+  RegDFT<N1, false>::run(r2);
+  if (lane < N2) {
+#pragma unroll
+    for (int k1 = 0; k1 < N1; ++k1) r2[k1] = cmul(r2[k1], __ldg(mask + N2 * k1 + lane));
+  }
+  RegDFT<N1, true>::run(r2);
+  __syncwarp();
+  if (lane < N2) {
+#pragma unroll
+    for (int k2 = 0; k2 < N1; ++k2) col[k2 * S2 + lane] = cmul(r2[k2], __ldg(twB + k2 * N2 + lane));
+  }
+  __syncwarp();
+  float2 r3[N2];
+  if (lane < N1) {
+#pragma unroll
+    for (int n1 = 0; n1 < N2; ++n1) r3[n1] = col[lane * S2 + n1];
+  } else {
+#pragma unroll
+    for (int n1 = 0; n1 < N2; ++n1) r3[n1] = make_float2(0.f, 0.f);
+  }
+  RegDFT<N2, true>::run(r3);
+  __syncwarp();
+  float *colI = reinterpret_cast<float *>(col);   // this column's intensity, y = N1 k1 + lane
+  if (lane < N1) {
+#pragma unroll
+    for (int k1 = 0; k1 < N2; ++k1)
+      colI[N1 * k1 + lane] = (r3[k1].x * r3[k1].x + r3[k1].y * r3[k1].y) * scale;
+  }
+  __syncthreads();
+  const int nd = N / bsz, nbx = TC / bsz;
+  const int gi = item0 + it;
+  const int b = gi / n_mod, m = gi - b * n_mod;
+  float *dst = part + ((size_t)(b % nbw) * n_mod + m) * nd * nd;
+  const float *s_I = reinterpret_cast<const float *>(smem);
+  for (int q = threadIdx.x; q < nd * nbx; q += blockDim.x) {
+    const int yb = q / nbx, xb = q - yb * nbx;
+    float v = 0.f;
+    for (int rr = 0; rr < bsz; ++rr)
+      for (int cc = 0; cc < bsz; ++cc) v += s_I[(size_t)(xb * bsz + cc) * 2 * CS + yb * bsz + rr];
+    dst[(size_t)yb * nd + col0 / bsz + xb] = v;
+  }
+}
+
+// --------------------------------------------------------------------------
 // D: det[b] = sum over m = 0 .. n_mod-1 of part[b % nbw][m], in order.
 // grid (ceil(nd^2 / 256), number of batch elements from b0).
 __global__ void __launch_bounds__(256) k_bin_reduce(const float *__restrict__ part,
@@ -331,12 +535,30 @@ static int configure(PwfsPlan *p) {
   p->smemC = (size_t)(nvecC * S::XB) * sizeof(float2);
   if (p->smemA > 227 * 1024 || p->smemB > 227 * 1024 || p->smemC > 227 * 1024)
     return SPECULA_EUNSUPPORTED;
-  SPECULA_CK(cudaFuncSetAttribute(k_rows_fwd<N1, N2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)p->smemA));
-  SPECULA_CK(cudaFuncSetAttribute(k_cols<N1, N2, kColsTile>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smemB));
-  SPECULA_CK(cudaFuncSetAttribute(k_rows_inv_part<N1, N2>,
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->smemC));
+  int s;
+  if ((s = ensure_dynamic_smem((const void *)k_rows_fwd<N1, N2>, p->smemA)) ||
+      (s = ensure_dynamic_smem((const void *)k_cols<N1, N2, kColsTile>, p->smemB)) ||
+      (s = ensure_dynamic_smem((const void *)k_rows_inv_part<N1, N2>, p->smemC)))
+    return s;
+  // two-pass form: column tiles of TC = k bsz columns, k the largest divisor
+  // of 2 n_sub with TC G <= 256
+  p->two_ok = false;
+  p->blockR = 256;
+  p->smemR = (size_t)(256 / S::G) * RowFiltCfg<N1, N2>::XBF * sizeof(float2);
+  int k = 0;
+  for (int d = 1; d <= 2 * p->n_sub; ++d)
+    if ((2 * p->n_sub) % d == 0 && d * bsz * S::G <= 256) k = d;
+  if (k > 0 && p->smemR <= 227 * 1024) {
+    const int tc = k * bsz;
+    p->blockK = tc * S::G;
+    p->smemK = (size_t)tc * ColFiltCfg<N1, N2>::CS * sizeof(float2);
+    if (p->smemK <= 227 * 1024 && S::N % tc == 0) {
+      if ((s = ensure_dynamic_smem((const void *)k_rowfilt<N1, N2>, p->smemR)) ||
+          (s = ensure_dynamic_smem((const void *)k_colfilt_bin<N1, N2>, p->smemK)))
+        return s;
+      p->two_ok = true;
+    }
+  }
   return SPECULA_OK;
 }
 
@@ -364,21 +586,36 @@ static int run_split(specula_ctx *ctx, PwfsPlan *p, const float *amp, const floa
       field_done = b1;
     }
     dim3 gA((Np + vpcA - 1) / vpcA, (ni + p->ka - 1) / p->ka);
-    SPECULA_LAUNCH(ctx, SPECULA_K_PWFS_ROWS_FWD, st,
-                   k_rows_fwd<N1, N2><<<gA, p->blockA, p->smemA, st>>>(
-                       p->field.as<float2>(), p->gx.as<float2>(), p->gy.as<float2>(),
-                       p->twA.as<float2>(), p->rows.as<float2>(), Np, p->n_mod, p->nbw, i0, ni,
-                       p->ka));
-    dim3 gB(S::N / kColsTile, ni);
-    SPECULA_LAUNCH(ctx, SPECULA_K_PWFS_COLS, st,
-                   k_cols<N1, N2, kColsTile><<<gB, p->blockB, p->smemB, st>>>(
-                       p->rows.as<float2>(), p->cols.as<float2>(), p->twA.as<float2>(),
-                       p->twB.as<float2>(), p->mask.as<float2>(), Np));
-    dim3 gC(S::N / bsz, ni);
-    SPECULA_LAUNCH(ctx, SPECULA_K_PWFS_ROWS_INV, st,
-                   k_rows_inv_part<N1, N2><<<gC, p->blockC, p->smemC, st>>>(
-                       p->cols.as<float2>(), p->twA.as<float2>(), p->part.as<float>(), bsz,
-                       scale, p->n_mod, p->nbw, i0));
+    if (p->passes == 2) {
+      SPECULA_LAUNCH(ctx, SPECULA_K_PWFS_ROWFILT, st,
+                     k_rowfilt<N1, N2><<<gA, p->blockR, p->smemR, st>>>(
+                         p->field.as<float2>(), p->gx.as<float2>(), p->gy.as<float2>(),
+                         p->twA.as<float2>(), p->twB.as<float2>(), p->mask.as<float2>(),
+                         p->rows.as<float2>(), Np, p->n_mod, p->nbw, i0, ni, p->ka));
+      const int tc = p->blockK / S::G;
+      dim3 gK(S::N / tc, ni);
+      SPECULA_LAUNCH(ctx, SPECULA_K_PWFS_COLFILT, st,
+                     k_colfilt_bin<N1, N2><<<gK, p->blockK, p->smemK, st>>>(
+                         p->rows.as<float2>(), p->twA.as<float2>(), p->twB.as<float2>(),
+                         p->mask.as<float2>(), p->part.as<float>(), Np, bsz, scale, p->n_mod,
+                         p->nbw, i0));
+    } else {
+      SPECULA_LAUNCH(ctx, SPECULA_K_PWFS_ROWS_FWD, st,
+                     k_rows_fwd<N1, N2><<<gA, p->blockA, p->smemA, st>>>(
+                         p->field.as<float2>(), p->gx.as<float2>(), p->gy.as<float2>(),
+                         p->twA.as<float2>(), p->rows.as<float2>(), Np, p->n_mod, p->nbw, i0,
+                         ni, p->ka));
+      dim3 gB(S::N / kColsTile, ni);
+      SPECULA_LAUNCH(ctx, SPECULA_K_PWFS_COLS, st,
+                     k_cols<N1, N2, kColsTile><<<gB, p->blockB, p->smemB, st>>>(
+                         p->rows.as<float2>(), p->cols.as<float2>(), p->twA.as<float2>(),
+                         p->twB.as<float2>(), p->mask.as<float2>(), Np));
+      dim3 gC(S::N / bsz, ni);
+      SPECULA_LAUNCH(ctx, SPECULA_K_PWFS_ROWS_INV, st,
+                     k_rows_inv_part<N1, N2><<<gC, p->blockC, p->smemC, st>>>(
+                         p->cols.as<float2>(), p->twA.as<float2>(), p->part.as<float>(), bsz,
+                         scale, p->n_mod, p->nbw, i0));
+    }
     // batch elements whose last modulation point is in this chunk
     const int complete = (i0 + ni) / p->n_mod - 1;
     if (complete > det_done) {
@@ -403,12 +640,14 @@ bool pwfs_split_for(int N, int *N1, int *N2) {
   }
 }
 
-int pwfs_set_tiles(PwfsPlan *p, int chunk, int ka) {
+int pwfs_set_tiles(PwfsPlan *p, int chunk, int ka, int passes) {
+  if (passes != 2 && passes != 3) return SPECULA_EINVAL;
+  if (passes == 2 && !p->two_ok) return SPECULA_EUNSUPPORTED;
   const int nd = 2 * p->n_sub;
   const int nbw = (chunk + p->n_mod - 1) / p->n_mod + 1;
   const size_t need_field = (size_t)nbw * p->n_pix * p->n_pix * sizeof(float2);
   const size_t need_rows = (size_t)chunk * p->n_pix * p->N * sizeof(float2);
-  const size_t need_cols = (size_t)chunk * p->N * p->N * sizeof(float2);
+  const size_t need_cols = passes == 3 ? (size_t)chunk * p->N * p->N * sizeof(float2) : 0;
   const size_t need_part = (size_t)nbw * p->n_mod * nd * nd * sizeof(float);
   int s;
   if (need_rows > p->rows.bytes || need_cols > p->cols.bytes || need_field > p->field.bytes ||
@@ -416,12 +655,13 @@ int pwfs_set_tiles(PwfsPlan *p, int chunk, int ka) {
     cudaDeviceSynchronize();   // the old workspace may still be in use
     if ((s = p->field.alloc(std::max(need_field, p->field.bytes)))) return s;
     if ((s = p->rows.alloc(std::max(need_rows, p->rows.bytes)))) return s;
-    if ((s = p->cols.alloc(std::max(need_cols, p->cols.bytes)))) return s;
+    if (need_cols > p->cols.bytes && (s = p->cols.alloc(need_cols))) return s;
     if ((s = p->part.alloc(std::max(need_part, p->part.bytes)))) return s;
   }
   p->chunk = chunk;
   p->ka = ka;
   p->nbw = nbw;
+  p->passes = passes;
   return SPECULA_OK;
 }
 
@@ -441,36 +681,41 @@ int pwfs_run(specula_ctx *ctx, PwfsPlan *p, const float *amp, const float *phase
 // reallocate the workspace and synchronises) and keep the fastest.
 int pwfs_autotune(specula_ctx *ctx, PwfsPlan *p, const float *amp, const float *phase,
                   int n_batch, float *det, cudaStream_t st, int reps, size_t max_ws_bytes,
-                  int *best_chunk, int *best_ka) {
+                  int *best_chunk, int *best_ka, int *best_passes) {
   static const int kChunks[] = {1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64};
   const size_t per_item = ((size_t)p->n_pix * p->N + (size_t)p->N * p->N) * sizeof(float2);
   const int total = n_batch * p->n_mod;
   float best = 1e30f;
-  int bc = p->chunk, bk = p->ka;
+  int bc = p->chunk, bk = p->ka, bp = p->passes;
   cudaEvent_t e0, e1;
   SPECULA_CK(cudaEventCreate(&e0));
   SPECULA_CK(cudaEventCreate(&e1));
   int status = SPECULA_OK;
-  for (int c : kChunks) {
-    if (c > std::max(total, 1) && c != 1) break;
-    if ((size_t)c * per_item > max_ws_bytes && c != 1) break;
-    for (int ka = 1; ka <= 2; ++ka) {
-      if (ka > c) break;
-      if ((status = pwfs_set_tiles(p, c, ka))) goto done;
-      if ((status = pwfs_run(ctx, p, amp, phase, n_batch, det, st))) goto done;   // warm-up
-      cudaEventRecord(e0, st);
-      for (int r = 0; r < reps; ++r)
-        if ((status = pwfs_run(ctx, p, amp, phase, n_batch, det, st))) goto done;
-      cudaEventRecord(e1, st);
-      if (cudaEventSynchronize(e1) != cudaSuccess) { status = SPECULA_ECUDA; goto done; }
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      if (ms < best) { best = ms; bc = c; bk = ka; }
+  for (int passes = 2; passes <= 3; ++passes) {
+    if (passes == 2 && !p->two_ok) continue;
+    const size_t item = passes == 2 ? (size_t)p->n_pix * p->N * sizeof(float2) : per_item;
+    for (int c : kChunks) {
+      if (c > std::max(total, 1) && c != 1) break;
+      if ((size_t)c * item > max_ws_bytes && c != 1) break;
+      for (int ka = 1; ka <= 2; ++ka) {
+        if (ka > c) break;
+        if ((status = pwfs_set_tiles(p, c, ka, passes))) goto done;
+        if ((status = pwfs_run(ctx, p, amp, phase, n_batch, det, st))) goto done;   // warm-up
+        cudaEventRecord(e0, st);
+        for (int r = 0; r < reps; ++r)
+          if ((status = pwfs_run(ctx, p, amp, phase, n_batch, det, st))) goto done;
+        cudaEventRecord(e1, st);
+        if (cudaEventSynchronize(e1) != cudaSuccess) { status = SPECULA_ECUDA; goto done; }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) { best = ms; bc = c; bk = ka; bp = passes; }
+      }
     }
   }
-  status = pwfs_set_tiles(p, bc, bk);
+  status = pwfs_set_tiles(p, bc, bk, bp);
   *best_chunk = bc;
   *best_ka = bk;
+  *best_passes = bp;
 done:
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -580,7 +825,7 @@ int pwfs_plan_build(specula_ctx *ctx, const specula_pupil_desc *pupil,
   const size_t per_item = ((size_t)Np * N + (size_t)N * N) * sizeof(float2);
   int chunk = (int)std::max<size_t>(1, (48u << 20) / per_item);
   chunk = std::min(chunk, 64);
-  if ((s = pwfs_set_tiles(p.get(), chunk, 1))) return s;
+  if ((s = pwfs_set_tiles(p.get(), chunk, 1, p->two_ok ? 2 : 3))) return s;
   *out = p.get();
   ctx->pwfs.push_back(std::move(p));
   return SPECULA_OK;

@@ -331,8 +331,7 @@ extern "C" int specula_screen_generate(specula_ctx *ctx, int32_t side, double pi
                                                           A.as<double2>(), M, Md, coef, k0);
   SPECULA_CK_LAUNCH();
   const size_t sm = 2 * (size_t)M * sizeof(double2);
-  if (sm > 48 * 1024)
-    SPECULA_CK(cudaFuncSetAttribute(k_fft_rows_f64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  if ((s = ensure_dynamic_smem((const void *)k_fft_rows_f64, sm))) return s;
   k_fft_rows_f64<<<M, 256, sm, st>>>(A.as<double2>(), dtw.as<double2>(), M, logM);
   SPECULA_CK_LAUNCH();
   k_transpose_f64<<<dim3(M / 32, M / 32), dim3(32, 8), 0, st>>>(A.as<double2>(), B.as<double2>(), M);
@@ -419,9 +418,7 @@ extern "C" int specula_screen_generate_batch(specula_ctx *ctx, int32_t n_screens
       (s = cf.alloc((size_t)G * 27 * sizeof(double2))) || (s = sm.alloc((size_t)G * sizeof(double))))
     return s;
   const size_t smem = 2 * (size_t)M * sizeof(double2);
-  if (smem > 48 * 1024)
-    SPECULA_CK(cudaFuncSetAttribute(k_fft_rows_f64, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)smem));
+  if ((s = ensure_dynamic_smem((const void *)k_fft_rows_f64, smem))) return s;
   for (int g0 = 0; g0 < n_screens; g0 += G) {
     const int ng = std::min(G, n_screens - g0);
     const long long pairs = (long long)M * M / 2;

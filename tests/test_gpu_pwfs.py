@@ -36,12 +36,14 @@ def env():
     ctx.close()
 
 
-def _run(torch, sp, ctx, n_pix, n_mod, r, obsc, n_sub, phases, chunk=None, ka=None):
+def _run(torch, sp, ctx, n_pix, n_mod, r, obsc, n_sub, phases, chunk=None, ka=None,
+         passes=None):
     pu = sp.PupilDesc(n_pix, 0.1, obsc)
     pw = sp.PwfsDesc(2, n_mod, n_sub, n_pix, r)
     sp.specula_pwfs_plan(ctx, pu, pw)
-    if chunk:
-        sp.specula_pwfs_set_tiles(ctx, pu, pw, chunk, ka)
+    if chunk or passes:
+        ch0, ka0, ps0 = sp.specula_pwfs_get_tiles(ctx, pu, pw)
+        sp.specula_pwfs_set_tiles(ctx, pu, pw, chunk or ch0, ka or ka0, passes or ps0)
     amp = torch.empty(n_pix, n_pix, device="cuda", dtype=torch.float32)
     sp.specula_pupil_mask(ctx, pu, amp)
     ph = torch.tensor(np.stack(phases).astype(np.float32), device="cuda")
@@ -51,16 +53,19 @@ def _run(torch, sp, ctx, n_pix, n_mod, r, obsc, n_sub, phases, chunk=None, ka=No
     return det.cpu().numpy().astype(np.float64)
 
 
+@pytest.mark.parametrize("passes", [2, 3])
 @pytest.mark.parametrize("case", CASES, ids=lambda c: f"N{2 * c[0]}")
-def test_pwfs_intensity_and_detector_parity(env, case):
+def test_pwfs_intensity_and_detector_parity(env, case, passes):
+    """Both forms of the 2D filter (separable two-pass, three-pass) against
+    the oracle."""
     torch, sp, ctx = env
     n_pix, n_mod, r, obsc, n_sub, nb, chunk, ka = case
     amp = pupil_amp(n_pix, obsc)
     phases = [kolmogorov_phase(n_pix, 8.0 / n_pix, 0.15, seed=11 + k).astype(np.float32)
               for k in range(nb)]
     # unbinned: n_sub = n_pix gives the N x N intensity
-    I_gpu = _run(torch, sp, ctx, n_pix, n_mod, r, obsc, n_pix, phases, chunk, ka)
-    det_gpu = _run(torch, sp, ctx, n_pix, n_mod, r, obsc, n_sub, phases, chunk, ka)
+    I_gpu = _run(torch, sp, ctx, n_pix, n_mod, r, obsc, n_pix, phases, chunk, ka, passes)
+    det_gpu = _run(torch, sp, ctx, n_pix, n_mod, r, obsc, n_sub, phases, chunk, ka, passes)
     for k in range(nb):
         I_ref = pyramid.pwfs_intensity(amp, phases[k].astype(np.float64), 2, n_mod, r, n_pix)
         e1 = norm_intensity_error(I_gpu[k], I_ref)
@@ -124,17 +129,19 @@ def test_pwfs_slopes_parity(env):
 
 def test_pwfs_full_size_elt(env):
     """The 39 m ELT-scale geometry at full size (480 px pupil, 960^2 FFT, 48
-    modulation points, 96 x 96 subapertures), one frame, compared in full."""
+    modulation points, 96 x 96 subapertures), one frame, compared in full,
+    in both forms of the 2D filter."""
     torch, sp, ctx = env
     n_pix, n_mod, r, obsc, n_sub = 480, 48, 4.0, 0.28, 96
     amp = pupil_amp(n_pix, obsc)
     phi = kolmogorov_phase(n_pix, 39.0 / n_pix, 0.157, seed=5, side=1024).astype(np.float32)
-    det_gpu = _run(torch, sp, ctx, n_pix, n_mod, r, obsc, n_sub, [phi])[0]
     I_ref = pyramid.pwfs_intensity(amp, phi.astype(np.float64), 2, n_mod, r, n_pix)
     det_ref = pyramid.bin_image(I_ref, n_pix // n_sub)
-    assert norm_intensity_error(det_gpu, det_ref) <= EPS
-    I_gpu = _run(torch, sp, ctx, n_pix, n_mod, r, obsc, n_pix, [phi])[0]
-    assert norm_intensity_error(I_gpu, I_ref) <= EPS
+    for passes in (2, 3):
+        det_gpu = _run(torch, sp, ctx, n_pix, n_mod, r, obsc, n_sub, [phi], passes=passes)[0]
+        assert norm_intensity_error(det_gpu, det_ref) <= EPS, passes
+        I_gpu = _run(torch, sp, ctx, n_pix, n_mod, r, obsc, n_pix, [phi], passes=passes)[0]
+        assert norm_intensity_error(I_gpu, I_ref) <= EPS, passes
 
 
 def test_plan_required_and_bad_args(env):
@@ -155,9 +162,10 @@ def test_plan_required_and_bad_args(env):
 
 
 def test_tiling_invariance_and_autotune(env):
-    """Every (chunk, ka) tiling gives a bit-identical detector (item bins are
-    reduced in modulation order whatever the chunking), and the autotuner
-    returns one of the candidates."""
+    """For each form of the 2D filter, every (chunk, ka) tiling gives a
+    bit-identical detector (item bins are reduced in modulation order
+    whatever the chunking); the two forms agree to float rounding; the
+    autotuner returns one of the candidates."""
     torch, sp, ctx = env
     n_pix, n_mod, n_sub = 32, 8, 8
     pu = sp.PupilDesc(n_pix, 0.25, 0.2)
@@ -167,19 +175,24 @@ def test_tiling_invariance_and_autotune(env):
     sp.specula_pupil_mask(ctx, pu, amp)
     ph = torch.tensor(np.stack([kolmogorov_phase(n_pix, 0.25, 0.15, seed=s) for s in (1, 2, 3)])
                       .astype(np.float32), device="cuda")
-    outs = []
-    for chunk, ka in [(1, 1), (3, 2), (5, 1), (8, 2), (24, 1)]:
-        sp.specula_pwfs_set_tiles(ctx, pu, pw, chunk, ka)
-        det = torch.empty(3, 2 * n_sub, 2 * n_sub, device="cuda")
-        sp.specula_pwfs_image(ctx, pu, pw, amp, ph, det)
-        torch.cuda.synchronize()
-        outs.append(det.cpu())
-    for o in outs[1:]:
-        assert torch.equal(o, outs[0])
+    first = {}
+    for passes in (2, 3):
+        outs = []
+        for chunk, ka in [(1, 1), (3, 2), (5, 1), (8, 2), (24, 1)]:
+            sp.specula_pwfs_set_tiles(ctx, pu, pw, chunk, ka, passes)
+            det = torch.empty(3, 2 * n_sub, 2 * n_sub, device="cuda")
+            sp.specula_pwfs_image(ctx, pu, pw, amp, ph, det)
+            torch.cuda.synchronize()
+            outs.append(det.cpu())
+        for o in outs[1:]:
+            assert torch.equal(o, outs[0])
+        first[passes] = outs[0]
+    for k in range(3):
+        assert norm_intensity_error(first[2][k].numpy(), first[3][k].numpy()) <= 1e-6
     det = torch.empty(3, 2 * n_sub, 2 * n_sub, device="cuda")
-    ch, ka = sp.specula_pwfs_autotune(ctx, pu, pw, amp, ph, det, reps=2)
-    assert ch in (1, 2, 3, 4, 6, 8, 12, 16, 24) and ka in (1, 2)
-    assert sp.specula_pwfs_get_tiles(ctx, pu, pw) == (ch, ka)
+    ch, ka, ps = sp.specula_pwfs_autotune(ctx, pu, pw, amp, ph, det, reps=2)
+    assert ch in (1, 2, 3, 4, 6, 8, 12, 16, 24) and ka in (1, 2) and ps in (2, 3)
+    assert sp.specula_pwfs_get_tiles(ctx, pu, pw) == (ch, ka, ps)
     sp.specula_pwfs_image(ctx, pu, pw, amp, ph, det)
     torch.cuda.synchronize()
-    assert torch.equal(det.cpu(), outs[0])
+    assert torch.equal(det.cpu(), first[ps])
