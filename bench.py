@@ -56,20 +56,24 @@ def fft_flops(n):
 
 
 def kernel_flops(wl):
-    """Algorithmic FLOPs per (batch, modulation point) item of each pyramid
-    pass (benchFFT convention 5 N log2 N per N-point transform, pruned inputs
-    counted as full transforms; element-wise work not counted).  Two-pass
-    form: the row filter transforms the n_pix pupil rows forward and back,
-    the column filter all N columns forward and back; three-pass form: n_pix
-    forward rows, N columns forward and back, N inverse rows."""
+    """Algorithmic FLOPs per frame of each pyramid pass (benchFFT convention
+    5 N log2 N per N-point transform, pruned inputs counted as full
+    transforms; element-wise work not counted).  Two-pass form: the row
+    filter transforms the n_pix pupil rows forward and back once per distinct
+    cosine of the modulation angles (n_mod / 2 + 1 of them: points m and
+    n_mod - m share the row filter), the column filter all N columns forward
+    and back for every modulation point; three-pass form: n_pix forward rows,
+    N columns forward and back, N inverse rows, per modulation point."""
     s = wl.sensors[0]
     n = s.pupil.n_pix
     N = s.pwfs.pad * n
-    return {"pwfs_rowfilt": 2 * n * fft_flops(N),
-            "pwfs_colfilt_bin": 2 * N * fft_flops(N),
-            "pwfs_rows_fwd": n * fft_flops(N),
-            "pwfs_cols": 2 * N * fft_flops(N),
-            "pwfs_rows_inv": N * fft_flops(N)}
+    n_mod = s.pwfs.n_mod
+    nc = n_mod // 2 + 1
+    return {"pwfs_rowfilt": nc * 2 * n * fft_flops(N),
+            "pwfs_colfilt_bin": n_mod * 2 * N * fft_flops(N),
+            "pwfs_rows_fwd": n_mod * n * fft_flops(N),
+            "pwfs_cols": n_mod * 2 * N * fft_flops(N),
+            "pwfs_rows_inv": n_mod * N * fft_flops(N)}
 
 
 class ClockSampler:
@@ -577,7 +581,7 @@ def gpu_leg(args, ws, rank, local):
     sp.specula_prof_enable(ctx, 0)
     pk, how = peaks()
     flops = kernel_flops(wl)
-    n_items = wl.sensors[0].pwfs.n_mod * K
+    n_frames = K
     kern = {}
     for name, (tms, n) in prof.items():
         kern[name] = {"total_ms": tms, "launches": n, "share": 0.0}
@@ -591,16 +595,16 @@ def gpu_leg(args, ws, rank, local):
     roof = None
     traffic = read_traffic()
     if dom in flops:
-        achieved = flops[dom] * n_items / (kern[dom]["total_ms"] / 1e3) / 1e12
+        achieved = flops[dom] * n_frames / (kern[dom]["total_ms"] / 1e3) / 1e12
         tr = traffic.get((dom, WORKLOAD))
         roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak_alu,
                 "unit": "TFLOP/s", "frac": achieved / peak_alu,
                 "traffic": tr * 1.0 if tr is not None else None,
                 "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz (derived)",
-                "flops_per_launch": flops[dom] * n_items / kern[dom]["launches"]}
+                "flops_per_launch": flops[dom] * n_frames / kern[dom]["launches"]}
     for name in flops:
         if name in kern:
-            kern[name]["achieved_tflops"] = flops[name] * n_items / (kern[name]["total_ms"] / 1e3) / 1e12
+            kern[name]["achieved_tflops"] = flops[name] * n_frames / (kern[name]["total_ms"] / 1e3) / 1e12
     if "recon" in kern:
         rb = fr.n_modes * fr.n_slopes * 4.0
         gbs = rb * kern["recon"]["launches"] / (kern["recon"]["total_ms"] / 1e3) / 1e9

@@ -66,6 +66,7 @@ struct PwfsPlan {
   int blockA, blockB, blockC;
   size_t smemA, smemB, smemC;
   int passes;           // 2: row filter + column filter/bins; 3: rows, cols, rows
+  int nc;               // row-filter slots per batch element (distinct cosines)
   bool two_ok;          // the two-pass form fits this geometry
   int blockR, blockK;   // two-pass blocks (K: TC columns x G lanes)
   size_t smemR, smemK;

@@ -312,13 +312,18 @@ template <int N1, int N2> struct RowFiltCfg {
   static constexpr int XBF = N2 * S::S1 > N1 * S::S2 ? N2 * S::S1 : N1 * S::S2;
 };
 
-// R: grid (ceil(n_pix / VPC), ceil(n_items / ka)); block VPC * G threads.
+// Points m and n_mod - m share cos(theta), hence the x factor of the tilt;
+// their y factors are constant along a row and commute with the row filter.
+// So the row filter runs once per distinct cosine ("slot" c = 0 .. nc-1,
+// representative m = c) without the y factor, and the column pass applies
+// each item's own y factor gy[m][row] to its input.
+// R: grid (ceil(n_pix / VPC), ceil(n_slots / ka)); block VPC * G threads.
 template <int N1, int N2>
 __global__ void __launch_bounds__(256, 2) k_rowfilt(
     const float2 *__restrict__ field, const float2 *__restrict__ gx,
-    const float2 *__restrict__ gy, const float2 *__restrict__ twA, const float2 *__restrict__ twB,
-    const float2 *__restrict__ mask, float2 *__restrict__ rows_out, int n_pix, int n_mod, int nbw,
-    int item0, int n_items, int ka) {
+    const float2 *__restrict__ twA, const float2 *__restrict__ twB,
+    const float2 *__restrict__ mask, float2 *__restrict__ rows_out, int n_pix, int nc, int nbw,
+    int slot0, int n_slots, int ka) {
   using S = Split<N1, N2>;
   constexpr int N = S::N, G = S::G, S1 = S::S1, S2 = S::S2;
   constexpr int Q0 = N2 / 4, QH = N2 / 2;
@@ -334,9 +339,9 @@ __global__ void __launch_bounds__(256, 2) k_rowfilt(
   const int it_begin = blockIdx.y * ka;
   for (int q = 0; q < ka; ++q) {
     const int it = it_begin + q;
-    if (it >= n_items) break;
-    const int gi = item0 + it;
-    const int b = gi / n_mod, m = gi - b * n_mod;
+    if (it >= n_slots) break;
+    const int gi = slot0 + it;
+    const int b = gi / nc, c = gi - b * nc;
     if (b != cur_b) {
       cur_b = b;
       const float2 *src = field + ((size_t)(b % nbw) * n_pix + (row_ok ? j : 0)) * n_pix + lane;
@@ -345,13 +350,12 @@ __global__ void __launch_bounds__(256, 2) k_rowfilt(
     }
     // forward row transform, pruned input (standard split)
     float2 r[N2];
-    const float2 gyv = row_ok ? gy[(size_t)m * n_pix + j] : make_float2(0.f, 0.f);
 #pragma unroll
     for (int n2 = 0; n2 < N2; ++n2) r[n2] = make_float2(0.f, 0.f);
     if (in_lane) {
-      const float2 *g = gx + (size_t)m * n_pix + lane;
+      const float2 *g = gx + (size_t)c * n_pix + lane;
 #pragma unroll
-      for (int h = 0; h < QH; ++h) r[Q0 + h] = cmul(cmul(e[h], __ldg(g + N1 * h)), gyv);
+      for (int h = 0; h < QH; ++h) r[Q0 + h] = cmul(e[h], __ldg(g + N1 * h));
     }
     RegDFT<N2, false>::run(r);
     __syncwarp();
@@ -400,8 +404,9 @@ __global__ void __launch_bounds__(256, 2) k_rowfilt(
 }
 
 // K: per tile of TC = blockDim.x / G columns (a multiple of the bin side):
-// column filter, |.|^2 / n_mod, b x b bins -> part[b % nbw][m][ybin][xbin].
-// grid (N / TC, n_items).
+// the item's y tilt, column filter, |.|^2 / n_mod, b x b bins ->
+// part[b % nbw][m][ybin][xbin].  grid (N / TC, 2 n_slots): y = 2 p + w is
+// item m = c (w = 0) or m = n_mod - c (w = 1, when distinct) of slot p.
 template <int N1, int N2> struct ColFiltCfg {
   using S = Split<N1, N2>;
   static constexpr int CS = imax3(S::N, N2 * S::S1, N1 * S::S2) | 1;   // odd column stride
@@ -409,9 +414,10 @@ template <int N1, int N2> struct ColFiltCfg {
 
 template <int N1, int N2>
 __global__ void __launch_bounds__(256, 3) k_colfilt_bin(
-    const float2 *__restrict__ rows_in, const float2 *__restrict__ twA,
-    const float2 *__restrict__ twB, const float2 *__restrict__ mask, float *__restrict__ part,
-    int n_pix, int bsz, float scale, int n_mod, int nbw, int item0) {
+    const float2 *__restrict__ rows_in, const float2 *__restrict__ gy,
+    const float2 *__restrict__ twA, const float2 *__restrict__ twB,
+    const float2 *__restrict__ mask, float *__restrict__ part, int n_pix, int bsz, float scale,
+    int n_mod, int nc, int nbw, int slot0) {
   using S = Split<N1, N2>;
   constexpr int N = S::N, G = S::G, S1 = S::S1, S2 = S::S2;
   constexpr int CS = ColFiltCfg<N1, N2>::CS;
@@ -420,7 +426,11 @@ __global__ void __launch_bounds__(256, 3) k_colfilt_bin(
   extern __shared__ float2 smem[];
   float2 *s_tile = smem;
   const int TC = blockDim.x / G;
-  const int it = blockIdx.y;
+  const int it = blockIdx.y >> 1;              // slot within the chunk
+  const int gs = slot0 + it;
+  const int b = gs / nc, cslot = gs - b * nc;
+  const int m = (blockIdx.y & 1) ? n_mod - cslot : cslot;
+  if ((blockIdx.y & 1) && (cslot == 0 || 2 * cslot == n_mod)) return;   // no second item
   const int col0 = blockIdx.x * TC;
   {
     // each thread stages one column of the tile, every G-th row, all
@@ -438,8 +448,9 @@ __global__ void __launch_bounds__(256, 3) k_colfilt_bin(
 #pragma unroll
   for (int n2 = 0; n2 < N2; ++n2) r[n2] = make_float2(0.f, 0.f);
   if (lane < N1) {
+    const float2 *g = gy + (size_t)m * n_pix + lane;   // pupil row lane + N1 h
 #pragma unroll
-    for (int h = 0; h < QH; ++h) r[Q0 + h] = col[lane + N1 * (Q0 + h)];
+    for (int h = 0; h < QH; ++h) r[Q0 + h] = cmul(col[lane + N1 * (Q0 + h)], __ldg(g + N1 * h));
   }
   RegDFT<N2, false>::run(r);
   __syncwarp();
@@ -486,8 +497,6 @@ __global__ void __launch_bounds__(256, 3) k_colfilt_bin(
   }
   __syncthreads();
   const int nd = N / bsz, nbx = TC / bsz;
-  const int gi = item0 + it;
-  const int b = gi / n_mod, m = gi - b * n_mod;
   float *dst = part + ((size_t)(b % nbw) * n_mod + m) * nd * nd;
   const float *s_I = reinterpret_cast<const float *>(smem);
   for (int q = threadIdx.x; q < nd * nbx; q += blockDim.x) {
@@ -562,9 +571,60 @@ static int configure(PwfsPlan *p) {
   return SPECULA_OK;
 }
 
+// Two-pass form, one chunk of `chunk` row-filter slots (batch element,
+// distinct cosine) at a time; each slot feeds one or two column items.
+template <int N1, int N2>
+static int run_split2(specula_ctx *ctx, PwfsPlan *p, const float *amp, const float *phase,
+                      int n_batch, float *det, cudaStream_t st) {
+  using S = Split<N1, N2>;
+  const int Np = p->n_pix;
+  const int bsz = Np / p->n_sub;
+  const int nd = S::N / bsz;
+  const int nc = p->nc;
+  const int total = n_batch * nc;
+  const int vpc = p->blockR / S::G;
+  const int tc = p->blockK / S::G;
+  const float scale = 1.0f / (float)p->n_mod;
+  int field_done = -1, det_done = -1;
+  for (int j0 = 0; j0 < total; j0 += p->chunk) {
+    const int nj = std::min(p->chunk, total - j0);
+    const int b0 = j0 / nc, b1 = (j0 + nj - 1) / nc;
+    const int fb = std::max(b0, field_done + 1);
+    if (fb <= b1) {
+      dim3 gF((Np * Np + 255) / 256, b1 - fb + 1);
+      SPECULA_LAUNCH(ctx, SPECULA_K_PWFS_FIELD, st,
+                     k_field<<<gF, 256, 0, st>>>(amp, phase, p->field.as<float2>(), Np * Np, fb,
+                                                 p->nbw));
+      field_done = b1;
+    }
+    dim3 gR((Np + vpc - 1) / vpc, (nj + p->ka - 1) / p->ka);
+    SPECULA_LAUNCH(ctx, SPECULA_K_PWFS_ROWFILT, st,
+                   k_rowfilt<N1, N2><<<gR, p->blockR, p->smemR, st>>>(
+                       p->field.as<float2>(), p->gx.as<float2>(), p->twA.as<float2>(),
+                       p->twB.as<float2>(), p->mask.as<float2>(), p->rows.as<float2>(), Np, nc,
+                       p->nbw, j0, nj, p->ka));
+    dim3 gK(S::N / tc, 2 * nj);
+    SPECULA_LAUNCH(ctx, SPECULA_K_PWFS_COLFILT, st,
+                   k_colfilt_bin<N1, N2><<<gK, p->blockK, p->smemK, st>>>(
+                       p->rows.as<float2>(), p->gy.as<float2>(), p->twA.as<float2>(),
+                       p->twB.as<float2>(), p->mask.as<float2>(), p->part.as<float>(), Np, bsz,
+                       scale, p->n_mod, nc, p->nbw, j0));
+    const int complete = (j0 + nj) / nc - 1;
+    if (complete > det_done) {
+      dim3 gD((nd * nd + 255) / 256, complete - det_done);
+      SPECULA_LAUNCH(ctx, SPECULA_K_PWFS_BIN, st,
+                     k_bin_reduce<<<gD, 256, 0, st>>>(p->part.as<float>(), det, nd * nd,
+                                                      p->n_mod, p->nbw, det_done + 1));
+      det_done = complete;
+    }
+  }
+  return SPECULA_OK;
+}
+
 template <int N1, int N2>
 static int run_split(specula_ctx *ctx, PwfsPlan *p, const float *amp, const float *phase,
                      int n_batch, float *det, cudaStream_t st) {
+  if (p->passes == 2) return run_split2<N1, N2>(ctx, p, amp, phase, n_batch, det, st);
   using S = Split<N1, N2>;
   const int Np = p->n_pix;
   const int bsz = Np / p->n_sub;
@@ -586,20 +646,7 @@ static int run_split(specula_ctx *ctx, PwfsPlan *p, const float *amp, const floa
       field_done = b1;
     }
     dim3 gA((Np + vpcA - 1) / vpcA, (ni + p->ka - 1) / p->ka);
-    if (p->passes == 2) {
-      SPECULA_LAUNCH(ctx, SPECULA_K_PWFS_ROWFILT, st,
-                     k_rowfilt<N1, N2><<<gA, p->blockR, p->smemR, st>>>(
-                         p->field.as<float2>(), p->gx.as<float2>(), p->gy.as<float2>(),
-                         p->twA.as<float2>(), p->twB.as<float2>(), p->mask.as<float2>(),
-                         p->rows.as<float2>(), Np, p->n_mod, p->nbw, i0, ni, p->ka));
-      const int tc = p->blockK / S::G;
-      dim3 gK(S::N / tc, ni);
-      SPECULA_LAUNCH(ctx, SPECULA_K_PWFS_COLFILT, st,
-                     k_colfilt_bin<N1, N2><<<gK, p->blockK, p->smemK, st>>>(
-                         p->rows.as<float2>(), p->twA.as<float2>(), p->twB.as<float2>(),
-                         p->mask.as<float2>(), p->part.as<float>(), Np, bsz, scale, p->n_mod,
-                         p->nbw, i0));
-    } else {
+    {
       SPECULA_LAUNCH(ctx, SPECULA_K_PWFS_ROWS_FWD, st,
                      k_rows_fwd<N1, N2><<<gA, p->blockA, p->smemA, st>>>(
                          p->field.as<float2>(), p->gx.as<float2>(), p->gy.as<float2>(),
@@ -644,7 +691,10 @@ int pwfs_set_tiles(PwfsPlan *p, int chunk, int ka, int passes) {
   if (passes != 2 && passes != 3) return SPECULA_EINVAL;
   if (passes == 2 && !p->two_ok) return SPECULA_EUNSUPPORTED;
   const int nd = 2 * p->n_sub;
-  const int nbw = (chunk + p->n_mod - 1) / p->n_mod + 1;
+  // batch elements one chunk can touch: chunk items (three-pass) or chunk
+  // row-filter slots, nc per batch element (two-pass)
+  const int per_b = passes == 2 ? p->nc : p->n_mod;
+  const int nbw = (chunk + per_b - 1) / per_b + 1;
   const size_t need_field = (size_t)nbw * p->n_pix * p->n_pix * sizeof(float2);
   const size_t need_rows = (size_t)chunk * p->n_pix * p->N * sizeof(float2);
   const size_t need_cols = passes == 3 ? (size_t)chunk * p->N * p->N * sizeof(float2) : 0;
@@ -810,6 +860,8 @@ int pwfs_plan_build(specula_ctx *ctx, const specula_pupil_desc *pupil,
   p->n_pix = Np; p->pad = d->pad; p->n_mod = d->n_mod; p->n_sub = d->n_sub;
   p->pup_dist = d->pup_dist_px; p->mod_amp = d->mod_amp;
   p->N = N; p->N1 = N1; p->N2 = N2;
+  // distinct cosines of the modulation angles 2 pi m / n_mod: m and n_mod - m
+  p->nc = d->n_mod / 2 + 1;
   int s = configure_for(p.get());
   if (s) return s;
   PwfsTablesHost T;
