@@ -14,16 +14,17 @@ __device__ __forceinline__ float warp_sum(float v) {
   return v;
 }
 
-// One CTA per batch element.
-// An index outside [0, n_sub^2) is recorded in the status word and read as
-// subaperture 0 (never out of bounds).
-__device__ __forceinline__ int checked_idx(const int32_t *idx, int k, int n_sub, int32_t *status) {
-  int s = idx[k];
-  if (s < 0 || s >= n_sub * n_sub) {
-    atomicExch(status, SPECULA_EINVAL);
-    s = 0;
-  }
-  return s;
+// grid (ceil(n_valid / kPyrThreads), n_batch): every CTA forms the global
+// normalisation T itself (the detector is small and L2-resident; the same
+// fixed-order reduction in every CTA gives the same T bit for bit), then
+// the slopes of its kPyrThreads subapertures.  Index checks are branch-free
+// (an out-of-range index reads subaperture 0 and is reported once per CTA),
+// so the loads of several subapertures are in flight together.
+__device__ __forceinline__ float quad_sum(const float *d, int s, int n_sub, int w2) {
+  const int a = s / n_sub, c = s - a * n_sub;
+  const float q1 = d[(n_sub + a) * w2 + n_sub + c], q2 = d[(n_sub + a) * w2 + c];
+  const float q3 = d[a * w2 + c], q4 = d[a * w2 + n_sub + c];
+  return ((q1 + q2) + q3) + q4;
 }
 
 __global__ void __launch_bounds__(kPyrThreads) k_pyr_slopes(
@@ -31,44 +32,55 @@ __global__ void __launch_bounds__(kPyrThreads) k_pyr_slopes(
     int n_sub, int n_valid, float *__restrict__ out, int32_t *status) {
   __shared__ float s_w[kPyrThreads / 32];
   __shared__ float s_T;
-  const int b = blockIdx.x;
+  const int b = blockIdx.y;
   const int w2 = 2 * n_sub;
+  const unsigned n2 = (unsigned)(n_sub * n_sub);
   const float *d = det + (size_t)b * w2 * w2;
   float part = 0.f;
-#pragma unroll 4
-  for (int k = threadIdx.x; k < n_valid; k += blockDim.x) {
-    const int s = checked_idx(idx, k, n_sub, status);
-    const int a = s / n_sub, c = s % n_sub;
-    const float q1 = d[(n_sub + a) * w2 + n_sub + c], q2 = d[(n_sub + a) * w2 + c];
-    const float q3 = d[a * w2 + c], q4 = d[a * w2 + n_sub + c];
-    part += ((q1 + q2) + q3) + q4;
+  int bad = 0;
+  for (int k0 = threadIdx.x; k0 < n_valid; k0 += 4 * kPyrThreads) {
+    int sv[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int k = k0 + u * kPyrThreads;
+      int s = k < n_valid ? __ldg(idx + k) : 0;
+      bad |= (unsigned)s >= n2;
+      sv[u] = (unsigned)s < n2 ? s : 0;
+    }
+    float q[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) q[u] = quad_sum(d, sv[u], n_sub, w2);
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (k0 + u * kPyrThreads < n_valid) part += q[u];
   }
   part = warp_sum(part);
   if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = part;
-  __syncthreads();
+  bad = __syncthreads_or(bad);
   if (threadIdx.x == 0) {
     float t = 0.f;
-    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += s_w[i];
+    for (int i = 0; i < kPyrThreads / 32; ++i) t += s_w[i];
     s_T = t / (float)n_valid;
+    if (bad) atomicExch(status, SPECULA_EINVAL);
   }
   __syncthreads();
   const float T = s_T;
+  const int k = blockIdx.x * kPyrThreads + threadIdx.x;
+  if (k >= n_valid) return;
   float *o = out + (size_t)b * 2 * n_valid;
-#pragma unroll 4
-  for (int k = threadIdx.x; k < n_valid; k += blockDim.x) {
-    const int s = checked_idx(idx, k, n_sub, status);
-    const int a = s / n_sub, c = s % n_sub;
-    const float q1 = d[(n_sub + a) * w2 + n_sub + c], q2 = d[(n_sub + a) * w2 + c];
-    const float q3 = d[a * w2 + c], q4 = d[a * w2 + n_sub + c];
-    float sx = ((q1 + q4) - (q2 + q3)) / T;
-    float sy = ((q1 + q2) - (q3 + q4)) / T;
-    if (ref) {
-      sx -= ref[k];
-      sy -= ref[n_valid + k];
-    }
-    o[k] = sx;
-    o[n_valid + k] = sy;
+  int s = __ldg(idx + k);
+  s = (unsigned)s < n2 ? s : 0;
+  const int a = s / n_sub, c = s - a * n_sub;
+  const float q1 = d[(n_sub + a) * w2 + n_sub + c], q2 = d[(n_sub + a) * w2 + c];
+  const float q3 = d[a * w2 + c], q4 = d[a * w2 + n_sub + c];
+  float sx = ((q1 + q4) - (q2 + q3)) / T;
+  float sy = ((q1 + q2) - (q3 + q4)) / T;
+  if (ref) {
+    sx -= ref[k];
+    sy -= ref[n_valid + k];
   }
+  o[k] = sx;
+  o[n_valid + k] = sy;
 }
 
 // One warp per (batch element, subaperture): centre of gravity of the spot.
@@ -107,8 +119,9 @@ __global__ void __launch_bounds__(256) k_sh_cog(const float *__restrict__ spots,
 int slopes_pyr_run(specula_ctx *ctx, const int32_t *idx, int n_sub, int n_valid,
                    const float *det, const float *ref, int n_batch, float *out, cudaStream_t st) {
   SPECULA_LAUNCH(ctx, SPECULA_K_SLOPES, st,
-                 k_pyr_slopes<<<n_batch, kPyrThreads, 0, st>>>(det, idx, ref, n_sub, n_valid, out,
-                                                               ctx->status_dev));
+                 k_pyr_slopes<<<dim3((n_valid + kPyrThreads - 1) / kPyrThreads, n_batch),
+                                kPyrThreads, 0, st>>>(det, idx, ref, n_sub, n_valid, out,
+                                                      ctx->status_dev));
   return SPECULA_OK;
 }
 
