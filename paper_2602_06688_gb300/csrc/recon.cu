@@ -43,7 +43,7 @@ template <int NB>
 __global__ void __launch_bounds__(kReconWarps * 32) k_mvm_f32(
     const float *__restrict__ R, const float *__restrict__ s, float *__restrict__ m, int n_modes,
     int n_slopes, int n_batch, int b0) {
-  const int row = blockIdx.x * kReconWarps + threadIdx.x / 32;
+  const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (row >= n_modes) return;
   const float4 *r4 = reinterpret_cast<const float4 *>(R + (size_t)row * n_slopes);
@@ -51,14 +51,15 @@ __global__ void __launch_bounds__(kReconWarps * 32) k_mvm_f32(
   float acc[NB];
 #pragma unroll
   for (int q = 0; q < NB; ++q) acc[q] = 0.f;
-  // four independent 16-byte row loads in flight per lane
-  for (int j0 = lane; j0 < n4; j0 += 4 * 32) {
-    float4 a[4];
+  // UL independent 16-byte row loads in flight per lane
+  constexpr int UL = NB == 1 ? 8 : 4;
+  for (int j0 = lane; j0 < n4; j0 += UL * 32) {
+    float4 a[UL];
 #pragma unroll
-    for (int u = 0; u < 4; ++u)
+    for (int u = 0; u < UL; ++u)
       a[u] = (j0 + 32 * u < n4) ? ld_stream(r4 + j0 + 32 * u) : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < UL; ++u) {
       const int j = j0 + 32 * u;
       if (j < n4) {
 #pragma unroll
@@ -99,7 +100,7 @@ template <int NB, bool SPLIT>
 __global__ void __launch_bounds__(kReconWarps * 32) k_mvm_bf16(
     const uint16_t *__restrict__ Rh, const uint16_t *__restrict__ Rl, const float *__restrict__ s,
     float *__restrict__ m, int n_modes, int n_slopes, int n_batch, int b0) {
-  const int row = blockIdx.x * kReconWarps + threadIdx.x / 32;
+  const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (row >= n_modes) return;
   const uint4 *h8 = reinterpret_cast<const uint4 *>(Rh + (size_t)row * n_slopes);
@@ -108,23 +109,35 @@ __global__ void __launch_bounds__(kReconWarps * 32) k_mvm_bf16(
   float acc[NB];
 #pragma unroll
   for (int q = 0; q < NB; ++q) acc[q] = 0.f;
-#pragma unroll 4
-  for (int j = lane; j < n8; j += 32) {
-    const uint4 hv = ld_stream_u4(h8 + j);
-    float r[8] = {bf_lo(hv.x), bf_hi(hv.x), bf_lo(hv.y), bf_hi(hv.y),
-                  bf_lo(hv.z), bf_hi(hv.z), bf_lo(hv.w), bf_hi(hv.w)};
-    if (SPLIT) {
-      const uint4 lv = ld_stream_u4(l8 + j);
-      r[0] += bf_lo(lv.x); r[1] += bf_hi(lv.x); r[2] += bf_lo(lv.y); r[3] += bf_hi(lv.y);
-      r[4] += bf_lo(lv.z); r[5] += bf_hi(lv.z); r[6] += bf_lo(lv.w); r[7] += bf_hi(lv.w);
+  // UL independent 16-byte loads (per operand) in flight per lane, issued
+  // before any use
+  constexpr int UL = NB == 1 ? (SPLIT ? 4 : 8) : 2;
+  for (int j0 = lane; j0 < n8; j0 += UL * 32) {
+    uint4 hv[UL], lv[UL];
+#pragma unroll
+    for (int u = 0; u < UL; ++u) {
+      const bool ok = j0 + 32 * u < n8;
+      hv[u] = ok ? ld_stream_u4(h8 + j0 + 32 * u) : make_uint4(0u, 0u, 0u, 0u);
+      if (SPLIT) lv[u] = ok ? ld_stream_u4(l8 + j0 + 32 * u) : make_uint4(0u, 0u, 0u, 0u);
     }
 #pragma unroll
-    for (int q = 0; q < NB; ++q) {
-      if (b0 + q < n_batch) {
-        const float4 *sv = reinterpret_cast<const float4 *>(s + (size_t)(b0 + q) * n_slopes) + 2 * j;
-        const float4 x0 = __ldg(sv), x1 = __ldg(sv + 1);
-        acc[q] += r[0] * x0.x + r[1] * x0.y + r[2] * x0.z + r[3] * x0.w +
-                  r[4] * x1.x + r[5] * x1.y + r[6] * x1.z + r[7] * x1.w;
+    for (int u = 0; u < UL; ++u) {
+      const int j = j0 + 32 * u;
+      if (j >= n8) break;
+      float r[8] = {bf_lo(hv[u].x), bf_hi(hv[u].x), bf_lo(hv[u].y), bf_hi(hv[u].y),
+                    bf_lo(hv[u].z), bf_hi(hv[u].z), bf_lo(hv[u].w), bf_hi(hv[u].w)};
+      if (SPLIT) {
+        r[0] += bf_lo(lv[u].x); r[1] += bf_hi(lv[u].x); r[2] += bf_lo(lv[u].y); r[3] += bf_hi(lv[u].y);
+        r[4] += bf_lo(lv[u].z); r[5] += bf_hi(lv[u].z); r[6] += bf_lo(lv[u].w); r[7] += bf_hi(lv[u].w);
+      }
+#pragma unroll
+      for (int q = 0; q < NB; ++q) {
+        if (b0 + q < n_batch) {
+          const float4 *sv = reinterpret_cast<const float4 *>(s + (size_t)(b0 + q) * n_slopes) + 2 * j;
+          const float4 x0 = __ldg(sv), x1 = __ldg(sv + 1);
+          acc[q] += r[0] * x0.x + r[1] * x0.y + r[2] * x0.z + r[3] * x0.w +
+                    r[4] * x1.x + r[5] * x1.y + r[6] * x1.z + r[7] * x1.w;
+        }
       }
     }
   }
@@ -159,6 +172,10 @@ extern "C" int specula_recon(specula_ctx *ctx, const specula_recon_desc *rec,
   cudaStream_t st = (cudaStream_t)stream;
   const unsigned grid = (rec->n_modes + kReconWarps - 1) / kReconWarps;
   const int blk = kReconWarps * 32;
+  // one slope vector: one warp per CTA, so the rows spread over the SMs
+  // within one row of each other (8-row CTAs leave some SMs a third more)
+  const unsigned grid1 = (unsigned)rec->n_modes;
+  const int blk1 = 32;
   const bool al16 = ((uintptr_t)rec->R_dev % 16 == 0) && ((uintptr_t)slopes_dev % 16 == 0);
   constexpr int NB = 4;
   switch (rec->precision) {
@@ -166,7 +183,7 @@ extern "C" int specula_recon(specula_ctx *ctx, const specula_recon_desc *rec,
       if (rec->n_slopes % 4 == 0 && al16) {
         for (int b0 = 0; b0 < n_batch; b0 += NB) {
           if (n_batch - b0 == 1)
-            SPECULA_LAUNCH(ctx, SPECULA_K_RECON, st, k_mvm_f32<1><<<grid, blk, 0, st>>>((const float *)rec->R_dev, slopes_dev, modes_dev,
+            SPECULA_LAUNCH(ctx, SPECULA_K_RECON, st, k_mvm_f32<1><<<grid1, blk1, 0, st>>>((const float *)rec->R_dev, slopes_dev, modes_dev,
                                                rec->n_modes, rec->n_slopes, n_batch, b0));
           else
             SPECULA_LAUNCH(ctx, SPECULA_K_RECON, st, k_mvm_f32<NB><<<grid, blk, 0, st>>>((const float *)rec->R_dev, slopes_dev, modes_dev,
@@ -187,10 +204,10 @@ extern "C" int specula_recon(specula_ctx *ctx, const specula_recon_desc *rec,
         const bool one = n_batch - b0 == 1;
         const uint16_t *h = (const uint16_t *)rec->R_dev, *l = (const uint16_t *)rec->R_lo_dev;
         if (split) {
-          if (one) SPECULA_LAUNCH(ctx, SPECULA_K_RECON, st, k_mvm_bf16<1, true><<<grid, blk, 0, st>>>(h, l, slopes_dev, modes_dev, rec->n_modes, rec->n_slopes, n_batch, b0));
+          if (one) SPECULA_LAUNCH(ctx, SPECULA_K_RECON, st, k_mvm_bf16<1, true><<<grid1, blk1, 0, st>>>(h, l, slopes_dev, modes_dev, rec->n_modes, rec->n_slopes, n_batch, b0));
           else SPECULA_LAUNCH(ctx, SPECULA_K_RECON, st, k_mvm_bf16<NB, true><<<grid, blk, 0, st>>>(h, l, slopes_dev, modes_dev, rec->n_modes, rec->n_slopes, n_batch, b0));
         } else {
-          if (one) SPECULA_LAUNCH(ctx, SPECULA_K_RECON, st, k_mvm_bf16<1, false><<<grid, blk, 0, st>>>(h, l, slopes_dev, modes_dev, rec->n_modes, rec->n_slopes, n_batch, b0));
+          if (one) SPECULA_LAUNCH(ctx, SPECULA_K_RECON, st, k_mvm_bf16<1, false><<<grid1, blk1, 0, st>>>(h, l, slopes_dev, modes_dev, rec->n_modes, rec->n_slopes, n_batch, b0));
           else SPECULA_LAUNCH(ctx, SPECULA_K_RECON, st, k_mvm_bf16<NB, false><<<grid, blk, 0, st>>>(h, l, slopes_dev, modes_dev, rec->n_modes, rec->n_slopes, n_batch, b0));
         }
       }
