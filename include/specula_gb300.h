@@ -509,6 +509,14 @@ int specula_mlp_get_grad(specula_mlp *mlp, int32_t layer, float *dW_host, float 
 /* Y_dev (nullable): batch x n_out floats; X_dev: batch x n_in floats. */
 int specula_mlp_forward(specula_mlp *mlp, const float *X_dev, int32_t batch, float *Y_dev,
                         void *stream);
+/* Inference only (keeps no state for backward): Y_dev = the network applied
+ * to X_dev.  For batch <= 4 each layer streams its bf16 weight rows once
+ * against the float32 inputs (one warp per output, float32 accumulation and
+ * activations): the way to run the network inside a frame.  Larger batches
+ * run as specula_mlp_forward (whose tensor-core GEMMs take bf16 activations,
+ * so results differ at the bf16 level).  Per-frame call: enqueues only. */
+int specula_mlp_infer(specula_mlp *mlp, const float *X_dev, int32_t batch, float *Y_dev,
+                      void *stream);
 /* Gradients of loss = mean over batch and outputs of (Y - T)^2 for the last
  * forward (same batch); T_dev: batch x n_out floats; loss_dev (nullable): one
  * float. */

@@ -517,6 +517,16 @@ class MLP:
             _dev(Y, torch.float32, B * self.sizes[3], "Y"), _stream(stream)),
             "specula_mlp_forward")
 
+    def infer(self, X, Y, stream=None):
+        """Inference only (specula_mlp_infer): the weight-streaming path for
+        batch <= 4, the forward pass otherwise."""
+        import torch
+        B = X.shape[0]
+        _abi.check(lib().specula_mlp_infer(
+            self.handle, _dev(X, torch.float32, B * self.sizes[0], "X"), int(B),
+            _dev(Y, torch.float32, B * self.sizes[3], "Y"), _stream(stream)),
+            "specula_mlp_infer")
+
     def backward(self, T, loss=None, stream=None):
         import torch
         B = T.shape[0]
@@ -551,6 +561,10 @@ def specula_mlp_get_grad(mlp, layer):
 
 def specula_mlp_forward(mlp, X, Y=None, stream=None):
     mlp.forward(X, Y, stream)
+
+
+def specula_mlp_infer(mlp, X, Y, stream=None):
+    mlp.infer(X, Y, stream)
 
 
 def specula_mlp_backward(mlp, T, loss=None, stream=None):

@@ -115,6 +115,7 @@ SIGNATURES = {
     "specula_mlp_get_grad": (C.c_int, [vp, i32, vp, vp]),
     "specula_mlp_forward": (C.c_int, [vp, vp, i32, vp, vp]),
     "specula_mlp_backward": (C.c_int, [vp, vp, i32, vp, vp]),
+    "specula_mlp_infer": (C.c_int, [vp, vp, i32, vp, vp]),
     "specula_mlp_adam": (C.c_int, [vp, C.c_float, C.c_float, C.c_float, C.c_float, vp]),
     "specula_modal_basis_host": (C.c_int, [P(PupilDesc), i32, vp]),
     "specula_modal_basis": (C.c_int, [vp, P(PupilDesc), i32, vp, vp]),

@@ -227,10 +227,83 @@ struct specula_mlp {
   DevBuf W[3], b[3], mW[3], vW[3], mb[3], vb[3], Wb[3], WbT[3], gW[3], gb[3];
   DevBuf Xb, XbT, Z[2], H[2], HT[2], Y, dYf, dYb, dYbT, dA[2], dZb[2], dZbT[2];
   DevBuf work, part, loss;
+  DevBuf Hi[2];    // inference activations, [kInferMax][np] float32
   size_t work_floats = 0;
 };
 
 static inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+// ---- inference for a few vectors (specula_mlp_infer) ---------------------------
+// A batch of a few slope vectors leaves the tensor-core GEMMs (128-row tiles)
+// mostly padding, and the time goes to reading the bf16 weights.  Each layer
+// is instead one warp per output row streaming that row (16-byte loads, 8 in
+// flight per lane) against every input vector in float32, then bias and
+// GELU: the weights are read once, activations stay float32.
+constexpr int kInferMax = 4;
+
+__device__ __forceinline__ uint4 ld_stream_w(const uint4 *p) {
+  uint4 v;
+  asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "l"(p));
+  return v;
+}
+__device__ __forceinline__ float bf16_lo(uint32_t u) { return __uint_as_float(u << 16); }
+__device__ __forceinline__ float bf16_hi(uint32_t u) { return __uint_as_float(u & 0xffff0000u); }
+
+// out[b][o] = act(sum_k W[o][k] x[b][k] + bias[o]), o < n_out, b < nb;
+// W bf16 [.][ldw]; x float [nb][ldx] with k < K read; grid n_out, block 32.
+template <int NB, bool GELU>
+__global__ void __launch_bounds__(32) k_mlp_gemv(const __nv_bfloat16 *__restrict__ W, int ldw,
+                                                 const float *__restrict__ x, int ldx, int K,
+                                                 int nb, const float *__restrict__ bias,
+                                                 float *__restrict__ out, int ldo) {
+  const int o = blockIdx.x, lane = threadIdx.x;
+  const uint4 *w8 = reinterpret_cast<const uint4 *>(W + (size_t)o * ldw);
+  const int k8 = K / 8;
+  float acc[NB];
+#pragma unroll
+  for (int q = 0; q < NB; ++q) acc[q] = 0.f;
+  constexpr int UL = 8;
+  for (int j0 = lane; j0 < k8; j0 += UL * 32) {
+    uint4 wv[UL];
+#pragma unroll
+    for (int u = 0; u < UL; ++u)
+      wv[u] = j0 + 32 * u < k8 ? ld_stream_w(w8 + j0 + 32 * u) : make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+    for (int u = 0; u < UL; ++u) {
+      const int j = j0 + 32 * u;
+      if (j >= k8) break;
+      const float r[8] = {bf16_lo(wv[u].x), bf16_hi(wv[u].x), bf16_lo(wv[u].y), bf16_hi(wv[u].y),
+                          bf16_lo(wv[u].z), bf16_hi(wv[u].z), bf16_lo(wv[u].w), bf16_hi(wv[u].w)};
+#pragma unroll
+      for (int q = 0; q < NB; ++q) {
+        if (q < nb) {
+          const float *xv = x + (size_t)q * ldx + 8 * j;
+#pragma unroll
+          for (int e = 0; e < 8; ++e) acc[q] += r[e] * __ldg(xv + e);
+        }
+      }
+    }
+  }
+  // the K % 8 tail
+  for (int k = 8 * k8 + lane; k < K; k += 32) {
+    const float wk = __bfloat162float(W[(size_t)o * ldw + k]);
+#pragma unroll
+    for (int q = 0; q < NB; ++q)
+      if (q < nb) acc[q] += wk * __ldg(x + (size_t)q * ldx + k);
+  }
+#pragma unroll
+  for (int q = 0; q < NB; ++q) {
+    float v = acc[q];
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
+    if (lane == 0 && q < nb) {
+      v += bias[o];
+      out[(size_t)q * ldo + o] = GELU ? gelu_f(v) : v;
+    }
+  }
+}
 
 static int mlp_splits(int M, int N, int K) {
   const int tiles = (M / 128) * (N / 128);
@@ -308,6 +381,9 @@ extern "C" int specula_mlp_create(specula_ctx *ctx, int32_t n_in, int32_t n_h1, 
   }
   p->work_floats = wf;
   if ((s = p->work.alloc(wf * 4))) return s;
+  if ((s = p->Hi[0].alloc((size_t)kInferMax * h1 * 4)) ||
+      (s = p->Hi[1].alloc((size_t)kInferMax * h2 * 4)))
+    return s;
   const int tiles = ((o + TT - 1) / TT) * ((Bp + TT - 1) / TT);
   if ((s = p->part.alloc((size_t)tiles * 4)) || (s = p->loss.alloc(4))) return s;
   for (int l = 0; l < 3; ++l)
@@ -408,6 +484,38 @@ extern "C" int specula_mlp_forward(specula_mlp *p, const float *X_dev, int32_t b
   }
   p->last_b = batch;
   (void)h1;
+  return SPECULA_OK;
+}
+
+extern "C" int specula_mlp_infer(specula_mlp *p, const float *X_dev, int32_t batch,
+                                 float *Y_dev, void *stream) {
+  if (!p || !X_dev || !Y_dev || batch < 1) return SPECULA_EINVAL;
+  if (batch > kInferMax) return specula_mlp_forward(p, X_dev, batch, Y_dev, stream);
+  cudaStream_t st = (cudaStream_t)stream;
+  specula_ctx *ctx = p->ctx;
+  const __nv_bfloat16 *W0 = p->Wb[0].as<__nv_bfloat16>(), *W1 = p->Wb[1].as<__nv_bfloat16>(),
+                      *W2 = p->Wb[2].as<__nv_bfloat16>();
+  float *H0 = p->Hi[0].as<float>(), *H1 = p->Hi[1].as<float>();
+  const int h1 = p->n[1], h2 = p->n[2];
+#define SPECULA_GEMV(NB)                                                                      \
+  do {                                                                                        \
+    SPECULA_LAUNCH(ctx, SPECULA_K_MLP, st,                                                    \
+                   (k_mlp_gemv<NB, true><<<h1, 32, 0, st>>>(W0, p->np[0], X_dev, p->n[0],     \
+                                                            p->n[0], batch,                   \
+                                                            p->b[0].as<float>(), H0, h1)));   \
+    SPECULA_LAUNCH(ctx, SPECULA_K_MLP, st,                                                    \
+                   (k_mlp_gemv<NB, true><<<h2, 32, 0, st>>>(W1, p->np[1], H0, h1, h1, batch,  \
+                                                            p->b[1].as<float>(), H1, h2)));   \
+    SPECULA_LAUNCH(ctx, SPECULA_K_MLP, st,                                                    \
+                   (k_mlp_gemv<NB, false><<<p->n[3], 32, 0, st>>>(W2, p->np[2], H1, h2, h2,   \
+                                                                  batch, p->b[2].as<float>(), \
+                                                                  Y_dev, p->n[3])));          \
+  } while (0)
+  if (batch == 1)
+    SPECULA_GEMV(1);
+  else
+    SPECULA_GEMV(kInferMax);
+#undef SPECULA_GEMV
   return SPECULA_OK;
 }
 

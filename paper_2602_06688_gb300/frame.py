@@ -125,7 +125,7 @@ class PwfsFrame:
                            stream=stream)
         specula_slopes(ctx, self.slopec, self.det, self.ref, self.slopes, stream=stream)
         if self.learned is not None:
-            self.learned.forward(self.slopes.view(1, -1), self.modes.view(1, -1), stream=stream)
+            self.learned.infer(self.slopes.view(1, -1), self.modes.view(1, -1), stream=stream)
         else:
             specula_recon(ctx, self.rec, self.slopes, self.modes, stream=stream)
         return self.modes

@@ -148,3 +148,23 @@ def test_model_outliving_its_context_leaves_no_error(env):
     torch.cuda.synchronize()
     assert torch.isfinite(Y).all()
     c3.close()
+
+
+@pytest.mark.parametrize("nb", [1, 3, 9])
+def test_infer_matches_oracle(env, nb):
+    """The inference entry point (weight streaming for batch <= 4, the forward
+    pass above) against the FP64 oracle on the bf16-rounded weights."""
+    torch, sp, ctx = env
+    sizes = [203, 256, 384, 77]   # an input width that is not a multiple of 8
+    params = _params32(sizes, seed=4)
+    m = _model(sp, ctx, params, sizes, 128)
+    rng = np.random.default_rng(nb)
+    X = rng.standard_normal((nb, sizes[0])).astype(np.float32)
+    Y = torch.empty(nb, sizes[3], device="cuda")
+    m.infer(torch.tensor(X, device="cuda"), Y)
+    torch.cuda.synchronize()
+    bf = lambda a: torch.tensor(a).to(torch.bfloat16).float().numpy().astype(np.float64)
+    ref, _ = omlp.forward([(bf(W), b.astype(np.float64)) for W, b in params], X)
+    ok, info = _close(Y.cpu().numpy(), ref, rel=1e-2 if nb > 4 else 1e-4)
+    assert ok, info
+    m.close()
