@@ -400,11 +400,29 @@ def systems_leg(ctx, steps=50):
         ms = time_graph(g, lambda k: fr.t_dev.fill_(wl.dt_s * k), steps)
         res[name] = {"frames_per_s": steps / (sum(ms) / 1e3), "ms_per_step": sum(ms) / steps}
         g.close()
+    # the batched form: B consecutive open-loop frames per graph launch
+    def batched(name, B):
+        w = synth.workload(name)
+        fb = PwfsFrame(ctx, w, autotune=True, batch=B)
+        g = fb.capture(st)
+        ar = torch.arange(B, dtype=torch.float64, device="cuda") * w.dt_s
+        set_t = lambda k: fb.t_dev.copy_(ar + k * B * w.dt_s)
+        time_graph(g, set_t, 5)
+        ms = time_graph(g, set_t, steps)
+        g.close()
+        res = {"batch": B, "frames_per_s": B * steps / (sum(ms) / 1e3),
+               "ms_per_step": sum(ms) / steps,
+               "tiles": {"chunk": fb.tiles[0], "ka": fb.tiles[1], "passes": fb.tiles[2]}}
+        del fb
+        torch.cuda.empty_cache()
+        return res
+
     out["pwfs8m"] = {"config": "8.4 m, 160 px pupil, 320^2 FFT, 24 mod points, 40x40 subaps, "
                                "3 layers, 500 modes",
                       "tiles": {"chunk": fr.tiles[0], "ka": fr.tiles[1], "passes": fr.tiles[2]},
-                      "recon_variants": res}
+                      "recon_variants": res, "batched_fp32": batched("pwfs8m", 16)}
     del fr
+    out["pwfs39m_batched_fp32"] = batched("pwfs39m", 8)
     wl = synth.workload("mwfs39m")
     S = System(ctx, wl)
     res = {}

@@ -23,7 +23,11 @@ def seeded_reconstructor(n_modes, n_slopes, seed):
 
 class PwfsFrame:
     def __init__(self, ctx, wl, sensor=0, precision=PREC_FP32, R=None, n_modes=None,
-                 seed_offset=0, device="cuda", autotune=False):
+                 seed_offset=0, device="cuda", autotune=False, batch=1):
+        """batch > 1: every step computes `batch` consecutive frames (times t,
+        t + dt, ...) of the open-loop sequence together: one extraction per
+        frame, then one pyramid call, one slope call and one MVM call over
+        the whole batch."""
         import torch
         self.torch = torch
         self.ctx = ctx
@@ -54,11 +58,19 @@ class PwfsFrame:
         self.n_modes = n_modes or wl.n_modes
         specula_pwfs_plan(ctx, self.pupil, self.pwfs)
         d = 2 * s.pwfs.n_sub
-        self.phase = torch.zeros(n, n, device=device)
-        self.det = torch.empty(d, d, device=device)
-        self.slopes = torch.empty(self.n_slopes, device=device)
+        self.batch = batch
+        self.dt = wl.dt_s
+        if batch == 1:
+            self.phase = torch.zeros(n, n, device=device)
+            self.det = torch.empty(d, d, device=device)
+            self.slopes = torch.empty(self.n_slopes, device=device)
+            self.modes = torch.empty(self.n_modes, device=device)
+        else:
+            self.phase = torch.zeros(batch, n, n, device=device)
+            self.det = torch.empty(batch, d, d, device=device)
+            self.slopes = torch.empty(batch, self.n_slopes, device=device)
+            self.modes = torch.empty(batch, self.n_modes, device=device)
         self.ref = torch.empty(self.n_slopes, device=device)
-        self.modes = torch.empty(self.n_modes, device=device)
         self.slopec = slopec_desc(SLOPES_PYR, s.pwfs.n_sub, self.valid)
         if R is None:
             R = seeded_reconstructor(self.n_modes, self.n_slopes, seed=7 + seed_offset)
@@ -66,14 +78,16 @@ class PwfsFrame:
         self.learned = None
         self.set_precision(precision)
         # reference slopes: a flat wavefront in the same geometry
-        specula_pwfs_image(ctx, self.pupil, self.pwfs, self.amp, self.phase, self.det)
-        specula_slopes(ctx, self.slopec, self.det, None, self.ref)
+        flat, fdet = torch.zeros(n, n, device=device), torch.empty(d, d, device=device)
+        specula_pwfs_image(ctx, self.pupil, self.pwfs, self.amp, flat, fdet)
+        specula_slopes(ctx, self.slopec, fdet, None, self.ref)
         torch.cuda.synchronize()
         self.tiles = None
         if autotune:
             from .autotune import tune_pwfs
-            specula_atmo_extract(ctx, self.layers, self.screens, self.src, self.pupil, 0.0,
-                                 self.phase)
+            for k in range(batch):
+                specula_atmo_extract(ctx, self.layers, self.screens, self.src, self.pupil,
+                                     k * self.dt, self.phase.view(batch, n, n)[k])
             self.tiles = tune_pwfs(ctx, self.pupil, self.pwfs, self.amp, self.phase, self.det,
                                    force=autotune == "force")
             torch.cuda.synchronize()
@@ -99,7 +113,7 @@ class PwfsFrame:
         the graph reads the frame time from self.t_dev."""
         from . import specula_graph_begin, specula_graph_end
         torch = self.torch
-        self.t_dev = torch.zeros(1, dtype=torch.float64, device=self.R.device)
+        self.t_dev = torch.zeros(self.batch, dtype=torch.float64, device=self.R.device)
         torch.cuda.synchronize()
         specula_graph_begin(self.ctx, stream)
         try:
@@ -112,20 +126,35 @@ class PwfsFrame:
         """Set the frame time and launch the captured frame on `stream`."""
         torch = self.torch
         with torch.cuda.stream(stream):
-            self.t_dev.fill_(t)
+            if self.batch == 1:
+                self.t_dev.fill_(t)
+            else:
+                self.t_dev.copy_(t + self.dt * torch.arange(self.batch, dtype=torch.float64,
+                                                            device=self.t_dev.device))
         self.graph.launch(stream)
         return self.modes
 
     def frame(self, t, t_dev=None, stream=None):
-        """Enqueue one frame at time t (or *t_dev) on the current stream."""
+        """Enqueue one frame at time t (or *t_dev) on the current stream; with
+        batch > 1 the frames at t, t + dt, ... (t_dev: one device time per
+        frame)."""
         ctx = self.ctx
-        specula_atmo_extract(ctx, self.layers, self.screens, self.src, self.pupil, t,
-                             self.phase, t_dev=t_dev, stream=stream)
+        if self.batch == 1:
+            specula_atmo_extract(ctx, self.layers, self.screens, self.src, self.pupil, t,
+                                 self.phase, t_dev=t_dev, stream=stream)
+        else:
+            n = self.n_pix
+            for k in range(self.batch):
+                specula_atmo_extract(ctx, self.layers, self.screens, self.src, self.pupil,
+                                     t + k * self.dt, self.phase.view(self.batch, n, n)[k],
+                                     t_dev=None if t_dev is None else t_dev[k:k + 1],
+                                     stream=stream)
         specula_pwfs_image(ctx, self.pupil, self.pwfs, self.amp, self.phase, self.det,
                            stream=stream)
         specula_slopes(ctx, self.slopec, self.det, self.ref, self.slopes, stream=stream)
         if self.learned is not None:
-            self.learned.infer(self.slopes.view(1, -1), self.modes.view(1, -1), stream=stream)
+            self.learned.infer(self.slopes.view(self.batch, -1), self.modes.view(self.batch, -1),
+                               stream=stream)
         else:
             specula_recon(ctx, self.rec, self.slopes, self.modes, stream=stream)
         return self.modes

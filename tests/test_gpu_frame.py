@@ -71,3 +71,29 @@ def test_graph_replay_matches_eager(env):
         torch.cuda.synchronize()
         assert torch.equal(fr.modes, eager)
     g.close()
+
+
+def test_batched_frames_match_single_frames(env):
+    """A batch of B consecutive frames (one pyramid, slope and MVM call over
+    the batch) gives the same modes as B single frames at those times."""
+    torch, sp, ctx = env
+    from paper_2602_06688_gb300.frame import PwfsFrame
+    wl = synth.workload("pwfs8m_tiny")
+    one = PwfsFrame(ctx, wl)
+    four = PwfsFrame(ctx, wl, batch=4)
+    four.frame(0.2)
+    torch.cuda.synchronize()
+    got = four.modes.clone()
+    for k in range(4):
+        one.frame(0.2 + k * wl.dt_s)
+        torch.cuda.synchronize()
+        ref = one.modes.cpu().numpy().astype(np.float64)
+        R = one.R.cpu().numpy().astype(np.float64)
+        mag = np.abs(R) @ np.abs(one.slopes.cpu().numpy().astype(np.float64))
+        assert np.all(np.abs(got[k].cpu().numpy() - ref) <= 2e-5 * mag + 1e-7), k
+    st = torch.cuda.Stream()
+    g = four.capture(st)
+    four.replay(0.2, st)
+    torch.cuda.synchronize()
+    assert torch.equal(four.modes, got)
+    g.close()
