@@ -143,6 +143,14 @@ int specula_ctx_destroy(specula_ctx *ctx);
  * device-side condition was recorded) in *device_status and clear it. */
 int specula_ctx_status(specula_ctx *ctx, int32_t *device_status);
 
+/* Non-finite guard (on by default).  While on, every slope computer (the
+ * pyramid and Shack-Hartmann slope calls, the slope stages of the
+ * multi-sensor launch) records SPECULA_ENONFINITE in the device status word
+ * when one of its outputs is NaN or infinite (a NaN in a phase screen, a
+ * dark pupil).  The outputs are still written.  `on` is 0 or 1; takes effect
+ * for launches made after the call. */
+int specula_ctx_set_guard(specula_ctx *ctx, int32_t on);
+
 /* ---- tracing -----------------------------------------------------------------
  * LoopControl reports the simulation speed (Sect. 2.4); these calls give the
  * per-kernel view behind it.  Kernel ids: */
@@ -451,11 +459,21 @@ int specula_mwfs_schedule(const specula_mwfs *mwfs, int32_t *n_tasks, int32_t *g
  * it except for float rounding order, which it does not change either
  * (every reduction has a fixed order). */
 int specula_mwfs_set_grid(specula_mwfs *mwfs, int32_t ctas);
+/* Limit of one dependency wait inside the launch, in ns (0: the default of
+ * 2 s; at most 10 s), and fault injection for tests of the failure path:
+ * task `stall_task` (0 .. n_tasks-1; -1: none) waits for an arrival count
+ * that never comes.  That wait expires after limit_ns, records
+ * SPECULA_ETIMEOUT in the context status word and makes every CTA leave;
+ * the launch's outputs are then undefined and the next launch starts from
+ * clean counters.  Takes effect for launches made after the call (a
+ * captured graph keeps the values of its capture). */
+int specula_mwfs_set_wait(specula_mwfs *mwfs, int64_t limit_ns, int32_t stall_task);
 /* One frame at time t (t = *t_dev if t_dev is not NULL): slopes_dev
  * (n_slopes floats) minus ref_dev (nullable, same layout), and modes_dev
  * (n_modes floats; must be NULL exactly when n_modes = 0).  Per-frame call:
- * enqueues one kernel, allocates nothing.  A dependency wait longer than 2 s
- * ends the launch early with SPECULA_ETIMEOUT in the context status word. */
+ * enqueues one kernel, allocates nothing.  A dependency wait longer than the
+ * limit (2 s unless set) ends the launch early with SPECULA_ETIMEOUT in the
+ * context status word. */
 int specula_mwfs_frame(specula_mwfs *mwfs, double t_s, const double *t_dev,
                        const float *ref_dev, float *slopes_dev, float *modes_dev, void *stream);
 /* Slopes of a flat wavefront (no layers), no reference subtracted: the

@@ -128,6 +128,10 @@ def specula_ctx_status(ctx):
     return v.value
 
 
+def specula_ctx_set_guard(ctx, on):
+    _abi.check(lib().specula_ctx_set_guard(ctx.handle, int(on)), "specula_ctx_set_guard")
+
+
 (K_PWFS_ROWS_FWD, K_PWFS_COLS, K_PWFS_ROWS_INV, K_ATMO, K_SLOPES, K_RECON, K_SH,
  K_PWFS_FIELD, K_PWFS_BIN, K_CALIB, K_GEMM, K_MLP, K_MWFS, K_PWFS_ROWFILT,
  K_PWFS_COLFILT) = range(15)
@@ -713,6 +717,10 @@ class Mwfs:
     def set_grid(self, ctas):
         _abi.check(lib().specula_mwfs_set_grid(self.handle, int(ctas)), "specula_mwfs_set_grid")
 
+    def set_wait(self, limit_ns=0, stall_task=-1):
+        _abi.check(lib().specula_mwfs_set_wait(self.handle, int(limit_ns), int(stall_task)),
+                   "specula_mwfs_set_wait")
+
     def frame(self, t, slopes, modes=None, ref=None, t_dev=None, stream=None):
         import torch
         _abi.check(lib().specula_mwfs_frame(
@@ -767,3 +775,7 @@ def specula_mwfs_schedule(m):
 
 def specula_mwfs_set_grid(m, ctas):
     m.set_grid(ctas)
+
+
+def specula_mwfs_set_wait(m, limit_ns, stall_task):
+    m.set_wait(limit_ns, stall_task)

@@ -71,6 +71,7 @@ SIGNATURES = {
     "specula_ctx_create": (C.c_int, [P(vp), C.c_int]),
     "specula_ctx_destroy": (C.c_int, [vp]),
     "specula_ctx_status": (C.c_int, [vp, P(i32)]),
+    "specula_ctx_set_guard": (C.c_int, [vp, i32]),
     "specula_prof_enable": (C.c_int, [vp, i32]),
     "specula_prof_read": (C.c_int, [vp, vp, vp]),
     "specula_launch_count": (C.c_int, [vp, P(C.c_int64)]),
@@ -128,6 +129,7 @@ SIGNATURES = {
     "specula_mwfs_info": (C.c_int, [vp, i32, P(i32), P(i32), P(i32)]),
     "specula_mwfs_schedule": (C.c_int, [vp, P(i32), P(i32), P(i32)]),
     "specula_mwfs_set_grid": (C.c_int, [vp, i32]),
+    "specula_mwfs_set_wait": (C.c_int, [vp, C.c_int64, i32]),
     "specula_mwfs_frame": (C.c_int, [vp, dbl, vp, vp, vp, vp, vp]),
     "specula_mwfs_reference": (C.c_int, [vp, vp, vp, vp]),
     "specula_mwfs_read": (C.c_int, [vp, i32, i32, vp, vp]),

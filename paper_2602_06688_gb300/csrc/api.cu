@@ -208,6 +208,12 @@ extern "C" int specula_ctx_status(specula_ctx *ctx, int32_t *device_status) {
   return SPECULA_OK;
 }
 
+extern "C" int specula_ctx_set_guard(specula_ctx *ctx, int32_t on) {
+  if (!ctx || (on != 0 && on != 1)) return SPECULA_EINVAL;
+  ctx->guard = on != 0;
+  return SPECULA_OK;
+}
+
 // ---- integer geometry --------------------------------------------------------
 
 namespace specula {

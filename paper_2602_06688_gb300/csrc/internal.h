@@ -96,6 +96,7 @@ struct ShPlan {
 struct specula_ctx {
   int device = 0;
   int32_t *status_dev = nullptr;
+  bool guard = true;                // slope kernels record non-finite outputs
   int *atmo_tab_i = nullptr;        // [64][2][8192] screen sample index
   float *atmo_tab_f = nullptr;      // [64][2][8192] interpolation fraction
   std::vector<std::unique_ptr<specula::PwfsPlan>> pwfs;

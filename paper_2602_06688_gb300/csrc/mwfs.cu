@@ -61,7 +61,8 @@ constexpr int kMwCoordsPerTask = kMwThreads;
 constexpr int kMwBinPerTask = 1024;
 constexpr int kMwMvmRows = 32;
 constexpr int kMwFinalRows = 1024;
-constexpr unsigned long long kMwWaitNs = 2000000000ull;
+constexpr unsigned long long kMwWaitNs = 2000000000ull;      // default wait limit
+constexpr long long kMwWaitMaxNs = 10000000000ll;            // largest settable limit
 
 enum : int {
   MT_COORDS = 0, MT_FIELD, MT_SH, MT_ROWS, MT_COLS, MT_RINV, MT_BIN, MT_SLOPES, MT_MVM, MT_FINAL
@@ -110,6 +111,9 @@ struct MwParams {
   const float *ref;
   float *slopes, *modes, *mpart;
   int32_t *status;
+  int32_t *nf_status;          // non-finite guard: status word, or null when off
+  unsigned long long wait_ns;  // limit of one dependency wait
+  int stall_task;              // fault injection: this task waits for a count never reached
 };
 
 // ---- synchronisation ---------------------------------------------------------
@@ -133,19 +137,25 @@ __device__ __forceinline__ unsigned long long global_ns() {
 }
 
 // Thread 0 only: wait until *c >= need.  0 if the frame was aborted.
-__device__ int mw_wait(const int *c, int need, int *abortf, int32_t *status) {
+__device__ int mw_wait(const int *c, int need, int *abortf, int32_t *status,
+                       unsigned long long limit_ns) {
   if (ld_acquire_gpu(c) >= need) return 1;
   const unsigned long long t0 = global_ns();
   for (;;) {
     __nanosleep(128);
     if (ld_acquire_gpu(c) >= need) return 1;
     if (ld_relaxed_gpu(abortf)) return 0;
-    if (global_ns() - t0 > kMwWaitNs) {
+    if (global_ns() - t0 > limit_ns) {
       atomicExch(status, SPECULA_ETIMEOUT);
       atomicExch(abortf, 1);
       return 0;
     }
   }
+}
+
+// Non-finite guard on a slope pair: a status write only when one is NaN/Inf.
+__device__ __forceinline__ void mw_guard(float a, float b, int32_t *nf_status) {
+  if (nf_status && !(isfinite(a) && isfinite(b))) atomicExch(nf_status, SPECULA_ENONFINITE);
 }
 
 __device__ __forceinline__ float mw_warp_sum(float v) {
@@ -640,6 +650,7 @@ __device__ void mw_sh(const MwParams &P, const MwSensor &S, int v0, int v1, floa
       }
       P.slopes[S.slope_off + v] = gx;
       P.slopes[S.slope_off + S.n_valid + v] = gy;
+      mw_guard(gx, gy, P.nf_status);
     }
     __syncwarp();
   }
@@ -880,6 +891,7 @@ __device__ void mw_pyr_slopes(const MwParams &P, const MwSensor &S, float *s_w) 
     }
     o[k] = sx;
     o[S.n_valid + k] = sy;
+    mw_guard(sx, sy, P.nf_status);
   }
 }
 
@@ -942,9 +954,13 @@ __global__ void __launch_bounds__(kMwThreads, 3) k_mwfs(const __grid_constant__ 
       const int t = atomicAdd(ticket, 1);
       int ok = 1;
       if (t < P.n_tasks) {
-        const int wc = P.tasks[t].wait_ctr;
+        int wc = P.tasks[t].wait_ctr, wv = P.tasks[t].wait_val;
+        if (t == P.stall_task) {       // its own completion count: never reached
+          wc = P.tasks[t].done_ctr;
+          wv = 0x7fffffff;
+        }
         if (ld_relaxed_gpu(abortf)) ok = 0;
-        else if (wc >= 0) ok = mw_wait(P.ctr + wc, P.tasks[t].wait_val, abortf, P.status);
+        else if (wc >= 0) ok = mw_wait(P.ctr + wc, wv, abortf, P.status, P.wait_ns);
       }
       s_t = t;
       s_ok = ok;
@@ -1405,6 +1421,8 @@ extern "C" int specula_mwfs_create(specula_ctx *ctx, int32_t n_sensors,
   P.ctr = m->ctr.as<int>();
   P.n_ctr = nctr;
   P.status = ctx->status_dev;
+  P.wait_ns = kMwWaitNs;
+  P.stall_task = -1;
 
   m->smem = var->smem(max_slopes, max_field_slots);
   if (m->smem > 227 * 1024) return SPECULA_EUNSUPPORTED;
@@ -1455,6 +1473,14 @@ extern "C" int specula_mwfs_set_grid(specula_mwfs *m, int32_t ctas) {
   return SPECULA_OK;
 }
 
+extern "C" int specula_mwfs_set_wait(specula_mwfs *m, int64_t limit_ns, int32_t stall_task) {
+  if (!m || limit_ns < 0 || limit_ns > kMwWaitMaxNs) return SPECULA_EINVAL;
+  if (stall_task < -1 || stall_task >= m->P.n_tasks) return SPECULA_EINVAL;
+  m->P.wait_ns = limit_ns == 0 ? kMwWaitNs : (unsigned long long)limit_ns;
+  m->P.stall_task = stall_task;
+  return SPECULA_OK;
+}
+
 static int mwfs_launch(specula_mwfs *m, double t_s, const double *t_dev, const float *ref_dev,
                        float *slopes_dev, float *modes_dev, int flat, void *stream) {
   cudaStream_t st = (cudaStream_t)stream;
@@ -1465,6 +1491,7 @@ static int mwfs_launch(specula_mwfs *m, double t_s, const double *t_dev, const f
   P.ref = ref_dev;
   P.slopes = slopes_dev;
   P.modes = modes_dev;
+  P.nf_status = m->ctx->guard ? m->ctx->status_dev : nullptr;
   SPECULA_LAUNCH(m->ctx, SPECULA_K_MWFS, st,
                  m->var->fn<<<m->grid, kMwThreads, m->smem, st>>>(P));
   return SPECULA_OK;

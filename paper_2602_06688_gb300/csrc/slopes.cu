@@ -14,6 +14,12 @@ __device__ __forceinline__ float warp_sum(float v) {
   return v;
 }
 
+// Non-finite guard: one status write per offending output, so the cost is
+// nil when the slopes are finite.
+__device__ __forceinline__ void guard_finite(float a, float b, int32_t *nf_status) {
+  if (nf_status && !(isfinite(a) && isfinite(b))) atomicExch(nf_status, SPECULA_ENONFINITE);
+}
+
 // grid (ceil(n_valid / kPyrThreads), n_batch): every CTA forms the global
 // normalisation T itself (the detector is small and L2-resident; the same
 // fixed-order reduction in every CTA gives the same T bit for bit), then
@@ -29,7 +35,7 @@ __device__ __forceinline__ float quad_sum(const float *d, int s, int n_sub, int 
 
 __global__ void __launch_bounds__(kPyrThreads) k_pyr_slopes(
     const float *__restrict__ det, const int32_t *__restrict__ idx, const float *__restrict__ ref,
-    int n_sub, int n_valid, float *__restrict__ out, int32_t *status) {
+    int n_sub, int n_valid, float *__restrict__ out, int32_t *status, int32_t *nf_status) {
   __shared__ float s_w[kPyrThreads / 32];
   __shared__ float s_T;
   const int b = blockIdx.y;
@@ -81,13 +87,14 @@ __global__ void __launch_bounds__(kPyrThreads) k_pyr_slopes(
   }
   o[k] = sx;
   o[n_valid + k] = sy;
+  guard_finite(sx, sy, nf_status);
 }
 
 // One warp per (batch element, subaperture): centre of gravity of the spot.
 __global__ void __launch_bounds__(256) k_sh_cog(const float *__restrict__ spots,
                                                 const float *__restrict__ ref, int nf,
                                                 int n_valid, int n_batch,
-                                                float *__restrict__ out) {
+                                                float *__restrict__ out, int32_t *nf_status) {
   const long long task = (long long)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
   const int lane = threadIdx.x & 31;
   if (task >= (long long)n_valid * n_batch) return;   // warp-uniform
@@ -113,6 +120,7 @@ __global__ void __launch_bounds__(256) k_sh_cog(const float *__restrict__ spots,
     }
     out[(size_t)b * 2 * n_valid + k] = gx;
     out[(size_t)b * 2 * n_valid + n_valid + k] = gy;
+    guard_finite(gx, gy, nf_status);
   }
 }
 
@@ -121,7 +129,8 @@ int slopes_pyr_run(specula_ctx *ctx, const int32_t *idx, int n_sub, int n_valid,
   SPECULA_LAUNCH(ctx, SPECULA_K_SLOPES, st,
                  k_pyr_slopes<<<dim3((n_valid + kPyrThreads - 1) / kPyrThreads, n_batch),
                                 kPyrThreads, 0, st>>>(det, idx, ref, n_sub, n_valid, out,
-                                                      ctx->status_dev));
+                                                      ctx->status_dev,
+                                                      ctx->guard ? ctx->status_dev : nullptr));
   return SPECULA_OK;
 }
 
@@ -145,7 +154,8 @@ extern "C" int specula_slopes(specula_ctx *ctx, const specula_slopec_desc *d, co
     const long long tasks = (long long)d->n_valid * n_batch;
     SPECULA_LAUNCH(ctx, SPECULA_K_SLOPES, st,
                    k_sh_cog<<<(unsigned)((tasks + 7) / 8), 256, 0, st>>>(
-                       img_dev, ref_dev, d->fft_n, d->n_valid, n_batch, slopes_dev));
+                       img_dev, ref_dev, d->fft_n, d->n_valid, n_batch, slopes_dev,
+                       ctx->guard ? ctx->status_dev : nullptr));
   } else {
     return SPECULA_EINVAL;
   }
