@@ -126,7 +126,47 @@ template <int N> struct first_factor {
   static constexpr int value = (N % 4 == 0 && N != 8) ? 4 : (N % 2 == 0 ? 2 : (N % 3 == 0 ? 3 : (N % 5 == 0 ? 5 : N)));
 };
 
-template <int N, bool INV> struct RegDFT {
+// Coprime split N = A B for the prime-factor (Good-Thomas) form: A is the
+// power of 2 in N, else the power of 3, when that is a proper factor; 0 if
+// N has no such split (prime powers).
+constexpr int prime_power_part(int n, int p) { return n % p == 0 ? p * prime_power_part(n / p, p) : 1; }
+constexpr int inverse_mod(int a, int m, int x = 1) {
+  return x >= m ? 1 : ((a * x) % m == 1 ? x : inverse_mod(a, m, x + 1));
+}
+template <int N> struct pfa_factor {
+  static constexpr int p2 = prime_power_part(N, 2), p3 = prime_power_part(N, 3);
+  static constexpr int value = (p2 > 1 && p2 < N) ? p2 : ((p3 > 1 && p3 < N) ? p3 : 0);
+};
+
+template <int N, bool INV, int A = pfa_factor<N>::value> struct RegDFT {
+  // Prime-factor form, no twiddles: with N = A B, gcd(A, B) = 1, the input
+  // index n = (a B + b A) mod N and the output index
+  // k = (ka B (B^-1 mod A) + kb A (A^-1 mod B)) mod N make W_N^{nk} factor
+  // into W_A^{a ka} W_B^{b kb}: a B-point DFT along b for every a, then an
+  // A-point DFT along a for every kb.
+  static __device__ __forceinline__ void run(float2 (&x)[N]) {
+    constexpr int B = N / A;
+    constexpr int U = inverse_mod(B % A, A), V = inverse_mod(A % B, B);
+    float2 y[A][B];
+#pragma unroll
+    for (int a = 0; a < A; ++a) {
+#pragma unroll
+      for (int b = 0; b < B; ++b) y[a][b] = x[(a * B + b * A) % N];
+      RegDFT<B, INV>::run(y[a]);
+    }
+#pragma unroll
+    for (int kb = 0; kb < B; ++kb) {
+      float2 z[A];
+#pragma unroll
+      for (int a = 0; a < A; ++a) z[a] = y[a][kb];
+      RegDFT<A, INV>::run(z);
+#pragma unroll
+      for (int ka = 0; ka < A; ++ka) x[(ka * B * U + kb * A * V) % N] = z[ka];
+    }
+  }
+};
+
+template <int N, bool INV> struct RegDFT<N, INV, 0> {
   static __device__ __forceinline__ void run(float2 (&x)[N]) {
     constexpr int P = first_factor<N>::value;
     constexpr int Q = N / P;
@@ -155,19 +195,19 @@ template <int N, bool INV> struct RegDFT {
   }
 };
 
-template <bool INV> struct RegDFT<1, INV> {
+template <bool INV> struct RegDFT<1, INV, 0> {
   static __device__ __forceinline__ void run(float2 (&)[1]) {}
 };
-template <bool INV> struct RegDFT<2, INV> {
+template <bool INV> struct RegDFT<2, INV, 0> {
   static __device__ __forceinline__ void run(float2 (&x)[2]) { bfly2<INV>(x[0], x[1]); }
 };
-template <bool INV> struct RegDFT<3, INV> {
+template <bool INV> struct RegDFT<3, INV, 0> {
   static __device__ __forceinline__ void run(float2 (&x)[3]) { bfly3<INV>(x[0], x[1], x[2]); }
 };
-template <bool INV> struct RegDFT<4, INV> {
+template <bool INV> struct RegDFT<4, INV, 0> {
   static __device__ __forceinline__ void run(float2 (&x)[4]) { bfly4<INV>(x[0], x[1], x[2], x[3]); }
 };
-template <bool INV> struct RegDFT<5, INV> {
+template <bool INV> struct RegDFT<5, INV, 0> {
   static __device__ __forceinline__ void run(float2 (&x)[5]) { bfly5<INV>(x[0], x[1], x[2], x[3], x[4]); }
 };
 

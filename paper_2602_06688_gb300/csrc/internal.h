@@ -70,6 +70,7 @@ struct PwfsPlan {
   bool two_ok;          // the two-pass form fits this geometry
   int blockR, blockK;   // two-pass blocks (K: TC columns x G lanes)
   size_t smemR, smemK;
+  int csK = 0;                      // column stride of the column-pass tile (complex)
   DevBuf gx, gy;        // [n_mod][n_pix] float2: tilt x pre-phase (x and y parts)
   DevBuf mask;          // [N] float2: pyramid mask factor per axis, x (1/N)
   DevBuf twA, twB;      // [N] float2: inter-step twiddles (cos, sin)

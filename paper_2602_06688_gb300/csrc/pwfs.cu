@@ -407,9 +407,20 @@ __global__ void __launch_bounds__(256, 2) k_rowfilt(
 // the item's y tilt, column filter, |.|^2 / n_mod, b x b bins ->
 // part[b % nbw][m][ybin][xbin].  grid (N / TC, 2 n_slots): y = 2 p + w is
 // item m = c (w = 0) or m = n_mod - c (w = 1, when distinct) of slot p.
+// Column stride CS (complex) of the tile: at least the exchange buffer of a
+// column, odd, and for odd TC with CS TC = 1 (mod 16), so the staging copy
+// of element e = TC jj + c (column c, row jj) lands in 8-byte bank slot
+// (c CS + jj) mod 16 = TC^-1 e mod 16, a bijection on every 16 consecutive e: the
+// cp.async writes of a warp are free of bank conflicts.
 template <int N1, int N2> struct ColFiltCfg {
   using S = Split<N1, N2>;
-  static constexpr int CS = imax3(S::N, N2 * S::S1, N1 * S::S2) | 1;   // odd column stride
+  static constexpr int base = imax3(S::N, N2 * S::S1, N1 * S::S2);
+  static int stride(int tc) {
+    int cs = base | 1;
+    if (tc % 2 == 1)
+      while ((cs * tc) % 16 != 1) cs += 2;
+    return cs;
+  }
 };
 
 template <int N1, int N2>
@@ -417,10 +428,9 @@ __global__ void __launch_bounds__(256, 3) k_colfilt_bin(
     const float2 *__restrict__ rows_in, const float2 *__restrict__ gy,
     const float2 *__restrict__ twA, const float2 *__restrict__ twB,
     const float2 *__restrict__ mask, float *__restrict__ part, int n_pix, int bsz, float scale,
-    int n_mod, int nc, int nbw, int slot0) {
+    int n_mod, int nc, int nbw, int slot0, int CS) {
   using S = Split<N1, N2>;
   constexpr int N = S::N, G = S::G, S1 = S::S1, S2 = S::S2;
-  constexpr int CS = ColFiltCfg<N1, N2>::CS;
   constexpr int Q0 = N2 / 4, QH = N2 / 2;
   constexpr int off = N / 4;
   extern __shared__ float2 smem[];
@@ -560,7 +570,8 @@ static int configure(PwfsPlan *p) {
   if (k > 0 && p->smemR <= 227 * 1024) {
     const int tc = k * bsz;
     p->blockK = tc * S::G;
-    p->smemK = (size_t)tc * ColFiltCfg<N1, N2>::CS * sizeof(float2);
+    p->csK = ColFiltCfg<N1, N2>::stride(tc);
+    p->smemK = (size_t)tc * p->csK * sizeof(float2);
     if (p->smemK <= 227 * 1024 && S::N % tc == 0) {
       if ((s = ensure_dynamic_smem((const void *)k_rowfilt<N1, N2>, p->smemR)) ||
           (s = ensure_dynamic_smem((const void *)k_colfilt_bin<N1, N2>, p->smemK)))
@@ -608,7 +619,7 @@ static int run_split2(specula_ctx *ctx, PwfsPlan *p, const float *amp, const flo
                    k_colfilt_bin<N1, N2><<<gK, p->blockK, p->smemK, st>>>(
                        p->rows.as<float2>(), p->gy.as<float2>(), p->twA.as<float2>(),
                        p->twB.as<float2>(), p->mask.as<float2>(), p->part.as<float>(), Np, bsz,
-                       scale, p->n_mod, nc, p->nbw, j0));
+                       scale, p->n_mod, nc, p->nbw, j0, p->csK));
     const int complete = (j0 + nj) / nc - 1;
     if (complete > det_done) {
       dim3 gD((nd * nd + 255) / 256, complete - det_done);
