@@ -51,6 +51,10 @@ __device__ __forceinline__ void cp_async8(void *smem_dst, const void *gsrc) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(gsrc) : "memory");
 }
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gsrc) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gsrc) : "memory");
+}
 __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.wait_all;" ::: "memory");
 }
@@ -407,24 +411,20 @@ __global__ void __launch_bounds__(256, 2) k_rowfilt(
 // the item's y tilt, column filter, |.|^2 / n_mod, b x b bins ->
 // part[b % nbw][m][ybin][xbin].  grid (N / TC, 2 n_slots): y = 2 p + w is
 // item m = c (w = 0) or m = n_mod - c (w = 1, when distinct) of slot p.
-// Column stride CS (complex) of the tile: at least the exchange buffer of a
-// column, odd, and for odd TC with CS TC = 1 (mod 16), so the staging copy
-// of element e = TC jj + c (column c, row jj) lands in 8-byte bank slot
-// (c CS + jj) mod 16 = TC^-1 e mod 16, a bijection on every 16 consecutive e: the
-// cp.async writes of a warp are free of bank conflicts.
+// Column stride CS (complex) of the exchange buffers: at least the exchange
+// buffer of a column, odd.
 template <int N1, int N2> struct ColFiltCfg {
   using S = Split<N1, N2>;
   static constexpr int base = imax3(S::N, N2 * S::S1, N1 * S::S2);
-  static int stride(int tc) {
-    int cs = base | 1;
-    if (tc % 2 == 1)
-      while ((cs * tc) % 16 != 1) cs += 2;
-    return cs;
-  }
+  static int stride(int) { return base | 1; }
 };
 
-template <int N1, int N2>
-__global__ void __launch_bounds__(256, 3) k_colfilt_bin(
+// One-warp columns in tiles of at most 160 threads (five columns for the
+// 39 m pupil's bin side 5) take the variant bounded at 160 threads x 4 CTAs
+// per SM, the occupancy that 80 registers per thread gave them already:
+// 96 registers per thread, so the twiddle loads can be issued earlier.
+template <int N1, int N2, int MAXT = 256>
+__global__ void __launch_bounds__(MAXT, MAXT <= 160 ? 4 : 3) k_colfilt_bin(
     const float2 *__restrict__ rows_in, const float2 *__restrict__ gy,
     const float2 *__restrict__ twA, const float2 *__restrict__ twB,
     const float2 *__restrict__ mask, float *__restrict__ part, int n_pix, int bsz, float scale,
@@ -432,9 +432,8 @@ __global__ void __launch_bounds__(256, 3) k_colfilt_bin(
   using S = Split<N1, N2>;
   constexpr int N = S::N, G = S::G, S1 = S::S1, S2 = S::S2;
   constexpr int Q0 = N2 / 4, QH = N2 / 2;
-  constexpr int off = N / 4;
-  extern __shared__ float2 smem[];
-  float2 *s_tile = smem;
+  extern __shared__ __align__(16) float2 smem_k[];
+  float2 *s_tile = smem_k;
   const int TC = blockDim.x / G;
   const int it = blockIdx.y >> 1;              // slot within the chunk
   const int gs = slot0 + it;
@@ -442,26 +441,35 @@ __global__ void __launch_bounds__(256, 3) k_colfilt_bin(
   const int m = (blockIdx.y & 1) ? n_mod - cslot : cslot;
   if ((blockIdx.y & 1) && (cslot == 0 || 2 * cslot == n_mod)) return;   // no second item
   const int col0 = blockIdx.x * TC;
+  // Stage the tile's n_pix rows as a row-major window of W complex starting
+  // at the even column col0e (16-byte copies: W and col0e even), with
+  // cp.async.cg, which bypasses L1 and so leaves the twiddle, mask and tilt
+  // tables resident there.  For odd TC the window has one spare column
+  // (it may read the first entry of the next row: the row buffer carries
+  // two complex of padding after its last row).
+  const int col0e = col0 & ~1, sh = col0 - col0e;
+  const int W = (TC + 1) & ~1, nch = W / 2;
   {
-    // each thread stages one column of the tile, every G-th row, all
-    // copies in flight at once
-    const int c = threadIdx.x % TC;
-    const float2 *src = rows_in + (size_t)it * n_pix * N + col0 + c;
-    for (int jj = threadIdx.x / TC; jj < n_pix; jj += G)
-      cp_async8(s_tile + c * CS + off + jj, src + (size_t)jj * N);
+    const float2 *src = rows_in + (size_t)it * n_pix * N + col0e;
+    for (int e = threadIdx.x; e < n_pix * nch; e += blockDim.x) {
+      const int jj = e / nch, q = e - jj * nch;
+      cp_async16(s_tile + jj * W + 2 * q, src + (size_t)jj * N + 2 * q);
+    }
   }
   const int vec = threadIdx.x / G, lane = threadIdx.x % G;
   cp_async_wait_all();
   __syncthreads();
-  float2 *col = s_tile + vec * CS;
   float2 r[N2];
 #pragma unroll
   for (int n2 = 0; n2 < N2; ++n2) r[n2] = make_float2(0.f, 0.f);
   if (lane < N1) {
     const float2 *g = gy + (size_t)m * n_pix + lane;   // pupil row lane + N1 h
+    const float2 *w = s_tile + sh + vec + lane * W;
 #pragma unroll
-    for (int h = 0; h < QH; ++h) r[Q0 + h] = cmul(col[lane + N1 * (Q0 + h)], __ldg(g + N1 * h));
+    for (int h = 0; h < QH; ++h) r[Q0 + h] = cmul(w[N1 * h * W], __ldg(g + N1 * h));
   }
+  __syncthreads();                             // the window is reused below
+  float2 *col = s_tile + vec * CS;
   RegDFT<N2, false>::run(r);
   __syncwarp();
   if (lane < N1) {
@@ -508,7 +516,7 @@ __global__ void __launch_bounds__(256, 3) k_colfilt_bin(
   __syncthreads();
   const int nd = N / bsz, nbx = TC / bsz;
   float *dst = part + ((size_t)(b % nbw) * n_mod + m) * nd * nd;
-  const float *s_I = reinterpret_cast<const float *>(smem);
+  const float *s_I = reinterpret_cast<const float *>(smem_k);
   for (int q = threadIdx.x; q < nd * nbx; q += blockDim.x) {
     const int yb = q / nbx, xb = q - yb * nbx;
     float v = 0.f;
@@ -571,10 +579,13 @@ static int configure(PwfsPlan *p) {
     const int tc = k * bsz;
     p->blockK = tc * S::G;
     p->csK = ColFiltCfg<N1, N2>::stride(tc);
-    p->smemK = (size_t)tc * p->csK * sizeof(float2);
+    // exchange buffers, or the staging window of n_pix rows x W complex
+    const size_t win = (size_t)p->n_pix * ((tc + 1) & ~1);
+    p->smemK = std::max((size_t)tc * p->csK, win) * sizeof(float2);
     if (p->smemK <= 227 * 1024 && S::N % tc == 0) {
       if ((s = ensure_dynamic_smem((const void *)k_rowfilt<N1, N2>, p->smemR)) ||
-          (s = ensure_dynamic_smem((const void *)k_colfilt_bin<N1, N2>, p->smemK)))
+          (s = ensure_dynamic_smem((const void *)k_colfilt_bin<N1, N2>, p->smemK)) ||
+          (s = ensure_dynamic_smem((const void *)k_colfilt_bin<N1, N2, 160>, p->smemK)))
         return s;
       p->two_ok = true;
     }
@@ -615,11 +626,18 @@ static int run_split2(specula_ctx *ctx, PwfsPlan *p, const float *amp, const flo
                        p->twB.as<float2>(), p->mask.as<float2>(), p->rows.as<float2>(), Np, nc,
                        p->nbw, j0, nj, p->ka));
     dim3 gK(S::N / tc, 2 * nj);
-    SPECULA_LAUNCH(ctx, SPECULA_K_PWFS_COLFILT, st,
-                   k_colfilt_bin<N1, N2><<<gK, p->blockK, p->smemK, st>>>(
-                       p->rows.as<float2>(), p->gy.as<float2>(), p->twA.as<float2>(),
-                       p->twB.as<float2>(), p->mask.as<float2>(), p->part.as<float>(), Np, bsz,
-                       scale, p->n_mod, nc, p->nbw, j0, p->csK));
+    if (S::G == 32 && p->blockK <= 160)
+      SPECULA_LAUNCH(ctx, SPECULA_K_PWFS_COLFILT, st,
+                     k_colfilt_bin<N1, N2, 160><<<gK, p->blockK, p->smemK, st>>>(
+                         p->rows.as<float2>(), p->gy.as<float2>(), p->twA.as<float2>(),
+                         p->twB.as<float2>(), p->mask.as<float2>(), p->part.as<float>(), Np, bsz,
+                         scale, p->n_mod, nc, p->nbw, j0, p->csK));
+    else
+      SPECULA_LAUNCH(ctx, SPECULA_K_PWFS_COLFILT, st,
+                     k_colfilt_bin<N1, N2><<<gK, p->blockK, p->smemK, st>>>(
+                         p->rows.as<float2>(), p->gy.as<float2>(), p->twA.as<float2>(),
+                         p->twB.as<float2>(), p->mask.as<float2>(), p->part.as<float>(), Np, bsz,
+                         scale, p->n_mod, nc, p->nbw, j0, p->csK));
     const int complete = (j0 + nj) / nc - 1;
     if (complete > det_done) {
       dim3 gD((nd * nd + 255) / 256, complete - det_done);
@@ -707,7 +725,9 @@ int pwfs_set_tiles(PwfsPlan *p, int chunk, int ka, int passes) {
   const int per_b = passes == 2 ? p->nc : p->n_mod;
   const int nbw = (chunk + per_b - 1) / per_b + 1;
   const size_t need_field = (size_t)nbw * p->n_pix * p->n_pix * sizeof(float2);
-  const size_t need_rows = (size_t)chunk * p->n_pix * p->N * sizeof(float2);
+  // two complex of padding: the column pass's staging window may read one
+  // entry past the last row
+  const size_t need_rows = ((size_t)chunk * p->n_pix * p->N + 2) * sizeof(float2);
   const size_t need_cols = passes == 3 ? (size_t)chunk * p->N * p->N * sizeof(float2) : 0;
   const size_t need_part = (size_t)nbw * p->n_mod * nd * nd * sizeof(float);
   int s;
