@@ -32,6 +32,7 @@ struct AtmoParams {
   const float *scr[kMaxLayers];
   int side[kMaxLayers];
   double pitch[kMaxLayers], h[kMaxLayers], vx[kMaxLayers], vy[kMaxLayers];
+  double s[kMaxLayers];   // cone factor 1 - h / H, rounded as on the device
   int n_layers;
   int n_pix;
   double pupil_pitch;
@@ -50,7 +51,7 @@ __global__ void __launch_bounds__(256) k_atmo_coords(const AtmoParams P, double 
   const int l = e / (2 * n), r = e % (2 * n);
   const int axis = r / n, idx = r % n;
   const double t = t_dev ? *t_dev : t_host;
-  const double s = __dsub_rn(1.0, __ddiv_rn(P.h[l], P.H));
+  const double s = P.s[l];
   const double theta = axis ? P.theta_y : P.theta_x;
   const double v = axis ? P.vy[l] : P.vx[l];
   const int side = P.side[l];
@@ -157,6 +158,7 @@ extern "C" int specula_atmo_extract(specula_ctx *ctx, int32_t n_layers,
     P.h[l] = L.height_m;
     P.vx[l] = L.vx_mps;
     P.vy[l] = L.vy_mps;
+    P.s[l] = 1.0 - L.height_m / src->height_m;   // one IEEE division, one subtraction
   }
   cudaStream_t st = (cudaStream_t)stream;
   const int nc = n_layers * 2 * pupil->n_pix;
@@ -250,6 +252,7 @@ extern "C" int specula_atmo_extract_noalloc(int32_t n_layers, const specula_laye
     P.h[l] = L.height_m;
     P.vx[l] = L.vx_mps;
     P.vy[l] = L.vy_mps;
+    P.s[l] = 1.0 - L.height_m / src->height_m;   // one IEEE division, one subtraction
   }
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return SPECULA_ECUDA;

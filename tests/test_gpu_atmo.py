@@ -67,6 +67,15 @@ def _layers_case(kind):
               for h, v, a in zip([0.0, 5e3, 10e3], [5.0, 12.5, 20.0], rng.uniform(0, 6.28, 3))]
         src = NS(theta_x_rad=2e-5, theta_y_rad=-1e-5, height_m=math.inf, wavelength_nm=750.0)
         return Ls, src, 160, 0.0525
+    if kind == "mixed":
+        # screens coarser than the pupil (window path) and finer than it (window too
+        # large: gathered from global memory) in one call; 100 px: ragged tiles
+        Ls = [NS(side=s_, pitch_m=p_, height_m=h, vx_mps=float(rng.uniform(-20, 20)),
+                 vy_mps=float(rng.uniform(-20, 20)))
+              for s_, p_, h in [(256, 0.1, 0.0), (1024, 0.02, 2e3), (512, 0.05, 4e3),
+                                (1024, 0.0125, 8e3)]]
+        src = NS(theta_x_rad=1e-5, theta_y_rad=2e-5, height_m=math.inf, wavelength_nm=750.0)
+        return Ls, src, 100, 0.05
     # laser star, cone effect, off axis, ten layers, screens coarser than the pupil
     Ls = [NS(side=256, pitch_m=0.1, height_m=float(h), vx_mps=float(rng.uniform(-20, 20)),
              vy_mps=float(rng.uniform(-20, 20))) for h in np.linspace(0, 20e3, 10)]
@@ -75,7 +84,7 @@ def _layers_case(kind):
     return Ls, src, 200, 0.0478
 
 
-@pytest.mark.parametrize("kind", ["tiny", "ngs3", "lgs10"])
+@pytest.mark.parametrize("kind", ["tiny", "ngs3", "lgs10", "mixed"])
 def test_atmo_extract_parity(env, kind):
     torch, sp, ctx = env
     Ls, src, n, pitch = _layers_case(kind)
