@@ -536,8 +536,17 @@ __global__ void __launch_bounds__(256) k_bin_reduce(const float *__restrict__ pa
   if (pix >= nd2) return;
   const int b = b0 + blockIdx.y;
   const float *src = part + (size_t)(b % nbw) * n_mod * nd2 + pix;
+  // sixteen loads in flight, then the adds in order m = 0, 1, ...
   float v = 0.f;
-  for (int m = 0; m < n_mod; ++m) v += src[(size_t)m * nd2];
+  int m = 0;
+  for (; m + 16 <= n_mod; m += 16) {
+    float x[16];
+#pragma unroll
+    for (int u = 0; u < 16; ++u) x[u] = src[(size_t)(m + u) * nd2];
+#pragma unroll
+    for (int u = 0; u < 16; ++u) v += x[u];
+  }
+  for (; m < n_mod; ++m) v += src[(size_t)m * nd2];
   det[(size_t)b * nd2 + pix] = v;
 }
 

@@ -44,20 +44,20 @@ __global__ void __launch_bounds__(kPyrThreads) k_pyr_slopes(
   const float *d = det + (size_t)b * w2 * w2;
   float part = 0.f;
   int bad = 0;
-  for (int k0 = threadIdx.x; k0 < n_valid; k0 += 4 * kPyrThreads) {
-    int sv[4];
+  for (int k0 = threadIdx.x; k0 < n_valid; k0 += 8 * kPyrThreads) {
+    int sv[8];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < 8; ++u) {
       const int k = k0 + u * kPyrThreads;
       int s = k < n_valid ? __ldg(idx + k) : 0;
       bad |= (unsigned)s >= n2;
       sv[u] = (unsigned)s < n2 ? s : 0;
     }
-    float q[4];
+    float q[8];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) q[u] = quad_sum(d, sv[u], n_sub, w2);
+    for (int u = 0; u < 8; ++u) q[u] = quad_sum(d, sv[u], n_sub, w2);
 #pragma unroll
-    for (int u = 0; u < 4; ++u)
+    for (int u = 0; u < 8; ++u)
       if (k0 + u * kPyrThreads < n_valid) part += q[u];
   }
   part = warp_sum(part);
