@@ -588,6 +588,40 @@ def gpu_leg(args, ws, rank, local):
                                       % (fr.n_slopes, fr.n_modes)}
     fr.use_learned(None)
     mlp.close()
+
+    # shifted-mask modulation (one forward transform per image, the mask moved
+    # per point): its frame rate, and its deviation from the tilt form on the
+    # same phase (detector and reference-subtracted slopes)
+    t_cmp = 5 * fr.dt
+    fr.frame(t_cmp)
+    torch.cuda.synchronize()
+    det_t, sl_t, ref_t = fr.det.clone(), fr.slopes.clone(), fr.ref.clone()
+    sp.specula_pwfs_set_form(ctx, fr.pupil, fr.pwfs, sp.PWFS_FORM_SHIFTED)
+    flat, fdet = torch.zeros_like(fr.phase), torch.empty_like(fr.det)
+    sp.specula_pwfs_image(ctx, fr.pupil, fr.pwfs, fr.amp, flat, fdet)
+    sp.specula_slopes(ctx, fr.slopec, fdet, None, fr.ref)      # flat reference, this form
+    fr.frame(t_cmp)
+    torch.cuda.synchronize()
+    a = det_t.double() / det_t.double().sum()
+    b = fr.det.double() / fr.det.double().sum()
+    dev_img = float((a - b).abs().max() / a.abs().max())
+    dev_sl = float((fr.slopes.double() - sl_t.double()).norm() / sl_t.double().norm())
+    fr.graph.close()
+    fr.capture(st)
+    timed(3, W)
+    mss = timed(K, W)
+    sp.specula_prof_enable(ctx, 64 * (K + 4))
+    timed(K, W, graph=False)
+    prof_s = sp.specula_prof_read(ctx)
+    sp.specula_prof_enable(ctx, 0)
+    variants["shifted_mask"] = {
+        "frames_per_s": K / (sum(mss) / 1e3), "ms_per_step": sum(mss) / K,
+        "detector_norm_max_dev_vs_tilt": dev_img, "slope_rel_rms_dev_vs_tilt": dev_sl,
+        "kernels_us": {k: 1e3 * v[0] / K for k, v in prof_s.items()},
+        "form": "one forward 2D FFT per image; per point the analytic mask at the shifted "
+                "frequencies, inverse FFT, |.|^2 (a different discretisation of the modulation)"}
+    sp.specula_pwfs_set_form(ctx, fr.pupil, fr.pwfs, sp.PWFS_FORM_TILT)
+    fr.ref.copy_(ref_t)
     fr.graph.close()
     fr.capture(st)
 

@@ -169,7 +169,10 @@ int specula_ctx_set_guard(specula_ctx *ctx, int32_t on);
 #define SPECULA_K_MWFS          12  /* multi-sensor frame, one persistent launch  */
 #define SPECULA_K_PWFS_ROWFILT  13  /* pyramid two-pass form: row filter          */
 #define SPECULA_K_PWFS_COLFILT  14  /* pyramid two-pass form: column filter, bins */
-#define SPECULA_K_COUNT         15
+#define SPECULA_K_PWFS_SM_FWD   15  /* shifted-mask form: forward 2-D transform   */
+#define SPECULA_K_PWFS_SM_ROWS  16  /* shifted-mask form: row pass                */
+#define SPECULA_K_PWFS_SM_COLS  17  /* shifted-mask form: column pass, bins       */
+#define SPECULA_K_COUNT         18
 
 /* Enable (capacity > 0: room for that many kernel records; allocates CUDA
  * events; set-up call) or disable (capacity = 0) per-kernel event timing.
@@ -337,6 +340,26 @@ int specula_pwfs_set_tiles(specula_ctx *ctx, const specula_pupil_desc *pupil,
 int specula_pwfs_get_tiles(specula_ctx *ctx, const specula_pupil_desc *pupil,
                            const specula_pwfs_desc *pwfs, int32_t *chunk, int32_t *ka,
                            int32_t *passes);
+
+/* Modulation form of a pyramid plan (set-up call; may allocate).
+ *  SPECULA_PWFS_FORM_TILT (default): the modulation steps as listed for
+ *    ModulatedPyramid (App. A, Tab. 4): per point, tilt the field, forward
+ *    2-D transform, mask, inverse transform, |.|^2.
+ *  SPECULA_PWFS_FORM_SHIFTED: one forward 2-D transform per image; per point
+ *    the analytic mask at the frequencies moved by -s_m, s_m = mod_amp pad
+ *    (cos t_m, sin t_m) bins, inverse transform, |.|^2.  A different
+ *    discretisation: it equals the tilt form where no shifted frequency wraps
+ *    and differs by the spectrum's wrapped wings otherwise (at pad 2, 13-16 %
+ *    of the peak normalised intensity for a flat wavefront on 64-120 px
+ *    pupils).  Needs pad = 2 and the sizes of the two-pass form;
+ *    SPECULA_EUNSUPPORTED else.
+ * specula_pwfs_image then computes the image in the plan's form.  The
+ * autotuner and the tile settings apply to the tilt form; autotune on a
+ * plan in the shifted form returns SPECULA_EUNSUPPORTED. */
+#define SPECULA_PWFS_FORM_TILT    0
+#define SPECULA_PWFS_FORM_SHIFTED 1
+int specula_pwfs_set_form(specula_ctx *ctx, const specula_pupil_desc *pupil,
+                          const specula_pwfs_desc *pwfs, int32_t form);
 
 /* Autotuner: time every candidate (passes in {2, 3}; chunk in
  * {1,2,3,4,6,8,12,16,24,32,48,64} up to the batch's item count and with

@@ -22,6 +22,23 @@ Then the N x N intensity is binned in b x b blocks, b = Np / n_sub, to the
 Readings (the paper prints no formula): centred grids (see ``dft``); amplitude
 1 per in-pupil pixel, so the detector sums to the number of pupil pixels;
 pup_dist = Np so the four images tile the padded grid exactly.
+
+Shifted-mask form (a second discretisation of the same modulation).  The
+tilt of step 1 is exp(2 pi i (s_x x + s_y y) / N) on the padded grid, with
+s = r pad (cos t_m, sin t_m) frequency bins, so the spectrum of step 3 is the
+field's spectrum moved by s.  Moving the mask instead, by -s, gives the same
+image up to a phase that vanishes in |O|^2:
+
+  F = centred DFT of the padded field (once per frame);
+  O_m = centred inverse DFT of M(u + s_x, v + s_y) F(u, v);
+  I = sum over m of |O_m|^2 / n_mod,
+
+with M the analytic mask exp(-2 pi i c (|u + s_x| + |v + s_y|) / N)
+evaluated at the shifted frequencies.  The two forms agree exactly when the
+field's spectrum vanishes wherever u + s_x or v + s_y leaves the centred
+frequency range (whole-bin shifts of a band-limited field); for a pupil-
+limited field they differ where the spectrum wraps: the shifted form applies
+the non-periodic mask to the spectrum's far wings instead of wrapping them.
 """
 import numpy as np
 
@@ -70,4 +87,64 @@ def pwfs_image(amp, phase, pad, n_mod, mod_amp, n_sub, pup_dist):
     """Detector image 2 n_sub x 2 n_sub (with pad = 2 and pup_dist = Np)."""
     Np = amp.shape[0]
     I = pwfs_intensity(amp, phase, pad, n_mod, mod_amp, pup_dist)
+    return bin_image(I, Np // n_sub)
+
+
+def shift_bins(n_mod: int, mod_amp: float, pad: int):
+    """Spectrum shift of each modulation point in frequency bins:
+    s = r pad (cos t_m, sin t_m) (a tilt of r cycles across Np pupil pixels
+    is r pad cycles across the N = pad Np grid)."""
+    cs, sn = mod_angles(n_mod)
+    return mod_amp * pad * cs, mod_amp * pad * sn
+
+
+def tilted_intensity(P: np.ndarray, sx, sy, pup_dist: float) -> np.ndarray:
+    """Steps 1-6 on a padded N x N field P: per point, the tilt
+    exp(2 pi i (s_x x + s_y y) / N) on the centred grid, DFT, mask, inverse
+    DFT, |.|^2, averaged over the points."""
+    N = P.shape[0]
+    x = centred_coords(N)
+    M = pyramid_mask(N, pup_dist)
+    I = np.zeros((N, N))
+    for a, b in zip(sx, sy):
+        tilt = np.exp(2j * np.pi * (x[None, :] * a + x[:, None] * b) / N)
+        I += np.abs(centred_idft2(centred_dft2(P * tilt) * M)) ** 2
+    return I / len(sx)
+
+
+def shifted_mask(N: int, pup_dist: float, sx: float, sy: float) -> np.ndarray:
+    """exp(-2 pi i c (|u + s_x| + |v + s_y|) / N) on the centred grid."""
+    c = pup_dist / 2.0
+    u = centred_coords(N)
+    mx = np.exp(-2j * np.pi * c * np.abs(u + sx) / N)
+    my = np.exp(-2j * np.pi * c * np.abs(u + sy) / N)
+    return my[:, None] * mx[None, :]
+
+
+def shifted_mask_intensity(P: np.ndarray, sx, sy, pup_dist: float) -> np.ndarray:
+    """Shifted-mask form on a padded field: one DFT, then per point the mask
+    at the shifted frequencies, inverse DFT, |.|^2, averaged."""
+    N = P.shape[0]
+    F = centred_dft2(P)
+    I = np.zeros((N, N))
+    for a, b in zip(sx, sy):
+        I += np.abs(centred_idft2(F * shifted_mask(N, pup_dist, a, b))) ** 2
+    return I / len(sx)
+
+
+def pwfs_intensity_shifted(amp, phase, pad, n_mod, mod_amp, pup_dist) -> np.ndarray:
+    """Modulation-averaged N x N intensity in the shifted-mask form."""
+    Np = amp.shape[0]
+    N = pad * Np
+    off = (N - Np) // 2
+    P = np.zeros((N, N), dtype=np.complex128)
+    P[off:off + Np, off:off + Np] = amp * np.exp(1j * phase)
+    sx, sy = shift_bins(n_mod, mod_amp, pad)
+    return shifted_mask_intensity(P, sx, sy, pup_dist)
+
+
+def pwfs_image_shifted(amp, phase, pad, n_mod, mod_amp, n_sub, pup_dist):
+    """Detector image of the shifted-mask form."""
+    Np = amp.shape[0]
+    I = pwfs_intensity_shifted(amp, phase, pad, n_mod, mod_amp, pup_dist)
     return bin_image(I, Np // n_sub)

@@ -14,7 +14,8 @@ import numpy as np
 from . import _abi
 from ._abi import (  # noqa: F401
     PupilDesc, SourceDesc, LayerDesc, PwfsDesc, ShDesc, SlopecDesc, ReconDesc, WfsDesc,
-    SpeculaError, SLOPES_PYR, SLOPES_SH, PREC_FP32, PREC_BF16, PREC_BF16X2,
+    SpeculaError, SLOPES_PYR, SLOPES_SH, PWFS_FORM_TILT, PWFS_FORM_SHIFTED, PREC_FP32, PREC_BF16,
+    PREC_BF16X2,
     OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED, ENONFINITE, ENOPLAN,
 )
 
@@ -134,11 +135,12 @@ def specula_ctx_set_guard(ctx, on):
 
 (K_PWFS_ROWS_FWD, K_PWFS_COLS, K_PWFS_ROWS_INV, K_ATMO, K_SLOPES, K_RECON, K_SH,
  K_PWFS_FIELD, K_PWFS_BIN, K_CALIB, K_GEMM, K_MLP, K_MWFS, K_PWFS_ROWFILT,
- K_PWFS_COLFILT) = range(15)
-K_COUNT = 15
+ K_PWFS_COLFILT, K_PWFS_SM_FWD, K_PWFS_SM_ROWS, K_PWFS_SM_COLS) = range(18)
+K_COUNT = 18
 KERNEL_NAMES = ["pwfs_rows_fwd", "pwfs_cols", "pwfs_rows_inv", "atmo_extract", "slopes",
                 "recon", "sh_spots", "pwfs_field", "pwfs_bin", "calib", "gemm", "mlp", "mwfs",
-                "pwfs_rowfilt", "pwfs_colfilt_bin"]
+                "pwfs_rowfilt", "pwfs_colfilt_bin", "pwfs_sm_fwd", "pwfs_sm_rows",
+                "pwfs_sm_colfilt_bin"]
 
 
 def specula_prof_enable(ctx, capacity):
@@ -346,6 +348,11 @@ def specula_atmo_extract_noalloc(layers, screens, source, pupil, t, phase, t_dev
 def specula_pwfs_plan(ctx, pupil, pwfs):
     _abi.check(lib().specula_pwfs_plan(ctx.handle, C.byref(pupil), C.byref(pwfs)),
                "specula_pwfs_plan")
+
+
+def specula_pwfs_set_form(ctx, pupil, pwfs, form):
+    _abi.check(lib().specula_pwfs_set_form(ctx.handle, C.byref(pupil), C.byref(pwfs), int(form)),
+               "specula_pwfs_set_form")
 
 
 def specula_pwfs_set_tiles(ctx, pupil, pwfs, chunk, ka, passes=2):

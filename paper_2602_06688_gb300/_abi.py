@@ -12,6 +12,7 @@ LIB_PATH = os.path.join(HERE, "libspecula_gb300.so")
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED, ENONFINITE, ENOPLAN = \
     0, -1, -2, -3, -4, -5, -6, -7
 SLOPES_PYR, SLOPES_SH = 0, 1
+PWFS_FORM_TILT, PWFS_FORM_SHIFTED = 0, 1
 PREC_FP32, PREC_BF16, PREC_BF16X2 = 0, 1, 2
 
 
@@ -96,6 +97,7 @@ SIGNATURES = {
                                                P(PupilDesc), dbl, vp, vp, vp]),
     "specula_pwfs_plan": (C.c_int, [vp, P(PupilDesc), P(PwfsDesc)]),
     "specula_pwfs_set_tiles": (C.c_int, [vp, P(PupilDesc), P(PwfsDesc), i32, i32, i32]),
+    "specula_pwfs_set_form": (C.c_int, [vp, P(PupilDesc), P(PwfsDesc), i32]),
     "specula_pwfs_get_tiles": (C.c_int, [vp, P(PupilDesc), P(PwfsDesc), P(i32), P(i32),
                                          P(i32)]),
     "specula_pwfs_autotune": (C.c_int, [vp, P(PupilDesc), P(PwfsDesc), vp, vp, i32, vp, i32,

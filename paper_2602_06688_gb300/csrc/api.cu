@@ -51,6 +51,7 @@ extern "C" int specula_ctx_create(specula_ctx **out, int device) {
   int s = pwfs_init_device();
   if (!s) s = sh_init_device();
   if (!s) s = mwfs_init_device();
+  if (!s) s = pwfs_shifted_init_device();
   if (!s) s = atmo_alloc_tables(c);
   if (s) {
     cudaFree(c->status_dev);
@@ -429,6 +430,23 @@ extern "C" int specula_pwfs_set_tiles(specula_ctx *ctx, const specula_pupil_desc
   return pwfs_set_tiles(p, chunk, ka, passes);
 }
 
+extern "C" int specula_pwfs_set_form(specula_ctx *ctx, const specula_pupil_desc *pupil,
+                                     const specula_pwfs_desc *pwfs, int32_t form) {
+  if (!ctx) return SPECULA_EINVAL;
+  int s = check_pwfs(pupil, pwfs);
+  if (s) return s;
+  if (form != SPECULA_PWFS_FORM_TILT && form != SPECULA_PWFS_FORM_SHIFTED) return SPECULA_EINVAL;
+  PwfsPlan *p = pwfs_plan_find(ctx, pupil, pwfs);
+  if (!p) return SPECULA_ENOPLAN;
+  SPECULA_CK(cudaSetDevice(ctx->device));
+  if (form == SPECULA_PWFS_FORM_SHIFTED && !p->sm_chunk) {
+    SPECULA_CK(cudaDeviceSynchronize());
+    if ((s = pwfs_shifted_prepare(p))) return s;
+  }
+  p->form = form;
+  return SPECULA_OK;
+}
+
 extern "C" int specula_pwfs_autotune(specula_ctx *ctx, const specula_pupil_desc *pupil,
                                      const specula_pwfs_desc *pwfs, const float *amp_dev,
                                      const float *phase_dev, int32_t n_batch, float *det_dev,
@@ -441,6 +459,7 @@ extern "C" int specula_pwfs_autotune(specula_ctx *ctx, const specula_pupil_desc 
   if (s) return s;
   PwfsPlan *p = pwfs_plan_find(ctx, pupil, pwfs);
   if (!p) return SPECULA_ENOPLAN;
+  if (p->form != SPECULA_PWFS_FORM_TILT) return SPECULA_EUNSUPPORTED;
   SPECULA_CK(cudaSetDevice(ctx->device));
   int bc = 0, bk = 0, bp = 0;
   s = pwfs_autotune(ctx, p, amp_dev, phase_dev, n_batch, det_dev, (cudaStream_t)stream, reps,

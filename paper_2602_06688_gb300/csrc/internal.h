@@ -78,6 +78,16 @@ struct PwfsPlan {
   DevBuf rows;          // [chunk][n_pix][N] float2: after the row transform
   DevBuf cols;          // [chunk][N][N] float2: after the column pass (three-pass form)
   DevBuf part;          // [chunk][nd][nd] float: binned intensity per item
+  // shifted-mask form (SPECULA_PWFS_FORM_SHIFTED)
+  int form = 0;
+  int sm_blockK = 0, sm_chunk = 0;
+  size_t sm_smemK = 0, sm_smemR = 0, sm_smemC = 0;
+  DevBuf sm_pre;        // [Np] float2: centred-DFT input phase over the pupil
+  DevBuf sm_mx, sm_my;  // [nc][N], [n_mod][N] float2: shifted mask factors / N
+  DevBuf sm_frows;      // [Np][N] float2: after the forward row transform
+  DevBuf sm_fspec;      // [N][N] float2: the field's spectrum
+  DevBuf sm_rows;       // [sm_chunk][N][N] float2 (+2): after the inverse row transform
+  DevBuf sm_part;       // [n_mod][nd][nd] float: binned intensity per point
 };
 
 struct ShPlan {
@@ -138,6 +148,12 @@ inline void prof_end(specula_ctx *c, int slot, int kid, cudaStream_t st) {
 int pwfs_init_device();
 int sh_init_device();
 int mwfs_init_device();
+int pwfs_shifted_init_device();
+int pwfs_shifted_prepare(PwfsPlan *p);
+int pwfs_shifted_run(specula_ctx *ctx, PwfsPlan *p, const float *amp, const float *phase,
+                     int n_batch, float *det, cudaStream_t st);
+int pwfs_bin_reduce(specula_ctx *ctx, const float *part, float *det, int nd2, int n_mod,
+                    cudaStream_t st);
 int atmo_alloc_tables(specula_ctx *ctx);
 
 // launchers implemented in the kernel translation units

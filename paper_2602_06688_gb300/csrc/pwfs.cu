@@ -755,8 +755,18 @@ int pwfs_set_tiles(PwfsPlan *p, int chunk, int ka, int passes) {
   return SPECULA_OK;
 }
 
+int pwfs_bin_reduce(specula_ctx *ctx, const float *part, float *det, int nd2, int n_mod,
+                    cudaStream_t st) {
+  SPECULA_LAUNCH(ctx, SPECULA_K_PWFS_BIN, st,
+                 k_bin_reduce<<<dim3((nd2 + 255) / 256, 1), 256, 0, st>>>(part, det, nd2, n_mod,
+                                                                          1, 0));
+  return SPECULA_OK;
+}
+
 int pwfs_run(specula_ctx *ctx, PwfsPlan *p, const float *amp, const float *phase, int n_batch,
              float *det, cudaStream_t st) {
+  if (p->form == SPECULA_PWFS_FORM_SHIFTED)
+    return pwfs_shifted_run(ctx, p, amp, phase, n_batch, det, st);
   switch (p->N) {
     case 64: return run_split<8, 8>(ctx, p, amp, phase, n_batch, det, st);
     case 128: return run_split<8, 16>(ctx, p, amp, phase, n_batch, det, st);
