@@ -29,7 +29,10 @@ Modules and their pins (tests/test_oracle_*.py):
                 identity.
 * ``pyramid``   modulated pyramid intensity and binning; pinned to Parseval
                 flux, mirror/transpose symmetries, equal quadrant flux, tilt
-                antisymmetry, and the unit-mask identity.
+                antisymmetry, and the unit-mask identity.  Its shifted-mask
+                form is pinned to the tilt form for whole-bin shifts of a
+                band-limited field and without modulation, to a brute-force
+                tiny case, Parseval flux and the flat-wavefront symmetries.
 * ``sh``        Shack-Hartmann spots; pinned to zero centroid for a flat
                 wavefront, exact circular roll under an integer tilt, and
                 per-subaperture Parseval flux.
@@ -51,4 +54,8 @@ Modules and their pins (tests/test_oracle_*.py):
                 concatenated; pinned to zero slopes for flat screens, equal
                 SH slopes in every subaperture for a linear phase ramp, and
                 block-wise agreement with the single-sensor chains.
+* ``loop``      the closed loop (modal mirror, integrator, one-step delay)
+                and its residual RMS / Strehl ratio; pinned to the scalar
+                recursion of an ideal sensor on a static modal aberration,
+                the zero-gain identity and closed-form statistics.
 """
