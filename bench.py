@@ -362,6 +362,53 @@ def learned_leg(ctx, n_train=200000, n_test=5000, epochs=12):
                                        "linear_batched": n_test / (lin_ms / 1e3)}}
 
 
+def closed_loop_leg(ctx, steps=400, settle=150):
+    """The closed loop on the 8 m pyramid (160 px pupil, 24 points, three
+    layers, 500 calibrated Zernike modes, integrator gain 0.4): one step
+    (extraction, mirror shape, residual statistics, pyramid, slopes, MVM,
+    integrator update) per replay of a CUDA graph, steps back to back as a
+    running loop.  Reports the step rate and the loop's residual RMS and
+    H-band (1650 nm) Strehl ratio averaged after `settle` steps, against the
+    open loop (gain 0) over the same atmosphere.  The residual RMS covers the
+    whole pupil, including edge pixels outside every valid subaperture: the
+    sensor never sees them, and the high-order modes' commands drift there
+    without bound (the Strehl ratio, dominated by the sensed interior, is the
+    figure of merit)."""
+    import torch
+    import synth
+    from paper_2602_06688_gb300.loop import ClosedLoop
+    st = torch.cuda.Stream()
+    out = {"workload": "pwfs8m", "gain": 0.4, "sci_wavelength_nm": 1650.0}
+    cl = ClosedLoop(ctx, synth.workload("pwfs8m"), gain=0.4)
+    for label, gain in (("closed", 0.4), ("open", 0.0)):
+        cl.gain = gain
+        cl.reset()
+        cl.close()
+        cl.capture(st)
+        hist = torch.zeros(steps, 2, dtype=torch.float64, device="cuda")
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        with torch.cuda.stream(st):
+            e0.record()
+            for k in range(steps):
+                cl.replay(k * cl.fr.dt, st)
+                hist[k].copy_(cl.stats)
+            e1.record()
+        torch.cuda.synchronize()
+        h = hist.cpu().numpy()[settle:]
+        out[label] = {"strehl": float(h[:, 1].mean()),
+                      "resid_rms_rad_wfs_full_pupil": float(h[:, 0].mean())}
+        if label == "closed":
+            ms = e0.elapsed_time(e1)
+            out.update({"frames_per_s": steps / (ms / 1e3), "ms_per_step": ms / steps,
+                        "n_modes": cl.n_modes, "rank": cl.rank,
+                        "graph_kernels": cl.graph.kernel_count(),
+                        "timing": "back-to-back steps, each with a 16-byte copy of its "
+                                  "statistics; L2 not flushed"})
+    cl.close()
+    return out
+
+
 def systems_leg(ctx, steps=50):
     """The other systems of the paper's scale list, one frame per step from a
     CUDA graph, L2 flushed between frames outside the events: the 8 m single
@@ -717,6 +764,8 @@ def gpu_leg(args, ws, rank, local):
                 "peaks": {"source": how, "hbm_gbs": pk.get("hbm_gbs")}}
         if not args.no_systems:
             line["systems"] = systems_leg(ctx)
+        if not args.no_loop:
+            line["closed_loop"] = closed_loop_leg(ctx)
         if not args.no_learned:
             line["learned"] = learned_leg(ctx)
             line["gemm_bf16"] = gemm_leg(ctx, pk)
@@ -742,6 +791,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-systems", action="store_true",
                     help="skip the 8 m and 39 m multi-sensor system timings")
+    ap.add_argument("--no-loop", action="store_true",
+                    help="skip the closed-loop run on the 8 m system")
     ap.add_argument("--no-learned", action="store_true",
                     help="skip the learned-reconstructor training run on the 8 m system")
     ap.add_argument("--quick", action="store_true",

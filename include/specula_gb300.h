@@ -172,7 +172,8 @@ int specula_ctx_set_guard(specula_ctx *ctx, int32_t on);
 #define SPECULA_K_PWFS_SM_FWD   15  /* shifted-mask form: forward 2-D transform   */
 #define SPECULA_K_PWFS_SM_ROWS  16  /* shifted-mask form: row pass                */
 #define SPECULA_K_PWFS_SM_COLS  17  /* shifted-mask form: column pass, bins       */
-#define SPECULA_K_COUNT         18
+#define SPECULA_K_LOOP          18  /* closed loop: mirror shape, residual, update */
+#define SPECULA_K_COUNT         19
 
 /* Enable (capacity > 0: room for that many kernel records; allocates CUDA
  * events; set-up call) or disable (capacity = 0) per-kernel event timing.
@@ -611,6 +612,39 @@ int specula_calib_intmat(specula_ctx *ctx, const specula_pupil_desc *pupil,
 int specula_pinv_fp64(specula_ctx *ctx, const double *A_dev, int32_t m, int32_t n,
                       double rcond, double *R_dev, float *R32_dev, int32_t *rank,
                       void *stream);
+
+/* ---- closed loop (per-frame calls: enqueue only, allocate nothing) ---------
+ * The closed-loop objects of the SOUL example (App. B, Listing 2: a DM with a
+ * modal influence-function basis, an IirFilter integrator, the ":-1" delayed
+ * connection of Sect. 2.2).  Step k of a loop:
+ *   residual = phi_atm(t_k) - B^T c_{k-1}        (specula_dm_shape, then
+ *                                                 specula_loop_residual)
+ *   m = R (slopes(residual) - reference)         (pyramid, slopes, recon calls)
+ *   c_k = (1 - leak) c_{k-1} + gain m            (specula_loop_integrate)
+ * All sums run in a fixed order: a loop is bit-reproducible. */
+
+/* phase_dev[p] = sum over j (in order) of cmd_dev[j] basis_dev[j][p]:
+ * basis n_modes x n_pix2 row-major floats (zero outside the pupil), cmd
+ * n_modes floats, phase n_pix2 floats (radians at the sensor wavelength).
+ * n_modes <= 12288 (SPECULA_EUNSUPPORTED above). */
+int specula_dm_shape(specula_ctx *ctx, int32_t n_modes, int32_t n_pix2, const float *basis_dev,
+                     const float *cmd_dev, float *phase_dev, void *stream);
+
+/* resid_dev = atm_dev - dm_dev (n_pix2 floats each) and, over the pupil
+ * (weights amp_dev), stats_dev[0] = the residual's RMS with its piston
+ * removed and stats_dev[1] = the Strehl ratio at the science wavelength,
+ * |sum amp exp(i r wfs_over_sci)|^2 / (sum amp)^2, with wfs_over_sci =
+ * lambda_wfs / lambda_sci > 0 (two device doubles; float64 partial sums in
+ * a fixed order).  Uses the context's statistics workspace: calls on one
+ * context must not overlap on the GPU. */
+int specula_loop_residual(specula_ctx *ctx, int32_t n_pix2, const float *amp_dev,
+                          const float *atm_dev, const float *dm_dev, double wfs_over_sci,
+                          float *resid_dev, double *stats_dev, void *stream);
+
+/* cmd_dev = (1 - leak) cmd_dev + gain modes_dev (n_modes floats each);
+ * 0 <= leak <= 1. */
+int specula_loop_integrate(specula_ctx *ctx, int32_t n_modes, float gain, float leak,
+                           const float *modes_dev, float *cmd_dev, void *stream);
 
 #ifdef __cplusplus
 }

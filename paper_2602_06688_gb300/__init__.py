@@ -135,12 +135,12 @@ def specula_ctx_set_guard(ctx, on):
 
 (K_PWFS_ROWS_FWD, K_PWFS_COLS, K_PWFS_ROWS_INV, K_ATMO, K_SLOPES, K_RECON, K_SH,
  K_PWFS_FIELD, K_PWFS_BIN, K_CALIB, K_GEMM, K_MLP, K_MWFS, K_PWFS_ROWFILT,
- K_PWFS_COLFILT, K_PWFS_SM_FWD, K_PWFS_SM_ROWS, K_PWFS_SM_COLS) = range(18)
-K_COUNT = 18
+ K_PWFS_COLFILT, K_PWFS_SM_FWD, K_PWFS_SM_ROWS, K_PWFS_SM_COLS, K_LOOP) = range(19)
+K_COUNT = 19
 KERNEL_NAMES = ["pwfs_rows_fwd", "pwfs_cols", "pwfs_rows_inv", "atmo_extract", "slopes",
                 "recon", "sh_spots", "pwfs_field", "pwfs_bin", "calib", "gemm", "mlp", "mwfs",
                 "pwfs_rowfilt", "pwfs_colfilt_bin", "pwfs_sm_fwd", "pwfs_sm_rows",
-                "pwfs_sm_colfilt_bin"]
+                "pwfs_sm_colfilt_bin", "loop"]
 
 
 def specula_prof_enable(ctx, capacity):
@@ -435,6 +435,38 @@ def specula_recon(ctx, rec, slopes, modes, stream=None):
         ctx.handle, C.byref(rec), _dev(slopes, torch.float32, nb * rec.n_slopes, "slopes"), nb,
         _dev(modes, torch.float32, nb * rec.n_modes, "modes"), _stream(stream)),
         "specula_recon")
+
+
+def specula_dm_shape(ctx, basis, cmd, phase, stream=None):
+    """phase = B^T cmd: basis (n_modes, ...) float32, cmd (n_modes,), phase of
+    the basis' trailing size."""
+    import torch
+    nm = basis.shape[0]
+    npx = basis.numel() // nm
+    _abi.check(lib().specula_dm_shape(
+        ctx.handle, int(nm), int(npx), _dev(basis, torch.float32, nm * npx, "basis"),
+        _dev(cmd, torch.float32, nm, "cmd"), _dev(phase, torch.float32, npx, "phase"),
+        _stream(stream)), "specula_dm_shape")
+
+
+def specula_loop_residual(ctx, amp, atm, dm, wfs_over_sci, resid, stats, stream=None):
+    """resid = atm - dm; stats (2 float64) = (piston-free RMS, Strehl)."""
+    import torch
+    n = amp.numel()
+    _abi.check(lib().specula_loop_residual(
+        ctx.handle, int(n), _dev(amp, torch.float32, n, "amp"), _dev(atm, torch.float32, n, "atm"),
+        _dev(dm, torch.float32, n, "dm"), float(wfs_over_sci),
+        _dev(resid, torch.float32, n, "resid"), _dev(stats, torch.float64, 2, "stats"),
+        _stream(stream)), "specula_loop_residual")
+
+
+def specula_loop_integrate(ctx, gain, leak, modes, cmd, stream=None):
+    """cmd = (1 - leak) cmd + gain modes."""
+    import torch
+    n = cmd.numel()
+    _abi.check(lib().specula_loop_integrate(
+        ctx.handle, int(n), float(gain), float(leak), _dev(modes, torch.float32, n, "modes"),
+        _dev(cmd, torch.float32, n, "cmd"), _stream(stream)), "specula_loop_integrate")
 
 
 def specula_recon_convert(ctx, R, precision, hi, lo=None, stream=None):

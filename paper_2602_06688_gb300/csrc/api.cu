@@ -53,8 +53,10 @@ extern "C" int specula_ctx_create(specula_ctx **out, int device) {
   if (!s) s = mwfs_init_device();
   if (!s) s = pwfs_shifted_init_device();
   if (!s) s = atmo_alloc_tables(c);
+  if (!s) s = loop_alloc_workspace(c);
   if (s) {
     cudaFree(c->status_dev);
+    if (c->loop_part) cudaFree(c->loop_part);
     if (c->atmo_tab_i) cudaFree(c->atmo_tab_i);
     if (c->atmo_tab_f) cudaFree(c->atmo_tab_f);
     delete c;
@@ -80,6 +82,7 @@ extern "C" int specula_ctx_destroy(specula_ctx *ctx) {
   ctx->pwfs.clear();
   ctx->sh.clear();
   if (ctx->status_dev) cudaFree(ctx->status_dev);
+  if (ctx->loop_part) cudaFree(ctx->loop_part);
   if (ctx->atmo_tab_i) cudaFree(ctx->atmo_tab_i);
   if (ctx->atmo_tab_f) cudaFree(ctx->atmo_tab_f);
   delete ctx;

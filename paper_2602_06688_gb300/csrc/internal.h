@@ -107,6 +107,7 @@ struct ShPlan {
 struct specula_ctx {
   int device = 0;
   int32_t *status_dev = nullptr;
+  double *loop_part = nullptr;      // [kLoopMaxBlocks][5] closed-loop statistics partials
   bool guard = true;                // slope kernels record non-finite outputs
   int *atmo_tab_i = nullptr;        // [64][2][8192] screen sample index
   float *atmo_tab_f = nullptr;      // [64][2][8192] interpolation fraction
@@ -148,6 +149,8 @@ inline void prof_end(specula_ctx *c, int slot, int kid, cudaStream_t st) {
 int pwfs_init_device();
 int sh_init_device();
 int mwfs_init_device();
+constexpr int kLoopMaxBlocks = 512;
+int loop_alloc_workspace(specula_ctx *ctx);
 int pwfs_shifted_init_device();
 int pwfs_shifted_prepare(PwfsPlan *p);
 int pwfs_shifted_run(specula_ctx *ctx, PwfsPlan *p, const float *amp, const float *phase,
