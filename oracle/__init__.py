@@ -54,6 +54,10 @@ Modules and their pins (tests/test_oracle_*.py):
                 concatenated; pinned to zero slopes for flat screens, equal
                 SH slopes in every subaperture for a linear phase ramp, and
                 block-wise agreement with the single-sensor chains.
+* ``ccd``       detector photon (Poisson) and readout noise from Philox draws;
+                pinned to the Poisson mean, variance and zero-count
+                probability in both samplers, the readout normal's moments
+                and determinism per (seed, frame).
 * ``loop``      the closed loop (modal mirror, integrator, one-step delay)
                 and its residual RMS / Strehl ratio; pinned to the scalar
                 recursion of an ideal sensor on a static modal aberration,
