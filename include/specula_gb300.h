@@ -173,7 +173,8 @@ int specula_ctx_set_guard(specula_ctx *ctx, int32_t on);
 #define SPECULA_K_PWFS_SM_ROWS  16  /* shifted-mask form: row pass                */
 #define SPECULA_K_PWFS_SM_COLS  17  /* shifted-mask form: column pass, bins       */
 #define SPECULA_K_LOOP          18  /* closed loop: mirror shape, residual, update */
-#define SPECULA_K_COUNT         19
+#define SPECULA_K_CCD           19  /* detector photon and readout noise          */
+#define SPECULA_K_COUNT         20
 
 /* Enable (capacity > 0: room for that many kernel records; allocates CUDA
  * events; set-up call) or disable (capacity = 0) per-kernel event timing.
@@ -612,6 +613,21 @@ int specula_calib_intmat(specula_ctx *ctx, const specula_pupil_desc *pupil,
 int specula_pinv_fp64(specula_ctx *ctx, const double *A_dev, int32_t m, int32_t n,
                       double rcond, double *R_dev, float *R32_dev, int32_t *rank,
                       void *stream);
+
+/* ---- detector noise (per-frame call: enqueue only, allocates nothing) ------
+ * CCD object (App. A, Tab. 4; App. B, Listing 2: photon_noise,
+ * readout_noise, quantum_eff): pixel p of out_dev = k + ron g, with
+ * k ~ Poisson(det_dev[p] scale) (scale = photons per frame x quantum
+ * efficiency / pupil pixels, det_dev the noise-free detector image) and g a
+ * standard normal.  Draws from Philox4x32-10, counter (p, frame, block,
+ * stream), key = seed: up to a mean of 30 the multiplicative method (the
+ * number of uniforms whose running float64 product stays above
+ * exp(-lambda), at most 1000; stream 2), above it floor(lambda +
+ * sqrt(lambda) g0 + 1/2) clamped at 0 (Box-Muller normals of stream 3, whose
+ * second normal is g).  Reproducible per (seed, frame).  n floats in and
+ * out (out may alias det); scale >= 0, ron >= 0. */
+int specula_ccd(specula_ctx *ctx, int32_t n, const float *det_dev, double scale, double ron,
+                uint64_t seed, uint32_t frame, float *out_dev, void *stream);
 
 /* ---- closed loop (per-frame calls: enqueue only, allocate nothing) ---------
  * The closed-loop objects of the SOUL example (App. B, Listing 2: a DM with a

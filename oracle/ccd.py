@@ -14,7 +14,8 @@ counter (pixel, frame, block, stream) and key (seed low, seed high):
   product stays above exp(-lambda), in float64, at most KMAX draws; uniform j
   is word j mod 4 of the block j // 4 of stream 2;
 * lambda > LAMBDA_SWITCH: k = max(0, floor(lambda + sqrt(lambda) g0 + 1/2))
-  with g0 the first Box-Muller normal of block 0 of stream 3;
+  (at most 2^31 - 1) with g0 the first Box-Muller normal of block 0 of
+  stream 3;
 * the readout normal g is the second normal of that block.
 
 Both the integer decision and the sum are taken in float64; the result is
@@ -49,7 +50,7 @@ def poisson_count(lam: float, pix: int, frame: int, seed: int) -> int:
     """The photo-electron count of one pixel (see the module docstring)."""
     if lam > LAMBDA_SWITCH:
         g0, _ = _normals(pix, frame, seed)
-        return max(0, int(np.floor(lam + np.sqrt(lam) * g0 + 0.5)))
+        return min(max(0, int(np.floor(lam + np.sqrt(lam) * g0 + 0.5))), 2147483647)
     L = np.exp(-lam)
     p = 1.0
     k = 0

@@ -135,12 +135,12 @@ def specula_ctx_set_guard(ctx, on):
 
 (K_PWFS_ROWS_FWD, K_PWFS_COLS, K_PWFS_ROWS_INV, K_ATMO, K_SLOPES, K_RECON, K_SH,
  K_PWFS_FIELD, K_PWFS_BIN, K_CALIB, K_GEMM, K_MLP, K_MWFS, K_PWFS_ROWFILT,
- K_PWFS_COLFILT, K_PWFS_SM_FWD, K_PWFS_SM_ROWS, K_PWFS_SM_COLS, K_LOOP) = range(19)
-K_COUNT = 19
+ K_PWFS_COLFILT, K_PWFS_SM_FWD, K_PWFS_SM_ROWS, K_PWFS_SM_COLS, K_LOOP, K_CCD) = range(20)
+K_COUNT = 20
 KERNEL_NAMES = ["pwfs_rows_fwd", "pwfs_cols", "pwfs_rows_inv", "atmo_extract", "slopes",
                 "recon", "sh_spots", "pwfs_field", "pwfs_bin", "calib", "gemm", "mlp", "mwfs",
                 "pwfs_rowfilt", "pwfs_colfilt_bin", "pwfs_sm_fwd", "pwfs_sm_rows",
-                "pwfs_sm_colfilt_bin", "loop"]
+                "pwfs_sm_colfilt_bin", "loop", "ccd"]
 
 
 def specula_prof_enable(ctx, capacity):
@@ -435,6 +435,16 @@ def specula_recon(ctx, rec, slopes, modes, stream=None):
         ctx.handle, C.byref(rec), _dev(slopes, torch.float32, nb * rec.n_slopes, "slopes"), nb,
         _dev(modes, torch.float32, nb * rec.n_modes, "modes"), _stream(stream)),
         "specula_recon")
+
+
+def specula_ccd(ctx, det, scale, ron, seed, frame, out, stream=None):
+    """out = Poisson(det scale) + ron N(0, 1), reproducible per (seed, frame)."""
+    import torch
+    n = det.numel()
+    _abi.check(lib().specula_ccd(
+        ctx.handle, int(n), _dev(det, torch.float32, n, "det"), float(scale), float(ron),
+        int(seed) & 0xFFFFFFFFFFFFFFFF, int(frame) & 0xFFFFFFFF, _dev(out, torch.float32, n, "out"),
+        _stream(stream)), "specula_ccd")
 
 
 def specula_dm_shape(ctx, basis, cmd, phase, stream=None):

@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "internal.h"
+#include "philox.cuh"
 
 namespace specula {
 
@@ -98,28 +99,6 @@ __global__ void k_screen_final(const double2 *__restrict__ T, const double2 *__r
           sub += c.x * e.x - c.y * e.y;
         }
     out[(size_t)y * M + x] = (float)(v + (sub - sub_mean));
-  }
-}
-
-// ---- counter-based noise: Philox4x32-10 (Salmon et al., SC 2011) ------------
-// Ten rounds of (hi0, lo0) = M0 c0, (hi1, lo1) = M1 c2,
-// c <- (hi1 ^ c1 ^ k0, lo1, hi0 ^ c3 ^ k1, lo0), key bumped by the Weyl
-// constants between rounds; uniforms (x + 0.5) 2^-32; Box-Muller normals.
-__device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1) {
-#pragma unroll
-  for (int r = 0; r < 10; ++r) {
-    const uint64_t p0 = (uint64_t)0xD2511F53u * c[0];
-    const uint64_t p1 = (uint64_t)0xCD9E8D57u * c[2];
-    const uint32_t n0 = (uint32_t)(p1 >> 32) ^ c[1] ^ k0;
-    const uint32_t n2 = (uint32_t)(p0 >> 32) ^ c[3] ^ k1;
-    c[1] = (uint32_t)p1;
-    c[3] = (uint32_t)p0;
-    c[0] = n0;
-    c[2] = n2;
-    if (r < 9) {
-      k0 += 0x9E3779B9u;
-      k1 += 0xBB67AE85u;
-    }
   }
 }
 
