@@ -669,6 +669,24 @@ def gpu_leg(args, ws, rank, local):
                 "frequencies, inverse FFT, |.|^2 (a different discretisation of the modulation)"}
     sp.specula_pwfs_set_form(ctx, fr.pupil, fr.pwfs, sp.PWFS_FORM_TILT)
     fr.ref.copy_(ref_t)
+    # detector photon and readout noise in the frame (CCD call after the
+    # image): frame rate, and the slope noise against the noise-free frame
+    noise = {"photons": 2.0e6, "qe": 0.8, "ron": 0.5, "seed": 7}
+    fr.noise = noise
+    fr.noise_scale = noise["photons"] * noise["qe"] / float(
+        sp.specula_pupil_mask_host(fr.pupil).sum())
+    fr.frame(t_cmp)
+    torch.cuda.synchronize()
+    dev_noise = float((fr.slopes.double() - sl_t.double()).norm() / sl_t.double().norm())
+    fr.graph.close()
+    fr.capture(st)
+    timed(3, W)
+    msn = timed(K, W)
+    variants["ccd_noise"] = {"frames_per_s": K / (sum(msn) / 1e3), "ms_per_step": sum(msn) / K,
+                             "photons_per_frame": noise["photons"], "qe": noise["qe"],
+                             "ron_e": noise["ron"],
+                             "slope_rel_rms_noise": dev_noise}
+    fr.noise = None
     fr.graph.close()
     fr.capture(st)
 

@@ -624,10 +624,13 @@ int specula_pinv_fp64(specula_ctx *ctx, const double *A_dev, int32_t m, int32_t 
  * number of uniforms whose running float64 product stays above
  * exp(-lambda), at most 1000; stream 2), above it floor(lambda +
  * sqrt(lambda) g0 + 1/2) clamped at 0 (Box-Muller normals of stream 3, whose
- * second normal is g).  Reproducible per (seed, frame).  n floats in and
- * out (out may alias det); scale >= 0, ron >= 0. */
+ * second normal is g).  Reproducible per (seed, frame); the frame index is
+ * frame + *frame_dev when frame_dev (one device uint32, nullable) is given,
+ * so a captured graph draws new noise when the caller advances *frame_dev.
+ * n floats in and out (out may alias det); scale >= 0, ron >= 0. */
 int specula_ccd(specula_ctx *ctx, int32_t n, const float *det_dev, double scale, double ron,
-                uint64_t seed, uint32_t frame, float *out_dev, void *stream);
+                uint64_t seed, uint32_t frame, const uint32_t *frame_dev, float *out_dev,
+                void *stream);
 
 /* ---- closed loop (per-frame calls: enqueue only, allocate nothing) ---------
  * The closed-loop objects of the SOUL example (App. B, Listing 2: a DM with a

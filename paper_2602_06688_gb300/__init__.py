@@ -437,13 +437,15 @@ def specula_recon(ctx, rec, slopes, modes, stream=None):
         "specula_recon")
 
 
-def specula_ccd(ctx, det, scale, ron, seed, frame, out, stream=None):
-    """out = Poisson(det scale) + ron N(0, 1), reproducible per (seed, frame)."""
+def specula_ccd(ctx, det, scale, ron, seed, frame, out, frame_dev=None, stream=None):
+    """out = Poisson(det scale) + ron N(0, 1), reproducible per (seed, frame);
+    frame_dev (one int32 CUDA tensor, nullable) adds a device-side index."""
     import torch
     n = det.numel()
     _abi.check(lib().specula_ccd(
         ctx.handle, int(n), _dev(det, torch.float32, n, "det"), float(scale), float(ron),
-        int(seed) & 0xFFFFFFFFFFFFFFFF, int(frame) & 0xFFFFFFFF, _dev(out, torch.float32, n, "out"),
+        int(seed) & 0xFFFFFFFFFFFFFFFF, int(frame) & 0xFFFFFFFF,
+        _dev(frame_dev, torch.int32, 1, "frame_dev"), _dev(out, torch.float32, n, "out"),
         _stream(stream)), "specula_ccd")
 
 

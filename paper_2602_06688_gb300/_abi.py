@@ -99,7 +99,8 @@ SIGNATURES = {
     "specula_pwfs_set_tiles": (C.c_int, [vp, P(PupilDesc), P(PwfsDesc), i32, i32, i32]),
     "specula_pwfs_set_form": (C.c_int, [vp, P(PupilDesc), P(PwfsDesc), i32]),
     "specula_dm_shape": (C.c_int, [vp, i32, i32, vp, vp, vp, vp]),
-    "specula_ccd": (C.c_int, [vp, i32, vp, C.c_double, C.c_double, C.c_uint64, C.c_uint32, vp, vp]),
+    "specula_ccd": (C.c_int, [vp, i32, vp, C.c_double, C.c_double, C.c_uint64, C.c_uint32, vp,
+                              vp, vp]),
     "specula_loop_residual": (C.c_int, [vp, i32, vp, vp, vp, C.c_double, vp, vp, vp]),
     "specula_loop_integrate": (C.c_int, [vp, i32, C.c_float, C.c_float, vp, vp, vp]),
     "specula_pwfs_get_tiles": (C.c_int, [vp, P(PupilDesc), P(PwfsDesc), P(i32), P(i32),

@@ -10,7 +10,8 @@ import numpy as np
 import synth
 from . import (PREC_BF16, PREC_BF16X2, PREC_FP32, SLOPES_PYR, layer_desc, pupil_desc,
                pwfs_desc, recon_desc, slopec_desc, source_desc, specula_atmo_extract,
-               specula_pupil_mask, specula_pwfs_image, specula_pwfs_plan, specula_recon,
+               specula_ccd, specula_pupil_mask, specula_pupil_mask_host, specula_pwfs_image,
+               specula_pwfs_plan, specula_recon,
                specula_recon_convert, specula_screen_generate, specula_slopes,
                specula_valid_subaps_host)
 
@@ -23,11 +24,16 @@ def seeded_reconstructor(n_modes, n_slopes, seed):
 
 class PwfsFrame:
     def __init__(self, ctx, wl, sensor=0, precision=PREC_FP32, R=None, n_modes=None,
-                 seed_offset=0, device="cuda", autotune=False, batch=1):
+                 seed_offset=0, device="cuda", autotune=False, batch=1, noise=None):
         """batch > 1: every step computes `batch` consecutive frames (times t,
         t + dt, ...) of the open-loop sequence together: one extraction per
         frame, then one pyramid call, one slope call and one MVM call over
-        the whole batch."""
+        the whole batch.
+
+        noise: None (noise-free detector) or a dict with ``photons`` (per frame
+        over the pupil), ``qe``, ``ron`` (electrons RMS) and ``seed``: the
+        detector image then carries photon and readout noise (the CCD call),
+        frame index round(t / dt)."""
         import torch
         self.torch = torch
         self.ctx = ctx
@@ -43,11 +49,12 @@ class PwfsFrame:
         self.n_pix = n
         self.screens = []
         for l in wl.layers:
-            noise = torch.tensor(synth.screen_noise(l.seed + seed_offset, l.side), device=device)
+            scr_noise = torch.tensor(synth.screen_noise(l.seed + seed_offset, l.side),
+                                     device=device)
             scr = torch.empty(l.side, l.side, device=device, dtype=torch.float32)
-            specula_screen_generate(ctx, l.side, l.pitch_m, l.r0_m, l.L0_m, noise,
+            specula_screen_generate(ctx, l.side, l.pitch_m, l.r0_m, l.L0_m, scr_noise,
                                     synth.subharmonic_noise(l.seed + seed_offset), scr)
-            del noise
+            del scr_noise
             self.screens.append(scr)
         self.amp = torch.empty(n, n, device=device)
         specula_pupil_mask(ctx, self.pupil, self.amp)
@@ -71,6 +78,8 @@ class PwfsFrame:
             self.slopes = torch.empty(batch, self.n_slopes, device=device)
             self.modes = torch.empty(batch, self.n_modes, device=device)
         self.ref = torch.empty(self.n_slopes, device=device)
+        self.noise = dict(noise) if noise else None
+        self.frame_dev = torch.zeros(1, dtype=torch.int32, device=device)
         self.slopec = slopec_desc(SLOPES_PYR, s.pwfs.n_sub, self.valid)
         if R is None:
             R = seeded_reconstructor(self.n_modes, self.n_slopes, seed=7 + seed_offset)
@@ -81,6 +90,11 @@ class PwfsFrame:
         flat, fdet = torch.zeros(n, n, device=device), torch.empty(d, d, device=device)
         specula_pwfs_image(ctx, self.pupil, self.pwfs, self.amp, flat, fdet)
         specula_slopes(ctx, self.slopec, fdet, None, self.ref)
+        if self.noise:
+            # expected photo-electrons per unit of the image (it sums to the
+            # number of pupil pixels)
+            npup = float(specula_pupil_mask_host(self.pupil).sum())
+            self.noise_scale = self.noise["photons"] * self.noise.get("qe", 1.0) / npup
         torch.cuda.synchronize()
         self.tiles = None
         if autotune:
@@ -126,6 +140,8 @@ class PwfsFrame:
         """Set the frame time and launch the captured frame on `stream`."""
         torch = self.torch
         with torch.cuda.stream(stream):
+            if self.noise:
+                self.frame_dev.fill_(int(round(t / self.dt)))
             if self.batch == 1:
                 self.t_dev.fill_(t)
             else:
@@ -151,6 +167,12 @@ class PwfsFrame:
                                      stream=stream)
         specula_pwfs_image(ctx, self.pupil, self.pwfs, self.amp, self.phase, self.det,
                            stream=stream)
+        if self.noise:
+            # eager: frame index from t; captured: from self.frame_dev
+            k = 0 if t_dev is not None else int(round(t / self.dt))
+            specula_ccd(ctx, self.det, self.noise_scale, self.noise.get("ron", 0.0),
+                        self.noise.get("seed", 1), k, self.det,
+                        frame_dev=self.frame_dev if t_dev is not None else None, stream=stream)
         specula_slopes(ctx, self.slopec, self.det, self.ref, self.slopes, stream=stream)
         if self.learned is not None:
             self.learned.infer(self.slopes.view(self.batch, -1), self.modes.view(self.batch, -1),

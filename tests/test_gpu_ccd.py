@@ -1,6 +1,7 @@
-"""GPU parity of the detector noise against the FP64 oracle: photon counts
-bit-exact (both sides decide them in float64 from the same Philox words),
-the readout-noise sum within one float32 rounding."""
+"""GPU parity of the detector noise against the oracle: photon counts
+bit-exact (both sides decide them with the same IEEE operations on the same
+Philox words), the readout-noise sum within one float32 rounding plus the
+float32 readout normal's last-bit differences."""
 import numpy as np
 import pytest
 
@@ -53,7 +54,9 @@ def test_readout_noise_and_frames(env):
     assert torch.equal(a, b) and not torch.equal(a, c)
     ref = ccd.ccd_read(det.cpu().numpy(), 20.0, 3.0, 99, 4).astype(np.float64)
     got = a.cpu().numpy().astype(np.float64)
-    assert np.all(np.abs(got - ref) <= 2.0 ** -23 * np.abs(ref) + 1e-30)
+    # the readout normal is float32 on both sides (library log/sin may differ
+    # in the last bit): one float32 rounding of the sum plus ron x 1e-6
+    assert np.all(np.abs(got - ref) <= 2.0 ** -23 * np.abs(ref) + 3.0 * 1e-6)
     with pytest.raises(sp.SpeculaError):
         sp.specula_ccd(ctx, det, -1.0, 0.0, 1, 0, a)
 
@@ -70,3 +73,39 @@ def test_noise_statistics_on_the_gpu(env):
         k = out.cpu().numpy().astype(np.float64)
         assert abs(k.mean() - lam) < 5 * np.sqrt(lam / n)
         assert abs(k.var() - lam) < 5 * np.sqrt((lam + 2 * lam * lam) / n)
+
+
+def test_device_frame_index(env):
+    torch, sp, ctx = env
+    det = _det(torch, 33)
+    a, b = torch.empty_like(det), torch.empty_like(det)
+    fd = torch.tensor([3], dtype=torch.int32, device="cuda")
+    sp.specula_ccd(ctx, det, 20.0, 1.0, 5, 2, a, frame_dev=fd)
+    sp.specula_ccd(ctx, det, 20.0, 1.0, 5, 5, b)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+
+
+def test_noisy_frame_replay_matches_eager(env):
+    """The pyramid frame with detector noise: a graph replay at t = k dt draws
+    the noise of frame k, as the eager frame at that time does."""
+    torch, sp, ctx = env
+    import synth
+    from paper_2602_06688_gb300.frame import PwfsFrame
+    fr = PwfsFrame(ctx, synth.workload("pwfs8m_tiny"),
+                   noise={"photons": 1e5, "qe": 0.9, "ron": 1.0, "seed": 3})
+    st = torch.cuda.Stream()
+    fr.capture(st)
+    seen = []
+    for k in (1, 4):
+        fr.frame(k * fr.dt)
+        torch.cuda.synchronize()
+        eager = fr.slopes.clone()
+        fr.slopes.zero_()
+        torch.cuda.synchronize()
+        fr.replay(k * fr.dt, st)
+        torch.cuda.synchronize()
+        assert torch.equal(fr.slopes, eager)
+        seen.append(eager)
+    assert not torch.equal(seen[0], seen[1])
+    fr.graph.close()

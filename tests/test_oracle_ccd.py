@@ -46,3 +46,18 @@ def test_branch_switch_is_continuous_in_law():
     hi = np.array([ccd.poisson_count(30.1, p, 1, 5) for p in range(n)], dtype=np.float64)
     assert abs(lo.mean() - hi.mean()) < 0.2 + 5 * math.sqrt(2 * 30 / n)
     assert abs(lo.var() - hi.var()) < 5 * math.sqrt(2 * (30 + 2 * 900) / n)
+
+
+def test_exp_threshold_accuracy():
+    """The float32 threshold T(lambda/64)^64 against exp(-lambda): relative
+    error below 1e-5 over [0, 30] (it only shifts Poisson probabilities)."""
+    for lam in np.linspace(0.0, 30.0, 301):
+        v = float(ccd.exp_neg_f32(lam))
+        assert abs(v / math.exp(-lam) - 1.0) < 1e-5, lam
+
+
+def test_irwin_hall_moments():
+    g = np.array([ccd.irwin_hall(p, 2, 11, 0) for p in range(6000)])
+    assert abs(g.mean()) < 5 / math.sqrt(6000)
+    assert abs(g.var() - 1.0) < 5 * math.sqrt(2.0 / 6000)
+    assert np.abs(g).max() <= 6.0
