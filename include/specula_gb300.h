@@ -390,6 +390,21 @@ int specula_pwfs_image(specula_ctx *ctx, const specula_pupil_desc *pupil,
                        const float *phase_dev, int32_t n_batch, float *det_dev,
                        void *stream);
 
+/* Polychromatic pyramid image (PolyCromPyramid, App. A, Tab. 4): for n_batch
+ * phase maps in radians at the reference wavelength,
+ *   det = sum over i of weight[i] image_i,
+ * image_i the image above at lambda_i: phase times ratio[i] = lambda_ref /
+ * lambda_i and the modulation radius mod_amp ratio[i] (lambda_i / D); the
+ * pupil images' separation pup_dist is geometric and the same at every
+ * wavelength.  ratio, weight: n_lambda host doubles (1 <= n_lambda <= 64,
+ * ratio > 0).  Needs a plan for every wavelength: the descriptor with
+ * mod_amp = pwfs->mod_amp * ratio[i] (SPECULA_ENOPLAN else, checked before
+ * anything is enqueued).  Per-frame call: enqueues only. */
+int specula_pwfs_image_poly(specula_ctx *ctx, const specula_pupil_desc *pupil,
+                            const specula_pwfs_desc *pwfs, int32_t n_lambda, const double *ratio,
+                            const double *weight, const float *amp_dev, const float *phase_dev,
+                            int32_t n_batch, float *det_dev, void *stream);
+
 /* Build (or reuse) the tables of a Shack-Hartmann geometry and its valid
  * subaperture list (host rule above).  May allocate.  Supported fft_n: 24
  * with sub_pix 12, and 16 with sub_pix 8.  *n_valid receives the count. */

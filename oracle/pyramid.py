@@ -148,3 +148,16 @@ def pwfs_image_shifted(amp, phase, pad, n_mod, mod_amp, n_sub, pup_dist):
     Np = amp.shape[0]
     I = pwfs_intensity_shifted(amp, phase, pad, n_mod, mod_amp, pup_dist)
     return bin_image(I, Np // n_sub)
+
+
+def pwfs_image_poly(amp, phase, pad, n_mod, mod_amp, n_sub, pup_dist, ratios, weights):
+    """Polychromatic image (PolyCromPyramid, App. A, Tab. 4): the weighted sum
+    over wavelengths of the monochromatic image, phase and modulation radius
+    (in lambda / D) scaled by ratio = lambda_ref / lambda_i; the pupil
+    images' separation is geometric (the same at every wavelength).
+    Reading: the paper gives the object, not its model."""
+    det = None
+    for r, w in zip(ratios, weights):
+        d = w * pwfs_image(amp, phase * r, pad, n_mod, mod_amp * r, n_sub, pup_dist)
+        det = d if det is None else det + d
+    return det

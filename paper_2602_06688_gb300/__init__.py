@@ -400,6 +400,36 @@ def specula_pwfs_image(ctx, pupil, pwfs, amp, phase, det, stream=None):
         "specula_pwfs_image")
 
 
+def _pwfs_at(pwfs, ratio):
+    d = PwfsDesc(pwfs.pad, pwfs.n_mod, pwfs.n_sub, pwfs.pup_dist_px, pwfs.mod_amp * float(ratio))
+    return d
+
+
+def specula_pwfs_plan_poly(ctx, pupil, pwfs, ratios):
+    """Plans for every wavelength of a polychromatic image (set-up)."""
+    for r in ratios:
+        specula_pwfs_plan(ctx, pupil, _pwfs_at(pwfs, r))
+
+
+def specula_pwfs_image_poly(ctx, pupil, pwfs, ratios, weights, amp, phase, det, stream=None):
+    """det = sum_i weights[i] image(phase * ratios[i], mod_amp * ratios[i]);
+    ratios = lambda_ref / lambda_i."""
+    import torch
+    n = pupil.n_pix
+    nb = phase.numel() // (n * n)
+    side = 2 * pwfs.n_sub
+    r = np.ascontiguousarray(ratios, dtype=np.float64)
+    w = np.ascontiguousarray(weights, dtype=np.float64)
+    if r.shape != w.shape or r.ndim != 1:
+        raise ValueError("ratios and weights must be 1-D of equal length")
+    _abi.check(lib().specula_pwfs_image_poly(
+        ctx.handle, C.byref(pupil), C.byref(pwfs), int(r.size), r.ctypes.data_as(C.c_void_p),
+        w.ctypes.data_as(C.c_void_p), _dev(amp, torch.float32, n * n, "amp"),
+        _dev(phase, torch.float32, nb * n * n, "phase"), nb,
+        _dev(det, torch.float32, nb * side * side, "det"), _stream(stream)),
+        "specula_pwfs_image_poly")
+
+
 def specula_sh_plan(ctx, pupil, sh):
     nv = C.c_int32()
     _abi.check(lib().specula_sh_plan(ctx.handle, C.byref(pupil), C.byref(sh), C.byref(nv)),

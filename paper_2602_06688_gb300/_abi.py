@@ -98,6 +98,8 @@ SIGNATURES = {
     "specula_pwfs_plan": (C.c_int, [vp, P(PupilDesc), P(PwfsDesc)]),
     "specula_pwfs_set_tiles": (C.c_int, [vp, P(PupilDesc), P(PwfsDesc), i32, i32, i32]),
     "specula_pwfs_set_form": (C.c_int, [vp, P(PupilDesc), P(PwfsDesc), i32]),
+    "specula_pwfs_image_poly": (C.c_int, [vp, P(PupilDesc), P(PwfsDesc), i32, vp, vp, vp, vp, i32,
+                                          vp, vp]),
     "specula_dm_shape": (C.c_int, [vp, i32, i32, vp, vp, vp, vp]),
     "specula_ccd": (C.c_int, [vp, i32, vp, C.c_double, C.c_double, C.c_uint64, C.c_uint32, vp,
                               vp, vp]),

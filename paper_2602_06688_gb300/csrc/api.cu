@@ -501,6 +501,41 @@ extern "C" int specula_pwfs_image(specula_ctx *ctx, const specula_pupil_desc *pu
   return pwfs_run(ctx, p, amp_dev, phase_dev, n_batch, det_dev, (cudaStream_t)stream);
 }
 
+extern "C" int specula_pwfs_image_poly(specula_ctx *ctx, const specula_pupil_desc *pupil,
+                                       const specula_pwfs_desc *pwfs, int32_t n_lambda,
+                                       const double *ratio, const double *weight,
+                                       const float *amp_dev, const float *phase_dev,
+                                       int32_t n_batch, float *det_dev, void *stream) {
+  if (!ctx || !amp_dev || !phase_dev || !det_dev || !ratio || !weight || n_batch < 0)
+    return SPECULA_EINVAL;
+  if (n_lambda < 1 || n_lambda > 64) return SPECULA_EINVAL;
+  int s = check_pwfs(pupil, pwfs);
+  if (s) return s;
+  // every wavelength's plan first (mod_amp in its own lambda / D), so that a
+  // missing one fails before anything is enqueued
+  PwfsPlan *plans[64];
+  for (int i = 0; i < n_lambda; ++i) {
+    if (!(ratio[i] > 0.0) || !isfinite(ratio[i]) || !isfinite(weight[i])) return SPECULA_EINVAL;
+    specula_pwfs_desc d = *pwfs;
+    d.mod_amp = pwfs->mod_amp * ratio[i];
+    if ((s = check_pwfs(pupil, &d))) return s;
+    if (!(plans[i] = pwfs_plan_find(ctx, pupil, &d))) return SPECULA_ENOPLAN;
+  }
+  if (n_batch == 0) return SPECULA_OK;
+  for (int i = 0; i < n_lambda; ++i) {
+    PwfsPlan *p = plans[i];
+    p->run_phase_scale = (float)ratio[i];
+    p->run_alpha = (float)weight[i];
+    p->run_beta = i == 0 ? 0.f : 1.f;
+    s = pwfs_run(ctx, p, amp_dev, phase_dev, n_batch, det_dev, (cudaStream_t)stream);
+    p->run_phase_scale = 1.f;
+    p->run_alpha = 1.f;
+    p->run_beta = 0.f;
+    if (s) return s;
+  }
+  return SPECULA_OK;
+}
+
 static int check_sh(const specula_pupil_desc *pupil, const specula_sh_desc *sh) {
   int s = check_pupil(pupil);
   if (s) return s;

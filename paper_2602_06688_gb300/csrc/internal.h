@@ -78,6 +78,10 @@ struct PwfsPlan {
   DevBuf rows;          // [chunk][n_pix][N] float2: after the row transform
   DevBuf cols;          // [chunk][N][N] float2: after the column pass (three-pass form)
   DevBuf part;          // [chunk][nd][nd] float: binned intensity per item
+  // per-call settings of the polychromatic image (defaults: a plain image):
+  // the phase is multiplied by run_phase_scale and the detector becomes
+  // run_beta det + run_alpha image
+  float run_phase_scale = 1.f, run_alpha = 1.f, run_beta = 0.f;
   // shifted-mask form (SPECULA_PWFS_FORM_SHIFTED)
   int form = 0;
   int sm_blockK = 0, sm_chunk = 0;
@@ -156,7 +160,7 @@ int pwfs_shifted_prepare(PwfsPlan *p);
 int pwfs_shifted_run(specula_ctx *ctx, PwfsPlan *p, const float *amp, const float *phase,
                      int n_batch, float *det, cudaStream_t st);
 int pwfs_bin_reduce(specula_ctx *ctx, const float *part, float *det, int nd2, int n_mod,
-                    cudaStream_t st);
+                    float alpha, float beta, cudaStream_t st);
 int atmo_alloc_tables(specula_ctx *ctx);
 
 // launchers implemented in the kernel translation units

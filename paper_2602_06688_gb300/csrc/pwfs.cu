@@ -64,12 +64,12 @@ __device__ __forceinline__ void cp_async_wait_all() {
 __global__ void __launch_bounds__(256) k_field(const float *__restrict__ amp,
                                                const float *__restrict__ phase,
                                                float2 *__restrict__ field, int npix2, int b0,
-                                               int nbw) {
+                                               int nbw, float phase_scale) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= npix2) return;
   const int b = b0 + blockIdx.y;
   float sv, cv;
-  sincosf(phase[(size_t)b * npix2 + e], &sv, &cv);
+  sincosf(phase[(size_t)b * npix2 + e] * phase_scale, &sv, &cv);
   const float a = amp[e];
   field[(size_t)(b % nbw) * npix2 + e] = make_float2(a * cv, a * sv);
 }
@@ -531,7 +531,7 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 160 ? 4 : 3) k_colfilt_bin(
 // grid (ceil(nd^2 / 256), number of batch elements from b0).
 __global__ void __launch_bounds__(256) k_bin_reduce(const float *__restrict__ part,
                                                     float *__restrict__ det, int nd2, int n_mod,
-                                                    int nbw, int b0) {
+                                                    int nbw, int b0, float alpha, float beta) {
   const int pix = blockIdx.x * blockDim.x + threadIdx.x;
   if (pix >= nd2) return;
   const int b = b0 + blockIdx.y;
@@ -547,7 +547,9 @@ __global__ void __launch_bounds__(256) k_bin_reduce(const float *__restrict__ pa
     for (int u = 0; u < 16; ++u) v += x[u];
   }
   for (; m < n_mod; ++m) v += src[(size_t)m * nd2];
-  det[(size_t)b * nd2 + pix] = v;
+  // det = alpha v (beta = 0) or beta det + alpha v (accumulating images)
+  float *d = det + (size_t)b * nd2 + pix;
+  *d = beta == 0.f ? alpha * v : beta * *d + alpha * v;
 }
 
 // --------------------------------------------------------------------------
@@ -625,7 +627,7 @@ static int run_split2(specula_ctx *ctx, PwfsPlan *p, const float *amp, const flo
       dim3 gF((Np * Np + 255) / 256, b1 - fb + 1);
       SPECULA_LAUNCH(ctx, SPECULA_K_PWFS_FIELD, st,
                      k_field<<<gF, 256, 0, st>>>(amp, phase, p->field.as<float2>(), Np * Np, fb,
-                                                 p->nbw));
+                                                 p->nbw, p->run_phase_scale));
       field_done = b1;
     }
     dim3 gR((Np + vpc - 1) / vpc, (nj + p->ka - 1) / p->ka);
@@ -652,7 +654,8 @@ static int run_split2(specula_ctx *ctx, PwfsPlan *p, const float *amp, const flo
       dim3 gD((nd * nd + 255) / 256, complete - det_done);
       SPECULA_LAUNCH(ctx, SPECULA_K_PWFS_BIN, st,
                      k_bin_reduce<<<gD, 256, 0, st>>>(p->part.as<float>(), det, nd * nd,
-                                                      p->n_mod, p->nbw, det_done + 1));
+                                                      p->n_mod, p->nbw, det_done + 1,
+                                                      p->run_alpha, p->run_beta));
       det_done = complete;
     }
   }
@@ -680,7 +683,7 @@ static int run_split(specula_ctx *ctx, PwfsPlan *p, const float *amp, const floa
       dim3 gF((Np * Np + 255) / 256, b1 - fb + 1);
       SPECULA_LAUNCH(ctx, SPECULA_K_PWFS_FIELD, st,
                      k_field<<<gF, 256, 0, st>>>(amp, phase, p->field.as<float2>(), Np * Np, fb,
-                                                 p->nbw));
+                                                 p->nbw, p->run_phase_scale));
       field_done = b1;
     }
     dim3 gA((Np + vpcA - 1) / vpcA, (ni + p->ka - 1) / p->ka);
@@ -707,7 +710,8 @@ static int run_split(specula_ctx *ctx, PwfsPlan *p, const float *amp, const floa
       dim3 gD((nd * nd + 255) / 256, complete - det_done);
       SPECULA_LAUNCH(ctx, SPECULA_K_PWFS_BIN, st,
                      k_bin_reduce<<<gD, 256, 0, st>>>(p->part.as<float>(), det, nd * nd,
-                                                      p->n_mod, p->nbw, det_done + 1));
+                                                      p->n_mod, p->nbw, det_done + 1,
+                                                      p->run_alpha, p->run_beta));
       det_done = complete;
     }
   }
@@ -756,10 +760,10 @@ int pwfs_set_tiles(PwfsPlan *p, int chunk, int ka, int passes) {
 }
 
 int pwfs_bin_reduce(specula_ctx *ctx, const float *part, float *det, int nd2, int n_mod,
-                    cudaStream_t st) {
+                    float alpha, float beta, cudaStream_t st) {
   SPECULA_LAUNCH(ctx, SPECULA_K_PWFS_BIN, st,
                  k_bin_reduce<<<dim3((nd2 + 255) / 256, 1), 256, 0, st>>>(part, det, nd2, n_mod,
-                                                                          1, 0));
+                                                                          1, 0, alpha, beta));
   return SPECULA_OK;
 }
 

@@ -67,7 +67,8 @@ __global__ void __launch_bounds__(256) k_sm_fwd_rows(const float *__restrict__ a
                                                      const float *__restrict__ phase,
                                                      const float2 *__restrict__ pre,
                                                      const float2 *__restrict__ twA,
-                                                     float2 *__restrict__ frows, int n_pix) {
+                                                     float2 *__restrict__ frows, int n_pix,
+                                                     float phase_scale) {
   using S = Split<N1, N2>;
   constexpr int N = S::N, G = S::G, S1 = S::S1;
   constexpr int Q0 = N2 / 4, QH = N2 / 2;
@@ -85,7 +86,7 @@ __global__ void __launch_bounds__(256) k_sm_fwd_rows(const float *__restrict__ a
     for (int h = 0; h < QH; ++h) {
       const int i = lane + N1 * h;                      // pupil column
       float sv, cv;
-      sincosf(phase[(size_t)j * n_pix + i], &sv, &cv);
+      sincosf(phase[(size_t)j * n_pix + i] * phase_scale, &sv, &cv);
       const float a = amp[(size_t)j * n_pix + i];
       r[Q0 + h] = cmul(make_float2(a * cv, a * sv), __ldg(pre + i));
     }
@@ -366,7 +367,7 @@ int sm_run(specula_ctx *ctx, PwfsPlan *p, const float *amp, const float *phase, 
     SPECULA_LAUNCH(ctx, SPECULA_K_PWFS_SM_FWD, st,
                    k_sm_fwd_rows<N1, N2><<<(Np + vpc - 1) / vpc, 256, p->sm_smemR, st>>>(
                        amp, phase + (size_t)b * Np * Np, p->sm_pre.as<float2>(),
-                       p->twA.as<float2>(), p->sm_frows.as<float2>(), Np));
+                       p->twA.as<float2>(), p->sm_frows.as<float2>(), Np, p->run_phase_scale));
     SPECULA_LAUNCH(ctx, SPECULA_K_PWFS_SM_FWD, st,
                    k_sm_fwd_cols<N1, N2><<<N / kSmFwdColsTC, kSmFwdColsTC * G, p->sm_smemC, st>>>(
                        p->sm_frows.as<float2>(), p->sm_pre.as<float2>(), p->twA.as<float2>(),
@@ -390,7 +391,7 @@ int sm_run(specula_ctx *ctx, PwfsPlan *p, const float *amp, const float *phase, 
                            p->sm_part.as<float>(), bsz, scale, p->n_mod, j0));
     }
     int s = pwfs_bin_reduce(ctx, p->sm_part.as<float>(), det + (size_t)b * nd * nd, nd * nd,
-                            p->n_mod, st);
+                            p->n_mod, p->run_alpha, p->run_beta, st);
     if (s) return s;
   }
   return SPECULA_OK;

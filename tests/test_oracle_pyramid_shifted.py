@@ -96,3 +96,21 @@ def test_flat_wavefront_mirror_symmetry_shifted():
     assert np.allclose(q, amp.sum() / 4, rtol=1e-12)
     assert np.allclose(I, I[:, ::-1], atol=1e-13)
     assert np.allclose(I, I[::-1, :], atol=1e-13)
+
+
+def test_polychromatic_image_pins():
+    """One wavelength at the reference is the monochromatic image; the flux is
+    the weighted pupil count; flat-wavefront images stay mirror-symmetric."""
+    amp, phi = _pupil_field(8)
+    mono = pyramid.pwfs_image(amp, phi, 2, 8, 2.5, 8, NP)
+    one = pyramid.pwfs_image_poly(amp, phi, 2, 8, 2.5, 8, NP, [1.0], [1.0])
+    assert np.array_equal(one, mono)
+    r, w = [1.25, 1.0, 0.8], [0.2, 0.5, 0.3]
+    det = pyramid.pwfs_image_poly(amp, phi, 2, 8, 2.5, 8, NP, r, w)
+    assert abs(det.sum() - amp.sum() * sum(w)) < 1e-12 * amp.sum()
+    flat = pyramid.pwfs_image_poly(amp, np.zeros_like(phi), 2, 8, 2.5, 8, NP, r, w)
+    assert np.allclose(flat, flat[:, ::-1], atol=1e-13) and np.allclose(flat, flat[::-1], atol=1e-13)
+    # a longer wavelength sees a smaller phase: ratio 0 would be a flat wavefront
+    d0 = pyramid.pwfs_image_poly(amp, phi, 2, 8, 2.5, 8, NP, [1e-12], [1.0])
+    ref = pyramid.pwfs_image(amp, np.zeros_like(phi), 2, 8, 2.5e-12, 8, NP)
+    assert np.max(np.abs(d0 - ref)) < 1e-9
