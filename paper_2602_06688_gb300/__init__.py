@@ -702,8 +702,10 @@ def specula_pinv_fp64(ctx, A, rcond, R, R32=None, stream=None):
 def slopec_desc(kind, n_sub, idx_dev, fft_n=0):
     import torch
     _dev(idx_dev, torch.int32, None, "subap_idx")
-    return SlopecDesc(int(kind), int(n_sub), int(idx_dev.numel()), int(fft_n),
-                      C.c_void_p(idx_dev.data_ptr()))
+    d = SlopecDesc(int(kind), int(n_sub), int(idx_dev.numel()), int(fft_n),
+                   C.c_void_p(idx_dev.data_ptr()))
+    d._keep = (idx_dev,)          # the descriptor holds a raw pointer: keep the tensor alive
+    return d
 
 
 def recon_desc(n_modes, n_slopes, precision, R_dev, R_lo_dev=None):
@@ -717,8 +719,10 @@ def recon_desc(n_modes, n_slopes, precision, R_dev, R_lo_dev=None):
         if not ok or not t.is_cuda or not t.is_contiguous() or t.numel() < n_modes * n_slopes:
             raise ValueError(f"reconstructor tensor must be a contiguous CUDA tensor of "
                              f"{n_modes}x{n_slopes} {want}, got {t.dtype} {tuple(t.shape)}")
-    return ReconDesc(int(n_modes), int(n_slopes), int(precision), C.c_void_p(R_dev.data_ptr()),
-                     C.c_void_p(R_lo_dev.data_ptr()) if R_lo_dev is not None else None)
+    d = ReconDesc(int(n_modes), int(n_slopes), int(precision), C.c_void_p(R_dev.data_ptr()),
+                  C.c_void_p(R_lo_dev.data_ptr()) if R_lo_dev is not None else None)
+    d._keep = (R_dev, R_lo_dev)   # the descriptor holds raw pointers: keep the tensors alive
+    return d
 
 
 # ---- multi-sensor system in one persistent launch -----------------------------------
