@@ -79,6 +79,49 @@ __global__ void __launch_bounds__(kReconWarps * 32) k_mvm_f32(
   }
 }
 
+// FP32, one slope vector, one row per CTA of kSplitWarps warps: warp w streams
+// the w-th contiguous segment of the row (UL 16-byte loads in flight per
+// lane), then the warps' sums are added in warp order.  Four streams per row
+// keep more bytes in flight per row than one warp does.
+constexpr int kSplitWarps = 4;
+__global__ void __launch_bounds__(kSplitWarps * 32) k_mvm_f32_split(
+    const float *__restrict__ R, const float *__restrict__ s, float *__restrict__ m, int n_modes,
+    int n_slopes) {
+  __shared__ float s_w[kSplitWarps];
+  const int row = blockIdx.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const float4 *r4 = reinterpret_cast<const float4 *>(R + (size_t)row * n_slopes);
+  const float4 *s4 = reinterpret_cast<const float4 *>(s);
+  const int n4 = n_slopes / 4;
+  const int seg = (n4 + kSplitWarps - 1) / kSplitWarps;
+  const int lo = warp * seg, hi = min(n4, lo + seg);
+  constexpr int UL = 4;
+  float acc = 0.f;
+  for (int j0 = lo + lane; j0 < hi; j0 += UL * 32) {
+    float4 a[UL];
+#pragma unroll
+    for (int u = 0; u < UL; ++u)
+      a[u] = (j0 + 32 * u < hi) ? ld_stream(r4 + j0 + 32 * u) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int u = 0; u < UL; ++u) {
+      const int j = j0 + 32 * u;
+      if (j < hi) {
+        const float4 x = __ldg(s4 + j);
+        acc += a[u].x * x.x + a[u].y * x.y + a[u].z * x.z + a[u].w * x.w;
+      }
+    }
+  }
+  acc = warp_sum_r(acc);
+  if (lane == 0) s_w[warp] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float v = 0.f;
+#pragma unroll
+    for (int w = 0; w < kSplitWarps; ++w) v += s_w[w];
+    m[row] = v;
+  }
+}
+
 // FP32, scalar fallback for unaligned sizes.
 __global__ void __launch_bounds__(kReconWarps * 32) k_mvm_f32_scalar(
     const float *__restrict__ R, const float *__restrict__ s, float *__restrict__ m, int n_modes,
@@ -182,7 +225,12 @@ extern "C" int specula_recon(specula_ctx *ctx, const specula_recon_desc *rec,
     case SPECULA_PREC_FP32:
       if (rec->n_slopes % 4 == 0 && al16) {
         for (int b0 = 0; b0 < n_batch; b0 += NB) {
-          if (n_batch - b0 == 1)
+          if (n_batch == 1)
+            SPECULA_LAUNCH(ctx, SPECULA_K_RECON, st,
+                           k_mvm_f32_split<<<grid1, kSplitWarps * 32, 0, st>>>(
+                               (const float *)rec->R_dev, slopes_dev, modes_dev, rec->n_modes,
+                               rec->n_slopes));
+          else if (n_batch - b0 == 1)
             SPECULA_LAUNCH(ctx, SPECULA_K_RECON, st, k_mvm_f32<1><<<grid1, blk1, 0, st>>>((const float *)rec->R_dev, slopes_dev, modes_dev,
                                                rec->n_modes, rec->n_slopes, n_batch, b0));
           else
