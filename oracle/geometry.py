@@ -80,3 +80,36 @@ def mod_angles(n_mod: int):
         c[m] = math.cos(th)
         s[m] = math.sin(th)
     return c, s
+
+
+def pyr_image_index(valid: np.ndarray, n_sub: int, pad: int, pup_dist: int,
+                    n_pix: int) -> np.ndarray:
+    """Detector linear indices of the four pupil images of each subaperture
+    for any padding and image separation (the SOUL example's ``pup_diam`` /
+    ``pup_dist`` / ``output_resolution``, App. B, Listing 2).
+
+    The padded grid (pad n_pix) is binned in b x b blocks, b = n_pix / n_sub,
+    to an n_det = pad n_sub detector.  The four images, n_sub detector pixels
+    wide, are centred d = pup_dist / (2 b) detector pixels from the detector
+    centre along +-x and +-y (face (+x, +y) to larger row and column);
+    subaperture (a, c) of image Q sits at row r0_Q + a, column c0_Q + c with
+        r0 = n_det / 2 + sy d - n_sub / 2,  c0 = n_det / 2 + sx d - n_sub / 2,
+    (sx, sy) = (+,+) Q1, (-,+) Q2, (-,-) Q3, (+,-) Q4.  Needs integer image
+    corners (pup_dist a multiple of b and pup_dist / b - n_sub even); returns
+    a (4, n_valid) int64 array.  With pad 2 and pup_dist = n_pix it is
+    ``pyr_quadrant_index``.
+    """
+    b = n_pix // n_sub
+    assert n_pix % n_sub == 0 and pup_dist % b == 0
+    n_det = pad * n_sub
+    two_d = pup_dist // b
+    assert (two_d - n_sub) % 2 == 0 and n_det % 2 == 0
+    a = valid // n_sub
+    c = valid % n_sub
+    out = []
+    for sx, sy in ((1, 1), (-1, 1), (-1, -1), (1, -1)):
+        r0 = (n_det + sy * two_d - n_sub) // 2
+        c0 = (n_det + sx * two_d - n_sub) // 2
+        assert 0 <= r0 and r0 + n_sub <= n_det and 0 <= c0 and c0 + n_sub <= n_det
+        out.append((r0 + a).astype(np.int64) * n_det + (c0 + c))
+    return np.stack(out)

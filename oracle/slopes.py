@@ -31,6 +31,16 @@ def pyr_slopes(det: np.ndarray, n_sub: int, valid: np.ndarray,
     return s
 
 
+def pyr_slopes_maps(det: np.ndarray, maps: np.ndarray, ref=None) -> np.ndarray:
+    """The same slopes from explicit detector indices of the four pupil
+    images (``geometry.pyr_image_index``): maps[0..3] = Q1..Q4."""
+    d = det.ravel()
+    q1, q2, q3, q4 = (d[maps[i]] for i in range(4))
+    T = np.mean(q1 + q2 + q3 + q4)
+    s = np.concatenate([((q1 + q4) - (q2 + q3)) / T, ((q1 + q2) - (q3 + q4)) / T])
+    return s - ref if ref is not None else s
+
+
 def sh_slopes(spots: np.ndarray, ref=None) -> np.ndarray:
     """Centre-of-gravity slopes in pixels over the whole n x n window:
     Sx = sum x I / sum I, Sy = sum y I / sum I with x = j - (n-1)/2 (no
