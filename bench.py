@@ -470,6 +470,18 @@ def systems_leg(ctx, steps=50):
                       "recon_variants": res, "batched_fp32": batched("pwfs8m", 16)}
     del fr
     out["pwfs39m_batched_fp32"] = batched("pwfs39m", 8)
+    # the paper's SOUL example geometry: 40 x 40 subapertures, images 48 px
+    # apart on a 120 px detector (80 px pupil padded three times, 2 x 2 bins)
+    ws = synth.workload("soul8m")
+    fs = PwfsFrame(ctx, ws)
+    gs = fs.capture(st)
+    time_graph(gs, lambda k: fs.t_dev.fill_(ws.dt_s * k), 5)
+    mss = time_graph(gs, lambda k: fs.t_dev.fill_(ws.dt_s * k), steps)
+    out["soul8m"] = {"config": "8.2 m, 80 px pupil padded 3x (240^2 FFT), 16 mod points, "
+                               "40x40 subaps, images 48 px apart on a 120 px detector, "
+                               "%d modes, FP32" % fs.n_modes,
+                     "frames_per_s": steps / (sum(mss) / 1e3), "ms_per_step": sum(mss) / steps}
+    gs.close()
     wl = synth.workload("mwfs39m")
     S = System(ctx, wl)
     res = {}

@@ -100,15 +100,20 @@ typedef struct {
   int32_t n_sub, sub_pix, fft_n;
 } specula_sh_desc;
 
-#define SPECULA_SLOPES_PYR 0
-#define SPECULA_SLOPES_SH  1
+#define SPECULA_SLOPES_PYR      0
+#define SPECULA_SLOPES_SH       1
+#define SPECULA_SLOPES_PYR_MAPS 2
 
 /* Slope computer (PyrSlopec / ShSlopec, App. A, Tab. 4).  subap_idx_dev lists
  * the valid subapertures as a * n_sub + b (row a, column b), ascending; for
- * SH, the image holds one fft_n^2 spot per listed subaperture. */
+ * SH, the image holds one fft_n^2 spot per listed subaperture.  For
+ * PYR_MAPS, subap_idx_dev holds 4 n_valid detector linear indices (the
+ * subapertures' pixels in images Q1, Q2, Q3, Q4, one block each; see
+ * specula_pyr_image_index_host) and n_sub is the detector side. */
 typedef struct {
-  int32_t kind;            /* SPECULA_SLOPES_PYR or SPECULA_SLOPES_SH  */
-  int32_t n_sub;           /* subapertures across one pupil image       */
+  int32_t kind;            /* SPECULA_SLOPES_PYR, _SH or _PYR_MAPS      */
+  int32_t n_sub;           /* subapertures across one pupil image (PYR,
+                              SH); detector side (PYR_MAPS)             */
   int32_t n_valid;         /* entries of subap_idx_dev                  */
   int32_t fft_n;           /* SH spot side (ignored for PYR)            */
   const int32_t *subap_idx_dev;
@@ -222,6 +227,24 @@ int specula_pupil_mask_host(const specula_pupil_desc *pupil, uint8_t *mask_host)
  * n_sub^2) and their count to *n_valid. */
 int specula_valid_subaps_host(const specula_pupil_desc *pupil, int32_t n_sub,
                               int32_t *idx_host, int32_t *n_valid);
+
+/* Detector indices of the four pupil images of each valid subaperture for
+ * any padding and image separation (PyrPupdataCalibrator; the SOUL example's
+ * pup_diam / pup_dist / output_resolution, App. B, Listing 2).  The padded
+ * grid (pad n_pix) binned in b x b blocks (b = n_pix / n_sub) is an n_det =
+ * pad n_sub detector; image Q, n_sub pixels wide, is centred
+ * d = pup_dist_px / (2 b) pixels from the detector centre along (sx, sy) =
+ * (+,+) Q1, (-,+) Q2, (-,-) Q3, (+,-) Q4 (face (+x, +y) to larger row and
+ * column); subaperture (a, c) of image Q is at row n_det/2 + sy d - n_sub/2
+ * + a, column n_det/2 + sx d - n_sub/2 + c.  Writes 4 n_valid indices (Q1
+ * block first) to idx_host (capacity 4 n_sub^2) and *n_valid.
+ * SPECULA_EUNSUPPORTED unless the image corners are whole detector pixels
+ * (pup_dist_px a multiple of b, pup_dist_px / b - n_sub and n_det even) and
+ * the images lie on the detector.  With pad 2 and pup_dist_px = n_pix the
+ * blocks are the quadrant layout of SPECULA_SLOPES_PYR. */
+int specula_pyr_image_index_host(const specula_pupil_desc *pupil, int32_t pad,
+                                 int32_t pup_dist_px, int32_t n_sub, int32_t *idx_host,
+                                 int32_t *n_valid);
 
 /* Modulation points (ModulatedPyramid `mod_amp`): theta_m = (2 pi m) / n_mod,
  * m = 0..n_mod-1, counter-clockwise from +x; writes cos/sin in float64. */
@@ -427,6 +450,9 @@ int specula_sh_image(specula_ctx *ctx, const specula_pupil_desc *pupil,
  *   (a, b), Q4 (+x,-y) at (a, n_sub + b):
  *   Sx = ((Q1 + Q4) - (Q2 + Q3)) / T, Sy = ((Q1 + Q2) - (Q3 + Q4)) / T,
  *   T = mean over the listed subapertures of Q1 + Q2 + Q3 + Q4.
+ *  PYR_MAPS: the same slopes with Q1..Q4 read at the listed detector
+ *   indices (any padding and image separation); an index outside the
+ *   n_sub x n_sub detector reads pixel 0 and records SPECULA_EINVAL.
  *  SH: img holds n_valid spots of fft_n^2; centre of gravity over the whole
  *   window, x = j - (fft_n - 1)/2 pixels.
  * ref_dev (nullable): 2 * n_valid reference slopes subtracted from each

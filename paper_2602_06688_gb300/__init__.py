@@ -14,7 +14,7 @@ import numpy as np
 from . import _abi
 from ._abi import (  # noqa: F401
     PupilDesc, SourceDesc, LayerDesc, PwfsDesc, ShDesc, SlopecDesc, ReconDesc, WfsDesc,
-    SpeculaError, SLOPES_PYR, SLOPES_SH, PWFS_FORM_TILT, PWFS_FORM_SHIFTED, PREC_FP32, PREC_BF16,
+    SpeculaError, SLOPES_PYR, SLOPES_SH, SLOPES_PYR_MAPS, PWFS_FORM_TILT, PWFS_FORM_SHIFTED, PREC_FP32, PREC_BF16,
     PREC_BF16X2,
     OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED, ENONFINITE, ENOPLAN,
 )
@@ -240,6 +240,17 @@ def specula_valid_subaps_host(pupil, n_sub):
     return idx[:nv.value].copy()
 
 
+def specula_pyr_image_index_host(pupil, pad, pup_dist_px, n_sub):
+    """(4, n_valid) int32 detector indices of the four pupil images of each
+    valid subaperture (Q1..Q4) on the pad n_sub detector."""
+    buf = np.zeros(4 * n_sub * n_sub, dtype=np.int32)
+    nv = C.c_int32()
+    _abi.check(lib().specula_pyr_image_index_host(C.byref(pupil), int(pad), int(pup_dist_px),
+                                                  int(n_sub), buf.ctypes.data_as(C.c_void_p),
+                                                  C.byref(nv)), "specula_pyr_image_index_host")
+    return buf[:4 * nv.value].reshape(4, nv.value).copy()
+
+
 def specula_mod_table_host(n_mod):
     c = np.zeros(n_mod)
     s = np.zeros(n_mod)
@@ -377,7 +388,7 @@ def specula_pwfs_autotune(ctx, pupil, pwfs, amp, phase, det, reps=3,
     import torch
     n = pupil.n_pix
     nb = phase.numel() // (n * n)
-    side = 2 * pwfs.n_sub
+    side = pwfs.pad * pwfs.n_sub
     ch, ka, ps = C.c_int32(), C.c_int32(), C.c_int32()
     _abi.check(lib().specula_pwfs_autotune(
         ctx.handle, C.byref(pupil), C.byref(pwfs), _dev(amp, torch.float32, n * n, "amp"),
@@ -392,7 +403,7 @@ def specula_pwfs_image(ctx, pupil, pwfs, amp, phase, det, stream=None):
     import torch
     n = pupil.n_pix
     nb = phase.numel() // (n * n)
-    side = 2 * pwfs.n_sub
+    side = pwfs.pad * pwfs.n_sub
     _abi.check(lib().specula_pwfs_image(
         ctx.handle, C.byref(pupil), C.byref(pwfs), _dev(amp, torch.float32, n * n, "amp"),
         _dev(phase, torch.float32, nb * n * n, "phase"), nb,
@@ -417,7 +428,7 @@ def specula_pwfs_image_poly(ctx, pupil, pwfs, ratios, weights, amp, phase, det, 
     import torch
     n = pupil.n_pix
     nb = phase.numel() // (n * n)
-    side = 2 * pwfs.n_sub
+    side = pwfs.pad * pwfs.n_sub
     r = np.ascontiguousarray(ratios, dtype=np.float64)
     w = np.ascontiguousarray(weights, dtype=np.float64)
     if r.shape != w.shape or r.ndim != 1:
@@ -702,8 +713,8 @@ def specula_pinv_fp64(ctx, A, rcond, R, R32=None, stream=None):
 def slopec_desc(kind, n_sub, idx_dev, fft_n=0):
     import torch
     _dev(idx_dev, torch.int32, None, "subap_idx")
-    d = SlopecDesc(int(kind), int(n_sub), int(idx_dev.numel()), int(fft_n),
-                   C.c_void_p(idx_dev.data_ptr()))
+    nv = idx_dev.numel() // 4 if kind == SLOPES_PYR_MAPS else idx_dev.numel()
+    d = SlopecDesc(int(kind), int(n_sub), int(nv), int(fft_n), C.c_void_p(idx_dev.data_ptr()))
     d._keep = (idx_dev,)          # the descriptor holds a raw pointer: keep the tensor alive
     return d
 

@@ -11,7 +11,7 @@ LIB_PATH = os.path.join(HERE, "libspecula_gb300.so")
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED, ENONFINITE, ENOPLAN = \
     0, -1, -2, -3, -4, -5, -6, -7
-SLOPES_PYR, SLOPES_SH = 0, 1
+SLOPES_PYR, SLOPES_SH, SLOPES_PYR_MAPS = 0, 1, 2
 PWFS_FORM_TILT, PWFS_FORM_SHIFTED = 0, 1
 PREC_FP32, PREC_BF16, PREC_BF16X2 = 0, 1, 2
 
@@ -98,6 +98,7 @@ SIGNATURES = {
     "specula_pwfs_plan": (C.c_int, [vp, P(PupilDesc), P(PwfsDesc)]),
     "specula_pwfs_set_tiles": (C.c_int, [vp, P(PupilDesc), P(PwfsDesc), i32, i32, i32]),
     "specula_pwfs_set_form": (C.c_int, [vp, P(PupilDesc), P(PwfsDesc), i32]),
+    "specula_pyr_image_index_host": (C.c_int, [P(PupilDesc), i32, i32, i32, vp, P(i32)]),
     "specula_pwfs_image_poly": (C.c_int, [vp, P(PupilDesc), P(PwfsDesc), i32, vp, vp, vp, vp, i32,
                                           vp, vp]),
     "specula_dm_shape": (C.c_int, [vp, i32, i32, vp, vp, vp, vp]),

@@ -9,6 +9,8 @@
 #include <new>
 #include <utility>
 
+#include <vector>
+
 #include "internal.h"
 
 using namespace specula;
@@ -306,6 +308,32 @@ extern "C" int specula_valid_subaps_host(const specula_pupil_desc *pupil, int32_
   return host_valid_subaps(pupil->n_pix, pupil->obsc_frac, n_sub, idx_host, n_valid);
 }
 
+extern "C" int specula_pyr_image_index_host(const specula_pupil_desc *pupil, int32_t pad,
+                                            int32_t pup_dist_px, int32_t n_sub,
+                                            int32_t *idx_host, int32_t *n_valid) {
+  int s = check_pupil(pupil);
+  if (s) return s;
+  if (!idx_host || !n_valid || n_sub < 1 || pad < 1 || pupil->n_pix % n_sub) return SPECULA_EINVAL;
+  const int b = pupil->n_pix / n_sub, n_det = pad * n_sub;
+  if (pup_dist_px < 0 || pup_dist_px % b) return SPECULA_EUNSUPPORTED;
+  const int two_d = pup_dist_px / b;
+  if ((two_d - n_sub) % 2 || n_det % 2) return SPECULA_EUNSUPPORTED;
+  std::vector<int32_t> valid((size_t)n_sub * n_sub);
+  int32_t nv = 0;
+  if ((s = host_valid_subaps(pupil->n_pix, pupil->obsc_frac, n_sub, valid.data(), &nv))) return s;
+  const int sxs[4] = {1, -1, -1, 1}, sys[4] = {1, 1, -1, -1};
+  for (int q = 0; q < 4; ++q) {
+    const int r0 = (n_det + sys[q] * two_d - n_sub) / 2, c0 = (n_det + sxs[q] * two_d - n_sub) / 2;
+    if (r0 < 0 || r0 + n_sub > n_det || c0 < 0 || c0 + n_sub > n_det) return SPECULA_EUNSUPPORTED;
+    for (int k = 0; k < nv; ++k) {
+      const int a = valid[k] / n_sub, c = valid[k] % n_sub;
+      idx_host[(size_t)q * nv + k] = (r0 + a) * n_det + (c0 + c);
+    }
+  }
+  *n_valid = nv;
+  return SPECULA_OK;
+}
+
 extern "C" int specula_mod_table_host(int32_t n_mod, double *cos_host, double *sin_host) {
   if (n_mod < 1 || !cos_host || !sin_host) return SPECULA_EINVAL;
   for (int m = 0; m < n_mod; ++m) {
@@ -404,7 +432,11 @@ static int check_pwfs(const specula_pupil_desc *pupil, const specula_pwfs_desc *
   if (p->pad < 1 || p->n_mod < 1 || p->n_mod > 4096 || p->n_sub < 1) return SPECULA_EINVAL;
   if (pupil->n_pix % p->n_sub) return SPECULA_EINVAL;
   if (!(p->mod_amp >= 0.0) || !isfinite(p->mod_amp)) return SPECULA_EINVAL;
-  if (p->pad != 2 || p->pup_dist_px != pupil->n_pix) return SPECULA_EUNSUPPORTED;
+  // padding 2-4; the four pupil images (n_pix wide, centres pup_dist apart)
+  // inside the padded grid
+  if (p->pad < 2 || p->pad > 4) return SPECULA_EUNSUPPORTED;
+  if (p->pup_dist_px < 1 || p->pup_dist_px + pupil->n_pix > p->pad * pupil->n_pix)
+    return SPECULA_EUNSUPPORTED;
   return SPECULA_OK;
 }
 

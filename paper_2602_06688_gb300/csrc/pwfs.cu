@@ -322,12 +322,15 @@ template <int N1, int N2> struct RowFiltCfg {
 // representative m = c) without the y factor, and the column pass applies
 // each item's own y factor gy[m][row] to its input.
 // R: grid (ceil(n_pix / VPC), ceil(n_slots / ka)); block VPC * G threads.
-template <int N1, int N2>
+// GEN: any padding (the pupil at padded offset `off`, each lane loading the
+// registers whose padded index falls in the pupil); otherwise the pad-2
+// layout, where the pupil is exactly registers N2/4 .. 3 N2/4 of every lane.
+template <int N1, int N2, bool GEN = false>
 __global__ void __launch_bounds__(256, 2) k_rowfilt(
     const float2 *__restrict__ field, const float2 *__restrict__ gx,
     const float2 *__restrict__ twA, const float2 *__restrict__ twB,
     const float2 *__restrict__ mask, float2 *__restrict__ rows_out, int n_pix, int nc, int nbw,
-    int slot0, int n_slots, int ka) {
+    int slot0, int n_slots, int ka, int off) {
   using S = Split<N1, N2>;
   constexpr int N = S::N, G = S::G, S1 = S::S1, S2 = S::S2;
   constexpr int Q0 = N2 / 4, QH = N2 / 2;
@@ -338,7 +341,7 @@ __global__ void __launch_bounds__(256, 2) k_rowfilt(
   const int j = blockIdx.x * vpc + vec;
   const bool row_ok = j < n_pix;
   const bool in_lane = row_ok && lane < N1;
-  float2 e[QH];
+  float2 e[GEN ? 1 : QH];
   int cur_b = -1;
   const int it_begin = blockIdx.y * ka;
   for (int q = 0; q < ka; ++q) {
@@ -346,20 +349,30 @@ __global__ void __launch_bounds__(256, 2) k_rowfilt(
     if (it >= n_slots) break;
     const int gi = slot0 + it;
     const int b = gi / nc, c = gi - b * nc;
-    if (b != cur_b) {
+    if (!GEN && b != cur_b) {
       cur_b = b;
       const float2 *src = field + ((size_t)(b % nbw) * n_pix + (row_ok ? j : 0)) * n_pix + lane;
 #pragma unroll
-      for (int h = 0; h < QH; ++h) e[h] = in_lane ? src[N1 * h] : make_float2(0.f, 0.f);
+      for (int h = 0; h < (GEN ? 1 : QH); ++h) e[h] = in_lane ? src[N1 * h] : make_float2(0.f, 0.f);
     }
     // forward row transform, pruned input (standard split)
     float2 r[N2];
 #pragma unroll
     for (int n2 = 0; n2 < N2; ++n2) r[n2] = make_float2(0.f, 0.f);
     if (in_lane) {
-      const float2 *g = gx + (size_t)c * n_pix + lane;
+      if constexpr (GEN) {
+        const float2 *src = field + ((size_t)(b % nbw) * n_pix + j) * n_pix;
+        const float2 *g = gx + (size_t)c * n_pix;
 #pragma unroll
-      for (int h = 0; h < QH; ++h) r[Q0 + h] = cmul(e[h], __ldg(g + N1 * h));
+        for (int n2 = 0; n2 < N2; ++n2) {
+          const int i = lane + N1 * n2 - off;                // pupil column
+          if (i >= 0 && i < n_pix) r[n2] = cmul(src[i], __ldg(g + i));
+        }
+      } else {
+        const float2 *g = gx + (size_t)c * n_pix + lane;
+#pragma unroll
+        for (int h = 0; h < QH; ++h) r[Q0 + h] = cmul(e[h], __ldg(g + N1 * h));
+      }
     }
     RegDFT<N2, false>::run(r);
     __syncwarp();
@@ -423,12 +436,12 @@ template <int N1, int N2> struct ColFiltCfg {
 // 39 m pupil's bin side 5) take the variant bounded at 160 threads x 4 CTAs
 // per SM, the occupancy that 80 registers per thread gave them already:
 // 96 registers per thread, so the twiddle loads can be issued earlier.
-template <int N1, int N2, int MAXT = 256>
+template <int N1, int N2, int MAXT = 256, bool GEN = false>
 __global__ void __launch_bounds__(MAXT, MAXT <= 160 ? 4 : 3) k_colfilt_bin(
     const float2 *__restrict__ rows_in, const float2 *__restrict__ gy,
     const float2 *__restrict__ twA, const float2 *__restrict__ twB,
     const float2 *__restrict__ mask, float *__restrict__ part, int n_pix, int bsz, float scale,
-    int n_mod, int nc, int nbw, int slot0, int CS) {
+    int n_mod, int nc, int nbw, int slot0, int CS, int off) {
   using S = Split<N1, N2>;
   constexpr int N = S::N, G = S::G, S1 = S::S1, S2 = S::S2;
   constexpr int Q0 = N2 / 4, QH = N2 / 2;
@@ -463,10 +476,20 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 160 ? 4 : 3) k_colfilt_bin(
 #pragma unroll
   for (int n2 = 0; n2 < N2; ++n2) r[n2] = make_float2(0.f, 0.f);
   if (lane < N1) {
-    const float2 *g = gy + (size_t)m * n_pix + lane;   // pupil row lane + N1 h
-    const float2 *w = s_tile + sh + vec + lane * W;
+    if constexpr (GEN) {
+      const float2 *g = gy + (size_t)m * n_pix;
+      const float2 *w = s_tile + sh + vec;
 #pragma unroll
-    for (int h = 0; h < QH; ++h) r[Q0 + h] = cmul(w[N1 * h * W], __ldg(g + N1 * h));
+      for (int n2 = 0; n2 < N2; ++n2) {
+        const int row = lane + N1 * n2 - off;                // pupil row
+        if (row >= 0 && row < n_pix) r[n2] = cmul(w[row * W], __ldg(g + row));
+      }
+    } else {
+      const float2 *g = gy + (size_t)m * n_pix + lane;   // pupil row lane + N1 h
+      const float2 *w = s_tile + sh + vec + lane * W;
+#pragma unroll
+      for (int h = 0; h < QH; ++h) r[Q0 + h] = cmul(w[N1 * h * W], __ldg(g + N1 * h));
+    }
   }
   __syncthreads();                             // the window is reused below
   float2 *col = s_tile + vec * CS;
@@ -595,8 +618,11 @@ static int configure(PwfsPlan *p) {
     p->smemK = std::max((size_t)tc * p->csK, win) * sizeof(float2);
     if (p->smemK <= 227 * 1024 && S::N % tc == 0) {
       if ((s = ensure_dynamic_smem((const void *)k_rowfilt<N1, N2>, p->smemR)) ||
+          (s = ensure_dynamic_smem((const void *)k_rowfilt<N1, N2, true>, p->smemR)) ||
           (s = ensure_dynamic_smem((const void *)k_colfilt_bin<N1, N2>, p->smemK)) ||
-          (s = ensure_dynamic_smem((const void *)k_colfilt_bin<N1, N2, 160>, p->smemK)))
+          (s = ensure_dynamic_smem((const void *)k_colfilt_bin<N1, N2, 160>, p->smemK)) ||
+          (s = ensure_dynamic_smem((const void *)k_colfilt_bin<N1, N2, 256, true>, p->smemK)) ||
+          (s = ensure_dynamic_smem((const void *)k_colfilt_bin<N1, N2, 160, true>, p->smemK)))
         return s;
       p->two_ok = true;
     }
@@ -631,24 +657,36 @@ static int run_split2(specula_ctx *ctx, PwfsPlan *p, const float *amp, const flo
       field_done = b1;
     }
     dim3 gR((Np + vpc - 1) / vpc, (nj + p->ka - 1) / p->ka);
-    SPECULA_LAUNCH(ctx, SPECULA_K_PWFS_ROWFILT, st,
-                   k_rowfilt<N1, N2><<<gR, p->blockR, p->smemR, st>>>(
-                       p->field.as<float2>(), p->gx.as<float2>(), p->twA.as<float2>(),
-                       p->twB.as<float2>(), p->mask.as<float2>(), p->rows.as<float2>(), Np, nc,
-                       p->nbw, j0, nj, p->ka));
-    dim3 gK(S::N / tc, 2 * nj);
-    if (S::G == 32 && p->blockK <= 160)
-      SPECULA_LAUNCH(ctx, SPECULA_K_PWFS_COLFILT, st,
-                     k_colfilt_bin<N1, N2, 160><<<gK, p->blockK, p->smemK, st>>>(
-                         p->rows.as<float2>(), p->gy.as<float2>(), p->twA.as<float2>(),
-                         p->twB.as<float2>(), p->mask.as<float2>(), p->part.as<float>(), Np, bsz,
-                         scale, p->n_mod, nc, p->nbw, j0, p->csK));
+    const int off = (S::N - Np) / 2;                // the pupil's padded offset
+    const bool gen = p->pad != 2;
+#define SPECULA_ROWFILT(GEN_)                                                                  \
+  SPECULA_LAUNCH(ctx, SPECULA_K_PWFS_ROWFILT, st,                                              \
+                 k_rowfilt<N1, N2, GEN_><<<gR, p->blockR, p->smemR, st>>>(                     \
+                     p->field.as<float2>(), p->gx.as<float2>(), p->twA.as<float2>(),           \
+                     p->twB.as<float2>(), p->mask.as<float2>(), p->rows.as<float2>(), Np, nc,  \
+                     p->nbw, j0, nj, p->ka, off))
+#define SPECULA_COLFILT(MAXT_, GEN_)                                                           \
+  SPECULA_LAUNCH(ctx, SPECULA_K_PWFS_COLFILT, st,                                              \
+                 k_colfilt_bin<N1, N2, MAXT_, GEN_><<<gK, p->blockK, p->smemK, st>>>(          \
+                     p->rows.as<float2>(), p->gy.as<float2>(), p->twA.as<float2>(),            \
+                     p->twB.as<float2>(), p->mask.as<float2>(), p->part.as<float>(), Np, bsz,  \
+                     scale, p->n_mod, nc, p->nbw, j0, p->csK, off))
+    if (gen)
+      SPECULA_ROWFILT(true);
     else
-      SPECULA_LAUNCH(ctx, SPECULA_K_PWFS_COLFILT, st,
-                     k_colfilt_bin<N1, N2><<<gK, p->blockK, p->smemK, st>>>(
-                         p->rows.as<float2>(), p->gy.as<float2>(), p->twA.as<float2>(),
-                         p->twB.as<float2>(), p->mask.as<float2>(), p->part.as<float>(), Np, bsz,
-                         scale, p->n_mod, nc, p->nbw, j0, p->csK));
+      SPECULA_ROWFILT(false);
+    dim3 gK(S::N / tc, 2 * nj);
+    const bool k160 = S::G == 32 && p->blockK <= 160;
+    if (k160 && gen)
+      SPECULA_COLFILT(160, true);
+    else if (k160)
+      SPECULA_COLFILT(160, false);
+    else if (gen)
+      SPECULA_COLFILT(256, true);
+    else
+      SPECULA_COLFILT(256, false);
+#undef SPECULA_ROWFILT
+#undef SPECULA_COLFILT
     const int complete = (j0 + nj) / nc - 1;
     if (complete > det_done) {
       dim3 gD((nd * nd + 255) / 256, complete - det_done);
@@ -732,6 +770,7 @@ bool pwfs_split_for(int N, int *N1, int *N2) {
 int pwfs_set_tiles(PwfsPlan *p, int chunk, int ka, int passes) {
   if (passes != 2 && passes != 3) return SPECULA_EINVAL;
   if (passes == 2 && !p->two_ok) return SPECULA_EUNSUPPORTED;
+  if (passes == 3 && p->pad != 2) return SPECULA_EUNSUPPORTED;   // pad-2 layout only
   const int nd = 2 * p->n_sub;
   // batch elements one chunk can touch: chunk items (three-pass) or chunk
   // row-filter slots, nc per batch element (two-pass)
@@ -795,7 +834,7 @@ int pwfs_autotune(specula_ctx *ctx, PwfsPlan *p, const float *amp, const float *
   SPECULA_CK(cudaEventCreate(&e0));
   SPECULA_CK(cudaEventCreate(&e1));
   int status = SPECULA_OK;
-  for (int passes = 2; passes <= 3; ++passes) {
+  for (int passes = 2; passes <= (p->pad == 2 ? 3 : 2); ++passes) {
     if (passes == 2 && !p->two_ok) continue;
     const size_t item = passes == 2 ? (size_t)p->n_pix * p->N * sizeof(float2) : per_item;
     for (int c : kChunks) {

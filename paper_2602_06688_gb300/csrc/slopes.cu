@@ -90,6 +90,68 @@ __global__ void __launch_bounds__(kPyrThreads) k_pyr_slopes(
   guard_finite(sx, sy, nf_status);
 }
 
+// The same slopes from explicit detector indices of the four pupil images
+// (map[q n_valid + k] for image q = Q1..Q4 of subaperture k; any padding and
+// image separation): same grid, same fixed-order sums.
+__global__ void __launch_bounds__(kPyrThreads) k_pyr_slopes_maps(
+    const float *__restrict__ det, const int32_t *__restrict__ map, const float *__restrict__ ref,
+    int n_det2, int n_valid, float *__restrict__ out, int32_t *status, int32_t *nf_status) {
+  __shared__ float s_w[kPyrThreads / 32];
+  __shared__ float s_T;
+  const int b = blockIdx.y;
+  const float *d = det + (size_t)b * n_det2;
+  const unsigned lim = (unsigned)n_det2;
+  float part = 0.f;
+  int bad = 0;
+  for (int k0 = threadIdx.x; k0 < n_valid; k0 += 8 * kPyrThreads) {
+    float q[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int k = k0 + u * kPyrThreads;
+      int i[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int v = k < n_valid ? __ldg(map + (size_t)c * n_valid + k) : 0;
+        bad |= (unsigned)v >= lim;
+        i[c] = (unsigned)v < lim ? v : 0;
+      }
+      q[u] = ((d[i[0]] + d[i[1]]) + d[i[2]]) + d[i[3]];
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      if (k0 + u * kPyrThreads < n_valid) part += q[u];
+  }
+  part = warp_sum(part);
+  if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = part;
+  bad = __syncthreads_or(bad);
+  if (threadIdx.x == 0) {
+    float t = 0.f;
+    for (int i = 0; i < kPyrThreads / 32; ++i) t += s_w[i];
+    s_T = t / (float)n_valid;
+    if (bad) atomicExch(status, SPECULA_EINVAL);
+  }
+  __syncthreads();
+  const float T = s_T;
+  const int k = blockIdx.x * kPyrThreads + threadIdx.x;
+  if (k >= n_valid) return;
+  float *o = out + (size_t)b * 2 * n_valid;
+  float q[4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const int v = __ldg(map + (size_t)c * n_valid + k);
+    q[c] = d[(unsigned)v < lim ? v : 0];
+  }
+  float sx = ((q[0] + q[3]) - (q[1] + q[2])) / T;
+  float sy = ((q[0] + q[1]) - (q[2] + q[3])) / T;
+  if (ref) {
+    sx -= ref[k];
+    sy -= ref[n_valid + k];
+  }
+  o[k] = sx;
+  o[n_valid + k] = sy;
+  guard_finite(sx, sy, nf_status);
+}
+
 // One warp per (batch element, subaperture): centre of gravity of the spot.
 __global__ void __launch_bounds__(256) k_sh_cog(const float *__restrict__ spots,
                                                 const float *__restrict__ ref, int nf,
@@ -149,6 +211,13 @@ extern "C" int specula_slopes(specula_ctx *ctx, const specula_slopec_desc *d, co
     if (!d->subap_idx_dev || d->n_valid > d->n_sub * d->n_sub) return SPECULA_EINVAL;
     return slopes_pyr_run(ctx, d->subap_idx_dev, d->n_sub, d->n_valid, img_dev, ref_dev, n_batch,
                           slopes_dev, st);
+  } else if (d->kind == SPECULA_SLOPES_PYR_MAPS) {
+    if (!d->subap_idx_dev || d->n_sub < 1) return SPECULA_EINVAL;
+    SPECULA_LAUNCH(ctx, SPECULA_K_SLOPES, st,
+                   k_pyr_slopes_maps<<<dim3((d->n_valid + kPyrThreads - 1) / kPyrThreads, n_batch),
+                                       kPyrThreads, 0, st>>>(
+                       img_dev, d->subap_idx_dev, ref_dev, d->n_sub * d->n_sub, d->n_valid,
+                       slopes_dev, ctx->status_dev, ctx->guard ? ctx->status_dev : nullptr));
   } else if (d->kind == SPECULA_SLOPES_SH) {
     if (d->fft_n < 2) return SPECULA_EINVAL;
     const long long tasks = (long long)d->n_valid * n_batch;

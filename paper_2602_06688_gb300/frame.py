@@ -8,10 +8,11 @@ libspecula_gb300; this class only owns buffers and issues the calls.
 import numpy as np
 
 import synth
-from . import (PREC_BF16, PREC_BF16X2, PREC_FP32, SLOPES_PYR, layer_desc, pupil_desc,
+from . import (PREC_BF16, PREC_BF16X2, PREC_FP32, SLOPES_PYR, SLOPES_PYR_MAPS, layer_desc,
+               pupil_desc,
                pwfs_desc, recon_desc, slopec_desc, source_desc, specula_atmo_extract,
                specula_ccd, specula_pupil_mask, specula_pupil_mask_host, specula_pwfs_image,
-               specula_pwfs_plan, specula_recon,
+               specula_pwfs_plan, specula_pyr_image_index_host, specula_recon,
                specula_recon_convert, specula_screen_generate, specula_slopes,
                specula_valid_subaps_host)
 
@@ -58,13 +59,22 @@ class PwfsFrame:
             self.screens.append(scr)
         self.amp = torch.empty(n, n, device=device)
         specula_pupil_mask(ctx, self.pupil, self.amp)
-        valid = specula_valid_subaps_host(self.pupil, s.pwfs.n_sub)
-        self.valid = torch.tensor(valid, device=device)
-        self.n_valid = len(valid)
+        # the quadrant layout when the four pupil images tile a pad-2 grid,
+        # explicit image index maps for any other padding or separation
+        self.quadrants = s.pwfs.pad == 2 and s.pwfs.pup_dist_px == n
+        if self.quadrants:
+            valid = specula_valid_subaps_host(self.pupil, s.pwfs.n_sub)
+            self.valid = torch.tensor(valid, device=device)
+            self.n_valid = len(valid)
+        else:
+            maps = specula_pyr_image_index_host(self.pupil, s.pwfs.pad, s.pwfs.pup_dist_px,
+                                                s.pwfs.n_sub)
+            self.valid = torch.tensor(maps.ravel(), device=device)
+            self.n_valid = maps.shape[1]
         self.n_slopes = 2 * self.n_valid
         self.n_modes = n_modes or wl.n_modes
         specula_pwfs_plan(ctx, self.pupil, self.pwfs)
-        d = 2 * s.pwfs.n_sub
+        d = s.pwfs.pad * s.pwfs.n_sub
         self.batch = batch
         self.dt = wl.dt_s
         if batch == 1:
@@ -80,7 +90,8 @@ class PwfsFrame:
         self.ref = torch.empty(self.n_slopes, device=device)
         self.noise = dict(noise) if noise else None
         self.frame_dev = torch.zeros(1, dtype=torch.int32, device=device)
-        self.slopec = slopec_desc(SLOPES_PYR, s.pwfs.n_sub, self.valid)
+        self.slopec = (slopec_desc(SLOPES_PYR, s.pwfs.n_sub, self.valid) if self.quadrants else
+                       slopec_desc(SLOPES_PYR_MAPS, s.pwfs.pad * s.pwfs.n_sub, self.valid))
         if R is None:
             R = seeded_reconstructor(self.n_modes, self.n_slopes, seed=7 + seed_offset)
         self.R = torch.tensor(np.asarray(R, dtype=np.float32), device=device)

@@ -131,6 +131,22 @@ def _pwfs8m():
                     layers, n_modes=500, n_frames=1000, dt_s=1e-3, r0_m=0.12)
 
 
+def _soul8m():
+    """The geometry of the paper's SOUL example (App. B, Listing 2): 40
+    subapertures across each pupil image, images 48 detector pixels apart on
+    a 120 px detector, modulation 3 lambda/D.  Sampled with an 80 px pupil
+    padded three times (240^2 FFT) and 2 x 2 binning; LBT 8.2 m, 750 nm;
+    16 modulation points, two layers (readings: the listing's sampling and
+    atmosphere are not all given)."""
+    D, n = 8.2, 80
+    pup = Pupil(n, D / n, 0.11)
+    src = Source(0.0, 0.0, math.inf, 750.0)
+    geom = PwfsGeom(pad=3, n_mod=16, mod_amp=3.0, n_sub=40, pup_dist_px=96)
+    layers = _profile(6, 2, 0.14, [0.0, 6000.0], [0.7, 0.3], [6.0, 15.0], 512, D / n, 40.0, 6)
+    return Workload('soul8m', D, (Sensor('pwfs', pup, src, pwfs=geom),),
+                    layers, n_modes=300, n_frames=1000, dt_s=1e-3, r0_m=0.14)
+
+
 def _learned8m():
     base = _pwfs8m()
     return Workload('learned8m', base.diameter_m, base.sensors, base.layers[:1],
@@ -211,6 +227,7 @@ WORKLOADS = {
     'mwfs39m': _mwfs39m,
     'mwfs8m_small': _mwfs8m_small,
     'pwfs39m': _pwfs39m,
+    'soul8m': _soul8m,
 }
 
 

@@ -107,3 +107,21 @@ def test_host_validation_returns_codes(sp):
                                     None) == sp.EINVAL
     assert lib.specula_ctx_create(None, 0) == sp.EINVAL
     assert lib.specula_ctx_destroy(None) == sp.EINVAL
+
+
+def test_pyr_image_index_host_matches_oracle(sp):
+    """Host image maps for the SOUL geometry and, at pad 2 with touching
+    images, the quadrant layout; refused where image corners fall between
+    detector pixels."""
+    from oracle import geometry
+    pu = sp.PupilDesc(80, 0.1025, 0.11)
+    m = sp.specula_pyr_image_index_host(pu, 3, 96, 40)
+    v = geometry.valid_subaps(geometry.pupil_mask(80, 0.11).astype(np.uint8), 40)
+    assert np.array_equal(m, geometry.pyr_image_index(v, 40, 3, 96, 80))
+    pu2 = sp.PupilDesc(64, 0.1, 0.0)
+    v2 = geometry.valid_subaps(geometry.pupil_mask(64, 0.0).astype(np.uint8), 16)
+    assert np.array_equal(sp.specula_pyr_image_index_host(pu2, 2, 64, 16),
+                          geometry.pyr_quadrant_index(v2, 16))
+    with pytest.raises(sp.SpeculaError) as e:
+        sp.specula_pyr_image_index_host(pu, 3, 97, 40)       # not a multiple of b = 2
+    assert e.value.status == sp.EUNSUPPORTED

@@ -156,8 +156,11 @@ def test_plan_required_and_bad_args(env):
     with pytest.raises(sp.SpeculaError) as e:
         sp.specula_pwfs_plan(ctx, sp.PupilDesc(50, 0.1, 0.0), sp.PwfsDesc(2, 4, 10, 50, 3.0))
     assert e.value.status == sp.EUNSUPPORTED
-    with pytest.raises(sp.SpeculaError) as e:
-        sp.specula_pwfs_plan(ctx, pu, sp.PwfsDesc(2, 4, 16, 60, 3.0))
+    with pytest.raises(sp.SpeculaError) as e:                 # images beyond the grid
+        sp.specula_pwfs_plan(ctx, pu, sp.PwfsDesc(2, 4, 16, 70, 3.0))
+    assert e.value.status == sp.EUNSUPPORTED
+    with pytest.raises(sp.SpeculaError) as e:                 # padding 5
+        sp.specula_pwfs_plan(ctx, pu, sp.PwfsDesc(5, 4, 16, 64, 3.0))
     assert e.value.status == sp.EUNSUPPORTED
 
 

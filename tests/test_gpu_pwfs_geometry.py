@@ -1,0 +1,113 @@
+"""GPU parity of the pyramid with other paddings and image separations (the
+SOUL example's geometry) and of the slope computer driven by image index
+maps, against the FP64 oracle; the whole SOUL-geometry frame against the
+oracle chain.  Tolerances as for the pad-2 pyramid: normalised-intensity
+error <= 1e-5; slopes within 2 (5e-5 max(det) / T + 1e-5 max|S|)."""
+import numpy as np
+import pytest
+
+import synth
+from gpu_common import kolmogorov_phase, load_pkg, need_gpu, norm_intensity_error
+from oracle import atmo, geometry, pyramid, recon, slopes
+
+pytestmark = pytest.mark.gpu
+
+# (n_pix, pad, pup_dist_px, n_sub, n_mod): SOUL (N 240), pad 4 (N 128, 64),
+# the 960^2 grid at pad 3, and pad 2 with images closer than their width
+CASES = [(80, 3, 96, 40, 16), (32, 4, 48, 8, 8), (16, 4, 24, 4, 8), (320, 3, 384, 80, 16),
+         (64, 2, 48, 16, 12)]
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = need_gpu()
+    sp = load_pkg()
+    ctx = sp.Context(0)
+    yield torch, sp, ctx
+    ctx.close()
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: f"np{c[0]}_pad{c[1]}_pd{c[2]}")
+def test_image_and_map_slopes_parity(env, case):
+    torch, sp, ctx = env
+    n, pad, pd, nsub, nmod = case
+    pu = sp.PupilDesc(n, 8.0 / n, 0.11)
+    pw = sp.PwfsDesc(pad, nmod, nsub, pd, 3.0)
+    sp.specula_pwfs_plan(ctx, pu, pw)
+    amp = torch.empty(n, n, device="cuda")
+    sp.specula_pupil_mask(ctx, pu, amp)
+    ph = kolmogorov_phase(n, 8.0 / n, 0.15, seed=7).astype(np.float32)
+    side = pad * nsub
+    det = torch.full((1, side, side), float("nan"), device="cuda")
+    sp.specula_pwfs_image(ctx, pu, pw, amp, torch.tensor(ph[None], device="cuda"), det)
+    torch.cuda.synchronize()
+    a64 = amp.cpu().numpy().astype(np.float64)
+    ref = pyramid.pwfs_image(a64, ph.astype(np.float64), pad, nmod, 3.0, nsub, pd)
+    assert norm_intensity_error(det[0].cpu().numpy(), ref) <= 1e-5
+    # slopes from image maps (host maps = oracle maps), against the oracle on
+    # the GPU's own detector
+    maps = sp.specula_pyr_image_index_host(pu, pad, pd, nsub)
+    valid = geometry.valid_subaps(a64.astype(np.uint8), nsub)
+    assert np.array_equal(maps, geometry.pyr_image_index(valid, nsub, pad, pd, n))
+    mt = torch.tensor(maps.ravel(), device="cuda")
+    sc = sp.slopec_desc(sp.SLOPES_PYR_MAPS, side, mt)
+    sl = torch.empty(2 * maps.shape[1], device="cuda")
+    sp.specula_slopes(ctx, sc, det, None, sl)
+    torch.cuda.synchronize()
+    s_ref = slopes.pyr_slopes_maps(det[0].cpu().numpy().astype(np.float64), maps)
+    assert np.max(np.abs(sl.cpu().numpy() - s_ref)) <= 1e-5 * (1 + np.abs(s_ref).max())
+
+
+def test_maps_equal_quadrants_bit_exact(env):
+    """At pad 2 with touching images the map-driven kernel reproduces the
+    quadrant kernel bit for bit (same indices, same summation order)."""
+    torch, sp, ctx = env
+    n, nsub = 64, 16
+    pu = sp.PupilDesc(n, 0.125, 0.1)
+    pw = sp.PwfsDesc(2, 12, nsub, n, 3.0)
+    sp.specula_pwfs_plan(ctx, pu, pw)
+    amp = torch.empty(n, n, device="cuda")
+    sp.specula_pupil_mask(ctx, pu, amp)
+    ph = torch.tensor(kolmogorov_phase(n, 0.125, 0.15, seed=9).astype(np.float32)[None],
+                      device="cuda")
+    det = torch.empty(1, 2 * nsub, 2 * nsub, device="cuda")
+    sp.specula_pwfs_image(ctx, pu, pw, amp, ph, det)
+    valid = torch.tensor(sp.specula_valid_subaps_host(pu, nsub), device="cuda")
+    maps = torch.tensor(sp.specula_pyr_image_index_host(pu, 2, n, nsub).ravel(), device="cuda")
+    a, b = torch.empty(2 * valid.numel(), device="cuda"), torch.empty(2 * valid.numel(), device="cuda")
+    sp.specula_slopes(ctx, sp.slopec_desc(sp.SLOPES_PYR, nsub, valid), det, None, a)
+    sp.specula_slopes(ctx, sp.slopec_desc(sp.SLOPES_PYR_MAPS, 2 * nsub, maps), det, None, b)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+
+
+def test_soul_frame_vs_oracle_chain(env):
+    """The SOUL-geometry frame (80 px pupil, pad 3, 40 x 40 subapertures,
+    images 48 detector px apart on 120 px): extraction, image, map slopes,
+    MVM against the oracle chain."""
+    torch, sp, ctx = env
+    from paper_2602_06688_gb300.frame import PwfsFrame
+    wl = synth.workload("soul8m")
+    fr = PwfsFrame(ctx, wl)
+    s = wl.sensors[0]
+    n, g = s.pupil.n_pix, s.pwfs
+    t = 0.071
+    fr.frame(t)
+    torch.cuda.synchronize()
+    assert fr.det.shape[-1] == 120 and not fr.quadrants
+    scr = [x.cpu().numpy().astype(np.float64) for x in fr.screens]
+    phi = atmo.atmo_extract(scr, wl.layers, s.source, n, s.pupil.pitch_m, t)
+    amp = geometry.pupil_mask(n, s.pupil.obsc_frac).astype(np.float64)
+    valid = geometry.valid_subaps(amp.astype(np.uint8), g.n_sub)
+    maps = geometry.pyr_image_index(valid, g.n_sub, g.pad, g.pup_dist_px, n)
+    det_ref = pyramid.pwfs_image(amp, phi, g.pad, g.n_mod, g.mod_amp, g.n_sub, g.pup_dist_px)
+    flat = pyramid.pwfs_image(amp, np.zeros_like(phi), g.pad, g.n_mod, g.mod_amp, g.n_sub,
+                              g.pup_dist_px)
+    assert norm_intensity_error(fr.det.cpu().numpy().astype(np.float64), det_ref) <= 1e-5
+    s_ref = slopes.pyr_slopes_maps(det_ref, maps, ref=slopes.pyr_slopes_maps(flat, maps))
+    T = det_ref.ravel()[maps].sum() / len(valid)
+    tol = 2 * (5e-5 * det_ref.max() / T + 1e-5 * np.abs(s_ref).max())
+    sl = fr.slopes.cpu().numpy().astype(np.float64)
+    assert np.max(np.abs(sl - s_ref)) <= tol
+    R = fr.R.cpu().numpy().astype(np.float64)
+    assert np.all(np.abs(fr.modes.cpu().numpy() - recon.mvm(R, sl)) <= 1e-5 * (np.abs(R) @ np.abs(sl)))
