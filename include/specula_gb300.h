@@ -86,9 +86,13 @@ typedef struct {
 
 /* Modulated pyramid (ModulatedPyramid, Listing 2): FFT side N = pad * n_pix;
  * n_mod modulation points on a circle of mod_amp lambda/D; images binned to
- * n_sub x n_sub per pupil image; pup_dist_px = separation of the pupil images
- * (this library supports pad = 2 and pup_dist_px = n_pix, where the four
- * images tile the padded grid). */
+ * n_sub x n_sub per pupil image (a pad n_sub detector); pup_dist_px =
+ * separation of the pupil images' centres in grid pixels.  Supported: pad
+ * 2-4 with N one of 64, 128, 240, 320, 960, and pup_dist_px + n_pix <= N
+ * (the images inside the grid; SPECULA_EUNSUPPORTED else).  With pad 2 and
+ * pup_dist_px = n_pix the four images tile the grid (quadrant slopes);
+ * otherwise read the slopes with SPECULA_SLOPES_PYR_MAPS.  The three-pass
+ * form and the shifted-mask form need pad 2. */
 typedef struct {
   int32_t pad, n_mod, n_sub, pup_dist_px;
   double mod_amp;
