@@ -639,7 +639,7 @@ int specula_modal_basis(specula_ctx *ctx, const specula_pupil_desc *pupil, int32
 
 /* Push-pull interaction matrix (ImCalibrator + PushPullGenerator, App. A,
  * Tab. 4): IM[s][j] = (S_s(+a Z_j) - S_s(-a Z_j)) / (2a), S the pyramid slopes
- * (kind PYR, no reference) of the phase +-a Z_j, a = push_amp radians at the
+ * (kind PYR or PYR_MAPS, no reference) of the phase +-a Z_j, a = push_amp radians at the
  * WFS wavelength.  basis_dev: n_modes * n_pix^2 floats; im_dev: n_slopes *
  * n_modes doubles, row-major (n_slopes = 2 n_valid).  Requires a pyramid
  * plan.  Allocates a 16-mode workspace for the call. */

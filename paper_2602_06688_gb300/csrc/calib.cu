@@ -312,16 +312,19 @@ extern "C" int specula_calib_intmat(specula_ctx *ctx, const specula_pupil_desc *
                                     void *stream) {
   if (!ctx || !pupil || !pwfs || !amp_dev || !basis_dev || !slopec || !im_dev) return SPECULA_EINVAL;
   if (n_modes < 1 || !(push_amp > 0) || !isfinite(push_amp)) return SPECULA_EINVAL;
-  if (slopec->kind != SPECULA_SLOPES_PYR || !slopec->subap_idx_dev || slopec->n_valid < 1)
+  if ((slopec->kind != SPECULA_SLOPES_PYR && slopec->kind != SPECULA_SLOPES_PYR_MAPS) ||
+      !slopec->subap_idx_dev || slopec->n_valid < 1)
     return SPECULA_EINVAL;
   PwfsPlan *p = pwfs_plan_find(ctx, pupil, pwfs);
   if (!p) return SPECULA_ENOPLAN;
-  if (slopec->n_sub != pwfs->n_sub) return SPECULA_EINVAL;
+  // quadrant slopes: n_sub subapertures per image; image maps: the detector side
+  if (slopec->n_sub != (slopec->kind == SPECULA_SLOPES_PYR ? pwfs->n_sub : pwfs->pad * pwfs->n_sub))
+    return SPECULA_EINVAL;
   SPECULA_CK(cudaSetDevice(ctx->device));
   cudaStream_t st = (cudaStream_t)stream;
   const int MB = 16;
   const int npix2 = pupil->n_pix * pupil->n_pix;
-  const int nd = 2 * pwfs->n_sub;
+  const int nd = pwfs->pad * pwfs->n_sub;
   const int ns = 2 * slopec->n_valid;
   DevBuf ph, det, sl;
   int s;
@@ -335,8 +338,7 @@ extern "C" int specula_calib_intmat(specula_ctx *ctx, const specula_pupil_desc *
                    k_pushpull<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(
                        basis_dev, npix2, j0, nq, (float)push_amp, ph.as<float>()));
     if ((s = pwfs_run(ctx, p, amp_dev, ph.as<float>(), 2 * nq, det.as<float>(), st))) return s;
-    if ((s = slopes_pyr_run(ctx, slopec->subap_idx_dev, slopec->n_sub, slopec->n_valid,
-                            det.as<float>(), nullptr, 2 * nq, sl.as<float>(), st)))
+    if ((s = specula_slopes(ctx, slopec, det.as<float>(), nullptr, 2 * nq, sl.as<float>(), st)))
       return s;
     SPECULA_LAUNCH(ctx, SPECULA_K_CALIB, st,
                    k_im_cols<<<(ns * nq + 255) / 256, 256, 0, st>>>(sl.as<float>(), ns, n_modes,

@@ -602,13 +602,13 @@ static int configure(PwfsPlan *p) {
       (s = ensure_dynamic_smem((const void *)k_rows_inv_part<N1, N2>, p->smemC)))
     return s;
   // two-pass form: column tiles of TC = k bsz columns, k the largest divisor
-  // of 2 n_sub with TC G <= 256
+  // of the detector side pad n_sub with TC G <= 256
   p->two_ok = false;
   p->blockR = 256;
   p->smemR = (size_t)(256 / S::G) * RowFiltCfg<N1, N2>::XBF * sizeof(float2);
   int k = 0;
-  for (int d = 1; d <= 2 * p->n_sub; ++d)
-    if ((2 * p->n_sub) % d == 0 && d * bsz * S::G <= 256) k = d;
+  for (int d = 1; d <= p->pad * p->n_sub; ++d)
+    if ((p->pad * p->n_sub) % d == 0 && d * bsz * S::G <= 256) k = d;
   if (k > 0 && p->smemR <= 227 * 1024) {
     const int tc = k * bsz;
     p->blockK = tc * S::G;
@@ -771,7 +771,7 @@ int pwfs_set_tiles(PwfsPlan *p, int chunk, int ka, int passes) {
   if (passes != 2 && passes != 3) return SPECULA_EINVAL;
   if (passes == 2 && !p->two_ok) return SPECULA_EUNSUPPORTED;
   if (passes == 3 && p->pad != 2) return SPECULA_EUNSUPPORTED;   // pad-2 layout only
-  const int nd = 2 * p->n_sub;
+  const int nd = p->pad * p->n_sub;   // detector side
   // batch elements one chunk can touch: chunk items (three-pass) or chunk
   // row-filter slots, nc per batch element (two-pass)
   const int per_b = passes == 2 ? p->nc : p->n_mod;

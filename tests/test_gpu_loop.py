@@ -119,3 +119,21 @@ def test_loop_graph_replay_is_bit_identical(env, cl):
     torch.cuda.synchronize()
     assert torch.equal(cl.cmd, eager[0]) and torch.equal(cl.stats, eager[1])
     cl.close()
+
+
+def test_closed_loop_on_the_soul_geometry(env):
+    """The loop on the SOUL example's geometry (pad 3, separated images, map
+    slopes, calibrated with map slopes): the residual falls and the Strehl
+    ratio rises over 40 steps."""
+    torch, sp, ctx = env
+    from paper_2602_06688_gb300.loop import ClosedLoop
+    lp = ClosedLoop(ctx, synth.workload("soul8m"), n_modes=150, gain=0.4)
+    assert lp.rank == 150
+    sr = []
+    for k in range(40):
+        lp.step(k * lp.fr.dt)
+        torch.cuda.synchronize()
+        sr.append(lp.stats.cpu().numpy().copy())
+    sr = np.array(sr)
+    assert sr[-1, 1] > 5 * sr[0, 1] and sr[-5:, 0].mean() < 0.5 * sr[0, 0]
+    lp.close()

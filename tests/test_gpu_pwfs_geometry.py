@@ -36,14 +36,20 @@ def test_image_and_map_slopes_parity(env, case):
     sp.specula_pwfs_plan(ctx, pu, pw)
     amp = torch.empty(n, n, device="cuda")
     sp.specula_pupil_mask(ctx, pu, amp)
-    ph = kolmogorov_phase(n, 8.0 / n, 0.15, seed=7).astype(np.float32)
-    side = pad * nsub
-    det = torch.full((1, side, side), float("nan"), device="cuda")
-    sp.specula_pwfs_image(ctx, pu, pw, amp, torch.tensor(ph[None], device="cuda"), det)
-    torch.cuda.synchronize()
     a64 = amp.cpu().numpy().astype(np.float64)
-    ref = pyramid.pwfs_image(a64, ph.astype(np.float64), pad, nmod, 3.0, nsub, pd)
-    assert norm_intensity_error(det[0].cpu().numpy(), ref) <= 1e-5
+    phs = [kolmogorov_phase(n, 8.0 / n, 0.15, seed=7 + k).astype(np.float32) for k in range(3)]
+    ph = phs[0]
+    side = pad * nsub
+    det = torch.full((3, side, side), float("nan"), device="cuda")
+    ph_t = torch.tensor(np.stack(phs), device="cuda")
+    sp.specula_pwfs_image(ctx, pu, pw, amp, ph_t, det)
+    torch.cuda.synchronize()
+    # the inputs are untouched (a canary for writes outside the plan's buffers)
+    assert np.array_equal(amp.cpu().numpy().astype(np.float64), a64)
+    assert np.array_equal(ph_t.cpu().numpy(), np.stack(phs))
+    for k in range(3):
+        ref = pyramid.pwfs_image(a64, phs[k].astype(np.float64), pad, nmod, 3.0, nsub, pd)
+        assert norm_intensity_error(det[k].cpu().numpy(), ref) <= 1e-5, k
     # slopes from image maps (host maps = oracle maps), against the oracle on
     # the GPU's own detector
     maps = sp.specula_pyr_image_index_host(pu, pad, pd, nsub)
@@ -52,10 +58,11 @@ def test_image_and_map_slopes_parity(env, case):
     mt = torch.tensor(maps.ravel(), device="cuda")
     sc = sp.slopec_desc(sp.SLOPES_PYR_MAPS, side, mt)
     sl = torch.empty(2 * maps.shape[1], device="cuda")
-    sp.specula_slopes(ctx, sc, det, None, sl)
+    sp.specula_slopes(ctx, sc, det[0], None, sl)
     torch.cuda.synchronize()
     s_ref = slopes.pyr_slopes_maps(det[0].cpu().numpy().astype(np.float64), maps)
     assert np.max(np.abs(sl.cpu().numpy() - s_ref)) <= 1e-5 * (1 + np.abs(s_ref).max())
+    del ph
 
 
 def test_maps_equal_quadrants_bit_exact(env):
