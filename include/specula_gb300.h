@@ -160,6 +160,17 @@ int specula_ctx_status(specula_ctx *ctx, int32_t *device_status);
  * for launches made after the call. */
 int specula_ctx_set_guard(specula_ctx *ctx, int32_t on);
 
+/* Workspace guard bands.  Every device buffer the library allocates (plan
+ * tables and workspaces, the multi-sensor and learned-reconstructor buffers)
+ * is followed by 256 bytes of the pattern 0xA5.  A kernel that writes past
+ * its workspace stays inside the allocation, so the write does not fault;
+ * this call finds it afterwards.  Synchronises the device, then compares the
+ * band of every live library buffer on the context's device: *n_checked =
+ * the buffers compared, *n_bad = those whose band changed (0 when no kernel
+ * wrote out of bounds).  Host-synchronous; not for use inside a capture.
+ * Buffers the caller owns (inputs, outputs) are not covered. */
+int specula_check_guards(specula_ctx *ctx, int32_t *n_checked, int32_t *n_bad);
+
 /* ---- tracing -----------------------------------------------------------------
  * LoopControl reports the simulation speed (Sect. 2.4); these calls give the
  * per-kernel view behind it.  Kernel ids: */

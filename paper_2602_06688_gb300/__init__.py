@@ -133,6 +133,14 @@ def specula_ctx_set_guard(ctx, on):
     _abi.check(lib().specula_ctx_set_guard(ctx.handle, int(on)), "specula_ctx_set_guard")
 
 
+def specula_check_guards(ctx):
+    """(buffers compared, buffers whose guard band past the end changed)."""
+    nc, nb = C.c_int32(), C.c_int32()
+    _abi.check(lib().specula_check_guards(ctx.handle, C.byref(nc), C.byref(nb)),
+               "specula_check_guards")
+    return nc.value, nb.value
+
+
 (K_PWFS_ROWS_FWD, K_PWFS_COLS, K_PWFS_ROWS_INV, K_ATMO, K_SLOPES, K_RECON, K_SH,
  K_PWFS_FIELD, K_PWFS_BIN, K_CALIB, K_GEMM, K_MLP, K_MWFS, K_PWFS_ROWFILT,
  K_PWFS_COLFILT, K_PWFS_SM_FWD, K_PWFS_SM_ROWS, K_PWFS_SM_COLS, K_LOOP, K_CCD) = range(20)

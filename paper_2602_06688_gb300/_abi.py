@@ -73,6 +73,7 @@ SIGNATURES = {
     "specula_ctx_destroy": (C.c_int, [vp]),
     "specula_ctx_status": (C.c_int, [vp, P(i32)]),
     "specula_ctx_set_guard": (C.c_int, [vp, i32]),
+    "specula_check_guards": (C.c_int, [vp, P(i32), P(i32)]),
     "specula_prof_enable": (C.c_int, [vp, i32]),
     "specula_prof_read": (C.c_int, [vp, vp, vp]),
     "specula_launch_count": (C.c_int, [vp, P(C.c_int64)]),

@@ -7,6 +7,7 @@
 #include <map>
 #include <mutex>
 #include <new>
+#include <unordered_set>
 #include <utility>
 
 #include <vector>
@@ -217,6 +218,51 @@ extern "C" int specula_ctx_status(specula_ctx *ctx, int32_t *device_status) {
 extern "C" int specula_ctx_set_guard(specula_ctx *ctx, int32_t on) {
   if (!ctx || (on != 0 && on != 1)) return SPECULA_EINVAL;
   ctx->guard = on != 0;
+  return SPECULA_OK;
+}
+
+// ---- workspace guard bands ----------------------------------------------------
+
+namespace specula {
+// Never destroyed: buffers may outlive static destruction at exit.
+static std::mutex &guard_mu() {
+  static std::mutex *m = new std::mutex;
+  return *m;
+}
+static std::unordered_set<DevBuf *> &guard_set() {
+  static std::unordered_set<DevBuf *> *s = new std::unordered_set<DevBuf *>;
+  return *s;
+}
+void guard_register(DevBuf *b) {
+  std::lock_guard<std::mutex> g(guard_mu());
+  guard_set().insert(b);
+}
+void guard_unregister(DevBuf *b) {
+  std::lock_guard<std::mutex> g(guard_mu());
+  guard_set().erase(b);
+}
+}  // namespace specula
+
+extern "C" int specula_check_guards(specula_ctx *ctx, int32_t *n_checked, int32_t *n_bad) {
+  if (!ctx || !n_checked || !n_bad) return SPECULA_EINVAL;
+  SPECULA_CK(cudaSetDevice(ctx->device));
+  SPECULA_CK(cudaDeviceSynchronize());
+  std::lock_guard<std::mutex> g(guard_mu());
+  unsigned char h[kGuardBytes];
+  int32_t nc = 0, nb = 0;
+  for (DevBuf *b : guard_set()) {
+    if (b->device != ctx->device) continue;
+    SPECULA_CK(cudaMemcpy(h, static_cast<const char *>(b->p) + b->bytes, kGuardBytes,
+                          cudaMemcpyDeviceToHost));
+    ++nc;
+    for (size_t i = 0; i < kGuardBytes; ++i)
+      if (h[i] != kGuardByte) {
+        ++nb;
+        break;
+      }
+  }
+  *n_checked = nc;
+  *n_bad = nb;
   return SPECULA_OK;
 }
 

@@ -33,19 +33,47 @@ void note_cuda_error(cudaError_t e, const char *file, int line);
 
 namespace specula {
 
+// Every buffer the library allocates carries kGuardBytes of a fixed pattern
+// past its end.  A kernel that writes past its workspace lands there rather
+// than in a neighbouring allocation, which would not fault;
+// specula_check_guards compares the bands (api.cu keeps the live buffers).
+constexpr size_t kGuardBytes = 256;
+constexpr unsigned char kGuardByte = 0xA5;
+struct DevBuf;
+void guard_register(DevBuf *b);
+void guard_unregister(DevBuf *b);
+
 // A device buffer owned by a plan.
 struct DevBuf {
   void *p = nullptr;
   size_t bytes = 0;
+  int device = -1;
   DevBuf() = default;
   DevBuf(const DevBuf &) = delete;
   DevBuf &operator=(const DevBuf &) = delete;
-  ~DevBuf() { if (p) cudaFree(p); }
+  ~DevBuf() { release(); }
+  void release() {
+    if (!p) return;
+    guard_unregister(this);
+    cudaFree(p);
+    p = nullptr;
+  }
   int alloc(size_t n) {
-    if (p) { cudaFree(p); p = nullptr; }
+    release();
     bytes = n;
     if (n == 0) return SPECULA_OK;
-    return cudaMalloc(&p, n) == cudaSuccess ? SPECULA_OK : SPECULA_ENOMEM;
+    if (cudaMalloc(&p, n + kGuardBytes) != cudaSuccess) {
+      p = nullptr;
+      return SPECULA_ENOMEM;
+    }
+    if (cudaGetDevice(&device) != cudaSuccess ||
+        cudaMemset(static_cast<char *>(p) + n, kGuardByte, kGuardBytes) != cudaSuccess) {
+      cudaFree(p);
+      p = nullptr;
+      return SPECULA_ECUDA;
+    }
+    guard_register(this);
+    return SPECULA_OK;
   }
   int upload(const void *h, size_t n) {
     int s = alloc(n);

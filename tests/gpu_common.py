@@ -23,6 +23,14 @@ def load_pkg():
     return sp
 
 
+def close_checked(sp, ctx):
+    """Close a test module's context after checking that no kernel wrote into
+    the guard band past any library workspace."""
+    n_checked, n_bad = sp.specula_check_guards(ctx)
+    ctx.close()
+    assert n_bad == 0, f"{n_bad} of {n_checked} workspace guard bands overwritten"
+
+
 def norm_intensity_error(got, ref):
     """max |I/sum I - I_ref/sum I_ref| / max(I_ref/sum I_ref): the normalised-
     intensity relative error (per-pixel relative error is meaningless at dark

@@ -6,7 +6,7 @@ import numpy as np
 import pytest
 
 import synth
-from gpu_common import load_pkg, need_gpu
+from gpu_common import close_checked, load_pkg, need_gpu
 from oracle import atmo, geometry, screens
 
 pytestmark = pytest.mark.gpu
@@ -18,7 +18,7 @@ def env():
     sp = load_pkg()
     ctx = sp.Context(0)
     yield torch, sp, ctx
-    ctx.close()
+    close_checked(sp, ctx)
 
 
 @pytest.mark.parametrize("n,eps,nsub", [(64, 0.0, 16), (160, 0.11, 40), (480, 0.28, 96),

@@ -2,7 +2,7 @@
 import numpy as np
 import pytest
 
-from gpu_common import load_pkg, need_gpu
+from gpu_common import close_checked, load_pkg, need_gpu
 from oracle import calib, geometry, modal
 
 pytestmark = pytest.mark.gpu
@@ -16,7 +16,7 @@ def env():
     sp = load_pkg()
     ctx = sp.Context(0)
     yield torch, sp, ctx
-    ctx.close()
+    close_checked(sp, ctx)
 
 
 def _gpu_im(torch, sp, ctx, n, obsc, nsub, nmod, r, nm, a):

@@ -5,7 +5,7 @@ float32 readout normal's last-bit differences."""
 import numpy as np
 import pytest
 
-from gpu_common import load_pkg, need_gpu
+from gpu_common import close_checked, load_pkg, need_gpu
 from oracle import ccd
 
 pytestmark = pytest.mark.gpu
@@ -17,7 +17,7 @@ def env():
     sp = load_pkg()
     ctx = sp.Context(0)
     yield torch, sp, ctx
-    ctx.close()
+    close_checked(sp, ctx)
 
 
 def _det(torch, n):

@@ -9,7 +9,7 @@ from types import SimpleNamespace as NS
 import numpy as np
 import pytest
 
-from gpu_common import kolmogorov_phase, load_pkg, need_gpu, norm_intensity_error
+from gpu_common import close_checked, kolmogorov_phase, load_pkg, need_gpu, norm_intensity_error
 from oracle import atmo, pyramid, recon
 
 pytestmark = pytest.mark.gpu
@@ -21,7 +21,7 @@ def env():
     sp = load_pkg()
     ctx = sp.Context(0)
     yield torch, sp, ctx
-    ctx.close()
+    close_checked(sp, ctx)
 
 
 def _ptr(t):
@@ -133,3 +133,19 @@ def test_extraction_at_the_layer_limit(env):
                                 sp.PupilDesc(8193, 0.07, 0.0), 0.3,
                                 torch.empty(8193 * 8193, device="cuda"))
     assert e.value.status == sp.EUNSUPPORTED
+
+
+def test_guard_bands_cover_the_workspaces(env):
+    """Plans at padding 3 and 4 (the sizes an undersized per-point buffer
+    once overran) leave every workspace guard band intact."""
+    torch, sp, ctx = env
+    for pad, n, nsub, dist in ((3, 80, 16, 40), (4, 32, 8, 16)):
+        pu = sp.PupilDesc(n, 0.1, 0.1)
+        pw = sp.PwfsDesc(pad, 6, nsub, dist, 2.0)
+        sp.specula_pwfs_plan(ctx, pu, pw)
+        amp = torch.empty(n, n, device="cuda")
+        sp.specula_pupil_mask(ctx, pu, amp)
+        det = torch.empty(pad * nsub, pad * nsub, device="cuda")
+        sp.specula_pwfs_image(ctx, pu, pw, amp, torch.zeros(n, n, device="cuda"), det)
+    n_checked, n_bad = sp.specula_check_guards(ctx)
+    assert n_checked >= 8 and n_bad == 0

@@ -4,7 +4,7 @@ import numpy as np
 import pytest
 
 import synth
-from gpu_common import load_pkg, need_gpu, norm_intensity_error
+from gpu_common import close_checked, load_pkg, need_gpu, norm_intensity_error
 from oracle import atmo, geometry, pyramid, recon, slopes
 
 pytestmark = pytest.mark.gpu
@@ -16,7 +16,7 @@ def env():
     sp = load_pkg()
     ctx = sp.Context(0)
     yield torch, sp, ctx
-    ctx.close()
+    close_checked(sp, ctx)
 
 
 @pytest.mark.parametrize("name", ["pwfs8m_tiny", "pwfs8m"])

@@ -3,7 +3,7 @@ bf16-rounded operands.  FP32 accumulation: |C - ref| <= 2e-5 sum_k |a_ik b_jk|."
 import numpy as np
 import pytest
 
-from gpu_common import load_pkg, need_gpu
+from gpu_common import close_checked, load_pkg, need_gpu
 
 pytestmark = pytest.mark.gpu
 
@@ -14,7 +14,7 @@ def env():
     sp = load_pkg()
     ctx = sp.Context(0)
     yield torch, sp, ctx
-    ctx.close()
+    close_checked(sp, ctx)
 
 
 @pytest.mark.parametrize("M,N,K,splits", [(128, 128, 64, 1), (128, 128, 256, 1),

@@ -10,7 +10,7 @@ import numpy as np
 import pytest
 
 import synth
-from gpu_common import load_pkg, need_gpu
+from gpu_common import close_checked, load_pkg, need_gpu
 from oracle import modal
 
 pytestmark = pytest.mark.gpu
@@ -25,7 +25,7 @@ def pipe():
     wl = synth.workload("learned8m")
     p = LearnedPipeline(ctx, wl, n_modes=200, hidden=(512, 512))
     yield torch, sp, ctx, p
-    ctx.close()
+    close_checked(sp, ctx)
 
 
 def test_labels_are_modal_projections(pipe):

@@ -12,7 +12,7 @@ import numpy as np
 import pytest
 
 import synth
-from gpu_common import load_pkg, need_gpu
+from gpu_common import close_checked, load_pkg, need_gpu
 from oracle import loop as oloop
 
 pytestmark = pytest.mark.gpu
@@ -26,7 +26,7 @@ def env():
     sp = load_pkg()
     ctx = sp.Context(0)
     yield torch, sp, ctx
-    ctx.close()
+    close_checked(sp, ctx)
 
 
 @pytest.fixture(scope="module")

@@ -7,7 +7,7 @@ checked tightly on identical gradients."""
 import numpy as np
 import pytest
 
-from gpu_common import load_pkg, need_gpu
+from gpu_common import close_checked, load_pkg, need_gpu
 from oracle import mlp as omlp
 
 pytestmark = pytest.mark.gpu
@@ -21,7 +21,7 @@ def env():
     sp = load_pkg()
     ctx = sp.Context(0)
     yield torch, sp, ctx
-    ctx.close()
+    close_checked(sp, ctx)
 
 
 def _params32(sizes, seed):

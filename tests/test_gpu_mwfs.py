@@ -6,7 +6,7 @@ import numpy as np
 import pytest
 
 import synth
-from gpu_common import load_pkg, need_gpu, norm_intensity_error
+from gpu_common import close_checked, load_pkg, need_gpu, norm_intensity_error
 from oracle import atmo, geometry, pyramid, recon, sh, slopes, system
 
 pytestmark = pytest.mark.gpu
@@ -18,7 +18,7 @@ def env():
     sp = load_pkg()
     ctx = sp.Context(0)
     yield torch, sp, ctx
-    ctx.close()
+    close_checked(sp, ctx)
 
 
 @pytest.fixture(scope="module")

@@ -11,7 +11,8 @@ import math
 import numpy as np
 import pytest
 
-from gpu_common import kolmogorov_phase, load_pkg, need_gpu, norm_intensity_error, pupil_amp
+from gpu_common import (close_checked, kolmogorov_phase, load_pkg,
+                        need_gpu, norm_intensity_error, pupil_amp)
 from oracle import geometry, pyramid, slopes
 
 pytestmark = pytest.mark.gpu
@@ -33,7 +34,7 @@ def env():
     sp = load_pkg()
     ctx = sp.Context(0)
     yield torch, sp, ctx
-    ctx.close()
+    close_checked(sp, ctx)
 
 
 def _run(torch, sp, ctx, n_pix, n_mod, r, obsc, n_sub, phases, chunk=None, ka=None,

@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 
 import synth
-from gpu_common import kolmogorov_phase, load_pkg, need_gpu, norm_intensity_error
+from gpu_common import close_checked, kolmogorov_phase, load_pkg, need_gpu, norm_intensity_error
 from oracle import atmo, geometry, pyramid, recon, slopes
 
 pytestmark = pytest.mark.gpu
@@ -24,7 +24,7 @@ def env():
     sp = load_pkg()
     ctx = sp.Context(0)
     yield torch, sp, ctx
-    ctx.close()
+    close_checked(sp, ctx)
 
 
 @pytest.mark.parametrize("case", CASES, ids=lambda c: f"np{c[0]}_pad{c[1]}_pd{c[2]}")

@@ -5,7 +5,7 @@ the monochromatic image; both modulation forms; batch of two."""
 import numpy as np
 import pytest
 
-from gpu_common import kolmogorov_phase, load_pkg, need_gpu, norm_intensity_error
+from gpu_common import close_checked, kolmogorov_phase, load_pkg, need_gpu, norm_intensity_error
 from oracle import pyramid
 
 pytestmark = pytest.mark.gpu
@@ -20,7 +20,7 @@ def env():
     sp = load_pkg()
     ctx = sp.Context(0)
     yield torch, sp, ctx
-    ctx.close()
+    close_checked(sp, ctx)
 
 
 @pytest.mark.parametrize("n_pix,n_mod,r,obsc,n_sub,form", [

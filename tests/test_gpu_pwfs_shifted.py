@@ -6,7 +6,7 @@ point in FP32; the tilt form does two forward and one inverse)."""
 import numpy as np
 import pytest
 
-from gpu_common import kolmogorov_phase, load_pkg, need_gpu, norm_intensity_error
+from gpu_common import close_checked, kolmogorov_phase, load_pkg, need_gpu, norm_intensity_error
 from oracle import pyramid
 
 pytestmark = pytest.mark.gpu
@@ -28,7 +28,7 @@ def env():
     sp = load_pkg()
     ctx = sp.Context(0)
     yield torch, sp, ctx
-    ctx.close()
+    close_checked(sp, ctx)
 
 
 def _image(torch, sp, ctx, n_pix, n_mod, r, obsc, n_sub, phases, form):

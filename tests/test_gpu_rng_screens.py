@@ -4,7 +4,7 @@ import math
 import numpy as np
 import pytest
 
-from gpu_common import load_pkg, need_gpu
+from gpu_common import close_checked, load_pkg, need_gpu
 from oracle import philox, screens
 
 pytestmark = pytest.mark.gpu
@@ -16,7 +16,7 @@ def env():
     sp = load_pkg()
     ctx = sp.Context(0)
     yield torch, sp, ctx
-    ctx.close()
+    close_checked(sp, ctx)
 
 
 def test_rng_matches_oracle(env):

@@ -2,7 +2,7 @@
 import numpy as np
 import pytest
 
-from gpu_common import kolmogorov_phase, load_pkg, need_gpu, pupil_amp
+from gpu_common import close_checked, kolmogorov_phase, load_pkg, need_gpu, pupil_amp
 from oracle import geometry, recon, sh, slopes
 
 pytestmark = pytest.mark.gpu
@@ -14,7 +14,7 @@ def env():
     sp = load_pkg()
     ctx = sp.Context(0)
     yield torch, sp, ctx
-    ctx.close()
+    close_checked(sp, ctx)
 
 
 @pytest.mark.parametrize("n_sub,sub_pix,fft_n,obsc,nb", [(10, 8, 16, 0.2, 2), (68, 12, 24, 0.28, 1)])
