@@ -756,6 +756,7 @@ def gpu_leg(args, ws, rank, local):
         gbs = rb * kern["recon"]["launches"] / (kern["recon"]["total_ms"] / 1e3) / 1e9
         kern["recon"]["achieved_gbs"] = gbs
         kern["recon"]["hbm_frac"] = gbs / pk["hbm_gbs"]
+        kern["recon"]["traffic"] = traffic.get(("recon", WORKLOAD))
 
     # ---- end to end through the public API with host buffers: per frame the
     # time goes host -> device, the captured frame runs, the modes come back
