@@ -62,4 +62,11 @@ Modules and their pins (tests/test_oracle_*.py):
                 and its residual RMS / Strehl ratio; pinned to the scalar
                 recursion of an ideal sensor on a static modal aberration,
                 the zero-gain identity and closed-form statistics.
+* ``infinite``  infinite phase screens grown line by line from the Gaussian
+                conditional on a stencil of lines; pinned to a numerical
+                Hankel transform of the screens' spectrum, the variance
+                integral, the small-separation Bessel expansion, the joint
+                covariance and the precision-matrix form of the conditional,
+                exact mirror / transpose identities, and the structure
+                function of a long grown strip.
 """
