@@ -409,6 +409,68 @@ def closed_loop_leg(ctx, steps=400, settle=150):
     return out
 
 
+def infinite_leg(ctx, st, flush, steps):
+    """The 8 m pyramid frame on infinite screens: 256 px rings, two stencil
+    lines; before each frame the host picks the lines the footprints need and
+    the line kernel grows them, then the captured frame runs.  Timed from
+    10 s of flow on (every layer growing), growth inside the events."""
+    import torch
+    import synth
+    import paper_2602_06688_gb300 as sp
+    from paper_2602_06688_gb300.frame import PwfsFrame
+    wl = synth.workload("pwfs8m")
+    fi = PwfsFrame(ctx, wl, infinite=dict(side=256, n_st=2, seed=4))
+    g = fi.capture(st)
+    t0 = 10.0
+    with torch.cuda.stream(st):
+        for k in range(5):
+            fi.replay(t0 + k * wl.dt_s, st)
+    torch.cuda.synchronize()
+    n0 = fi.inf.lines_grown
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    launches = 0
+    with torch.cuda.stream(st):
+        for k in range(steps):
+            flush.zero_()
+            fi.t_dev.fill_(t0 + (k + 5) * wl.dt_s)
+            ev[k][0].record(st)
+            launches += fi.inf.advance(t0 + (k + 5) * wl.dt_s, stream=st)
+            g.launch(st)
+            ev[k][1].record(st)
+    torch.cuda.synchronize()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    lines = fi.inf.lines_grown - n0
+    # the line kernel alone: one line in each of the three rings per call,
+    # 20 calls captured in a graph (device time without host issue)
+    A, B, _ = next(iter(fi.inf.ops.values()))
+    tasks = [(fi.screens[i], A, B, 1.0, 0, 1, 100 + i, 10 ** 6) for i in range(3)]
+    torch.cuda.synchronize()
+    sp.specula_graph_begin(ctx, st)
+    try:
+        for k in range(20):
+            sp.specula_infscreen_lines(ctx, 256, 2, tasks, seed=9, stream=st)
+    finally:
+        gl = sp.specula_graph_end(ctx, st)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(st):
+        for k in range(3):
+            gl.launch(st)
+        e0.record(st)
+        for k in range(10):
+            gl.launch(st)
+        e1.record(st)
+    torch.cuda.synchronize()
+    gl.close()
+    g.close()
+    return {"config": "pwfs8m frame (3 layers) on 256 px infinite rings, 2 stencil lines, "
+                      "from t = 10 s",
+            "frames_per_s": steps / (sum(ms) / 1e3), "ms_per_step": sum(ms) / steps,
+            "lines_per_frame": lines / steps, "line_calls_per_frame": launches / steps,
+            "line_call_us_3_rings": e0.elapsed_time(e1) / 200 * 1e3,
+            "note": "the periodic pwfs8m frame (1024 px screens) is systems.pwfs8m"}
+
+
 def systems_leg(ctx, steps=50):
     """The other systems of the paper's scale list, one frame per step from a
     CUDA graph, L2 flushed between frames outside the events: the 8 m single
@@ -482,6 +544,7 @@ def systems_leg(ctx, steps=50):
                                "%d modes, FP32" % fs.n_modes,
                      "frames_per_s": steps / (sum(mss) / 1e3), "ms_per_step": sum(mss) / steps}
     gs.close()
+    out["infinite8m"] = infinite_leg(ctx, st, flush, steps)
     wl = synth.workload("mwfs39m")
     S = System(ctx, wl)
     res = {}

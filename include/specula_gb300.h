@@ -194,7 +194,8 @@ int specula_check_guards(specula_ctx *ctx, int32_t *n_checked, int32_t *n_bad);
 #define SPECULA_K_PWFS_SM_COLS  17  /* shifted-mask form: column pass, bins       */
 #define SPECULA_K_LOOP          18  /* closed loop: mirror shape, residual, update */
 #define SPECULA_K_CCD           19  /* detector photon and readout noise          */
-#define SPECULA_K_COUNT         20
+#define SPECULA_K_INFSCREEN     20  /* infinite screens: set-up and line growth   */
+#define SPECULA_K_COUNT         21
 
 /* Enable (capacity > 0: room for that many kernel records; allocates CUDA
  * events; set-up call) or disable (capacity = 0) per-kernel event timing.
@@ -316,6 +317,103 @@ int specula_screen_generate_batch(specula_ctx *ctx, int32_t n_screens, int32_t s
  * lambda). */
 int specula_random_phase(specula_ctx *ctx, const float *screens_dev, int32_t n, int32_t side,
                          int32_t n_pix, const float *scale_dev, float *phase_dev, void *stream);
+
+/* ---- infinite phase screens ----------------------------------------------
+ * InfinitePhaseScreen (Tab. 3) and AtmoInfiniteEvolution (Tab. 4).  The paper
+ * names them without their construction; this follows the conditional growth
+ * of Assemat, Wilson and Gendron (Optics Express 14, 988, 2006).  A screen is
+ * a side x side ring: line L (a row, axis 0, or a column, axis 1) sits at
+ * slot L mod side (rows: screen[slot][*], columns: screen[*][slot]).  It grows
+ * one line at a time.  Each new line Z is drawn from its Gaussian distribution
+ * given the stencil X: the n_st lines behind it, nearest first, full width.
+ *   Z = A X + b_scale B b,   A = C_ZX C_XX^+,   B = (C_ZZ - A C_XZ)^(1/2).
+ * Extraction reads such a ring unchanged: specula_atmo_extract's periodic
+ * addressing is the ring's. */
+
+/* Set-up: the operators of the draw.  C is the von Karman phase covariance, in
+ * rad^2 at 500 nm, of the spectrum of specula_screen_generate:
+ *   C(r) = 0.023 (2 pi / (2^(5/6) Gamma(11/6))) (L0/r0)^(5/3) x^(5/6) K_5/6(x),
+ *   x = 2 pi r / L0.
+ * Pixel p of a line lies at p pitch_m along it, and stencil line d (1..n_st)
+ * lies d pitch_m behind the new line; X index (d - 1) side + p.  C_XX^+ drops
+ * the eigenvalues at or below rcond times the largest.  B is the symmetric
+ * square root, with negative round-off eigenvalues set to 0.
+ * A_dev: side x (n_st side) floats, B_dev: side x side floats, row-major.
+ * A64_dev, B64_dev: optional float64 copies (NULL to skip).
+ * side 2..1024, n_st 1..4 and n_st < side, pitch_m, r0_m and L0_m finite and
+ * > 0, 0 < rcond < 1; else SPECULA_EINVAL.  A does not depend on r0, and B
+ * scales as r0^(-5/6): operators built for one r0 serve any layer through
+ * b_scale = (r0 / r0_layer)^(5/6).
+ * Set-up call: allocates float64 work arrays (about 3 (n_st side)^2 doubles),
+ * runs Jacobi eigen-decompositions and synchronises the stream. */
+int specula_infscreen_operators(specula_ctx *ctx, int32_t side, int32_t n_st, double pitch_m,
+                                double r0_m, double L0_m, double rcond, float *A_dev,
+                                float *B_dev, double *A64_dev, double *B64_dev, void *stream);
+
+#define SPECULA_INF_MAX_TASKS 32
+typedef struct {
+  float *screen_dev;      /* side x side float ring screen                      */
+  const float *A_dev;     /* operators of specula_infscreen_operators           */
+  const float *B_dev;
+  float b_scale;          /* noise scale, (r0_ops / r0_layer)^(5/6)             */
+  int32_t axis;           /* 0: add a row, 1: add a column                      */
+  int32_t direction;      /* +1: stencil lines L-1, L-2, ..; -1: L+1, L+2, ..   */
+  int32_t stream_id;      /* Philox counter word 3 (one per layer)              */
+  int64_t line;           /* the line L written (signed)                        */
+} specula_inf_line;
+
+/* Per-frame call: write one new line in each of n_tasks ring screens (0..32,
+ * distinct screen_dev, all of this side and n_st).  The noise b of line L:
+ * element p is normal (p mod 4) of the Philox4x32-10 counter (p / 4, L low 32
+ * bits, L high 32 bits, stream_id), key = seed, by Box-Muller with the
+ * uniforms (x + 0.5) 2^-32 (the transform of specula_rng_complex, evaluated
+ * here in float32).  If noise_dev is not NULL it is used instead:
+ * n_tasks x side floats, row t for task t.  The two dot products run in
+ * float32.  A line that depends on another line of the same screen needs a
+ * later call.  Enqueues one kernel; no allocation, no synchronisation.
+ * Errors: SPECULA_EINVAL for a bad size, axis, direction or repeated screen. */
+int specula_infscreen_lines(specula_ctx *ctx, int32_t side, int32_t n_st, int32_t n_tasks,
+                            const specula_inf_line *tasks, uint64_t seed, const float *noise_dev,
+                            void *stream);
+
+/* Ring planner (host only, no GPU): the lines a set of layers must grow so
+ * that each ring window covers its pupil footprint at time t.  For layer l
+ * and axis a (0: rows = y, 1: columns = x), lo[2 l + a] is the lowest line in
+ * the ring's window [lo, lo + side - 1].  A fresh ring from an FFT screen has
+ * lo = 0.  The footprint is the range of floor(u) that the extraction reads,
+ *   u = ((x s) + ((h theta) - (v t))) / pitch + side / 2,
+ * at the two pupil edges x = -+(n_pix - 1) / 2 pupil pitch, s = 1 - h / H, plus
+ * the bilinear neighbour, widened by `margin` lines on each side (0..64).  The
+ * moves are listed per layer in order: columns, then rows, each in growth
+ * order.  Growing down (direction -1) writes line lo - 1 from lines lo,
+ * lo + 1, ...; growing up writes line lo + side from the lines below it.  On
+ * success lo is updated and *n_moves is set.  If more than max_moves are
+ * needed, the call returns SPECULA_EUNSUPPORTED, sets *n_moves to the count
+ * needed and leaves lo unchanged.  A footprint wider than the ring also gives
+ * SPECULA_EUNSUPPORTED.  n_layers 0..32; layers' side is ignored (the ring's
+ * side is `side`). */
+typedef struct {
+  int32_t layer, axis, direction;
+  int64_t line;
+} specula_inf_move;
+int specula_infscreen_plan(int32_t n_layers, const specula_layer_desc *layers,
+                           const specula_source_desc *source, const specula_pupil_desc *pupil,
+                           int32_t side, int32_t margin, double t, int64_t *lo,
+                           int32_t max_moves, specula_inf_move *moves, int32_t *n_moves);
+
+/* Per-frame call: plan as specula_infscreen_plan (no move limit), then grow
+ * the lines.  Round k is one specula_infscreen_lines call carrying the k-th
+ * move of every layer, with stream_id = 2 layer + axis and b_scale[l].
+ * screens_dev, A_dev, B_dev: host arrays of n_layers device pointers (rings
+ * of this side; operators of this side and n_st).  *n_calls (may be NULL)
+ * is set to the number of calls.  lo is updated once every call has been
+ * enqueued.  Enqueues kernels only; host work is the plan. */
+int specula_infscreen_advance(specula_ctx *ctx, int32_t n_layers, const specula_layer_desc *layers,
+                              const specula_source_desc *source, const specula_pupil_desc *pupil,
+                              int32_t side, int32_t n_st, int32_t margin,
+                              float *const *screens_dev, const float *const *A_dev,
+                              const float *const *B_dev, const float *b_scale, int64_t *lo,
+                              double t, uint64_t seed, int32_t *n_calls, void *stream);
 
 /* ---- per-frame calls ------------------------------------------------------- */
 

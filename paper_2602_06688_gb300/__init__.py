@@ -13,7 +13,8 @@ import numpy as np
 
 from . import _abi
 from ._abi import (  # noqa: F401
-    PupilDesc, SourceDesc, LayerDesc, PwfsDesc, ShDesc, SlopecDesc, ReconDesc, WfsDesc,
+    PupilDesc, SourceDesc, LayerDesc, PwfsDesc, ShDesc, SlopecDesc, ReconDesc, WfsDesc, InfLine,
+    InfMove, INF_MAX_TASKS,
     SpeculaError, SLOPES_PYR, SLOPES_SH, SLOPES_PYR_MAPS, PWFS_FORM_TILT, PWFS_FORM_SHIFTED, PREC_FP32, PREC_BF16,
     PREC_BF16X2,
     OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED, ENONFINITE, ENOPLAN,
@@ -143,12 +144,13 @@ def specula_check_guards(ctx):
 
 (K_PWFS_ROWS_FWD, K_PWFS_COLS, K_PWFS_ROWS_INV, K_ATMO, K_SLOPES, K_RECON, K_SH,
  K_PWFS_FIELD, K_PWFS_BIN, K_CALIB, K_GEMM, K_MLP, K_MWFS, K_PWFS_ROWFILT,
- K_PWFS_COLFILT, K_PWFS_SM_FWD, K_PWFS_SM_ROWS, K_PWFS_SM_COLS, K_LOOP, K_CCD) = range(20)
-K_COUNT = 20
+ K_PWFS_COLFILT, K_PWFS_SM_FWD, K_PWFS_SM_ROWS, K_PWFS_SM_COLS, K_LOOP, K_CCD,
+ K_INFSCREEN) = range(21)
+K_COUNT = 21
 KERNEL_NAMES = ["pwfs_rows_fwd", "pwfs_cols", "pwfs_rows_inv", "atmo_extract", "slopes",
                 "recon", "sh_spots", "pwfs_field", "pwfs_bin", "calib", "gemm", "mlp", "mwfs",
                 "pwfs_rowfilt", "pwfs_colfilt_bin", "pwfs_sm_fwd", "pwfs_sm_rows",
-                "pwfs_sm_colfilt_bin", "loop", "ccd"]
+                "pwfs_sm_colfilt_bin", "loop", "ccd", "infscreen"]
 
 
 def specula_prof_enable(ctx, capacity):
@@ -528,6 +530,83 @@ def specula_loop_integrate(ctx, gain, leak, modes, cmd, stream=None):
     _abi.check(lib().specula_loop_integrate(
         ctx.handle, int(n), float(gain), float(leak), _dev(modes, torch.float32, n, "modes"),
         _dev(cmd, torch.float32, n, "cmd"), _stream(stream)), "specula_loop_integrate")
+
+
+def specula_infscreen_operators(ctx, side, n_st, pitch_m, r0_m, L0_m, rcond=1e-12,
+                                want_f64=False, stream=None):
+    """(A [side, n_st side], B [side, side]) float32 operators of the line draw
+    (plus their float64 copies when want_f64)."""
+    import torch
+    dev = torch.device("cuda", ctx.device)
+    A = torch.empty(side, n_st * side, device=dev)
+    B = torch.empty(side, side, device=dev)
+    A64 = torch.empty(side, n_st * side, dtype=torch.float64, device=dev) if want_f64 else None
+    B64 = torch.empty(side, side, dtype=torch.float64, device=dev) if want_f64 else None
+    _abi.check(lib().specula_infscreen_operators(
+        ctx.handle, int(side), int(n_st), float(pitch_m), float(r0_m), float(L0_m), float(rcond),
+        _dev(A), _dev(B), _dev(A64), _dev(B64), _stream(stream)), "specula_infscreen_operators")
+    return (A, B, A64, B64) if want_f64 else (A, B)
+
+
+def specula_infscreen_lines(ctx, side, n_st, tasks, seed=0, noise=None, stream=None):
+    """One new line per task; tasks: (screen, A, B, b_scale, axis, direction,
+    stream_id, line) tuples with distinct screens."""
+    import torch
+    if len(tasks) > INF_MAX_TASKS:
+        raise ValueError(f"at most {INF_MAX_TASKS} tasks per call")
+    arr = (InfLine * max(len(tasks), 1))()
+    for i, (scr, A, B, bs, axis, direction, sid, line) in enumerate(tasks):
+        arr[i] = InfLine(_dev(scr, torch.float32, side * side, "screen").value,
+                         _dev(A, torch.float32, side * side * n_st, "A").value,
+                         _dev(B, torch.float32, side * side, "B").value,
+                         float(bs), int(axis), int(direction), int(sid), int(line))
+    nz = _dev(noise, torch.float32, len(tasks) * side, "noise")
+    _abi.check(lib().specula_infscreen_lines(ctx.handle, int(side), int(n_st), len(tasks),
+                                             C.cast(arr, C.c_void_p), C.c_uint64(seed), nz,
+                                             _stream(stream)), "specula_infscreen_lines")
+
+
+def specula_infscreen_advance(ctx, layers, source, pupil, side, n_st, margin, screens, A, B,
+                              b_scale, lo, t, seed=0, stream=None):
+    """Plan and grow one frame's lines; lo (list of 2 n_layers ints) is
+    updated in place; returns the number of kernel calls.  A, B: one operator
+    tensor per layer."""
+    import torch
+    n = len(layers)
+    L = (LayerDesc * max(n, 1))(*layers)
+    lo_a = (C.c_int64 * max(2 * n, 1))(*lo)
+    scr = (C.c_void_p * max(n, 1))(*[_dev(x, torch.float32, side * side, "screen").value
+                                     for x in screens])
+    Ap = (C.c_void_p * max(n, 1))(*[_dev(x, torch.float32, side * side * n_st, "A").value
+                                    for x in A])
+    Bp = (C.c_void_p * max(n, 1))(*[_dev(x, torch.float32, side * side, "B").value for x in B])
+    bs = (C.c_float * max(n, 1))(*[float(x) for x in b_scale])
+    calls = C.c_int32()
+    _abi.check(lib().specula_infscreen_advance(
+        ctx.handle, n, C.cast(L, C.c_void_p), C.byref(source), C.byref(pupil), int(side),
+        int(n_st), int(margin), C.cast(scr, C.c_void_p), C.cast(Ap, C.c_void_p),
+        C.cast(Bp, C.c_void_p), C.cast(bs, C.c_void_p), C.cast(lo_a, C.c_void_p), float(t),
+        C.c_uint64(seed), C.byref(calls), _stream(stream)), "specula_infscreen_advance")
+    lo[:] = list(lo_a[:2 * n])
+    return calls.value
+
+
+def specula_infscreen_plan(layers, source, pupil, side, margin, t, lo, max_moves=4096):
+    """Host-only ring planner: (moves [(layer, axis, direction, line)], new lo).
+    layers: LayerDesc list; lo: list of 2 n_layers ints (rows, columns per
+    layer)."""
+    n = len(layers)
+    L = (LayerDesc * max(n, 1))(*layers)
+    lo_a = (C.c_int64 * max(2 * n, 1))(*lo)
+    mv = (InfMove * max(max_moves, 1))()
+    nm = C.c_int32()
+    _abi.check(lib().specula_infscreen_plan(n, C.cast(L, C.c_void_p), C.byref(source),
+                                            C.byref(pupil), int(side), int(margin), float(t),
+                                            C.cast(lo_a, C.c_void_p), int(max_moves),
+                                            C.cast(mv, C.c_void_p), C.byref(nm)),
+               "specula_infscreen_plan")
+    return ([(m.layer, m.axis, m.direction, m.line) for m in mv[:nm.value]],
+            list(lo_a[:2 * n]))
 
 
 def specula_recon_convert(ctx, R, precision, hi, lo=None, stream=None):

@@ -59,6 +59,19 @@ class ReconDesc(C.Structure):
                 ("R_lo_dev", C.c_void_p)]
 
 
+class InfLine(C.Structure):
+    _fields_ = [("screen_dev", C.c_void_p), ("A_dev", C.c_void_p), ("B_dev", C.c_void_p),
+                ("b_scale", C.c_float), ("axis", C.c_int32), ("direction", C.c_int32),
+                ("stream_id", C.c_int32), ("line", C.c_int64)]
+
+
+class InfMove(C.Structure):
+    _fields_ = [("layer", C.c_int32), ("axis", C.c_int32), ("direction", C.c_int32),
+                ("line", C.c_int64)]
+
+
+INF_MAX_TASKS = 32
+
 P = C.POINTER
 vp = C.c_void_p
 i32 = C.c_int32
@@ -107,6 +120,14 @@ SIGNATURES = {
                               vp, vp]),
     "specula_loop_residual": (C.c_int, [vp, i32, vp, vp, vp, C.c_double, vp, vp, vp]),
     "specula_loop_integrate": (C.c_int, [vp, i32, C.c_float, C.c_float, vp, vp, vp]),
+    "specula_infscreen_operators": (C.c_int, [vp, i32, i32, dbl, dbl, dbl, dbl, vp, vp, vp, vp,
+                                              vp]),
+    "specula_infscreen_lines": (C.c_int, [vp, i32, i32, i32, vp, C.c_uint64, vp, vp]),
+    "specula_infscreen_plan": (C.c_int, [i32, vp, P(SourceDesc), P(PupilDesc), i32, i32, dbl, vp,
+                                         i32, vp, P(i32)]),
+    "specula_infscreen_advance": (C.c_int, [vp, i32, vp, P(SourceDesc), P(PupilDesc), i32, i32,
+                                            i32, vp, vp, vp, vp, vp, dbl, C.c_uint64, P(i32),
+                                            vp]),
     "specula_pwfs_get_tiles": (C.c_int, [vp, P(PupilDesc), P(PwfsDesc), P(i32), P(i32),
                                          P(i32)]),
     "specula_pwfs_autotune": (C.c_int, [vp, P(PupilDesc), P(PwfsDesc), vp, vp, i32, vp, i32,

@@ -147,9 +147,8 @@ __global__ void __launch_bounds__(256) k_gemm_f64(const double *__restrict__ X, 
     }
 }
 
-static int gemm_f64(specula_ctx *ctx, cudaStream_t st, const double *X, long xi, long xk,
-                    const double *Y, long yk, long yj, const double *d, double *C, int M, int N,
-                    int K) {
+int gemm_f64(specula_ctx *ctx, cudaStream_t st, const double *X, long xi, long xk,
+             const double *Y, long yk, long yj, const double *d, double *C, int M, int N, int K) {
   dim3 grid((N + GT - 1) / GT, (M + GT - 1) / GT);
   SPECULA_LAUNCH(ctx, SPECULA_K_CALIB, st,
                  k_gemm_f64<<<grid, 256, 0, st>>>(X, xi, xk, Y, yk, yj, d, C, M, N, K));
@@ -275,6 +274,43 @@ __global__ void k_f64_to_f32(const double *__restrict__ a, float *__restrict__ b
     b[i] = (float)a[i];
 }
 
+// Eigen-decomposition of the symmetric n x n float64 matrix G (row-major) by
+// parallel cyclic Jacobi: on return G's diagonal holds the eigenvalues and the
+// columns of V the eigenvectors.  Sweeps until the off-diagonal squared norm
+// is below 1e-30 of the total (at most 40); synchronises the stream per sweep.
+int sym_eig_f64(specula_ctx *ctx, cudaStream_t st, double *G_, double *V_, int n) {
+  DevBuf PQ, CS, NRM;
+  const int np = n + (n & 1);
+  int s;
+  if ((s = PQ.alloc((size_t)np / 2 * sizeof(int2)))) return s;
+  if ((s = CS.alloc((size_t)np / 2 * sizeof(double2)))) return s;
+  if ((s = NRM.alloc(2 * sizeof(double)))) return s;
+  SPECULA_LAUNCH(ctx, SPECULA_K_CALIB, st,
+                 k_identity<<<(unsigned)(((size_t)n * n + 255) / 256), 256, 0, st>>>(V_, n));
+  const int npairs = np / 2;
+  const dim3 gr((n + 255) / 256, npairs);
+  for (int sweep = 0; sweep < 40; ++sweep) {
+    for (int r = 0; r < np - 1; ++r) {
+      SPECULA_LAUNCH(ctx, SPECULA_K_CALIB, st,
+                     k_jacobi_params<<<(npairs + 127) / 128, 128, 0, st>>>(
+                         G_, n, np, r, PQ.as<int2>(), CS.as<double2>()));
+      SPECULA_LAUNCH(ctx, SPECULA_K_CALIB, st,
+                     k_jacobi_rows<<<gr, 256, 0, st>>>(G_, n, PQ.as<int2>(),
+                                                       CS.as<double2>()));
+      SPECULA_LAUNCH(ctx, SPECULA_K_CALIB, st,
+                     k_jacobi_cols<<<gr, 256, 0, st>>>(G_, V_, n,
+                                                       PQ.as<int2>(), CS.as<double2>()));
+    }
+    SPECULA_LAUNCH(ctx, SPECULA_K_CALIB, st,
+                   k_offnorm<<<1, 256, 0, st>>>(G_, n, NRM.as<double>()));
+    double h[2];
+    SPECULA_CK(cudaMemcpyAsync(h, NRM.p, sizeof(h), cudaMemcpyDeviceToHost, st));
+    SPECULA_CK(cudaStreamSynchronize(st));
+    if (!(h[0] > 1e-30 * h[1])) break;
+  }
+  return SPECULA_OK;
+}
+
 }  // namespace specula
 
 using namespace specula;
@@ -355,41 +391,15 @@ extern "C" int specula_pinv_fp64(specula_ctx *ctx, const double *A_dev, int32_t 
   if (m < 1 || n < 1 || n > 8192 || !(rcond > 0) || !(rcond < 1)) return SPECULA_EINVAL;
   SPECULA_CK(cudaSetDevice(ctx->device));
   cudaStream_t st = (cudaStream_t)stream;
-  DevBuf G, V, D, PQ, CS, NRM, RK;
-  const int np = n + (n & 1);
+  DevBuf G, V, D, RK;
   int s;
   if ((s = G.alloc((size_t)n * n * sizeof(double)))) return s;
   if ((s = V.alloc((size_t)n * n * sizeof(double)))) return s;
   if ((s = D.alloc((size_t)n * sizeof(double)))) return s;
-  if ((s = PQ.alloc((size_t)np / 2 * sizeof(int2)))) return s;
-  if ((s = CS.alloc((size_t)np / 2 * sizeof(double2)))) return s;
-  if ((s = NRM.alloc(2 * sizeof(double)))) return s;
   if ((s = RK.alloc(sizeof(int)))) return s;
   // G = A^T A
   if ((s = gemm_f64(ctx, st, A_dev, 1, n, A_dev, n, 1, nullptr, G.as<double>(), n, n, m))) return s;
-  SPECULA_LAUNCH(ctx, SPECULA_K_CALIB, st,
-                 k_identity<<<(unsigned)(((size_t)n * n + 255) / 256), 256, 0, st>>>(V.as<double>(), n));
-  const int npairs = np / 2;
-  const dim3 gr((n + 255) / 256, npairs);
-  for (int sweep = 0; sweep < 40; ++sweep) {
-    for (int r = 0; r < np - 1; ++r) {
-      SPECULA_LAUNCH(ctx, SPECULA_K_CALIB, st,
-                     k_jacobi_params<<<(npairs + 127) / 128, 128, 0, st>>>(
-                         G.as<double>(), n, np, r, PQ.as<int2>(), CS.as<double2>()));
-      SPECULA_LAUNCH(ctx, SPECULA_K_CALIB, st,
-                     k_jacobi_rows<<<gr, 256, 0, st>>>(G.as<double>(), n, PQ.as<int2>(),
-                                                       CS.as<double2>()));
-      SPECULA_LAUNCH(ctx, SPECULA_K_CALIB, st,
-                     k_jacobi_cols<<<gr, 256, 0, st>>>(G.as<double>(), V.as<double>(), n,
-                                                       PQ.as<int2>(), CS.as<double2>()));
-    }
-    SPECULA_LAUNCH(ctx, SPECULA_K_CALIB, st,
-                   k_offnorm<<<1, 256, 0, st>>>(G.as<double>(), n, NRM.as<double>()));
-    double h[2];
-    SPECULA_CK(cudaMemcpyAsync(h, NRM.p, sizeof(h), cudaMemcpyDeviceToHost, st));
-    SPECULA_CK(cudaStreamSynchronize(st));
-    if (!(h[0] > 1e-30 * h[1])) break;
-  }
+  if ((s = sym_eig_f64(ctx, st, G.as<double>(), V.as<double>(), n))) return s;
   SPECULA_LAUNCH(ctx, SPECULA_K_CALIB, st,
                  k_inv_eigs<<<1, 256, 0, st>>>(G.as<double>(), n, rcond, D.as<double>(),
                                                RK.as<int>()));

@@ -181,6 +181,13 @@ inline void prof_end(specula_ctx *c, int slot, int kid, cudaStream_t st) {
 int pwfs_init_device();
 int sh_init_device();
 int mwfs_init_device();
+// float64 helpers of the calibration file, shared with the infinite screens:
+// C[i][j] = sum_k X(i,k) d(k) Y(k,j), X(i,k) = X[i xi + k xk], Y(k,j) = Y[k yk + j yj]
+// (d may be NULL); and the Jacobi eigen-decomposition of a symmetric matrix
+// (eigenvalues on G's diagonal, eigenvectors in V's columns).
+int gemm_f64(specula_ctx *ctx, cudaStream_t st, const double *X, long xi, long xk,
+             const double *Y, long yk, long yj, const double *d, double *C, int M, int N, int K);
+int sym_eig_f64(specula_ctx *ctx, cudaStream_t st, double *G, double *V, int n);
 constexpr int kLoopMaxBlocks = 512;
 int loop_alloc_workspace(specula_ctx *ctx);
 int pwfs_shifted_init_device();

@@ -4,6 +4,7 @@
 // c <- (hi1 ^ c1 ^ k0, lo1, hi0 ^ c3 ^ k1, lo0), the key bumped by the Weyl
 // constants between rounds; uniforms (x + 0.5) 2^-32.
 #pragma once
+#include <math.h>
 #include <stdint.h>
 
 namespace specula {
@@ -28,6 +29,22 @@ __device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32
 
 __device__ __forceinline__ double philox_uniform(uint32_t x) {
   return ((double)x + 0.5) * (1.0 / 4294967296.0);
+}
+
+// Four standard normals from counter c (Box-Muller on the uniforms of words
+// 0/1 and 2/3, in float64): (r0 cos 2 pi u1, r0 sin 2 pi u1, r1 cos 2 pi u3,
+// r1 sin 2 pi u3), r = sqrt(-2 ln u).
+__device__ __forceinline__ void philox_normals4(uint32_t c[4], uint64_t seed, double g[4]) {
+  philox4x32_10(c, (uint32_t)seed, (uint32_t)(seed >> 32));
+  double u[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) u[i] = philox_uniform(c[i]);
+  const double r0 = sqrt(-2.0 * log(u[0])), r1 = sqrt(-2.0 * log(u[2]));
+  const double t0 = 2.0 * M_PI * u[1], t1 = 2.0 * M_PI * u[3];
+  g[0] = r0 * cos(t0);
+  g[1] = r0 * sin(t0);
+  g[2] = r1 * cos(t1);
+  g[3] = r1 * sin(t1);
 }
 
 }  // namespace specula

@@ -106,16 +106,7 @@ __global__ void k_screen_final(const double2 *__restrict__ T, const double2 *__r
 __device__ __forceinline__ void normals4(uint64_t pair, uint32_t sample, uint32_t stream,
                                          uint64_t seed, double g[4]) {
   uint32_t c[4] = {(uint32_t)pair, (uint32_t)(pair >> 32), sample, stream};
-  philox4x32_10(c, (uint32_t)seed, (uint32_t)(seed >> 32));
-  double u[4];
-#pragma unroll
-  for (int i = 0; i < 4; ++i) u[i] = ((double)c[i] + 0.5) * (1.0 / 4294967296.0);
-  const double r0 = sqrt(-2.0 * log(u[0])), r1 = sqrt(-2.0 * log(u[2]));
-  const double t0 = 2.0 * M_PI * u[1], t1 = 2.0 * M_PI * u[3];
-  g[0] = r0 * cos(t0);
-  g[1] = r0 * sin(t0);
-  g[2] = r1 * cos(t1);
-  g[3] = r1 * sin(t1);
+  philox_normals4(c, seed, g);
 }
 
 // n complex normals per sample: element 2i, 2i+1 from counter i

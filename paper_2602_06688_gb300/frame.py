@@ -25,7 +25,8 @@ def seeded_reconstructor(n_modes, n_slopes, seed):
 
 class PwfsFrame:
     def __init__(self, ctx, wl, sensor=0, precision=PREC_FP32, R=None, n_modes=None,
-                 seed_offset=0, device="cuda", autotune=False, batch=1, noise=None):
+                 seed_offset=0, device="cuda", autotune=False, batch=1, noise=None,
+                 infinite=None):
         """batch > 1: every step computes `batch` consecutive frames (times t,
         t + dt, ...) of the open-loop sequence together: one extraction per
         frame, then one pyramid call, one slope call and one MVM call over
@@ -34,7 +35,12 @@ class PwfsFrame:
         noise: None (noise-free detector) or a dict with ``photons`` (per frame
         over the pupil), ``qe``, ``ron`` (electrons RMS) and ``seed``: the
         detector image then carries photon and readout noise (the CCD call),
-        frame index round(t / dt)."""
+        frame index round(t / dt).
+
+        infinite: None (periodic FFT screens of the workload's side) or a dict
+        with ``side`` (ring side), ``n_st`` (stencil lines, default 2) and
+        ``seed``: the layers then run on infinite screens, grown before each
+        frame (batch 1 only)."""
         import torch
         self.torch = torch
         self.ctx = ctx
@@ -48,8 +54,18 @@ class PwfsFrame:
         self.layers = [layer_desc(l) for l in wl.layers]
         n = s.pupil.n_pix
         self.n_pix = n
-        self.screens = []
-        for l in wl.layers:
+        self.inf = None
+        if infinite:
+            if batch != 1:
+                raise ValueError("infinite screens run one frame per step")
+            from .infinite import InfiniteAtmosphere
+            self.inf = InfiniteAtmosphere(ctx, wl.layers, s.source, s.pupil, infinite["side"],
+                                          n_st=infinite.get("n_st", 2),
+                                          seed=infinite.get("seed", 1), device=device)
+            for d in self.layers:
+                d.side = self.inf.side
+        self.screens = [] if self.inf is None else self.inf.screens
+        for l in (wl.layers if self.inf is None else ()):
             scr_noise = torch.tensor(synth.screen_noise(l.seed + seed_offset, l.side),
                                      device=device)
             scr = torch.empty(l.side, l.side, device=device, dtype=torch.float32)
@@ -150,6 +166,8 @@ class PwfsFrame:
     def replay(self, t, stream):
         """Set the frame time and launch the captured frame on `stream`."""
         torch = self.torch
+        if self.inf is not None:
+            self.inf.advance(t, stream=stream)
         with torch.cuda.stream(stream):
             if self.noise:
                 self.frame_dev.fill_(int(round(t / self.dt)))
@@ -166,6 +184,8 @@ class PwfsFrame:
         batch > 1 the frames at t, t + dt, ... (t_dev: one device time per
         frame)."""
         ctx = self.ctx
+        if self.inf is not None and t_dev is None:
+            self.inf.advance(t, stream=stream)
         if self.batch == 1:
             specula_atmo_extract(ctx, self.layers, self.screens, self.src, self.pupil, t,
                                  self.phase, t_dev=t_dev, stream=stream)
