@@ -36,6 +36,10 @@ Modules and their pins (tests/test_oracle_*.py):
 * ``sh``        Shack-Hartmann spots; pinned to zero centroid for a flat
                 wavefront, exact circular roll under an integer tilt, and
                 per-subaperture Parseval flux.
+* ``pyramid.rebin_area``  area-weighted detector rebinning for a
+                non-integer pixel ratio; pinned to exact rational interval
+                overlaps, block binning at integer ratios, flux, a constant
+                image and a hand-placed point source.
 * ``slopes``    pyramid and centre-of-gravity slopes; pinned through the
                 pyramid / SH invariants above and hand-computed detectors.
 * ``recon``     modal reconstructor MVM; pinned to a direct sum.

@@ -83,6 +83,27 @@ def bin_image(I: np.ndarray, b: int) -> np.ndarray:
     return I.reshape(k, b, k, b).sum(axis=(1, 3))
 
 
+def rebin_weights(n_in: int, n_out: int) -> np.ndarray:
+    """W[I, i] = length of [i, i + 1) inside [I b, (I + 1) b), b = n_in / n_out
+    (grid-pixel units): the share of grid pixel i that detector pixel I
+    collects.  Computed exactly in units of 1 / n_out, then divided."""
+    I = np.arange(n_out)[:, None]
+    i = np.arange(n_in)[None, :]
+    lo = np.maximum(i * n_out, I * n_in)
+    hi = np.minimum((i + 1) * n_out, (I + 1) * n_in)
+    return np.maximum(hi - lo, 0).astype(np.float64) / n_out
+
+
+def rebin_area(img: np.ndarray, n_out: int) -> np.ndarray:
+    """Area-weighted rebinning of a square image (n_in x n_in, intensity
+    constant over each grid pixel) to n_out x n_out detector pixels that tile
+    the same field: D = W img W^T.  Flux is kept; an integer ratio is b x b
+    binning.  This is the detector sampling a pyramid's output_resolution
+    asks for when it is not a whole fraction of the padded grid (Listing 2)."""
+    W = rebin_weights(img.shape[-1], n_out)
+    return W @ np.asarray(img, dtype=np.float64) @ W.T
+
+
 def pwfs_image(amp, phase, pad, n_mod, mod_amp, n_sub, pup_dist):
     """Detector image 2 n_sub x 2 n_sub (with pad = 2 and pup_dist = Np)."""
     Np = amp.shape[0]
