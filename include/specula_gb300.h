@@ -786,6 +786,20 @@ int specula_ccd(specula_ctx *ctx, int32_t n, const float *det_dev, double scale,
                 uint64_t seed, uint32_t frame, const uint32_t *frame_dev, float *out_dev,
                 void *stream);
 
+/* Detector sampling at a non-integer pixel ratio (a pyramid output_resolution
+ * that is not a whole fraction of the padded grid, Listing 2): area-weighted
+ * rebinning of n_batch square images n_in x n_in to n_out x n_out,
+ *   out[J][I] = sum_j sum_i wy(J, j) wx(I, i) in[j][i],
+ *   w(I, i) = |[i, i + 1) n [I b, (I + 1) b)|,   b = n_in / n_out,
+ * the grid pixel's area that detector pixel I collects (flux is kept; an
+ * integer b is b x b binning).  The overlaps are exact integers in units of
+ * 1/n_out; the sums run in float32, row by row in index order, scaled by
+ * 1/n_out^2.  in_dev, out_dev: n_batch images, row-major.  1 <= n_in, n_out
+ * <= 4096 (n_out > n_in spreads each grid pixel over several detector
+ * pixels); n_batch 0 is a no-op.  Per-frame call: one kernel. */
+int specula_rebin(specula_ctx *ctx, const float *in_dev, int32_t n_in, int32_t n_out,
+                  int32_t n_batch, float *out_dev, void *stream);
+
 /* ---- closed loop (per-frame calls: enqueue only, allocate nothing) ---------
  * The closed-loop objects of the SOUL example (App. B, Listing 2: a DM with a
  * modal influence-function basis, an IirFilter integrator, the ":-1" delayed

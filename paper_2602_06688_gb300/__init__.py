@@ -532,6 +532,17 @@ def specula_loop_integrate(ctx, gain, leak, modes, cmd, stream=None):
         _dev(cmd, torch.float32, n, "cmd"), _stream(stream)), "specula_loop_integrate")
 
 
+def specula_rebin(ctx, img, n_out, out, stream=None):
+    """Area-weighted rebinning of (..., n_in, n_in) images to (..., n_out, n_out)."""
+    import torch
+    n_in = img.shape[-1]
+    nb = img.numel() // (n_in * n_in)
+    _abi.check(lib().specula_rebin(ctx.handle, _dev(img, torch.float32, nb * n_in * n_in, "img"),
+                                   int(n_in), int(n_out), int(nb),
+                                   _dev(out, torch.float32, nb * n_out * n_out, "out"),
+                                   _stream(stream)), "specula_rebin")
+
+
 def specula_infscreen_operators(ctx, side, n_st, pitch_m, r0_m, L0_m, rcond=1e-12,
                                 want_f64=False, stream=None):
     """(A [side, n_st side], B [side, side]) float32 operators of the line draw

@@ -106,9 +106,55 @@ __global__ void __launch_bounds__(256) k_ccd(const float *__restrict__ det, floa
   out[p] = (float)__dadd_rn((double)k, rd);
 }
 
+// Area-weighted rebinning n_in -> n_out (detector sampling at a non-integer
+// pixel ratio): out[J][I] = sum_j sum_i wy(J, j) wx(I, i) in[j][i] with
+// w(I, i) = |[i, i + 1) n [I b, (I + 1) b)|, b = n_in / n_out.  In units of
+// 1 / n_out the overlaps are integers (n_in, n_out <= 4096 keep them exact in
+// float32); the sum is taken row by row in index order and scaled by
+// 1 / n_out^2 at the end.  One thread per output pixel.
+__global__ void k_rebin(const float *__restrict__ in, int n_in, int n_out, int n_batch,
+                        float *__restrict__ out) {
+  const size_t per = (size_t)n_out * n_out;
+  const float inv = 1.0f / ((float)n_out * (float)n_out);
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < per * n_batch;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const size_t b = e / per;
+    const int J = (int)((e % per) / n_out), I = (int)(e % n_out);
+    const float *src = in + b * (size_t)n_in * n_in;
+    const int j0 = (J * n_in) / n_out, j1 = ((J + 1) * n_in - 1) / n_out;
+    const int i0 = (I * n_in) / n_out, i1 = ((I + 1) * n_in - 1) / n_out;
+    float acc = 0.f;
+    for (int j = j0; j <= j1; ++j) {
+      const int wy = min((j + 1) * n_out, (J + 1) * n_in) - max(j * n_out, J * n_in);
+      float row = 0.f;
+      for (int i = i0; i <= i1; ++i) {
+        const int wx = min((i + 1) * n_out, (I + 1) * n_in) - max(i * n_out, I * n_in);
+        row = fmaf((float)wx, src[(size_t)j * n_in + i], row);
+      }
+      acc = fmaf((float)wy, row, acc);
+    }
+    out[e] = acc * inv;
+  }
+}
+
 }  // namespace specula
 
 using namespace specula;
+
+extern "C" int specula_rebin(specula_ctx *ctx, const float *in_dev, int32_t n_in, int32_t n_out,
+                             int32_t n_batch, float *out_dev, void *stream) {
+  if (!ctx || n_in < 1 || n_out < 1 || n_in > 4096 || n_out > 4096 || n_batch < 0)
+    return SPECULA_EINVAL;
+  if (n_batch == 0) return SPECULA_OK;
+  if (!in_dev || !out_dev) return SPECULA_EINVAL;
+  SPECULA_CK(cudaSetDevice(ctx->device));
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t n = (size_t)n_out * n_out * n_batch;
+  const unsigned grid = (unsigned)(n < (size_t)152 * 8 * 256 ? (n + 255) / 256 : 152 * 8);
+  SPECULA_LAUNCH(ctx, SPECULA_K_CCD, st,
+                 k_rebin<<<grid, 256, 0, st>>>(in_dev, n_in, n_out, n_batch, out_dev));
+  return SPECULA_OK;
+}
 
 extern "C" int specula_ccd(specula_ctx *ctx, int32_t n, const float *det_dev, double scale,
                            double ron, uint64_t seed, uint32_t frame, const uint32_t *frame_dev,
