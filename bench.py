@@ -77,7 +77,10 @@ def kernel_flops(wl):
 
 
 class ClockSampler:
-    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+    """nvidia-smi clock / throttle-reason samples every 20 ms, started before
+    the timed region (the first sample is awaited) and kept for the samples
+    whose timestamps fall inside it (mark_start / mark_end)."""
+    FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
               "clocks_event_reasons.sw_power_cap")
 
@@ -85,48 +88,74 @@ class ClockSampler:
         self.index = index
         self.proc = None
         self.lines = []
+        self.t0 = self.t1 = None
+        self._thread = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            if line.strip():
+                self.lines.append(line.strip())
 
     def __enter__(self):
+        import threading
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "20"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except (OSError, ValueError):
             self.proc = None
+            return self
+        self._thread = threading.Thread(target=self._read, daemon=True)
+        self._thread.start()
+        end = time.time() + 3.0
+        while not self.lines and time.time() < end and self.proc.poll() is None:
+            time.sleep(0.01)
         return self
+
+    def mark_start(self):
+        self.t0 = time.time()
+
+    def mark_end(self):
+        self.t1 = time.time()
 
     def __exit__(self, *a):
         if self.proc is None:
             return
-        time.sleep(0.3)
+        time.sleep(0.05)
         self.proc.terminate()
         try:
-            out, _ = self.proc.communicate(timeout=5)
+            self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
-            out, _ = self.proc.communicate()
-        self.lines = [l for l in out.splitlines() if l.strip()]
+            self.proc.wait()
+        if self._thread is not None:
+            self._thread.join(timeout=2)
 
     def summary(self):
-        sm, smax, reasons = [], [], set()
+        import datetime
+        rows = []
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for l in self.lines:
+        for l in list(self.lines):
             f = [x.strip() for x in l.split(",")]
-            if len(f) < 7:
+            if len(f) < 8:
                 continue
             try:
-                sm.append(float(f[0]))
-                smax.append(float(f[1]))
+                ts = datetime.datetime.strptime(f[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                rows.append((ts, float(f[1]), float(f[2]),
+                             {n for k, n in enumerate(names) if f[4 + k].lower().startswith("active")}))
             except ValueError:
                 continue
-            for k, name in enumerate(names):
-                if f[3 + k].lower().startswith("active"):
-                    reasons.add(name)
-        if not sm:
+        if not rows:
             return None
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
-                "reasons": sorted(reasons), "samples": len(sm)}
+        inside = [r for r in rows if self.t0 is not None and self.t1 is not None
+                  and self.t0 - 0.02 <= r[0] <= self.t1 + 0.02]
+        use = inside or rows
+        reasons = set().union(*[r[3] for r in use])
+        return {"sm_mhz": statistics.median(r[1] for r in use),
+                "sm_max_mhz": max(r[2] for r in use), "reasons": sorted(reasons),
+                "samples": len(use), "samples_in_timed_region": len(inside),
+                "interval_ms": 20}
 
 
 def read_traffic():
@@ -651,9 +680,11 @@ def gpu_leg(args, ws, rank, local):
         dist.barrier()
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
+        clk.mark_start()
         wall0 = time.perf_counter()
         ms = timed(K, W)
         wall1 = time.perf_counter()
+        clk.mark_end()
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -879,7 +910,7 @@ def gpu_leg(args, ws, rank, local):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=500)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="specula", choices=["specula", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
