@@ -819,8 +819,8 @@ def gpu_leg(args, ws, rank, local):
     traffic = read_traffic()
     # The FFT/mask/accumulate stage (the pyramid's 2D filter and |E|^2, one
     # launch of each of its kernels per frame) is the dominant work.  Its
-    # algorithmic FLOPs per frame follow the survey's convention: two full
-    # N x N transforms per modulation point, 5 N^2 log2(N^2) each, pruning
+    # algorithmic FLOPs per frame count two full N x N transforms per
+    # modulation point, 5 N^2 log2(N^2) each, pruning
     # and shared row filters not subtracted (so the rate compares with a
     # plain implementation); achieved = that count / the summed time of the
     # stage's kernels.

@@ -4,7 +4,8 @@ to modal coefficients, trained on simulator-generated pairs.
 Not in the paper (its reconstructor is the linear Modalrec, App. A, Tab. 4);
 the learned reconstructor, its sizes (2400 -> 1024 -> 1024 -> 500 and
 14000 -> 2048 -> 2048 -> 4000), BF16 weights with FP32 accumulation, batch
-256 and Adam come from the task's learned-reconstructor configuration.
+256 and Adam are this library's learned-reconstructor configuration (the
+learned8m workload and the ELT-scale network).
 Readings:
 
 * layers y = W x + b, GELU with the exact error function between layers:
