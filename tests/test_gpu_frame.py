@@ -97,3 +97,39 @@ def test_batched_frames_match_single_frames(env):
     torch.cuda.synchronize()
     assert torch.equal(four.modes, got)
     g.close()
+
+
+def test_elt_frame_in_the_bench_configuration(env):
+    """The full-size ELT frame (pwfs39m: 35 layers, 960^2 FFT, 48 points,
+    4000 x 13344 MVM) as the bench times it: autotuned tiles, replayed from a
+    CUDA graph on a side stream, against the oracle chain on the same screens
+    (every detector pixel, every slope and mode)."""
+    torch, sp, ctx = env
+    from paper_2602_06688_gb300.frame import PwfsFrame
+    wl = synth.workload("pwfs39m")
+    fr = PwfsFrame(ctx, wl, autotune=True)
+    st = torch.cuda.Stream()
+    fr.capture(st)
+    t = 0.0371
+    fr.replay(t, st)
+    torch.cuda.synchronize()
+    s = wl.sensors[0]
+    n, nsub, g = s.pupil.n_pix, s.pwfs.n_sub, s.pwfs
+    scr = [x.cpu().numpy().astype(np.float64) for x in fr.screens]
+    phi = atmo.atmo_extract(scr, wl.layers, s.source, n, s.pupil.pitch_m, t)
+    assert np.max(np.abs(fr.phase.cpu().numpy() - phi)) <= 1e-5 * (1 + np.abs(phi).max())
+    amp = geometry.pupil_mask(n, s.pupil.obsc_frac).astype(np.float64)
+    valid = geometry.valid_subaps(amp.astype(np.uint8), nsub)
+    det_ref = pyramid.pwfs_image(amp, phi, g.pad, g.n_mod, g.mod_amp, nsub, n)
+    det = fr.det.cpu().numpy().astype(np.float64)
+    assert norm_intensity_error(det, det_ref) <= 1e-5
+    flat = pyramid.pwfs_image(amp, np.zeros_like(phi), g.pad, g.n_mod, g.mod_amp, nsub, n)
+    s_ref = slopes.pyr_slopes(det_ref, nsub, valid, ref=slopes.pyr_slopes(flat, nsub, valid))
+    T = det_ref.sum() / len(valid)
+    tol = 2 * (5e-5 * det_ref.max() / T + 1e-5 * np.abs(s_ref).max())
+    sl = fr.slopes.cpu().numpy().astype(np.float64)
+    assert np.max(np.abs(sl - s_ref)) <= tol
+    R = fr.R.cpu().numpy().astype(np.float64)
+    mag = np.abs(R) @ np.abs(sl)
+    assert np.all(np.abs(fr.modes.cpu().numpy() - recon.mvm(R, sl)) <= 1e-5 * mag)
+    fr.graph.close()
