@@ -389,8 +389,8 @@ int specula_infscreen_lines(specula_ctx *ctx, int32_t side, int32_t n_st, int32_
  * lo + 1, ...; growing up writes line lo + side from the lines below it.  On
  * success lo is updated and *n_moves is set.  If more than max_moves are
  * needed, the call returns SPECULA_EUNSUPPORTED, sets *n_moves to the count
- * needed and leaves lo unchanged.  A footprint wider than the ring also gives
- * SPECULA_EUNSUPPORTED.  n_layers 0..32; layers' side is ignored (the ring's
+ * needed and leaves lo unchanged.  A footprint wider than the ring, or more
+ * than 2^20 lines for one layer and axis, also gives SPECULA_EUNSUPPORTED.  n_layers 0..32; layers' side is ignored (the ring's
  * side is `side`). */
 typedef struct {
   int32_t layer, axis, direction;

@@ -328,6 +328,10 @@ static void inf_footprint(const specula_layer_desc &l, const specula_source_desc
   *last = fmax(u0, u1);
 }
 
+// at most this many lines per layer and axis in one plan (a larger jump in t
+// is refused before any move is listed)
+constexpr int64_t kInfMaxMovesPerAxis = (int64_t)1 << 20;
+
 static int inf_plan(int32_t n_layers, const specula_layer_desc *layers,
                     const specula_source_desc *src, const specula_pupil_desc *pupil, int32_t side,
                     int32_t margin, double t, int64_t *lo, std::vector<specula_inf_move> *out) {
@@ -346,6 +350,8 @@ static int inf_plan(int32_t n_layers, const specula_layer_desc *layers,
       const int64_t first = (int64_t)floor(a) - margin, last = (int64_t)floor(b) + 1 + margin;
       if (last - first + 1 > side) return SPECULA_EUNSUPPORTED;   // ring too small
       int64_t w = lo2[axis];
+      const int64_t need = w > first ? w - first : (last > w + side - 1 ? last - (w + side - 1) : 0);
+      if (need > kInfMaxMovesPerAxis) return SPECULA_EUNSUPPORTED;
       while (w > first) {
         --w;
         out->push_back({l, axis, -1, w});

@@ -79,6 +79,9 @@ def test_plan_errors_and_move_limit(sp):
     with pytest.raises(sp.SpeculaError) as e:
         sp.specula_infscreen_plan(layers, src, pu, 128, 1, 0.0, lo, 100)
     assert e.value.status == sp.EUNSUPPORTED
+    with pytest.raises(sp.SpeculaError) as e:      # a jump of about 4e8 lines
+        sp.specula_infscreen_plan(layers, src, pu, 256, 1, 1e6, lo, 100)
+    assert e.value.status == sp.EUNSUPPORTED
     with pytest.raises(sp.SpeculaError) as e:
         sp.specula_infscreen_plan(layers, src, pu, 256, 1, math.nan, lo, 100)
     assert e.value.status == sp.EINVAL
