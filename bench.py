@@ -485,6 +485,35 @@ def closed_loop_leg(ctx, steps=400, settle=150):
     return out
 
 
+def fma_peaks_leg(ctx):
+    """Measured fused multiply-add rates (the library's probe kernel, 8 CTAs
+    of 256 threads per SM, 8 independent chains per thread), best of 3
+    event-timed launches after one warm-up: the check on the derived FP32
+    peak, and the float64 rate of the set-up paths."""
+    import torch
+    import paper_2602_06688_gb300 as sp
+    n_sm = torch.cuda.get_device_properties(0).multi_processor_count
+    n_ctas = 8 * n_sm
+    out = {}
+    for bits, n_iter, dt in ((32, 20000, torch.float32), (64, 1000, torch.float64)):
+        sink = torch.empty(n_ctas * 256, dtype=dt, device="cuda")
+        sp.specula_fma_probe(ctx, bits, n_ctas, n_iter, sink)
+        best = None
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            sp.specula_fma_probe(ctx, bits, n_ctas, n_iter, sink)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            best = ms if best is None else min(best, ms)
+        flops = 2.0 * 8 * n_iter * 256 * n_ctas
+        out["fp%d_fma_tflops" % bits] = flops / (best / 1e3) / 1e12
+        assert bool(torch.isfinite(sink).all())
+    out["sms"] = n_sm
+    return out
+
+
 def infinite_leg(ctx, st, flush, steps):
     """The 8 m pyramid frame on infinite screens: 256 px rings, two stencil
     lines; before each frame the host picks the lines the footprints need and
@@ -934,6 +963,12 @@ def gpu_leg(args, ws, rank, local):
                         "note": "per step: pinned host time -> device, frame, modes -> pinned host, sync"},
                 "gpu_launches": launches, "clocks": clocks,
                 "peaks": {"source": how, "hbm_gbs": pk.get("hbm_gbs")}}
+        meas = fma_peaks_leg(ctx)
+        meas["fp32_derived_tflops"] = peak_alu
+        meas["fp32_measured_over_derived"] = meas["fp32_fma_tflops"] / peak_alu
+        meas["fft_stage_frac_of_measured_fp32"] = (roof["achieved"] / meas["fp32_fma_tflops"]
+                                                   if roof else None)
+        line["peaks"]["measured_fma"] = meas
         if not args.no_systems:
             line["systems"] = systems_leg(ctx)
         if not args.no_loop:

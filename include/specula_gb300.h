@@ -195,7 +195,8 @@ int specula_check_guards(specula_ctx *ctx, int32_t *n_checked, int32_t *n_bad);
 #define SPECULA_K_LOOP          18  /* closed loop: mirror shape, residual, update */
 #define SPECULA_K_CCD           19  /* detector photon and readout noise          */
 #define SPECULA_K_INFSCREEN     20  /* infinite screens: set-up and line growth   */
-#define SPECULA_K_COUNT         21
+#define SPECULA_K_PEAK          21  /* fused multiply-add rate probe              */
+#define SPECULA_K_COUNT         22
 
 /* Enable (capacity > 0: room for that many kernel records; allocates CUDA
  * events; set-up call) or disable (capacity = 0) per-kernel event timing.
@@ -208,6 +209,15 @@ int specula_prof_enable(specula_ctx *ctx, int32_t capacity);
  * elapsed milliseconds ms_host[k] and the number of records n_host[k] since
  * the last read (arrays of SPECULA_K_COUNT entries), and clear the records. */
 int specula_prof_read(specula_ctx *ctx, double *ms_host, int64_t *n_host);
+
+/* Arithmetic peak probe: n_ctas CTAs of 256 threads; each thread runs 8
+ * independent fused multiply-add chains of n_iter steps in float32 (bits 32)
+ * or float64 (bits 64) and writes one value to sink_dev (n_ctas * 256
+ * elements of that type).  Work: 2 * 8 * n_iter * 256 * n_ctas flops; timed
+ * with events on the stream it gives the part's FMA rate (the roof of
+ * CUDA-core arithmetic).  n_ctas 1..65535, n_iter 1..2^24.  One kernel. */
+int specula_fma_probe(specula_ctx *ctx, int32_t bits, int32_t n_ctas, int32_t n_iter,
+                      void *sink_dev, void *stream);
 
 /* Number of kernels this context has launched since it was created. */
 int specula_launch_count(specula_ctx *ctx, int64_t *count);

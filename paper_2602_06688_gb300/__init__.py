@@ -145,12 +145,12 @@ def specula_check_guards(ctx):
 (K_PWFS_ROWS_FWD, K_PWFS_COLS, K_PWFS_ROWS_INV, K_ATMO, K_SLOPES, K_RECON, K_SH,
  K_PWFS_FIELD, K_PWFS_BIN, K_CALIB, K_GEMM, K_MLP, K_MWFS, K_PWFS_ROWFILT,
  K_PWFS_COLFILT, K_PWFS_SM_FWD, K_PWFS_SM_ROWS, K_PWFS_SM_COLS, K_LOOP, K_CCD,
- K_INFSCREEN) = range(21)
-K_COUNT = 21
+ K_INFSCREEN, K_PEAK) = range(22)
+K_COUNT = 22
 KERNEL_NAMES = ["pwfs_rows_fwd", "pwfs_cols", "pwfs_rows_inv", "atmo_extract", "slopes",
                 "recon", "sh_spots", "pwfs_field", "pwfs_bin", "calib", "gemm", "mlp", "mwfs",
                 "pwfs_rowfilt", "pwfs_colfilt_bin", "pwfs_sm_fwd", "pwfs_sm_rows",
-                "pwfs_sm_colfilt_bin", "loop", "ccd", "infscreen"]
+                "pwfs_sm_colfilt_bin", "loop", "ccd", "infscreen", "fma_probe"]
 
 
 def specula_prof_enable(ctx, capacity):
@@ -530,6 +530,16 @@ def specula_loop_integrate(ctx, gain, leak, modes, cmd, stream=None):
     _abi.check(lib().specula_loop_integrate(
         ctx.handle, int(n), float(gain), float(leak), _dev(modes, torch.float32, n, "modes"),
         _dev(cmd, torch.float32, n, "cmd"), _stream(stream)), "specula_loop_integrate")
+
+
+def specula_fma_probe(ctx, bits, n_ctas, n_iter, sink, stream=None):
+    """FMA-rate probe kernel (see the header); sink: n_ctas * 256 elements of
+    float32 (bits 32) or float64 (bits 64)."""
+    import torch
+    dt = torch.float32 if bits == 32 else torch.float64
+    _abi.check(lib().specula_fma_probe(ctx.handle, int(bits), int(n_ctas), int(n_iter),
+                                       _dev(sink, dt, n_ctas * 256, "sink"), _stream(stream)),
+               "specula_fma_probe")
 
 
 def specula_rebin(ctx, img, n_out, out, stream=None):

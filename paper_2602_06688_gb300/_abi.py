@@ -123,6 +123,7 @@ SIGNATURES = {
     "specula_infscreen_operators": (C.c_int, [vp, i32, i32, dbl, dbl, dbl, dbl, vp, vp, vp, vp,
                                               vp]),
     "specula_rebin": (C.c_int, [vp, vp, i32, i32, i32, vp, vp]),
+    "specula_fma_probe": (C.c_int, [vp, i32, i32, i32, vp, vp]),
     "specula_infscreen_lines": (C.c_int, [vp, i32, i32, i32, vp, C.c_uint64, vp, vp]),
     "specula_infscreen_plan": (C.c_int, [i32, vp, P(SourceDesc), P(PupilDesc), i32, i32, dbl, vp,
                                          i32, vp, P(i32)]),

@@ -149,3 +149,24 @@ def test_guard_bands_cover_the_workspaces(env):
         sp.specula_pwfs_image(ctx, pu, pw, amp, torch.zeros(n, n, device="cuda"), det)
     n_checked, n_bad = sp.specula_check_guards(ctx)
     assert n_checked >= 8 and n_bad == 0
+
+
+@pytest.mark.parametrize("bits,rtol", [(32, 1e-6), (64, 1e-14)])
+def test_fma_probe_computes_its_chains(env, bits, rtol):
+    """The peak probe's output is the sum of its 8 chains a = a x + y started
+    at (thread + i): the work it claims is done, not optimised away."""
+    torch, sp, ctx = env
+    dt = torch.float32 if bits == 32 else torch.float64
+    sink = torch.full((3 * 256,), float("nan"), dtype=dt, device="cuda")
+    sp.specula_fma_probe(ctx, bits, 3, 7, sink)
+    torch.cuda.synchronize()
+    x = float(np.float32(1.0000001)) if bits == 32 else 1.0000001
+    y = float(np.float32(-1e-7)) if bits == 32 else -1e-7
+    ref = np.zeros(256)
+    for i in range(8):
+        a = np.arange(256, dtype=np.float64) + i
+        for _ in range(7):
+            a = a * x + y
+        ref += a
+    got = sink.cpu().numpy().astype(np.float64).reshape(3, 256)
+    assert np.allclose(got, ref[None, :], rtol=rtol, atol=0)
