@@ -489,6 +489,20 @@ int specula_pwfs_get_tiles(specula_ctx *ctx, const specula_pupil_desc *pupil,
                            const specula_pwfs_desc *pwfs, int32_t *chunk, int32_t *ka,
                            int32_t *passes);
 
+/* Imaged modulation slots of a pyramid plan (set-up call; synchronises).
+ * Slot c (0 <= c <= n_mod / 2) holds the points m = c and m = n_mod - c,
+ * which share a modulation cosine.  After this call, specula_pwfs_image
+ * images only the points of slots [slot_begin, slot_end) and still
+ * normalises by 1 / n_mod.  So the detectors of disjoint slot ranges that
+ * cover 0 .. n_mod / 2 add up to the full image: the modulation-point
+ * partition of one frame across GPUs, summed by a reduction.  The range
+ * [0, n_mod / 2 + 1) restores the full image.  A partial range needs the
+ * two-pass tilt form (SPECULA_EUNSUPPORTED from specula_pwfs_image
+ * otherwise) and is refused by the autotuner.  Errors: SPECULA_EINVAL for
+ * an empty or out-of-range interval, SPECULA_ENOPLAN without a plan. */
+int specula_pwfs_set_slots(specula_ctx *ctx, const specula_pupil_desc *pupil,
+                           const specula_pwfs_desc *pwfs, int32_t slot_begin, int32_t slot_end);
+
 /* Modulation form of a pyramid plan (set-up call; may allocate).
  *  SPECULA_PWFS_FORM_TILT (default): the modulation steps as listed for
  *    ModulatedPyramid (App. A, Tab. 4): per point, tilt the field, forward

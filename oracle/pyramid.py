@@ -55,8 +55,10 @@ def pyramid_mask(N: int, pup_dist: float) -> np.ndarray:
 
 
 def pwfs_intensity(amp: np.ndarray, phase: np.ndarray, pad: int, n_mod: int,
-                   mod_amp: float, pup_dist: float, mask=None) -> np.ndarray:
-    """Modulation-averaged N x N intensity (steps 1-6)."""
+                   mod_amp: float, pup_dist: float, mask=None, points=None) -> np.ndarray:
+    """Modulation-averaged N x N intensity (steps 1-6).  points: the subset of
+    modulation points to image (None: all); the sum is still divided by
+    n_mod, so subsets that partition the points add up to the full image."""
     Np = amp.shape[0]
     N = pad * Np
     off = (N - Np) // 2
@@ -65,7 +67,7 @@ def pwfs_intensity(amp: np.ndarray, phase: np.ndarray, pad: int, n_mod: int,
     M = pyramid_mask(N, pup_dist) if mask is None else mask
     cs, sn = mod_angles(n_mod)
     I = np.zeros((N, N))
-    for m in range(n_mod):
+    for m in (range(n_mod) if points is None else points):
         tilt = np.exp(2j * np.pi * mod_amp
                       * (x[None, :] * cs[m] + x[:, None] * sn[m]) / Np)
         P = np.zeros((N, N), dtype=np.complex128)

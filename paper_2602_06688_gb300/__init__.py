@@ -371,6 +371,13 @@ def specula_pwfs_plan(ctx, pupil, pwfs):
                "specula_pwfs_plan")
 
 
+def specula_pwfs_set_slots(ctx, pupil, pwfs, slot_begin, slot_end):
+    """Image only the modulation points of cosine slots [slot_begin, slot_end)."""
+    _abi.check(lib().specula_pwfs_set_slots(ctx.handle, C.byref(pupil), C.byref(pwfs),
+                                            int(slot_begin), int(slot_end)),
+               "specula_pwfs_set_slots")
+
+
 def specula_pwfs_set_form(ctx, pupil, pwfs, form):
     _abi.check(lib().specula_pwfs_set_form(ctx.handle, C.byref(pupil), C.byref(pwfs), int(form)),
                "specula_pwfs_set_form")

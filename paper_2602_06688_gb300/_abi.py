@@ -112,6 +112,7 @@ SIGNATURES = {
     "specula_pwfs_plan": (C.c_int, [vp, P(PupilDesc), P(PwfsDesc)]),
     "specula_pwfs_set_tiles": (C.c_int, [vp, P(PupilDesc), P(PwfsDesc), i32, i32, i32]),
     "specula_pwfs_set_form": (C.c_int, [vp, P(PupilDesc), P(PwfsDesc), i32]),
+    "specula_pwfs_set_slots": (C.c_int, [vp, P(PupilDesc), P(PwfsDesc), i32, i32]),
     "specula_pyr_image_index_host": (C.c_int, [P(PupilDesc), i32, i32, i32, vp, P(i32)]),
     "specula_pwfs_image_poly": (C.c_int, [vp, P(PupilDesc), P(PwfsDesc), i32, vp, vp, vp, vp, i32,
                                           vp, vp]),

@@ -528,6 +528,24 @@ extern "C" int specula_pwfs_set_form(specula_ctx *ctx, const specula_pupil_desc 
   return SPECULA_OK;
 }
 
+extern "C" int specula_pwfs_set_slots(specula_ctx *ctx, const specula_pupil_desc *pupil,
+                                      const specula_pwfs_desc *pwfs, int32_t slot_begin,
+                                      int32_t slot_end) {
+  if (!ctx) return SPECULA_EINVAL;
+  int s = check_pwfs(pupil, pwfs);
+  if (s) return s;
+  PwfsPlan *p = pwfs_plan_find(ctx, pupil, pwfs);
+  if (!p) return SPECULA_ENOPLAN;
+  if (slot_begin < 0 || slot_end <= slot_begin || slot_end > p->nc) return SPECULA_EINVAL;
+  SPECULA_CK(cudaSetDevice(ctx->device));
+  SPECULA_CK(cudaDeviceSynchronize());   // the workspace may be in use
+  const bool all = slot_begin == 0 && slot_end == p->nc;
+  p->slot_lo = all ? 0 : slot_begin;
+  p->slot_hi = all ? -1 : slot_end;
+  if (p->part.p) SPECULA_CK(cudaMemset(p->part.p, 0, p->part.bytes));
+  return SPECULA_OK;
+}
+
 extern "C" int specula_pwfs_autotune(specula_ctx *ctx, const specula_pupil_desc *pupil,
                                      const specula_pwfs_desc *pwfs, const float *amp_dev,
                                      const float *phase_dev, int32_t n_batch, float *det_dev,
@@ -540,7 +558,7 @@ extern "C" int specula_pwfs_autotune(specula_ctx *ctx, const specula_pupil_desc 
   if (s) return s;
   PwfsPlan *p = pwfs_plan_find(ctx, pupil, pwfs);
   if (!p) return SPECULA_ENOPLAN;
-  if (p->form != SPECULA_PWFS_FORM_TILT) return SPECULA_EUNSUPPORTED;
+  if (p->form != SPECULA_PWFS_FORM_TILT || p->slot_hi >= 0) return SPECULA_EUNSUPPORTED;
   SPECULA_CK(cudaSetDevice(ctx->device));
   int bc = 0, bk = 0, bp = 0;
   s = pwfs_autotune(ctx, p, amp_dev, phase_dev, n_batch, det_dev, (cudaStream_t)stream, reps,

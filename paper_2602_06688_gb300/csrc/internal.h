@@ -95,6 +95,8 @@ struct PwfsPlan {
   size_t smemA, smemB, smemC;
   int passes;           // 2: row filter + column filter/bins; 3: rows, cols, rows
   int nc;               // row-filter slots per batch element (distinct cosines)
+  int slot_lo = 0;      // cosine slots [slot_lo, slot_hi) imaged (slot_hi < 0: all)
+  int slot_hi = -1;
   bool two_ok;          // the two-pass form fits this geometry
   int blockR, blockK;   // two-pass blocks (K: TC columns x G lanes)
   size_t smemR, smemK;

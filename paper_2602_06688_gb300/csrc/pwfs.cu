@@ -330,7 +330,7 @@ __global__ void __launch_bounds__(256, 2) k_rowfilt(
     const float2 *__restrict__ field, const float2 *__restrict__ gx,
     const float2 *__restrict__ twA, const float2 *__restrict__ twB,
     const float2 *__restrict__ mask, float2 *__restrict__ rows_out, int n_pix, int nc, int nbw,
-    int slot0, int n_slots, int ka, int off) {
+    int slot0, int n_slots, int ka, int off, int s0) {
   using S = Split<N1, N2>;
   constexpr int N = S::N, G = S::G, S1 = S::S1, S2 = S::S2;
   constexpr int Q0 = N2 / 4, QH = N2 / 2;
@@ -348,7 +348,7 @@ __global__ void __launch_bounds__(256, 2) k_rowfilt(
     const int it = it_begin + q;
     if (it >= n_slots) break;
     const int gi = slot0 + it;
-    const int b = gi / nc, c = gi - b * nc;
+    const int b = gi / nc, c = s0 + (gi - b * nc);   // nc slots per element from s0
     if (!GEN && b != cur_b) {
       cur_b = b;
       const float2 *src = field + ((size_t)(b % nbw) * n_pix + (row_ok ? j : 0)) * n_pix + lane;
@@ -441,7 +441,7 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 160 ? 4 : 3) k_colfilt_bin(
     const float2 *__restrict__ rows_in, const float2 *__restrict__ gy,
     const float2 *__restrict__ twA, const float2 *__restrict__ twB,
     const float2 *__restrict__ mask, float *__restrict__ part, int n_pix, int bsz, float scale,
-    int n_mod, int nc, int nbw, int slot0, int CS, int off) {
+    int n_mod, int nc, int nbw, int slot0, int CS, int off, int s0) {
   using S = Split<N1, N2>;
   constexpr int N = S::N, G = S::G, S1 = S::S1, S2 = S::S2;
   constexpr int Q0 = N2 / 4, QH = N2 / 2;
@@ -450,7 +450,7 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 160 ? 4 : 3) k_colfilt_bin(
   const int TC = blockDim.x / G;
   const int it = blockIdx.y >> 1;              // slot within the chunk
   const int gs = slot0 + it;
-  const int b = gs / nc, cslot = gs - b * nc;
+  const int b = gs / nc, cslot = s0 + (gs - b * nc);   // nc slots per element from s0
   const int m = (blockIdx.y & 1) ? n_mod - cslot : cslot;
   if ((blockIdx.y & 1) && (cslot == 0 || 2 * cslot == n_mod)) return;   // no second item
   const int col0 = blockIdx.x * TC;
@@ -639,7 +639,9 @@ static int run_split2(specula_ctx *ctx, PwfsPlan *p, const float *amp, const flo
   const int Np = p->n_pix;
   const int bsz = Np / p->n_sub;
   const int nd = S::N / bsz;
-  const int nc = p->nc;
+  // the imaged cosine slots [s0, s0 + nc) of every batch element
+  const int s0 = p->slot_lo;
+  const int nc = (p->slot_hi < 0 ? p->nc : p->slot_hi) - s0;
   const int total = n_batch * nc;
   const int vpc = p->blockR / S::G;
   const int tc = p->blockK / S::G;
@@ -664,13 +666,13 @@ static int run_split2(specula_ctx *ctx, PwfsPlan *p, const float *amp, const flo
                  k_rowfilt<N1, N2, GEN_><<<gR, p->blockR, p->smemR, st>>>(                     \
                      p->field.as<float2>(), p->gx.as<float2>(), p->twA.as<float2>(),           \
                      p->twB.as<float2>(), p->mask.as<float2>(), p->rows.as<float2>(), Np, nc,  \
-                     p->nbw, j0, nj, p->ka, off))
+                     p->nbw, j0, nj, p->ka, off, s0))
 #define SPECULA_COLFILT(MAXT_, GEN_)                                                           \
   SPECULA_LAUNCH(ctx, SPECULA_K_PWFS_COLFILT, st,                                              \
                  k_colfilt_bin<N1, N2, MAXT_, GEN_><<<gK, p->blockK, p->smemK, st>>>(          \
                      p->rows.as<float2>(), p->gy.as<float2>(), p->twA.as<float2>(),            \
                      p->twB.as<float2>(), p->mask.as<float2>(), p->part.as<float>(), Np, bsz,  \
-                     scale, p->n_mod, nc, p->nbw, j0, p->csK, off))
+                     scale, p->n_mod, nc, p->nbw, j0, p->csK, off, s0))
     if (gen)
       SPECULA_ROWFILT(true);
     else
@@ -790,6 +792,8 @@ int pwfs_set_tiles(PwfsPlan *p, int chunk, int ka, int passes) {
     if ((s = p->rows.alloc(std::max(need_rows, p->rows.bytes)))) return s;
     if (need_cols > p->cols.bytes && (s = p->cols.alloc(need_cols))) return s;
     if ((s = p->part.alloc(std::max(need_part, p->part.bytes)))) return s;
+    // items outside an imaged slot range are never written: they read as 0
+    SPECULA_CK(cudaMemset(p->part.p, 0, p->part.bytes));
   }
   p->chunk = chunk;
   p->ka = ka;
@@ -808,6 +812,8 @@ int pwfs_bin_reduce(specula_ctx *ctx, const float *part, float *det, int nd2, in
 
 int pwfs_run(specula_ctx *ctx, PwfsPlan *p, const float *amp, const float *phase, int n_batch,
              float *det, cudaStream_t st) {
+  if (p->slot_hi >= 0 && (p->form != SPECULA_PWFS_FORM_TILT || p->passes != 2))
+    return SPECULA_EUNSUPPORTED;   // slot ranges: the two-pass tilt form only
   if (p->form == SPECULA_PWFS_FORM_SHIFTED)
     return pwfs_shifted_run(ctx, p, amp, phase, n_batch, det, st);
   switch (p->N) {
