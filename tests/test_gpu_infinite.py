@@ -249,3 +249,30 @@ def test_native_advance_equals_planned_calls(env):
     for x, y in zip(ra, rb):
         assert torch.equal(x, y)
 
+
+
+def test_argument_checks(env):
+    torch, sp, ctx = env
+    import math
+    bad_ops = [(1, 1, 0.1, 0.1, 10.0), (1025, 2, 0.1, 0.1, 10.0), (8, 5, 0.1, 0.1, 10.0),
+               (8, 8, 0.1, 0.1, 10.0), (8, 2, 0.1, 0.1, math.inf), (8, 2, -0.1, 0.1, 10.0),
+               (8, 2, 0.1, 0.0, 10.0)]
+    for side, n_st, pitch, r0, L0 in bad_ops:
+        with pytest.raises(sp.SpeculaError) as e:
+            sp.specula_infscreen_operators(ctx, side, n_st, pitch, r0, L0)
+        assert e.value.status == sp.EINVAL
+    side, n_st = 16, 2
+    A, B = sp.specula_infscreen_operators(ctx, side, n_st, 0.1, 0.1, 10.0)
+    scr = torch.zeros(side, side, device="cuda")
+    for task in [(scr, A, B, 1.0, 2, 1, 0, 5), (scr, A, B, 1.0, 0, 0, 0, 5),
+                 (scr, A, B, float("nan"), 0, 1, 0, 5)]:
+        with pytest.raises(sp.SpeculaError) as e:
+            sp.specula_infscreen_lines(ctx, side, n_st, [task])
+        assert e.value.status == sp.EINVAL
+    with pytest.raises(sp.SpeculaError) as e:       # the same ring twice in one call
+        sp.specula_infscreen_lines(ctx, side, n_st, [(scr, A, B, 1.0, 0, 1, 0, 5),
+                                                     (scr, A, B, 1.0, 1, 1, 1, 5)])
+    assert e.value.status == sp.EINVAL
+    sp.specula_infscreen_lines(ctx, side, n_st, [])  # no task: a no-op
+    torch.cuda.synchronize()
+    assert bool((scr == 0).all())
