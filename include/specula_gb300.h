@@ -160,7 +160,8 @@ int specula_ctx_status(specula_ctx *ctx, int32_t *device_status);
  * for launches made after the call. */
 int specula_ctx_set_guard(specula_ctx *ctx, int32_t on);
 
-/* Workspace guard bands.  Every device buffer the library allocates (plan
+/* Workspace guard bands (failure detection of this library; the paper has
+ * no counterpart).  Every device buffer the library allocates (plan
  * tables and workspaces, the multi-sensor and learned-reconstructor buffers)
  * is followed by 256 bytes of the pattern 0xA5.  A kernel that writes past
  * its workspace stays inside the allocation, so the write does not fault;
@@ -210,7 +211,8 @@ int specula_prof_enable(specula_ctx *ctx, int32_t capacity);
  * the last read (arrays of SPECULA_K_COUNT entries), and clear the records. */
 int specula_prof_read(specula_ctx *ctx, double *ms_host, int64_t *n_host);
 
-/* Arithmetic peak probe: n_ctas CTAs of 256 threads; each thread runs 8
+/* Arithmetic peak probe (a measurement utility; the paper has no
+ * counterpart): n_ctas CTAs of 256 threads; each thread runs 8
  * independent fused multiply-add chains of n_iter steps in float32 (bits 32)
  * or float64 (bits 64) and writes one value to sink_dev (n_ctas * 256
  * elements of that type).  Work: 2 * 8 * n_iter * 256 * n_ctas flops; timed
