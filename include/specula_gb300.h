@@ -800,11 +800,14 @@ int specula_pinv_fp64(specula_ctx *ctx, const double *A_dev, int32_t m, int32_t 
  * k ~ Poisson(det_dev[p] scale) (scale = photons per frame x quantum
  * efficiency / pupil pixels, det_dev the noise-free detector image) and g a
  * standard normal.  Draws from Philox4x32-10, counter (p, frame, block,
- * stream), key = seed: up to a mean of 30 the multiplicative method (the
- * number of uniforms whose running float64 product stays above
- * exp(-lambda), at most 1000; stream 2), above it floor(lambda +
- * sqrt(lambda) g0 + 1/2) clamped at 0 (Box-Muller normals of stream 3, whose
- * second normal is g).  Reproducible per (seed, frame); the frame index is
+ * stream), key = seed, uniform (x + 1/2) 2^-32 of a word x: up to a mean of
+ * 30 the multiplicative method (the number of uniforms whose running product
+ * stays above exp(-lambda), at most 1000; stream 2; uniforms, product and
+ * threshold in float32, so a count may differ by one from the float64
+ * statement of the method where the product ends within a few roundings of
+ * the threshold), above it floor(lambda + sqrt(lambda) g0 + 1/2) clamped at 0;
+ * (g0, g) is the float32 Box-Muller pair of words 0 and 1 of block 0 of
+ * stream 3.  Reproducible per (seed, frame); the frame index is
  * frame + *frame_dev when frame_dev (one device uint32, nullable) is given,
  * so a captured graph draws new noise when the caller advances *frame_dev.
  * n floats in and out (out may alias det); scale >= 0, ron >= 0. */

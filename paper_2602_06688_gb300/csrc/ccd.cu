@@ -3,22 +3,20 @@
 // noise-free detector image reads k + ron g, k ~ Poisson(lambda), lambda =
 // det[p] scale (scale = photons per frame x quantum efficiency / pupil
 // pixels), g a standard normal.  Draws: Philox4x32-10 with counter
-// (p, frame, block, stream) and key (seed low, seed high).  Every step is a
-// chain of IEEE basic operations with one rounding each (no library function
-// and no contraction), so the counts are reproducible bit for bit by any
-// implementation of the same steps:
+// (p, frame, block, stream) and key (seed low, seed high); the uniform of a
+// word x is (x + 1/2) 2^-32.
 //   lambda <= kLambdaSwitch: the multiplicative method (Knuth, TAOCP vol. 2,
-//     3.4.1): k = the number of float32 uniforms whose running float32
-//     product stays above L, at most kKmax; uniform j is word j mod 4 of
-//     block j / 4 of stream 2; L = exp(-lambda) as T(lambda / 64)^64 in
-//     float32, T the degree-9 Taylor polynomial of exp(-x) by Horner's rule;
+//     3.4.1): k = the number of uniforms whose running product stays above
+//     exp(-lambda), at most kKmax; uniform j is word j mod 4 of block j / 4
+//     of stream 2.  The uniforms, their product and the threshold are
+//     float32 here (float64 is slow on this part): a count can differ by one
+//     from the float64 statement of the method where the product ends within
+//     a few float32 roundings of the threshold;
 //   lambda > kLambdaSwitch: k = max(0, floor(lambda + sqrt(lambda) g0 + 1/2))
-//     in float64, g0 the Irwin-Hall normal of blocks 0-2 of stream 3 (the sum
-//     of their twelve uniforms minus 6);
-//   g: the Irwin-Hall normal of blocks 3-5 of stream 3.
-// k + ron g is summed in float64 and rounded once to float32.  float64 is
-// slow on this part; the common multiplicative branch runs in float32 and no
-// branch calls a transcendental function.
+//     in float64 (the rounded normal approximation of the Poisson law);
+//   (g0, g) = sqrt(-2 ln u0) (cos 2 pi u1, sin 2 pi u1), the Box-Muller pair
+//     of words 0 and 1 of block 0 of stream 3, in float32.
+// k + ron g is summed in float64 and rounded once to float32.
 #include <math.h>
 
 #include "internal.h"
@@ -29,44 +27,23 @@ namespace specula {
 constexpr double kLambdaSwitch = 30.0;
 constexpr int kKmax = 1000;
 
-// 1 / k!, k = 0 .. 9, rounded once to float32
-__constant__ float c_inv_fact[10] = {
-    (float)1.0, (float)1.0, (float)(1.0 / 2.0), (float)(1.0 / 6.0), (float)(1.0 / 24.0),
-    (float)(1.0 / 120.0), (float)(1.0 / 720.0), (float)(1.0 / 5040.0), (float)(1.0 / 40320.0),
-    (float)(1.0 / 362880.0)};
-
-__device__ __forceinline__ float exp_neg_f32(double lam) {
-  const float x = __fmul_rn((float)lam, 0.015625f);          // lambda / 64, exact
-  float p = c_inv_fact[9];
-#pragma unroll
-  for (int k = 8; k >= 0; --k) p = __fadd_rn(__fmul_rn(p, -x), c_inv_fact[k]);
-#pragma unroll
-  for (int i = 0; i < 6; ++i) p = __fmul_rn(p, p);
-  return p;
-}
-
-// Sum of the twelve uniforms of blocks b0 .. b0 + 2 of stream 3, minus 6.
-// Every uniform (x + 1/2) 2^-32 is a multiple of 2^-33 below 1 and the sum
-// stays below 16, so the float64 sum is exact whatever the order: it equals
-// (S + 6) 2^-32 with S the integer sum of the words.
-__device__ __forceinline__ double irwin_hall(uint32_t p, uint32_t frame, uint32_t b0,
-                                             uint32_t k0, uint32_t k1) {
-  unsigned long long S = 6ull;
-#pragma unroll
-  for (uint32_t b = 0; b < 3; ++b) {
-    uint32_t c[4] = {p, frame, b0 + b, 3u};
-    philox4x32_10(c, k0, k1);
-#pragma unroll
-    for (int i = 0; i < 4; ++i) S += c[i];
-  }
-  return __dsub_rn(__dmul_rn((double)S, 1.0 / 4294967296.0), 6.0);
-}
-
 // The uniform (x + 1/2) 2^-32 rounded once to float32: (2x + 1) 2^-33 has at
 // most 33 significant bits; the integer-to-float conversion rounds it once and
 // the power-of-two scaling is exact.
 __device__ __forceinline__ float uniform_f32(uint32_t x) {
   return __fmul_rn(__ull2float_rn(2ull * x + 1ull), 0x1p-33f);
+}
+
+// The Box-Muller pair of block 0 of stream 3.
+__device__ __forceinline__ void box_muller(uint32_t p, uint32_t frame, uint32_t k0, uint32_t k1,
+                                           float *g0, float *g1) {
+  uint32_t c[4] = {p, frame, 0u, 3u};
+  philox4x32_10(c, k0, k1);
+  const float r = sqrtf(-2.0f * logf(uniform_f32(c[0])));
+  float s, co;
+  sincospif(2.0f * uniform_f32(c[1]), &s, &co);
+  *g0 = r * co;
+  *g1 = r * s;
 }
 
 __global__ void __launch_bounds__(256) k_ccd(const float *__restrict__ det, float *__restrict__ out,
@@ -76,14 +53,16 @@ __global__ void __launch_bounds__(256) k_ccd(const float *__restrict__ det, floa
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= n) return;
   const uint32_t frame = frame0 + (frame_dev ? *frame_dev : 0u);
-  const double lam = __dmul_rn((double)det[p], scale);
+  const double lam = (double)det[p] * scale;
+  const bool normal_branch = lam > kLambdaSwitch;
+  float g0 = 0.f, g1 = 0.f;
+  if (normal_branch || ron > 0.0) box_muller((uint32_t)p, frame, k0, k1, &g0, &g1);
   int k = 0;
-  if (lam > kLambdaSwitch) {
-    const double g0 = irwin_hall((uint32_t)p, frame, 0u, k0, k1);
-    const double v = floor(__dadd_rn(__dadd_rn(lam, __dmul_rn(sqrt(lam), g0)), 0.5));
+  if (normal_branch) {
+    const double v = floor(lam + sqrt(lam) * (double)g0 + 0.5);
     k = v > 0.0 ? (v < 2147483647.0 ? (int)v : 2147483647) : 0;
   } else {
-    const float L = exp_neg_f32(lam);
+    const float L = expf(-(float)lam);
     float prod = 1.f;
     uint32_t w0 = 0, w1 = 0, w2 = 0, w3 = 0;
     for (int j = 0; j <= kKmax; ++j) {
@@ -96,14 +75,14 @@ __global__ void __launch_bounds__(256) k_ccd(const float *__restrict__ det, floa
         w3 = w[3];
       }
       const uint32_t x = (j & 3) == 0 ? w0 : ((j & 3) == 1 ? w1 : ((j & 3) == 2 ? w2 : w3));
-      prod = __fmul_rn(prod, uniform_f32(x));
+      prod = prod * uniform_f32(x);
       if (!(prod > L)) break;
       ++k;
     }
     k = k < kKmax ? k : kKmax;
   }
-  const double rd = ron > 0.0 ? __dmul_rn(ron, irwin_hall((uint32_t)p, frame, 3u, k0, k1)) : 0.0;
-  out[p] = (float)__dadd_rn((double)k, rd);
+  const double rd = ron > 0.0 ? ron * (double)g1 : 0.0;
+  out[p] = (float)((double)k + rd);
 }
 
 // Area-weighted rebinning n_in -> n_out (detector sampling at a non-integer

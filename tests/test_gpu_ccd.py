@@ -1,7 +1,21 @@
-"""GPU parity of the detector noise against the oracle: photon counts
-bit-exact (both sides decide them with the same IEEE operations on the same
-Philox words), the readout-noise sum within one float32 rounding plus the
-float32 readout normal's last-bit differences."""
+"""GPU detector noise against the FP64 oracle.  The kernel evaluates the
+oracle's model on the same Philox words in float32 (the multiplicative
+method's uniforms, product and exp(-lambda) threshold; the Box-Muller pair),
+the oracle in float64, so per pixel:
+
+* photon counts agree on all but a small fraction of pixels and every
+  disagreement is one count: the float32 product can end on the other side
+  of the threshold when it lands within a few roundings of it, and the
+  rounded normal can cross a half-integer by the float32 normal's error;
+* reads agree within one float32 rounding plus ron times the float32
+  Box-Muller error (at most 5e-4 absolute: sqrt of the error of r^2, reached
+  only where u0 rounds to 1);
+
+and over many pixels of one flux the GPU's counts follow Poisson(lambda)
+below the switch and the rounded normal above it (moments and chi-squared),
+and its readout normal passes a Kolmogorov-Smirnov test."""
+import math
+
 import numpy as np
 import pytest
 
@@ -9,6 +23,8 @@ from gpu_common import close_checked, load_pkg, need_gpu
 from oracle import ccd
 
 pytestmark = pytest.mark.gpu
+
+G_ABS = 5e-4          # float32 Box-Muller normal against float64, absolute
 
 
 @pytest.fixture(scope="module")
@@ -28,8 +44,19 @@ def _det(torch, n):
     return torch.tensor(d.astype(np.float32), device="cuda")
 
 
+def _agree(got, ref, ron):
+    """Per-pixel agreement: the count difference (0 or 1 in magnitude) and the
+    read within the float32 bound; returns the number of count differences."""
+    got, ref = got.astype(np.float64).ravel(), ref.astype(np.float64).ravel()
+    dk = np.round(got - ref)
+    assert np.all(np.abs(dk) <= 1.0)
+    tol = 2.0 ** -22 * np.abs(ref) + ron * G_ABS + 2.0 ** -22 * np.abs(got)
+    assert np.all(np.abs(got - ref - dk) <= tol)
+    return int(np.count_nonzero(dk))
+
+
 @pytest.mark.parametrize("scale", [3.0, 60.0, 400.0])
-def test_photon_counts_bit_exact(env, scale):
+def test_photon_counts_agree(env, scale):
     torch, sp, ctx = env
     det = _det(torch, 33)                                    # 1089 px: ragged last block
     out = torch.empty_like(det)
@@ -37,7 +64,9 @@ def test_photon_counts_bit_exact(env, scale):
     torch.cuda.synchronize()
     ref = ccd.ccd_read(det.cpu().numpy(), scale, 0.0, 0x1234_5678_9ABC, 17)
     got = out.cpu().numpy()
-    assert np.array_equal(got, ref)
+    assert np.all(got == np.round(got))
+    n_diff = _agree(got, ref, 0.0)
+    assert n_diff <= 2 + got.size // 500, n_diff
     lam = det.cpu().numpy().astype(np.float64) * scale
     if scale == 60.0:                                        # both samplers in one image
         assert (lam <= ccd.LAMBDA_SWITCH).any() and (lam > ccd.LAMBDA_SWITCH).any()
@@ -52,17 +81,38 @@ def test_readout_noise_and_frames(env):
     sp.specula_ccd(ctx, det, 20.0, 3.0, 99, 5, c)
     torch.cuda.synchronize()
     assert torch.equal(a, b) and not torch.equal(a, c)
-    ref = ccd.ccd_read(det.cpu().numpy(), 20.0, 3.0, 99, 4).astype(np.float64)
-    got = a.cpu().numpy().astype(np.float64)
-    # the readout normal is float32 on both sides (library log/sin may differ
-    # in the last bit): one float32 rounding of the sum plus ron x 1e-6
-    assert np.all(np.abs(got - ref) <= 2.0 ** -23 * np.abs(ref) + 3.0 * 1e-6)
+    ref = ccd.ccd_read(det.cpu().numpy(), 20.0, 3.0, 99, 4)
+    n_diff = _agree(a.cpu().numpy(), ref, 3.0)
+    assert n_diff <= 2 + ref.size // 500, n_diff
     with pytest.raises(sp.SpeculaError):
         sp.specula_ccd(ctx, det, -1.0, 0.0, 1, 0, a)
 
 
+def _chi2_pvalue(k, pmf, kmax):
+    from scipy import stats
+    n = k.size
+    probs = np.array([pmf(j) for j in range(kmax + 1)])
+    probs = np.append(probs, max(0.0, 1.0 - probs.sum()))
+    obs = np.bincount(np.minimum(k, kmax + 1), minlength=kmax + 2).astype(np.float64)
+    exp_, ob, acc_e, acc_o = [], [], 0.0, 0.0
+    for e, o in zip(probs * n, obs):
+        acc_e += e
+        acc_o += o
+        if acc_e >= 5.0:
+            exp_.append(acc_e)
+            ob.append(acc_o)
+            acc_e = acc_o = 0.0
+    exp_[-1] += acc_e
+    ob[-1] += acc_o
+    exp_, ob = np.array(exp_), np.array(ob)
+    return float(stats.chi2.sf(float(((ob - exp_) ** 2 / exp_).sum()), len(exp_) - 1))
+
+
 def test_noise_statistics_on_the_gpu(env):
-    """Many pixels of one flux: Poisson mean and variance (both samplers)."""
+    """200k pixels of one flux: Poisson(lambda) in moments and by chi-squared
+    below the switch, the rounded normal of mean and variance lambda above
+    it; the readout normal of dark pixels by Kolmogorov-Smirnov."""
+    from scipy import stats
     torch, sp, ctx = env
     n = 200_000
     for lam in (4.0, 120.0):
@@ -70,9 +120,22 @@ def test_noise_statistics_on_the_gpu(env):
         out = torch.empty_like(det)
         sp.specula_ccd(ctx, det, lam, 0.0, 7, 0, out)
         torch.cuda.synchronize()
-        k = out.cpu().numpy().astype(np.float64)
+        k = out.cpu().numpy().astype(np.int64)
         assert abs(k.mean() - lam) < 5 * np.sqrt(lam / n)
         assert abs(k.var() - lam) < 5 * np.sqrt((lam + 2 * lam * lam) / n)
+        if lam <= ccd.LAMBDA_SWITCH:
+            pmf = lambda j: math.exp(-lam + j * math.log(lam) - math.lgamma(j + 1))
+        else:
+            s = math.sqrt(lam)
+            cdf = lambda x: 0.5 * math.erfc(-x / math.sqrt(2.0))
+            pmf = lambda j: cdf((j + 0.5 - lam) / s) - (cdf((j - 0.5 - lam) / s) if j else 0.0)
+        assert _chi2_pvalue(k, pmf, int(lam + 8 * math.sqrt(lam) + 8)) > 1e-3
+    dark = torch.zeros(n, device="cuda")
+    out = torch.empty_like(dark)
+    sp.specula_ccd(ctx, dark, 1.0, 2.0, 11, 3, out)
+    torch.cuda.synchronize()
+    g = out.cpu().numpy().astype(np.float64) / 2.0
+    assert stats.kstest(g, "norm").pvalue > 1e-3
 
 
 def test_device_frame_index(env):
