@@ -480,10 +480,16 @@ int specula_pwfs_plan(specula_ctx *ctx, const specula_pupil_desc *pupil,
  * column FFT + mask + inverse, row inverse FFTs + |.|^2 + bins; 2 = the
  * separable form (the mask is Mx(u) My(v)): row FFT + x mask + row inverse,
  * then column FFT + y mask + column inverse + |.|^2 + bins, without the
- * N x N intermediate.  Both compute the same image (float rounding aside).
+ * N x N intermediate; 4 = the separable form evaluated with packed float32
+ * pairs (two transforms per thread: two pupil rows in the row filter, the
+ * two modulation points of one cosine in the column filter; pad 2 with
+ * touching pupil images, N = 320 or 960; runs whole batch elements, so the
+ * chunk is rounded down to a multiple of n_mod / 2 + 1 slots, at least one
+ * element).  All compute the same image (float rounding aside).
  * set: may reallocate the workspace (set-up call); chunk in [1, 4096], ka in
- * [1, 64], passes 2 or 3 (2 returns SPECULA_EUNSUPPORTED where its column
- * tile does not fit).  get: reads the current values. */
+ * [1, 64], passes 2, 3 or 4 (2 and 4 return SPECULA_EUNSUPPORTED where their
+ * column tile does not fit or the geometry is not supported).  get: reads
+ * the current values. */
 int specula_pwfs_set_tiles(specula_ctx *ctx, const specula_pupil_desc *pupil,
                            const specula_pwfs_desc *pwfs, int32_t chunk, int32_t ka,
                            int32_t passes);
@@ -525,9 +531,10 @@ int specula_pwfs_set_slots(specula_ctx *ctx, const specula_pupil_desc *pupil,
 int specula_pwfs_set_form(specula_ctx *ctx, const specula_pupil_desc *pupil,
                           const specula_pwfs_desc *pwfs, int32_t form);
 
-/* Autotuner: time every candidate (passes in {2, 3}; chunk in
+/* Autotuner: time every candidate (passes in {2, 3, 4}; chunk in
  * {1,2,3,4,6,8,12,16,24,32,48,64} up to the batch's item count and with
- * workspace <= max_workspace_bytes; ka in {1, 2}) with CUDA events over
+ * workspace <= max_workspace_bytes, for passes 4 whole batch elements
+ * {1, 2, 4, ...} up to the batch; ka in {1, 2}) with CUDA events over
  * `reps` images of the caller's inputs on
  * `stream`, keep the fastest in the plan and return it.  Set-up call: may
  * reallocate the workspace and synchronises the stream.  det_dev is

@@ -55,6 +55,7 @@ extern "C" int specula_ctx_create(specula_ctx **out, int device) {
   if (!s) s = sh_init_device();
   if (!s) s = mwfs_init_device();
   if (!s) s = pwfs_shifted_init_device();
+  if (!s) s = pwfs_pair_init_device();
   if (!s) s = atmo_alloc_tables(c);
   if (!s) s = loop_alloc_workspace(c);
   if (s) {
@@ -504,7 +505,7 @@ extern "C" int specula_pwfs_set_tiles(specula_ctx *ctx, const specula_pupil_desc
   int s = check_pwfs(pupil, pwfs);
   if (s) return s;
   if (chunk < 1 || chunk > 4096 || ka < 1 || ka > 64) return SPECULA_EINVAL;
-  if (passes != 2 && passes != 3) return SPECULA_EINVAL;
+  if (passes < 2 || passes > 4) return SPECULA_EINVAL;
   PwfsPlan *p = pwfs_plan_find(ctx, pupil, pwfs);
   if (!p) return SPECULA_ENOPLAN;
   SPECULA_CK(cudaSetDevice(ctx->device));

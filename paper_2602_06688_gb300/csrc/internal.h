@@ -122,6 +122,18 @@ struct PwfsPlan {
   DevBuf sm_fspec;      // [N][N] float2: the field's spectrum
   DevBuf sm_rows;       // [sm_chunk][N][N] float2 (+2): after the inverse row transform
   DevBuf sm_part;       // [n_mod][nd][nd] float: binned intensity per point
+  // two-pass form with packed-pair arithmetic (passes == 4, pwfs_pair.cu)
+  bool pair_ok = false;
+  int pair_blockR = 0, pair_blockK = 0;
+  size_t pair_smemR = 0, pair_smemK = 0;
+  DevBuf twA2, twB2;    // [N] float4 (re, re, im, im): inter-step twiddles
+  DevBuf mask2;         // [N] float4: mask factor per axis, x (1/N)
+  DevBuf gx2;           // [n_mod][n_pix] float4: x factor of the tilt x pre-phase
+  DevBuf pair_units;    // [n_pair_units] int4: (slot a, point a, slot b, point b or -1)
+  DevBuf gyp;           // [n_pair_units][n_pix] float4: the units' y factors (re_a, re_b, im_a, im_b)
+  int n_pair_units = 0;
+  int pair_units_for = -1;   // the slot range the unit table was built for
+  std::vector<float2> gy_host;
 };
 
 struct ShPlan {
@@ -198,6 +210,18 @@ int pwfs_shifted_run(specula_ctx *ctx, PwfsPlan *p, const float *amp, const floa
                      int n_batch, float *det, cudaStream_t st);
 int pwfs_bin_reduce(specula_ctx *ctx, const float *part, float *det, int nd2, int n_mod,
                     float alpha, float beta, cudaStream_t st);
+// the field of batch elements fb .. fb + nb - 1 into the plan's field slots,
+// and their detectors from the plan's per-point bins
+int pwfs_field_launch(specula_ctx *ctx, PwfsPlan *p, const float *amp, const float *phase,
+                      int fb, int nb, cudaStream_t st);
+int pwfs_bin_reduce_range(specula_ctx *ctx, PwfsPlan *p, float *det, int nd2, int b0, int nb,
+                          cudaStream_t st);
+struct PwfsTablesHost;
+int pwfs_pair_init_device();
+int pwfs_pair_configure(PwfsPlan *p);
+int pwfs_pair_tables(PwfsPlan *p, const PwfsTablesHost &T);
+int pwfs_pair_run(specula_ctx *ctx, PwfsPlan *p, const float *amp, const float *phase,
+                  int n_batch, float *det, cudaStream_t st);
 int atmo_alloc_tables(specula_ctx *ctx);
 
 // launchers implemented in the kernel translation units

@@ -770,14 +770,17 @@ bool pwfs_split_for(int N, int *N1, int *N2) {
 }
 
 int pwfs_set_tiles(PwfsPlan *p, int chunk, int ka, int passes) {
-  if (passes != 2 && passes != 3) return SPECULA_EINVAL;
+  if (passes < 2 || passes > 4) return SPECULA_EINVAL;
   if (passes == 2 && !p->two_ok) return SPECULA_EUNSUPPORTED;
   if (passes == 3 && p->pad != 2) return SPECULA_EUNSUPPORTED;   // pad-2 layout only
+  if (passes == 4 && !p->pair_ok) return SPECULA_EUNSUPPORTED;
   const int nd = p->pad * p->n_sub;   // detector side
   // batch elements one chunk can touch: chunk items (three-pass) or chunk
-  // row-filter slots, nc per batch element (two-pass)
-  const int per_b = passes == 2 ? p->nc : p->n_mod;
-  const int nbw = (chunk + per_b - 1) / per_b + 1;
+  // row-filter slots, nc per batch element (two-pass); the paired form runs
+  // whole batch elements, chunk / nc (at least one) per launch
+  const int per_b = passes == 3 ? p->n_mod : p->nc;
+  if (passes == 4) chunk = std::max(1, chunk / p->nc) * p->nc;
+  const int nbw = passes == 4 ? chunk / p->nc : (chunk + per_b - 1) / per_b + 1;
   const size_t need_field = (size_t)nbw * p->n_pix * p->n_pix * sizeof(float2);
   // two complex of padding: the column pass's staging window may read one
   // entry past the last row
@@ -810,12 +813,32 @@ int pwfs_bin_reduce(specula_ctx *ctx, const float *part, float *det, int nd2, in
   return SPECULA_OK;
 }
 
+int pwfs_field_launch(specula_ctx *ctx, PwfsPlan *p, const float *amp, const float *phase,
+                      int fb, int nb, cudaStream_t st) {
+  const int Np = p->n_pix;
+  dim3 gF((Np * Np + 255) / 256, nb);
+  SPECULA_LAUNCH(ctx, SPECULA_K_PWFS_FIELD, st,
+                 k_field<<<gF, 256, 0, st>>>(amp, phase, p->field.as<float2>(), Np * Np, fb, p->nbw,
+                                             p->run_phase_scale));
+  return SPECULA_OK;
+}
+
+int pwfs_bin_reduce_range(specula_ctx *ctx, PwfsPlan *p, float *det, int nd2, int b0, int nb,
+                          cudaStream_t st) {
+  dim3 gD((nd2 + 255) / 256, nb);
+  SPECULA_LAUNCH(ctx, SPECULA_K_PWFS_BIN, st,
+                 k_bin_reduce<<<gD, 256, 0, st>>>(p->part.as<float>(), det, nd2, p->n_mod, p->nbw,
+                                                  b0, p->run_alpha, p->run_beta));
+  return SPECULA_OK;
+}
+
 int pwfs_run(specula_ctx *ctx, PwfsPlan *p, const float *amp, const float *phase, int n_batch,
              float *det, cudaStream_t st) {
-  if (p->slot_hi >= 0 && (p->form != SPECULA_PWFS_FORM_TILT || p->passes != 2))
-    return SPECULA_EUNSUPPORTED;   // slot ranges: the two-pass tilt form only
+  if (p->slot_hi >= 0 && (p->form != SPECULA_PWFS_FORM_TILT || p->passes == 3))
+    return SPECULA_EUNSUPPORTED;   // slot ranges: the two-pass tilt forms only
   if (p->form == SPECULA_PWFS_FORM_SHIFTED)
     return pwfs_shifted_run(ctx, p, amp, phase, n_batch, det, st);
+  if (p->passes == 4) return pwfs_pair_run(ctx, p, amp, phase, n_batch, det, st);
   switch (p->N) {
     case 64: return run_split<8, 8>(ctx, p, amp, phase, n_batch, det, st);
     case 128: return run_split<8, 16>(ctx, p, amp, phase, n_batch, det, st);
@@ -840,15 +863,24 @@ int pwfs_autotune(specula_ctx *ctx, PwfsPlan *p, const float *amp, const float *
   SPECULA_CK(cudaEventCreate(&e0));
   SPECULA_CK(cudaEventCreate(&e1));
   int status = SPECULA_OK;
-  for (int passes = 2; passes <= (p->pad == 2 ? 3 : 2); ++passes) {
+  for (int passes = 2; passes <= 4; ++passes) {
     if (passes == 2 && !p->two_ok) continue;
-    const size_t item = passes == 2 ? (size_t)p->n_pix * p->N * sizeof(float2) : per_item;
+    if (passes == 3 && p->pad != 2) continue;
+    if (passes == 4 && !p->pair_ok) continue;
+    const size_t item = passes != 3 ? (size_t)p->n_pix * p->N * sizeof(float2) : per_item;
     for (int c : kChunks) {
-      if (c > std::max(total, 1) && c != 1) break;
-      if ((size_t)c * item > max_ws_bytes && c != 1) break;
-      for (int ka = 1; ka <= 2; ++ka) {
+      if (passes == 4) {
+        // whole batch elements: nc, 2 nc, 4 nc, ... slots
+        if (c != 1 && (c & (c - 1))) continue;
+        if (c > std::max(n_batch, 1) && c != 1) break;
+        if ((size_t)c * p->nc * item > max_ws_bytes && c != 1) break;
+      } else {
+        if (c > std::max(total, 1) && c != 1) break;
+        if ((size_t)c * item > max_ws_bytes && c != 1) break;
+      }
+      for (int ka = 1; ka <= (passes == 4 ? 1 : 2); ++ka) {
         if (ka > c) break;
-        if ((status = pwfs_set_tiles(p, c, ka, passes))) goto done;
+        if ((status = pwfs_set_tiles(p, passes == 4 ? c * p->nc : c, ka, passes))) goto done;
         if ((status = pwfs_run(ctx, p, amp, phase, n_batch, det, st))) goto done;   // warm-up
         cudaEventRecord(e0, st);
         for (int r = 0; r < reps; ++r)
@@ -857,7 +889,7 @@ int pwfs_autotune(specula_ctx *ctx, PwfsPlan *p, const float *amp, const float *
         if (cudaEventSynchronize(e1) != cudaSuccess) { status = SPECULA_ECUDA; goto done; }
         float ms = 0.f;
         cudaEventElapsedTime(&ms, e0, e1);
-        if (ms < best) { best = ms; bc = c; bk = ka; bp = passes; }
+        if (ms < best) { best = ms; bc = p->chunk; bk = ka; bp = passes; }
       }
     }
   }
@@ -962,9 +994,11 @@ int pwfs_plan_build(specula_ctx *ctx, const specula_pupil_desc *pupil,
   // distinct cosines of the modulation angles 2 pi m / n_mod: m and n_mod - m
   p->nc = d->n_mod / 2 + 1;
   int s = configure_for(p.get());
+  if (!s) s = pwfs_pair_configure(p.get());
   if (s) return s;
   PwfsTablesHost T;
   pwfs_host_tables(Np, N, N1, N2, d->n_mod, d->mod_amp, d->pup_dist_px, &T);
+  if ((s = pwfs_pair_tables(p.get(), T))) return s;
   const std::vector<float2> &gx = T.gx, &gy = T.gy, &mk = T.mask, &ta = T.twA, &tb = T.twB;
   if ((s = p->gx.upload(gx.data(), gx.size() * sizeof(float2)))) return s;
   if ((s = p->gy.upload(gy.data(), gy.size() * sizeof(float2)))) return s;
