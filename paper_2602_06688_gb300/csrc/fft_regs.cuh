@@ -20,8 +20,21 @@
 namespace specula {
 
 // ---- small complex helpers ------------------------------------------------
-__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+// A complex value (re, im) sits in a register pair, so complex additions and
+// real scalings are single packed float32 instructions (add/mul/fma .f32x2 on
+// sm_100+), rounded as the two scalar operations would be.
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) {
+  return __fadd2_rn(a, make_float2(-b.x, -b.y));
+}
+// b + s e and b - s e with s = -i (forward) or +i (inverse): mixed signs per
+// component, so two scalar additions each
+template <bool INV> __device__ __forceinline__ float2 cadd_mi(float2 b, float2 e) {
+  return INV ? make_float2(b.x - e.y, b.y + e.x) : make_float2(b.x + e.y, b.y - e.x);
+}
+template <bool INV> __device__ __forceinline__ float2 csub_mi(float2 b, float2 e) {
+  return INV ? make_float2(b.x + e.y, b.y - e.x) : make_float2(b.x - e.y, b.y + e.x);
+}
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
@@ -49,6 +62,10 @@ constexpr int kCodeletTotal = codelet_total();
 
 // (cos, sin) of 2 pi j / n, per TU
 static __constant__ float2 c_codelet_tw[kCodeletTotal];
+// the base butterflies' real constants as broadcast pairs (c, c):
+// [0] cos 2pi/3, [1] sin 2pi/3, [2] cos 2pi/5, [3] cos 4pi/5, [4] sin 2pi/5,
+// [5] sin 4pi/5, [6] -sin 2pi/5
+static __constant__ float2 c_bfly_pairs[7];
 
 static inline cudaError_t upload_codelet_twiddles() {
   float2 h[kCodeletTotal];
@@ -60,7 +77,15 @@ static inline cudaError_t upload_codelet_twiddles() {
       h[off + j] = make_float2((float)cos(a), (float)sin(a));
     }
   }
-  return cudaMemcpyToSymbol(c_codelet_tw, h, sizeof(h));
+  cudaError_t e = cudaMemcpyToSymbol(c_codelet_tw, h, sizeof(h));
+  if (e != cudaSuccess) return e;
+  const float v[7] = {(float)cos(2.0 * M_PI / 3.0), (float)sin(2.0 * M_PI / 3.0),
+                      (float)cos(2.0 * M_PI / 5.0), (float)cos(4.0 * M_PI / 5.0),
+                      (float)sin(2.0 * M_PI / 5.0), (float)sin(4.0 * M_PI / 5.0),
+                      -(float)sin(2.0 * M_PI / 5.0)};
+  float2 hp[7];
+  for (int i = 0; i < 7; ++i) hp[i] = make_float2(v[i], v[i]);
+  return cudaMemcpyToSymbol(c_bfly_pairs, hp, sizeof(hp));
 }
 
 // W_N^J for the forward (exp(-2 pi i J/N)) or inverse (exp(+...)) sign.
@@ -84,41 +109,40 @@ template <bool INV> __device__ __forceinline__ void bfly2(float2 &a, float2 &b) 
 }
 
 template <bool INV> __device__ __forceinline__ void bfly3(float2 &x0, float2 &x1, float2 &x2) {
-  // c = cos(2pi/3) = -1/2, s = sin(2pi/3) from the table
-  const float2 w = c_codelet_tw[codelet_offset(3) + 1];
-  float2 t1 = cadd(x1, x2);
-  float2 t2 = make_float2(x0.x + w.x * t1.x, x0.y + w.x * t1.y);
-  float2 d = csub(x1, x2);
-  float2 t3 = mul_mi<INV>(make_float2(w.y * d.x, w.y * d.y));
+  // x0 + c (x1 + x2) +- s (x1 - x2) rotated, c = cos(2pi/3) = -1/2, s = sin(2pi/3)
+  const float2 t1 = cadd(x1, x2);
+  const float2 t2 = __ffma2_rn(c_bfly_pairs[0], t1, x0);
+  const float2 t3 = __fmul2_rn(c_bfly_pairs[1], csub(x1, x2));
   x0 = cadd(x0, t1);
-  x1 = cadd(t2, t3);
-  x2 = csub(t2, t3);
+  x1 = cadd_mi<INV>(t2, t3);
+  x2 = csub_mi<INV>(t2, t3);
 }
 
 template <bool INV> __device__ __forceinline__ void bfly4(float2 &x0, float2 &x1, float2 &x2, float2 &x3) {
-  float2 a = cadd(x0, x2), b = csub(x0, x2);
-  float2 c = cadd(x1, x3), d = mul_mi<INV>(csub(x1, x3));
+  const float2 a = cadd(x0, x2), b = csub(x0, x2);
+  const float2 c = cadd(x1, x3), e = csub(x1, x3);
   x0 = cadd(a, c);
   x2 = csub(a, c);
-  x1 = cadd(b, d);
-  x3 = csub(b, d);
+  x1 = cadd_mi<INV>(b, e);
+  x3 = csub_mi<INV>(b, e);
 }
 
 template <bool INV>
 __device__ __forceinline__ void bfly5(float2 &x0, float2 &x1, float2 &x2, float2 &x3, float2 &x4) {
-  const float2 w1 = c_codelet_tw[codelet_offset(5) + 1];  // (cos 2pi/5, sin 2pi/5)
-  const float2 w2 = c_codelet_tw[codelet_offset(5) + 2];  // (cos 4pi/5, sin 4pi/5)
-  float2 a1 = cadd(x1, x4), b1 = csub(x1, x4);
-  float2 a2 = cadd(x2, x3), b2 = csub(x2, x3);
-  float2 p1 = make_float2(x0.x + w1.x * a1.x + w2.x * a2.x, x0.y + w1.x * a1.y + w2.x * a2.y);
-  float2 p2 = make_float2(x0.x + w2.x * a1.x + w1.x * a2.x, x0.y + w2.x * a1.y + w1.x * a2.y);
-  float2 q1 = mul_mi<INV>(make_float2(w1.y * b1.x + w2.y * b2.x, w1.y * b1.y + w2.y * b2.y));
-  float2 q2 = mul_mi<INV>(make_float2(w2.y * b1.x - w1.y * b2.x, w2.y * b1.y - w1.y * b2.y));
-  x0 = make_float2(x0.x + a1.x + a2.x, x0.y + a1.y + a2.y);
-  x1 = cadd(p1, q1);
-  x4 = csub(p1, q1);
-  x2 = cadd(p2, q2);
-  x3 = csub(p2, q2);
+  // (cos, sin) of 2pi/5 and 4pi/5 as broadcast pairs
+  const float2 c1 = c_bfly_pairs[2], c2 = c_bfly_pairs[3];
+  const float2 s1 = c_bfly_pairs[4], s2 = c_bfly_pairs[5], ns1 = c_bfly_pairs[6];
+  const float2 a1 = cadd(x1, x4), b1 = csub(x1, x4);
+  const float2 a2 = cadd(x2, x3), b2 = csub(x2, x3);
+  const float2 p1 = __ffma2_rn(c1, a1, __ffma2_rn(c2, a2, x0));
+  const float2 p2 = __ffma2_rn(c2, a1, __ffma2_rn(c1, a2, x0));
+  const float2 q1 = __ffma2_rn(s1, b1, __fmul2_rn(s2, b2));
+  const float2 q2 = __ffma2_rn(s2, b1, __fmul2_rn(ns1, b2));
+  x0 = cadd(x0, cadd(a1, a2));
+  x1 = cadd_mi<INV>(p1, q1);
+  x4 = csub_mi<INV>(p1, q1);
+  x2 = cadd_mi<INV>(p2, q2);
+  x3 = csub_mi<INV>(p2, q2);
 }
 
 // ---- generic in-register DFT: X[k] = sum_n x[n] W_N^{nk}, natural order ----
