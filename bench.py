@@ -195,13 +195,49 @@ def dist_setup():
 
 # ------------------------------------------------------------------ CPU oracle
 
-class OracleSample:
-    """The FP64 oracle on one frame of the ELT workload: all 35 layers
-    extracted, n_mod_timed of the 48 modulation points imaged (time scaled to
-    48), slopes and the 4000-mode MVM.  Two oracle screens are cycled over the
-    35 layers (the timing does not depend on screen values)."""
+def _mod_points_sum(E, ms, mask, n, mod_amp, n_mod):
+    """Summed |IDFT(mask DFT(pad(E tilt_m)))|^2 over the modulation points ms:
+    the oracle's pyramid steps, point by point."""
+    from oracle import geometry
+    from oracle.dft import centred_coords, centred_dft2, centred_idft2
+    N = 2 * n
+    off = (N - n) // 2
+    x = centred_coords(n)
+    cs, sn = geometry.mod_angles(n_mod)
+    I = np.zeros((N, N))
+    for m in ms:
+        tilt = np.exp(2j * np.pi * mod_amp * (x[None, :] * cs[m] + x[:, None] * sn[m]) / n)
+        P = np.zeros((N, N), dtype=np.complex128)
+        P[off:off + n, off:off + n] = E * tilt
+        I += np.abs(centred_idft2(centred_dft2(P) * mask)) ** 2
+    return I
 
-    def __init__(self, n_mod_timed=4):
+
+_POOL = {}
+
+
+def _pool_init(mask, n, mod_amp, n_mod):
+    _POOL.update(mask=mask, n=n, mod_amp=mod_amp, n_mod=n_mod)
+
+
+def _pool_mod_points(args):
+    E, ms = args
+    return _mod_points_sum(E, ms, _POOL["mask"], _POOL["n"], _POOL["mod_amp"], _POOL["n_mod"])
+
+
+def host_cores():
+    return len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+
+
+class OracleFrame:
+    """The FP64 oracle on whole frames of the ELT workload: all 35 layers
+    extracted, all 48 modulation points imaged, binning, slopes and the
+    4000-mode MVM, nothing scaled.  Two oracle screens are cycled over the 35
+    layers (the timing does not depend on screen values).  frame() runs in
+    this process, or with the modulation points spread over a pool of
+    spawned processes (one per host core; every process single-threaded)."""
+
+    def __init__(self):
         import synth
         from oracle import geometry, pyramid, screens
         wl = synth.workload(WORKLOAD)
@@ -214,177 +250,102 @@ class OracleSample:
         self.scr = [base[k % 2].astype(np.float64) for k in range(len(wl.layers))]
         self.amp = geometry.pupil_mask(self.n, s.pupil.obsc_frac).astype(np.float64)
         self.valid = geometry.valid_subaps(self.amp.astype(np.uint8), s.pwfs.n_sub)
-        ns = 2 * len(self.valid)
-        self.R = synth.normal_draws(7, (wl.n_modes, ns)) / np.sqrt(ns)
+        self.n_slopes = 2 * len(self.valid)
+        self.R = synth.normal_draws(7, (wl.n_modes, self.n_slopes)) / np.sqrt(self.n_slopes)
         self.mask = pyramid.pyramid_mask(2 * self.n, self.n)
-        self.n_mod_timed = n_mod_timed
-        self.desc = (f"one {WORKLOAD} frame: 35-layer extraction + {n_mod_timed} of "
-                     f"{s.pwfs.n_mod} modulation points (time scaled x"
-                     f"{s.pwfs.n_mod // n_mod_timed}) + slopes + {wl.n_modes}x{ns} MVM; "
-                     f"FP64 NumPy oracle, single process")
+        self.pool = None
+        self.cores = 1
 
-    def step(self, t=0.001):
-        """Seconds of oracle work for one full frame (scaled as described)."""
-        from oracle import atmo, geometry, pyramid, recon, slopes
-        from oracle.dft import centred_coords, centred_dft2, centred_idft2
+    def open_pool(self):
+        import multiprocessing as mp
+        self.cores = host_cores()
+        s = self.s
+        self.pool = mp.get_context("spawn").Pool(
+            self.cores, initializer=_pool_init,
+            initargs=(self.mask, self.n, s.pwfs.mod_amp, s.pwfs.n_mod))
+        self.chunks = [list(range(k, s.pwfs.n_mod, self.cores))
+                       for k in range(min(self.cores, s.pwfs.n_mod))]
+
+    def close_pool(self):
+        if self.pool is not None:
+            self.pool.close()
+            self.pool.join()
+            self.pool = None
+
+    def describe(self, pooled):
+        where = (f"the {self.s.pwfs.n_mod} modulation points spread over {self.cores} spawned "
+                 f"single-threaded processes, the rest in the parent"
+                 if pooled else "all in one single-threaded process")
+        return (f"whole {WORKLOAD} frames (35-layer extraction, {self.s.pwfs.n_mod} modulation "
+                f"points, binning, slopes, {self.wl.n_modes}x{self.n_slopes} MVM), {where}; "
+                f"FP64 NumPy oracle, nothing scaled")
+
+    def frame(self, t=0.001):
+        """Seconds of one whole frame."""
+        from oracle import atmo, pyramid, recon, slopes
         s, n = self.s, self.n
         t0 = time.perf_counter()
         phi = atmo.atmo_extract(self.scr, self.wl.layers, s.source, n, s.pupil.pitch_m, t)
-        t1 = time.perf_counter()
-        cs, sn = geometry.mod_angles(s.pwfs.n_mod)
-        stride = s.pwfs.n_mod // self.n_mod_timed
-        N = 2 * n
-        off = (N - n) // 2
-        x = centred_coords(n)
         E = self.amp * np.exp(1j * phi)
-        I = np.zeros((N, N))
-        for m in range(0, s.pwfs.n_mod, stride):
-            tilt = np.exp(2j * np.pi * s.pwfs.mod_amp
-                          * (x[None, :] * cs[m] + x[:, None] * sn[m]) / n)
-            P = np.zeros((N, N), dtype=np.complex128)
-            P[off:off + n, off:off + n] = E * tilt
-            I += np.abs(centred_idft2(centred_dft2(P) * self.mask)) ** 2
-        t2 = time.perf_counter()
-        det = pyramid.bin_image(I / self.n_mod_timed, n // s.pwfs.n_sub)
-        sl = slopes.pyr_slopes(det, s.pwfs.n_sub, self.valid)
-        recon.mvm(self.R, sl)
-        t3 = time.perf_counter()
-        return (t1 - t0) + (t2 - t1) * (s.pwfs.n_mod / self.n_mod_timed) + (t3 - t2)
-
-    def unit(self, k, t=0.001):
-        """One unit of the frame, in rotation: k % 3 = 0 the 35-layer
-        extraction (kept for the next units), 1 one modulation point (cycling
-        over the 48), 2 binning, slopes and the MVM.  Returns (unit, seconds)."""
-        from oracle import atmo, geometry, pyramid, recon, slopes
-        from oracle.dft import centred_coords, centred_dft2, centred_idft2
-        s, n = self.s, self.n
-        u = k % 3
-        t0 = time.perf_counter()
-        if u == 0 or not hasattr(self, "_E"):
-            phi = atmo.atmo_extract(self.scr, self.wl.layers, s.source, n, s.pupil.pitch_m, t)
-            self._E = self.amp * np.exp(1j * phi)
-            self._I = np.zeros((2 * n, 2 * n))
-            u = 0
-        elif u == 1:
-            cs, sn = geometry.mod_angles(s.pwfs.n_mod)
-            m = (k // 3) % s.pwfs.n_mod
-            N = 2 * n
-            off = (N - n) // 2
-            x = centred_coords(n)
-            tilt = np.exp(2j * np.pi * s.pwfs.mod_amp * (x[None, :] * cs[m] + x[:, None] * sn[m]) / n)
-            P = np.zeros((N, N), dtype=np.complex128)
-            P[off:off + n, off:off + n] = self._E * tilt
-            self._I += np.abs(centred_idft2(centred_dft2(P) * self.mask)) ** 2
+        if self.pool is None:
+            I = _mod_points_sum(E, range(s.pwfs.n_mod), self.mask, n, s.pwfs.mod_amp,
+                                s.pwfs.n_mod)
         else:
-            det = pyramid.bin_image(self._I / s.pwfs.n_mod, n // s.pwfs.n_sub)
-            sl = slopes.pyr_slopes(det, s.pwfs.n_sub, self.valid)
-            recon.mvm(self.R, sl)
-        return u, time.perf_counter() - t0
-
-
-def cpu_cores_used():
-    # NumPy's pocketfft and the oracle loops run on one thread; BLAS is
-    # limited to one thread at start-up
-    return 1
-
-
-# ---- the oracle on all host cores: modulation points split over processes
-_POOL = {}
-
-
-def _pool_init(mask, n, mod_amp, n_mod):
-    _POOL.update(mask=mask, n=n, mod_amp=mod_amp, n_mod=n_mod)
-
-
-def _pool_mod_points(args):
-    """Summed |IDFT(mask DFT(pad(E tilt_m)))|^2 over the given points."""
-    E, ms = args
-    from oracle import geometry
-    from oracle.dft import centred_coords, centred_dft2, centred_idft2
-    n, N = _POOL["n"], 2 * _POOL["n"]
-    off = (N - n) // 2
-    x = centred_coords(n)
-    cs, sn = geometry.mod_angles(_POOL["n_mod"])
-    I = np.zeros((N, N))
-    for m in ms:
-        tilt = np.exp(2j * np.pi * _POOL["mod_amp"] * (x[None, :] * cs[m] + x[:, None] * sn[m]) / n)
-        P = np.zeros((N, N), dtype=np.complex128)
-        P[off:off + n, off:off + n] = E * tilt
-        I += np.abs(centred_idft2(centred_dft2(P) * _POOL["mask"])) ** 2
-    return I
-
-
-def all_cores_baseline(sample, n_frames=2):
-    """One full frame (all 48 modulation points) of the oracle with the
-    modulation points spread over one spawned process per host core."""
-    import multiprocessing as mp
-    from oracle import atmo, pyramid, recon, slopes
-    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
-    s = sample.s
-    pool = mp.get_context("spawn").Pool(cores, initializer=_pool_init,
-                                         initargs=(sample.mask, sample.n, s.pwfs.mod_amp,
-                                                   s.pwfs.n_mod))
-    try:
-        chunks = [list(range(k, s.pwfs.n_mod, cores)) for k in range(min(cores, s.pwfs.n_mod))]
-        times = []
-        for f in range(n_frames + 1):
-            t0 = time.perf_counter()
-            phi = atmo.atmo_extract(sample.scr, sample.wl.layers, s.source, sample.n,
-                                    s.pupil.pitch_m, 0.001 * (f + 1))
-            E = sample.amp * np.exp(1j * phi)
-            parts = pool.map_async(_pool_mod_points, [(E, c) for c in chunks]).get(timeout=600)
+            parts = self.pool.map_async(_pool_mod_points,
+                                        [(E, c) for c in self.chunks]).get(timeout=600)
             I = parts[0]
             for q in parts[1:]:
                 I = I + q
-            det = pyramid.bin_image(I / s.pwfs.n_mod, sample.n // s.pwfs.n_sub)
-            sl = slopes.pyr_slopes(det, s.pwfs.n_sub, sample.valid)
-            recon.mvm(sample.R, sl)
-            if f > 0:
-                times.append(time.perf_counter() - t0)
+        det = pyramid.bin_image(I / s.pwfs.n_mod, n // s.pwfs.n_sub)
+        sl = slopes.pyr_slopes(det, s.pwfs.n_sub, self.valid)
+        recon.mvm(self.R, sl)
+        return time.perf_counter() - t0
+
+
+def cpu_baselines(n_pooled=3):
+    """The oracle's frame rate on the host: whole frames with the points over
+    all cores (1 warm-up, n_pooled timed, mean), and one whole frame in one
+    process."""
+    sample = OracleFrame()
+    sample.open_pool()
+    try:
+        sample.frame(0.001)
+        tp = [sample.frame(0.001 * (k + 2)) for k in range(n_pooled)]
     finally:
-        pool.close()
-        pool.join()
-    return {"value": 1.0 / min(times), "unit": "frames/s", "cores": cores, "kind": "oracle",
-            "sample": "one full %s frame (all %d modulation points spread over %d spawned "
-                      "processes, extraction / slopes / MVM in the parent), best of %d"
-                      % (WORKLOAD, s.pwfs.n_mod, cores, n_frames)}
+        sample.close_pool()
+    pooled = {"value": n_pooled / sum(tp), "unit": "frames/s", "cores": sample.cores,
+              "kind": "oracle",
+              "sample": sample.describe(True) + f"; mean of {n_pooled} after one warm-up"}
+    t1 = sample.frame(0.001)
+    single = {"value": 1.0 / t1, "unit": "frames/s", "cores": 1, "kind": "oracle",
+              "sample": sample.describe(False) + "; one frame"}
+    return pooled, single
 
 
 def reference_leg(args, ws, rank):
+    """The reference arm: the oracle (the paper ships no program to run) on
+    whole frames, each step one frame with the points over all host cores."""
     if rank != 0:
         return
-    sample = OracleSample()
-    desc = sample.desc
-    n_mod = sample.s.pwfs.n_mod
-    if (args.warmup + args.steps) * 2.5 <= 180.0 or args.steps < 3:
-        # each step: the frame sample (about 2 s of host work)
+    sample = OracleFrame()
+    sample.open_pool()
+    try:
         times = []
         for k in range(args.warmup + args.steps):
-            t = sample.step(0.001 * (k + 1))
+            t = sample.frame(0.001 * (k + 1))
             if k >= args.warmup:
                 times.append(t)
-        per = sum(times) / len(times)
-    else:
-        # many steps: each step one unit of the frame in rotation (extraction,
-        # one modulation point, slopes + MVM; well under a second each), the
-        # frame time assembled from the units' mean times
-        acc = {0: [], 1: [], 2: []}
-        for k in range(args.warmup + args.steps):
-            u, t = sample.unit(k, 0.001 * (k // 3 + 1))
-            if k >= args.warmup:
-                acc[u].append(t)
-        mean = {u: sum(v) / len(v) for u, v in acc.items() if v}
-        per = mean.get(0, 0.0) + n_mod * mean.get(1, 0.0) + mean.get(2, 0.0)
-        desc = (f"one {WORKLOAD} frame assembled from per-step units in rotation: 35-layer "
-                f"extraction, one of {n_mod} modulation points (x{n_mod}), slopes + MVM; "
-                f"FP64 NumPy oracle, single process")
+    finally:
+        sample.close_pool()
+    per = sum(times) / len(times)
     value = 1.0 / per
+    desc = sample.describe(True)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "frames/s",
             "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": per * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "sample": desc},
-            "cpu_baseline": {"value": value, "unit": "frames/s", "cores": cpu_cores_used(),
+            "cpu_baseline": {"value": value, "unit": "frames/s", "cores": sample.cores,
                              "kind": "oracle", "sample": desc},
             "e2e": {"value": value, "unit": "frames/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
@@ -977,12 +938,7 @@ def gpu_leg(args, ws, rank, local):
             line["learned"] = learned_leg(ctx)
             line["gemm_bf16"] = gemm_leg(ctx, pk)
         if not args.no_cpu_baseline:
-            sample = OracleSample()
-            per = min(sample.step(0.001 * (k + 1)) for k in range(3))
-            desc = sample.desc + ", best of 3"
-            line["cpu_baseline"] = {"value": 1.0 / per, "unit": "frames/s",
-                                    "cores": cpu_cores_used(), "kind": "oracle", "sample": desc}
-            line["cpu_baseline_all_cores"] = all_cores_baseline(sample)
+            line["cpu_baseline"], line["cpu_baseline_single_core"] = cpu_baselines()
         print(json.dumps(line), flush=True)
     ctx.close()
     if dist:

@@ -463,10 +463,15 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 160 ? 4 : 3) k_colfilt_bin(
   const int col0e = col0 & ~1, sh = col0 - col0e;
   const int W = (TC + 1) & ~1, nch = W / 2;
   {
-    const float2 *src = rows_in + (size_t)it * n_pix * N + col0e;
-    for (int e = threadIdx.x; e < n_pix * nch; e += blockDim.x) {
-      const int jj = e / nch, q = e - jj * nch;
-      cp_async16(s_tile + jj * W + 2 * q, src + (size_t)jj * N + 2 * q);
+    // thread t copies chunk t % nch of the rows t / nch + k R (no division
+    // in the loop)
+    const int R = blockDim.x / nch, t = threadIdx.x;
+    if (t < R * nch) {
+      const int q = t % nch, r0 = t / nch;
+      const float2 *src = rows_in + ((size_t)it * n_pix + r0) * N + col0e + 2 * q;
+      float2 *dst = s_tile + r0 * W + 2 * q;
+      for (int r = r0; r < n_pix; r += R, src += (size_t)R * N, dst += R * W)
+        cp_async16(dst, src);
     }
   }
   const int vec = threadIdx.x / G, lane = threadIdx.x % G;
@@ -540,6 +545,19 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 160 ? 4 : 3) k_colfilt_bin(
   const int nd = N / bsz, nbx = TC / bsz;
   float *dst = part + ((size_t)(b % nbw) * n_mod + m) * nd * nd;
   const float *s_I = reinterpret_cast<const float *>(smem_k);
+  if (bsz == 5 && nbx == 1) {
+    // the 39 m pupil's 5 x 5 bins, one bin column per tile: unrolled sums
+    for (int yb = threadIdx.x; yb < nd; yb += blockDim.x) {
+      const float *c0 = s_I + yb * 5;
+      float v = 0.f;
+#pragma unroll
+      for (int rr = 0; rr < 5; ++rr)
+#pragma unroll
+        for (int cc = 0; cc < 5; ++cc) v += c0[cc * 2 * CS + rr];
+      dst[(size_t)yb * nd + col0 / 5] = v;
+    }
+    return;
+  }
   for (int q = threadIdx.x; q < nd * nbx; q += blockDim.x) {
     const int yb = q / nbx, xb = q - yb * nbx;
     float v = 0.f;
