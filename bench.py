@@ -774,7 +774,7 @@ def gpu_leg(args, ws, rank, local):
     timed(3, W)
     msl = timed(K, W)
     variants["learned_mlp"] = {"frames_per_s": K / (sum(msl) / 1e3), "ms_per_step": sum(msl) / K,
-                               "net": "%d-2048-2048-%d GELU, bf16 tcgen05 GEMMs, batch 1"
+                               "net": "%d-2048-2048-%d GELU, batch 1: bf16 weight rows streamed by k_mlp_gemv on CUDA cores (tcgen05 GEMMs serve batches above 4)"
                                       % (fr.n_slopes, fr.n_modes)}
     fr.use_learned(None)
     mlp.close()

@@ -457,7 +457,10 @@ int specula_atmo_extract(specula_ctx *ctx, int32_t n_layers,
  * current device.  The first call on a device looks up the array's device
  * address (cudaGetSymbolAddress): make that call before any stream capture.
  * All calls share the array, so calls whose kernels overlap on the GPU race
- * and must be ordered by the caller.  Allocates nothing. */
+ * and must be ordered by the caller.  The address is kept per device for
+ * the rest of the process: after a cudaDeviceReset (or anything else that
+ * destroys and recreates the device's primary context) it is stale, and this
+ * entry point must not be used on that device again.  Allocates nothing. */
 int specula_atmo_extract_noalloc(int32_t n_layers, const specula_layer_desc *layers,
                                  const float *const *screens_dev,
                                  const specula_source_desc *source,

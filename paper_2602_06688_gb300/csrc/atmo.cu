@@ -194,7 +194,10 @@ extern "C" int specula_atmo_extract(specula_ctx *ctx, int32_t n_layers,
 // The array's device address is looked up once per device, with that device
 // current, by the first call made on it (cudaGetSymbolAddress; in host code
 // the array's name is only a host-side stand-in).  Make that first call
-// before any stream capture on the device.
+// before any stream capture on the device.  The address is cached per device
+// number for the rest of the process, so a device reset (which recreates the
+// primary context and may move the array) leaves it stale: the header tells
+// callers not to use this entry point on a device after a reset.
 namespace {
 
 constexpr int kNoAllocEntries = SPECULA_ATMO_MAX_LAYERS * 2 * SPECULA_ATMO_MAX_PIX;

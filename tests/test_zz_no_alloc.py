@@ -50,19 +50,32 @@ def test_noalloc_matches_context_extraction_twice():
 
 
 def test_noalloc_rejects_sizes_beyond_its_array():
-    need_gpu()
+    """Sizes beyond the fixed array are refused before any launch; the calls
+    get real buffers of the requested sizes, so a regression in the checks
+    would fail the assertions (the output would change) rather than touch
+    memory outside them."""
+    torch = need_gpu()
     sp = load_pkg()
     lib = sp.lib()
     layers, src, screens, n, pitch = _case()
+    scr = torch.tensor(screens[0], device="cuda")               # 256 x 256, as described
     L1 = (sp.LayerDesc * 1)(sp.layer_desc(layers[0]))
-    ptr = (C.c_void_p * 1)(C.c_void_p(16))
-    too_wide = sp.PupilDesc(8193, 0.01, 0.0)
+    ptr = (C.c_void_p * 1)(C.c_void_p(scr.data_ptr()))
+    wide = 8193
+    out = torch.full((wide, wide), 7.0, device="cuda")
     st = lib.specula_atmo_extract_noalloc(1, L1, ptr, C.byref(sp.source_desc(src)),
-                                          C.byref(too_wide), 0.0, None, C.c_void_p(16), None)
+                                          C.byref(sp.PupilDesc(wide, 0.01, 0.0)), 0.0, None,
+                                          C.c_void_p(out.data_ptr()), None)
+    torch.cuda.synchronize()
     assert st == sp.EUNSUPPORTED
+    assert bool((out == 7.0).all())
+    del out
     many = (sp.LayerDesc * 65)(*([sp.layer_desc(layers[0])] * 65))
-    ptrs = (C.c_void_p * 65)(*([C.c_void_p(16)] * 65))
+    ptrs = (C.c_void_p * 65)(*([C.c_void_p(scr.data_ptr())] * 65))
+    out = torch.full((n, n), 7.0, device="cuda")
     st = lib.specula_atmo_extract_noalloc(65, many, ptrs, C.byref(sp.source_desc(src)),
                                           C.byref(sp.PupilDesc(n, pitch, 0.0)), 0.0, None,
-                                          C.c_void_p(16), None)
+                                          C.c_void_p(out.data_ptr()), None)
+    torch.cuda.synchronize()
     assert st == sp.EUNSUPPORTED
+    assert bool((out == 7.0).all())
