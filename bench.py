@@ -663,6 +663,95 @@ def gemm_leg(ctx, pk, n=8192, reps=10):
     return out
 
 
+def gemm_rate(ctx, M, N, K, tf32, reps=10):
+    """Best event-timed rate of the library's tcgen05 GEMM (TFLOP/s)."""
+    import torch
+    import paper_2602_06688_gb300 as sp
+    g = torch.Generator(device="cuda").manual_seed(M + N + K)
+    A = torch.randn(M, K, device="cuda", generator=g)
+    B = torch.randn(N, K, device="cuda", generator=g)
+    if not tf32:
+        A, B = A.to(torch.bfloat16), B.to(torch.bfloat16)
+    C = torch.empty(M, N, device="cuda")
+    run = (lambda: sp.specula_gemm_tf32(ctx, A, B, C)) if tf32 else \
+        (lambda: sp.specula_gemm_bf16(ctx, A, B, C))
+    for _ in range(3):
+        run()
+    best = float("inf")
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        run()
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    del A, B, C
+    return 2.0 * M * N * K / (best / 1e3) / 1e12
+
+
+def dftgemm_leg(ctx, reps=20):
+    """The DFT-as-GEMM pyramid forms (bf16 x 3, tf32 x 3) on the 8 m system
+    (pwfs8m: 160 px pupil, 320^2 grid, 24 points, 40 x 40 subapertures, its
+    3-layer atmosphere extracted on the GPU) against the register-FFT tilt
+    form (autotuned): time per image and the normalised-intensity deviation
+    from the FFT form (the error against the FP64 oracle is asserted by the
+    parity tests)."""
+    import torch
+    import paper_2602_06688_gb300 as sp
+    import synth
+    from paper_2602_06688_gb300.frame import PwfsFrame
+    fr = PwfsFrame(ctx, synth.workload("pwfs8m"))
+    fr.frame(0.05)
+    torch.cuda.synchronize()
+    pu, pw, amp = fr.pupil, fr.pwfs, fr.amp
+    ph = fr.phase.reshape(1, fr.n_pix, fr.n_pix).clone()
+    nd = 2 * pw.n_sub
+    det = torch.empty(1, nd, nd, device="cuda")
+    ch, ka, ps = sp.specula_pwfs_autotune(ctx, pu, pw, amp, ph, det, reps=5)
+
+    def timed():
+        for _ in range(3):
+            sp.specula_pwfs_image(ctx, pu, pw, amp, ph, det)
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            sp.specula_pwfs_image(ctx, pu, pw, amp, ph, det)
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts) * 1e3, det[0].double().clone()
+
+    out = {"geometry": "pwfs8m: 160 px pupil, 320^2 grid, 24 modulation points, 40x40 "
+                       "subapertures", "bound": "normalised intensity within 1e-5 of FP64"}
+    us, ref = timed()
+    out["fft_tilt"] = {"us_per_image": us, "tiles": {"chunk": ch, "ka": ka, "passes": ps}}
+    rn = ref / ref.sum()
+    for form, name in ((sp.PWFS_FORM_DFTGEMM_BF16, "dftgemm_bf16x3"),
+                       (sp.PWFS_FORM_DFTGEMM_TF32, "dftgemm_tf32x3")):
+        sp.specula_pwfs_set_form(ctx, pu, pw, form)
+        us, d = timed()
+        dn = d / d.sum()
+        sp.specula_prof_enable(ctx, 4096)
+        for _ in range(10):
+            sp.specula_pwfs_image(ctx, pu, pw, amp, ph, det)
+        prof = sp.specula_prof_read(ctx)
+        sp.specula_prof_enable(ctx, 0)
+        out[name] = {"us_per_image": us,
+                     "norm_dev_vs_fft_form": float((dn - rn).abs().max() / rn.max()),
+                     "kernels_us": {k: v[0] / 10 * 1e3 for k, v in prof.items()}}
+    sp.specula_pwfs_set_form(ctx, pu, pw, sp.PWFS_FORM_TILT)
+    best = min(out["dftgemm_bf16x3"]["us_per_image"], out["dftgemm_tf32x3"]["us_per_image"])
+    out["kept_in_frame"] = best < out["fft_tilt"]["us_per_image"]
+    n, n_mod = fr.n_pix, pw.n_mod
+    out["gemm_tflops_stage_shape"] = {
+        "shape": [n_mod * 2 * n, 4 * n, 6 * n],
+        "bf16": gemm_rate(ctx, n_mod * 2 * n, 4 * n, 6 * n, False),
+        "tf32": gemm_rate(ctx, n_mod * 2 * n, 4 * n, 6 * n, True)}
+    return out
+
+
 # ------------------------------------------------------------------ GPU leg
 
 def gpu_leg(args, ws, rank, local):
@@ -937,6 +1026,8 @@ def gpu_leg(args, ws, rank, local):
         if not args.no_learned:
             line["learned"] = learned_leg(ctx)
             line["gemm_bf16"] = gemm_leg(ctx, pk)
+        meas["tf32_gemm_tflops_8192"] = gemm_rate(ctx, 8192, 8192, 8192, True)
+        line["variants"]["dftgemm_8m"] = dftgemm_leg(ctx)
         if not args.no_cpu_baseline:
             line["cpu_baseline"], line["cpu_baseline_single_core"] = cpu_baselines()
         print(json.dumps(line), flush=True)

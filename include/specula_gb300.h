@@ -197,7 +197,8 @@ int specula_check_guards(specula_ctx *ctx, int32_t *n_checked, int32_t *n_bad);
 #define SPECULA_K_CCD           19  /* detector photon and readout noise          */
 #define SPECULA_K_INFSCREEN     20  /* infinite screens: set-up and line growth   */
 #define SPECULA_K_PEAK          21  /* fused multiply-add rate probe              */
-#define SPECULA_K_COUNT         22
+#define SPECULA_K_PWFS_DFTGEMM  22  /* pyramid DFT-as-GEMM form: packing, bins    */
+#define SPECULA_K_COUNT         23
 
 /* Enable (capacity > 0: room for that many kernel records; allocates CUDA
  * events; set-up call) or disable (capacity = 0) per-kernel event timing.
@@ -526,11 +527,25 @@ int specula_pwfs_set_slots(specula_ctx *ctx, const specula_pupil_desc *pupil,
  *    of the peak normalised intensity for a flat wavefront on 64-120 px
  *    pupils).  Needs pad = 2 and the sizes of the two-pass form;
  *    SPECULA_EUNSUPPORTED else.
+ *  SPECULA_PWFS_FORM_DFTGEMM_BF16, SPECULA_PWFS_FORM_DFTGEMM_TF32: the
+ *    modulation steps of the tilt form with the separable filter of every
+ *    row and every column (forward DFT of the pupil's half, mask, inverse
+ *    DFT: one N x n_pix complex operator, built in float64) applied as a
+ *    dense product on the tensor cores: one real GEMM per axis (the complex
+ *    product in its real embedding) with three-term split precision
+ *    (A B ~ A_hi B_hi + A_hi B_lo + A_lo B_hi) in bf16 or tf32 operands and
+ *    float32 accumulation; then |.|^2 / n_mod and the bins.  The DFT-as-GEMM
+ *    variant for small padded grids: N <= 512, 2N a multiple of 128,
+ *    6 n_pix a multiple of 64 (bf16) or 32 (tf32); SPECULA_EUNSUPPORTED
+ *    else, and for slot ranges.  Allocates the operator and its workspace
+ *    (for the 320^2 grid of the 8 m system about 45 MB).
  * specula_pwfs_image then computes the image in the plan's form.  The
  * autotuner and the tile settings apply to the tilt form; autotune on a
- * plan in the shifted form returns SPECULA_EUNSUPPORTED. */
+ * plan in another form returns SPECULA_EUNSUPPORTED. */
 #define SPECULA_PWFS_FORM_TILT    0
 #define SPECULA_PWFS_FORM_SHIFTED 1
+#define SPECULA_PWFS_FORM_DFTGEMM_BF16 2
+#define SPECULA_PWFS_FORM_DFTGEMM_TF32 3
 int specula_pwfs_set_form(specula_ctx *ctx, const specula_pupil_desc *pupil,
                           const specula_pwfs_desc *pwfs, int32_t form);
 
@@ -713,6 +728,16 @@ int specula_mwfs_read(const specula_mwfs *mwfs, int32_t sensor, int32_t what, fl
  * (splits * M * N floats, caller-owned) and are summed in slice order.
  * Per-frame call: enqueues only. */
 int specula_gemm_bf16(specula_ctx *ctx, const void *A_dev, const void *B_dev, int32_t M,
+                      int32_t N, int32_t K, float *C_dev, int32_t splits, float *work_dev,
+                      void *stream);
+
+/* The same product with tf32 operands (kind::tf32): A, B float32 row-major,
+ * of which the tensor cores use the tf32 part (sign, 8-bit exponent, 10-bit
+ * mantissa; the low 13 bits are ignored, so callers round to tf32 first
+ * where rounding matters).  K a multiple of 32; otherwise as
+ * specula_gemm_bf16.  It serves the tf32 split-precision DFT-as-GEMM
+ * pyramid form and the measured tf32 rate.  Per-frame call: enqueues only. */
+int specula_gemm_tf32(specula_ctx *ctx, const float *A_dev, const float *B_dev, int32_t M,
                       int32_t N, int32_t K, float *C_dev, int32_t splits, float *work_dev,
                       void *stream);
 

@@ -15,7 +15,8 @@ from . import _abi
 from ._abi import (  # noqa: F401
     PupilDesc, SourceDesc, LayerDesc, PwfsDesc, ShDesc, SlopecDesc, ReconDesc, WfsDesc, InfLine,
     InfMove, INF_MAX_TASKS,
-    SpeculaError, SLOPES_PYR, SLOPES_SH, SLOPES_PYR_MAPS, PWFS_FORM_TILT, PWFS_FORM_SHIFTED, PREC_FP32, PREC_BF16,
+    SpeculaError, SLOPES_PYR, SLOPES_SH, SLOPES_PYR_MAPS, PWFS_FORM_TILT, PWFS_FORM_SHIFTED,
+    PWFS_FORM_DFTGEMM_BF16, PWFS_FORM_DFTGEMM_TF32, PREC_FP32, PREC_BF16,
     PREC_BF16X2,
     OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED, ENONFINITE, ENOPLAN,
 )
@@ -145,12 +146,12 @@ def specula_check_guards(ctx):
 (K_PWFS_ROWS_FWD, K_PWFS_COLS, K_PWFS_ROWS_INV, K_ATMO, K_SLOPES, K_RECON, K_SH,
  K_PWFS_FIELD, K_PWFS_BIN, K_CALIB, K_GEMM, K_MLP, K_MWFS, K_PWFS_ROWFILT,
  K_PWFS_COLFILT, K_PWFS_SM_FWD, K_PWFS_SM_ROWS, K_PWFS_SM_COLS, K_LOOP, K_CCD,
- K_INFSCREEN, K_PEAK) = range(22)
-K_COUNT = 22
+ K_INFSCREEN, K_PEAK, K_PWFS_DFTGEMM) = range(23)
+K_COUNT = 23
 KERNEL_NAMES = ["pwfs_rows_fwd", "pwfs_cols", "pwfs_rows_inv", "atmo_extract", "slopes",
                 "recon", "sh_spots", "pwfs_field", "pwfs_bin", "calib", "gemm", "mlp", "mwfs",
                 "pwfs_rowfilt", "pwfs_colfilt_bin", "pwfs_sm_fwd", "pwfs_sm_rows",
-                "pwfs_sm_colfilt_bin", "loop", "ccd", "infscreen", "fma_probe"]
+                "pwfs_sm_colfilt_bin", "loop", "ccd", "infscreen", "fma_probe", "pwfs_dftgemm"]
 
 
 def specula_prof_enable(ctx, capacity):
@@ -657,6 +658,20 @@ def specula_gemm_bf16(ctx, A, B, C, splits=1, work=None, stream=None):
         ctx.handle, _dev(A, torch.bfloat16, M * K, "A"), _dev(B, torch.bfloat16, N * K, "B"),
         int(M), int(N), int(K), _dev(C, torch.float32, M * N, "C"), int(splits),
         _dev(work, torch.float32, None, "work"), _stream(stream)), "specula_gemm_bf16")
+
+
+def specula_gemm_tf32(ctx, A, B, C, splits=1, work=None, stream=None):
+    """C (M, N) float32 = A (M, K) @ B (N, K)^T with tf32 operands (float32
+    storage) on the tensor cores."""
+    import torch
+    M, K = A.shape
+    N = B.shape[0]
+    if B.shape[1] != K:
+        raise ValueError("A and B must share K")
+    _abi.check(lib().specula_gemm_tf32(
+        ctx.handle, _dev(A, torch.float32, M * K, "A"), _dev(B, torch.float32, N * K, "B"),
+        int(M), int(N), int(K), _dev(C, torch.float32, M * N, "C"), int(splits),
+        _dev(work, torch.float32, None, "work"), _stream(stream)), "specula_gemm_tf32")
 
 
 def specula_col_stats(ctx, X, mean, std, stream=None):

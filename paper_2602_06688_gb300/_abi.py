@@ -12,7 +12,7 @@ LIB_PATH = os.path.join(HERE, "libspecula_gb300.so")
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED, ENONFINITE, ENOPLAN = \
     0, -1, -2, -3, -4, -5, -6, -7
 SLOPES_PYR, SLOPES_SH, SLOPES_PYR_MAPS = 0, 1, 2
-PWFS_FORM_TILT, PWFS_FORM_SHIFTED = 0, 1
+PWFS_FORM_TILT, PWFS_FORM_SHIFTED, PWFS_FORM_DFTGEMM_BF16, PWFS_FORM_DFTGEMM_TF32 = 0, 1, 2, 3
 PREC_FP32, PREC_BF16, PREC_BF16X2 = 0, 1, 2
 
 
@@ -142,6 +142,7 @@ SIGNATURES = {
     "specula_recon": (C.c_int, [vp, P(ReconDesc), vp, i32, vp, vp]),
     "specula_recon_convert": (C.c_int, [vp, i32, i32, vp, i32, vp, vp, vp]),
     "specula_gemm_bf16": (C.c_int, [vp, vp, vp, i32, i32, i32, vp, i32, vp, vp]),
+    "specula_gemm_tf32": (C.c_int, [vp, vp, vp, i32, i32, i32, vp, i32, vp, vp]),
     "specula_col_stats": (C.c_int, [vp, vp, i32, i32, vp, vp, vp]),
     "specula_affine_cols": (C.c_int, [vp, vp, C.c_int64, i32, vp, vp, vp, vp]),
     "specula_mlp_create": (C.c_int, [vp, i32, i32, i32, i32, i32, P(vp)]),

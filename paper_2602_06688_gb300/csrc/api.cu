@@ -517,13 +517,18 @@ extern "C" int specula_pwfs_set_form(specula_ctx *ctx, const specula_pupil_desc 
   if (!ctx) return SPECULA_EINVAL;
   int s = check_pwfs(pupil, pwfs);
   if (s) return s;
-  if (form != SPECULA_PWFS_FORM_TILT && form != SPECULA_PWFS_FORM_SHIFTED) return SPECULA_EINVAL;
+  if (form < SPECULA_PWFS_FORM_TILT || form > SPECULA_PWFS_FORM_DFTGEMM_TF32) return SPECULA_EINVAL;
   PwfsPlan *p = pwfs_plan_find(ctx, pupil, pwfs);
   if (!p) return SPECULA_ENOPLAN;
   SPECULA_CK(cudaSetDevice(ctx->device));
   if (form == SPECULA_PWFS_FORM_SHIFTED && !p->sm_chunk) {
     SPECULA_CK(cudaDeviceSynchronize());
     if ((s = pwfs_shifted_prepare(p))) return s;
+  }
+  if ((form == SPECULA_PWFS_FORM_DFTGEMM_BF16 || form == SPECULA_PWFS_FORM_DFTGEMM_TF32) &&
+      p->dg_form != form) {
+    SPECULA_CK(cudaDeviceSynchronize());
+    if ((s = pwfs_dftgemm_prepare(p, form))) return s;
   }
   p->form = form;
   return SPECULA_OK;

@@ -1,11 +1,15 @@
-// BF16 GEMM on the 5th-generation tensor cores (tcgen05), FP32 accumulate:
+// BF16 and TF32 GEMMs on the 5th-generation tensor cores (tcgen05), FP32
+// accumulate:
 //     C[M][N] = A[M][K] . B[N][K]^T        (both operands K-major, row-major)
 // The dense contractions of the learned reconstructor (its forward layers,
-// their gradients) and batched reconstructor MVMs run here.
+// their gradients), batched reconstructor MVMs and the DFT-as-GEMM pyramid
+// variant run here.  The TF32 kernel reads float32 storage (the tensor cores
+// use its upper 19 bits).
 //
 // One CTA per 128 x 128 output tile and K slice (split-K for small grids):
-//   warp 0, one thread : TMA loads of A and B tiles (64 K-elements, 128-byte
-//                        swizzle) into a 4-stage shared-memory ring
+//   warp 0, one thread : TMA loads of A and B tiles (128 bytes of K: 64 bf16
+//                        or 32 tf32, 128-byte swizzle) into a 4-stage
+//                        shared-memory ring
 //   warp 1             : allocates 128 tensor-memory columns; one thread
 //                        issues 4 tcgen05.mma (K = 16 each) per stage and
 //                        commits each stage back to the producer
@@ -24,15 +28,18 @@
 
 namespace specula {
 
-constexpr int GBM = 128, GBN = 128, GBK = 64, GSTAGES = 4;
+constexpr int GBM = 128, GBN = 128, GBK = 64, GSTAGES = 4;   // GBK: bf16 elements
 constexpr uint32_t G_A_BYTES = GBM * GBK * 2, G_B_BYTES = GBN * GBK * 2;
+// K elements per 128-byte row of a stage: 64 bf16 (TF32 = false) or 32 tf32
+template <bool TF32> constexpr int gbk() { return TF32 ? 32 : 64; }
 constexpr size_t G_SMEM = 1024 + GSTAGES * (G_A_BYTES + G_B_BYTES) + 256;
 
 __device__ __forceinline__ bool wait_noabort(uint64_t *bar, uint32_t parity) {
   return tc::mbar_wait(bar, parity, nullptr);
 }
 
-__global__ void __launch_bounds__(256, 1) k_gemm_bf16_tn(const __grid_constant__ CUtensorMap ta,
+template <bool TF32>
+__global__ void __launch_bounds__(256, 1) k_gemm_tn(const __grid_constant__ CUtensorMap ta,
                                                          const __grid_constant__ CUtensorMap tb,
                                                          float *__restrict__ out, int M, int N,
                                                          int kb_per_split, int kb_total,
@@ -78,8 +85,8 @@ __global__ void __launch_bounds__(256, 1) k_gemm_bf16_tn(const __grid_constant__
           break;
         }
         tc::mbar_arrive_expect_tx(full + s, G_A_BYTES + G_B_BYTES);
-        tc::tma_load_2d(sA + s * G_A_BYTES, &ta, full + s, (kb0 + i) * GBK, m0);
-        tc::tma_load_2d(sB + s * G_B_BYTES, &tb, full + s, (kb0 + i) * GBK, n0);
+        tc::tma_load_2d(sA + s * G_A_BYTES, &ta, full + s, (kb0 + i) * gbk<TF32>(), m0);
+        tc::tma_load_2d(sB + s * G_B_BYTES, &tb, full + s, (kb0 + i) * gbk<TF32>(), n0);
         ++issued;
       }
       // every issued copy lands before the CTA may leave
@@ -90,7 +97,8 @@ __global__ void __launch_bounds__(256, 1) k_gemm_bf16_tn(const __grid_constant__
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      constexpr uint32_t idesc = tc::idesc_bf16_f32(GBM, GBN);
+      constexpr uint32_t idesc =
+          TF32 ? tc::idesc_tf32_f32(GBM, GBN) : tc::idesc_bf16_f32(GBM, GBN);
       for (int i = 0; i < nk; ++i) {
         const int s = i % GSTAGES;
         if (!tc::mbar_wait(full + s, (i / GSTAGES) & 1, abort_flag)) {
@@ -101,8 +109,12 @@ __global__ void __launch_bounds__(256, 1) k_gemm_bf16_tn(const __grid_constant__
         const uint64_t ad = tc::desc_sw128(tc::smem_u32(sA + s * G_A_BYTES));
         const uint64_t bd = tc::desc_sw128(tc::smem_u32(sB + s * G_B_BYTES));
 #pragma unroll
-        for (int kk = 0; kk < GBK / 16; ++kk)   // +32 bytes of K per step
-          tc::mma_bf16(tmem, ad + 2 * kk, bd + 2 * kk, idesc, (i | kk) ? 1u : 0u);
+        for (int kk = 0; kk < 4; ++kk) {   // +32 bytes of K per step (16 bf16 or 8 tf32)
+          if constexpr (TF32)
+            tc::mma_tf32(tmem, ad + 2 * kk, bd + 2 * kk, idesc, (i | kk) ? 1u : 0u);
+          else
+            tc::mma_bf16(tmem, ad + 2 * kk, bd + 2 * kk, idesc, (i | kk) ? 1u : 0u);
+        }
         tc::mma_commit(empty + s);
       }
       tc::mma_commit(done);   // arrives when every issued MMA has finished
@@ -168,58 +180,63 @@ static EncodeTiledFn encode_fn() {
   return fn;
 }
 
-// rows x K bf16 row-major, box 64 (K) x box_rows, 128-byte swizzle
-static int make_map(CUtensorMap *m, const void *ptr, int rows, int K, int box_rows) {
+// rows x K row-major (bf16, or float32 read as tf32), box of 128 bytes of K
+// x box_rows, 128-byte swizzle
+static int make_map(CUtensorMap *m, const void *ptr, int rows, int K, int box_rows,
+                    bool tf32 = false) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) return SPECULA_ECUDA;
+  const int es_bytes = tf32 ? 4 : 2;
   cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
-  cuuint64_t strides[1] = {(cuuint64_t)K * 2};
-  cuuint32_t box[2] = {(cuuint32_t)GBK, (cuuint32_t)box_rows};
+  cuuint64_t strides[1] = {(cuuint64_t)K * es_bytes};
+  cuuint32_t box[2] = {(cuuint32_t)(128 / es_bytes), (cuuint32_t)box_rows};
   cuuint32_t es[2] = {1, 1};
-  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(ptr), dims, strides,
+  CUresult r = fn(m, tf32 ? CU_TENSOR_MAP_DATA_TYPE_TFLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                  const_cast<void *>(ptr), dims, strides,
                   box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? SPECULA_OK : SPECULA_ECUDA;
 }
 
-int gemm_check(const void *A, const void *B, int M, int N, int K) {
+int gemm_check(const void *A, const void *B, int M, int N, int K, bool tf32) {
   if (!A || !B || M < 1 || N < 1 || K < 1) return SPECULA_EINVAL;
-  if (M % GBM || N % GBN || K % GBK) return SPECULA_EUNSUPPORTED;
+  if (M % GBM || N % GBN || K % (tf32 ? gbk<true>() : gbk<false>())) return SPECULA_EUNSUPPORTED;
   if ((uintptr_t)A % 16 || (uintptr_t)B % 16) return SPECULA_EINVAL;
   return SPECULA_OK;
 }
 
 // splits that keep every K slice non-empty
-int gemm_splits(int K, int want) {
-  const int kb = K / GBK;
+int gemm_splits(int K, int want, bool tf32) {
+  const int kb = K / (tf32 ? gbk<true>() : gbk<false>());
   int s = std::max(1, std::min(want, kb));
   const int per = (kb + s - 1) / s;
   return (kb + per - 1) / per;
 }
 
-int gemm_bf16_tn(specula_ctx *ctx, const void *A, const void *B, int M, int N, int K, float *C,
-                 int splits, float *work, cudaStream_t st) {
-  int s = gemm_check(A, B, M, N, K);
+template <bool TF32>
+static int gemm_tn(specula_ctx *ctx, const void *A, const void *B, int M, int N, int K, float *C,
+                   int splits, float *work, cudaStream_t st) {
+  int s = gemm_check(A, B, M, N, K, TF32);
   if (s) return s;
   static bool attr_done[64] = {};
   int dev = 0;
   SPECULA_CK(cudaGetDevice(&dev));
   if (dev < 64 && !attr_done[dev]) {
-    SPECULA_CK(cudaFuncSetAttribute(k_gemm_bf16_tn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    SPECULA_CK(cudaFuncSetAttribute(k_gemm_tn<TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)G_SMEM));
     attr_done[dev] = true;
   }
   CUtensorMap ta, tb;
-  if ((s = make_map(&ta, A, M, K, GBM))) return s;
-  if ((s = make_map(&tb, B, N, K, GBN))) return s;
-  const int kb = K / GBK;
-  splits = gemm_splits(K, splits);
+  if ((s = make_map(&ta, A, M, K, GBM, TF32))) return s;
+  if ((s = make_map(&tb, B, N, K, GBN, TF32))) return s;
+  const int kb = K / gbk<TF32>();
+  splits = gemm_splits(K, splits, TF32);
   const int per = (kb + splits - 1) / splits;
   if (splits > 1 && !work) return SPECULA_EINVAL;
   float *dst = splits > 1 ? work : C;
   dim3 grid(N / GBN, M / GBM, splits);
   SPECULA_LAUNCH(ctx, SPECULA_K_GEMM, st,
-                 k_gemm_bf16_tn<<<grid, 256, G_SMEM, st>>>(ta, tb, dst, M, N, per, kb,
+                 k_gemm_tn<TF32><<<grid, 256, G_SMEM, st>>>(ta, tb, dst, M, N, per, kb,
                                                            ctx->status_dev));
   if (splits > 1) {
     const size_t n = (size_t)M * N;
@@ -228,6 +245,16 @@ int gemm_bf16_tn(specula_ctx *ctx, const void *A, const void *B, int M, int N, i
                                     st>>>(work, splits, n, C));
   }
   return SPECULA_OK;
+}
+
+int gemm_bf16_tn(specula_ctx *ctx, const void *A, const void *B, int M, int N, int K, float *C,
+                 int splits, float *work, cudaStream_t st) {
+  return gemm_tn<false>(ctx, A, B, M, N, K, C, splits, work, st);
+}
+
+int gemm_tf32_tn(specula_ctx *ctx, const float *A, const float *B, int M, int N, int K, float *C,
+                 int splits, float *work, cudaStream_t st) {
+  return gemm_tn<true>(ctx, A, B, M, N, K, C, splits, work, st);
 }
 
 }  // namespace specula
@@ -239,5 +266,13 @@ extern "C" int specula_gemm_bf16(specula_ctx *ctx, const void *A_dev, const void
                                  float *work_dev, void *stream) {
   if (!ctx || !C_dev || splits < 1) return SPECULA_EINVAL;
   return gemm_bf16_tn(ctx, A_dev, B_dev, M, N, K, C_dev, splits, work_dev,
+                      (cudaStream_t)stream);
+}
+
+extern "C" int specula_gemm_tf32(specula_ctx *ctx, const float *A_dev, const float *B_dev,
+                                 int32_t M, int32_t N, int32_t K, float *C_dev, int32_t splits,
+                                 float *work_dev, void *stream) {
+  if (!ctx || !C_dev || splits < 1) return SPECULA_EINVAL;
+  return gemm_tf32_tn(ctx, A_dev, B_dev, M, N, K, C_dev, splits, work_dev,
                       (cudaStream_t)stream);
 }

@@ -134,6 +134,13 @@ struct PwfsPlan {
   int n_pair_units = 0;
   int pair_units_for = -1;   // the slot range the unit table was built for
   std::vector<float2> gy_host;
+  // DFT-as-GEMM forms (pwfs_dftgemm.cu)
+  int dg_form = -1;     // the form the operator below was built for
+  int dg_M1 = 0, dg_M2 = 0;
+  DevBuf dg_B;          // [2N][6 n_pix] split operator (bf16 or float32/tf32)
+  DevBuf dg_A1, dg_A2;  // split operands of the row and column GEMMs
+  DevBuf dg_C1, dg_C2;  // [M][2N] float32 products
+  DevBuf dg_work;       // split-K partials of the row GEMM
 };
 
 struct ShPlan {
@@ -218,6 +225,9 @@ int pwfs_bin_reduce_range(specula_ctx *ctx, PwfsPlan *p, float *det, int nd2, in
                           cudaStream_t st);
 struct PwfsTablesHost;
 int pwfs_pair_init_device();
+int pwfs_dftgemm_prepare(PwfsPlan *p, int form);
+int pwfs_dftgemm_run(specula_ctx *ctx, PwfsPlan *p, const float *amp, const float *phase,
+                     int n_batch, float *det, cudaStream_t st);
 int pwfs_pair_configure(PwfsPlan *p);
 int pwfs_pair_tables(PwfsPlan *p, const PwfsTablesHost &T);
 int pwfs_pair_run(specula_ctx *ctx, PwfsPlan *p, const float *amp, const float *phase,
@@ -248,8 +258,10 @@ int sh_run(specula_ctx *ctx, ShPlan *plan, const float *amp, const float *phase,
 // what an earlier one relies on.  Needs up to 48 KB need no call.
 int ensure_dynamic_smem(const void *fn, size_t bytes);
 
-int gemm_check(const void *A, const void *B, int M, int N, int K);
-int gemm_splits(int K, int want);
+int gemm_check(const void *A, const void *B, int M, int N, int K, bool tf32 = false);
+int gemm_splits(int K, int want, bool tf32 = false);
+int gemm_tf32_tn(specula_ctx *ctx, const float *A, const float *B, int M, int N, int K, float *C,
+                 int splits, float *work, cudaStream_t st);
 int gemm_bf16_tn(specula_ctx *ctx, const void *A, const void *B, int M, int N, int K, float *C,
                  int splits, float *work, cudaStream_t st);
 

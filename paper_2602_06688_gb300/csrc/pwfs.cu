@@ -856,6 +856,8 @@ int pwfs_run(specula_ctx *ctx, PwfsPlan *p, const float *amp, const float *phase
     return SPECULA_EUNSUPPORTED;   // slot ranges: the two-pass tilt forms only
   if (p->form == SPECULA_PWFS_FORM_SHIFTED)
     return pwfs_shifted_run(ctx, p, amp, phase, n_batch, det, st);
+  if (p->form == SPECULA_PWFS_FORM_DFTGEMM_BF16 || p->form == SPECULA_PWFS_FORM_DFTGEMM_TF32)
+    return pwfs_dftgemm_run(ctx, p, amp, phase, n_batch, det, st);
   if (p->passes == 4) return pwfs_pair_run(ctx, p, amp, phase, n_batch, det, st);
   switch (p->N) {
     case 64: return run_split<8, 8>(ctx, p, amp, phase, n_batch, det, st);
