@@ -607,6 +607,20 @@ int specula_sh_image(specula_ctx *ctx, const specula_pupil_desc *pupil,
                      const float *phase_dev, int32_t n_batch, float *spots_dev,
                      void *stream);
 
+/* Imaged subapertures of a Shack-Hartmann plan (set-up call; synchronises):
+ * after this call specula_sh_image computes the spots of the valid
+ * subapertures sub_begin .. sub_end - 1 only (positions in the ascending
+ * valid list), compact: n_batch * (sub_end - sub_begin) * fft_n^2 floats.
+ * Their slopes are specula_slopes over the same count; the slope vectors of
+ * disjoint blocks that cover the list, each laid out all x then all y, make
+ * up the full vector.  This is the subaperture partition of one sensor
+ * across GPUs, the analogue of the paper's DistributedSH (Sect. 6; App. A,
+ * Tab. 4), joined by an all-gather of slopes.  [0, n_valid) restores the
+ * whole sensor.  Errors: SPECULA_EINVAL for a range outside [0, n_valid],
+ * SPECULA_ENOPLAN without a plan. */
+int specula_sh_set_range(specula_ctx *ctx, const specula_pupil_desc *pupil,
+                         const specula_sh_desc *sh, int32_t sub_begin, int32_t sub_end);
+
 /* Slopes (PyrSlopec / ShSlopec).  Output per batch element: all x slopes of
  * the listed subapertures, then all y slopes (2 * n_valid floats).
  *  PYR: img is the 2 n_sub x 2 n_sub detector; with Q1 (+x,+y) at

@@ -477,6 +477,12 @@ def specula_sh_image(ctx, pupil, sh, amp, phase, spots, n_valid, stream=None):
         "specula_sh_image")
 
 
+def specula_sh_set_range(ctx, pupil, sh, sub_begin, sub_end):
+    """Image only the valid subapertures [sub_begin, sub_end) (set-up call)."""
+    _abi.check(lib().specula_sh_set_range(ctx.handle, C.byref(pupil), C.byref(sh),
+                                          int(sub_begin), int(sub_end)), "specula_sh_set_range")
+
+
 def specula_slopes(ctx, slopec, img, ref, slopes, stream=None):
     import torch
     nb = slopes.numel() // (2 * slopec.n_valid)

@@ -663,6 +663,22 @@ extern "C" int specula_sh_plan(specula_ctx *ctx, const specula_pupil_desc *pupil
   return SPECULA_OK;
 }
 
+extern "C" int specula_sh_set_range(specula_ctx *ctx, const specula_pupil_desc *pupil,
+                                    const specula_sh_desc *sh, int32_t sub_begin,
+                                    int32_t sub_end) {
+  if (!ctx) return SPECULA_EINVAL;
+  int s = check_sh(pupil, sh);
+  if (s) return s;
+  ShPlan *p = sh_plan_find(ctx, pupil, sh);
+  if (!p) return SPECULA_ENOPLAN;
+  if (sub_begin < 0 || sub_end < sub_begin || sub_end > p->n_valid) return SPECULA_EINVAL;
+  SPECULA_CK(cudaSetDevice(ctx->device));
+  SPECULA_CK(cudaDeviceSynchronize());   // calls in flight use the old range
+  p->sub_lo = sub_begin;
+  p->sub_hi = (sub_begin == 0 && sub_end == p->n_valid) ? -1 : sub_end;
+  return SPECULA_OK;
+}
+
 extern "C" int specula_sh_image(specula_ctx *ctx, const specula_pupil_desc *pupil,
                                 const specula_sh_desc *sh, const float *amp_dev,
                                 const float *phase_dev, int32_t n_batch, float *spots_dev,

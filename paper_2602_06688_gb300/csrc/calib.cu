@@ -6,7 +6,9 @@
 //
 //  * basis: Zernike modes in Noll order without piston (j = 2 .. n_modes+1),
 //    unit RMS on the unit disk, sampled at pupil pixel centres, zero outside
-//    the stop; evaluated on the host in float64, stored as float32.
+//    the stop; radial polynomials by Kintner's recurrence, evaluated in
+//    float64 (on the device, one thread per pixel; the host variant runs the
+//    same routine), stored as float32.
 //  * IM[:, j] = (s(+a Z_j) - s(-a Z_j)) / (2 a): batches of 16 modes, 32 phase
 //    maps, run through the pyramid and slope kernels; columns formed in
 //    float64 from the float32 slopes.
@@ -24,7 +26,7 @@
 
 namespace specula {
 
-// ---------------------------------------------------------------- basis (host)
+// ---------------------------------------------------------------- basis
 
 static void noll_nm(int j, int *n_out, int *m_out) {
   int n = 0;
@@ -35,44 +37,120 @@ static void noll_nm(int j, int *n_out, int *m_out) {
   *m_out = (mabs == 0 || j % 2 == 0) ? mabs : -mabs;
 }
 
-static double factorial(int k) {
-  double f = 1.0;
-  for (int i = 2; i <= k; ++i) f *= (double)i;
-  return f;
+// Mode slots of every (n, |m|) up to the radial order of the last mode:
+// tab[n (n_max + 1) + |m|] = (q of the cosine or m = 0 mode, q of the sine
+// mode), q = j - 2, -1 where absent or beyond n_modes.
+static int modal_table(int n_modes, std::vector<int2> *tab) {
+  int n_max, m_last;
+  noll_nm(n_modes + 1, &n_max, &m_last);
+  tab->assign((size_t)(n_max + 1) * (n_max + 1), make_int2(-1, -1));
+  for (int j = 2; j <= n_modes + 1; ++j) {
+    int n, m;
+    noll_nm(j, &n, &m);
+    int2 &e = (*tab)[(size_t)n * (n_max + 1) + (m < 0 ? -m : m)];
+    if (m < 0)
+      e.y = j - 2;
+    else
+      e.x = j - 2;
+  }
+  return n_max;
 }
 
-static double zernike_value(int j, double rho, double theta) {
-  int n, m;
-  noll_nm(j, &n, &m);
-  const int ma = m < 0 ? -m : m;
-  double r = 0.0;
-  for (int s = 0; s <= (n - ma) / 2; ++s) {
-    const double c = ((s % 2) ? -1.0 : 1.0) * factorial(n - s) /
-                     (factorial(s) * factorial((n + ma) / 2 - s) * factorial((n - ma) / 2 - s));
-    r += c * pow(rho, n - 2 * s);
+// Every Zernike value of one pupil pixel (dx, dy from the centre, rho =
+// |(dx, dy)| / half <= 1): the radial polynomials R_n^m by Kintner's
+// recurrence in n for each m (stable at the high radial orders a 4000-mode
+// basis needs, where the alternating factorial sum cancels catastrophically
+// in float64),
+//   R_m^m = rho^m,  R_{m+2}^m = ((m + 2) rho^2 - (m + 1)) rho^m,
+//   K1 R_p^m = (K2 rho^2 + K3) R_{p-2}^m + K4 R_{p-4}^m,
+//   K1 = (p + m)(p - m)(p - 2) / 2,  K2 = 2 p (p - 1)(p - 2),
+//   K3 = -m^2 (p - 1) - p (p - 1)(p - 2),  K4 = -p (p + m - 2)(p - m - 2) / 2,
+// and cos / sin (m theta) by angle addition; emit(q, value) per mode slot.
+template <class Emit>
+__host__ __device__ inline void zernike_pixel(double dx, double dy, double half, int n_max,
+                                              const int2 *tab, Emit &emit) {
+  const double r = sqrt(dx * dx + dy * dy);
+  const double rho = r / half, rho2 = rho * rho;
+  const double c1 = r > 0.0 ? dx / r : 1.0, s1 = r > 0.0 ? dy / r : 0.0;
+  double cm = 1.0, sm = 0.0, rm = 1.0;   // cos, sin of m theta; rho^m
+  for (int m = 0; m <= n_max; ++m) {
+    double rp4 = 0.0, rp2 = 0.0;
+    for (int p = m; p <= n_max; p += 2) {
+      double R;
+      if (p == m) {
+        R = rm;
+      } else if (p == m + 2) {
+        R = ((m + 2) * rho2 - (m + 1)) * rm;
+      } else {
+        const double k1 = 0.5 * (double)(p + m) * (double)(p - m) * (double)(p - 2);
+        const double k2 = 2.0 * p * (double)(p - 1) * (double)(p - 2);
+        const double k3 = -(double)m * m * (double)(p - 1) - (double)p * (p - 1) * (double)(p - 2);
+        const double k4 = -0.5 * p * (double)(p + m - 2) * (double)(p - m - 2);
+        R = ((k2 * rho2 + k3) * rp2 + k4 * rp4) / k1;
+      }
+      rp4 = rp2;
+      rp2 = R;
+      const int2 e = tab[(size_t)p * (n_max + 1) + m];
+      if (m == 0) {
+        if (e.x >= 0) emit(e.x, sqrt((double)(p + 1)) * R);
+      } else {
+        const double a = sqrt(2.0 * (p + 1)) * R;
+        if (e.x >= 0) emit(e.x, a * cm);
+        if (e.y >= 0) emit(e.y, a * sm);
+      }
+    }
+    const double cn = cm * c1 - sm * s1, sn = sm * c1 + cm * s1;
+    cm = cn;
+    sm = sn;
+    rm *= rho;
   }
-  if (m == 0) return sqrt((double)(n + 1)) * r;
-  const double ang = m > 0 ? cos(ma * theta) : sin(ma * theta);
-  return sqrt(2.0 * (n + 1)) * r * ang;
+}
+
+struct EmitHost {
+  double *out;
+  size_t stride, p;
+  __host__ __device__ void operator()(int q, double v) { out[(size_t)q * stride + p] = v; }
+};
+struct EmitDev {
+  float *out;
+  size_t stride, p;
+  __device__ void operator()(int q, double v) { out[(size_t)q * stride + p] = (float)v; }
+};
+
+// The basis of a pupil on the device: one thread per pixel; zero outside
+// the stop (the integer rule of specula_pupil_mask).
+__global__ void k_modal_basis(int n, double thr, int n_modes, int n_max,
+                              const int2 *__restrict__ tab, float *__restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+  if (i >= n) return;
+  const size_t np2 = (size_t)n * n, p = (size_t)j * n + i;
+  const long long dx = 2LL * i - n + 1, dy = 2LL * j - n + 1;
+  const long long r4 = dx * dx + dy * dy;
+  if (!(r4 <= (long long)n * n && (double)r4 > thr)) {
+    for (int q = 0; q < n_modes; ++q) out[(size_t)q * np2 + p] = 0.f;
+    return;
+  }
+  EmitDev em{out, np2, p};
+  zernike_pixel(0.5 * (double)dx, 0.5 * (double)dy, 0.5 * n, n_max, tab, em);
 }
 
 int modal_basis_host(int n_pix, double obsc, int n_modes, double *out) {
   std::vector<uint8_t> mask((size_t)n_pix * n_pix);
   host_pupil_mask(n_pix, obsc, mask.data());
-  const double half = n_pix / 2.0, c0 = (n_pix - 1) / 2.0;
-  for (int q = 0; q < n_modes; ++q) {
-    const int j = q + 2;
-    for (int y = 0; y < n_pix; ++y)
-      for (int x = 0; x < n_pix; ++x) {
-        const size_t p = (size_t)y * n_pix + x;
-        double v = 0.0;
-        if (mask[p]) {
-          const double dx = x - c0, dy = y - c0;
-          v = zernike_value(j, sqrt(dx * dx + dy * dy) / half, atan2(dy, dx));
-        }
-        out[(size_t)q * n_pix * n_pix + p] = v;
+  std::vector<int2> tab;
+  const int n_max = modal_table(n_modes, &tab);
+  const size_t np2 = (size_t)n_pix * n_pix;
+  for (int y = 0; y < n_pix; ++y)
+    for (int x = 0; x < n_pix; ++x) {
+      const size_t p = (size_t)y * n_pix + x;
+      if (!mask[p]) {
+        for (int q = 0; q < n_modes; ++q) out[(size_t)q * np2 + p] = 0.0;
+        continue;
       }
-  }
+      EmitHost em{out, np2, p};
+      zernike_pixel(x - (n_pix - 1) / 2.0, y - (n_pix - 1) / 2.0, n_pix / 2.0, n_max, tab.data(),
+                    em);
+    }
   return SPECULA_OK;
 }
 
@@ -199,12 +277,16 @@ __global__ void k_jacobi_rows(double *__restrict__ G, int n, const int2 *__restr
 }
 
 // G <- G J and V <- V J: columns p, q of each pair
-__global__ void k_jacobi_cols(double *__restrict__ G, double *__restrict__ V, int n,
+// Column rotations: one grid row per matrix row, threads over the pairs, so
+// every matrix row is read and written once per round (the rows are 8 n
+// bytes; a thread per row and pair would scatter sector-sized accesses).
+__global__ void k_jacobi_cols(double *__restrict__ G, double *__restrict__ V, int n, int npairs,
                               const int2 *__restrict__ pq, const double2 *__restrict__ cs) {
-  const int i = blockIdx.y;
-  const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  const int row = blockIdx.y;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= npairs) return;
   const int2 e = pq[i];
-  if (row >= n || e.x == e.y) return;
+  if (e.x == e.y) return;
   const double2 r = cs[i];
   double *g = G + (size_t)row * n;
   double gp = g[e.x], gq = g[e.y];
@@ -289,6 +371,7 @@ int sym_eig_f64(specula_ctx *ctx, cudaStream_t st, double *G_, double *V_, int n
                  k_identity<<<(unsigned)(((size_t)n * n + 255) / 256), 256, 0, st>>>(V_, n));
   const int npairs = np / 2;
   const dim3 gr((n + 255) / 256, npairs);
+  const dim3 gc((npairs + 255) / 256, n);
   for (int sweep = 0; sweep < 40; ++sweep) {
     for (int r = 0; r < np - 1; ++r) {
       SPECULA_LAUNCH(ctx, SPECULA_K_CALIB, st,
@@ -298,8 +381,8 @@ int sym_eig_f64(specula_ctx *ctx, cudaStream_t st, double *G_, double *V_, int n
                      k_jacobi_rows<<<gr, 256, 0, st>>>(G_, n, PQ.as<int2>(),
                                                        CS.as<double2>()));
       SPECULA_LAUNCH(ctx, SPECULA_K_CALIB, st,
-                     k_jacobi_cols<<<gr, 256, 0, st>>>(G_, V_, n,
-                                                       PQ.as<int2>(), CS.as<double2>()));
+                     k_jacobi_cols<<<gc, 256, 0, st>>>(G_, V_, n, npairs, PQ.as<int2>(),
+                                                       CS.as<double2>()));
     }
     SPECULA_LAUNCH(ctx, SPECULA_K_CALIB, st,
                    k_offnorm<<<1, 256, 0, st>>>(G_, n, NRM.as<double>()));
@@ -328,16 +411,20 @@ extern "C" int specula_modal_basis(specula_ctx *ctx, const specula_pupil_desc *p
   if (!ctx || !basis_dev) return SPECULA_EINVAL;
   if (!pupil || n_modes < 1 || n_modes > 20000 || pupil->n_pix < 2 || pupil->n_pix > 8192)
     return SPECULA_EINVAL;
-  const size_t np2 = (size_t)pupil->n_pix * pupil->n_pix;
-  std::vector<double> h(np2 * n_modes);
-  int s = modal_basis_host(pupil->n_pix, pupil->obsc_frac, n_modes, h.data());
-  if (s) return s;
-  std::vector<float> f(h.size());
-  for (size_t i = 0; i < h.size(); ++i) f[i] = (float)h[i];
+  if (!(pupil->obsc_frac >= 0 && pupil->obsc_frac < 1)) return SPECULA_EINVAL;
+  std::vector<int2> tab;
+  const int n_max = modal_table(n_modes, &tab);
   SPECULA_CK(cudaSetDevice(ctx->device));
-  SPECULA_CK(cudaMemcpyAsync(basis_dev, f.data(), f.size() * sizeof(float),
-                             cudaMemcpyHostToDevice, (cudaStream_t)stream));
-  SPECULA_CK(cudaStreamSynchronize((cudaStream_t)stream));
+  cudaStream_t st = (cudaStream_t)stream;
+  DevBuf T;
+  int s;
+  if ((s = T.upload(tab.data(), tab.size() * sizeof(int2)))) return s;
+  const int n = pupil->n_pix;
+  const double e = pupil->obsc_frac * (double)n;
+  SPECULA_LAUNCH(ctx, SPECULA_K_CALIB, st,
+                 k_modal_basis<<<dim3((n + 127) / 128, n), 128, 0, st>>>(
+                     n, e * e, n_modes, n_max, T.as<int2>(), basis_dev));
+  SPECULA_CK(cudaStreamSynchronize(st));   // the table is freed on return
   return SPECULA_OK;
 }
 

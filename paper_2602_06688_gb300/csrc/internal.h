@@ -145,7 +145,9 @@ struct PwfsPlan {
 
 struct ShPlan {
   int n_pix, n_sub, sub_pix, fft_n;
+  double obsc = 0.0;   // the pupil's obscuration (the valid list depends on it)
   int n_valid;
+  int sub_lo = 0, sub_hi = -1;   // imaged valid subapertures [sub_lo, sub_hi) (-1: all)
   DevBuf valid;         // [n_valid] int32
   DevBuf pre;           // [fft_n] float2: centred-DFT input phase
   DevBuf tw;            // [fft_n] float2 twiddles

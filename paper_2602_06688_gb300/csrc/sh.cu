@@ -83,7 +83,7 @@ __global__ void __launch_bounds__(kShWarps * 32) k_sh_spots(
 ShPlan *sh_plan_find(specula_ctx *ctx, const specula_pupil_desc *pupil, const specula_sh_desc *sh) {
   for (auto &p : ctx->sh)
     if (p->n_pix == pupil->n_pix && p->n_sub == sh->n_sub && p->sub_pix == sh->sub_pix &&
-        p->fft_n == sh->fft_n)
+        p->fft_n == sh->fft_n && p->obsc == pupil->obsc_frac)
       return p.get();
   return nullptr;
 }
@@ -95,6 +95,7 @@ int sh_plan_build(specula_ctx *ctx, const specula_pupil_desc *pupil, const specu
   p->n_sub = sh->n_sub;
   p->sub_pix = sh->sub_pix;
   p->fft_n = sh->fft_n;
+  p->obsc = pupil->obsc_frac;
   std::vector<int32_t> idx((size_t)sh->n_sub * sh->n_sub);
   int32_t nv = 0;
   host_valid_subaps(pupil->n_pix, pupil->obsc_frac, sh->n_sub, idx.data(), &nv);
@@ -116,19 +117,22 @@ int sh_plan_build(specula_ctx *ctx, const specula_pupil_desc *pupil, const specu
 
 int sh_run(specula_ctx *ctx, ShPlan *p, const float *amp, const float *phase, int n_batch,
            float *spots, cudaStream_t st) {
-  const long long tasks = (long long)p->n_valid * n_batch;
+  // the imaged block of the valid list: spots are compact over it
+  const int lo = p->sub_lo, nv = (p->sub_hi < 0 ? p->n_valid : p->sub_hi) - lo;
+  const int32_t *valid = p->valid.as<int32_t>() + lo;
+  const long long tasks = (long long)nv * n_batch;
   if (tasks == 0) return SPECULA_OK;
   const unsigned grid = (unsigned)((tasks + kShWarps - 1) / kShWarps);
   if (p->fft_n == 24 && p->sub_pix == 12)
     SPECULA_LAUNCH(ctx, SPECULA_K_SH, st,
                    k_sh_spots<24, 12><<<grid, kShWarps * 32, 0, st>>>(
-                       amp, phase, p->valid.as<int32_t>(), p->pre.as<float2>(), p->n_pix,
-                       p->n_sub, p->n_valid, n_batch, spots));
+                       amp, phase, valid, p->pre.as<float2>(), p->n_pix, p->n_sub, nv, n_batch,
+                       spots));
   else if (p->fft_n == 16 && p->sub_pix == 8)
     SPECULA_LAUNCH(ctx, SPECULA_K_SH, st,
                    k_sh_spots<16, 8><<<grid, kShWarps * 32, 0, st>>>(
-                       amp, phase, p->valid.as<int32_t>(), p->pre.as<float2>(), p->n_pix,
-                       p->n_sub, p->n_valid, n_batch, spots));
+                       amp, phase, valid, p->pre.as<float2>(), p->n_pix, p->n_sub, nv, n_batch,
+                       spots));
   else
     return SPECULA_EUNSUPPORTED;
   return SPECULA_OK;

@@ -120,3 +120,36 @@ def test_calibrated_reconstructor_recovers_modes(env):
         assert abs(mv[j] - amp_j) < 0.05 * amp_j, (j, mv[j])
         others = np.delete(mv, j)
         assert np.max(np.abs(others)) < 0.05 * amp_j
+
+
+def test_modal_basis_to_high_radial_order(env):
+    """The device basis (Kintner's recurrence in float64, stored as float32)
+    against the oracle: all of the first 40 modes against the float64
+    definition, and 400 sampled (mode, pixel) values of a 4000-mode basis
+    (radial order 88) against the 60-digit evaluation of the same definition;
+    the host variant gives the same values."""
+    torch, sp, ctx = env
+    n, obsc, nm = 160, 0.28, 4000
+    pu = sp.PupilDesc(n, 8.0 / n, obsc)
+    basis = torch.empty(nm, n, n, device="cuda")
+    sp.specula_modal_basis(ctx, pu, nm, basis)
+    torch.cuda.synchronize()
+    low = modal.modal_basis(n, obsc, 40)
+    got = basis[:40].cpu().numpy().astype(np.float64)
+    assert np.all(np.abs(got - low) <= 2.0 ** -23 * np.abs(low) + 1e-12)
+    mask = geometry.pupil_mask(n, obsc).astype(bool)
+    rho, theta = modal.pupil_polar(n)
+    rng = np.random.default_rng(17)
+    inside = np.flatnonzero(mask.ravel())
+    qs = np.concatenate([rng.integers(0, nm, 300), np.arange(nm - 100, nm)])
+    ps = rng.choice(inside, qs.size)
+    vals = basis.reshape(nm, -1)[torch.tensor(qs, device="cuda"),
+                                 torch.tensor(ps, device="cuda")].cpu().numpy().astype(np.float64)
+    for q, p, v in zip(qs, ps, vals):
+        ref = modal.zernike_mp(int(q) + 2, float(rho.ravel()[p]), float(theta.ravel()[p]))
+        assert abs(v - ref) <= 2.0 ** -22 * abs(ref) + 1e-9, (q, p, v, ref)
+    out = basis.reshape(nm, -1)[:, ~mask.ravel()]
+    assert float(out.abs().max()) == 0.0
+    host = sp.specula_modal_basis_host(pu, 60).reshape(60, n, n)
+    assert np.all(np.abs(basis[:60].cpu().numpy() - host.astype(np.float32)) <=
+                  2.0 ** -23 * np.abs(host) + 1e-12)

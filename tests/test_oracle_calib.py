@@ -99,3 +99,35 @@ def test_reconstructor_closure(small_im):
     R, k = calib.pinv_truncated(IM, 1e-3)
     assert k == IM.shape[1]
     assert np.allclose(R @ IM, np.eye(k), atol=1e-10)
+
+
+def test_radial_mp_matches_float64_at_low_order_and_closed_forms():
+    """At low radial order the float64 sum is exact to rounding: the two agree;
+    R_n^m(1) = 1 for every order (the sum of the coefficients); R_n^n = rho^n."""
+    rho = np.linspace(0.0, 1.0, 17)
+    for n in range(0, 16):
+        for m in range(n % 2, n + 1, 2):
+            ref = modal.radial(n, m, rho)
+            got = np.array([modal.radial_mp(n, m, r) for r in rho])
+            # float64 rounding bound of the alternating sum: eps sum_s |c_s| (times the terms)
+            csum = sum(math.factorial(n - s) // (math.factorial(s) * math.factorial((n + m) // 2 - s)
+                                                 * math.factorial((n - m) // 2 - s))
+                       for s in range((n - m) // 2 + 1))
+            assert np.max(np.abs(got - ref)) <= 4 * (n + 1) * 2.0 ** -52 * csum, (n, m)
+    for n, m in [(40, 0), (61, 3), (88, 2), (89, 89), (90, 44)]:
+        assert abs(modal.radial_mp(n, m, 1.0) - 1.0) <= 1e-14
+    assert abs(modal.radial_mp(37, 37, 0.9) - 0.9 ** 37) <= 1e-15
+
+
+def test_radial_mp_orthogonality_at_high_order():
+    """int_0^1 R_n^m R_n'^m rho d rho = delta_nn' / (2 (n + 1)), by Gauss-Legendre
+    quadrature (exact for these degrees) on radial_mp, at the orders a
+    4000-mode basis reaches (radial order 88)."""
+    x, w = np.polynomial.legendre.leggauss(120)
+    rho, wt = 0.5 * (x + 1.0), 0.5 * w
+    for (n1, n2, m) in [(84, 84, 0), (84, 86, 0), (87, 87, 5), (85, 87, 5), (88, 88, 20)]:
+        f1 = np.array([modal.radial_mp(n1, m, r) for r in rho])
+        f2 = np.array([modal.radial_mp(n2, m, r) for r in rho])
+        v = float(np.sum(wt * f1 * f2 * rho))
+        ref = 1.0 / (2 * (n1 + 1)) if n1 == n2 else 0.0
+        assert abs(v - ref) <= 1e-10, (n1, n2, m, v)
