@@ -404,25 +404,26 @@ def closed_loop_leg(ctx, steps=400, settle=150):
     layers, 500 calibrated Zernike modes, integrator gain 0.4): one step
     (extraction, mirror shape, residual statistics, pyramid, slopes, MVM,
     integrator update) per replay of a CUDA graph, steps back to back as a
-    running loop.  Reports the step rate and the loop's residual RMS and
-    H-band (1650 nm) Strehl ratio averaged after `settle` steps, against the
-    open loop (gain 0) over the same atmosphere.  The residual RMS covers the
-    whole pupil, including edge pixels outside every valid subaperture: the
-    sensor never sees them, and the high-order modes' commands drift there
-    without bound (the Strehl ratio, dominated by the sensed interior, is the
-    figure of merit)."""
+    running loop.  Reports the step rate and, averaged after `settle` steps,
+    the residual RMS over the whole pupil (edge pixels outside every valid
+    subaperture included: the sensor never sees them) and the H-band
+    (1650 nm) Strehl ratio, with the leaky integrator (leak 0.01, the
+    default), without leak, and open (gain 0), over the same atmosphere; and
+    the largest command every 100 steps (bounded commands: no mode drifts)."""
     import torch
     import synth
     from paper_2602_06688_gb300.loop import ClosedLoop
     st = torch.cuda.Stream()
     out = {"workload": "pwfs8m", "gain": 0.4, "sci_wavelength_nm": 1650.0}
     cl = ClosedLoop(ctx, synth.workload("pwfs8m"), gain=0.4)
-    for label, gain in (("closed", 0.4), ("open", 0.0)):
-        cl.gain = gain
+    for label, gain, leak in (("closed", 0.4, 0.01), ("closed_no_leak", 0.4, 0.0),
+                              ("open", 0.0, 0.0)):
+        cl.gain, cl.leak = gain, leak
         cl.reset()
         cl.close()
         cl.capture(st)
         hist = torch.zeros(steps, 2, dtype=torch.float64, device="cuda")
+        cmax = torch.zeros(steps, device="cuda")
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         with torch.cuda.stream(st):
@@ -432,9 +433,18 @@ def closed_loop_leg(ctx, steps=400, settle=150):
                 hist[k].copy_(cl.stats)
             e1.record()
         torch.cuda.synchronize()
+        # the command trajectory, from a second (untimed) run of the same steps
+        cl.reset()
+        with torch.cuda.stream(st):
+            for k in range(steps):
+                cl.replay(k * cl.fr.dt, st)
+                cmax[k] = cl.cmd.abs().max()
+        torch.cuda.synchronize()
         h = hist.cpu().numpy()[settle:]
-        out[label] = {"strehl": float(h[:, 1].mean()),
-                      "resid_rms_rad_wfs_full_pupil": float(h[:, 0].mean())}
+        c = cmax.cpu().numpy()
+        out[label] = {"leak": leak, "strehl": float(h[:, 1].mean()),
+                      "resid_rms_rad_wfs_full_pupil": float(h[:, 0].mean()),
+                      "max_abs_cmd_every_100": [float(c[k]) for k in range(99, steps, 100)]}
         if label == "closed":
             ms = e0.elapsed_time(e1)
             out.update({"frames_per_s": steps / (ms / 1e3), "ms_per_step": ms / steps,
@@ -660,6 +670,38 @@ def gemm_leg(ctx, pk, n=8192, reps=10):
            "peak_tflops": peak, "frac": (tf / peak) if peak else None,
            "peak_source": "measured cuBLAS bf16 burst" if peak else None}
     del A, B, Cm
+    return out
+
+
+def elt_calibrated_leg(ctx, fr, variants):
+    """The ELT pyramid's 4000-mode reconstructor calibrated on the GPU (basis,
+    push-pull interaction matrix, float64 pseudo-inverse) and compared at
+    equal wavefront accuracy: the residual wavefront RMS left by the float32,
+    split-bf16 and bf16 MVMs and by the 13344-2048-2048-4000 network (trained
+    on synthetic modal phases) on held-out scaled atmospheric phases, next to
+    each form's frame rate from the headline frame's variants."""
+    import torch
+    from paper_2602_06688_gb300.calibrated import CalibratedRecon
+    t0 = time.perf_counter()
+    cr = CalibratedRecon(ctx, fr)
+    torch.cuda.synchronize()
+    t_cal = time.perf_counter() - t0
+    res = cr.compare()
+    out = {"calibration_s": t_cal, "n_modes": cr.n_modes, "rank": res.pop("rank"),
+           "residual_rms_rad": {k: res[k] for k in ("no_correction", "fp32", "bf16x2", "bf16",
+                                                     "learned")},
+           "test": {"n_test": res["n_test"], "phase_rms_rad": res["phase_rms_rad"]},
+           "learned_train": res["learned_train"],
+           "frames_per_s": {"fp32": variants.get("fp32", {}).get("frames_per_s"),
+                            "bf16x2": variants.get("bf16x2", {}).get("frames_per_s"),
+                            "bf16": variants.get("bf16", {}).get("frames_per_s"),
+                            "learned": variants.get("learned_mlp", {}).get("frames_per_s")}}
+    f = out["residual_rms_rad"]["fp32"]
+    out["within_1pct_of_fp32"] = {k: abs(v - f) <= 0.01 * f
+                                  for k, v in out["residual_rms_rad"].items()
+                                  if k not in ("no_correction", "fp32")}
+    del cr
+    torch.cuda.empty_cache()
     return out
 
 
@@ -1027,6 +1069,7 @@ def gpu_leg(args, ws, rank, local):
             line["learned"] = learned_leg(ctx)
             line["gemm_bf16"] = gemm_leg(ctx, pk)
         meas["tf32_gemm_tflops_8192"] = gemm_rate(ctx, 8192, 8192, 8192, True)
+        line["variants"]["elt_calibrated"] = elt_calibrated_leg(ctx, fr, line["variants"])
         line["variants"]["dftgemm_8m"] = dftgemm_leg(ctx)
         if not args.no_cpu_baseline:
             line["cpu_baseline"], line["cpu_baseline_single_core"] = cpu_baselines()

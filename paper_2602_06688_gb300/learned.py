@@ -29,7 +29,81 @@ from . import (MLP, PREC_FP32, SLOPES_PYR, pupil_desc, pwfs_desc, recon_desc, sl
                specula_valid_subaps_host)
 
 
-class LearnedPipeline:
+class MlpRegressor:
+    """A slopes -> modes perceptron fitted on the device: inputs and outputs
+    standardised per column, Kaiming-uniform start from a seed, Adam with a
+    cosine learning-rate decay on the tcgen05 GEMMs.  Needs self.ctx,
+    self.torch, self.n_slopes, self.n_modes and self.hidden."""
+
+    def _stats(self, A):
+        torch = self.torch
+        m = torch.empty(A.shape[1], device="cuda")
+        s = torch.empty(A.shape[1], device="cuda")
+        specula_col_stats(self.ctx, A, m, s)
+        torch.cuda.synchronize()
+        mh, sh = m.cpu().numpy().astype(np.float64), s.cpu().numpy().astype(np.float64)
+        sh = np.where(sh > 1e-12, sh, 1.0)
+        return mh, sh
+
+    def fit(self, X, T, epochs=10, batch=256, lr=1e-3, lr_final=1e-4, init_seed=5,
+            per_column_targets=True, per_column_inputs=True):
+        """per_column_targets False scales every target column by the same
+        factor (the largest column deviation), so the loss weighs each mode
+        by its variance, as a residual-wavefront metric does, instead of
+        equally; per_column_inputs False scales every input column by their
+        RMS deviation, so inputs whose spectrum differs from the training
+        set's are not magnified column by column."""
+        torch = self.torch
+        xm, xs = self._stats(X)
+        tm, ts = self._stats(T)
+        if not per_column_targets:
+            ts = np.full_like(ts, ts.max())
+        if not per_column_inputs:
+            xs = np.full_like(xs, np.sqrt(np.mean(xs ** 2)))
+        dev = lambda a: torch.tensor(np.asarray(a, dtype=np.float32), device="cuda")
+        self.x_shift, self.x_mul = dev(xm), dev(1.0 / xs)
+        self.t_shift, self.t_mul = dev(tm), dev(1.0 / ts)
+        self.y_shift, self.y_mul = dev(-tm / ts), dev(ts)     # undo: y = yn * s + m
+        Xn = torch.empty_like(X)
+        Tn = torch.empty_like(T)
+        specula_affine_cols(self.ctx, X, self.x_shift, self.x_mul, Xn)
+        specula_affine_cols(self.ctx, T, self.t_shift, self.t_mul, Tn)
+        sizes = (self.n_slopes, self.hidden[0], self.hidden[1], self.n_modes)
+        self.mlp = MLP(self.ctx, sizes, max(batch, 1024))
+        dims = list(sizes)
+        for l in range(3):
+            bound = 1.0 / math.sqrt(dims[l])
+            W = synth.uniform_draws(init_seed * 100 + 2 * l, (dims[l + 1], dims[l]), -bound, bound)
+            b = synth.uniform_draws(init_seed * 100 + 2 * l + 1, (dims[l + 1],), -bound, bound)
+            self.mlp.set_layer(l, W, b)
+        loss = torch.empty(1, device="cuda")
+        n = X.shape[0]
+        steps = max(1, epochs * (n // batch))
+        hist, k = [], 0
+        for ep in range(epochs):
+            for b0 in range(0, n - batch + 1, batch):
+                # cosine decay from lr to lr_final
+                lr_k = lr_final + 0.5 * (lr - lr_final) * (1 + math.cos(math.pi * k / steps))
+                self.mlp.forward(Xn[b0:b0 + batch])
+                self.mlp.backward(Tn[b0:b0 + batch], loss)
+                self.mlp.adam(lr_k)
+                k += 1
+            hist.append(float(loss.item()))
+        return hist
+
+    def predict(self, X, chunk=1024):
+        torch = self.torch
+        Xn = torch.empty_like(X)
+        specula_affine_cols(self.ctx, X, self.x_shift, self.x_mul, Xn)
+        Y = torch.empty(X.shape[0], self.n_modes, device="cuda")
+        for b0 in range(0, X.shape[0], chunk):
+            b1 = min(X.shape[0], b0 + chunk)
+            self.mlp.forward(Xn[b0:b1], Y[b0:b1])
+        specula_affine_cols(self.ctx, Y, self.y_shift, self.y_mul, Y)
+        return Y
+
+
+class LearnedPipeline(MlpRegressor):
     def __init__(self, ctx, wl, n_modes=None, hidden=None, screen_side=256, push_amp=0.1,
                  rcond=1e-3, seed=77):
         import torch
@@ -105,63 +179,6 @@ class LearnedPipeline:
             specula_recon(self.ctx, self.proj, ph[:g].reshape(g, n * n), T[g0:g0 + g])
         torch.cuda.synchronize()
         return X, T
-
-    # ------------------------------------------------------------------ model
-    def _stats(self, A):
-        torch = self.torch
-        m = torch.empty(A.shape[1], device="cuda")
-        s = torch.empty(A.shape[1], device="cuda")
-        specula_col_stats(self.ctx, A, m, s)
-        torch.cuda.synchronize()
-        mh, sh = m.cpu().numpy().astype(np.float64), s.cpu().numpy().astype(np.float64)
-        sh = np.where(sh > 1e-12, sh, 1.0)
-        return mh, sh
-
-    def fit(self, X, T, epochs=10, batch=256, lr=1e-3, lr_final=1e-4, init_seed=5):
-        torch = self.torch
-        xm, xs = self._stats(X)
-        tm, ts = self._stats(T)
-        dev = lambda a: torch.tensor(np.asarray(a, dtype=np.float32), device="cuda")
-        self.x_shift, self.x_mul = dev(xm), dev(1.0 / xs)
-        self.t_shift, self.t_mul = dev(tm), dev(1.0 / ts)
-        self.y_shift, self.y_mul = dev(-tm / ts), dev(ts)     # undo: y = yn * s + m
-        Xn = torch.empty_like(X)
-        Tn = torch.empty_like(T)
-        specula_affine_cols(self.ctx, X, self.x_shift, self.x_mul, Xn)
-        specula_affine_cols(self.ctx, T, self.t_shift, self.t_mul, Tn)
-        sizes = (self.n_slopes, self.hidden[0], self.hidden[1], self.n_modes)
-        self.mlp = MLP(self.ctx, sizes, max(batch, 1024))
-        dims = list(sizes)
-        for l in range(3):
-            bound = 1.0 / math.sqrt(dims[l])
-            W = synth.uniform_draws(init_seed * 100 + 2 * l, (dims[l + 1], dims[l]), -bound, bound)
-            b = synth.uniform_draws(init_seed * 100 + 2 * l + 1, (dims[l + 1],), -bound, bound)
-            self.mlp.set_layer(l, W, b)
-        loss = torch.empty(1, device="cuda")
-        n = X.shape[0]
-        steps = max(1, epochs * (n // batch))
-        hist, k = [], 0
-        for ep in range(epochs):
-            for b0 in range(0, n - batch + 1, batch):
-                # cosine decay from lr to lr_final
-                lr_k = lr_final + 0.5 * (lr - lr_final) * (1 + math.cos(math.pi * k / steps))
-                self.mlp.forward(Xn[b0:b0 + batch])
-                self.mlp.backward(Tn[b0:b0 + batch], loss)
-                self.mlp.adam(lr_k)
-                k += 1
-            hist.append(float(loss.item()))
-        return hist
-
-    def predict(self, X, chunk=1024):
-        torch = self.torch
-        Xn = torch.empty_like(X)
-        specula_affine_cols(self.ctx, X, self.x_shift, self.x_mul, Xn)
-        Y = torch.empty(X.shape[0], self.n_modes, device="cuda")
-        for b0 in range(0, X.shape[0], chunk):
-            b1 = min(X.shape[0], b0 + chunk)
-            self.mlp.forward(Xn[b0:b1], Y[b0:b1])
-        specula_affine_cols(self.ctx, Y, self.y_shift, self.y_mul, Y)
-        return Y
 
     def linear(self, X):
         Y = self.torch.empty(X.shape[0], self.n_modes, device="cuda")

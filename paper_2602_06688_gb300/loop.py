@@ -21,7 +21,7 @@ from .frame import PwfsFrame
 
 
 class ClosedLoop:
-    def __init__(self, ctx, wl, n_modes=None, gain=0.4, leak=0.0, push_amp=0.1, rcond=1e-3,
+    def __init__(self, ctx, wl, n_modes=None, gain=0.4, leak=0.01, push_amp=0.1, rcond=1e-3,
                  sci_wavelength_nm=1650.0, seed_offset=0, device="cuda"):
         import torch
         self.torch = torch

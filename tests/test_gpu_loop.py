@@ -5,7 +5,7 @@ system with a calibrated 60-mode reconstructor.
 Tolerances: the mirror shape is a float32 sum of n_modes products
 (|error| <= n_modes eps_32 sum_j |c_j B_j|); per step the pyramid image
 carries ~1e-5 of normalised-intensity error, so the slopes and modes carry
-~1e-5 relative error, which the integrator (gain g, no leak) keeps bounded
+~1e-5 relative error, which the integrator (gain g, leak) keeps bounded
 at the same order over the run; the checks use 2e-4 of the largest command
 and of the open-loop residual RMS, and 2e-4 absolute on the Strehl ratio."""
 import numpy as np
