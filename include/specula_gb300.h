@@ -641,7 +641,15 @@ int specula_slopes(specula_ctx *ctx, const specula_slopec_desc *slopec,
 
 /* Modal reconstruction (Modalrec): modes[b] = R slopes[b] for n_batch slope
  * vectors of n_slopes floats; modes_dev: n_batch * n_modes floats.
- * Accumulation in float32 for every precision. */
+ * Accumulation in float32 for every precision.  FP32 runs on the CUDA
+ * cores at every batch.  BF16 and BF16X2 (n_slopes a multiple of 8, 16-byte
+ * aligned operands) run on the CUDA cores below 32 vectors; from 32 on, the
+ * slopes are split into bfloat16 halves xh + xl in a context-owned
+ * workspace and one tensor-core GEMM forms xh Rh^T + xh Rl^T + xl Rh^T
+ * (BF16X2) or (xh + xl) Rh^T (BF16).  That workspace grows on the first
+ * batched call of a new size, which synchronises the stream; inside stream
+ * capture a call that would grow it returns SPECULA_EUNSUPPORTED (make one
+ * call of the largest batch before capturing). */
 int specula_recon(specula_ctx *ctx, const specula_recon_desc *rec,
                   const float *slopes_dev, int32_t n_batch, float *modes_dev,
                   void *stream);
@@ -735,10 +743,14 @@ int specula_mwfs_read(const specula_mwfs *mwfs, int32_t sensor, int32_t what, fl
 /* ---- tensor-core GEMM ---------------------------------------------------------
  * C[M][N] = A[M][K] . B[N][K]^T with A, B bfloat16 row-major (both K-major),
  * accumulated in float32 on the tcgen05 tensor cores; C float32 row-major.
- * The dense contractions of the learned reconstructor use it (the paper's
- * own reconstructor, Modalrec, is the MVM above).  M and N multiples
- * of 128, K a multiple of 64, A and B 16-byte aligned.  splits > 1 divides K
- * into slices computed by separate CTAs whose float32 partials go to work_dev
+ * The dense contractions of the learned reconstructor and the batched bf16
+ * reconstructor products use it (the paper's own reconstructor, Modalrec,
+ * is the MVM above).  Any M, N >= 1; K a multiple of 8 (rows of a multiple
+ * of 16 bytes); A and B 16-byte aligned (else SPECULA_EINVAL; a K that is
+ * not a multiple of 8 gives SPECULA_EUNSUPPORTED).  A persistent grid of at
+ * most one CTA per SM works through 128 x 256 output tiles (128 x 128 where
+ * N is a multiple of 128 but not of 256).  splits > 1 divides K into slices
+ * computed as separate work items whose float32 partials go to work_dev
  * (splits * M * N floats, caller-owned) and are summed in slice order.
  * Per-frame call: enqueues only. */
 int specula_gemm_bf16(specula_ctx *ctx, const void *A_dev, const void *B_dev, int32_t M,
@@ -748,7 +760,7 @@ int specula_gemm_bf16(specula_ctx *ctx, const void *A_dev, const void *B_dev, in
 /* The same product with tf32 operands (kind::tf32): A, B float32 row-major,
  * of which the tensor cores use the tf32 part (sign, 8-bit exponent, 10-bit
  * mantissa; the low 13 bits are ignored, so callers round to tf32 first
- * where rounding matters).  K a multiple of 32; otherwise as
+ * where rounding matters).  K a multiple of 4; otherwise as
  * specula_gemm_bf16.  It serves the tf32 split-precision DFT-as-GEMM
  * pyramid form and the measured tf32 rate.  Per-frame call: enqueues only. */
 int specula_gemm_tf32(specula_ctx *ctx, const float *A_dev, const float *B_dev, int32_t M,

@@ -174,6 +174,9 @@ struct specula_ctx {
   std::vector<cudaEvent_t> ev;      // 2 per record
   size_t ev_next = 0;
   std::vector<int> rec_kid;         // kernel id of record i (events 2i, 2i+1)
+  // batched bf16 reconstructor products: the slopes' bf16 halves and the
+  // split-K partials (grown on demand outside stream capture)
+  specula::DevBuf recon_ws;
 };
 
 namespace specula {
@@ -266,6 +269,11 @@ int gemm_tf32_tn(specula_ctx *ctx, const float *A, const float *B, int M, int N,
                  int splits, float *work, cudaStream_t st);
 int gemm_bf16_tn(specula_ctx *ctx, const void *A, const void *B, int M, int N, int K, float *C,
                  int splits, float *work, cudaStream_t st);
+// C = sum over t < n_terms (<= 3) of A_t B_t^T, one accumulation on the
+// tensor cores (split-precision products); every A_t is M x K, every B_t is
+// N x K, bf16, row-major
+int gemm_bf16_terms(specula_ctx *ctx, int n_terms, const void *const *A, const void *const *B,
+                    int M, int N, int K, float *C, int splits, float *work, cudaStream_t st);
 
 int slopes_pyr_run(specula_ctx *ctx, const int32_t *idx, int n_sub, int n_valid,
                    const float *det, const float *ref, int n_batch, float *out, cudaStream_t st);

@@ -21,12 +21,12 @@ import math
 import numpy as np
 
 import synth
-from . import (MLP, PREC_FP32, SLOPES_PYR, pupil_desc, pwfs_desc, recon_desc, slopec_desc,
-               specula_affine_cols, specula_calib_intmat, specula_col_stats,
+from . import (MLP, PREC_BF16X2, PREC_FP32, SLOPES_PYR, pupil_desc, pwfs_desc, recon_desc,
+               slopec_desc, specula_affine_cols, specula_calib_intmat, specula_col_stats,
                specula_modal_basis, specula_modal_basis_host, specula_pinv_fp64,
                specula_pupil_mask, specula_pwfs_image, specula_pwfs_plan, specula_random_phase,
-               specula_recon, specula_screen_generate_batch, specula_slopes,
-               specula_valid_subaps_host)
+               specula_recon, specula_recon_convert, specula_screen_generate_batch,
+               specula_slopes, specula_valid_subaps_host)
 
 
 class MlpRegressor:
@@ -153,6 +153,13 @@ class LearnedPipeline(MlpRegressor):
         self.rank = specula_pinv_fp64(ctx, im, rcond, R64, self.R)
         del im, R64
         self.rec = recon_desc(self.n_modes, self.n_slopes, PREC_FP32, self.R)
+        # the same R as split bf16 (hi + lo): batches of 32 and more run it on
+        # the tensor cores at float32-level error
+        self.R_hi = torch.empty(self.R.shape, dtype=torch.int16, device="cuda")
+        self.R_lo = torch.empty(self.R.shape, dtype=torch.int16, device="cuda")
+        specula_recon_convert(ctx, self.R, PREC_BF16X2, self.R_hi, self.R_lo)
+        self.rec_split = recon_desc(self.n_modes, self.n_slopes, PREC_BF16X2, self.R_hi,
+                                    self.R_lo)
         torch.cuda.synchronize()
 
     # ------------------------------------------------------------------ data
@@ -180,20 +187,23 @@ class LearnedPipeline(MlpRegressor):
         torch.cuda.synchronize()
         return X, T
 
-    def linear(self, X):
+    def linear(self, X, split_bf16=False):
+        """Modes of the calibrated linear reconstructor: R in float32 (CUDA
+        cores), or its split-bf16 copy (tensor cores from 32 frames on)."""
         Y = self.torch.empty(X.shape[0], self.n_modes, device="cuda")
-        specula_recon(self.ctx, self.rec, X, Y)
+        specula_recon(self.ctx, self.rec_split if split_bf16 else self.rec, X, Y)
         return Y
 
     def evaluate(self, X, T):
         """Modal residual RMS [rad] of both reconstructors and of the labels."""
         torch = self.torch
         ml = self.linear(X)
+        ms = self.linear(X, split_bf16=True)
         mm = self.predict(X)
         torch.cuda.synchronize()
         t = T.cpu().numpy().astype(np.float64)
         res = {}
-        for name, m in (("linear", ml), ("learned", mm)):
+        for name, m in (("linear", ml), ("linear_split_bf16", ms), ("learned", mm)):
             d = m.cpu().numpy().astype(np.float64) - t
             res[name] = float(np.sqrt(np.mean(np.sum(d * d, axis=1))))
         res["labels"] = float(np.sqrt(np.mean(np.sum(t * t, axis=1))))

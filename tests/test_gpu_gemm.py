@@ -1,6 +1,9 @@
 """GPU parity: the tcgen05 BF16 and TF32 GEMMs against a float64 product of
 the same bf16- or tf32-rounded operands.  FP32 accumulation:
-|C - ref| <= 2e-5 sum_k |a_ik b_jk|."""
+|C - ref| <= 2e-5 sum_k |a_ik b_jk|.  Shapes cover both output tile widths
+(128 and 256 columns), ragged M, N and K (zero-filled tiles, masked
+stores), split-K, and more work items than SMs (the persistent loop with
+its two alternating accumulators)."""
 import numpy as np
 import pytest
 
@@ -20,7 +23,9 @@ def env():
 
 @pytest.mark.parametrize("M,N,K,splits", [(128, 128, 64, 1), (128, 128, 256, 1),
                                           (256, 384, 640, 1), (256, 384, 640, 3),
-                                          (128, 256, 2560, 8), (384, 128, 1024, 5)])
+                                          (128, 256, 2560, 8), (384, 128, 1024, 5),
+                                          (64, 200, 520, 1), (130, 300, 136, 2),
+                                          (96, 4000, 1336, 3), (2560, 4096, 128, 1)])
 def test_gemm_bf16_parity(env, M, N, K, splits):
     torch, sp, ctx = env
     g = torch.Generator(device="cpu").manual_seed(M * 7 + N * 3 + K)
@@ -67,7 +72,7 @@ def tf32_round(x):
 
 @pytest.mark.parametrize("M,N,K,splits", [(128, 128, 32, 1), (128, 128, 256, 1),
                                           (256, 384, 640, 1), (256, 384, 640, 3),
-                                          (384, 128, 960, 5)])
+                                          (384, 128, 960, 5), (72, 200, 100, 1)])
 def test_gemm_tf32_parity(env, M, N, K, splits):
     torch, sp, ctx = env
     rng = np.random.default_rng(M * 5 + N + K)
@@ -102,6 +107,6 @@ def test_gemm_tf32_reads_only_the_tf32_bits(env):
     torch.cuda.synchronize()
     assert torch.equal(C1, C2)
     with pytest.raises(sp.SpeculaError) as e:
-        sp.specula_gemm_tf32(ctx, torch.zeros(128, 48, device="cuda"),
-                             torch.zeros(128, 48, device="cuda"), C1)
+        sp.specula_gemm_tf32(ctx, torch.zeros(128, 50, device="cuda"),
+                             torch.zeros(128, 50, device="cuda"), C1)
     assert e.value.status == sp.EUNSUPPORTED

@@ -58,3 +58,9 @@ def test_learned_beats_linear(pipe):
     res = p.evaluate(Xte, Tte)
     # the network must reduce the modal residual of the linear reconstructor
     assert res["learned"] < 0.8 * res["linear"], res
+    # the split-bf16 copy of R (tensor cores at this batch) leaves the same
+    # residual as float32 R on the CUDA cores
+    assert abs(res["linear_split_bf16"] - res["linear"]) <= 1e-4 * res["linear"], res
+    a = p.linear(Xte).double()
+    b = p.linear(Xte, split_bf16=True).double()
+    assert float((a - b).norm() / a.norm()) <= 1e-4

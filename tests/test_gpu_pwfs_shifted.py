@@ -81,8 +81,8 @@ def test_form_switch_and_errors(env):
     assert norm_intensity_error(d_s, d_t) > 100 * EPS
     pu = sp.PupilDesc(n_pix, 0.1, obsc)
     pw = sp.PwfsDesc(2, n_mod, n_sub, n_pix, r)
-    with pytest.raises(sp.SpeculaError) as e:
-        sp.specula_pwfs_set_form(ctx, pu, pw, 2)
+    with pytest.raises(sp.SpeculaError) as e:      # forms 0-3 exist
+        sp.specula_pwfs_set_form(ctx, pu, pw, 7)
     assert e.value.status == sp.EINVAL
     sp.specula_pwfs_set_form(ctx, pu, pw, sp.PWFS_FORM_SHIFTED)
     at = torch.tensor(amp.astype(np.float32), device="cuda")

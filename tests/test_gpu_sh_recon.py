@@ -54,7 +54,10 @@ def test_sh_spots_and_slopes(env, n_sub, sub_pix, fft_n, obsc, nb):
         assert np.max(np.abs(s_t[k].cpu().numpy() - s_same)) <= 2e-6 * fft_n
 
 
-@pytest.mark.parametrize("nm,ns,nb", [(200, 416, 1), (500, 2512, 3), (4000, 13344, 1), (37, 104, 5)])
+# batches of 32 and more run the bf16 forms on the tensor cores (one
+# multi-term GEMM over the slopes' bf16 halves)
+@pytest.mark.parametrize("nm,ns,nb", [(200, 416, 1), (500, 2512, 3), (4000, 13344, 1), (37, 104, 5),
+                                      (37, 104, 64), (500, 2512, 40), (4000, 13344, 128)])
 def test_recon_precisions(env, nm, ns, nb):
     torch, sp, ctx = env
     rng = np.random.default_rng(nm)
