@@ -34,15 +34,21 @@ def pupil_mask(n_pix: int, obsc_frac: float) -> np.ndarray:
 def valid_subaps(mask: np.ndarray, n_sub: int) -> np.ndarray:
     """Valid subapertures of an n_sub x n_sub grid over the pupil stop.
 
-    A subaperture of b x b pupil pixels (b = n_pix / n_sub) is valid iff at
-    least half of its pixels are inside the stop: 2 * count >= b^2.  Returns
-    int32 linear indices a * n_sub + b_col in row-major (row a first) order.
+    A subaperture covers b x b pupil pixels, b = n_pix / n_sub (whole or
+    fractional: the subaperture lattice tiles the pupil grid).  It is valid
+    iff at least half of its area is inside the stop.  With ov(i, A) the
+    overlap of pixel i with subaperture A in units of 1 / n_sub (an integer),
+    the condition is 2 sum ov(y, A) ov(x, C) mask[y, x] >= n_pix^2, exact in
+    integers; for a whole b it is 2 * count >= b^2.  Returns int32 linear
+    indices a * n_sub + b_col in row-major (row a first) order.
     """
     n = mask.shape[0]
-    assert n % n_sub == 0
-    b = n // n_sub
-    counts = mask.reshape(n_sub, b, n_sub, b).sum(axis=(1, 3)).astype(np.int64)
-    ok = 2 * counts >= b * b
+    i = np.arange(n)[None, :]
+    A = np.arange(n_sub)[:, None]
+    ov = np.maximum(np.minimum((i + 1) * n_sub, (A + 1) * n)
+                    - np.maximum(i * n_sub, A * n), 0).astype(np.int64)
+    counts = ov @ mask.astype(np.int64) @ ov.T
+    ok = 2 * counts >= n * n
     return np.flatnonzero(ok.ravel()).astype(np.int32)
 
 
@@ -88,21 +94,23 @@ def pyr_image_index(valid: np.ndarray, n_sub: int, pad: int, pup_dist: int,
     for any padding and image separation (the SOUL example's ``pup_diam`` /
     ``pup_dist`` / ``output_resolution``, App. B, Listing 2).
 
-    The padded grid (pad n_pix) is binned in b x b blocks, b = n_pix / n_sub,
-    to an n_det = pad n_sub detector.  The four images, n_sub detector pixels
-    wide, are centred d = pup_dist / (2 b) detector pixels from the detector
-    centre along +-x and +-y (face (+x, +y) to larger row and column);
-    subaperture (a, c) of image Q sits at row r0_Q + a, column c0_Q + c with
+    The padded grid (pad n_pix) is sampled onto an n_det = pad n_sub
+    detector whose pixel is b = n_pix / n_sub grid pixels (whole: b x b
+    binning; fractional: area-weighted rebinning).  The four images, n_sub
+    detector pixels wide, are centred d = pup_dist / (2 b) detector pixels
+    from the detector centre along +-x and +-y (face (+x, +y) to larger row
+    and column); subaperture (a, c) of image Q sits at row r0_Q + a, column
+    c0_Q + c with
         r0 = n_det / 2 + sy d - n_sub / 2,  c0 = n_det / 2 + sx d - n_sub / 2,
     (sx, sy) = (+,+) Q1, (-,+) Q2, (-,-) Q3, (+,-) Q4.  Needs integer image
-    corners (pup_dist a multiple of b and pup_dist / b - n_sub even); returns
-    a (4, n_valid) int64 array.  With pad 2 and pup_dist = n_pix it is
+    corners (2 d = pup_dist n_sub / n_pix an integer and 2 d - n_sub even),
+    so each image's subapertures fall on whole detector pixels; returns a
+    (4, n_valid) int64 array.  With pad 2 and pup_dist = n_pix it is
     ``pyr_quadrant_index``.
     """
-    b = n_pix // n_sub
-    assert n_pix % n_sub == 0 and pup_dist % b == 0
+    assert (pup_dist * n_sub) % n_pix == 0
     n_det = pad * n_sub
-    two_d = pup_dist // b
+    two_d = pup_dist * n_sub // n_pix
     assert (two_d - n_sub) % 2 == 0 and n_det % 2 == 0
     a = valid // n_sub
     c = valid % n_sub

@@ -17,7 +17,8 @@ modulation point m = 0..n_mod-1:
   5. IFFT:  O = centred inverse DFT (1/N^2);
   6. accumulate I += |O|^2 / n_mod.
 Then the N x N intensity is binned in b x b blocks, b = Np / n_sub, to the
-2 n_sub x 2 n_sub detector.
+pad n_sub detector (area-weighted rebinning where b is fractional, see
+``detector``).
 
 Readings (the paper prints no formula): centred grids (see ``dft``); amplitude
 1 per in-pupil pixel, so the detector sums to the number of pupil pixels;
@@ -106,11 +107,20 @@ def rebin_area(img: np.ndarray, n_out: int) -> np.ndarray:
     return W @ np.asarray(img, dtype=np.float64) @ W.T
 
 
+def detector(I: np.ndarray, n_det: int) -> np.ndarray:
+    """The N x N intensity sampled onto the n_det x n_det detector: b x b
+    binning for a whole ratio b = N / n_det, area-weighted rebinning
+    otherwise (a pixel of Np / n_sub grid pixels, e.g. 220 / 40 = 5.5 for
+    the SOUL example's output_resolution 120 on a 660 grid)."""
+    N = I.shape[0]
+    return bin_image(I, N // n_det) if N % n_det == 0 else rebin_area(I, n_det)
+
+
 def pwfs_image(amp, phase, pad, n_mod, mod_amp, n_sub, pup_dist):
-    """Detector image 2 n_sub x 2 n_sub (with pad = 2 and pup_dist = Np)."""
-    Np = amp.shape[0]
+    """Detector image pad n_sub x pad n_sub (2 n_sub x 2 n_sub with pad = 2
+    and pup_dist = Np, the quadrant layout)."""
     I = pwfs_intensity(amp, phase, pad, n_mod, mod_amp, pup_dist)
-    return bin_image(I, Np // n_sub)
+    return detector(I, pad * n_sub)
 
 
 def shift_bins(n_mod: int, mod_amp: float, pad: int):

@@ -54,3 +54,46 @@ def test_tilt_sign_on_separated_images():
     s = slopes.pyr_slopes_maps(pyramid.pwfs_image(amp, tilt, pad, 12, 3.0, nsub, pd), maps, ref)
     nv = len(valid)
     assert s[:nv].mean() > 0.01 and abs(s[nv:].mean()) < 1e-10
+
+
+def _valid_supersampled(mask, n_sub):
+    """Brute force: split every pupil pixel into n_sub x n_sub sub-pixels of
+    side 1 / n_sub; sub-pixel k (in those units) belongs to subaperture
+    k // n_pix along each axis.  Valid iff at least half the subaperture's
+    sub-pixels (n_pix^2 of them) lie in the stop."""
+    n = mask.shape[0]
+    fine = np.kron(mask.astype(np.int64), np.ones((n_sub, n_sub), dtype=np.int64))
+    counts = fine.reshape(n_sub, n, n_sub, n).sum(axis=(1, 3))
+    return np.flatnonzero((2 * counts >= n * n).ravel()).astype(np.int32)
+
+
+def test_valid_subaps_fractional_against_supersampling():
+    for n, nsub, obsc in ((22, 4, 0.2), (33, 6, 0.3), (220, 40, 0.12), (32, 8, 0.2), (25, 10, 0.0)):
+        m = geometry.pupil_mask(n, obsc)
+        assert np.array_equal(geometry.valid_subaps(m, nsub), _valid_supersampled(m, nsub)), (n, nsub)
+
+
+def test_fractional_detector_soul_scaled():
+    """The SOUL example's ratios at a tenth of the size: a 22 px pupil of 4
+    subapertures (5.5 px each, as 220 / 40), pad 3 (66 grid), images
+    6 detector pixels apart on a 12 px detector (48 / 40 x 5), so each
+    detector pixel integrates 5.5 x 5.5 grid pixels.  The flux is kept, a
+    flat wavefront gives mirror-symmetric images that hold most of the light
+    on their mapped pixels and zero mean slopes."""
+    n, nsub, pad, pd = 22, 4, 3, 33
+    amp = geometry.pupil_mask(n, 0.0).astype(np.float64)
+    valid = geometry.valid_subaps(amp.astype(np.uint8), nsub)
+    maps = geometry.pyr_image_index(valid, nsub, pad, pd, n)
+    # corners: 12 / 2 +- 3 - 2 = 1 and 7
+    assert set(np.unique(maps // 12)) <= set(range(1, 5)) | set(range(7, 11))
+    det = pyramid.pwfs_image(amp, np.zeros((n, n)), pad, 8, 2.0, nsub, pd)
+    assert det.shape == (12, 12)
+    assert abs(det.sum() - amp.sum()) < 1e-12 * amp.sum()
+    assert np.allclose(det, det[:, ::-1], atol=1e-12) and np.allclose(det, det[::-1], atol=1e-12)
+    assert det.ravel()[maps].sum() > 0.7 * det.sum()
+    s = slopes.pyr_slopes_maps(det, maps)
+    nv = len(valid)
+    assert abs(s[:nv].sum()) < 1e-10 and abs(s[nv:].sum()) < 1e-10
+    # the detector is the area-weighted rebinning of the grid intensity
+    I = pyramid.pwfs_intensity(amp, np.zeros((n, n)), pad, 8, 2.0, pd)
+    assert np.allclose(det, pyramid.rebin_area(I, 12), rtol=0, atol=1e-12)
