@@ -628,6 +628,25 @@ def systems_leg(ctx, steps=50):
                                "%d modes, FP32" % fs.n_modes,
                      "frames_per_s": steps / (sum(mss) / 1e3), "ms_per_step": sum(mss) / steps}
     gs.close()
+    del fs
+    # the same example as the paper states it: 220 px pupil oversampled 3x
+    # (660^2 FFT, Tab. 2's 24 x 660 x 660), detector pixels of 5.5 x 5.5 grid
+    # pixels (area-weighted rebinning in the column pass), 500 modes
+    ws = synth.workload("soul220")
+    fs = PwfsFrame(ctx, ws)
+    gs = fs.capture(st)
+    time_graph(gs, lambda k: fs.t_dev.fill_(ws.dt_s * k), 5)
+    mss = time_graph(gs, lambda k: fs.t_dev.fill_(ws.dt_s * k), steps)
+    out["soul220"] = {"config": "8.2 m, 220 px pupil padded 3x (660^2 FFT = 30 x 22), 24 mod "
+                                "points, 40x40 subaps of 5.5 px, images 48 px apart on a 120 px "
+                                "detector (area-weighted rebinning), %d modes, FP32" % fs.n_modes,
+                      "tiles": {"chunk": fs.tiles[0], "ka": fs.tiles[1], "passes": fs.tiles[2]}
+                      if fs.tiles else None,
+                      "frames_per_s": steps / (sum(mss) / 1e3), "ms_per_step": sum(mss) / steps,
+                      "paper_context": "SOUL full loop 162.2 Hz (6.2 ms per step) on one GPU, "
+                                       "Sect. 6 Tab. 1"}
+    gs.close()
+    del fs
     out["infinite8m"] = infinite_leg(ctx, st, flush, steps)
     wl = synth.workload("mwfs39m")
     S = System(ctx, wl)
@@ -662,7 +681,7 @@ def gemm_leg(ctx, pk, n=8192, reps=10):
     B = torch.randn(n, n, device="cuda", generator=g).to(torch.bfloat16)
     Cm = torch.empty(n, n, device="cuda")
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    best = float("inf")
+    best, tot = float("inf"), 0.0
     for _ in range(3):
         sp.specula_gemm_bf16(ctx, A, B, Cm)
     for _ in range(reps):
@@ -671,10 +690,13 @@ def gemm_leg(ctx, pk, n=8192, reps=10):
         e1.record()
         torch.cuda.synchronize()
         best = min(best, e0.elapsed_time(e1))
+        tot += e0.elapsed_time(e1)
     tf = 2.0 * n ** 3 / (best / 1e3) / 1e12
     peak = pk.get("bf16_tflops")
-    out = {"kernel": "k_gemm_bf16_tn (TMA + tcgen05, 128x128 tiles, TMEM accumulator)",
-           "shape": [n, n, n], "best_ms": best, "achieved_tflops": tf,
+    out = {"kernel": "k_gemm_tn<bf16, 256> (persistent, one CTA per SM; TMA ring of 4 x 48 KB; "
+                     "tcgen05 128x256x16 MMAs; two TMEM accumulators, epilogue overlapped)",
+           "shape": [n, n, n], "best_ms": best, "mean_ms": tot / reps, "achieved_tflops": tf,
+           "achieved_tflops_mean": 2.0 * n ** 3 / (tot / reps / 1e3) / 1e12,
            "peak_tflops": peak, "frac": (tf / peak) if peak else None,
            "peak_source": "measured cuBLAS bf16 burst" if peak else None}
     del A, B, Cm
@@ -711,6 +733,44 @@ def elt_calibrated_leg(ctx, fr, variants):
     del cr
     torch.cuda.empty_cache()
     return out
+
+
+def recon_batched_leg(ctx, nb=2048, n_modes=4000, n_slopes=13344):
+    """The ELT-size reconstructor applied to a batch of slope vectors: float32
+    R on the CUDA cores against the split-bf16 and bf16 copies on the tensor
+    cores (one multi-term GEMM), each with its relative error against a
+    float64 product."""
+    import torch
+    import paper_2602_06688_gb300 as sp
+    g = torch.Generator(device="cuda").manual_seed(17)
+    R = torch.randn(n_modes, n_slopes, device="cuda", generator=g) / n_slopes ** 0.5
+    X = torch.randn(nb, n_slopes, device="cuda", generator=g)
+    hi = torch.empty(n_modes, n_slopes, dtype=torch.int16, device="cuda")
+    lo = torch.empty_like(hi)
+    sp.specula_recon_convert(ctx, R, sp.PREC_BF16X2, hi, lo)
+    recs = {"fp32_cuda_cores": sp.recon_desc(n_modes, n_slopes, sp.PREC_FP32, R),
+            "bf16x2_tensor": sp.recon_desc(n_modes, n_slopes, sp.PREC_BF16X2, hi, lo),
+            "bf16_tensor": sp.recon_desc(n_modes, n_slopes, sp.PREC_BF16, hi)}
+    ref = X.double() @ R.double().t()
+    out = torch.empty(nb, n_modes, device="cuda")
+    res = {"shape": [n_modes, n_slopes], "batch": nb}
+    for name, rec in recs.items():
+        sp.specula_recon(ctx, rec, X, out)
+        torch.cuda.synchronize()
+        err = float((out.double() - ref).norm() / ref.norm())
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 2 if name.startswith("fp32") else 10
+        e0.record()
+        for _ in range(reps):
+            sp.specula_recon(ctx, rec, X, out)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        res[name] = {"frames_per_s": nb / ms * 1e3, "ms_per_batch": ms,
+                     "tflops": 2.0 * n_modes * n_slopes * nb / ms / 1e9, "rel_err_vs_fp64": err}
+    del R, X, hi, lo, ref, out
+    torch.cuda.empty_cache()
+    return res
 
 
 def gemm_rate(ctx, M, N, K, tf32, reps=10):
@@ -1079,6 +1139,7 @@ def gpu_leg(args, ws, rank, local):
         meas["tf32_gemm_tflops_8192"] = gemm_rate(ctx, 8192, 8192, 8192, True)
         line["variants"]["elt_calibrated"] = elt_calibrated_leg(ctx, fr, line["variants"])
         line["variants"]["dftgemm_8m"] = dftgemm_leg(ctx)
+        line["variants"]["recon_batched_elt"] = recon_batched_leg(ctx)
         if not args.no_cpu_baseline:
             line["cpu_baseline"], line["cpu_baseline_single_core"] = cpu_baselines()
         print(json.dumps(line), flush=True)

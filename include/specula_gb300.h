@@ -85,14 +85,20 @@ typedef struct {
 } specula_layer_desc;
 
 /* Modulated pyramid (ModulatedPyramid, Listing 2): FFT side N = pad * n_pix;
- * n_mod modulation points on a circle of mod_amp lambda/D; images binned to
- * n_sub x n_sub per pupil image (a pad n_sub detector); pup_dist_px =
- * separation of the pupil images' centres in grid pixels.  Supported: pad
- * 2-4 with N one of 64, 128, 240, 320, 960, and pup_dist_px + n_pix <= N
- * (the images inside the grid; SPECULA_EUNSUPPORTED else).  With pad 2 and
- * pup_dist_px = n_pix the four images tile the grid (quadrant slopes);
- * otherwise read the slopes with SPECULA_SLOPES_PYR_MAPS.  The three-pass
- * form and the shifted-mask form need pad 2. */
+ * n_mod modulation points on a circle of mod_amp lambda/D; a pad n_sub
+ * detector (output_resolution) with n_sub pixels across each pupil image;
+ * pup_dist_px = separation of the pupil images' centres in grid pixels.
+ * A detector pixel is b = n_pix / n_sub grid pixels: a whole b is b x b
+ * binning; a fractional b (the SOUL example: 220 / 40 = 5.5) is
+ * area-weighted rebinning, each detector pixel collecting the overlapped
+ * area of every grid pixel, the intensity constant over a grid pixel.
+ * Supported: pad 2-4 with N one of 64, 128, 240, 320, 660 (pad 3 or 4),
+ * 960, pup_dist_px + n_pix <= N (the images inside the grid), and column
+ * tiles of whole detector pixels within 352 threads (SPECULA_EUNSUPPORTED
+ * else).  With pad 2 and pup_dist_px = n_pix the four images tile the grid
+ * (quadrant slopes); otherwise read the slopes with SPECULA_SLOPES_PYR_MAPS.
+ * The three-pass, shifted-mask, paired and DFT-as-GEMM forms need pad 2 and
+ * a whole b. */
 typedef struct {
   int32_t pad, n_mod, n_sub, pup_dist_px;
   double mod_amp;
@@ -251,25 +257,30 @@ int specula_pupil_mask_host(const specula_pupil_desc *pupil, uint8_t *mask_host)
 
 /* Valid subapertures (PupData / SubapData; PyrPupdataCalibrator /
  * ShSubapCalibrator, App. A, Tab. 4; geometric reading of the flux threshold):
- * a b x b block (b = n_pix / n_sub) is valid iff 2 * (pixels inside) >= b^2.
- * Writes the ascending linear indices a * n_sub + b to idx_host (capacity
- * n_sub^2) and their count to *n_valid. */
+ * a subaperture of b x b pupil pixels (b = n_pix / n_sub, whole or
+ * fractional; 1 <= n_sub <= n_pix) is valid iff at least half of its area is
+ * inside the stop, evaluated exactly with each pixel's overlap of the
+ * subaperture in units of 1 / n_sub (for a whole b: 2 * (pixels inside) >=
+ * b^2).  Writes the ascending linear indices a * n_sub + b to idx_host
+ * (capacity n_sub^2) and their count to *n_valid. */
 int specula_valid_subaps_host(const specula_pupil_desc *pupil, int32_t n_sub,
                               int32_t *idx_host, int32_t *n_valid);
 
 /* Detector indices of the four pupil images of each valid subaperture for
  * any padding and image separation (PyrPupdataCalibrator; the SOUL example's
  * pup_diam / pup_dist / output_resolution, App. B, Listing 2).  The padded
- * grid (pad n_pix) binned in b x b blocks (b = n_pix / n_sub) is an n_det =
- * pad n_sub detector; image Q, n_sub pixels wide, is centred
+ * grid (pad n_pix) sampled in detector pixels of b x b grid pixels (b =
+ * n_pix / n_sub) is an n_det = pad n_sub detector; image Q, n_sub pixels wide, is centred
  * d = pup_dist_px / (2 b) pixels from the detector centre along (sx, sy) =
  * (+,+) Q1, (-,+) Q2, (-,-) Q3, (+,-) Q4 (face (+x, +y) to larger row and
  * column); subaperture (a, c) of image Q is at row n_det/2 + sy d - n_sub/2
  * + a, column n_det/2 + sx d - n_sub/2 + c.  Writes 4 n_valid indices (Q1
  * block first) to idx_host (capacity 4 n_sub^2) and *n_valid.
  * SPECULA_EUNSUPPORTED unless the image corners are whole detector pixels
- * (pup_dist_px a multiple of b, pup_dist_px / b - n_sub and n_det even) and
- * the images lie on the detector.  With pad 2 and pup_dist_px = n_pix the
+ * (pup_dist_px / b = pup_dist_px n_sub / n_pix a whole number, it minus
+ * n_sub and n_det even) and the images lie on the detector; b may be
+ * fractional (the SOUL example: 220 px pupil, 40 subapertures, 5.5 grid
+ * pixels per detector pixel, pup_dist_px 264 -> images 48 pixels apart).  With pad 2 and pup_dist_px = n_pix the
  * blocks are the quadrant layout of SPECULA_SLOPES_PYR. */
 int specula_pyr_image_index_host(const specula_pupil_desc *pupil, int32_t pad,
                                  int32_t pup_dist_px, int32_t n_sub, int32_t *idx_host,
@@ -471,7 +482,7 @@ int specula_atmo_extract_noalloc(int32_t n_layers, const specula_layer_desc *lay
 /* Build (or reuse) the tables and workspace of a pyramid geometry: modulation
  * tilt tables, pyramid-mask tables and FFT twiddles, computed in float64 on
  * the host and rounded once to float32.  May allocate.  Supported FFT sides
- * N = pad * n_pix: 64, 128, 240, 320, 960. */
+ * N = pad * n_pix: 64, 128, 240, 320, 660, 960. */
 int specula_pwfs_plan(specula_ctx *ctx, const specula_pupil_desc *pupil,
                       const specula_pwfs_desc *pwfs);
 

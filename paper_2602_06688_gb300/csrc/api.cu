@@ -12,6 +12,8 @@
 
 #include <vector>
 
+#include <algorithm>
+
 #include "internal.h"
 
 using namespace specula;
@@ -314,18 +316,33 @@ int host_pupil_mask(int n, double obsc, uint8_t *mask) {
   return SPECULA_OK;
 }
 
+// A subaperture (n / n_sub pupil pixels a side, whole or fractional) is valid
+// iff at least half of its area is in the stop: with ov(i, A) the overlap of
+// pixel i with subaperture A in units of 1 / n_sub,
+// 2 sum ov(y, A) ov(x, C) mask[y][x] >= n^2, exact in integers (for a whole
+// side b it is 2 count >= b^2).
 int host_valid_subaps(int n, double obsc, int n_sub, int32_t *idx, int32_t *n_valid) {
-  const int b = n / n_sub;
   std::vector<uint8_t> m((size_t)n * n);
   host_pupil_mask(n, obsc, m.data());
+  auto ov = [&](int i, int A) -> int64_t {
+    const int64_t lo = std::max<int64_t>((int64_t)i * n_sub, (int64_t)A * n);
+    const int64_t hi = std::min<int64_t>((int64_t)(i + 1) * n_sub, (int64_t)(A + 1) * n);
+    return hi > lo ? hi - lo : 0;
+  };
   int cnt = 0;
-  for (int a = 0; a < n_sub; ++a)
+  for (int a = 0; a < n_sub; ++a) {
+    const int y0 = (int)((int64_t)a * n / n_sub), y1 = (int)(((int64_t)(a + 1) * n + n_sub - 1) / n_sub);
     for (int c = 0; c < n_sub; ++c) {
-      int in = 0;
-      for (int y = 0; y < b; ++y)
-        for (int x = 0; x < b; ++x) in += m[(size_t)(a * b + y) * n + (c * b + x)];
-      if (2 * in >= b * b) idx[cnt++] = a * n_sub + c;
+      const int x0 = (int)((int64_t)c * n / n_sub), x1 = (int)(((int64_t)(c + 1) * n + n_sub - 1) / n_sub);
+      int64_t in = 0;
+      for (int y = y0; y < y1; ++y) {
+        const int64_t wy = ov(y, a);
+        for (int x = x0; x < x1; ++x)
+          if (m[(size_t)y * n + x]) in += wy * ov(x, c);
+      }
+      if (2 * in >= (int64_t)n * n) idx[cnt++] = a * n_sub + c;
     }
+  }
   *n_valid = cnt;
   return SPECULA_OK;
 }
@@ -351,7 +368,7 @@ extern "C" int specula_valid_subaps_host(const specula_pupil_desc *pupil, int32_
                                          int32_t *idx_host, int32_t *n_valid) {
   int s = check_pupil(pupil);
   if (s) return s;
-  if (!idx_host || !n_valid || n_sub < 1 || pupil->n_pix % n_sub) return SPECULA_EINVAL;
+  if (!idx_host || !n_valid || n_sub < 1 || n_sub > pupil->n_pix) return SPECULA_EINVAL;
   return host_valid_subaps(pupil->n_pix, pupil->obsc_frac, n_sub, idx_host, n_valid);
 }
 
@@ -360,10 +377,12 @@ extern "C" int specula_pyr_image_index_host(const specula_pupil_desc *pupil, int
                                             int32_t *idx_host, int32_t *n_valid) {
   int s = check_pupil(pupil);
   if (s) return s;
-  if (!idx_host || !n_valid || n_sub < 1 || pad < 1 || pupil->n_pix % n_sub) return SPECULA_EINVAL;
-  const int b = pupil->n_pix / n_sub, n_det = pad * n_sub;
-  if (pup_dist_px < 0 || pup_dist_px % b) return SPECULA_EUNSUPPORTED;
-  const int two_d = pup_dist_px / b;
+  if (!idx_host || !n_valid || n_sub < 1 || n_sub > pupil->n_pix || pad < 1) return SPECULA_EINVAL;
+  // image centres 2 d = pup_dist / b detector pixels apart, b = n_pix / n_sub
+  // grid pixels per detector pixel (whole or fractional)
+  const int n_det = pad * n_sub;
+  if (pup_dist_px < 0 || ((int64_t)pup_dist_px * n_sub) % pupil->n_pix) return SPECULA_EUNSUPPORTED;
+  const int two_d = (int)((int64_t)pup_dist_px * n_sub / pupil->n_pix);
   if ((two_d - n_sub) % 2 || n_det % 2) return SPECULA_EUNSUPPORTED;
   std::vector<int32_t> valid((size_t)n_sub * n_sub);
   int32_t nv = 0;
@@ -477,7 +496,7 @@ static int check_pwfs(const specula_pupil_desc *pupil, const specula_pwfs_desc *
   if (s) return s;
   if (!p) return SPECULA_EINVAL;
   if (p->pad < 1 || p->n_mod < 1 || p->n_mod > 4096 || p->n_sub < 1) return SPECULA_EINVAL;
-  if (pupil->n_pix % p->n_sub) return SPECULA_EINVAL;
+  if (p->n_sub > pupil->n_pix) return SPECULA_EINVAL;
   if (!(p->mod_amp >= 0.0) || !isfinite(p->mod_amp)) return SPECULA_EINVAL;
   // padding 2-4; the four pupil images (n_pix wide, centres pup_dist apart)
   // inside the padded grid

@@ -101,6 +101,9 @@ struct PwfsPlan {
   int blockR, blockK;   // two-pass blocks (K: TC columns x G lanes)
   size_t smemR, smemK;
   int csK = 0;                      // column stride of the column-pass tile (complex)
+  // a detector pixel is fp / fq grid pixels (N / (pad n_sub) in lowest
+  // terms; fq = 1: fp x fp binning, else area-weighted rebinning)
+  int fp = 1, fq = 1;
   DevBuf gx, gy;        // [n_mod][n_pix] float2: tilt x pre-phase (x and y parts)
   DevBuf mask;          // [N] float2: pyramid mask factor per axis, x (1/N)
   DevBuf twA, twB;      // [N] float2: inter-step twiddles (cos, sin)

@@ -437,11 +437,11 @@ template <int N1, int N2> struct ColFiltCfg {
 // per SM, the occupancy that 80 registers per thread gave them already:
 // 96 registers per thread, so the twiddle loads can be issued earlier.
 template <int N1, int N2, int MAXT = 256, bool GEN = false>
-__global__ void __launch_bounds__(MAXT, MAXT <= 160 ? 4 : 3) k_colfilt_bin(
+__global__ void __launch_bounds__(MAXT, MAXT <= 160 ? 4 : (MAXT <= 256 ? 3 : 2)) k_colfilt_bin(
     const float2 *__restrict__ rows_in, const float2 *__restrict__ gy,
     const float2 *__restrict__ twA, const float2 *__restrict__ twB,
-    const float2 *__restrict__ mask, float *__restrict__ part, int n_pix, int bsz, float scale,
-    int n_mod, int nc, int nbw, int slot0, int CS, int off, int s0) {
+    const float2 *__restrict__ mask, float *__restrict__ part, int n_pix, int fp, int fq,
+    float scale, int n_mod, int nc, int nbw, int slot0, int CS, int off, int s0) {
   using S = Split<N1, N2>;
   constexpr int N = S::N, G = S::G, S1 = S::S1, S2 = S::S2;
   constexpr int Q0 = N2 / 4, QH = N2 / 2;
@@ -542,9 +542,33 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 160 ? 4 : 3) k_colfilt_bin(
       colI[N1 * k1 + lane] = (r3[k1].x * r3[k1].x + r3[k1].y * r3[k1].y) * scale;
   }
   __syncthreads();
-  const int nd = N / bsz, nbx = TC / bsz;
-  float *dst = part + ((size_t)(b % nbw) * n_mod + m) * nd * nd;
+  float *dst = part + ((size_t)(b % nbw) * n_mod + m) * (N * fq / fp) * (N * fq / fp);
   const float *s_I = reinterpret_cast<const float *>(smem_k);
+  if (fq != 1) {
+    // fractional detector pixels of fp / fq grid pixels (area-weighted
+    // rebinning): output pixel o covers [o fp, (o + 1) fp) and grid pixel i
+    // covers [i fq, (i + 1) fq) in units of 1 / fq; the weight is their
+    // overlap, an integer, and the sum is divided by fq^2 once.  The tile's
+    // TC = k fp columns hold exactly its k fq output columns.
+    const int nd = N * fq / fp, nxo = TC / fp * fq, xo0 = col0 / fp * fq;
+    const float inv = 1.0f / (float)(fq * fq);
+    for (int q = threadIdx.x; q < nd * nxo; q += blockDim.x) {
+      const int yo = q / nxo, X = xo0 + (q - yo * nxo);
+      const int px0 = X * fp / fq, px1 = ((X + 1) * fp + fq - 1) / fq;
+      const int py0 = yo * fp / fq, py1 = ((yo + 1) * fp + fq - 1) / fq;
+      float v = 0.f;
+      for (int py = py0; py < py1; ++py) {
+        const int wy = min((py + 1) * fq, (yo + 1) * fp) - max(py * fq, yo * fp);
+        for (int px = px0; px < px1; ++px) {
+          const int wx = min((px + 1) * fq, (X + 1) * fp) - max(px * fq, X * fp);
+          v += (float)(wx * wy) * s_I[(size_t)(px - col0) * 2 * CS + py];
+        }
+      }
+      dst[(size_t)yo * nd + X] = v * inv;
+    }
+    return;
+  }
+  const int bsz = fp, nd = N / bsz, nbx = TC / bsz;
   if (bsz == 5 && nbx == 1) {
     // the 39 m pupil's 5 x 5 bins, one bin column per tile: unrolled sums
     for (int yb = threadIdx.x; yb < nd; yb += blockDim.x) {
@@ -601,7 +625,18 @@ constexpr int kColsTile = 8;
 template <int N1, int N2>
 static int configure(PwfsPlan *p) {
   using S = Split<N1, N2>;
-  const int bsz = p->n_pix / p->n_sub;
+  {
+    const int nd = p->pad * p->n_sub;
+    int a = S::N, b = nd;
+    while (b) {
+      const int t = a % b;
+      a = b;
+      b = t;
+    }
+    p->fp = S::N / a;
+    p->fq = nd / a;
+  }
+  const int bsz = p->fq == 1 ? p->fp : 0;   // whole bins only below the two-pass form
   p->blockA = 256;
   const int vpcA = 256 / S::G;
   p->smemA = (size_t)(vpcA * S::XB) * sizeof(float2);
@@ -609,7 +644,7 @@ static int configure(PwfsPlan *p) {
   p->smemB = ColsCfg<N1, N2, kColsTile>::smem;
   const int thrC = ((bsz * S::G + 31) / 32) * 32;
   if (thrC > 256) return SPECULA_EUNSUPPORTED;   // bin side too large for one CTA strip
-  p->blockC = thrC;
+  p->blockC = bsz ? thrC : 0;                     // 0: no three-pass form (fractional bins)
   const int nvecC = thrC / S::G;
   p->smemC = (size_t)(nvecC * S::XB) * sizeof(float2);
   if (p->smemA > 227 * 1024 || p->smemB > 227 * 1024 || p->smemC > 227 * 1024)
@@ -619,16 +654,19 @@ static int configure(PwfsPlan *p) {
       (s = ensure_dynamic_smem((const void *)k_cols<N1, N2, kColsTile>, p->smemB)) ||
       (s = ensure_dynamic_smem((const void *)k_rows_inv_part<N1, N2>, p->smemC)))
     return s;
-  // two-pass form: column tiles of TC = k bsz columns, k the largest divisor
-  // of the detector side pad n_sub with TC G <= 256
+  // two-pass form: column tiles of TC = k fp grid columns (k fq detector
+  // columns, so every detector pixel lies in one CTA), k the largest divisor
+  // of pad n_sub / fq with TC G <= 256 threads (352 where a detector pixel
+  // is a fraction of grid pixels: the SOUL example's 11-column tiles)
   p->two_ok = false;
   p->blockR = 256;
   p->smemR = (size_t)(256 / S::G) * RowFiltCfg<N1, N2>::XBF * sizeof(float2);
+  const int ndq = p->pad * p->n_sub / p->fq, maxt = p->fq == 1 ? 256 : 352;
   int k = 0;
-  for (int d = 1; d <= p->pad * p->n_sub; ++d)
-    if ((p->pad * p->n_sub) % d == 0 && d * bsz * S::G <= 256) k = d;
+  for (int d = 1; d <= ndq; ++d)
+    if (ndq % d == 0 && d * p->fp * S::G <= maxt) k = d;
   if (k > 0 && p->smemR <= 227 * 1024) {
-    const int tc = k * bsz;
+    const int tc = k * p->fp;
     p->blockK = tc * S::G;
     p->csK = ColFiltCfg<N1, N2>::stride(tc);
     // exchange buffers, or the staging window of n_pix rows x W complex
@@ -640,7 +678,9 @@ static int configure(PwfsPlan *p) {
           (s = ensure_dynamic_smem((const void *)k_colfilt_bin<N1, N2>, p->smemK)) ||
           (s = ensure_dynamic_smem((const void *)k_colfilt_bin<N1, N2, 160>, p->smemK)) ||
           (s = ensure_dynamic_smem((const void *)k_colfilt_bin<N1, N2, 256, true>, p->smemK)) ||
-          (s = ensure_dynamic_smem((const void *)k_colfilt_bin<N1, N2, 160, true>, p->smemK)))
+          (s = ensure_dynamic_smem((const void *)k_colfilt_bin<N1, N2, 160, true>, p->smemK)) ||
+          (s = ensure_dynamic_smem((const void *)k_colfilt_bin<N1, N2, 352>, p->smemK)) ||
+          (s = ensure_dynamic_smem((const void *)k_colfilt_bin<N1, N2, 352, true>, p->smemK)))
         return s;
       p->two_ok = true;
     }
@@ -655,8 +695,7 @@ static int run_split2(specula_ctx *ctx, PwfsPlan *p, const float *amp, const flo
                       int n_batch, float *det, cudaStream_t st) {
   using S = Split<N1, N2>;
   const int Np = p->n_pix;
-  const int bsz = Np / p->n_sub;
-  const int nd = S::N / bsz;
+  const int nd = p->pad * p->n_sub;   // detector side
   // the imaged cosine slots [s0, s0 + nc) of every batch element
   const int s0 = p->slot_lo;
   const int nc = (p->slot_hi < 0 ? p->nc : p->slot_hi) - s0;
@@ -678,7 +717,7 @@ static int run_split2(specula_ctx *ctx, PwfsPlan *p, const float *amp, const flo
     }
     dim3 gR((Np + vpc - 1) / vpc, (nj + p->ka - 1) / p->ka);
     const int off = (S::N - Np) / 2;                // the pupil's padded offset
-    const bool gen = p->pad != 2;
+    const bool gen = p->pad != 2 || N2 % 4 != 0;   // general-offset loads
 #define SPECULA_ROWFILT(GEN_)                                                                  \
   SPECULA_LAUNCH(ctx, SPECULA_K_PWFS_ROWFILT, st,                                              \
                  k_rowfilt<N1, N2, GEN_><<<gR, p->blockR, p->smemR, st>>>(                     \
@@ -689,15 +728,19 @@ static int run_split2(specula_ctx *ctx, PwfsPlan *p, const float *amp, const flo
   SPECULA_LAUNCH(ctx, SPECULA_K_PWFS_COLFILT, st,                                              \
                  k_colfilt_bin<N1, N2, MAXT_, GEN_><<<gK, p->blockK, p->smemK, st>>>(          \
                      p->rows.as<float2>(), p->gy.as<float2>(), p->twA.as<float2>(),            \
-                     p->twB.as<float2>(), p->mask.as<float2>(), p->part.as<float>(), Np, bsz,  \
-                     scale, p->n_mod, nc, p->nbw, j0, p->csK, off, s0))
+                     p->twB.as<float2>(), p->mask.as<float2>(), p->part.as<float>(), Np, p->fp, \
+                     p->fq, scale, p->n_mod, nc, p->nbw, j0, p->csK, off, s0))
     if (gen)
       SPECULA_ROWFILT(true);
     else
       SPECULA_ROWFILT(false);
     dim3 gK(S::N / tc, 2 * nj);
     const bool k160 = S::G == 32 && p->blockK <= 160;
-    if (k160 && gen)
+    if (p->blockK > 256 && gen)     // tiles of fractional detector pixels
+      SPECULA_COLFILT(352, true);
+    else if (p->blockK > 256)
+      SPECULA_COLFILT(352, false);
+    else if (k160 && gen)
       SPECULA_COLFILT(160, true);
     else if (k160)
       SPECULA_COLFILT(160, false);
@@ -782,6 +825,7 @@ bool pwfs_split_for(int N, int *N1, int *N2) {
     case 128: *N1 = 8; *N2 = 16; return true;
     case 240: *N1 = 15; *N2 = 16; return true;
     case 320: *N1 = 20; *N2 = 16; return true;
+    case 660: *N1 = 30; *N2 = 22; return true;   // 22 = 2 x 11, prime-factor form
     case 960: *N1 = 30; *N2 = 32; return true;
     default: return false;
   }
@@ -790,7 +834,7 @@ bool pwfs_split_for(int N, int *N1, int *N2) {
 int pwfs_set_tiles(PwfsPlan *p, int chunk, int ka, int passes) {
   if (passes < 2 || passes > 4) return SPECULA_EINVAL;
   if (passes == 2 && !p->two_ok) return SPECULA_EUNSUPPORTED;
-  if (passes == 3 && p->pad != 2) return SPECULA_EUNSUPPORTED;   // pad-2 layout only
+  if (passes == 3 && (p->pad != 2 || !p->blockC)) return SPECULA_EUNSUPPORTED;   // pad-2, whole bins
   if (passes == 4 && !p->pair_ok) return SPECULA_EUNSUPPORTED;
   const int nd = p->pad * p->n_sub;   // detector side
   // batch elements one chunk can touch: chunk items (three-pass) or chunk
@@ -864,6 +908,7 @@ int pwfs_run(specula_ctx *ctx, PwfsPlan *p, const float *amp, const float *phase
     case 128: return run_split<8, 16>(ctx, p, amp, phase, n_batch, det, st);
     case 240: return run_split<15, 16>(ctx, p, amp, phase, n_batch, det, st);
     case 320: return run_split<20, 16>(ctx, p, amp, phase, n_batch, det, st);
+    case 660: return run_split<30, 22>(ctx, p, amp, phase, n_batch, det, st);
     case 960: return run_split<30, 32>(ctx, p, amp, phase, n_batch, det, st);
     default: return SPECULA_EUNSUPPORTED;
   }
@@ -929,6 +974,7 @@ static int configure_for(PwfsPlan *p) {
     case 128: return configure<8, 16>(p);
     case 240: return configure<15, 16>(p);
     case 320: return configure<20, 16>(p);
+    case 660: return configure<30, 22>(p);
     case 960: return configure<30, 32>(p);
     default: return SPECULA_EUNSUPPORTED;
   }
@@ -1007,6 +1053,7 @@ int pwfs_plan_build(specula_ctx *ctx, const specula_pupil_desc *pupil,
   const int Np = pupil->n_pix, N = d->pad * Np;
   int N1, N2;
   if (!pwfs_split_for(N, &N1, &N2)) return SPECULA_EUNSUPPORTED;
+  if (N2 % 4 && d->pad == 2) return SPECULA_EUNSUPPORTED;   // pruned pad-2 loads need N2 % 4 == 0
   std::unique_ptr<PwfsPlan> p(new PwfsPlan());
   p->n_pix = Np; p->pad = d->pad; p->n_mod = d->n_mod; p->n_sub = d->n_sub;
   p->pup_dist = d->pup_dist_px; p->mod_amp = d->mod_amp;

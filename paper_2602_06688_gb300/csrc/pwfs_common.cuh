@@ -16,7 +16,9 @@ template <int N1_, int N2_> struct Split {
   static constexpr int S1 = N1_ | 1;   // exchange stride, standard split (odd: no conflicts)
   static constexpr int S2 = N2_ | 1;   // exchange stride, swapped split
   static constexpr int XB = N2_ * S1;  // exchange buffer per vector (complex)
-  static_assert(N2_ % 4 == 0, "pruned zero-padded input needs N2 % 4 == 0");
+  // the pruned pad-2 loads take the pupil as rows N2/4 .. 3 N2/4 of the
+  // strided input and need N2 % 4 == 0; other splits (660 = 30 x 22) run the
+  // general-offset loads only (the plan refuses pad 2 for them)
   static_assert(MX <= 32, "one vector per warp at most");
   static_assert(2 * XB >= N, "a vector's exchange buffer must hold N floats");
 };

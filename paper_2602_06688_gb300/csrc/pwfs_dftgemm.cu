@@ -150,6 +150,7 @@ int pwfs_dftgemm_prepare(PwfsPlan *p, int form) {
   // operand's 128-byte row: 64 bf16 or 32 tf32); dense operators are meant
   // for small padded grids
   if (N > 512 || (2 * N) % 128 || (6 * Np) % (tf32 ? 32 : 64)) return SPECULA_EUNSUPPORTED;
+  if (p->fq != 1) return SPECULA_EUNSUPPORTED;   // whole bins
   // circulant kernel row h[d] = sum_k mask[k] exp(2 pi i k d / N), float64
   std::vector<std::complex<double>> mk(N), h(N);
   for (int k = 0; k < N; ++k) {

@@ -520,7 +520,7 @@ static int pair_configure_t(PwfsPlan *p) {
   using P = PairCfg<N1, N2>;
   const int bsz = p->n_pix / p->n_sub;
   p->pair_ok = false;
-  if (p->pad != 2 || p->pup_dist != p->n_pix) return SPECULA_OK;   // pad-2 quadrant layout
+  if (p->pad != 2 || p->pup_dist != p->n_pix || p->fq != 1) return SPECULA_OK;   // pad-2 quadrants
   // column tile: TC = k bsz columns, the largest k dividing the detector
   // side with TC <= 5 warps (two CTAs per SM by shared memory)
   int k = 0;

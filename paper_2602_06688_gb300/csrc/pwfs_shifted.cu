@@ -298,6 +298,7 @@ int sm_prepare(PwfsPlan *p) {
   constexpr int N = S::N, G = S::G;
   const int Np = p->n_pix, bsz = Np / p->n_sub;
   if (2 * Np != N || Np != N1 * (N2 / 2)) return SPECULA_EUNSUPPORTED;   // pad 2: pruned halves
+  if (p->fq != 1) return SPECULA_EUNSUPPORTED;                          // whole bins
   // column tile: TC = k bsz with TC G <= 256 (every bin in one CTA)
   int k = 0;
   for (int d = 1; d <= 2 * p->n_sub; ++d)

@@ -147,6 +147,23 @@ def _soul8m():
                     layers, n_modes=300, n_frames=1000, dt_s=1e-3, r0_m=0.14)
 
 
+def _soul220():
+    """The paper's SOUL example as stated (App. B, Listing 2; Sect. 6,
+    Tab. 2): 220 px pupil (0.037 m pixels on LBT's 8.2 m), 3x oversampling
+    (660^2 FFT), 24 modulation points of 3 lambda/D, pup_diam 40 and
+    pup_dist 48 subapertures (264 grid pixels) on an output_resolution 120
+    detector, so a detector pixel is 5.5 x 5.5 grid pixels; 750 nm; 500
+    modes.  Two layers as in soul8m (the listing's atmosphere is not all
+    given)."""
+    D, n = 8.2, 220
+    pup = Pupil(n, D / n, 0.11)
+    src = Source(0.0, 0.0, math.inf, 750.0)
+    geom = PwfsGeom(pad=3, n_mod=24, mod_amp=3.0, n_sub=40, pup_dist_px=264)
+    layers = _profile(6, 2, 0.14, [0.0, 6000.0], [0.7, 0.3], [6.0, 15.0], 512, D / n, 40.0, 6)
+    return Workload('soul220', D, (Sensor('pwfs', pup, src, pwfs=geom),),
+                    layers, n_modes=500, n_frames=1000, dt_s=1e-3, r0_m=0.14)
+
+
 def _learned8m():
     base = _pwfs8m()
     return Workload('learned8m', base.diameter_m, base.sensors, base.layers[:1],
@@ -228,6 +245,7 @@ WORKLOADS = {
     'mwfs8m_small': _mwfs8m_small,
     'pwfs39m': _pwfs39m,
     'soul8m': _soul8m,
+    'soul220': _soul220,
 }
 
 

@@ -91,8 +91,8 @@ def test_host_validation_returns_codes(sp):
     assert lib.specula_pupil_mask_host(C.byref(good), None) == sp.EINVAL
     nv = C.c_int32()
     idx = np.zeros(16, dtype=np.int32)
-    assert lib.specula_valid_subaps_host(C.byref(good), 3, idx.ctypes.data_as(C.c_void_p),
-                                         C.byref(nv)) == sp.EINVAL    # 4 % 3 != 0
+    assert lib.specula_valid_subaps_host(C.byref(good), 5, idx.ctypes.data_as(C.c_void_p),
+                                         C.byref(nv)) == sp.EINVAL    # n_sub > n_pix
     assert lib.specula_mod_table_host(0, None, None) == sp.EINVAL
     # per-frame calls reject a null context before touching the device
     pw = sp.PwfsDesc(2, 12, 16, 64, 3.0)
@@ -125,3 +125,22 @@ def test_pyr_image_index_host_matches_oracle(sp):
     with pytest.raises(sp.SpeculaError) as e:
         sp.specula_pyr_image_index_host(pu, 3, 97, 40)       # not a multiple of b = 2
     assert e.value.status == sp.EUNSUPPORTED
+    # the paper's own SOUL numbers: 220 px pupil, 40 subapertures of 5.5 px,
+    # images 264 grid px = 48 detector px apart on the 120 px detector
+    pu3 = sp.PupilDesc(220, 8.2 / 220, 0.11)
+    v3 = geometry.valid_subaps(geometry.pupil_mask(220, 0.11).astype(np.uint8), 40)
+    assert np.array_equal(sp.specula_valid_subaps_host(pu3, 40), v3)
+    m3 = sp.specula_pyr_image_index_host(pu3, 3, 264, 40)
+    assert np.array_equal(m3, geometry.pyr_image_index(v3, 40, 3, 264, 220))
+    assert m3.min() // 120 == 16 and m3.max() // 120 == 103
+    with pytest.raises(sp.SpeculaError) as e:
+        sp.specula_pyr_image_index_host(pu3, 3, 265, 40)     # 265 / 5.5 is not whole
+    assert e.value.status == sp.EUNSUPPORTED
+
+
+@pytest.mark.parametrize("n,n_sub,obsc", [(22, 4, 0.0), (33, 6, 0.3), (100, 7, 0.2), (63, 10, 0.11)])
+def test_valid_subaps_host_fractional(sp, n, n_sub, obsc):
+    """Fractional subaperture sides: the host rule is the oracle's, exactly."""
+    from oracle import geometry
+    got = sp.specula_valid_subaps_host(sp.PupilDesc(n, 0.1, obsc), n_sub)
+    assert np.array_equal(got, geometry.valid_subaps(geometry.pupil_mask(n, obsc), n_sub))

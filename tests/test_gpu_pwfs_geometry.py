@@ -13,9 +13,13 @@ from oracle import atmo, geometry, pyramid, recon, slopes
 pytestmark = pytest.mark.gpu
 
 # (n_pix, pad, pup_dist_px, n_sub, n_mod): SOUL (N 240), pad 4 (N 128, 64),
-# the 960^2 grid at pad 3, and pad 2 with images closer than their width
+# the 960^2 grid at pad 3, and pad 2 with images closer than their width;
+# fractional detector pixels (area-weighted rebinning in the column pass):
+# the paper's SOUL as stated (220 px pupil, 660^2 grid, 24 points, 5.5 grid
+# pixels per detector pixel), a 240 grid with 2.5 px detector pixels
+# (16-lane transforms), pad 2 on a 320 grid with 2.5 px detector pixels
 CASES = [(80, 3, 96, 40, 16), (32, 4, 48, 8, 8), (16, 4, 24, 4, 8), (320, 3, 384, 80, 16),
-         (64, 2, 48, 16, 12)]
+         (64, 2, 48, 16, 12), (220, 3, 264, 40, 24), (80, 3, 100, 32, 16), (160, 2, 160, 64, 12)]
 
 
 @pytest.fixture(scope="module")
@@ -88,13 +92,15 @@ def test_maps_equal_quadrants_bit_exact(env):
     assert torch.equal(a, b)
 
 
-def test_soul_frame_vs_oracle_chain(env):
-    """The SOUL-geometry frame (80 px pupil, pad 3, 40 x 40 subapertures,
-    images 48 detector px apart on 120 px): extraction, image, map slopes,
-    MVM against the oracle chain."""
+@pytest.mark.parametrize("name", ["soul8m", "soul220"])
+def test_soul_frame_vs_oracle_chain(env, name):
+    """The SOUL-geometry frame (40 x 40 subapertures, images 48 detector px
+    apart on 120 px; soul8m: 80 px pupil with 2 x 2 bins, soul220: the
+    paper's 220 px pupil on a 660^2 grid with 5.5 px detector pixels):
+    extraction, image, map slopes, MVM against the oracle chain."""
     torch, sp, ctx = env
     from paper_2602_06688_gb300.frame import PwfsFrame
-    wl = synth.workload("soul8m")
+    wl = synth.workload(name)
     fr = PwfsFrame(ctx, wl)
     s = wl.sensors[0]
     n, g = s.pupil.n_pix, s.pwfs
