@@ -618,6 +618,27 @@ int specula_sh_image(specula_ctx *ctx, const specula_pupil_desc *pupil,
                      const float *phase_dev, int32_t n_batch, float *spots_dev,
                      void *stream);
 
+/* Polychromatic Shack-Hartmann spots (PolyChromSH, App. A, Tab. 4): for
+ * n_batch phase maps in radians at the reference wavelength,
+ *   spots = sum over i (in order) of weight[i] ratio[i]^2 W_i S_i W_i^T,
+ * S_i the spots above at lambda_i (phase times ratio[i] = lambda_ref /
+ * lambda_i, the same fft_n, so a spot pixel is lambda_i / (fft_n d) = 1 /
+ * ratio[i] reference pixels) and W_i[o][j] the overlap of reference pixel o,
+ * [o - fft_n/2 - 1/2, o - fft_n/2 + 1/2), with spot pixel j, [(j - fft_n/2 -
+ * 1/2) / ratio, (j - fft_n/2 + 1/2) / ratio), both centred on the zero
+ * frequency: the detector integrates each wavelength's piecewise-constant
+ * spot over its own pixels; light beyond a subaperture's fft_n window is
+ * dropped (a field stop per subaperture).  ratio[i] = 1 reproduces
+ * specula_sh_image.  ratio, weight: n_lambda host doubles (1 <= n_lambda
+ * <= 64, ratio > 0).  spots_dev as specula_sh_image (the plan's imaged
+ * range).  Uses a context workspace of one wavelength's spots, grown on the
+ * first call of a new size (synchronising the stream; refused with
+ * SPECULA_EUNSUPPORTED inside stream capture).  fft_n 24 or 16. */
+int specula_sh_image_poly(specula_ctx *ctx, const specula_pupil_desc *pupil,
+                          const specula_sh_desc *sh, int32_t n_lambda, const double *ratio,
+                          const double *weight, const float *amp_dev, const float *phase_dev,
+                          int32_t n_batch, float *spots_dev, void *stream);
+
 /* Imaged subapertures of a Shack-Hartmann plan (set-up call; synchronises):
  * after this call specula_sh_image computes the spots of the valid
  * subapertures sub_begin .. sub_end - 1 only (positions in the ascending

@@ -477,6 +477,26 @@ def specula_sh_image(ctx, pupil, sh, amp, phase, spots, n_valid, stream=None):
         "specula_sh_image")
 
 
+def specula_sh_image_poly(ctx, pupil, sh, ratios, weights, amp, phase, spots, n_valid,
+                          stream=None):
+    """spots = sum_i weights[i] ratios[i]^2 W_i spots(phase * ratios[i]) W_i^T,
+    each wavelength's spots integrated over the reference pixels;
+    ratios = lambda_ref / lambda_i."""
+    import torch
+    n = pupil.n_pix
+    nb = phase.numel() // (n * n)
+    r = np.ascontiguousarray(ratios, dtype=np.float64)
+    w = np.ascontiguousarray(weights, dtype=np.float64)
+    if r.shape != w.shape or r.ndim != 1:
+        raise ValueError("ratios and weights must be 1-D of equal length")
+    _abi.check(lib().specula_sh_image_poly(
+        ctx.handle, C.byref(pupil), C.byref(sh), int(r.size), r.ctypes.data_as(C.c_void_p),
+        w.ctypes.data_as(C.c_void_p), _dev(amp, torch.float32, n * n, "amp"),
+        _dev(phase, torch.float32, nb * n * n, "phase"), nb,
+        _dev(spots, torch.float32, nb * n_valid * sh.fft_n ** 2, "spots"), _stream(stream)),
+        "specula_sh_image_poly")
+
+
 def specula_sh_set_range(ctx, pupil, sh, sub_begin, sub_end):
     """Image only the valid subapertures [sub_begin, sub_end) (set-up call)."""
     _abi.check(lib().specula_sh_set_range(ctx.handle, C.byref(pupil), C.byref(sh),

@@ -138,6 +138,8 @@ SIGNATURES = {
     "specula_pwfs_image": (C.c_int, [vp, P(PupilDesc), P(PwfsDesc), vp, vp, i32, vp, vp]),
     "specula_sh_plan": (C.c_int, [vp, P(PupilDesc), P(ShDesc), P(i32)]),
     "specula_sh_image": (C.c_int, [vp, P(PupilDesc), P(ShDesc), vp, vp, i32, vp, vp]),
+    "specula_sh_image_poly": (C.c_int, [vp, P(PupilDesc), P(ShDesc), i32, vp, vp, vp, vp, i32,
+                                        vp, vp]),
     "specula_sh_set_range": (C.c_int, [vp, P(PupilDesc), P(ShDesc), i32, i32]),
     "specula_slopes": (C.c_int, [vp, P(SlopecDesc), vp, vp, i32, vp, vp]),
     "specula_recon": (C.c_int, [vp, P(ReconDesc), vp, i32, vp, vp]),

@@ -710,3 +710,40 @@ extern "C" int specula_sh_image(specula_ctx *ctx, const specula_pupil_desc *pupi
   if (n_batch == 0) return SPECULA_OK;
   return sh_run(ctx, p, amp_dev, phase_dev, n_batch, spots_dev, (cudaStream_t)stream);
 }
+
+extern "C" int specula_sh_image_poly(specula_ctx *ctx, const specula_pupil_desc *pupil,
+                                     const specula_sh_desc *sh, int32_t n_lambda,
+                                     const double *ratio, const double *weight,
+                                     const float *amp_dev, const float *phase_dev,
+                                     int32_t n_batch, float *spots_dev, void *stream) {
+  if (!ctx || !amp_dev || !phase_dev || !spots_dev || n_batch < 0 || !ratio || !weight)
+    return SPECULA_EINVAL;
+  if (n_lambda < 1 || n_lambda > 64) return SPECULA_EINVAL;
+  for (int i = 0; i < n_lambda; ++i)
+    if (!(ratio[i] > 0.0) || !isfinite(ratio[i]) || !isfinite(weight[i])) return SPECULA_EINVAL;
+  int s = check_sh(pupil, sh);
+  if (s) return s;
+  ShPlan *p = sh_plan_find(ctx, pupil, sh);
+  if (!p) return SPECULA_ENOPLAN;
+  if (sh->fft_n != 24 && sh->fft_n != 16) return SPECULA_EUNSUPPORTED;
+  const int nv = (p->sub_hi < 0 ? p->n_valid : p->sub_hi) - p->sub_lo;
+  const size_t n_spots = (size_t)nv * n_batch;
+  if (n_spots == 0) return SPECULA_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t need = n_spots * sh->fft_n * sh->fft_n * sizeof(float);
+  if (ctx->sh_poly_ws.bytes < need) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    SPECULA_CK(cudaStreamIsCapturing(st, &cs));
+    if (cs != cudaStreamCaptureStatusNone) return SPECULA_EUNSUPPORTED;   // grow before capture
+    SPECULA_CK(cudaStreamSynchronize(st));
+    if ((s = ctx->sh_poly_ws.alloc(need))) return s;
+  }
+  float *ws = ctx->sh_poly_ws.as<float>();
+  for (int i = 0; i < n_lambda; ++i) {
+    if ((s = sh_run(ctx, p, amp_dev, phase_dev, n_batch, ws, st, (float)ratio[i]))) return s;
+    if ((s = sh_poly_acc(ctx, sh->fft_n, ws, (int)n_spots, ratio[i], weight[i], i == 0,
+                         spots_dev, st)))
+      return s;
+  }
+  return SPECULA_OK;
+}

@@ -180,6 +180,9 @@ struct specula_ctx {
   // batched bf16 reconstructor products: the slopes' bf16 halves and the
   // split-K partials (grown on demand outside stream capture)
   specula::DevBuf recon_ws;
+  // one wavelength's spots of the polychromatic Shack-Hartmann (grown on
+  // demand outside stream capture)
+  specula::DevBuf sh_poly_ws;
 };
 
 namespace specula {
@@ -258,7 +261,11 @@ int sh_plan_build(specula_ctx *ctx, const specula_pupil_desc *pupil,
 ShPlan *sh_plan_find(specula_ctx *ctx, const specula_pupil_desc *pupil,
                      const specula_sh_desc *sh);
 int sh_run(specula_ctx *ctx, ShPlan *plan, const float *amp, const float *phase,
-           int n_batch, float *spots, cudaStream_t st);
+           int n_batch, float *spots, cudaStream_t st, float phase_scale = 1.0f);
+// out = (first ? 0 : out) + weight ratio^2 W spots W^T for n_spots fft_n^2
+// spots of one wavelength (ratio = lambda_ref / lambda): the polychromatic SH
+int sh_poly_acc(specula_ctx *ctx, int fft_n, const float *spots, int n_spots, double ratio,
+                double weight, bool first, float *out, cudaStream_t st);
 
 // Raise (never lower) a kernel's dynamic shared-memory limit to `bytes` on
 // the current device.  The limit belongs to the function, shared by every

@@ -27,7 +27,7 @@ template <int NF, int SP>
 __global__ void __launch_bounds__(kShWarps * 32) k_sh_spots(
     const float *__restrict__ amp, const float *__restrict__ phase,
     const int32_t *__restrict__ valid, const float2 *__restrict__ pre, int n_pix, int n_sub,
-    int n_valid, int n_batch, float *__restrict__ spots) {
+    int n_valid, int n_batch, float phase_scale, float *__restrict__ spots) {
   constexpr int OFF = (NF - SP) / 2;
   constexpr int XS = SP | 1;
   __shared__ float2 s_x[kShWarps][NF * XS];
@@ -52,7 +52,7 @@ __global__ void __launch_bounds__(kShWarps * 32) k_sh_spots(
 #pragma unroll
     for (int c = 0; c < SP; ++c) {
       float sv, cv;
-      sincosf(ph[c], &sv, &cv);
+      sincosf(ph[c] * phase_scale, &sv, &cv);
       const float A = am[c];
       v[OFF + c] = cmul(cmul(make_float2(A * cv, A * sv), pre[OFF + c]), py);
     }
@@ -116,7 +116,7 @@ int sh_plan_build(specula_ctx *ctx, const specula_pupil_desc *pupil, const specu
 }
 
 int sh_run(specula_ctx *ctx, ShPlan *p, const float *amp, const float *phase, int n_batch,
-           float *spots, cudaStream_t st) {
+           float *spots, cudaStream_t st, float phase_scale) {
   // the imaged block of the valid list: spots are compact over it
   const int lo = p->sub_lo, nv = (p->sub_hi < 0 ? p->n_valid : p->sub_hi) - lo;
   const int32_t *valid = p->valid.as<int32_t>() + lo;
@@ -127,12 +127,72 @@ int sh_run(specula_ctx *ctx, ShPlan *p, const float *amp, const float *phase, in
     SPECULA_LAUNCH(ctx, SPECULA_K_SH, st,
                    k_sh_spots<24, 12><<<grid, kShWarps * 32, 0, st>>>(
                        amp, phase, valid, p->pre.as<float2>(), p->n_pix, p->n_sub, nv, n_batch,
-                       spots));
+                       phase_scale, spots));
   else if (p->fft_n == 16 && p->sub_pix == 8)
     SPECULA_LAUNCH(ctx, SPECULA_K_SH, st,
                    k_sh_spots<16, 8><<<grid, kShWarps * 32, 0, st>>>(
                        amp, phase, valid, p->pre.as<float2>(), p->n_pix, p->n_sub, nv, n_batch,
-                       spots));
+                       phase_scale, spots));
+  else
+    return SPECULA_EUNSUPPORTED;
+  return SPECULA_OK;
+}
+
+// Polychromatic spots: accumulate weight r^2 (W S W^T) of one wavelength's
+// spots S (pixel lambda_i / (NF d), 1 / r detector pixels, r = lambda_ref /
+// lambda_i) onto the reference detector lattice.  W[o][j] is the overlap of
+// detector pixel o, [o - NF/2 - 1/2, o - NF/2 + 1/2), with spot pixel j,
+// [(j - NF/2 - 1/2) / r, (j - NF/2 + 1/2) / r), in detector pixels; r^2 turns
+// a spot pixel's value into the flux density over its area.  One CTA per
+// spot; out = (first ? 0 : out) + weight r^2 W S W^T, in the caller's order.
+template <int NF>
+__global__ void __launch_bounds__(256) k_sh_poly_acc(const float *__restrict__ spots, int n_spots,
+                                                     float r, float wr2, int first,
+                                                     float *__restrict__ out) {
+  __shared__ float s_S[NF * NF], s_T[NF * NF], s_W[NF * NF];
+  const int sp = blockIdx.x;
+  if (sp >= n_spots) return;
+  const float *S = spots + (size_t)sp * NF * NF;
+  for (int e = threadIdx.x; e < NF * NF; e += blockDim.x) {
+    s_S[e] = S[e];
+    const int o = e / NF, j = e - o * NF;
+    const float alo = (float)(o - NF / 2) - 0.5f, ahi = alo + 1.0f;
+    const float blo = ((float)(j - NF / 2) - 0.5f) / r, bhi = ((float)(j - NF / 2) + 0.5f) / r;
+    s_W[e] = fmaxf(0.f, fminf(ahi, bhi) - fmaxf(alo, blo));
+  }
+  __syncthreads();
+  // T[o][jx] = sum_jy W[o][jy] S[jy][jx]
+  for (int e = threadIdx.x; e < NF * NF; e += blockDim.x) {
+    const int o = e / NF, jx = e - o * NF;
+    float v = 0.f;
+#pragma unroll 8
+    for (int jy = 0; jy < NF; ++jy) v += s_W[o * NF + jy] * s_S[jy * NF + jx];
+    s_T[e] = v;
+  }
+  __syncthreads();
+  // D[oy][ox] = sum_jx T[oy][jx] W[ox][jx]
+  float *D = out + (size_t)sp * NF * NF;
+  for (int e = threadIdx.x; e < NF * NF; e += blockDim.x) {
+    const int oy = e / NF, ox = e - oy * NF;
+    float v = 0.f;
+#pragma unroll 8
+    for (int jx = 0; jx < NF; ++jx) v += s_T[oy * NF + jx] * s_W[ox * NF + jx];
+    D[e] = first ? wr2 * v : D[e] + wr2 * v;
+  }
+}
+
+int sh_poly_acc(specula_ctx *ctx, int fft_n, const float *spots, int n_spots, double ratio,
+                double weight, bool first, float *out, cudaStream_t st) {
+  if (n_spots == 0) return SPECULA_OK;
+  const float r = (float)ratio, wr2 = (float)(weight * ratio * ratio);
+  if (fft_n == 24)
+    SPECULA_LAUNCH(ctx, SPECULA_K_SH, st,
+                   k_sh_poly_acc<24><<<n_spots, 256, 0, st>>>(spots, n_spots, r, wr2,
+                                                              first ? 1 : 0, out));
+  else if (fft_n == 16)
+    SPECULA_LAUNCH(ctx, SPECULA_K_SH, st,
+                   k_sh_poly_acc<16><<<n_spots, 256, 0, st>>>(spots, n_spots, r, wr2,
+                                                              first ? 1 : 0, out));
   else
     return SPECULA_EUNSUPPORTED;
   return SPECULA_OK;
