@@ -420,13 +420,32 @@ def closed_loop_leg(ctx, steps=400, settle=150):
     the largest command every 100 steps (bounded commands: no mode drifts)."""
     import torch
     import synth
-    from paper_2602_06688_gb300.loop import ClosedLoop
+    import paper_2602_06688_gb300 as sp
+    from paper_2602_06688_gb300.loop import ClosedLoop, LoopNetwork
     st = torch.cuda.Stream()
     out = {"workload": "pwfs8m", "gain": 0.4, "sci_wavelength_nm": 1650.0}
     cl = ClosedLoop(ctx, synth.workload("pwfs8m"), gain=0.4)
+    # pixels the sensor sees: inside a valid subaperture and the pupil
+    fr = cl.fr
+    g = synth.workload("pwfs8m").sensors[0].pwfs
+    b = fr.n_pix // g.n_sub
+    seen = np.zeros((fr.n_pix, fr.n_pix), dtype=bool)
+    for v in sp.specula_valid_subaps_host(fr.pupil, g.n_sub):
+        a, c = divmod(int(v), g.n_sub)
+        seen[a * b:(a + 1) * b, c * b:(c + 1) * b] = True
+    seen &= fr.amp.cpu().numpy() > 0
+    seen_t = torch.tensor(seen, device="cuda")
+    n_seen = float(seen.sum())
+    nets = {}
     for label, gain, leak in (("closed", 0.4, 0.01), ("closed_no_leak", 0.4, 0.0),
-                              ("open", 0.0, 0.0)):
+                              ("open", 0.0, 0.0), ("closed_learned_correction", 0.4, 0.01),
+                              ("closed_learned_direct", 0.4, 0.01)):
         cl.gain, cl.leak = gain, leak
+        cl.net = None
+        if label.startswith("closed_learned"):
+            net = LoopNetwork(cl, residual=label.endswith("correction"))
+            nets[label] = net.train()
+            cl.net = net
         cl.reset()
         cl.close()
         cl.capture(st)
@@ -441,18 +460,26 @@ def closed_loop_leg(ctx, steps=400, settle=150):
                 hist[k].copy_(cl.stats)
             e1.record()
         torch.cuda.synchronize()
-        # the command trajectory, from a second (untimed) run of the same steps
+        # the command trajectory and the residual over the seen pixels, from a
+        # second (untimed) run of the same steps
         cl.reset()
+        seen_ms = torch.zeros(steps, dtype=torch.float64, device="cuda")
         with torch.cuda.stream(st):
             for k in range(steps):
                 cl.replay(k * cl.fr.dt, st)
                 cmax[k] = cl.cmd.abs().max()
+                r = cl.resid.double()[seen_t]
+                seen_ms[k] = ((r - r.mean()) ** 2).sum() / n_seen
         torch.cuda.synchronize()
         h = hist.cpu().numpy()[settle:]
         c = cmax.cpu().numpy()
         out[label] = {"leak": leak, "strehl": float(h[:, 1].mean()),
                       "resid_rms_rad_wfs_full_pupil": float(h[:, 0].mean()),
+                      "resid_rms_rad_wfs_seen_pixels":
+                          float(np.sqrt(seen_ms.cpu().numpy()[settle:]).mean()),
                       "max_abs_cmd_every_100": [float(c[k]) for k in range(99, steps, 100)]}
+        if label in nets:
+            out[label]["training"] = nets[label]
         if label == "closed":
             ms = e0.elapsed_time(e1)
             out.update({"frames_per_s": steps / (ms / 1e3), "ms_per_step": ms / steps,
@@ -460,7 +487,12 @@ def closed_loop_leg(ctx, steps=400, settle=150):
                         "graph_kernels": cl.graph.kernel_count(),
                         "timing": "back-to-back steps, each with a 16-byte copy of its "
                                   "statistics; L2 not flushed"})
+    cl.net = None
     cl.close()
+    out["learned_note"] = ("closed_learned_correction: m = R s + f(s), f the 2512-1024-1024-500 "
+                           "network trained on synthetic modal phases with 16x the loop's own "
+                           "residual spectrum (targets: what R s misses); closed_learned_direct: "
+                           "m = f(s) alone, same training phases")
     return out
 
 

@@ -91,6 +91,14 @@ class MlpRegressor:
             hist.append(float(loss.item()))
         return hist
 
+    def predict_into(self, X, Y, Xn, stream=None):
+        """Y = network(X) into preallocated buffers (Xn: X's shape), every step
+        a library call on `stream` (graph-capturable; batches of at most 4 take
+        the weight-streaming inference kernels)."""
+        specula_affine_cols(self.ctx, X, self.x_shift, self.x_mul, Xn, stream=stream)
+        self.mlp.infer(Xn, Y, stream=stream)
+        specula_affine_cols(self.ctx, Y, self.y_shift, self.y_mul, Y, stream=stream)
+
     def predict(self, X, chunk=1024):
         torch = self.torch
         Xn = torch.empty_like(X)

@@ -137,3 +137,47 @@ def test_closed_loop_on_the_soul_geometry(env):
     sr = np.array(sr)
     assert sr[-1, 1] > 5 * sr[0, 1] and sr[-5:, 0].mean() < 0.5 * sr[0, 0]
     lp.close()
+
+
+@pytest.mark.parametrize("residual", [True, False])
+def test_learned_reconstructor_in_the_loop(env, residual):
+    """The network in the loop (R s + f(s), or f(s) alone), trained on the
+    loop's own residual spectrum, runs from the captured graph: the graph
+    replay equals eager steps bit for bit, the commands stay bounded, and the
+    correction keeps the linear loop's Strehl ratio (within 5%)."""
+    torch, sp, ctx = env
+    from paper_2602_06688_gb300.loop import ClosedLoop, LoopNetwork
+    lp = ClosedLoop(ctx, synth.workload("pwfs8m_tiny"), n_modes=60, gain=0.4)
+    steps, settle = 120, 60
+
+    def run(graph):
+        lp.reset()
+        s = []
+        st = torch.cuda.Stream()
+        with torch.cuda.stream(st):
+            for k in range(steps):
+                if graph:
+                    lp.replay(k * lp.fr.dt, st)
+                else:
+                    lp.step(k * lp.fr.dt, stream=st)
+                s.append(lp.stats.clone())
+        torch.cuda.synchronize()
+        return torch.stack(s).cpu().numpy(), lp.cmd.clone()
+
+    lin, _ = run(False)
+    net = LoopNetwork(lp, hidden=(256, 256), residual=residual)
+    info = net.train(n_pairs=8192, epochs=10)
+    assert np.isfinite(info["final_loss"])
+    lp.net = net
+    eager, c_eager = run(False)
+    lp.capture(torch.cuda.Stream())
+    graph, c_graph = run(True)
+    lp.net = None
+    lp.close()
+    assert np.array_equal(eager, graph) and torch.equal(c_eager, c_graph)
+    assert float(c_eager.abs().max()) < 50.0
+    s_lin, s_net = lin[settle:, 1].mean(), eager[settle:, 1].mean()
+    if residual:
+        assert s_net >= 0.95 * s_lin, (s_net, s_lin)
+    else:
+        assert s_net > 0.5 * s_lin, (s_net, s_lin)
