@@ -604,8 +604,11 @@ int specula_pwfs_image_poly(specula_ctx *ctx, const specula_pupil_desc *pupil,
                             int32_t n_batch, float *det_dev, void *stream);
 
 /* Build (or reuse) the tables of a Shack-Hartmann geometry and its valid
- * subaperture list (host rule above).  May allocate.  Supported fft_n: 24
- * with sub_pix 12, and 16 with sub_pix 8.  *n_valid receives the count. */
+ * subaperture list (host rule above).  May allocate.  Supported (fft_n,
+ * sub_pix): (24, 12), (16, 8), and Sect. 6 Tab. 2's spot sizes (56, 8) (the
+ * SCAO SH: 20 x 20 lenslets on a 160 px pupil) and (68, 4) (ERIS: 40 x 40
+ * on 160 px), whose transforms are wider than a warp (56 = 8 x 7, 68 = 4 x
+ * 17, prime-factor form).  *n_valid receives the count. */
 int specula_sh_plan(specula_ctx *ctx, const specula_pupil_desc *pupil,
                     const specula_sh_desc *sh, int32_t *n_valid);
 

@@ -17,7 +17,7 @@ def cache_path():
 
 
 def _key(device_name, pupil, pwfs, n_batch):
-    return (f"v3|{device_name}|np{pupil.n_pix}|pad{pwfs.pad}|mod{pwfs.n_mod}|sub{pwfs.n_sub}"
+    return (f"v4|{device_name}|np{pupil.n_pix}|pad{pwfs.pad}|mod{pwfs.n_mod}|sub{pwfs.n_sub}"
             f"|b{n_batch}")
 
 

@@ -662,7 +662,8 @@ static int check_sh(const specula_pupil_desc *pupil, const specula_sh_desc *sh) 
   if (s) return s;
   if (!sh || sh->n_sub < 1 || sh->sub_pix < 1 || sh->fft_n < sh->sub_pix) return SPECULA_EINVAL;
   if (sh->n_sub * sh->sub_pix != pupil->n_pix) return SPECULA_EINVAL;
-  if (!((sh->fft_n == 24 && sh->sub_pix == 12) || (sh->fft_n == 16 && sh->sub_pix == 8)))
+  if (!((sh->fft_n == 24 && sh->sub_pix == 12) || (sh->fft_n == 16 && sh->sub_pix == 8) ||
+        (sh->fft_n == 56 && sh->sub_pix == 8) || (sh->fft_n == 68 && sh->sub_pix == 4)))
     return SPECULA_EUNSUPPORTED;
   return SPECULA_OK;
 }

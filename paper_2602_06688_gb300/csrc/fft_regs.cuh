@@ -64,10 +64,23 @@ constexpr int kCodeletTotal = codelet_total();
 static __constant__ float2 c_codelet_tw[kCodeletTotal];
 // the base butterflies' real constants as broadcast pairs (c, c):
 // [0] cos 2pi/3, [1] sin 2pi/3, [2] cos 2pi/5, [3] cos 4pi/5, [4] sin 2pi/5,
-// [5] sin 4pi/5, [6] -sin 2pi/5, [7 + m - 1] cos 2pi m/11, [12 + m - 1]
-// sin 2pi m/11, [17 + m - 1] -sin 2pi m/11 (m = 1 .. 5)
-constexpr int kBflyPairs = 22;
+// [5] sin 4pi/5, [6] -sin 2pi/5
+constexpr int kBflyPairs = 7;
 static __constant__ float2 c_bfly_pairs[kBflyPairs];
+// odd primes with a direct butterfly; for prime P (H = (P - 1) / 2) the
+// block at prime_off(P) holds cos 2pi m/P, then sin 2pi m/P, then
+// -sin 2pi m/P, m = 1 .. H, as broadcast pairs
+constexpr int kPrimes[] = {7, 11, 13, 17};
+constexpr int kNumPrimes = sizeof(kPrimes) / sizeof(int);
+constexpr int prime_off(int P, int i = 0, int acc = 0) {
+  return i >= kNumPrimes ? -1
+         : (kPrimes[i] == P ? acc : prime_off(P, i + 1, acc + 3 * (kPrimes[i] - 1) / 2));
+}
+constexpr int prime_total(int i = 0) {
+  return i >= kNumPrimes ? 0 : 3 * (kPrimes[i] - 1) / 2 + prime_total(i + 1);
+}
+constexpr int kPrimePairs = prime_total();
+static __constant__ float2 c_prime_pairs[kPrimePairs];
 
 static inline cudaError_t upload_codelet_twiddles() {
   float2 h[kCodeletTotal];
@@ -81,18 +94,25 @@ static inline cudaError_t upload_codelet_twiddles() {
   }
   cudaError_t e = cudaMemcpyToSymbol(c_codelet_tw, h, sizeof(h));
   if (e != cudaSuccess) return e;
-  float v[kBflyPairs] = {(float)cos(2.0 * M_PI / 3.0), (float)sin(2.0 * M_PI / 3.0),
-                         (float)cos(2.0 * M_PI / 5.0), (float)cos(4.0 * M_PI / 5.0),
-                         (float)sin(2.0 * M_PI / 5.0), (float)sin(4.0 * M_PI / 5.0),
-                         -(float)sin(2.0 * M_PI / 5.0)};
-  for (int m = 1; m <= 5; ++m) {
-    v[7 + m - 1] = (float)cos(2.0 * M_PI * m / 11.0);
-    v[12 + m - 1] = (float)sin(2.0 * M_PI * m / 11.0);
-    v[17 + m - 1] = -(float)sin(2.0 * M_PI * m / 11.0);
-  }
+  const float v[kBflyPairs] = {(float)cos(2.0 * M_PI / 3.0), (float)sin(2.0 * M_PI / 3.0),
+                               (float)cos(2.0 * M_PI / 5.0), (float)cos(4.0 * M_PI / 5.0),
+                               (float)sin(2.0 * M_PI / 5.0), (float)sin(4.0 * M_PI / 5.0),
+                               -(float)sin(2.0 * M_PI / 5.0)};
   float2 hp[kBflyPairs];
   for (int i = 0; i < kBflyPairs; ++i) hp[i] = make_float2(v[i], v[i]);
-  return cudaMemcpyToSymbol(c_bfly_pairs, hp, sizeof(hp));
+  e = cudaMemcpyToSymbol(c_bfly_pairs, hp, sizeof(hp));
+  if (e != cudaSuccess) return e;
+  float2 pp[kPrimePairs];
+  for (int i = 0; i < kNumPrimes; ++i) {
+    const int P = kPrimes[i], H = (P - 1) / 2, o = prime_off(P);
+    for (int m = 1; m <= H; ++m) {
+      const float c = (float)cos(2.0 * M_PI * m / P), sn = (float)sin(2.0 * M_PI * m / P);
+      pp[o + m - 1] = make_float2(c, c);
+      pp[o + H + m - 1] = make_float2(sn, sn);
+      pp[o + 2 * H + m - 1] = make_float2(-sn, -sn);
+    }
+  }
+  return cudaMemcpyToSymbol(c_prime_pairs, pp, sizeof(pp));
 }
 
 // W_N^J for the forward (exp(-2 pi i J/N)) or inverse (exp(+...)) sign.
@@ -152,35 +172,40 @@ __device__ __forceinline__ void bfly5(float2 &x0, float2 &x1, float2 &x2, float2
   x3 = csub_mi<INV>(p2, q2);
 }
 
-// 11-point DFT from the symmetric pairs a_j = x_j + x_{11-j}, b_j = x_j -
-// x_{11-j} (j = 1 .. 5): X_k = x_0 + sum_j a_j cos(2 pi jk/11) -+ i sum_j b_j
-// sin(2 pi jk/11), X_{11-k} the other sign, k = 1 .. 5; jk mod 11 folded
-// onto 1 .. 5 with the sine's sign.
-template <bool INV> __device__ __forceinline__ void bfly11(float2 (&x)[11]) {
-  float2 a[6], b[6];
+// P-point DFT for an odd prime P from the symmetric pairs a_j = x_j +
+// x_{P-j}, b_j = x_j - x_{P-j} (j = 1 .. H, H = (P - 1) / 2): X_k = x_0 +
+// sum_j a_j cos(2 pi jk/P) -+ i sum_j b_j sin(2 pi jk/P), X_{P-k} the other
+// sign, k = 1 .. H; jk mod P folded onto 1 .. H with the sine's sign.
+template <int P, bool INV> __device__ __forceinline__ void bfly_prime(float2 (&x)[P]) {
+  constexpr int H = (P - 1) / 2, O = prime_off(P);
+  static_assert(O >= 0, "prime not tabulated");
+  float2 a[H + 1], b[H + 1];
 #pragma unroll
-  for (int j = 1; j <= 5; ++j) {
-    a[j] = cadd(x[j], x[11 - j]);
-    b[j] = csub(x[j], x[11 - j]);
+  for (int j = 1; j <= H; ++j) {
+    a[j] = cadd(x[j], x[P - j]);
+    b[j] = csub(x[j], x[P - j]);
   }
-  float2 y[11];
-  y[0] = cadd(x[0], cadd(cadd(a[1], a[2]), cadd(cadd(a[3], a[4]), a[5])));
+  float2 y[P];
+  float2 sa = a[1];
 #pragma unroll
-  for (int k = 1; k <= 5; ++k) {
+  for (int j = 2; j <= H; ++j) sa = cadd(sa, a[j]);
+  y[0] = cadd(x[0], sa);
+#pragma unroll
+  for (int k = 1; k <= H; ++k) {
     float2 p = x[0], q = make_float2(0.f, 0.f);
 #pragma unroll
-    for (int j = 1; j <= 5; ++j) {
-      const int m = (j * k) % 11;
-      const int f = m <= 5 ? m : 11 - m;                       // cos(2 pi m/11) = cos(2 pi f/11)
-      const int si = m <= 5 ? 12 + f - 1 : 17 + f - 1;         // sin(2 pi m/11) = +-sin(2 pi f/11)
-      p = __ffma2_rn(c_bfly_pairs[7 + f - 1], a[j], p);
-      q = j == 1 ? __fmul2_rn(c_bfly_pairs[si], b[j]) : __ffma2_rn(c_bfly_pairs[si], b[j], q);
+    for (int j = 1; j <= H; ++j) {
+      const int m = (j * k) % P;
+      const int f = m <= H ? m : P - m;                      // cos(2 pi m/P) = cos(2 pi f/P)
+      const int si = m <= H ? O + H + f - 1 : O + 2 * H + f - 1;   // +-sin(2 pi f/P)
+      p = __ffma2_rn(c_prime_pairs[O + f - 1], a[j], p);
+      q = j == 1 ? __fmul2_rn(c_prime_pairs[si], b[j]) : __ffma2_rn(c_prime_pairs[si], b[j], q);
     }
     y[k] = cadd_mi<INV>(p, q);
-    y[11 - k] = csub_mi<INV>(p, q);
+    y[P - k] = csub_mi<INV>(p, q);
   }
 #pragma unroll
-  for (int k = 0; k < 11; ++k) x[k] = y[k];
+  for (int k = 0; k < P; ++k) x[k] = y[k];
 }
 
 // ---- generic in-register DFT: X[k] = sum_n x[n] W_N^{nk}, natural order ----
@@ -269,8 +294,17 @@ template <bool INV> struct RegDFT<3, INV, 0> {
 template <bool INV> struct RegDFT<4, INV, 0> {
   static __device__ __forceinline__ void run(float2 (&x)[4]) { bfly4<INV>(x[0], x[1], x[2], x[3]); }
 };
+template <bool INV> struct RegDFT<7, INV, 0> {
+  static __device__ __forceinline__ void run(float2 (&x)[7]) { bfly_prime<7, INV>(x); }
+};
 template <bool INV> struct RegDFT<11, INV, 0> {
-  static __device__ __forceinline__ void run(float2 (&x)[11]) { bfly11<INV>(x); }
+  static __device__ __forceinline__ void run(float2 (&x)[11]) { bfly_prime<11, INV>(x); }
+};
+template <bool INV> struct RegDFT<13, INV, 0> {
+  static __device__ __forceinline__ void run(float2 (&x)[13]) { bfly_prime<13, INV>(x); }
+};
+template <bool INV> struct RegDFT<17, INV, 0> {
+  static __device__ __forceinline__ void run(float2 (&x)[17]) { bfly_prime<17, INV>(x); }
 };
 template <bool INV> struct RegDFT<5, INV, 0> {
   static __device__ __forceinline__ void run(float2 (&x)[5]) { bfly5<INV>(x[0], x[1], x[2], x[3], x[4]); }

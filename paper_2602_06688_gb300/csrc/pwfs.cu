@@ -943,7 +943,10 @@ int pwfs_autotune(specula_ctx *ctx, PwfsPlan *p, const float *amp, const float *
         if (c > std::max(total, 1) && c != 1) break;
         if ((size_t)c * item > max_ws_bytes && c != 1) break;
       }
-      for (int ka = 1; ka <= (passes == 4 ? 1 : 2); ++ka) {
+      // ka sets the row pass's grid depth (slots per warp): values that fill
+      // whole waves of CTAs can win (the ELT frame: ka 5, 300 CTAs on 304
+      // slots), so the search goes to 8
+      for (int ka = 1; ka <= (passes == 4 ? 1 : 8); ++ka) {
         if (ka > c) break;
         if ((status = pwfs_set_tiles(p, passes == 4 ? c * p->nc : c, ka, passes))) goto done;
         if ((status = pwfs_run(ctx, p, amp, phase, n_batch, det, st))) goto done;   // warm-up

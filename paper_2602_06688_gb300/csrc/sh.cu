@@ -64,19 +64,22 @@ __global__ void __launch_bounds__(kShWarps * 32) k_sh_spots(
     for (int k = 0; k < NF; ++k) xs[k * XS + lane] = v[k];
   }
   __syncwarp();
-  // columns: lane k < NF
+  // columns: lane k < NF (spots wider than a warp: columns lane, lane + 32, ...)
+  constexpr float inv = 1.0f / (float)(NF * NF);
+#pragma unroll 1
+  for (int k = lane; k < (NF > 32 ? NF : 32); k += 32) {
 #pragma unroll
-  for (int n = 0; n < NF; ++n) v[n] = make_float2(0.f, 0.f);
-  if (lane < NF) {
+    for (int n = 0; n < NF; ++n) v[n] = make_float2(0.f, 0.f);
+    if (k < NF) {
 #pragma unroll
-    for (int r = 0; r < SP; ++r) v[OFF + r] = xs[lane * XS + r];
-  }
-  RegDFT<NF, false>::run(v);
-  if (ok && lane < NF) {
-    constexpr float inv = 1.0f / (float)(NF * NF);
-    float *dst = spots + (size_t)task * NF * NF + lane;
+      for (int r = 0; r < SP; ++r) v[OFF + r] = xs[k * XS + r];
+    }
+    RegDFT<NF, false>::run(v);
+    if (ok && k < NF) {
+      float *dst = spots + (size_t)task * NF * NF + k;
 #pragma unroll
-    for (int q = 0; q < NF; ++q) dst[q * NF] = (v[q].x * v[q].x + v[q].y * v[q].y) * inv;
+      for (int q = 0; q < NF; ++q) dst[q * NF] = (v[q].x * v[q].x + v[q].y * v[q].y) * inv;
+    }
   }
 }
 
@@ -131,6 +134,16 @@ int sh_run(specula_ctx *ctx, ShPlan *p, const float *amp, const float *phase, in
   else if (p->fft_n == 16 && p->sub_pix == 8)
     SPECULA_LAUNCH(ctx, SPECULA_K_SH, st,
                    k_sh_spots<16, 8><<<grid, kShWarps * 32, 0, st>>>(
+                       amp, phase, valid, p->pre.as<float2>(), p->n_pix, p->n_sub, nv, n_batch,
+                       phase_scale, spots));
+  else if (p->fft_n == 56 && p->sub_pix == 8)   // Tab. 2's SCAO SH spots (56 = 8 x 7)
+    SPECULA_LAUNCH(ctx, SPECULA_K_SH, st,
+                   k_sh_spots<56, 8><<<grid, kShWarps * 32, 0, st>>>(
+                       amp, phase, valid, p->pre.as<float2>(), p->n_pix, p->n_sub, nv, n_batch,
+                       phase_scale, spots));
+  else if (p->fft_n == 68 && p->sub_pix == 4)   // Tab. 2's ERIS spots (68 = 4 x 17)
+    SPECULA_LAUNCH(ctx, SPECULA_K_SH, st,
+                   k_sh_spots<68, 4><<<grid, kShWarps * 32, 0, st>>>(
                        amp, phase, valid, p->pre.as<float2>(), p->n_pix, p->n_sub, nv, n_batch,
                        phase_scale, spots));
   else

@@ -17,7 +17,10 @@ def env():
     close_checked(sp, ctx)
 
 
-@pytest.mark.parametrize("n_sub,sub_pix,fft_n,obsc,nb", [(10, 8, 16, 0.2, 2), (68, 12, 24, 0.28, 1)])
+# the last two: Sect. 6 Tab. 2's SCAO SH (20 x 20 lenslets of 8 px, 56^2
+# spots) and ERIS (40 x 40 of 4 px, 68^2 spots), transforms wider than a warp
+@pytest.mark.parametrize("n_sub,sub_pix,fft_n,obsc,nb", [(10, 8, 16, 0.2, 2), (68, 12, 24, 0.28, 1),
+                                                         (20, 8, 56, 0.14, 2), (40, 4, 68, 0.14, 1)])
 def test_sh_spots_and_slopes(env, n_sub, sub_pix, fft_n, obsc, nb):
     torch, sp, ctx = env
     n_pix = n_sub * sub_pix
