@@ -634,13 +634,21 @@ int specula_sh_image(specula_ctx *ctx, const specula_pupil_desc *pupil,
  * dropped (a field stop per subaperture).  ratio[i] = 1 reproduces
  * specula_sh_image.  ratio, weight: n_lambda host doubles (1 <= n_lambda
  * <= 64, ratio > 0).  spots_dev as specula_sh_image (the plan's imaged
- * range).  Uses a context workspace of one wavelength's spots, grown on the
- * first call of a new size (synchronising the stream; refused with
- * SPECULA_EUNSUPPORTED inside stream capture).  fft_n 24 or 16. */
+ * range).  Uses a context workspace of one wavelength's spots: reserve it
+ * with specula_sh_poly_reserve (set-up call) so that per-frame calls never
+ * allocate; a call that finds it too small grows it (synchronising the
+ * stream), or returns SPECULA_EUNSUPPORTED inside stream capture.  fft_n 24
+ * or 16. */
 int specula_sh_image_poly(specula_ctx *ctx, const specula_pupil_desc *pupil,
                           const specula_sh_desc *sh, int32_t n_lambda, const double *ratio,
                           const double *weight, const float *amp_dev, const float *phase_dev,
                           int32_t n_batch, float *spots_dev, void *stream);
+
+/* Set-up call (may allocate; synchronises the device when it grows): size
+ * the polychromatic SH workspace for batches up to max_batch of this plan's
+ * valid subapertures.  SPECULA_ENOPLAN without a plan. */
+int specula_sh_poly_reserve(specula_ctx *ctx, const specula_pupil_desc *pupil,
+                            const specula_sh_desc *sh, int32_t max_batch);
 
 /* Imaged subapertures of a Shack-Hartmann plan (set-up call; synchronises):
  * after this call specula_sh_image computes the spots of the valid
@@ -683,11 +691,17 @@ int specula_slopes(specula_ctx *ctx, const specula_slopec_desc *slopec,
  * workspace and one tensor-core GEMM forms xh Rh^T + xh Rl^T + xl Rh^T
  * (BF16X2) or (xh + xl) Rh^T (BF16).  That workspace grows on the first
  * batched call of a new size, which synchronises the stream; inside stream
- * capture a call that would grow it returns SPECULA_EUNSUPPORTED (make one
- * call of the largest batch before capturing). */
+ * capture a call that would grow it returns SPECULA_EUNSUPPORTED.
+ * specula_recon_reserve sizes it in advance, so per-frame calls then never
+ * allocate. */
 int specula_recon(specula_ctx *ctx, const specula_recon_desc *rec,
                   const float *slopes_dev, int32_t n_batch, float *modes_dev,
                   void *stream);
+
+/* Set-up call (may allocate; synchronises the device when it grows): size
+ * the context workspace of the batched bf16 products of rec for every batch
+ * up to max_batch (no-op for SPECULA_PREC_FP32 and batches below 32). */
+int specula_recon_reserve(specula_ctx *ctx, const specula_recon_desc *rec, int32_t max_batch);
 
 /* Reduced-precision copies of a float32 R: BF16 writes hi = bf16(R) (round to
  * nearest even); BF16X2 also writes lo = bf16(R - float(hi)).  hi_dev / lo_dev

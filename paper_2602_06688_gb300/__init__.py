@@ -664,6 +664,20 @@ def specula_infscreen_plan(layers, source, pupil, side, margin, t, lo, max_moves
             list(lo_a[:2 * n]))
 
 
+def specula_recon_reserve(ctx, rec, max_batch):
+    """Size the workspace of rec's batched bf16 products for batches up to
+    max_batch (set-up call)."""
+    _abi.check(lib().specula_recon_reserve(ctx.handle, C.byref(rec), int(max_batch)),
+               "specula_recon_reserve")
+
+
+def specula_sh_poly_reserve(ctx, pupil, sh, max_batch):
+    """Size the polychromatic SH workspace for batches up to max_batch (set-up
+    call)."""
+    _abi.check(lib().specula_sh_poly_reserve(ctx.handle, C.byref(pupil), C.byref(sh),
+                                             int(max_batch)), "specula_sh_poly_reserve")
+
+
 def specula_recon_convert(ctx, R, precision, hi, lo=None, stream=None):
     import torch
     nm, ns = R.shape

@@ -144,6 +144,8 @@ SIGNATURES = {
     "specula_slopes": (C.c_int, [vp, P(SlopecDesc), vp, vp, i32, vp, vp]),
     "specula_recon": (C.c_int, [vp, P(ReconDesc), vp, i32, vp, vp]),
     "specula_recon_convert": (C.c_int, [vp, i32, i32, vp, i32, vp, vp, vp]),
+    "specula_recon_reserve": (C.c_int, [vp, P(ReconDesc), i32]),
+    "specula_sh_poly_reserve": (C.c_int, [vp, P(PupilDesc), P(ShDesc), i32]),
     "specula_gemm_bf16": (C.c_int, [vp, vp, vp, i32, i32, i32, vp, i32, vp, vp]),
     "specula_gemm_tf32": (C.c_int, [vp, vp, vp, i32, i32, i32, vp, i32, vp, vp]),
     "specula_col_stats": (C.c_int, [vp, vp, i32, i32, vp, vp, vp]),

@@ -712,6 +712,20 @@ extern "C" int specula_sh_image(specula_ctx *ctx, const specula_pupil_desc *pupi
   return sh_run(ctx, p, amp_dev, phase_dev, n_batch, spots_dev, (cudaStream_t)stream);
 }
 
+extern "C" int specula_sh_poly_reserve(specula_ctx *ctx, const specula_pupil_desc *pupil,
+                                       const specula_sh_desc *sh, int32_t max_batch) {
+  if (!ctx || max_batch < 0) return SPECULA_EINVAL;
+  int s = check_sh(pupil, sh);
+  if (s) return s;
+  ShPlan *p = sh_plan_find(ctx, pupil, sh);
+  if (!p) return SPECULA_ENOPLAN;
+  const size_t need = (size_t)p->n_valid * max_batch * sh->fft_n * sh->fft_n * sizeof(float);
+  if (ctx->sh_poly_ws.bytes >= need) return SPECULA_OK;
+  SPECULA_CK(cudaSetDevice(ctx->device));
+  SPECULA_CK(cudaDeviceSynchronize());   // calls in flight may use the old workspace
+  return ctx->sh_poly_ws.alloc(need);
+}
+
 extern "C" int specula_sh_image_poly(specula_ctx *ctx, const specula_pupil_desc *pupil,
                                      const specula_sh_desc *sh, int32_t n_lambda,
                                      const double *ratio, const double *weight,

@@ -211,33 +211,52 @@ __global__ void k_convert_bf16(const float *__restrict__ R, uint16_t *__restrict
 // matrix's own rounding only), float32 accumulation.
 constexpr int kGemmBatch = 32;
 
+// K slices of the batched product: enough to fill the SMs, and at most
+// kMaxKb K blocks of 64 per accumulator: the tensor cores' float32
+// accumulation loses precision over long runs (relative error 6.8e-5 in one
+// 40k-long accumulation of 4000 x 13344 x 3 products, 1.1e-5 in slices of 70
+// blocks); the slices are summed in float32 on the CUDA cores
+static int recon_splits(const specula_recon_desc *rec, int nb, int sms) {
+  constexpr int kMaxKb = 128;
+  const bool split = rec->precision == SPECULA_PREC_BF16X2;
+  const int tiles = ((nb + 127) / 128) * ((rec->n_modes + 255) / 256);
+  const int kb = (split ? 3 : 2) * ((rec->n_slopes + 63) / 64);
+  return std::max(std::min(16, (kb + kMaxKb - 1) / kMaxKb),
+                  std::max(1, std::min(16, (sms + tiles / 2) / std::max(tiles, 1))));
+}
+
+// workspace bytes of a batch of nb: the slopes' two bf16 halves (256-byte
+// aligned) and the split-K partials
+static size_t recon_ws_bytes(const specula_recon_desc *rec, int nb, int sms, size_t *xb_out) {
+  const int splits = recon_splits(rec, nb, sms);
+  const size_t xb = ((size_t)nb * rec->n_slopes * 2 + 255) / 256 * 256;
+  if (xb_out) *xb_out = xb;
+  return 2 * xb + (splits > 1 ? (size_t)splits * nb * rec->n_modes * 4 : 0);
+}
+
+static int recon_sms(int *sms) {
+  int dev = 0;
+  SPECULA_CK(cudaGetDevice(&dev));
+  SPECULA_CK(cudaDeviceGetAttribute(sms, cudaDevAttrMultiProcessorCount, dev));
+  return SPECULA_OK;
+}
+
 static int recon_gemm(specula_ctx *ctx, const specula_recon_desc *rec, const float *X, int nb,
                       float *modes, cudaStream_t st) {
   const bool split = rec->precision == SPECULA_PREC_BF16X2;
   const int K = rec->n_slopes, N = rec->n_modes;
-  int dev = 0, sms = 0;
-  SPECULA_CK(cudaGetDevice(&dev));
-  SPECULA_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  const int tiles = ((nb + 127) / 128) * ((N + 255) / 256);
-  // enough K slices to fill the SMs, and at most kMaxKb K blocks of 64 per
-  // accumulator: the tensor cores' float32 accumulation loses precision over
-  // long runs (relative error 6.8e-5 in one 40k-long accumulation of
-  // 4000 x 13344 x 3 products, 1.1e-5 in slices of 70 blocks); the slices
-  // are summed in float32 on the CUDA cores
-  constexpr int kMaxKb = 128;
-  const int kb = (split ? 3 : 2) * ((K + 63) / 64);
-  const int splits = std::max(std::min(16, (kb + kMaxKb - 1) / kMaxKb),
-                              std::max(1, std::min(16, (sms + tiles / 2) / std::max(tiles, 1))));
+  int sms = 0, s = recon_sms(&sms);
+  if (s) return s;
+  const int splits = recon_splits(rec, nb, sms);
   const size_t nx = (size_t)nb * K;
-  const size_t xb = (nx * 2 + 255) / 256 * 256;   // one bf16 half, 256-byte aligned
-  const size_t need = 2 * xb + (splits > 1 ? (size_t)splits * nb * N * 4 : 0);
+  size_t xb = 0;
+  const size_t need = recon_ws_bytes(rec, nb, sms, &xb);
   if (ctx->recon_ws.bytes < need) {
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     SPECULA_CK(cudaStreamIsCapturing(st, &cs));
     if (cs != cudaStreamCaptureStatusNone) return SPECULA_EUNSUPPORTED;   // grow before capture
     SPECULA_CK(cudaStreamSynchronize(st));
-    const int s = ctx->recon_ws.alloc(need);
-    if (s) return s;
+    if ((s = ctx->recon_ws.alloc(need))) return s;
   }
   uint8_t *w = static_cast<uint8_t *>(ctx->recon_ws.p);
   uint16_t *xh = reinterpret_cast<uint16_t *>(w), *xl = reinterpret_cast<uint16_t *>(w + xb);
@@ -314,6 +333,23 @@ extern "C" int specula_recon(specula_ctx *ctx, const specula_recon_desc *rec,
     default:
       return SPECULA_EINVAL;
   }
+}
+
+extern "C" int specula_recon_reserve(specula_ctx *ctx, const specula_recon_desc *rec,
+                                     int32_t max_batch) {
+  if (!ctx || !rec || max_batch < 0 || rec->n_modes < 1 || rec->n_slopes < 1) return SPECULA_EINVAL;
+  if (rec->precision != SPECULA_PREC_BF16 && rec->precision != SPECULA_PREC_BF16X2)
+    return SPECULA_OK;   // the float32 products use no workspace
+  if (max_batch < kGemmBatch) return SPECULA_OK;
+  SPECULA_CK(cudaSetDevice(ctx->device));
+  int sms = 0, s = recon_sms(&sms);
+  if (s) return s;
+  size_t need = 0;
+  for (int nb = kGemmBatch; nb <= max_batch; ++nb)
+    need = std::max(need, recon_ws_bytes(rec, nb, sms, nullptr));
+  if (ctx->recon_ws.bytes >= need) return SPECULA_OK;
+  SPECULA_CK(cudaDeviceSynchronize());   // calls in flight may use the old workspace
+  return ctx->recon_ws.alloc(need);
 }
 
 extern "C" int specula_recon_convert(specula_ctx *ctx, int32_t n_modes, int32_t n_slopes,

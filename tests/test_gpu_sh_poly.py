@@ -80,3 +80,48 @@ def test_poly_arguments(env):
         sp.specula_sh_image_poly(ctx, sp.PupilDesc(64, 0.3, 0.28), sp.ShDesc(8, 8, 16), [1.0],
                                  [1.0], amp, torch.zeros(1, 64, 64, device="cuda"), out, nv)
     assert e.value.status == sp.ENOPLAN
+
+
+def test_reserved_workspaces_make_the_calls_capturable(env):
+    """After the set-up reserve calls, the batched bf16 reconstructor and the
+    polychromatic SH enqueue without allocating: both capture into a graph
+    whose replay equals the eager calls bit for bit."""
+    torch, sp, _ = env
+    ctx = sp.Context(0)
+    try:
+        n, n_sub, sub_pix, fft_n = 128, 16, 8, 16
+        pu, shd, nv, amp = _setup(torch, sp, ctx, n, n_sub, sub_pix, fft_n)
+        ph = torch.tensor(np.stack([kolmogorov_phase(n, 8.0 / n, 0.4, seed=s) for s in (1, 2)])
+                          .astype(np.float32), device="cuda")
+        nm, ns, nb = 300, 2 * nv, 64
+        g = torch.Generator(device="cuda").manual_seed(5)
+        R = torch.randn(nm, ns, device="cuda", generator=g) / ns ** 0.5
+        hi = torch.empty(nm, ns, dtype=torch.int16, device="cuda")
+        lo = torch.empty_like(hi)
+        sp.specula_recon_convert(ctx, R, sp.PREC_BF16X2, hi, lo)
+        rec = sp.recon_desc(nm, ns, sp.PREC_BF16X2, hi, lo)
+        X = torch.randn(nb, ns, device="cuda", generator=g)
+        sp.specula_recon_reserve(ctx, rec, nb)
+        sp.specula_sh_poly_reserve(ctx, pu, shd, 2)
+        ratios, weights = [1.2, 0.9], [0.5, 0.5]
+        st = torch.cuda.Stream()
+        m_g = torch.empty(nb, nm, device="cuda")
+        s_g = torch.empty(2, nv, fft_n, fft_n, device="cuda")
+        torch.cuda.synchronize()
+        sp.specula_graph_begin(ctx, st)
+        try:
+            sp.specula_recon(ctx, rec, X, m_g, stream=st)
+            sp.specula_sh_image_poly(ctx, pu, shd, ratios, weights, amp, ph, s_g, nv, stream=st)
+        finally:
+            graph = sp.specula_graph_end(ctx, st)
+        graph.launch(st)
+        torch.cuda.synchronize()
+        m_e = torch.empty_like(m_g)
+        s_e = torch.empty_like(s_g)
+        sp.specula_recon(ctx, rec, X, m_e)
+        sp.specula_sh_image_poly(ctx, pu, shd, ratios, weights, amp, ph, s_e, nv)
+        torch.cuda.synchronize()
+        assert torch.equal(m_g, m_e) and torch.equal(s_g, s_e)
+        graph.close()
+    finally:
+        close_checked(sp, ctx)
