@@ -651,13 +651,15 @@ def systems_leg(ctx, steps=50):
     # the paper's SOUL example geometry: 40 x 40 subapertures, images 48 px
     # apart on a 120 px detector (80 px pupil padded three times, 2 x 2 bins)
     ws = synth.workload("soul8m")
-    fs = PwfsFrame(ctx, ws)
+    fs = PwfsFrame(ctx, ws, autotune=True)
     gs = fs.capture(st)
     time_graph(gs, lambda k: fs.t_dev.fill_(ws.dt_s * k), 5)
     mss = time_graph(gs, lambda k: fs.t_dev.fill_(ws.dt_s * k), steps)
     out["soul8m"] = {"config": "8.2 m, 80 px pupil padded 3x (240^2 FFT), 16 mod points, "
                                "40x40 subaps, images 48 px apart on a 120 px detector, "
                                "%d modes, FP32" % fs.n_modes,
+                     "tiles": {"chunk": fs.tiles[0], "ka": fs.tiles[1], "passes": fs.tiles[2]}
+                     if fs.tiles else None,
                      "frames_per_s": steps / (sum(mss) / 1e3), "ms_per_step": sum(mss) / steps}
     gs.close()
     del fs
@@ -665,7 +667,7 @@ def systems_leg(ctx, steps=50):
     # (660^2 FFT, Tab. 2's 24 x 660 x 660), detector pixels of 5.5 x 5.5 grid
     # pixels (area-weighted rebinning in the column pass), 500 modes
     ws = synth.workload("soul220")
-    fs = PwfsFrame(ctx, ws)
+    fs = PwfsFrame(ctx, ws, autotune=True)
     gs = fs.capture(st)
     time_graph(gs, lambda k: fs.t_dev.fill_(ws.dt_s * k), 5)
     mss = time_graph(gs, lambda k: fs.t_dev.fill_(ws.dt_s * k), steps)
