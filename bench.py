@@ -753,13 +753,15 @@ def elt_calibrated_leg(ctx, fr, variants):
     res = cr.compare()
     out = {"calibration_s": t_cal, "n_modes": cr.n_modes, "rank": res.pop("rank"),
            "residual_rms_rad": {k: res[k] for k in ("no_correction", "fp32", "bf16x2", "bf16",
-                                                     "learned")},
+                                                     "learned", "learned_correction")},
            "test": {"n_test": res["n_test"], "phase_rms_rad": res["phase_rms_rad"]},
            "learned_train": res["learned_train"],
            "frames_per_s": {"fp32": variants.get("fp32", {}).get("frames_per_s"),
                             "bf16x2": variants.get("bf16x2", {}).get("frames_per_s"),
                             "bf16": variants.get("bf16", {}).get("frames_per_s"),
-                            "learned": variants.get("learned_mlp", {}).get("frames_per_s")}}
+                            "learned": variants.get("learned_mlp", {}).get("frames_per_s"),
+                            "learned_correction":
+                                variants.get("learned_mlp_correction", {}).get("frames_per_s")}}
     f = out["residual_rms_rad"]["fp32"]
     out["within_1pct_of_fp32"] = {k: abs(v - f) <= 0.01 * f
                                   for k, v in out["residual_rms_rad"].items()
@@ -1009,7 +1011,18 @@ def gpu_leg(args, ws, rank, local):
     variants["learned_mlp"] = {"frames_per_s": K / (sum(msl) / 1e3), "ms_per_step": sum(msl) / K,
                                "net": "%d-2048-2048-%d GELU, batch 1: bf16 weight rows streamed by k_mlp_gemv on CUDA cores (tcgen05 GEMMs serve batches above 4)"
                                       % (fr.n_slopes, fr.n_modes)}
+    # the network as a correction on top of the MVM (m = R s + f(s))
+    fr.use_learned(mlp, correction=True)
+    fr.graph.close()
+    fr.capture(st)
+    timed(3, W)
+    msc = timed(K, W)
+    variants["learned_mlp_correction"] = {
+        "frames_per_s": K / (sum(msc) / 1e3), "ms_per_step": sum(msc) / K,
+        "net": "FP32 MVM, then the same network by k_mlp_gemv, its output added to the modes"}
     fr.use_learned(None)
+    fr.graph.close()
+    fr.capture(st)
     mlp.close()
 
     # shifted-mask modulation (one forward transform per image, the mask moved

@@ -1,6 +1,7 @@
 """The ELT pyramid's calibrated reconstructors compared at equal wavefront
 accuracy: float32, split bf16 and bf16 MVMs of one calibrated R, and a
-learned network, by the residual wavefront they leave.
+learned network (alone, or as a correction on top of R), by the residual
+wavefront they leave.
 
 Calibration (ImCalibrator / RecCalibrator, App. A, Tab. 4) on the device:
 the Zernike modal basis (Kintner's recurrence), the push-pull interaction
@@ -171,9 +172,19 @@ class CalibratedRecon(MlpRegressor):
         # 1e-4 trains
         hist = self.fit(Xt, Tt, epochs=epochs, lr=lr, lr_final=lr_final,
                         per_column_targets=False, per_column_inputs=False)
-        del Xt, Tt
         out["learned"] = self.residual_rms(phases, self.predict(X))
         out["learned_train"] = {"pairs": n_train, "epochs": epochs, "lr": [lr, lr_final],
                                 "final_loss": hist[-1]}
+        # the network as a correction on top of R: m = R s + f(s), f trained on
+        # what the float32 R misses on the same pairs
+        Lt = torch.empty_like(Tt)
+        specula_recon(self.ctx, self.recs["fp32"], Xt, Lt)
+        hist_c = self.fit(Xt, Tt - Lt, epochs=epochs, lr=lr, lr_final=lr_final,
+                          per_column_targets=False, per_column_inputs=False)
+        del Xt, Tt, Lt
+        m_lin = torch.empty(n_test, self.n_modes, device="cuda")
+        specula_recon(self.ctx, self.recs["fp32"], X, m_lin)
+        out["learned_correction"] = self.residual_rms(phases, m_lin + self.predict(X))
+        out["learned_train"]["correction_final_loss"] = hist_c[-1]
         torch.cuda.synchronize()
         return out

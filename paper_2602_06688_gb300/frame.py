@@ -11,7 +11,8 @@ import synth
 from . import (PREC_BF16, PREC_BF16X2, PREC_FP32, SLOPES_PYR, SLOPES_PYR_MAPS, layer_desc,
                pupil_desc,
                pwfs_desc, recon_desc, slopec_desc, source_desc, specula_atmo_extract,
-               specula_ccd, specula_pupil_mask, specula_pupil_mask_host, specula_pwfs_image,
+               specula_ccd, specula_loop_integrate, specula_pupil_mask, specula_pupil_mask_host,
+               specula_pwfs_image,
                specula_pwfs_plan, specula_pyr_image_index_host, specula_recon,
                specula_recon_convert, specula_screen_generate, specula_slopes,
                specula_valid_subaps_host)
@@ -112,6 +113,7 @@ class PwfsFrame:
             R = seeded_reconstructor(self.n_modes, self.n_slopes, seed=7 + seed_offset)
         self.R = torch.tensor(np.asarray(R, dtype=np.float32), device=device)
         self.learned = None
+        self.learned_correction = False
         self.set_precision(precision)
         # reference slopes: a flat wavefront in the same geometry
         flat, fdet = torch.zeros(n, n, device=device), torch.empty(d, d, device=device)
@@ -205,14 +207,24 @@ class PwfsFrame:
                         self.noise.get("seed", 1), k, self.det,
                         frame_dev=self.frame_dev if t_dev is not None else None, stream=stream)
         specula_slopes(ctx, self.slopec, self.det, self.ref, self.slopes, stream=stream)
-        if self.learned is not None:
+        if self.learned is not None and not self.learned_correction:
             self.learned.infer(self.slopes.view(self.batch, -1), self.modes.view(self.batch, -1),
                                stream=stream)
         else:
             specula_recon(ctx, self.rec, self.slopes, self.modes, stream=stream)
+            if self.learned is not None:
+                # m = R s + f(s): the network's correction added by the
+                # library's integrator update (gain 1, no leak: an exact sum)
+                self.learned.infer(self.slopes.view(self.batch, -1), self.dmodes, stream=stream)
+                specula_loop_integrate(ctx, 1.0, 0.0, self.dmodes.view(-1),
+                                       self.modes.view(-1), stream=stream)
         return self.modes
 
-    def use_learned(self, mlp):
+    def use_learned(self, mlp, correction=False):
         """Reconstruct with a learned network (an MLP handle sized n_slopes ->
-        ... -> n_modes) instead of the linear MVM; None restores the MVM."""
+        ... -> n_modes) instead of the linear MVM, or with correction=True as
+        a correction on top of it (m = R s + f(s)); None restores the MVM."""
         self.learned = mlp
+        self.learned_correction = bool(correction) and mlp is not None
+        if self.learned_correction:
+            self.dmodes = self.torch.empty(self.batch, self.n_modes, device=self.modes.device)
