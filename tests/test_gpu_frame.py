@@ -133,3 +133,43 @@ def test_elt_frame_in_the_bench_configuration(env):
     mag = np.abs(R) @ np.abs(sl)
     assert np.all(np.abs(fr.modes.cpu().numpy() - recon.mvm(R, sl)) <= 1e-5 * mag)
     fr.graph.close()
+
+
+@pytest.mark.parametrize("correction", [False, True])
+def test_learned_reconstructor_in_the_frame(env, correction):
+    """The frame with a network in place of the MVM, or as a correction on
+    top of it (m = R s + f(s)): its modes equal the network (plus the MVM)
+    applied to the frame's own slopes by separate library calls, bit for bit,
+    eager and replayed from the frame's graph."""
+    torch, sp, ctx = env
+    from paper_2602_06688_gb300.frame import PwfsFrame
+    fr = PwfsFrame(ctx, synth.workload("pwfs8m_tiny"))
+    sizes = (fr.n_slopes, 128, 128, fr.n_modes)
+    mlp = sp.MLP(ctx, sizes, 8)
+    for l in range(3):
+        bnd = 1.0 / np.sqrt(sizes[l])
+        mlp.set_layer(l, synth.uniform_draws(40 + 2 * l, (sizes[l + 1], sizes[l]), -bnd, bnd),
+                      synth.uniform_draws(41 + 2 * l, (sizes[l + 1],), -bnd, bnd))
+    fr.use_learned(mlp, correction=correction)
+    st = torch.cuda.Stream()
+    fr.capture(st)
+    for t in (0.0, 0.023):
+        fr.frame(t)
+        torch.cuda.synchronize()
+        eager = fr.modes.clone()
+        f = torch.empty(1, fr.n_modes, device="cuda")
+        mlp.infer(fr.slopes.view(1, -1), f)
+        ref = f.view(-1).clone()
+        if correction:
+            lin = torch.empty(fr.n_modes, device="cuda")
+            sp.specula_recon(ctx, fr.rec, fr.slopes, lin)
+            torch.cuda.synchronize()
+            ref = lin + f.view(-1)
+        torch.cuda.synchronize()
+        assert torch.equal(eager.view(-1), ref)
+        fr.modes.zero_()
+        fr.replay(t, st)
+        torch.cuda.synchronize()
+        assert torch.equal(fr.modes, eager)
+    fr.use_learned(None)
+    mlp.close()
