@@ -185,7 +185,14 @@ class PwfsFrame:
         """Enqueue one frame at time t (or *t_dev) on the current stream; with
         batch > 1 the frames at t, t + dt, ... (t_dev: one device time per
         frame)."""
+        self.front(t, t_dev=t_dev, stream=stream)
+        return self.reconstruct(stream=stream)
+
+    def front(self, t, t_dev=None, stream=None, slopes=None):
+        """The frame up to its slopes (extraction, image, detector noise,
+        slopes) into `slopes` (default self.slopes)."""
         ctx = self.ctx
+        slopes = self.slopes if slopes is None else slopes
         if self.inf is not None and t_dev is None:
             self.inf.advance(t, stream=stream)
         if self.batch == 1:
@@ -206,19 +213,27 @@ class PwfsFrame:
             specula_ccd(ctx, self.det, self.noise_scale, self.noise.get("ron", 0.0),
                         self.noise.get("seed", 1), k, self.det,
                         frame_dev=self.frame_dev if t_dev is not None else None, stream=stream)
-        specula_slopes(ctx, self.slopec, self.det, self.ref, self.slopes, stream=stream)
+        specula_slopes(ctx, self.slopec, self.det, self.ref, slopes, stream=stream)
+        return slopes
+
+    def reconstruct(self, slopes=None, modes=None, stream=None):
+        """Modes of `slopes` (default self.slopes) into `modes` (default
+        self.modes): the MVM, the network in its place, or R s + f(s)."""
+        ctx = self.ctx
+        slopes = self.slopes if slopes is None else slopes
+        modes = self.modes if modes is None else modes
         if self.learned is not None and not self.learned_correction:
-            self.learned.infer(self.slopes.view(self.batch, -1), self.modes.view(self.batch, -1),
+            self.learned.infer(slopes.view(self.batch, -1), modes.view(self.batch, -1),
                                stream=stream)
         else:
-            specula_recon(ctx, self.rec, self.slopes, self.modes, stream=stream)
+            specula_recon(ctx, self.rec, slopes, modes, stream=stream)
             if self.learned is not None:
                 # m = R s + f(s): the network's correction added by the
                 # library's integrator update (gain 1, no leak: an exact sum)
-                self.learned.infer(self.slopes.view(self.batch, -1), self.dmodes, stream=stream)
-                specula_loop_integrate(ctx, 1.0, 0.0, self.dmodes.view(-1),
-                                       self.modes.view(-1), stream=stream)
-        return self.modes
+                self.learned.infer(slopes.view(self.batch, -1), self.dmodes, stream=stream)
+                specula_loop_integrate(ctx, 1.0, 0.0, self.dmodes.view(-1), modes.view(-1),
+                                       stream=stream)
+        return modes
 
     def use_learned(self, mlp, correction=False):
         """Reconstruct with a learned network (an MLP handle sized n_slopes ->
