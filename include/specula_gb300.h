@@ -93,9 +93,10 @@ typedef struct {
  * area-weighted rebinning, each detector pixel collecting the overlapped
  * area of every grid pixel, the intensity constant over a grid pixel.
  * Supported: pad 2-4 with N one of 64, 128, 240, 320, 660 (pad 3 or 4),
- * 960, pup_dist_px + n_pix <= N (the images inside the grid), and column
- * tiles of whole detector pixels within 352 threads (SPECULA_EUNSUPPORTED
- * else).  With pad 2 and pup_dist_px = n_pix the four images tile the grid
+ * 960, 1600 (pad 3 or 4: the ANDES grid of Sect. 6, Tab. 2, 400 px at pad
+ * 4), pup_dist_px + n_pix <= N (the images inside the grid), and column
+ * tiles of whole detector pixels within 352 threads (256 at N = 1600;
+ * SPECULA_EUNSUPPORTED else).  With pad 2 and pup_dist_px = n_pix the four images tile the grid
  * (quadrant slopes); otherwise read the slopes with SPECULA_SLOPES_PYR_MAPS.
  * The three-pass, shifted-mask, paired and DFT-as-GEMM forms need pad 2 and
  * a whole b. */
@@ -482,7 +483,7 @@ int specula_atmo_extract_noalloc(int32_t n_layers, const specula_layer_desc *lay
 /* Build (or reuse) the tables and workspace of a pyramid geometry: modulation
  * tilt tables, pyramid-mask tables and FFT twiddles, computed in float64 on
  * the host and rounded once to float32.  May allocate.  Supported FFT sides
- * N = pad * n_pix: 64, 128, 240, 320, 660, 960. */
+ * N = pad * n_pix: 64, 128, 240, 320, 660, 960, 1600. */
 int specula_pwfs_plan(specula_ctx *ctx, const specula_pupil_desc *pupil,
                       const specula_pwfs_desc *pwfs);
 

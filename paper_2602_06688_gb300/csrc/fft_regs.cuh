@@ -49,7 +49,7 @@ template <bool INV> __device__ __forceinline__ float2 mul_mi(float2 a) {
 
 // ---- codelet twiddle table -------------------------------------------------
 // Sizes for which W_n^j is tabulated; offsets are compile-time.
-constexpr int kCodeletSizes[] = {3, 5, 6, 8, 10, 12, 15, 16, 20, 24, 30, 32, 40, 48, 60, 64};
+constexpr int kCodeletSizes[] = {3, 5, 6, 8, 10, 12, 15, 16, 20, 24, 30, 32, 40, 48, 60, 64, 25};
 constexpr int kNumCodeletSizes = sizeof(kCodeletSizes) / sizeof(int);
 constexpr int codelet_offset(int n, int i = 0, int acc = 0) {
   return i >= kNumCodeletSizes ? -1

@@ -59,6 +59,40 @@ __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
+// The N1-point middle stage of a wide split (N2 > 32): lane k2 = lane + 32 t
+// (t < NT2) takes column k2 of the exchange xa (xa[k2 S1 + n1]), applies the
+// forward N1-point DFT, the mask factor of frequency N2 k1 + k2, the inverse
+// N1-point DFT and the twiddle of the swapped split, and writes
+// xo[k1 S2 + k2]; xo and xa do not overlap.
+template <int N1, int N2>
+__device__ __forceinline__ void wide_mid(const float2 *xa, float2 *xo,
+                                         const float2 *__restrict__ mask,
+                                         const float2 *__restrict__ twB, int lane) {
+  using S = Split<N1, N2>;
+#pragma unroll 1
+  for (int t = 0; t < S::NT2; ++t) {
+    const int k2 = lane + 32 * t;
+    float2 r2[N1];
+    if (k2 < N2) {
+#pragma unroll
+      for (int n1 = 0; n1 < N1; ++n1) r2[n1] = xa[k2 * S::S1 + n1];
+    } else {
+#pragma unroll
+      for (int n1 = 0; n1 < N1; ++n1) r2[n1] = make_float2(0.f, 0.f);
+    }
+    RegDFT<N1, false>::run(r2);
+    if (k2 < N2) {
+#pragma unroll
+      for (int k1 = 0; k1 < N1; ++k1) r2[k1] = cmul(r2[k1], __ldg(mask + N2 * k1 + k2));
+    }
+    RegDFT<N1, true>::run(r2);
+    if (k2 < N2) {
+#pragma unroll
+      for (int k1 = 0; k1 < N1; ++k1) xo[k1 * S::S2 + k2] = cmul(r2[k1], __ldg(twB + k1 * N2 + k2));
+    }
+  }
+}
+
 // --------------------------------------------------------------------------
 // F: field of the batch elements b0 .. b0 + gridDim.y - 1 into slots b % nbw.
 __global__ void __launch_bounds__(256) k_field(const float *__restrict__ amp,
@@ -313,7 +347,8 @@ __global__ void __launch_bounds__(256, 2) k_rows_inv_part(
 
 template <int N1, int N2> struct RowFiltCfg {
   using S = Split<N1, N2>;
-  static constexpr int XBF = N2 * S::S1 > N1 * S::S2 ? N2 * S::S1 : N1 * S::S2;
+  static constexpr int XBF =
+      S::WIDE ? S::XW : (N2 * S::S1 > N1 * S::S2 ? N2 * S::S1 : N1 * S::S2);
 };
 
 // Points m and n_mod - m share cos(theta), hence the x factor of the tilt;
@@ -326,7 +361,7 @@ template <int N1, int N2> struct RowFiltCfg {
 // registers whose padded index falls in the pupil); otherwise the pad-2
 // layout, where the pupil is exactly registers N2/4 .. 3 N2/4 of every lane.
 template <int N1, int N2, bool GEN = false>
-__global__ void __launch_bounds__(256, 2) k_rowfilt(
+__global__ void __launch_bounds__(256, Split<N1, N2>::WIDE ? 1 : 2) k_rowfilt(
     const float2 *__restrict__ field, const float2 *__restrict__ gx,
     const float2 *__restrict__ twA, const float2 *__restrict__ twB,
     const float2 *__restrict__ mask, float2 *__restrict__ rows_out, int n_pix, int nc, int nbw,
@@ -381,31 +416,38 @@ __global__ void __launch_bounds__(256, 2) k_rowfilt(
       for (int k2 = 0; k2 < N2; ++k2) xb[k2 * S1 + lane] = cmulc(r[k2], __ldg(twA + k2 * N1 + lane));
     }
     __syncwarp();
-    float2 r2[N1];
-    if (lane < N2) {
-#pragma unroll
-      for (int n1 = 0; n1 < N1; ++n1) r2[n1] = xb[lane * S1 + n1];
+    float2 *x3 = xb;   // input of the last stage
+    if constexpr (S::WIDE) {
+      x3 = xb + N2 * S1;
+      wide_mid<N1, N2>(xb, x3, mask, twB, lane);
     } else {
+      float2 r2[N1];
+      if (lane < N2) {
 #pragma unroll
-      for (int n1 = 0; n1 < N1; ++n1) r2[n1] = make_float2(0.f, 0.f);
-    }
-    RegDFT<N1, false>::run(r2);
-    // x mask, then the inverse row transform (swapped split)
-    if (lane < N2) {
+        for (int n1 = 0; n1 < N1; ++n1) r2[n1] = xb[lane * S1 + n1];
+      } else {
 #pragma unroll
-      for (int k1 = 0; k1 < N1; ++k1) r2[k1] = cmul(r2[k1], __ldg(mask + N2 * k1 + lane));
-    }
-    RegDFT<N1, true>::run(r2);
-    __syncwarp();
-    if (lane < N2) {
+        for (int n1 = 0; n1 < N1; ++n1) r2[n1] = make_float2(0.f, 0.f);
+      }
+      RegDFT<N1, false>::run(r2);
+      // x mask, then the inverse row transform (swapped split)
+      if (lane < N2) {
 #pragma unroll
-      for (int k2 = 0; k2 < N1; ++k2) xb[k2 * S2 + lane] = cmul(r2[k2], __ldg(twB + k2 * N2 + lane));
+        for (int k1 = 0; k1 < N1; ++k1) r2[k1] = cmul(r2[k1], __ldg(mask + N2 * k1 + lane));
+      }
+      RegDFT<N1, true>::run(r2);
+      __syncwarp();
+      if (lane < N2) {
+#pragma unroll
+        for (int k2 = 0; k2 < N1; ++k2)
+          xb[k2 * S2 + lane] = cmul(r2[k2], __ldg(twB + k2 * N2 + lane));
+      }
     }
     __syncwarp();
     float2 r3[N2];
     if (lane < N1) {
 #pragma unroll
-      for (int n1 = 0; n1 < N2; ++n1) r3[n1] = xb[lane * S2 + n1];
+      for (int n1 = 0; n1 < N2; ++n1) r3[n1] = x3[lane * S2 + n1];
     } else {
 #pragma unroll
       for (int n1 = 0; n1 < N2; ++n1) r3[n1] = make_float2(0.f, 0.f);
@@ -428,7 +470,7 @@ __global__ void __launch_bounds__(256, 2) k_rowfilt(
 // buffer of a column, odd.
 template <int N1, int N2> struct ColFiltCfg {
   using S = Split<N1, N2>;
-  static constexpr int base = imax3(S::N, N2 * S::S1, N1 * S::S2);
+  static constexpr int base = S::WIDE ? S::XW : imax3(S::N, N2 * S::S1, N1 * S::S2);
   static int stride(int) { return base | 1; }
 };
 
@@ -437,7 +479,10 @@ template <int N1, int N2> struct ColFiltCfg {
 // per SM, the occupancy that 80 registers per thread gave them already:
 // 96 registers per thread, so the twiddle loads can be issued earlier.
 template <int N1, int N2, int MAXT = 256, bool GEN = false>
-__global__ void __launch_bounds__(MAXT, MAXT <= 160 ? 4 : (MAXT <= 256 ? 3 : 2)) k_colfilt_bin(
+__global__ void __launch_bounds__(MAXT, Split<N1, N2>::WIDE
+                                              ? 1
+                                              : (MAXT <= 160 ? 4 : (MAXT <= 256 ? 3 : 2)))
+    k_colfilt_bin(
     const float2 *__restrict__ rows_in, const float2 *__restrict__ gy,
     const float2 *__restrict__ twA, const float2 *__restrict__ twB,
     const float2 *__restrict__ mask, float *__restrict__ part, int n_pix, int fp, int fq,
@@ -505,30 +550,37 @@ __global__ void __launch_bounds__(MAXT, MAXT <= 160 ? 4 : (MAXT <= 256 ? 3 : 2))
     for (int k2 = 0; k2 < N2; ++k2) col[k2 * S1 + lane] = cmulc(r[k2], __ldg(twA + k2 * N1 + lane));
   }
   __syncwarp();
-  float2 r2[N1];
-  if (lane < N2) {
-#pragma unroll
-    for (int n1 = 0; n1 < N1; ++n1) r2[n1] = col[lane * S1 + n1];
+  float2 *x3 = col;   // input of the last stage
+  if constexpr (S::WIDE) {
+    x3 = col + N2 * S1;
+    wide_mid<N1, N2>(col, x3, mask, twB, lane);
   } else {
+    float2 r2[N1];
+    if (lane < N2) {
 #pragma unroll
-    for (int n1 = 0; n1 < N1; ++n1) r2[n1] = make_float2(0.f, 0.f);
-  }
-  RegDFT<N1, false>::run(r2);
-  if (lane < N2) {
+      for (int n1 = 0; n1 < N1; ++n1) r2[n1] = col[lane * S1 + n1];
+    } else {
 #pragma unroll
-    for (int k1 = 0; k1 < N1; ++k1) r2[k1] = cmul(r2[k1], __ldg(mask + N2 * k1 + lane));
-  }
-  RegDFT<N1, true>::run(r2);
-  __syncwarp();
-  if (lane < N2) {
+      for (int n1 = 0; n1 < N1; ++n1) r2[n1] = make_float2(0.f, 0.f);
+    }
+    RegDFT<N1, false>::run(r2);
+    if (lane < N2) {
 #pragma unroll
-    for (int k2 = 0; k2 < N1; ++k2) col[k2 * S2 + lane] = cmul(r2[k2], __ldg(twB + k2 * N2 + lane));
+      for (int k1 = 0; k1 < N1; ++k1) r2[k1] = cmul(r2[k1], __ldg(mask + N2 * k1 + lane));
+    }
+    RegDFT<N1, true>::run(r2);
+    __syncwarp();
+    if (lane < N2) {
+#pragma unroll
+      for (int k2 = 0; k2 < N1; ++k2)
+        col[k2 * S2 + lane] = cmul(r2[k2], __ldg(twB + k2 * N2 + lane));
+    }
   }
   __syncwarp();
   float2 r3[N2];
   if (lane < N1) {
 #pragma unroll
-    for (int n1 = 0; n1 < N2; ++n1) r3[n1] = col[lane * S2 + n1];
+    for (int n1 = 0; n1 < N2; ++n1) r3[n1] = x3[lane * S2 + n1];
   } else {
 #pragma unroll
     for (int n1 = 0; n1 < N2; ++n1) r3[n1] = make_float2(0.f, 0.f);
@@ -636,24 +688,30 @@ static int configure(PwfsPlan *p) {
     p->fp = S::N / a;
     p->fq = nd / a;
   }
-  const int bsz = p->fq == 1 ? p->fp : 0;   // whole bins only below the two-pass form
-  p->blockA = 256;
-  const int vpcA = 256 / S::G;
-  p->smemA = (size_t)(vpcA * S::XB) * sizeof(float2);
-  p->blockB = kColsTile * S::G;
-  p->smemB = ColsCfg<N1, N2, kColsTile>::smem;
-  const int thrC = ((bsz * S::G + 31) / 32) * 32;
-  if (thrC > 256) return SPECULA_EUNSUPPORTED;   // bin side too large for one CTA strip
-  p->blockC = bsz ? thrC : 0;                     // 0: no three-pass form (fractional bins)
-  const int nvecC = thrC / S::G;
-  p->smemC = (size_t)(nvecC * S::XB) * sizeof(float2);
-  if (p->smemA > 227 * 1024 || p->smemB > 227 * 1024 || p->smemC > 227 * 1024)
-    return SPECULA_EUNSUPPORTED;
   int s;
-  if ((s = ensure_dynamic_smem((const void *)k_rows_fwd<N1, N2>, p->smemA)) ||
-      (s = ensure_dynamic_smem((const void *)k_cols<N1, N2, kColsTile>, p->smemB)) ||
-      (s = ensure_dynamic_smem((const void *)k_rows_inv_part<N1, N2>, p->smemC)))
-    return s;
+  if constexpr (S::WIDE) {
+    // wide splits: the two-pass form only
+    p->blockA = p->blockB = p->blockC = 0;
+    p->smemA = p->smemB = p->smemC = 0;
+  } else {
+    const int bsz = p->fq == 1 ? p->fp : 0;   // whole bins only below the two-pass form
+    p->blockA = 256;
+    const int vpcA = 256 / S::G;
+    p->smemA = (size_t)(vpcA * S::XB) * sizeof(float2);
+    p->blockB = kColsTile * S::G;
+    p->smemB = ColsCfg<N1, N2, kColsTile>::smem;
+    const int thrC = ((bsz * S::G + 31) / 32) * 32;
+    if (thrC > 256) return SPECULA_EUNSUPPORTED;   // bin side too large for one CTA strip
+    p->blockC = bsz ? thrC : 0;                     // 0: no three-pass form (fractional bins)
+    const int nvecC = thrC / S::G;
+    p->smemC = (size_t)(nvecC * S::XB) * sizeof(float2);
+    if (p->smemA > 227 * 1024 || p->smemB > 227 * 1024 || p->smemC > 227 * 1024)
+      return SPECULA_EUNSUPPORTED;
+    if ((s = ensure_dynamic_smem((const void *)k_rows_fwd<N1, N2>, p->smemA)) ||
+        (s = ensure_dynamic_smem((const void *)k_cols<N1, N2, kColsTile>, p->smemB)) ||
+        (s = ensure_dynamic_smem((const void *)k_rows_inv_part<N1, N2>, p->smemC)))
+      return s;
+  }
   // two-pass form: column tiles of TC = k fp grid columns (k fq detector
   // columns, so every detector pixel lies in one CTA), k the largest divisor
   // of pad n_sub / fq with TC G <= 256 threads (352 where a detector pixel
@@ -661,7 +719,8 @@ static int configure(PwfsPlan *p) {
   p->two_ok = false;
   p->blockR = 256;
   p->smemR = (size_t)(256 / S::G) * RowFiltCfg<N1, N2>::XBF * sizeof(float2);
-  const int ndq = p->pad * p->n_sub / p->fq, maxt = p->fq == 1 ? 256 : 352;
+  const int ndq = p->pad * p->n_sub / p->fq;
+  const int maxt = p->fq == 1 || S::WIDE ? 256 : 352;
   int k = 0;
   for (int d = 1; d <= ndq; ++d)
     if (ndq % d == 0 && d * p->fp * S::G <= maxt) k = d;
@@ -673,15 +732,22 @@ static int configure(PwfsPlan *p) {
     const size_t win = (size_t)p->n_pix * ((tc + 1) & ~1);
     p->smemK = std::max((size_t)tc * p->csK, win) * sizeof(float2);
     if (p->smemK <= 227 * 1024 && S::N % tc == 0) {
-      if ((s = ensure_dynamic_smem((const void *)k_rowfilt<N1, N2>, p->smemR)) ||
-          (s = ensure_dynamic_smem((const void *)k_rowfilt<N1, N2, true>, p->smemR)) ||
-          (s = ensure_dynamic_smem((const void *)k_colfilt_bin<N1, N2>, p->smemK)) ||
-          (s = ensure_dynamic_smem((const void *)k_colfilt_bin<N1, N2, 160>, p->smemK)) ||
-          (s = ensure_dynamic_smem((const void *)k_colfilt_bin<N1, N2, 256, true>, p->smemK)) ||
-          (s = ensure_dynamic_smem((const void *)k_colfilt_bin<N1, N2, 160, true>, p->smemK)) ||
-          (s = ensure_dynamic_smem((const void *)k_colfilt_bin<N1, N2, 352>, p->smemK)) ||
-          (s = ensure_dynamic_smem((const void *)k_colfilt_bin<N1, N2, 352, true>, p->smemK)))
-        return s;
+      if constexpr (S::WIDE) {
+        // general-offset loads only (N2 % 4 != 0 or pad != 2), tiles of up to 256 threads
+        if ((s = ensure_dynamic_smem((const void *)k_rowfilt<N1, N2, true>, p->smemR)) ||
+            (s = ensure_dynamic_smem((const void *)k_colfilt_bin<N1, N2, 256, true>, p->smemK)))
+          return s;
+      } else {
+        if ((s = ensure_dynamic_smem((const void *)k_rowfilt<N1, N2>, p->smemR)) ||
+            (s = ensure_dynamic_smem((const void *)k_rowfilt<N1, N2, true>, p->smemR)) ||
+            (s = ensure_dynamic_smem((const void *)k_colfilt_bin<N1, N2>, p->smemK)) ||
+            (s = ensure_dynamic_smem((const void *)k_colfilt_bin<N1, N2, 160>, p->smemK)) ||
+            (s = ensure_dynamic_smem((const void *)k_colfilt_bin<N1, N2, 256, true>, p->smemK)) ||
+            (s = ensure_dynamic_smem((const void *)k_colfilt_bin<N1, N2, 160, true>, p->smemK)) ||
+            (s = ensure_dynamic_smem((const void *)k_colfilt_bin<N1, N2, 352>, p->smemK)) ||
+            (s = ensure_dynamic_smem((const void *)k_colfilt_bin<N1, N2, 352, true>, p->smemK)))
+          return s;
+      }
       p->two_ok = true;
     }
   }
@@ -730,24 +796,29 @@ static int run_split2(specula_ctx *ctx, PwfsPlan *p, const float *amp, const flo
                      p->rows.as<float2>(), p->gy.as<float2>(), p->twA.as<float2>(),            \
                      p->twB.as<float2>(), p->mask.as<float2>(), p->part.as<float>(), Np, p->fp, \
                      p->fq, scale, p->n_mod, nc, p->nbw, j0, p->csK, off, s0))
-    if (gen)
-      SPECULA_ROWFILT(true);
-    else
-      SPECULA_ROWFILT(false);
     dim3 gK(S::N / tc, 2 * nj);
     const bool k160 = S::G == 32 && p->blockK <= 160;
-    if (p->blockK > 256 && gen)     // tiles of fractional detector pixels
-      SPECULA_COLFILT(352, true);
-    else if (p->blockK > 256)
-      SPECULA_COLFILT(352, false);
-    else if (k160 && gen)
-      SPECULA_COLFILT(160, true);
-    else if (k160)
-      SPECULA_COLFILT(160, false);
-    else if (gen)
+    if constexpr (S::WIDE) {
+      SPECULA_ROWFILT(true);   // the plan refuses pad 2 for N2 % 4 != 0; wide tiles <= 256
       SPECULA_COLFILT(256, true);
-    else
-      SPECULA_COLFILT(256, false);
+    } else {
+      if (gen)
+        SPECULA_ROWFILT(true);
+      else
+        SPECULA_ROWFILT(false);
+      if (p->blockK > 256 && gen)     // tiles of fractional detector pixels
+        SPECULA_COLFILT(352, true);
+      else if (p->blockK > 256)
+        SPECULA_COLFILT(352, false);
+      else if (k160 && gen)
+        SPECULA_COLFILT(160, true);
+      else if (k160)
+        SPECULA_COLFILT(160, false);
+      else if (gen)
+        SPECULA_COLFILT(256, true);
+      else
+        SPECULA_COLFILT(256, false);
+    }
 #undef SPECULA_ROWFILT
 #undef SPECULA_COLFILT
     const int complete = (j0 + nj) / nc - 1;
@@ -768,55 +839,59 @@ static int run_split(specula_ctx *ctx, PwfsPlan *p, const float *amp, const floa
                      int n_batch, float *det, cudaStream_t st) {
   if (p->passes == 2) return run_split2<N1, N2>(ctx, p, amp, phase, n_batch, det, st);
   using S = Split<N1, N2>;
-  const int Np = p->n_pix;
-  const int bsz = Np / p->n_sub;
-  const int nd = S::N / bsz;
-  const int total = n_batch * p->n_mod;
-  const int vpcA = p->blockA / S::G;
-  const float scale = 1.0f / (float)p->n_mod;
-  int field_done = -1;   // highest batch element whose field is in its slot
-  int det_done = -1;     // highest batch element whose detector is written
-  for (int i0 = 0; i0 < total; i0 += p->chunk) {
-    const int ni = std::min(p->chunk, total - i0);
-    const int b0 = i0 / p->n_mod, b1 = (i0 + ni - 1) / p->n_mod;
-    const int fb = std::max(b0, field_done + 1);
-    if (fb <= b1) {
-      dim3 gF((Np * Np + 255) / 256, b1 - fb + 1);
-      SPECULA_LAUNCH(ctx, SPECULA_K_PWFS_FIELD, st,
-                     k_field<<<gF, 256, 0, st>>>(amp, phase, p->field.as<float2>(), Np * Np, fb,
-                                                 p->nbw, p->run_phase_scale));
-      field_done = b1;
+  if constexpr (S::WIDE) {
+    return SPECULA_EUNSUPPORTED;   // the three-pass kernels hold N2 <= 32
+  } else {
+    const int Np = p->n_pix;
+    const int bsz = Np / p->n_sub;
+    const int nd = S::N / bsz;
+    const int total = n_batch * p->n_mod;
+    const int vpcA = p->blockA / S::G;
+    const float scale = 1.0f / (float)p->n_mod;
+    int field_done = -1;   // highest batch element whose field is in its slot
+    int det_done = -1;     // highest batch element whose detector is written
+    for (int i0 = 0; i0 < total; i0 += p->chunk) {
+      const int ni = std::min(p->chunk, total - i0);
+      const int b0 = i0 / p->n_mod, b1 = (i0 + ni - 1) / p->n_mod;
+      const int fb = std::max(b0, field_done + 1);
+      if (fb <= b1) {
+        dim3 gF((Np * Np + 255) / 256, b1 - fb + 1);
+        SPECULA_LAUNCH(ctx, SPECULA_K_PWFS_FIELD, st,
+                       k_field<<<gF, 256, 0, st>>>(amp, phase, p->field.as<float2>(), Np * Np, fb,
+                                                   p->nbw, p->run_phase_scale));
+        field_done = b1;
+      }
+      dim3 gA((Np + vpcA - 1) / vpcA, (ni + p->ka - 1) / p->ka);
+      {
+        SPECULA_LAUNCH(ctx, SPECULA_K_PWFS_ROWS_FWD, st,
+                       k_rows_fwd<N1, N2><<<gA, p->blockA, p->smemA, st>>>(
+                           p->field.as<float2>(), p->gx.as<float2>(), p->gy.as<float2>(),
+                           p->twA.as<float2>(), p->rows.as<float2>(), Np, p->n_mod, p->nbw, i0,
+                           ni, p->ka));
+        dim3 gB(S::N / kColsTile, ni);
+        SPECULA_LAUNCH(ctx, SPECULA_K_PWFS_COLS, st,
+                       k_cols<N1, N2, kColsTile><<<gB, p->blockB, p->smemB, st>>>(
+                           p->rows.as<float2>(), p->cols.as<float2>(), p->twA.as<float2>(),
+                           p->twB.as<float2>(), p->mask.as<float2>(), Np));
+        dim3 gC(S::N / bsz, ni);
+        SPECULA_LAUNCH(ctx, SPECULA_K_PWFS_ROWS_INV, st,
+                       k_rows_inv_part<N1, N2><<<gC, p->blockC, p->smemC, st>>>(
+                           p->cols.as<float2>(), p->twA.as<float2>(), p->part.as<float>(), bsz,
+                           scale, p->n_mod, p->nbw, i0));
+      }
+      // batch elements whose last modulation point is in this chunk
+      const int complete = (i0 + ni) / p->n_mod - 1;
+      if (complete > det_done) {
+        dim3 gD((nd * nd + 255) / 256, complete - det_done);
+        SPECULA_LAUNCH(ctx, SPECULA_K_PWFS_BIN, st,
+                       k_bin_reduce<<<gD, 256, 0, st>>>(p->part.as<float>(), det, nd * nd,
+                                                        p->n_mod, p->nbw, det_done + 1,
+                                                        p->run_alpha, p->run_beta));
+        det_done = complete;
+      }
     }
-    dim3 gA((Np + vpcA - 1) / vpcA, (ni + p->ka - 1) / p->ka);
-    {
-      SPECULA_LAUNCH(ctx, SPECULA_K_PWFS_ROWS_FWD, st,
-                     k_rows_fwd<N1, N2><<<gA, p->blockA, p->smemA, st>>>(
-                         p->field.as<float2>(), p->gx.as<float2>(), p->gy.as<float2>(),
-                         p->twA.as<float2>(), p->rows.as<float2>(), Np, p->n_mod, p->nbw, i0,
-                         ni, p->ka));
-      dim3 gB(S::N / kColsTile, ni);
-      SPECULA_LAUNCH(ctx, SPECULA_K_PWFS_COLS, st,
-                     k_cols<N1, N2, kColsTile><<<gB, p->blockB, p->smemB, st>>>(
-                         p->rows.as<float2>(), p->cols.as<float2>(), p->twA.as<float2>(),
-                         p->twB.as<float2>(), p->mask.as<float2>(), Np));
-      dim3 gC(S::N / bsz, ni);
-      SPECULA_LAUNCH(ctx, SPECULA_K_PWFS_ROWS_INV, st,
-                     k_rows_inv_part<N1, N2><<<gC, p->blockC, p->smemC, st>>>(
-                         p->cols.as<float2>(), p->twA.as<float2>(), p->part.as<float>(), bsz,
-                         scale, p->n_mod, p->nbw, i0));
-    }
-    // batch elements whose last modulation point is in this chunk
-    const int complete = (i0 + ni) / p->n_mod - 1;
-    if (complete > det_done) {
-      dim3 gD((nd * nd + 255) / 256, complete - det_done);
-      SPECULA_LAUNCH(ctx, SPECULA_K_PWFS_BIN, st,
-                     k_bin_reduce<<<gD, 256, 0, st>>>(p->part.as<float>(), det, nd * nd,
-                                                      p->n_mod, p->nbw, det_done + 1,
-                                                      p->run_alpha, p->run_beta));
-      det_done = complete;
-    }
+    return SPECULA_OK;
   }
-  return SPECULA_OK;
 }
 
 bool pwfs_split_for(int N, int *N1, int *N2) {
@@ -827,6 +902,7 @@ bool pwfs_split_for(int N, int *N1, int *N2) {
     case 320: *N1 = 20; *N2 = 16; return true;
     case 660: *N1 = 30; *N2 = 22; return true;   // 22 = 2 x 11, prime-factor form
     case 960: *N1 = 30; *N2 = 32; return true;
+    case 1600: *N1 = 32; *N2 = 50; return true;   // wide: 50 = 2 x 25 in two lane strides
     default: return false;
   }
 }
@@ -910,6 +986,7 @@ int pwfs_run(specula_ctx *ctx, PwfsPlan *p, const float *amp, const float *phase
     case 320: return run_split<20, 16>(ctx, p, amp, phase, n_batch, det, st);
     case 660: return run_split<30, 22>(ctx, p, amp, phase, n_batch, det, st);
     case 960: return run_split<30, 32>(ctx, p, amp, phase, n_batch, det, st);
+    case 1600: return run_split<32, 50>(ctx, p, amp, phase, n_batch, det, st);
     default: return SPECULA_EUNSUPPORTED;
   }
 }
@@ -979,6 +1056,7 @@ static int configure_for(PwfsPlan *p) {
     case 320: return configure<20, 16>(p);
     case 660: return configure<30, 22>(p);
     case 960: return configure<30, 32>(p);
+    case 1600: return configure<32, 50>(p);
     default: return SPECULA_EUNSUPPORTED;
   }
 }

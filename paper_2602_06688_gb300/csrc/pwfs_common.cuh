@@ -19,7 +19,14 @@ template <int N1_, int N2_> struct Split {
   // the pruned pad-2 loads take the pupil as rows N2/4 .. 3 N2/4 of the
   // strided input and need N2 % 4 == 0; other splits (660 = 30 x 22) run the
   // general-offset loads only (the plan refuses pad 2 for them)
-  static_assert(MX <= 32, "one vector per warp at most");
+  // Wide splits (N2 > 32, the two-pass kernels only): the N1-point stage
+  // runs on lanes k2 = lane + 32 t, t < NT2, and writes a second buffer of
+  // N1 S2 complex after the first, so that no lane overwrites exchange
+  // values another lane has yet to read.
+  static constexpr bool WIDE = N2_ > 32;
+  static constexpr int NT2 = (N2_ + 31) / 32;
+  static constexpr int XW = N2_ * S1 + N1_ * S2;   // both buffers of a wide split
+  static_assert(N1_ <= 32 && N2_ <= 64, "N1 lanes per warp; N2 in at most two lane strides");
   static_assert(2 * XB >= N, "a vector's exchange buffer must hold N floats");
 };
 

@@ -237,6 +237,25 @@ def _pwfs39m():
                     mlp_hidden=(2048, 2048))
 
 
+def _andes400():
+    """The ANDES pyramid of Sect. 6, Tab. 2 (24 x 1600 x 1600): a 400 px
+    pupil on the 39 m ELT (0.0975 m pixels), 100 x 100 subapertures,
+    oversampling 4 (1600^2 FFT), 24 modulation points.  The table gives
+    neither the modulation radius nor the pupil separation: 3 lambda/D and
+    120 subapertures (1.2 pupil diameters, as in the SOUL example's 48 / 40)
+    are taken, so a detector pixel is 4 x 4 grid pixels on a 400^2
+    detector.  The 35-layer ELT profile of pwfs39m at this pupil's pitch."""
+    D, n = 39.0, 400
+    pup = Pupil(n, D / n, 0.28)
+    src = Source(0.0, 0.0, math.inf, 750.0)
+    geom = PwfsGeom(pad=4, n_mod=24, mod_amp=3.0, n_sub=100, pup_dist_px=480)
+    h = np.linspace(0.0, 25e3, 35)
+    layers = _profile(5, 35, 0.157, h, np.exp(-h / 3e3),
+                      np.linspace(5.0, 40.0, 35), 2048, D / n, 40.0, 5)
+    return Workload('andes400', D, (Sensor('pwfs', pup, src, pwfs=geom),),
+                    layers, n_modes=4000, n_frames=1000, dt_s=1e-3, r0_m=0.157)
+
+
 WORKLOADS = {
     'pwfs8m_tiny': _pwfs8m_tiny,
     'pwfs8m': _pwfs8m,
@@ -246,6 +265,7 @@ WORKLOADS = {
     'pwfs39m': _pwfs39m,
     'soul8m': _soul8m,
     'soul220': _soul220,
+    'andes400': _andes400,
 }
 
 
