@@ -681,6 +681,25 @@ def systems_leg(ctx, steps=50):
                                        "Sect. 6 Tab. 1"}
     gs.close()
     del fs
+    # the ANDES pyramid (Tab. 2's 24 x 1600 x 1600): 400 px pupil oversampled
+    # 4x on the ELT, 100 x 100 subapertures, 35 layers, 4000 modes
+    ws = synth.workload("andes400")
+    fs = PwfsFrame(ctx, ws, autotune=True)
+    gs = fs.capture(st)
+    time_graph(gs, lambda k: fs.t_dev.fill_(ws.dt_s * k), 5)
+    mss = time_graph(gs, lambda k: fs.t_dev.fill_(ws.dt_s * k), steps)
+    out["andes400"] = {"config": "39 m, 400 px pupil padded 4x (1600^2 FFT = 32 x 50), 24 mod "
+                                 "points, 100x100 subaps of 4 px, images 120 subaps apart on a "
+                                 "400 px detector, 35 layers, 4000 x %d MVM, FP32"
+                                 % fs.R.shape[1],
+                       "tiles": {"chunk": fs.tiles[0], "ka": fs.tiles[1], "passes": fs.tiles[2]}
+                       if fs.tiles else None,
+                       "frames_per_s": steps / (sum(mss) / 1e3), "ms_per_step": sum(mss) / steps,
+                       "paper_context": "ANDES full loop 19.6 Hz (50.9 ms per step) on one GPU, "
+                                        "Sect. 6 Tab. 1"}
+    gs.close()
+    del fs
+    torch.cuda.empty_cache()
     out["infinite8m"] = infinite_leg(ctx, st, flush, steps)
     wl = synth.workload("mwfs39m")
     S = System(ctx, wl)
