@@ -93,11 +93,12 @@ typedef struct {
  * area-weighted rebinning, each detector pixel collecting the overlapped
  * area of every grid pixel, the intensity constant over a grid pixel.
  * Supported: pad 2-4 with N one of 64, 128, 240, 320, 660 (pad 3 or 4),
- * 960, 1600 (pad 3 or 4: the ANDES grid of Sect. 6, Tab. 2, 400 px at pad
- * 4), pup_dist_px + n_pix <= N (the images inside the grid), and column
- * tiles of whole detector pixels within 352 threads (256 at N = 1600;
- * SPECULA_EUNSUPPORTED else).  With pad 2 and pup_dist_px = n_pix the four images tile the grid
- * (quadrant slopes); otherwise read the slopes with SPECULA_SLOPES_PYR_MAPS.
+ * 960, 1600 (pad 4: the ANDES grid of Sect. 6, Tab. 2, a 400 px pupil);
+ * pup_dist_px + n_pix <= N (the images inside the grid); column tiles of
+ * whole detector pixels within 352 threads (128 at N = 1600);
+ * SPECULA_EUNSUPPORTED else.  With pad 2 and pup_dist_px = n_pix the four
+ * images tile the grid (quadrant slopes); otherwise read the slopes with
+ * SPECULA_SLOPES_PYR_MAPS.
  * The three-pass, shifted-mask, paired and DFT-as-GEMM forms need pad 2 and
  * a whole b. */
 typedef struct {

@@ -716,11 +716,13 @@ static int configure(PwfsPlan *p) {
   // columns, so every detector pixel lies in one CTA), k the largest divisor
   // of pad n_sub / fq with TC G <= 256 threads (352 where a detector pixel
   // is a fraction of grid pixels: the SOUL example's 11-column tiles)
+  // (wide splits: 128-thread CTAs, two per SM within the register budget of
+  // their 50-point transforms, so one CTA's barriers do not idle the SM)
   p->two_ok = false;
-  p->blockR = 256;
-  p->smemR = (size_t)(256 / S::G) * RowFiltCfg<N1, N2>::XBF * sizeof(float2);
+  p->blockR = S::WIDE ? 128 : 256;
+  p->smemR = (size_t)(p->blockR / S::G) * RowFiltCfg<N1, N2>::XBF * sizeof(float2);
   const int ndq = p->pad * p->n_sub / p->fq;
-  const int maxt = p->fq == 1 || S::WIDE ? 256 : 352;
+  const int maxt = S::WIDE ? 128 : (p->fq == 1 ? 256 : 352);
   int k = 0;
   for (int d = 1; d <= ndq; ++d)
     if (ndq % d == 0 && d * p->fp * S::G <= maxt) k = d;
@@ -733,7 +735,7 @@ static int configure(PwfsPlan *p) {
     p->smemK = std::max((size_t)tc * p->csK, win) * sizeof(float2);
     if (p->smemK <= 227 * 1024 && S::N % tc == 0) {
       if constexpr (S::WIDE) {
-        // general-offset loads only (N2 % 4 != 0 or pad != 2), tiles of up to 256 threads
+        // general-offset loads only (N2 % 4 != 0 or pad != 2), tiles of up to 128 threads
         if ((s = ensure_dynamic_smem((const void *)k_rowfilt<N1, N2, true>, p->smemR)) ||
             (s = ensure_dynamic_smem((const void *)k_colfilt_bin<N1, N2, 256, true>, p->smemK)))
           return s;
@@ -799,7 +801,7 @@ static int run_split2(specula_ctx *ctx, PwfsPlan *p, const float *amp, const flo
     dim3 gK(S::N / tc, 2 * nj);
     const bool k160 = S::G == 32 && p->blockK <= 160;
     if constexpr (S::WIDE) {
-      SPECULA_ROWFILT(true);   // the plan refuses pad 2 for N2 % 4 != 0; wide tiles <= 256
+      SPECULA_ROWFILT(true);   // the plan refuses pad 2 for N2 % 4 != 0; wide tiles <= 128
       SPECULA_COLFILT(256, true);
     } else {
       if (gen)
