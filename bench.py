@@ -1173,6 +1173,47 @@ def gpu_leg(args, ws, rank, local):
         kern["recon"]["hbm_frac"] = gbs / pk["hbm_gbs"]
         kern["recon"]["traffic"] = traffic.get(("recon", WORKLOAD))
 
+    # ---- each stage of the frame captured as its own CUDA graph and
+    # replayed after an L2 flush: per-stage device time without the tracing
+    # events that bracket every eager launch above
+    def stage_us(enqueue, n=max(K, 20)):
+        torch.cuda.synchronize()
+        sp.specula_graph_begin(ctx, st)
+        try:
+            enqueue()
+        finally:
+            g = sp.specula_graph_end(ctx, st)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(n + 3)]
+        with torch.cuda.stream(st):
+            for a, b in ev:
+                flush.zero_()
+                a.record(st)
+                g.launch(st)
+                b.record(st)
+        torch.cuda.synchronize()
+        kernels = g.kernel_count()
+        g.close()
+        t = [a.elapsed_time(b) * 1e3 for a, b in ev[3:]]
+        return {"us": sum(t) / len(t), "kernels": kernels}
+
+    fr.t_dev.fill_(W * dt)
+    stages = {
+        "extraction": stage_us(lambda: sp.specula_atmo_extract(
+            ctx, fr.layers, fr.screens, fr.src, fr.pupil, 0.0, fr.phase, t_dev=fr.t_dev,
+            stream=st)),
+        "image": stage_us(lambda: sp.specula_pwfs_image(ctx, fr.pupil, fr.pwfs, fr.amp,
+                                                        fr.phase, fr.det, stream=st)),
+        "slopes": stage_us(lambda: sp.specula_slopes(ctx, fr.slopec, fr.det, fr.ref, fr.slopes,
+                                                     stream=st)),
+        "reconstructor": stage_us(lambda: sp.specula_recon(ctx, fr.rec, fr.slopes, fr.modes,
+                                                           stream=st)),
+    }
+    stages["sum_us"] = sum(v["us"] for v in stages.values())
+    stages["whole_frame_graph_us"] = ms_per_step * 1e3
+    stages["note"] = ("each stage captured alone and replayed after an L2 flush (so each "
+                      "starts cold); the whole frame's graph chains them")
+
     # ---- end to end through the public API with host buffers: per frame the
     # time goes host -> device, the captured frame runs, the modes come back.
     # Synchronous: the host waits for every frame's modes before the next.
@@ -1226,7 +1267,8 @@ def gpu_leg(args, ws, rank, local):
                            "frame": "one CUDA graph per frame (%d kernels)" % graph_kernels,
                            "eager_frames_per_s": K / (sum(ms_eager) / 1e3),
                            "wall_ms_per_step_incl_flush": (wall1 - wall0) * 1e3 / K},
-                "roofline": roof, "kernels": kern, "variants": variants,
+                "roofline": roof, "kernels": kern, "stages_graph": stages,
+                "variants": variants,
                 "e2e": {"value": e2e, "unit": "frames/s", "h2d_bytes_per_step": 8,
                         "d2h_bytes_per_step": 4 * fr.n_modes,
                         "note": "per step: pinned host time -> device, frame, modes -> pinned "
