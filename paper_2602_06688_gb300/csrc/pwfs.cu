@@ -519,6 +519,18 @@ __global__ void __launch_bounds__(MAXT, Split<N1, N2>::WIDE
         cp_async16(dst, src);
     }
   }
+  // wide splits also stage the item's y factors beside the window (5% off
+  // their column pass; at 960 the factors come through L1 as fast)
+  float2 *s_gy = nullptr;
+  if constexpr (S::WIDE) {
+    s_gy = s_tile + ((max(TC * CS, n_pix * W) + 1) & ~1);   // 16-byte aligned
+    const float2 *g = gy + (size_t)m * n_pix;
+    if ((n_pix & 1) == 0) {
+      for (int i = threadIdx.x; 2 * i < n_pix; i += blockDim.x) cp_async16(s_gy + 2 * i, g + 2 * i);
+    } else {
+      for (int i = threadIdx.x; i < n_pix; i += blockDim.x) cp_async8(s_gy + i, g + i);
+    }
+  }
   const int vec = threadIdx.x / G, lane = threadIdx.x % G;
   cp_async_wait_all();
   __syncthreads();
@@ -532,7 +544,12 @@ __global__ void __launch_bounds__(MAXT, Split<N1, N2>::WIDE
 #pragma unroll
       for (int n2 = 0; n2 < N2; ++n2) {
         const int row = lane + N1 * n2 - off;                // pupil row
-        if (row >= 0 && row < n_pix) r[n2] = cmul(w[row * W], __ldg(g + row));
+        if (row >= 0 && row < n_pix) {
+          if constexpr (S::WIDE)
+            r[n2] = cmul(w[row * W], s_gy[row]);
+          else
+            r[n2] = cmul(w[row * W], __ldg(g + row));
+        }
       }
     } else {
       const float2 *g = gy + (size_t)m * n_pix + lane;   // pupil row lane + N1 h
@@ -732,7 +749,9 @@ static int configure(PwfsPlan *p) {
     p->csK = ColFiltCfg<N1, N2>::stride(tc);
     // exchange buffers, or the staging window of n_pix rows x W complex
     const size_t win = (size_t)p->n_pix * ((tc + 1) & ~1);
-    p->smemK = std::max((size_t)tc * p->csK, win) * sizeof(float2);
+    // (wide splits: and the item's n_pix y factors, after a 16-byte boundary)
+    p->smemK = (std::max((size_t)tc * p->csK, win) + (S::WIDE ? 1 + p->n_pix : 0)) *
+               sizeof(float2);
     if (p->smemK <= 227 * 1024 && S::N % tc == 0) {
       if constexpr (S::WIDE) {
         // general-offset loads only (N2 % 4 != 0 or pad != 2), tiles of up to 128 threads
