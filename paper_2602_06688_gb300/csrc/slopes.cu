@@ -23,16 +23,12 @@ __device__ __forceinline__ void guard_finite(float a, float b, int32_t *nf_statu
 // grid (ceil(n_valid / kPyrThreads), n_batch): every CTA forms the global
 // normalisation T itself (the detector is small and L2-resident; the same
 // fixed-order reduction in every CTA gives the same T bit for bit), then
-// the slopes of its kPyrThreads subapertures.  Index checks are branch-free
-// (an out-of-range index reads subaperture 0 and is reported once per CTA),
-// so the loads of several subapertures are in flight together.
-__device__ __forceinline__ float quad_sum(const float *d, int s, int n_sub, int w2) {
-  const int a = s / n_sub, c = s - a * n_sub;
-  const float q1 = d[(n_sub + a) * w2 + n_sub + c], q2 = d[(n_sub + a) * w2 + c];
-  const float q3 = d[a * w2 + c], q4 = d[a * w2 + n_sub + c];
-  return ((q1 + q2) + q3) + q4;
-}
-
+// the slopes of its kPyrThreads subapertures from the four values each
+// thread kept while summing T (its own subaperture is among those it
+// sums: two dependent rounds of loads per frame, not four).  Index checks
+// are branch-free (an out-of-range index reads subaperture 0 and is
+// reported once per CTA), so the loads of several subapertures are in
+// flight together.
 __global__ void __launch_bounds__(kPyrThreads) k_pyr_slopes(
     const float *__restrict__ det, const int32_t *__restrict__ idx, const float *__restrict__ ref,
     int n_sub, int n_valid, float *__restrict__ out, int32_t *status, int32_t *nf_status) {
@@ -42,6 +38,13 @@ __global__ void __launch_bounds__(kPyrThreads) k_pyr_slopes(
   const int w2 = 2 * n_sub;
   const unsigned n2 = (unsigned)(n_sub * n_sub);
   const float *d = det + (size_t)b * w2 * w2;
+  const int kown = blockIdx.x * kPyrThreads + threadIdx.x;   // this thread's output
+  float r0 = 0.f, r1 = 0.f;
+  if (ref && kown < n_valid) {
+    r0 = ref[kown];
+    r1 = ref[n_valid + kown];
+  }
+  float q1 = 0.f, q2 = 0.f, q3 = 0.f, q4 = 0.f;   // kown's four pupil-image values
   float part = 0.f;
   int bad = 0;
   for (int k0 = threadIdx.x; k0 < n_valid; k0 += 8 * kPyrThreads) {
@@ -55,7 +58,18 @@ __global__ void __launch_bounds__(kPyrThreads) k_pyr_slopes(
     }
     float q[8];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) q[u] = quad_sum(d, sv[u], n_sub, w2);
+    for (int u = 0; u < 8; ++u) {
+      const int s = sv[u], a = s / n_sub, c = s - a * n_sub;
+      const float v1 = d[(n_sub + a) * w2 + n_sub + c], v2 = d[(n_sub + a) * w2 + c];
+      const float v3 = d[a * w2 + c], v4 = d[a * w2 + n_sub + c];
+      q[u] = ((v1 + v2) + v3) + v4;
+      if (k0 + u * kPyrThreads == kown) {
+        q1 = v1;
+        q2 = v2;
+        q3 = v3;
+        q4 = v4;
+      }
+    }
 #pragma unroll
     for (int u = 0; u < 8; ++u)
       if (k0 + u * kPyrThreads < n_valid) part += q[u];
@@ -71,19 +85,14 @@ __global__ void __launch_bounds__(kPyrThreads) k_pyr_slopes(
   }
   __syncthreads();
   const float T = s_T;
-  const int k = blockIdx.x * kPyrThreads + threadIdx.x;
+  const int k = kown;
   if (k >= n_valid) return;
   float *o = out + (size_t)b * 2 * n_valid;
-  int s = __ldg(idx + k);
-  s = (unsigned)s < n2 ? s : 0;
-  const int a = s / n_sub, c = s - a * n_sub;
-  const float q1 = d[(n_sub + a) * w2 + n_sub + c], q2 = d[(n_sub + a) * w2 + c];
-  const float q3 = d[a * w2 + c], q4 = d[a * w2 + n_sub + c];
   float sx = ((q1 + q4) - (q2 + q3)) / T;
   float sy = ((q1 + q2) - (q3 + q4)) / T;
   if (ref) {
-    sx -= ref[k];
-    sy -= ref[n_valid + k];
+    sx -= r0;
+    sy -= r1;
   }
   o[k] = sx;
   o[n_valid + k] = sy;
@@ -92,7 +101,8 @@ __global__ void __launch_bounds__(kPyrThreads) k_pyr_slopes(
 
 // The same slopes from explicit detector indices of the four pupil images
 // (map[q n_valid + k] for image q = Q1..Q4 of subaperture k; any padding and
-// image separation): same grid, same fixed-order sums.
+// image separation): same grid, same fixed-order sums, the thread's own
+// four values kept from the T pass.
 __global__ void __launch_bounds__(kPyrThreads) k_pyr_slopes_maps(
     const float *__restrict__ det, const int32_t *__restrict__ map, const float *__restrict__ ref,
     int n_det2, int n_valid, float *__restrict__ out, int32_t *status, int32_t *nf_status) {
@@ -101,6 +111,13 @@ __global__ void __launch_bounds__(kPyrThreads) k_pyr_slopes_maps(
   const int b = blockIdx.y;
   const float *d = det + (size_t)b * n_det2;
   const unsigned lim = (unsigned)n_det2;
+  const int kown = blockIdx.x * kPyrThreads + threadIdx.x;   // this thread's output
+  float r0 = 0.f, r1 = 0.f;
+  if (ref && kown < n_valid) {
+    r0 = ref[kown];
+    r1 = ref[n_valid + kown];
+  }
+  float qo[4] = {0.f, 0.f, 0.f, 0.f};   // kown's four pupil-image values
   float part = 0.f;
   int bad = 0;
   for (int k0 = threadIdx.x; k0 < n_valid; k0 += 8 * kPyrThreads) {
@@ -115,7 +132,14 @@ __global__ void __launch_bounds__(kPyrThreads) k_pyr_slopes_maps(
         bad |= (unsigned)v >= lim;
         i[c] = (unsigned)v < lim ? v : 0;
       }
-      q[u] = ((d[i[0]] + d[i[1]]) + d[i[2]]) + d[i[3]];
+      float v[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) v[c] = d[i[c]];
+      q[u] = ((v[0] + v[1]) + v[2]) + v[3];
+      if (k == kown) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) qo[c] = v[c];
+      }
     }
 #pragma unroll
     for (int u = 0; u < 8; ++u)
@@ -132,20 +156,14 @@ __global__ void __launch_bounds__(kPyrThreads) k_pyr_slopes_maps(
   }
   __syncthreads();
   const float T = s_T;
-  const int k = blockIdx.x * kPyrThreads + threadIdx.x;
+  const int k = kown;
   if (k >= n_valid) return;
   float *o = out + (size_t)b * 2 * n_valid;
-  float q[4];
-#pragma unroll
-  for (int c = 0; c < 4; ++c) {
-    const int v = __ldg(map + (size_t)c * n_valid + k);
-    q[c] = d[(unsigned)v < lim ? v : 0];
-  }
-  float sx = ((q[0] + q[3]) - (q[1] + q[2])) / T;
-  float sy = ((q[0] + q[1]) - (q[2] + q[3])) / T;
+  float sx = ((qo[0] + qo[3]) - (qo[1] + qo[2])) / T;
+  float sy = ((qo[0] + qo[1]) - (qo[2] + qo[3])) / T;
   if (ref) {
-    sx -= ref[k];
-    sy -= ref[n_valid + k];
+    sx -= r0;
+    sy -= r1;
   }
   o[k] = sx;
   o[n_valid + k] = sy;
