@@ -360,8 +360,19 @@ template <int N1, int N2> struct RowFiltCfg {
 // GEN: any padding (the pupil at padded offset `off`, each lane loading the
 // registers whose padded index falls in the pupil); otherwise the pad-2
 // layout, where the pupil is exactly registers N2/4 .. 3 N2/4 of every lane.
+// One-warp transforms (G = 32) run five warps per CTA, four CTAs per SM at
+// 96 registers, and reload the field row for every slot (caching it across
+// slots needs 32 more registers: spills at that bound); smaller transforms
+// run 256 threads, two CTAs per SM, with the cached row.
+template <int N1, int N2> struct RowFiltLaunch {
+  using S = Split<N1, N2>;
+  static constexpr int threads = S::WIDE ? 256 : (S::G == 32 ? 160 : 256);
+  static constexpr int min_blocks = S::WIDE ? 1 : (S::G == 32 ? 4 : 2);
+  static constexpr bool reload = S::G == 32;
+};
 template <int N1, int N2, bool GEN = false>
-__global__ void __launch_bounds__(256, Split<N1, N2>::WIDE ? 1 : 2) k_rowfilt(
+__global__ void __launch_bounds__(RowFiltLaunch<N1, N2>::threads,
+                                  RowFiltLaunch<N1, N2>::min_blocks) k_rowfilt(
     const float2 *__restrict__ field, const float2 *__restrict__ gx,
     const float2 *__restrict__ twA, const float2 *__restrict__ twB,
     const float2 *__restrict__ mask, float2 *__restrict__ rows_out, int n_pix, int nc, int nbw,
@@ -384,7 +395,7 @@ __global__ void __launch_bounds__(256, Split<N1, N2>::WIDE ? 1 : 2) k_rowfilt(
     if (it >= n_slots) break;
     const int gi = slot0 + it;
     const int b = gi / nc, c = s0 + (gi - b * nc);   // nc slots per element from s0
-    if (!GEN && b != cur_b) {
+    if (!GEN && (RowFiltLaunch<N1, N2>::reload || b != cur_b)) {
       cur_b = b;
       const float2 *src = field + ((size_t)(b % nbw) * n_pix + (row_ok ? j : 0)) * n_pix + lane;
 #pragma unroll
@@ -736,7 +747,7 @@ static int configure(PwfsPlan *p) {
   // (wide splits: 128-thread CTAs, two per SM within the register budget of
   // their 50-point transforms, so one CTA's barriers do not idle the SM)
   p->two_ok = false;
-  p->blockR = S::WIDE ? 128 : 256;
+  p->blockR = S::WIDE ? 128 : RowFiltLaunch<N1, N2>::threads;
   p->smemR = (size_t)(p->blockR / S::G) * RowFiltCfg<N1, N2>::XBF * sizeof(float2);
   const int ndq = p->pad * p->n_sub / p->fq;
   const int maxt = S::WIDE ? 128 : (p->fq == 1 ? 256 : 352);
