@@ -569,10 +569,12 @@ __global__ void __launch_bounds__(MAXT, Split<N1, N2>::WIDE
       for (int h = 0; h < QH; ++h) r[Q0 + h] = cmul(w[N1 * h * W], __ldg(g + N1 * h));
     }
   }
-  __syncthreads();                             // the window is reused below
   float2 *col = s_tile + vec * CS;
   RegDFT<N2, false>::run(r);
-  __syncwarp();
+  // the window is reused below as the exchange buffers: the barrier comes
+  // after the first transform, which only needs registers, so a warp that
+  // loaded early computes instead of waiting
+  __syncthreads();
   if (lane < N1) {
 #pragma unroll
     for (int k2 = 0; k2 < N2; ++k2) col[k2 * S1 + lane] = cmulc(r[k2], __ldg(twA + k2 * N1 + lane));
