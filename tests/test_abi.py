@@ -51,7 +51,8 @@ def test_strerror_and_version(sp):
     assert sp.specula_version() >= 100
 
 
-@pytest.mark.parametrize("name", ["pwfs8m_tiny", "pwfs8m", "mwfs39m", "pwfs39m"])
+@pytest.mark.parametrize("name", ["pwfs8m_tiny", "pwfs8m", "mwfs39m", "pwfs39m", "soul220",
+                                  "andes400"])
 def test_host_geometry_bit_exact(sp, name):
     w = synth.workload(name)
     for s in w.sensors:
@@ -136,6 +137,13 @@ def test_pyr_image_index_host_matches_oracle(sp):
     with pytest.raises(sp.SpeculaError) as e:
         sp.specula_pyr_image_index_host(pu3, 3, 265, 40)     # 265 / 5.5 is not whole
     assert e.value.status == sp.EUNSUPPORTED
+    # the ANDES reading: 400 px pupil at pad 4, 100 subapertures of 4 px,
+    # images 480 grid px = 120 detector px apart on the 400 px detector
+    pu4 = sp.PupilDesc(400, 39.0 / 400, 0.28)
+    v4 = geometry.valid_subaps(geometry.pupil_mask(400, 0.28).astype(np.uint8), 100)
+    m4 = sp.specula_pyr_image_index_host(pu4, 4, 480, 100)
+    assert np.array_equal(m4, geometry.pyr_image_index(v4, 100, 4, 480, 400))
+    assert m4.min() // 400 == 90 and m4.max() // 400 == 309   # 200 -+ 60 -+ 50
 
 
 @pytest.mark.parametrize("n,n_sub,obsc", [(22, 4, 0.0), (33, 6, 0.3), (100, 7, 0.2), (63, 10, 0.11)])
