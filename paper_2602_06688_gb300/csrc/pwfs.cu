@@ -58,6 +58,12 @@ __device__ __forceinline__ void cp_async16(void *smem_dst, const void *gsrc) {
 __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.wait_all;" ::: "memory");
 }
+// a read-only load that does not allocate in L1 (data read once per CTA)
+__device__ __forceinline__ float2 ld_stream2(const float2 *p) {
+  float2 v;
+  asm("ld.global.nc.L1::no_allocate.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p));
+  return v;
+}
 
 // The N1-point middle stage of a wide split (N2 > 32): lane k2 = lane + 32 t
 // (t < NT2) takes column k2 of the exchange xa (xa[k2 S1 + n1]), applies the
@@ -349,6 +355,7 @@ template <int N1, int N2> struct RowFiltCfg {
   using S = Split<N1, N2>;
   static constexpr int XBF =
       S::WIDE ? S::XW : (N2 * S::S1 > N1 * S::S2 ? N2 * S::S1 : N1 * S::S2);
+  static_assert(S::N <= XBF, "a row fits its vector's exchange buffer");
 };
 
 // Points m and n_mod - m share cos(theta), hence the x factor of the tilt;
@@ -360,14 +367,15 @@ template <int N1, int N2> struct RowFiltCfg {
 // GEN: any padding (the pupil at padded offset `off`, each lane loading the
 // registers whose padded index falls in the pupil); otherwise the pad-2
 // layout, where the pupil is exactly registers N2/4 .. 3 N2/4 of every lane.
-// One-warp transforms (G = 32) run five warps per CTA, four CTAs per SM at
-// 96 registers, and reload the field row for every slot (caching it across
-// slots needs 32 more registers: spills at that bound); smaller transforms
-// run 256 threads, two CTAs per SM, with the cached row.
+// One-warp transforms (G = 32) run four warps per CTA, five CTAs per SM at
+// 96 registers (four rows per CTA: the transposed output goes out as whole
+// 32-byte sectors), and reload the field row for every slot (caching it
+// across slots needs 32 more registers: spills at that bound); smaller
+// transforms run 256 threads, two CTAs per SM, with the cached row.
 template <int N1, int N2> struct RowFiltLaunch {
   using S = Split<N1, N2>;
-  static constexpr int threads = S::WIDE ? 256 : (S::G == 32 ? 160 : 256);
-  static constexpr int min_blocks = S::WIDE ? 1 : (S::G == 32 ? 4 : 2);
+  static constexpr int threads = S::WIDE ? 256 : (S::G == 32 ? 128 : 256);
+  static constexpr int min_blocks = S::WIDE ? 1 : (S::G == 32 ? 5 : 2);
   static constexpr bool reload = S::G == 32;
 };
 template <int N1, int N2, bool GEN = false>
@@ -383,7 +391,11 @@ __global__ void __launch_bounds__(RowFiltLaunch<N1, N2>::threads,
   extern __shared__ float2 smem[];
   const int vpc = blockDim.x / G;
   const int vec = threadIdx.x / G, lane = threadIdx.x % G;
-  float2 *xb = smem + vec * RowFiltCfg<N1, N2>::XBF;
+  constexpr int XBF = RowFiltCfg<N1, N2>::XBF;
+  float2 *xb = smem + vec * XBF;
+  // where vector v's output row sits in its buffer (3 v complex in, as far as
+  // the buffer's slack allows)
+  auto row_tile_off = [](int v) { return min(3 * v, XBF - N); };
   const int j = blockIdx.x * vpc + vec;
   const bool row_ok = j < n_pix;
   const bool in_lane = row_ok && lane < N1;
@@ -464,12 +476,40 @@ __global__ void __launch_bounds__(RowFiltLaunch<N1, N2>::threads,
       for (int n1 = 0; n1 < N2; ++n1) r3[n1] = make_float2(0.f, 0.f);
     }
     RegDFT<N2, true>::run(r3);
-    __syncwarp();
-    if (row_ok && lane < N1) {
-      float2 *dst = rows_out + ((size_t)it * n_pix + j) * N + lane;
+    // The slot's block is column-major (rows_out[it][x][row]), so that the
+    // column pass loads a column coalesced.  Each vector puts its row in
+    // its own exchange buffer (T_v, offset a few complex per vector against
+    // bank conflicts), and the CTA writes one run of vpc rows per column x,
+    // as 16-byte row pairs where the rows allow.
+    __syncwarp();   // this vector's last-stage loads are done
+    if (lane < N1) {
 #pragma unroll
-      for (int k1 = 0; k1 < N2; ++k1) dst[N1 * k1] = r3[k1];   // x = N1 k1 + lane
+      for (int k1 = 0; k1 < N2; ++k1) xb[N1 * k1 + lane + row_tile_off(vec)] = r3[k1];   // x = N1 k1 + lane
     }
+    __syncthreads();
+    {
+      const int j0 = blockIdx.x * vpc;
+      float2 *dst = rows_out + ((size_t)it * N) * n_pix + j0;
+      if ((vpc & 1) == 0 && (n_pix & 1) == 0) {
+        const int hp = vpc / 2, h = threadIdx.x % hp;   // rows 2h and 2h + 1
+        if (j0 + 2 * h < n_pix) {                       // n_pix even: both rows exist
+          const float2 *ta = smem + (2 * h) * XBF + row_tile_off(2 * h);
+          const float2 *tb = smem + (2 * h + 1) * XBF + row_tile_off(2 * h + 1);
+          for (int x = threadIdx.x / hp; x < N; x += 2 * G) {
+            const float2 a = ta[x], c = tb[x];
+            *reinterpret_cast<float4 *>(dst + (size_t)x * n_pix + 2 * h) =
+                make_float4(a.x, a.y, c.x, c.y);
+          }
+        }
+      } else {
+        const int v = threadIdx.x % vpc;
+        if (j0 + v < n_pix) {
+          const float2 *tv = smem + v * XBF + row_tile_off(v);
+          for (int x = threadIdx.x / vpc; x < N; x += G) dst[(size_t)x * n_pix + v] = tv[x];
+        }
+      }
+    }
+    __syncthreads();   // the exchange buffers are the next slot's
   }
 }
 
@@ -510,71 +550,53 @@ __global__ void __launch_bounds__(MAXT, Split<N1, N2>::WIDE
   const int m = (blockIdx.y & 1) ? n_mod - cslot : cslot;
   if ((blockIdx.y & 1) && (cslot == 0 || 2 * cslot == n_mod)) return;   // no second item
   const int col0 = blockIdx.x * TC;
-  // Stage the tile's n_pix rows as a row-major window of W complex starting
-  // at the even column col0e (16-byte copies: W and col0e even), with
-  // cp.async.cg, which bypasses L1 and so leaves the twiddle, mask and tilt
-  // tables resident there.  For odd TC the window has one spare column
-  // (it may read the first entry of the next row: the row buffer carries
-  // two complex of padding after its last row).
-  const int col0e = col0 & ~1, sh = col0 - col0e;
-  const int W = (TC + 1) & ~1, nch = W / 2;
-  {
-    // thread t copies chunk t % nch of the rows t / nch + k R (no division
-    // in the loop)
-    const int R = blockDim.x / nch, t = threadIdx.x;
-    if (t < R * nch) {
-      const int q = t % nch, r0 = t / nch;
-      const float2 *src = rows_in + ((size_t)it * n_pix + r0) * N + col0e + 2 * q;
-      float2 *dst = s_tile + r0 * W + 2 * q;
-      for (int r = r0; r < n_pix; r += R, src += (size_t)R * N, dst += R * W)
-        cp_async16(dst, src);
-    }
-  }
-  // wide splits also stage the item's y factors beside the window (5% off
-  // their column pass; at 960 the factors come through L1 as fast)
+  const int vec = threadIdx.x / G, lane = threadIdx.x % G;
+  // wide splits stage the item's y factors in shared memory (5% off their
+  // column pass; at 960 the factors come through L1 as fast)
   float2 *s_gy = nullptr;
   if constexpr (S::WIDE) {
-    s_gy = s_tile + ((max(TC * CS, n_pix * W) + 1) & ~1);   // 16-byte aligned
+    s_gy = s_tile + ((TC * CS + 1) & ~1);   // 16-byte aligned
     const float2 *g = gy + (size_t)m * n_pix;
     if ((n_pix & 1) == 0) {
       for (int i = threadIdx.x; 2 * i < n_pix; i += blockDim.x) cp_async16(s_gy + 2 * i, g + 2 * i);
     } else {
       for (int i = threadIdx.x; i < n_pix; i += blockDim.x) cp_async8(s_gy + i, g + i);
     }
+    cp_async_wait_all();
+    __syncthreads();
   }
-  const int vec = threadIdx.x / G, lane = threadIdx.x % G;
-  cp_async_wait_all();
-  __syncthreads();
+  // this vector's column x = col0 + vec: n_pix contiguous rows of the
+  // slot's column-major block, loaded coalesced straight into registers and
+  // past L1 (which keeps the twiddle, mask and tilt tables)
+  const float2 *cx = rows_in + ((size_t)it * N + col0 + vec) * n_pix;
   float2 r[N2];
 #pragma unroll
   for (int n2 = 0; n2 < N2; ++n2) r[n2] = make_float2(0.f, 0.f);
   if (lane < N1) {
     if constexpr (GEN) {
       const float2 *g = gy + (size_t)m * n_pix;
-      const float2 *w = s_tile + sh + vec;
 #pragma unroll
       for (int n2 = 0; n2 < N2; ++n2) {
         const int row = lane + N1 * n2 - off;                // pupil row
         if (row >= 0 && row < n_pix) {
           if constexpr (S::WIDE)
-            r[n2] = cmul(w[row * W], s_gy[row]);
+            r[n2] = cmul(ld_stream2(cx + row), s_gy[row]);
           else
-            r[n2] = cmul(w[row * W], __ldg(g + row));
+            r[n2] = cmul(ld_stream2(cx + row), __ldg(g + row));
         }
       }
     } else {
       const float2 *g = gy + (size_t)m * n_pix + lane;   // pupil row lane + N1 h
-      const float2 *w = s_tile + sh + vec + lane * W;
+      const float2 *w = cx + lane;
+      float2 e[QH];
 #pragma unroll
-      for (int h = 0; h < QH; ++h) r[Q0 + h] = cmul(w[N1 * h * W], __ldg(g + N1 * h));
+      for (int h = 0; h < QH; ++h) e[h] = ld_stream2(w + N1 * h);
+#pragma unroll
+      for (int h = 0; h < QH; ++h) r[Q0 + h] = cmul(e[h], __ldg(g + N1 * h));
     }
   }
-  float2 *col = s_tile + vec * CS;
+  float2 *col = s_tile + vec * CS;   // this vector's exchange buffer
   RegDFT<N2, false>::run(r);
-  // the window is reused below as the exchange buffers: the barrier comes
-  // after the first transform, which only needs registers, so a warp that
-  // loaded early computes instead of waiting
-  __syncthreads();
   if (lane < N1) {
 #pragma unroll
     for (int k2 = 0; k2 < N2; ++k2) col[k2 * S1 + lane] = cmulc(r[k2], __ldg(twA + k2 * N1 + lane));
@@ -760,11 +782,9 @@ static int configure(PwfsPlan *p) {
     const int tc = k * p->fp;
     p->blockK = tc * S::G;
     p->csK = ColFiltCfg<N1, N2>::stride(tc);
-    // exchange buffers, or the staging window of n_pix rows x W complex
-    const size_t win = (size_t)p->n_pix * ((tc + 1) & ~1);
-    // (wide splits: and the item's n_pix y factors, after a 16-byte boundary)
-    p->smemK = (std::max((size_t)tc * p->csK, win) + (S::WIDE ? 1 + p->n_pix : 0)) *
-               sizeof(float2);
+    // the tile's exchange buffers (wide splits: and the item's n_pix y
+    // factors, after a 16-byte boundary)
+    p->smemK = ((size_t)tc * p->csK + (S::WIDE ? 1 + p->n_pix : 0)) * sizeof(float2);
     if (p->smemK <= 227 * 1024 && S::N % tc == 0) {
       if constexpr (S::WIDE) {
         // general-offset loads only (N2 % 4 != 0 or pad != 2), tiles of up to 128 threads
@@ -954,8 +974,8 @@ int pwfs_set_tiles(PwfsPlan *p, int chunk, int ka, int passes) {
   if (passes == 4) chunk = std::max(1, chunk / p->nc) * p->nc;
   const int nbw = passes == 4 ? chunk / p->nc : (chunk + per_b - 1) / per_b + 1;
   const size_t need_field = (size_t)nbw * p->n_pix * p->n_pix * sizeof(float2);
-  // two complex of padding: the column pass's staging window may read one
-  // entry past the last row
+  // two complex of padding: the paired form's column staging window may
+  // read one entry past the last row
   const size_t need_rows = ((size_t)chunk * p->n_pix * p->N + 2) * sizeof(float2);
   const size_t need_cols = passes == 3 ? (size_t)chunk * p->N * p->N * sizeof(float2) : 0;
   const size_t need_part = (size_t)nbw * p->n_mod * nd * nd * sizeof(float);
