@@ -348,7 +348,10 @@ __global__ void __launch_bounds__(256, 2) k_rows_inv_part(
 // the pruned input, x mask, inverse row FFT); pass K filters every column
 // (forward FFT of its n_pix non-zero entries, y mask, inverse FFT), squares,
 // scales by 1/n_mod and bins, so the N x N intermediate of the three-pass
-// form is never written.  The inverse row transform's output phase depends
+// form is never written.  Between the two, a slot's filtered rows are held
+// column-major ([slot][x][row]): pass R transposes its rows on the way out,
+// and pass K reads each column as one contiguous run, coalesced, straight
+// into registers.  The inverse row transform's output phase depends
 // on x only and vanishes in |.|^2.
 
 template <int N1, int N2> struct RowFiltCfg {
@@ -363,7 +366,8 @@ template <int N1, int N2> struct RowFiltCfg {
 // So the row filter runs once per distinct cosine ("slot" c = 0 .. nc-1,
 // representative m = c) without the y factor, and the column pass applies
 // each item's own y factor gy[m][row] to its input.
-// R: grid (ceil(n_pix / VPC), ceil(n_slots / ka)); block VPC * G threads.
+// R: grid (ceil(n_pix / VPC), ceil(n_slots / ka)); block VPC * G threads;
+// writes rows_out[slot][x][row].
 // GEN: any padding (the pupil at padded offset `off`, each lane loading the
 // registers whose padded index falls in the pupil); otherwise the pad-2
 // layout, where the pupil is exactly registers N2/4 .. 3 N2/4 of every lane.
@@ -513,8 +517,9 @@ __global__ void __launch_bounds__(RowFiltLaunch<N1, N2>::threads,
   }
 }
 
-// K: per tile of TC = blockDim.x / G columns (a multiple of the bin side):
-// the item's y tilt, column filter, |.|^2 / n_mod, b x b bins ->
+// K: per tile of TC = blockDim.x / G columns (a multiple of the bin side),
+// read from rows_in[slot][x][row]: the item's y tilt, column filter,
+// |.|^2 / n_mod, b x b bins ->
 // part[b % nbw][m][ybin][xbin].  grid (N / TC, 2 n_slots): y = 2 p + w is
 // item m = c (w = 0) or m = n_mod - c (w = 1, when distinct) of slot p.
 // Column stride CS (complex) of the exchange buffers: at least the exchange
