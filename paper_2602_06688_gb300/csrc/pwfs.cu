@@ -513,7 +513,7 @@ __global__ void __launch_bounds__(RowFiltLaunch<N1, N2>::threads,
         }
       }
     }
-    __syncthreads();   // the exchange buffers are the next slot's
+    if (q + 1 < ka && it + 1 < n_slots) __syncthreads();   // the buffers are the next slot's
   }
 }
 
