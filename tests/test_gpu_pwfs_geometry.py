@@ -17,9 +17,12 @@ pytestmark = pytest.mark.gpu
 # fractional detector pixels (area-weighted rebinning in the column pass):
 # the paper's SOUL as stated (220 px pupil, 660^2 grid, 24 points, 5.5 grid
 # pixels per detector pixel), a 240 grid with 2.5 px detector pixels
-# (16-lane transforms), pad 2 on a 320 grid with 2.5 px detector pixels
+# (16-lane transforms), pad 2 on a 320 grid with 2.5 px detector pixels, and
+# an odd pupil side (165 px at pad 4 on the 660 grid: the row pass writes
+# its transposed rows one complex at a time)
 CASES = [(80, 3, 96, 40, 16), (32, 4, 48, 8, 8), (16, 4, 24, 4, 8), (320, 3, 384, 80, 16),
-         (64, 2, 48, 16, 12), (220, 3, 264, 40, 24), (80, 3, 100, 32, 16), (160, 2, 160, 64, 12)]
+         (64, 2, 48, 16, 12), (220, 3, 264, 40, 24), (80, 3, 100, 32, 16), (160, 2, 160, 64, 12),
+         (165, 4, 195, 33, 8)]
 
 
 @pytest.fixture(scope="module")
