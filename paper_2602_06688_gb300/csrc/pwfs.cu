@@ -397,9 +397,10 @@ __global__ void __launch_bounds__(RowFiltLaunch<N1, N2>::threads,
   const int vec = threadIdx.x / G, lane = threadIdx.x % G;
   constexpr int XBF = RowFiltCfg<N1, N2>::XBF;
   float2 *xb = smem + vec * XBF;
-  // where vector v's output row sits in its buffer (3 v complex in, as far as
-  // the buffer's slack allows)
-  auto row_tile_off = [](int v) { return min(3 * v, XBF - N); };
+  // where vector v's output row sits in its buffer: 4 v complex in, as far
+  // as the buffer's slack allows, and even, so that with an even XBF two
+  // adjacent columns of a row are one aligned 16-byte load
+  auto row_tile_off = [](int v) { return min(4 * v, (XBF - N) & ~1); };
   const int j = blockIdx.x * vpc + vec;
   const bool row_ok = j < n_pix;
   const bool in_lane = row_ok && lane < N1;
@@ -499,10 +500,22 @@ __global__ void __launch_bounds__(RowFiltLaunch<N1, N2>::threads,
         if (j0 + 2 * h < n_pix) {                       // n_pix even: both rows exist
           const float2 *ta = smem + (2 * h) * XBF + row_tile_off(2 * h);
           const float2 *tb = smem + (2 * h + 1) * XBF + row_tile_off(2 * h + 1);
-          for (int x = threadIdx.x / hp; x < N; x += 2 * G) {
-            const float2 a = ta[x], c = tb[x];
-            *reinterpret_cast<float4 *>(dst + (size_t)x * n_pix + 2 * h) =
-                make_float4(a.x, a.y, c.x, c.y);
+          if constexpr (XBF % 2 == 0) {
+            // columns x and x + 1 of both rows: two 16-byte loads, two stores
+            for (int x = 2 * (threadIdx.x / hp); x < N; x += 4 * G) {
+              const float4 a = *reinterpret_cast<const float4 *>(ta + x);
+              const float4 c = *reinterpret_cast<const float4 *>(tb + x);
+              *reinterpret_cast<float4 *>(dst + (size_t)x * n_pix + 2 * h) =
+                  make_float4(a.x, a.y, c.x, c.y);
+              *reinterpret_cast<float4 *>(dst + (size_t)(x + 1) * n_pix + 2 * h) =
+                  make_float4(a.z, a.w, c.z, c.w);
+            }
+          } else {
+            for (int x = threadIdx.x / hp; x < N; x += 2 * G) {
+              const float2 a = ta[x], c = tb[x];
+              *reinterpret_cast<float4 *>(dst + (size_t)x * n_pix + 2 * h) =
+                  make_float4(a.x, a.y, c.x, c.y);
+            }
           }
         }
       } else {
