@@ -375,7 +375,9 @@ template <int N1, int N2> struct RowFiltCfg {
 // 96 registers (four rows per CTA: the transposed output goes out as whole
 // 32-byte sectors), and reload the field row for every slot (caching it
 // across slots needs 32 more registers: spills at that bound); smaller
-// transforms run 256 threads, two CTAs per SM, with the cached row.
+// transforms run 256 threads, two CTAs per SM, with the cached row; wide
+// splits run 128-thread CTAs (bounded for up to 256 threads, one CTA per SM,
+// so that their 50-point transforms keep their registers).
 template <int N1, int N2> struct RowFiltLaunch {
   using S = Split<N1, N2>;
   static constexpr int threads = S::WIDE ? 256 : (S::G == 32 ? 128 : 256);
