@@ -56,6 +56,43 @@ def test_tilt_sign_on_separated_images():
     assert s[:nv].mean() > 0.01 and abs(s[nv:].mean()) < 1e-10
 
 
+def _pins_for(n, nsub, pad, pd, obsc=0.28, mirror=True):
+    amp = geometry.pupil_mask(n, obsc).astype(np.float64)
+    valid = geometry.valid_subaps(amp.astype(np.uint8), nsub)
+    maps = geometry.pyr_image_index(valid, nsub, pad, pd, n)
+    flat = pyramid.pwfs_image(amp, np.zeros((n, n)), pad, 8, 3.0, nsub, pd)
+    assert flat.shape == (pad * nsub, pad * nsub)
+    assert abs(flat.sum() - amp.sum()) < 1e-12 * amp.sum()
+    assert np.allclose(flat, flat.T, atol=1e-13)            # x and y play the same part
+    nv = len(valid)
+    s = slopes.pyr_slopes_maps(flat, maps)
+    if mirror:
+        assert np.allclose(flat, flat[:, ::-1], atol=1e-13) and np.allclose(flat, flat[::-1], atol=1e-13)
+        assert abs(s[:nv].sum()) < 1e-10 and abs(s[nv:].sum()) < 1e-10
+    x = np.arange(n) - (n - 1) / 2.0
+    tilt = np.broadcast_to(0.3 * 2 * np.pi * x[None, :] / n, (n, n))
+    st = slopes.pyr_slopes_maps(pyramid.pwfs_image(amp, tilt, pad, 8, 3.0, nsub, pd), maps, s)
+    assert st[:nv].mean() > 0.01 and abs(st[nv:].mean()) < 1e-3 * st[:nv].mean()
+    return flat
+
+
+def test_andes_like_geometry():
+    """The ANDES reading scaled down: pad 4 (oversampling 4), 4 px
+    subapertures, images 1.2 pupil diameters apart: flux kept, four mirrored
+    images and zero mean slopes for a flat wavefront, +x tilt -> +x slopes."""
+    _pins_for(40, 10, 4, 48)
+
+
+def test_odd_pupil_side():
+    """An odd pupil side (33 px at pad 4) sits at offset floor((N - n)/2), so
+    its centre is half a grid pixel off the grid's: the flat-wavefront
+    images keep the flux and the x <-> y symmetry but are not mirror
+    images (that offset shows as a constant slope, which the reference
+    removes); the tilt sign holds."""
+    flat = _pins_for(33, 11, 4, 51, mirror=False)
+    assert np.abs(flat - flat[:, ::-1]).max() > 1e-3 * flat.max()
+
+
 def _valid_supersampled(mask, n_sub):
     """Brute force: split every pupil pixel into n_sub x n_sub sub-pixels of
     side 1 / n_sub; sub-pixel k (in those units) belongs to subaperture
