@@ -16,9 +16,14 @@ def cache_path():
         os.path.expanduser("~"), ".cache", "specula_gb300", "tiles.json")
 
 
+# bumped whenever the kernels' best tiling can change (v5: the two-pass form's
+# column-major slot blocks and 128-thread row filter)
+_VERSION = "v5"
+
+
 def _key(device_name, pupil, pwfs, n_batch):
-    return (f"v4|{device_name}|np{pupil.n_pix}|pad{pwfs.pad}|mod{pwfs.n_mod}|sub{pwfs.n_sub}"
-            f"|b{n_batch}")
+    return (f"{_VERSION}|{device_name}|np{pupil.n_pix}|pad{pwfs.pad}|mod{pwfs.n_mod}"
+            f"|sub{pwfs.n_sub}|b{n_batch}")
 
 
 def _load():
